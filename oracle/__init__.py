@@ -1,0 +1,211 @@
+"""FP64 CPU oracle of the TPC tracking path -- TEST INFRASTRUCTURE ONLY.
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The CUDA library never calls it and
+shares no code with it.  ``build()`` compiles ``tpc_oracle.cpp`` with plain
+g++ (OpenMP, no floating-point contraction, so FP32 neighbour decisions round
+once per operation exactly like the kernel's).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "_build", "liboracle.so")
+_lib = None
+
+N_SECTORS = 36
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("win_y", C.c_float), ("win_z", C.c_float), ("chi2_link", C.c_float),
+        ("sigma_y2", C.c_float), ("sigma_z2", C.c_float),
+        ("max_gap", C.c_int32), ("n_seg", C.c_int32), ("n_min", C.c_int32),
+        ("merge_max_row_gap", C.c_int32), ("merge_max_overlap", C.c_int32),
+        ("merge_z_slope", C.c_float), ("merge_z_margin", C.c_float),
+        ("chi2_merge", C.c_double), ("chi2_ext", C.c_double),
+        ("ext_max_miss", C.c_int32), ("bz", C.c_double),
+        ("prior", C.c_double * 5), ("seed_snp_max", C.c_double),
+        ("seed_qpt_max", C.c_double),
+        ("snp_max", C.c_double),
+    ]
+
+
+class Diag(C.Structure):
+    _fields_ = [
+        ("choice_dn", C.c_void_p), ("choice_up", C.c_void_p),
+        ("d2", C.c_void_p), ("d2_next", C.c_void_p),
+        ("link_dn", C.c_void_p), ("link_up", C.c_void_p),
+        ("seg_of", C.c_void_p), ("merge_margin", C.c_void_p),
+    ]
+
+
+def build(force: bool = False) -> str:
+    src = os.path.join(_HERE, "tpc_oracle.cpp")
+    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= max(
+            os.path.getmtime(src), os.path.getmtime(os.path.join(_HERE, "tpc_oracle.h"))):
+        return _SO
+    os.makedirs(os.path.dirname(_SO), exist_ok=True)
+    tmp = _SO + f".tmp{os.getpid()}"
+    cmd = ["g++", "-std=c++17", "-O2", "-fopenmp", "-ffp-contract=off", "-fPIC",
+           "-shared", "-o", tmp, src]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _SO)
+    return _SO
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        _lib = C.CDLL(_SO)
+        _lib.orc_find_tracks.restype = C.c_int64
+        _lib.orc_bruteforce_chains.restype = C.c_int64
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(C.c_void_p) if a is not None else None
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    lib().orc_default_params(C.byref(p))
+    for k, v in kw.items():
+        if k == "prior":
+            for i in range(5):
+                p.prior[i] = v[i]
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def set_threads(n: int):
+    lib().orc_set_threads(int(n))
+
+
+def get_threads() -> int:
+    return int(lib().orc_get_threads())
+
+
+def _c(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+def find_tracks(y, z, row, evt_sector_off, n_events, params=None, diag=False):
+    """Returns (track_of_cluster, trk_off, trk_hits[, diag dict])."""
+    y, z, row = _c(y, np.float32), _c(z, np.float32), _c(row, np.uint16)
+    off = _c(evt_sector_off, np.int64)
+    n = y.shape[0]
+    prm = params or default_params()
+    toc = np.empty(n, np.int32)
+    trk_off = np.empty(n + 1, np.int32)
+    hits = np.empty(max(n, 1), np.int32)
+    d = None
+    dg = None
+    if diag:
+        d = dict(choice_dn=np.empty(n, np.int32), choice_up=np.empty(n, np.int32),
+                 d2=np.empty(n, np.float32), d2_next=np.empty(n, np.float32),
+                 link_dn=np.empty(n, np.int32), link_up=np.empty(n, np.int32),
+                 seg_of=np.empty(n, np.int32), merge_margin=np.empty(n, np.float64))
+        dg = Diag(**{k: v.ctypes.data for k, v in d.items()})
+    T = lib().orc_find_tracks(_p(y), _p(z), _p(row), C.c_int64(n), _p(off),
+                              C.c_int32(n_events), C.byref(prm), _p(toc), _p(trk_off),
+                              _p(hits), C.byref(dg) if dg is not None else None)
+    if T < 0:
+        raise ValueError("oracle rejected the input")
+    trk_off = trk_off[:T + 1].copy()
+    hits = hits[:trk_off[-1]].copy()
+    return (toc, trk_off, hits, d) if diag else (toc, trk_off, hits)
+
+
+def fit_tracks(y, z, row, sector_of, trk_off, trk_hits, align=None, params=None,
+               reverse=False):
+    """FP64 fit; returns (params[T,5], cov[T,15], chi2[T], ndf[T])."""
+    y, z, row = _c(y, np.float32), _c(z, np.float32), _c(row, np.uint16)
+    sec = _c(sector_of, np.int32)
+    off, hits = _c(trk_off, np.int32), _c(trk_hits, np.int32)
+    T = off.shape[0] - 1
+    prm = params or default_params()
+    par = np.empty((T, 5)); cov = np.empty((T, 15)); chi2 = np.empty(T)
+    ndf = np.empty(T, np.int32)
+    al = _c(align, np.float64) if align is not None else None
+    lib().orc_fit_tracks_dir(_p(y), _p(z), _p(row), _p(sec), _p(off), _p(hits),
+                             C.c_int32(T), _p(al), C.byref(prm), C.c_int(1 if reverse else 0),
+                             _p(par), _p(cov), _p(chi2), _p(ndf))
+    return par, cov, chi2, ndf
+
+
+def fit_adjoint(y, z, row, sector_of, trk_off, trk_hits, align, params=None,
+                want_grad=True):
+    """Total chi2 and d chi2 / d align[216] (exact, dual numbers)."""
+    y, z, row = _c(y, np.float32), _c(z, np.float32), _c(row, np.uint16)
+    sec = _c(sector_of, np.int32)
+    off, hits = _c(trk_off, np.int32), _c(trk_hits, np.int32)
+    T = off.shape[0] - 1
+    prm = params or default_params()
+    al = _c(align, np.float64)
+    tot = C.c_double(0.0)
+    g = np.zeros(216) if want_grad else None
+    lib().orc_fit_adjoint(_p(y), _p(z), _p(row), _p(sec), _p(off), _p(hits),
+                          C.c_int32(T), _p(al), C.byref(prm), C.byref(tot), _p(g))
+    return (tot.value, g) if want_grad else tot.value
+
+
+def gauss_newton(y, z, row, sector_of, trk_off, trk_hits, align, params=None):
+    y, z, row = _c(y, np.float32), _c(z, np.float32), _c(row, np.uint16)
+    sec = _c(sector_of, np.int32)
+    off, hits = _c(trk_off, np.int32), _c(trk_hits, np.int32)
+    T = off.shape[0] - 1
+    prm = params or default_params()
+    al = _c(align, np.float64)
+    gn = np.zeros((216, 216))
+    lib().orc_gauss_newton(_p(y), _p(z), _p(row), _p(sec), _p(off), _p(hits),
+                           C.c_int32(T), _p(al), C.byref(prm), _p(gn))
+    return gn
+
+
+def propagate(x1, s1, p, x2, s2, params=None):
+    """One propagation; returns (p_out, jac[5,5], dx1[5], dx2[5]) or None."""
+    prm = params or default_params()
+    p = _c(p, np.float64)
+    po = np.empty(5); J = np.empty(25); d1 = np.empty(5); d2 = np.empty(5)
+    rc = lib().orc_propagate(C.c_double(x1), C.c_int(s1), _p(p), C.c_double(x2),
+                             C.c_int(s2), C.byref(prm), _p(po), _p(J), _p(d1), _p(d2))
+    if rc != 0:
+        return None
+    return po, J.reshape(5, 5), d1, d2
+
+
+def bruteforce_chains(y, z, row, sector, params=None, chi2ndf_max=5.0,
+                      cap_chains=100000, cap_hits=5000000):
+    y, z, row = _c(y, np.float32), _c(z, np.float32), _c(row, np.uint16)
+    prm = params or default_params()
+    off = np.empty(cap_chains + 1, np.int32)
+    hits = np.empty(cap_hits, np.int32)
+    k = lib().orc_bruteforce_chains(_p(y), _p(z), _p(row), C.c_int64(y.shape[0]),
+                                    C.c_int32(sector), C.byref(prm), C.c_double(chi2ndf_max),
+                                    C.c_int64(cap_chains), C.c_int64(cap_hits), _p(off), _p(hits))
+    if k < 0:
+        raise RuntimeError("brute-force capacity too small")
+    return [hits[off[i]:off[i + 1]].copy() for i in range(k)]
+
+
+def seed(y, z, row, sector_of, hits, first_is_outer=True, params=None):
+    """The fit seed: (x0, frame, p[5]) of a hit list in fit order."""
+    y, z, row = _c(y, np.float32), _c(z, np.float32), _c(row, np.uint16)
+    sec = _c(sector_of, np.int32)
+    hits = _c(hits, np.int32)
+    prm = params or default_params()
+    x0 = C.c_double(0.0); fr = C.c_int32(0); p = np.empty(5)
+    rc = lib().orc_seed(_p(y), _p(z), _p(row), _p(sec), _p(hits), C.c_int32(hits.shape[0]),
+                        C.c_int(1 if first_is_outer else 0), C.byref(prm), C.byref(x0),
+                        C.byref(fr), _p(p))
+    if rc != 0:
+        raise ValueError("seed needs >= 3 clusters")
+    return x0.value, fr.value, p

@@ -1,0 +1,1166 @@
+// TPC tracking oracle (FP64 CPU restatement).  TEST INFRASTRUCTURE ONLY:
+// loaded by the tests, the smoke check and the benchmark's CPU-baseline leg;
+// the CUDA library never calls it and the two share no code.
+//
+// The paper (arXiv 2412.13755) says TPC tracking runs on the GPUs of the
+// online farm and takes 99% of their compute (Sec. 4.2 and Sec. 5), but
+// describes no algorithm.  Each step below states the reading it follows:
+//   S1  binning per (event, sector, pad row), canonical id = input index;
+//   S2  cellular-automaton neighbour choice between pad rows (triplet D^2);
+//   S3  chaining of mutual links into segments;
+//   S4  greedy merging of segments within a sector or across phi-adjacent
+//       sectors by a 5-d chi2 on fitted states;
+//   S5  Kalman fit of (y, z, sin phi, tan lambda, q/pT) with 5x5 covariance
+//       in a uniform Bz, exact helix transport;
+//   S6  d(sum chi2)/d(216 per-sector rigid-body corrections), exact
+//       derivative of the fit as computed (forward-mode dual numbers).
+// Floating point that decides an integer in S2 (window cuts, D^2 and its
+// comparisons) is evaluated in FP32 with one rounding per operation, the
+// precision the GPU kernel decides in; everything else is FP64.
+#include "tpc_oracle.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <functional>
+#include <limits>
+#include <vector>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+namespace {
+
+constexpr int NSEC = 36;
+constexpr int NPHI = 18;
+constexpr int NROW = 152;
+constexpr double KAPPA = 2.99792458e-3;  // cm^-1 T^-1 (GeV/c)
+constexpr double PI = 3.14159265358979323846;
+const double TAN_HALF = std::tan(10.0 * PI / 180.0);
+
+int g_threads = 0;
+
+// ---- geometry (pad-row planes, sector frames) ---------------------------
+double row_x(int r) { return 85.0 + r * (162.0 / 151.0); }
+float row_xf(int r) { return (float)row_x(r); }
+double sector_alpha(int s) { return ((s % NPHI) + 0.5) * (20.0 * PI / 180.0); }
+double delta_alpha(int from, int to) {
+    double d = sector_alpha(to) - sector_alpha(from);
+    while (d > PI) d -= 2 * PI;
+    while (d <= -PI) d += 2 * PI;
+    return d;
+}
+
+// ---- dual numbers for the exact derivative of the fit (S6) ---------------
+template <int N>
+struct Dual {
+    double v;
+    double d[N];
+    Dual() : v(0) { for (int i = 0; i < N; ++i) d[i] = 0; }
+    Dual(double x) : v(x) { for (int i = 0; i < N; ++i) d[i] = 0; }
+};
+template <int N> Dual<N> operator+(const Dual<N>& a, const Dual<N>& b) {
+    Dual<N> r; r.v = a.v + b.v; for (int i = 0; i < N; ++i) r.d[i] = a.d[i] + b.d[i]; return r; }
+template <int N> Dual<N> operator-(const Dual<N>& a, const Dual<N>& b) {
+    Dual<N> r; r.v = a.v - b.v; for (int i = 0; i < N; ++i) r.d[i] = a.d[i] - b.d[i]; return r; }
+template <int N> Dual<N> operator-(const Dual<N>& a) {
+    Dual<N> r; r.v = -a.v; for (int i = 0; i < N; ++i) r.d[i] = -a.d[i]; return r; }
+template <int N> Dual<N> operator*(const Dual<N>& a, const Dual<N>& b) {
+    Dual<N> r; r.v = a.v * b.v; for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * b.v + a.v * b.d[i]; return r; }
+template <int N> Dual<N> operator/(const Dual<N>& a, const Dual<N>& b) {
+    Dual<N> r; r.v = a.v / b.v;
+    for (int i = 0; i < N; ++i) r.d[i] = (a.d[i] * b.v - a.v * b.d[i]) / (b.v * b.v);
+    return r; }
+template <int N> Dual<N> operator+(const Dual<N>& a, double b) { return a + Dual<N>(b); }
+template <int N> Dual<N> operator+(double a, const Dual<N>& b) { return Dual<N>(a) + b; }
+template <int N> Dual<N> operator-(const Dual<N>& a, double b) { return a - Dual<N>(b); }
+template <int N> Dual<N> operator-(double a, const Dual<N>& b) { return Dual<N>(a) - b; }
+template <int N> Dual<N> operator*(const Dual<N>& a, double b) {
+    Dual<N> r; r.v = a.v * b; for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * b; return r; }
+template <int N> Dual<N> operator*(double a, const Dual<N>& b) { return b * a; }
+template <int N> Dual<N> operator/(const Dual<N>& a, double b) { return a * (1.0 / b); }
+template <int N> Dual<N> operator/(double a, const Dual<N>& b) { return Dual<N>(a) / b; }
+template <int N> Dual<N>& operator+=(Dual<N>& a, const Dual<N>& b) { a = a + b; return a; }
+template <int N> Dual<N>& operator-=(Dual<N>& a, const Dual<N>& b) { a = a - b; return a; }
+template <int N> Dual<N> sqrt(const Dual<N>& a) {
+    Dual<N> r; r.v = std::sqrt(a.v); double f = 0.5 / r.v;
+    for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * f;
+    return r; }
+template <int N> Dual<N> asin(const Dual<N>& a) {
+    Dual<N> r; r.v = std::asin(a.v); double f = 1.0 / std::sqrt(1.0 - a.v * a.v);
+    for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * f;
+    return r; }
+template <int N> Dual<N> sin(const Dual<N>& a) {
+    Dual<N> r; r.v = std::sin(a.v); double f = std::cos(a.v);
+    for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * f;
+    return r; }
+template <int N> Dual<N> cos(const Dual<N>& a) {
+    Dual<N> r; r.v = std::cos(a.v); double f = -std::sin(a.v);
+    for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * f;
+    return r; }
+template <int N> double val(const Dual<N>& a) { return a.v; }
+inline double val(double a) { return a; }
+using std::asin;
+using std::cos;
+using std::sin;
+using std::sqrt;
+
+// ---- symmetric 5x5 storage ----------------------------------------------
+// order 00 01 02 03 04 11 12 13 14 22 23 24 33 34 44
+inline int sidx(int i, int j) {
+    if (i > j) std::swap(i, j);
+    static const int base[5] = {0, 5, 9, 12, 14};
+    return base[i] + (j - i);
+}
+
+// ---- S5: helix transport between planes x1 -> x2 of one frame ------------
+// Exact for a uniform Bz without material:
+//   s2 = s1 - k dx,  k = KAPPA Bz w
+//   y2 = y1 + dx (s1+s2)/(c1+c2)              (tan of the mean direction)
+//   chord L = |dx| sqrt(1 + ((s1+s2)/(c1+c2))^2), arc = L asin(u)/u, u = |k|L/2
+//   z2 = z1 + t * arc * sign(dx)
+// F is the analytic Jacobian d(p2)/d(p1); dX2 = d(p2)/d(x2) = -d(p2)/d(x1).
+template <class T>
+bool transport(const T& x1, const T& x2, T p[5], T F[25], T dX2[5],
+               const orc_params& prm) {
+    const T dx = x2 - x1;
+    const T s1 = p[2], t = p[3], w = p[4];
+    const double kb = KAPPA * prm.bz;
+    const T k = w * kb;
+    const T s2 = s1 - k * dx;
+    if (std::fabs(val(s1)) >= prm.snp_max || std::fabs(val(s2)) >= prm.snp_max) return false;
+    const T c1 = sqrt(1.0 - s1 * s1);
+    const T c2 = sqrt(1.0 - s2 * s2);
+    const T A = s1 + s2, B = c1 + c2;
+    const T tn = A / B;
+    const double sg = val(dx) >= 0 ? 1.0 : -1.0;
+    const T adx = dx * sg;
+    const T h = sqrt(1.0 + tn * tn);
+    const T L = adx * h;
+    const T v = k * k * L * L * 0.25;  // u^2
+    T g, m;                            // g = asin(u)/u, m = (1/sqrt(1-v) - g)/v
+    const T e = 1.0 / sqrt(1.0 - v);
+    if (val(v) < 1e-6) {
+        g = 1.0 + v * (1.0 / 6.0) + v * v * (3.0 / 40.0) + v * v * v * (5.0 / 112.0);
+        m = (1.0 / 3.0) + v * 0.3 + v * v * (15.0 / 56.0);
+    } else {
+        const T u = sqrt(v);
+        g = asin(u) / u;
+        m = (e - g) / v;
+    }
+    const T arc = L * g;
+    // derivatives of tn
+    const T dtn_s1p = (1.0 + tn * s1 / c1) / B;  // partial wrt s1 at fixed s2
+    const T dtn_s2p = (1.0 + tn * s2 / c2) / B;  // partial wrt s2 at fixed s1
+    const T ds2_w = dx * (-kb);
+    const T dtn_s1 = dtn_s1p + dtn_s2p;
+    const T dtn_w = dtn_s2p * ds2_w;
+    const T dtn_dx = dtn_s2p * (-k);
+    const T dy_s1 = dx * dtn_s1;
+    const T dy_w = dx * dtn_w;
+    const T dy_dx = tn + dx * dtn_dx;
+    const T dL_tn = adx * tn / h;
+    const T dL_s1 = dL_tn * dtn_s1;
+    const T dL_w = dL_tn * dtn_w;
+    const T dL_dx = h * sg + dL_tn * dtn_dx;
+    const T darc_k = k * L * L * L * m * 0.25;  // d(arc)/dk at fixed L
+    const T darc_s1 = e * dL_s1;
+    const T darc_w = e * dL_w + darc_k * kb;
+    const T darc_dx = e * dL_dx;
+    const T tsg = t * sg;
+
+    for (int i = 0; i < 25; ++i) F[i] = T(0.0);
+    F[0 * 5 + 0] = T(1.0);
+    F[0 * 5 + 2] = dy_s1;
+    F[0 * 5 + 4] = dy_w;
+    F[1 * 5 + 1] = T(1.0);
+    F[1 * 5 + 2] = tsg * darc_s1;
+    F[1 * 5 + 3] = arc * sg;
+    F[1 * 5 + 4] = tsg * darc_w;
+    F[2 * 5 + 2] = T(1.0);
+    F[2 * 5 + 4] = ds2_w;
+    F[3 * 5 + 3] = T(1.0);
+    F[4 * 5 + 4] = T(1.0);
+    dX2[0] = dy_dx;
+    dX2[1] = tsg * darc_dx;
+    dX2[2] = -k;
+    dX2[3] = T(0.0);
+    dX2[4] = T(0.0);
+
+    p[0] = p[0] + dx * tn;
+    p[1] = p[1] + tsg * arc;
+    p[2] = s2;
+    return true;
+}
+
+// Move the state from plane x of frame `frame` to plane x_to of frame `to`:
+// on a sector change rotate the frame by da (x' = x cos + y sin,
+// y' = -x sin + y cos, phi' = phi - da), then transport from x'(y) to x_to.
+// J is the full Jacobian of the composition with respect to p.
+template <class T>
+bool move_state(T& x, T p[5], int& frame, const T& x_to, int to, T J[25],
+                T dXto[5], const orc_params& prm) {
+    T F[25];
+    if (to != frame) {
+        const double da = delta_alpha(frame, to);
+        const double ca = std::cos(da), sa = std::sin(da);
+        const T s = p[2];
+        if (std::fabs(val(s)) >= prm.snp_max) return false;
+        const T c = sqrt(1.0 - s * s);
+        const T xn = x * ca + p[0] * sa;
+        const T yn = p[0] * ca - x * sa;
+        const T sn = s * ca - c * sa;
+        if (std::fabs(val(sn)) >= prm.snp_max) return false;
+        const T dsn_ds = ca + s * sa / c;
+        T q[5] = {yn, p[1], sn, p[3], p[4]};
+        if (!transport(xn, x_to, q, F, dXto, prm)) return false;
+        // d p_to / d p = F * Jrot + dT/dx1 (x) d xn / d p,  dT/dx1 = -dXto
+        for (int i = 0; i < 5; ++i) {
+            for (int j = 0; j < 5; ++j) J[i * 5 + j] = F[i * 5 + j];
+            J[i * 5 + 0] = F[i * 5 + 0] * ca - dXto[i] * sa;
+            J[i * 5 + 2] = F[i * 5 + 2] * dsn_ds;
+        }
+        for (int i = 0; i < 5; ++i) p[i] = q[i];
+    } else {
+        if (!transport(x, x_to, p, F, dXto, prm)) return false;
+        for (int i = 0; i < 25; ++i) J[i] = F[i];
+    }
+    x = x_to;
+    frame = to;
+    return true;
+}
+
+template <class T>
+void cov_transform(T C[15], const T J[25]) {
+    T full[25], tmp[25];
+    for (int i = 0; i < 5; ++i)
+        for (int j = 0; j < 5; ++j) full[i * 5 + j] = C[sidx(i, j)];
+    for (int i = 0; i < 5; ++i)
+        for (int j = 0; j < 5; ++j) {
+            T acc(0.0);
+            for (int l = 0; l < 5; ++l) acc += J[i * 5 + l] * full[l * 5 + j];
+            tmp[i * 5 + j] = acc;
+        }
+    for (int i = 0; i < 5; ++i)
+        for (int j = i; j < 5; ++j) {
+            T acc(0.0);
+            for (int l = 0; l < 5; ++l) acc += tmp[i * 5 + l] * J[j * 5 + l];
+            C[sidx(i, j)] = acc;
+        }
+}
+
+// Kalman update with the 2-d measurement (my, mz) of (y, z):
+// S = H C H^T + R, K = C H^T S^-1, p += K r, C -= K H C, chi2 += r^T S^-1 r
+// (r = predicted residual).
+template <class T>
+void kf_update(T p[5], T C[15], const T& my, const T& mz, double sy2, double sz2,
+               T& chi2, T res_out[2] = nullptr, T sinv_out[3] = nullptr) {
+    const T r0 = my - p[0], r1 = mz - p[1];
+    const T S00 = C[sidx(0, 0)] + sy2, S01 = C[sidx(0, 1)], S11 = C[sidx(1, 1)] + sz2;
+    const T det = S00 * S11 - S01 * S01;
+    const T i00 = S11 / det, i01 = -S01 / det, i11 = S00 / det;
+    T K0[5], K1[5], C0[5], C1[5];
+    for (int i = 0; i < 5; ++i) {
+        C0[i] = C[sidx(0, i)];
+        C1[i] = C[sidx(1, i)];
+    }
+    for (int i = 0; i < 5; ++i) {
+        K0[i] = C0[i] * i00 + C1[i] * i01;
+        K1[i] = C0[i] * i01 + C1[i] * i11;
+    }
+    for (int i = 0; i < 5; ++i) p[i] = p[i] + K0[i] * r0 + K1[i] * r1;
+    for (int i = 0; i < 5; ++i)
+        for (int j = i; j < 5; ++j) C[sidx(i, j)] = C[sidx(i, j)] - (K0[i] * C0[j] + K1[i] * C1[j]);
+    chi2 = chi2 + r0 * r0 * i00 + 2.0 * r0 * r1 * i01 + r1 * r1 * i11;
+    if (res_out) { res_out[0] = r0; res_out[1] = r1; }
+    if (sinv_out) { sinv_out[0] = i00; sinv_out[1] = i01; sinv_out[2] = i11; }
+}
+
+// ---- fit seed ------------------------------------------------------------
+// Circle through the innermost, middle and outermost clusters (nominal row
+// planes, uncorrected coordinates) gives q/pT and sin phi; tan lambda is the
+// z difference over the arc between the two end clusters; (y, z) are those
+// of the first cluster in fit order.  The seed is a pattern-recognition
+// product and does not depend on the alignment corrections.
+struct Seed {
+    double x, p[5];
+    int frame;
+};
+
+void local_to_frame(int from, double x, double y, int to, double& xo, double& yo) {
+    const double a = sector_alpha(from), b = sector_alpha(to);
+    const double X = x * std::cos(a) - y * std::sin(a);
+    const double Y = x * std::sin(a) + y * std::cos(a);
+    xo = X * std::cos(b) + Y * std::sin(b);
+    yo = -X * std::sin(b) + Y * std::cos(b);
+}
+
+// hits in fit order (first = start of the fit)
+Seed make_seed(const float* y, const float* z, const uint16_t* row, const int32_t* sec,
+               const int32_t* hits, int n, bool first_is_outer, const orc_params& prm) {
+    Seed sd;
+    const int h0 = hits[0], hm = hits[n / 2], hl = hits[n - 1];
+    sd.frame = sec[h0];
+    sd.x = row_x(row[h0]);
+    double px[3], py[3], pz[3];
+    const int hh[3] = {h0, hm, hl};
+    for (int i = 0; i < 3; ++i) {
+        local_to_frame(sec[hh[i]], row_x(row[hh[i]]), (double)y[hh[i]], sd.frame, px[i], py[i]);
+        pz[i] = (double)z[hh[i]];
+    }
+    // motion order: innermost q0 -> middle q1 -> outermost q2
+    const int i0 = first_is_outer ? 2 : 0, i2 = first_is_outer ? 0 : 2;
+    const double ax = px[1] - px[i0], ay = py[1] - py[i0];
+    const double bx = px[i2] - px[1], by = py[i2] - py[1];
+    const double cx = px[i2] - px[i0], cy = py[i2] - py[i0];
+    const double la = std::sqrt(ax * ax + ay * ay), lb = std::sqrt(bx * bx + by * by);
+    const double L = std::sqrt(cx * cx + cy * cy);
+    const double cross = ax * by - ay * bx;
+    double k = 0.0;
+    if (la > 0 && lb > 0 && L > 0) k = -2.0 * cross / (la * lb * L);
+    double hk = k * L * 0.5;
+    hk = std::max(-0.999, std::min(0.999, hk));
+    const double theta = std::atan2(cy, cx);
+    const double half = std::asin(hk);
+    const double phi = first_is_outer ? theta - half : theta + half;
+    double s = std::sin(phi);
+    s = std::max(-prm.seed_snp_max, std::min(prm.seed_snp_max, s));
+    const double au = std::fabs(hk);
+    const double arc = (au < 1e-9 || k == 0.0) ? L : 2.0 * std::asin(au) / std::fabs(k);
+    const double t = arc > 0 ? (pz[i2] - pz[i0]) / arc : 0.0;
+    double w = (prm.bz != 0.0) ? k / (KAPPA * prm.bz) : 0.0;
+    w = std::max(-prm.seed_qpt_max, std::min(prm.seed_qpt_max, w));
+    sd.p[0] = (double)y[h0];
+    sd.p[1] = (double)z[h0];
+    sd.p[2] = s;
+    sd.p[3] = t;
+    sd.p[4] = w;
+    return sd;
+}
+
+// corrected cluster position (sector-local): p' = R(a,b,g) (x_r, y, z) + D,
+// R = Rz(g) Ry(b) Rx(a)
+template <class T>
+void corrected(const T th[6], double xr, double y, double z, T& xo, T& yo, T& zo) {
+    const T ca = cos(th[3]), sa = sin(th[3]);
+    const T cb = cos(th[4]), sb = sin(th[4]);
+    const T cg = cos(th[5]), sg = sin(th[5]);
+    // Rx
+    const T x1 = T(xr);
+    const T y1 = ca * y - sa * z;
+    const T z1 = sa * y + ca * z;
+    // Ry
+    const T x2 = cb * x1 + sb * z1;
+    const T z2 = cb * z1 - sb * x1;
+    // Rz
+    xo = cg * x2 - sg * y1 + th[0];
+    yo = sg * x2 + cg * y1 + th[1];
+    zo = z2 + th[2];
+}
+
+// One full fit.  th(i) returns the 6 correction parameters of cluster hit i's
+// sector as T (or null alignment).  Returns false when a transport fails.
+template <class T, class ThFn>
+bool kf_fit(const float* y, const float* z, const uint16_t* row, const int32_t* sec,
+            const int32_t* hits, int n, bool first_is_outer, const orc_params& prm,
+            ThFn th, T p[5], T C[15], T& chi2, T* xlast = nullptr) {
+    const Seed sd = make_seed(y, z, row, sec, hits, n, first_is_outer, prm);
+    for (int i = 0; i < 5; ++i) p[i] = T(sd.p[i]);
+    for (int i = 0; i < 15; ++i) C[i] = T(0.0);
+    for (int i = 0; i < 5; ++i) C[sidx(i, i)] = T(prm.prior[i]);
+    T x = T(sd.x);
+    int frame = sd.frame;
+    chi2 = T(0.0);
+    T J[25], dX[5];
+    for (int j = 0; j < n; ++j) {
+        const int h = hits[j];
+        T xc, yc, zc;
+        const T* t6 = th(h);
+        if (t6) {
+            corrected<T>(t6, row_x(row[h]), (double)y[h], (double)z[h], xc, yc, zc);
+        } else {
+            xc = T(row_x(row[h]));
+            yc = T((double)y[h]);
+            zc = T((double)z[h]);
+        }
+        if (!move_state(x, p, frame, xc, sec[h], J, dX, prm)) return false;
+        cov_transform(C, J);
+        kf_update(p, C, yc, zc, prm.sigma_y2, prm.sigma_z2, chi2);
+    }
+    if (xlast) *xlast = x;
+    return true;
+}
+
+// ---- S2 neighbour decision in FP32 ----------------------------------------
+// Gap pairs in the order of increasing g_d + g_u, then increasing g_u.
+struct Gap { int d, u; };
+std::vector<Gap> gap_order(int max_gap) {
+    std::vector<Gap> g;
+    for (int sum = 2; sum <= 2 * max_gap; ++sum)
+        for (int gu = 1; gu <= max_gap; ++gu) {
+            const int gd = sum - gu;
+            if (gd >= 1 && gd <= max_gap) g.push_back({gd, gu});
+        }
+    return g;
+}
+
+// D^2 of the triplet (d, c, u): straight-line interpolation of c from d and
+// u, residuals normalised by the variance of (c - interpolation).
+// Evaluated in FP32, one rounding per operation (compiled without
+// contraction).
+float triplet_d2(float xd, float yd, float zd, float xc, float yc, float zc,
+                 float xu, float yu, float zu, float sy2, float sz2) {
+    const float a = (xc - xd) / (xu - xd);
+    const float yh = yd + a * (yu - yd);
+    const float zh = zd + a * (zu - zd);
+    const float ry = yc - yh;
+    const float rz = zc - zh;
+    const float b = 1.0f - a;
+    const float f = (1.0f + a * a) + b * b;
+    return (ry * ry) / (sy2 * f) + (rz * rz) / (sz2 * f);
+}
+
+bool in_window(float xa, float ya, float za, float xb, float yb, float zb, float wy, float wz) {
+    const float dx = std::fabs(xb - xa);
+    return std::fabs(yb - ya) <= wy * dx && std::fabs(zb - za) <= wz * dx;
+}
+
+struct Segment {
+    int event, sector;
+    std::vector<int32_t> hits;  // outermost first (input-order indices)
+    int32_t canon;              // smallest input index
+    bool ok_in = false, ok_out = false;
+    double p_in[5], c_in[15];   // inward fit: state at the innermost cluster
+    double p_out[5], c_out[15]; // outward fit: state at the outermost cluster
+    int row_min, row_max;
+};
+
+// S1-S3 for one (event, sector) group.
+void group_ca(const float* y, const float* z, const uint16_t* row, int64_t beg, int64_t end,
+              int event, int sector, const orc_params& prm, std::vector<Segment>& segs,
+              std::vector<std::vector<int32_t>>& rows, orc_diag* diag) {
+    const int64_t n = end - beg;
+    rows.assign(NROW, std::vector<int32_t>());
+    if (n <= 0) return;
+    // S1: rows, canonical order = input order
+    for (int64_t i = beg; i < end; ++i) rows[row[i]].push_back((int32_t)i);
+    std::vector<int32_t> cdn(n, -1), cup(n, -1), ldn(n, -1), lup(n, -1);
+    std::vector<float> d2v(n, std::numeric_limits<float>::infinity());
+    std::vector<float> d2n(n, std::numeric_limits<float>::infinity());
+    const std::vector<Gap> gaps = gap_order(prm.max_gap);
+    // S2a: each cluster chooses its best (down, up) pair
+    for (int64_t c = beg; c < end; ++c) {
+        const int r = row[c];
+        const float xc = row_xf(r), yc = y[c], zc = z[c];
+        float best_seen = std::numeric_limits<float>::infinity();
+        for (const Gap& gp : gaps) {
+            const int rd = r - gp.d, ru = r + gp.u;
+            if (rd < 0 || ru >= NROW) continue;
+            const float xd = row_xf(rd), xu = row_xf(ru);
+            bool found = false;
+            float bd2 = 0, second = std::numeric_limits<float>::infinity();
+            int32_t bd = -1, bu = -1;
+            for (int32_t d : rows[rd]) {
+                if (!in_window(xc, yc, zc, xd, y[d], z[d], prm.win_y, prm.win_z)) continue;
+                for (int32_t u : rows[ru]) {
+                    if (!in_window(xc, yc, zc, xu, y[u], z[u], prm.win_y, prm.win_z)) continue;
+                    const float d2 = triplet_d2(xd, y[d], z[d], xc, yc, zc, xu, y[u], z[u],
+                                                prm.sigma_y2, prm.sigma_z2);
+                    if (d2 < best_seen) best_seen = d2;
+                    if (!(d2 <= prm.chi2_link)) {
+                        if (found && d2 < second) second = d2;
+                        continue;
+                    }
+                    const bool better = !found || d2 < bd2 || (d2 == bd2 && (u < bu || (u == bu && d < bd)));
+                    if (better) {
+                        if (found) second = std::min(second, bd2);
+                        found = true;
+                        bd2 = d2; bd = d; bu = u;
+                    } else {
+                        second = std::min(second, d2);
+                    }
+                }
+            }
+            if (found) {
+                cdn[c - beg] = bd;
+                cup[c - beg] = bu;
+                d2v[c - beg] = bd2;
+                d2n[c - beg] = second;
+                break;
+            }
+        }
+        if (cdn[c - beg] < 0) d2v[c - beg] = best_seen;
+    }
+    // S2b: endpoints without a triplet of their own accept the best claimant
+    // (smallest D^2, then smallest canonical id)
+    std::vector<int32_t> claim_up(n, -1), claim_dn(n, -1);
+    auto better_claim = [&](int32_t a, int32_t b) {  // a better than b?
+        if (b < 0) return true;
+        const float da = d2v[a - beg], db = d2v[b - beg];
+        return da < db || (da == db && a < b);
+    };
+    for (int64_t c = beg; c < end; ++c) {
+        const int32_t u = cup[c - beg], d = cdn[c - beg];
+        if (u >= 0 && cdn[u - beg] < 0 && better_claim((int32_t)c, claim_up[u - beg])) claim_up[u - beg] = (int32_t)c;
+        if (d >= 0 && cup[d - beg] < 0 && better_claim((int32_t)c, claim_dn[d - beg])) claim_dn[d - beg] = (int32_t)c;
+    }
+    // S2c: links: mutual choices, or claims of endpoints
+    for (int64_t c = beg; c < end; ++c) {
+        const int32_t u = cup[c - beg], d = cdn[c - beg];
+        if (u >= 0) {
+            if (cdn[u - beg] == (int32_t)c || (cdn[u - beg] < 0 && claim_up[u - beg] == (int32_t)c)) {
+                lup[c - beg] = u;
+                ldn[u - beg] = (int32_t)c;
+            }
+        }
+        if (d >= 0) {
+            if (cup[d - beg] == (int32_t)c || (cup[d - beg] < 0 && claim_dn[d - beg] == (int32_t)c)) {
+                ldn[c - beg] = d;
+                lup[d - beg] = (int32_t)c;
+            }
+        }
+    }
+    if (diag) {
+        for (int64_t c = beg; c < end; ++c) {
+            if (diag->choice_dn) diag->choice_dn[c] = cdn[c - beg];
+            if (diag->choice_up) diag->choice_up[c] = cup[c - beg];
+            if (diag->d2) diag->d2[c] = d2v[c - beg];
+            if (diag->d2_next) diag->d2_next[c] = d2n[c - beg];
+            if (diag->link_dn) diag->link_dn[c] = ldn[c - beg];
+            if (diag->link_up) diag->link_up[c] = lup[c - beg];
+        }
+    }
+    // S3: chains from clusters with no down link and an up link
+    for (int64_t c = beg; c < end; ++c) {
+        if (ldn[c - beg] >= 0 || lup[c - beg] < 0) continue;
+        std::vector<int32_t> chain;
+        int32_t cur = (int32_t)c;
+        while (cur >= 0) {
+            chain.push_back(cur);
+            cur = lup[cur - beg];
+        }
+        if ((int)chain.size() < prm.n_seg) continue;
+        Segment s;
+        s.event = event;
+        s.sector = sector;
+        s.hits.assign(chain.rbegin(), chain.rend());  // outermost first
+        s.canon = *std::min_element(chain.begin(), chain.end());
+        s.row_min = row[chain.front()];
+        s.row_max = row[chain.back()];
+        segs.push_back(std::move(s));
+    }
+}
+
+// 5x5 SPD solve by Cholesky; returns false when not positive definite.
+bool chi2_5(const double dp[5], const double M[15], double& out) {
+    double Lm[5][5] = {};
+    for (int i = 0; i < 5; ++i)
+        for (int j = 0; j <= i; ++j) {
+            double s = M[sidx(i, j)];
+            for (int l = 0; l < j; ++l) s -= Lm[i][l] * Lm[j][l];
+            if (i == j) {
+                if (!(s > 0)) return false;
+                Lm[i][i] = std::sqrt(s);
+            } else {
+                Lm[i][j] = s / Lm[j][j];
+            }
+        }
+    double v[5];
+    for (int i = 0; i < 5; ++i) {
+        double s = dp[i];
+        for (int l = 0; l < i; ++l) s -= Lm[i][l] * v[l];
+        v[i] = s / Lm[i][i];
+    }
+    out = 0;
+    for (int i = 0; i < 5; ++i) out += v[i] * v[i];
+    return true;
+}
+
+// S3b: Kalman-guided extension.  From the state at plane x (frame =
+// sector), visit rows r_start, r_start+dir, ... ; in each row take the
+// cluster of the group with the smallest predicted-residual chi2
+// r^T (C_yz + R)^-1 r (ties: smaller canonical id) if it is <= chi2_ext and
+// update with it; stop after ext_max_miss consecutive rows without one, at
+// the last row, when the transport fails, or when the prediction leaves the
+// sector's acceptance.
+void extend_tracklet(const float* y, const float* z, const std::vector<std::vector<int32_t>>& rows,
+                     int sector, double& x, double p[5], double C[15], int r_start, int dir,
+                     const orc_params& prm, std::vector<int32_t>& added) {
+    int misses = 0;
+    for (int r = r_start; r >= 0 && r < NROW; r += dir) {
+        double J[25], dX[5];
+        int frame = sector;
+        if (!move_state<double>(x, p, frame, row_x(r), sector, J, dX, prm)) break;
+        // the track has left the sector when its prediction is outside the
+        // row's acceptance |y| <= x tan(10 deg)
+        if (std::fabs(p[0]) > row_x(r) * TAN_HALF) break;
+        cov_transform(C, J);
+        const double S00 = C[sidx(0, 0)] + prm.sigma_y2, S01 = C[sidx(0, 1)], S11 = C[sidx(1, 1)] + prm.sigma_z2;
+        const double det = S00 * S11 - S01 * S01;
+        int32_t best = -1;
+        double bchi = 0;
+        for (int32_t c : rows[r]) {
+            const double r0 = (double)y[c] - p[0], r1 = (double)z[c] - p[1];
+            const double chi = (r0 * r0 * S11 - 2.0 * r0 * r1 * S01 + r1 * r1 * S00) / det;
+            if (!(chi <= prm.chi2_ext)) continue;
+            if (best < 0 || chi < bchi || (chi == bchi && c < best)) {
+                best = c;
+                bchi = chi;
+            }
+        }
+        if (best >= 0) {
+            double chi2 = 0;
+            kf_update(p, C, (double)y[best], (double)z[best], prm.sigma_y2, prm.sigma_z2, chi2);
+            added.push_back(best);
+            misses = 0;
+        } else if (++misses >= prm.ext_max_miss) {
+            break;
+        }
+    }
+}
+
+struct MergePair {
+    double chi2;
+    int a, b;  // segment indices: a inner, b outer
+};
+
+// S4 candidate test: A's outward-fit state at its outermost cluster is moved
+// to B's innermost plane and compared with B's inward-fit state there.
+bool merge_chi2(const Segment& A, const Segment& B, const float* z, const orc_params& prm,
+                double& chi2) {
+    if (A.event != B.event) return false;
+    if ((A.sector < NPHI) != (B.sector < NPHI)) return false;
+    const int dphi = ((B.sector % NPHI) - (A.sector % NPHI) + NPHI) % NPHI;
+    if (!(dphi == 0 || dphi == 1 || dphi == NPHI - 1)) return false;
+    // rows: B starts at or above A's last row; across a sector boundary the
+    // two row ranges may overlap by up to merge_max_overlap rows (a track
+    // grazing the boundary crosses the row planes of both sectors)
+    const int gap = B.row_min - A.row_max;
+    const int min_gap = (dphi == 0) ? 0 : -prm.merge_max_overlap;
+    if (gap < min_gap || gap > prm.merge_max_row_gap) return false;
+    // z gate in FP32
+    const float zb = z[B.hits.back()], za = z[A.hits.front()];
+    const float dxr = std::fabs(row_xf(B.row_min) - row_xf(A.row_max));
+    if (!(std::fabs(zb - za) <= prm.merge_z_slope * dxr + prm.merge_z_margin)) return false;
+    if (!A.ok_out || !B.ok_in) return false;
+    double p[5], C[15], J[25], dX[5];
+    std::memcpy(p, A.p_out, sizeof p);
+    std::memcpy(C, A.c_out, sizeof C);
+    double x = row_x(A.row_max);
+    int frame = A.sector;
+    if (!move_state<double>(x, p, frame, row_x(B.row_min), B.sector, J, dX, prm)) return false;
+    cov_transform(C, J);
+    double dp[5], M[15];
+    for (int i = 0; i < 5; ++i) dp[i] = B.p_in[i] - p[i];
+    for (int i = 0; i < 15; ++i) M[i] = C[i] + B.c_in[i];
+    if (!chi2_5(dp, M, chi2)) return false;
+    return chi2 <= prm.chi2_merge;
+}
+
+}  // namespace
+
+extern "C" {
+
+void orc_default_params(orc_params* p) {
+    p->win_y = 3.0f;
+    p->win_z = 3.5f;
+    p->chi2_link = 16.0f;
+    p->sigma_y2 = 0.01f;
+    p->sigma_z2 = 0.0225f;
+    p->max_gap = 3;
+    p->n_seg = 5;
+    p->n_min = 10;
+    p->merge_max_row_gap = 24;
+    p->merge_max_overlap = 8;
+    p->merge_z_slope = 3.5f;
+    p->merge_z_margin = 2.0f;
+    p->chi2_merge = 30.0;
+    p->chi2_ext = 16.0;
+    p->ext_max_miss = 3;
+    p->bz = 0.5;
+    p->prior[0] = 4.0;
+    p->prior[1] = 4.0;
+    p->prior[2] = 0.25;
+    p->prior[3] = 0.25;
+    p->prior[4] = 25.0;
+    p->seed_snp_max = 0.99;
+    p->seed_qpt_max = 5.0;
+    p->snp_max = 0.999;
+}
+
+void orc_set_threads(int n) { g_threads = n; }
+int orc_get_threads(void) {
+#ifdef _OPENMP
+    return g_threads > 0 ? g_threads : omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+int64_t orc_find_tracks(const float* y, const float* z, const uint16_t* row, int64_t n,
+                        const int64_t* off, int32_t n_events, const orc_params* prm_,
+                        int32_t* track_of_cluster, int32_t* trk_off, int32_t* trk_hits,
+                        orc_diag* diag) {
+    const orc_params& prm = *prm_;
+    const int G = n_events * NSEC;
+    if (off[0] != 0 || off[G] != n) return -1;
+    for (int g = 0; g < G; ++g)
+        if (off[g + 1] < off[g]) return -1;
+    for (int64_t i = 0; i < n; ++i)
+        if (row[i] >= NROW || !std::isfinite(y[i]) || !std::isfinite(z[i])) return -1;
+    const int nt = orc_get_threads();
+    // S1-S3 per group
+    std::vector<std::vector<Segment>> per_group(G);
+    std::vector<std::vector<std::vector<int32_t>>> grp_rows(G);
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
+    for (int g = 0; g < G; ++g)
+        group_ca(y, z, row, off[g], off[g + 1], g / NSEC, g % NSEC, prm, per_group[g], grp_rows[g], diag);
+    std::vector<Segment> seeds;
+    for (int g = 0; g < G; ++g)
+        for (auto& s : per_group[g]) seeds.push_back(std::move(s));
+    std::sort(seeds.begin(), seeds.end(), [](const Segment& a, const Segment& b) { return a.canon < b.canon; });
+    const int S0 = (int)seeds.size();
+    // sector of every cluster
+    std::vector<int32_t> sec(n);
+    for (int g = 0; g < G; ++g)
+        for (int64_t i = off[g]; i < off[g + 1]; ++i) sec[i] = g % NSEC;
+    auto no_align = [](int) -> const double* { return nullptr; };
+    // S3b: each segment seeds a tracklet: inward fit + inward extension, then
+    // outward fit over everything + outward extension.
+    std::vector<std::vector<int32_t>> tl_hits(S0);
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nt)
+    for (int i = 0; i < S0; ++i) {
+        const Segment& sg = seeds[i];
+        const auto& rows = grp_rows[sg.event * NSEC + sg.sector];
+        std::vector<int32_t> H = sg.hits;
+        double p[5], C[15], chi2, x;
+        if (kf_fit<double>(y, z, row, sec.data(), H.data(), (int)H.size(), true, prm, no_align, p, C,
+                           chi2, &x)) {
+            std::vector<int32_t> add;
+            extend_tracklet(y, z, rows, sg.sector, x, p, C, row[H.back()] - 1, -1, prm, add);
+            H.insert(H.end(), add.begin(), add.end());
+        }
+        std::vector<int32_t> rev(H.rbegin(), H.rend());
+        if (kf_fit<double>(y, z, row, sec.data(), rev.data(), (int)rev.size(), false, prm, no_align, p, C,
+                           chi2, &x)) {
+            std::vector<int32_t> add;
+            extend_tracklet(y, z, rows, sg.sector, x, p, C, row[H.front()] + 1, +1, prm, add);
+            std::vector<int32_t> H2(add.rbegin(), add.rend());
+            H2.insert(H2.end(), H.begin(), H.end());
+            H.swap(H2);
+        }
+        tl_hits[i] = std::move(H);
+    }
+    // S3c: every cluster belongs to the best tracklet containing it: more
+    // clusters first, then the smaller canonical id of the seed segment.
+    // A tracklet keeps the clusters it owns if they are >= n_seg.
+    std::vector<int64_t> owner(n, std::numeric_limits<int64_t>::max());
+    auto tl_key = [&](int i) { return ((int64_t)(NROW * 4 - (int)tl_hits[i].size()) << 32) | (int64_t)seeds[i].canon; };
+    for (int i = 0; i < S0; ++i) {
+        const int64_t k = tl_key(i);
+        for (int32_t h : tl_hits[i]) owner[h] = std::min(owner[h], k);
+    }
+    std::vector<Segment> segs;
+    for (int i = 0; i < S0; ++i) {
+        const int64_t k = tl_key(i);
+        Segment t;
+        t.event = seeds[i].event;
+        t.sector = seeds[i].sector;
+        for (int32_t h : tl_hits[i])
+            if (owner[h] == k) t.hits.push_back(h);
+        if ((int)t.hits.size() < prm.n_seg) continue;
+        t.canon = *std::min_element(t.hits.begin(), t.hits.end());
+        t.row_min = row[t.hits.back()];
+        t.row_max = row[t.hits.front()];
+        segs.push_back(std::move(t));
+    }
+    std::sort(segs.begin(), segs.end(), [](const Segment& a, const Segment& b) { return a.canon < b.canon; });
+    const int S = (int)segs.size();
+    // S5 on tracklets: inward fit (state at innermost), outward fit (outermost)
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nt)
+    for (int i = 0; i < S; ++i) {
+        Segment& s = segs[i];
+        double chi2;
+        s.ok_in = kf_fit<double>(y, z, row, sec.data(), s.hits.data(), (int)s.hits.size(), true, prm,
+                                 no_align, s.p_in, s.c_in, chi2);
+        std::vector<int32_t> rev(s.hits.rbegin(), s.hits.rend());
+        s.ok_out = kf_fit<double>(y, z, row, sec.data(), rev.data(), (int)rev.size(), false, prm,
+                                  no_align, s.p_out, s.c_out, chi2);
+    }
+    // S4 candidates
+    std::vector<std::vector<MergePair>> cand_b(S);
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nt)
+    for (int b = 0; b < S; ++b)
+        for (int a = 0; a < S; ++a) {
+            if (a == b) continue;
+            double c2;
+            if (merge_chi2(segs[a], segs[b], z, prm, c2)) cand_b[b].push_back({c2, a, b});
+        }
+    std::vector<MergePair> cand;
+    for (auto& v : cand_b)
+        for (auto& m : v) cand.push_back(m);
+    // greedy: ascending chi2, ties by canonical ids of A then B
+    std::sort(cand.begin(), cand.end(), [&](const MergePair& p, const MergePair& q) {
+        if (p.chi2 != q.chi2) return p.chi2 < q.chi2;
+        if (segs[p.a].canon != segs[q.a].canon) return segs[p.a].canon < segs[q.a].canon;
+        return segs[p.b].canon < segs[q.b].canon;
+    });
+    std::vector<int> next(S, -1), prev(S, -1);
+    for (const MergePair& m : cand) {
+        if (next[m.a] < 0 && prev[m.b] < 0) {
+            next[m.a] = m.b;
+            prev[m.b] = m.a;
+        }
+    }
+    // decision margins per segment (for tracing disagreements)
+    std::vector<double> margin(S, std::numeric_limits<double>::infinity());
+    {
+        std::vector<std::vector<double>> side_a(S), side_b(S);
+        for (const MergePair& m : cand) {
+            side_a[m.a].push_back(m.chi2);
+            side_b[m.b].push_back(m.chi2);
+        }
+        auto rel = [](double u, double v) { return std::fabs(u - v) / std::max(std::fabs(u), std::fabs(v)); };
+        for (const MergePair& m : cand) {
+            double mg = rel(m.chi2, prm.chi2_merge);
+            for (double o : side_a[m.a]) if (o != m.chi2) mg = std::min(mg, rel(o, m.chi2));
+            for (double o : side_b[m.b]) if (o != m.chi2) mg = std::min(mg, rel(o, m.chi2));
+            margin[m.a] = std::min(margin[m.a], mg);
+            margin[m.b] = std::min(margin[m.b], mg);
+        }
+    }
+    // tracks: chains of merged segments, hits outermost first
+    struct Track { int32_t canon; std::vector<int32_t> hits; };
+    std::vector<Track> tracks;
+    for (int s0 = 0; s0 < S; ++s0) {
+        if (next[s0] >= 0) continue;  // start from the outermost segment
+        Track t;
+        t.canon = std::numeric_limits<int32_t>::max();
+        for (int s = s0; s >= 0; s = prev[s]) {
+            for (int32_t h : segs[s].hits) t.hits.push_back(h);
+            t.canon = std::min(t.canon, segs[s].canon);
+        }
+        if ((int)t.hits.size() >= prm.n_min) tracks.push_back(std::move(t));
+    }
+    std::sort(tracks.begin(), tracks.end(), [](const Track& a, const Track& b) { return a.canon < b.canon; });
+    for (int64_t i = 0; i < n; ++i) track_of_cluster[i] = -1;
+    trk_off[0] = 0;
+    for (size_t t = 0; t < tracks.size(); ++t) {
+        int32_t o = trk_off[t];
+        for (int32_t h : tracks[t].hits) {
+            trk_hits[o++] = h;
+            track_of_cluster[h] = (int32_t)t;
+        }
+        trk_off[t + 1] = o;
+    }
+    if (diag) {
+        if (diag->seg_of)
+            for (int64_t i = 0; i < n; ++i) diag->seg_of[i] = -1;
+        if (diag->merge_margin)
+            for (int64_t i = 0; i < n; ++i) diag->merge_margin[i] = std::numeric_limits<double>::infinity();
+        for (int s = 0; s < S; ++s)
+            for (int32_t h : segs[s].hits) {
+                if (diag->seg_of) diag->seg_of[h] = s;
+                if (diag->merge_margin) diag->merge_margin[h] = margin[s];
+            }
+    }
+    return (int64_t)tracks.size();
+}
+
+static int fit_common(const float* y, const float* z, const uint16_t* row, const int32_t* sec,
+                      const int32_t* trk_off, const int32_t* trk_hits, int32_t T,
+                      const double* align, const orc_params* prm, int reverse, double* params,
+                      double* cov, double* chi2o, int32_t* ndf) {
+    const int nt = orc_get_threads();
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nt)
+    for (int t = 0; t < T; ++t) {
+        const int n = trk_off[t + 1] - trk_off[t];
+        std::vector<int32_t> hits(trk_hits + trk_off[t], trk_hits + trk_off[t + 1]);
+        if (reverse) std::reverse(hits.begin(), hits.end());
+        double p[5], C[15], chi2 = 0;
+        bool ok = n >= 3;
+        if (ok) {
+            auto th = [&](int h) -> const double* { return align ? align + 6 * sec[h] : nullptr; };
+            ok = kf_fit<double>(y, z, row, sec, hits.data(), n, !reverse, *prm, th, p, C, chi2);
+        }
+        if (ok) {
+            for (int i = 0; i < 5; ++i) params[t * 5 + i] = p[i];
+            for (int i = 0; i < 15; ++i) cov[t * 15 + i] = C[i];
+            chi2o[t] = chi2;
+            ndf[t] = 2 * n - 5;
+        } else {
+            for (int i = 0; i < 5; ++i) params[t * 5 + i] = 0;
+            for (int i = 0; i < 15; ++i) cov[t * 15 + i] = 0;
+            chi2o[t] = 0;
+            ndf[t] = -1;
+        }
+    }
+    return 0;
+}
+
+int orc_fit_tracks(const float* y, const float* z, const uint16_t* row, const int32_t* sec,
+                   const int32_t* trk_off, const int32_t* trk_hits, int32_t T, const double* align,
+                   const orc_params* prm, double* params, double* cov, double* chi2, int32_t* ndf) {
+    return fit_common(y, z, row, sec, trk_off, trk_hits, T, align, prm, 0, params, cov, chi2, ndf);
+}
+
+int orc_fit_tracks_dir(const float* y, const float* z, const uint16_t* row, const int32_t* sec,
+                       const int32_t* trk_off, const int32_t* trk_hits, int32_t T,
+                       const double* align, const orc_params* prm, int reverse, double* params,
+                       double* cov, double* chi2, int32_t* ndf) {
+    return fit_common(y, z, row, sec, trk_off, trk_hits, T, align, prm, reverse, params, cov, chi2, ndf);
+}
+
+// Per track, the touched sectors (at most 24/6 = 4 per pass; more sectors
+// are handled in further passes) carry dual parts for their 6 parameters.
+constexpr int ND = 24;
+using D24 = Dual<ND>;
+
+int orc_fit_adjoint(const float* y, const float* z, const uint16_t* row, const int32_t* sec,
+                    const int32_t* trk_off, const int32_t* trk_hits, int32_t T, const double* align,
+                    const orc_params* prm, double* chi2_total, double* grad) {
+    const int nt = orc_get_threads();
+    std::vector<double> tchi2(T, 0.0);
+    std::vector<std::vector<double>> tgrad(grad ? T : 0);
+    static const double zero6[6] = {0, 0, 0, 0, 0, 0};
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nt)
+    for (int t = 0; t < T; ++t) {
+        const int n = trk_off[t + 1] - trk_off[t];
+        const int32_t* hits = trk_hits + trk_off[t];
+        if (n < 3) continue;
+        if (!grad) {
+            double p[5], C[15], chi2;
+            auto th = [&](int h) -> const double* { return align ? align + 6 * sec[h] : zero6; };
+            if (kf_fit<double>(y, z, row, sec, hits, n, true, *prm, th, p, C, chi2)) tchi2[t] = chi2;
+            continue;
+        }
+        std::vector<int> touched;
+        for (int j = 0; j < n; ++j)
+            if (std::find(touched.begin(), touched.end(), sec[hits[j]]) == touched.end())
+                touched.push_back(sec[hits[j]]);
+        std::vector<double> g(216, 0.0);
+        bool ok = true;
+        double chi2v = 0.0;
+        for (size_t base = 0; base < touched.size() && ok; base += ND / 6) {
+            std::vector<D24> th(36 * 6);
+            for (int s = 0; s < 36; ++s)
+                for (int q = 0; q < 6; ++q) th[s * 6 + q] = D24(align ? align[s * 6 + q] : 0.0);
+            for (size_t k = base; k < touched.size() && k < base + ND / 6; ++k)
+                for (int q = 0; q < 6; ++q) th[touched[k] * 6 + q].d[(k - base) * 6 + q] = 1.0;
+            D24 p[5], C[15], chi2;
+            auto thf = [&](int h) -> const D24* { return th.data() + 6 * sec[h]; };
+            ok = kf_fit<D24>(y, z, row, sec, hits, n, true, *prm, thf, p, C, chi2);
+            if (!ok) break;
+            chi2v = chi2.v;
+            for (size_t k = base; k < touched.size() && k < base + ND / 6; ++k)
+                for (int q = 0; q < 6; ++q) g[touched[k] * 6 + q] = chi2.d[(k - base) * 6 + q];
+        }
+        if (ok) {
+            tchi2[t] = chi2v;
+            tgrad[t] = std::move(g);
+        }
+    }
+    double tot = 0.0;
+    for (int t = 0; t < T; ++t) tot += tchi2[t];
+    *chi2_total = tot;
+    if (grad) {
+        for (int i = 0; i < 216; ++i) grad[i] = 0.0;
+        for (int t = 0; t < T; ++t)
+            if (!tgrad[t].empty())
+                for (int i = 0; i < 216; ++i) grad[i] += tgrad[t][i];
+    }
+    return 0;
+}
+
+// Gauss-Newton matrix: sum over tracks and clusters of 2 dr^T S^-1 dr, with
+// dr the derivative of each predicted residual with respect to the
+// parameters of the track's touched sectors.
+int orc_gauss_newton(const float* y, const float* z, const uint16_t* row, const int32_t* sec,
+                     const int32_t* trk_off, const int32_t* trk_hits, int32_t T, const double* align,
+                     const orc_params* prm, double* gn) {
+    const int nt = orc_get_threads();
+    std::vector<std::vector<double>> part(nt, std::vector<double>(216 * 216, 0.0));
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nt)
+    for (int t = 0; t < T; ++t) {
+#ifdef _OPENMP
+        const int tid = omp_get_thread_num();
+#else
+        const int tid = 0;
+#endif
+        const int n = trk_off[t + 1] - trk_off[t];
+        const int32_t* hits = trk_hits + trk_off[t];
+        if (n < 3) continue;
+        std::vector<int> touched;
+        for (int j = 0; j < n; ++j)
+            if (std::find(touched.begin(), touched.end(), sec[hits[j]]) == touched.end())
+                touched.push_back(sec[hits[j]]);
+        if ((int)touched.size() > ND / 6) continue;
+        std::vector<D24> th(36 * 6);
+        for (int s = 0; s < 36; ++s)
+            for (int q = 0; q < 6; ++q) th[s * 6 + q] = D24(align ? align[s * 6 + q] : 0.0);
+        for (size_t k = 0; k < touched.size(); ++k)
+            for (int q = 0; q < 6; ++q) th[touched[k] * 6 + q].d[k * 6 + q] = 1.0;
+        const Seed sd = make_seed(y, z, row, sec, hits, n, true, *prm);
+        D24 p[5], C[15], chi2(0.0), J[25], dX[5];
+        for (int i = 0; i < 5; ++i) p[i] = D24(sd.p[i]);
+        for (int i = 0; i < 15; ++i) C[i] = D24(0.0);
+        for (int i = 0; i < 5; ++i) C[sidx(i, i)] = D24(prm->prior[i]);
+        D24 x(sd.x);
+        int frame = sd.frame;
+        bool ok = true;
+        std::vector<double> local(24 * 24, 0.0);
+        for (int j = 0; j < n && ok; ++j) {
+            const int h = hits[j];
+            D24 xc, yc, zc;
+            corrected<D24>(th.data() + 6 * sec[h], row_x(row[h]), (double)y[h], (double)z[h], xc, yc, zc);
+            ok = move_state(x, p, frame, xc, sec[h], J, dX, *prm);
+            if (!ok) break;
+            cov_transform(C, J);
+            D24 res[2], si[3];
+            kf_update(p, C, yc, zc, prm->sigma_y2, prm->sigma_z2, chi2, res, si);
+            const int m = (int)touched.size() * 6;
+            for (int a = 0; a < m; ++a)
+                for (int b = 0; b < m; ++b)
+                    local[a * 24 + b] += 2.0 * (res[0].d[a] * (si[0].v * res[0].d[b] + si[1].v * res[1].d[b]) +
+                                                res[1].d[a] * (si[1].v * res[0].d[b] + si[2].v * res[1].d[b]));
+        }
+        if (!ok) continue;
+        for (size_t ka = 0; ka < touched.size(); ++ka)
+            for (size_t kb = 0; kb < touched.size(); ++kb)
+                for (int qa = 0; qa < 6; ++qa)
+                    for (int qb = 0; qb < 6; ++qb)
+                        part[tid][(touched[ka] * 6 + qa) * 216 + touched[kb] * 6 + qb] +=
+                            local[(ka * 6 + qa) * 24 + kb * 6 + qb];
+    }
+    for (int i = 0; i < 216 * 216; ++i) {
+        double s = 0;
+        for (int k = 0; k < nt; ++k) s += part[k][i];
+        gn[i] = s;
+    }
+    return 0;
+}
+
+int orc_seed(const float* y, const float* z, const uint16_t* row, const int32_t* sector_of,
+             const int32_t* hits, int32_t n, int first_is_outer, const orc_params* prm,
+             double* x0, int32_t* frame, double* p) {
+    if (n < 3) return 1;
+    const Seed sd = make_seed(y, z, row, sector_of, hits, n, first_is_outer != 0, *prm);
+    *x0 = sd.x;
+    *frame = sd.frame;
+    for (int i = 0; i < 5; ++i) p[i] = sd.p[i];
+    return 0;
+}
+
+int orc_propagate(double x1, int s1, const double* p, double x2, int s2, const orc_params* prm,
+                  double* p_out, double* jac, double* dx1, double* dx2) {
+    double q[5], J[25], dX[5];
+    for (int i = 0; i < 5; ++i) q[i] = p[i];
+    double x = x1;
+    int frame = s1;
+    if (!move_state<double>(x, q, frame, x2, s2, J, dX, *prm)) return 1;
+    for (int i = 0; i < 5; ++i) p_out[i] = q[i];
+    for (int i = 0; i < 25; ++i) jac[i] = J[i];
+    // derivative with respect to the start plane: by the same chain rule,
+    // moving x1 shifts the transport start (and x' on a sector change).
+    if (dx2)
+        for (int i = 0; i < 5; ++i) dx2[i] = dX[i];
+    if (dx1) {
+        const double ca = s1 == s2 ? 1.0 : std::cos(delta_alpha(s1, s2));
+        for (int i = 0; i < 5; ++i) dx1[i] = -dX[i] * ca;
+        if (s1 != s2) {
+            // y' = -x sin + y cos also moves with x1
+            const double sa = std::sin(delta_alpha(s1, s2));
+            // d p_out / d y' = F[:,0]; recover F[:,0] = (J[:,0] + dX sa)/ca
+            for (int i = 0; i < 5; ++i) {
+                const double f0 = (jac[i * 5 + 0] + dX[i] * sa) / ca;
+                dx1[i] += -f0 * sa;
+            }
+        }
+    }
+    return 0;
+}
+
+int64_t orc_bruteforce_chains(const float* y, const float* z, const uint16_t* row, int64_t n,
+                              int32_t sector, const orc_params* prm_, double chi2ndf_max,
+                              int64_t cap_chains, int64_t cap_hits, int32_t* out_off,
+                              int32_t* out_hits) {
+    // Exhaustive depth-first enumeration of maximal admissible chains of one
+    // group.  A chain (innermost first) has strictly rising rows; a step of
+    // g rows (g <= max_gap) may skip rows only when none of the skipped rows
+    // holds an admissible continuation; every consecutive pair lies inside
+    // the windows and every interior triplet has D^2 <= chi2_link.  A chain
+    // is maximal when it cannot be extended outwards and is not the outer
+    // part of a longer admissible chain.  Kept: length >= n_min and FP64 fit
+    // chi2/ndf <= chi2ndf_max.
+    const orc_params& prm = *prm_;
+    std::vector<int32_t> sec(n, sector);
+    std::vector<std::vector<int32_t>> byrow(NROW);
+    for (int64_t i = 0; i < n; ++i) byrow[row[i]].push_back((int32_t)i);
+    auto step_ok = [&](const std::vector<int32_t>& path, int32_t u) {
+        const int32_t c = path.back();
+        const float xc = row_xf(row[c]), xu = row_xf(row[u]);
+        if (!in_window(xc, y[c], z[c], xu, y[u], z[u], prm.win_y, prm.win_z)) return false;
+        if (path.size() < 2) return true;
+        const int32_t d = path[path.size() - 2];
+        const float xd = row_xf(row[d]);
+        const float d2 = triplet_d2(xd, y[d], z[d], xc, y[c], z[c], xu, y[u], z[u], prm.sigma_y2, prm.sigma_z2);
+        return d2 <= prm.chi2_link;
+    };
+    std::vector<std::vector<int32_t>> leaves;
+    std::vector<int32_t> path;
+    std::function<void()> dfs = [&]() {
+        const int r = row[path.back()];
+        bool extended = false;
+        for (int g = 1; g <= prm.max_gap && r + g < NROW; ++g) {
+            bool any = false;
+            for (int32_t u : byrow[r + g]) {
+                if (!step_ok(path, u)) continue;
+                any = true;
+                path.push_back(u);
+                dfs();
+                path.pop_back();
+            }
+            if (any) { extended = true; break; }  // no skipping past a continuation
+        }
+        if (!extended) leaves.push_back(path);
+    };
+    for (int r = 0; r < NROW; ++r)
+        for (int32_t c : byrow[r]) {
+            path.assign(1, c);
+            dfs();
+        }
+    // drop chains that are the outer part of a longer chain
+    std::vector<std::vector<int32_t>> found;
+    for (size_t i = 0; i < leaves.size(); ++i) {
+        const auto& a = leaves[i];
+        bool suffix = false;
+        for (size_t j = 0; j < leaves.size() && !suffix; ++j) {
+            const auto& b = leaves[j];
+            if (b.size() <= a.size()) continue;
+            suffix = std::equal(a.begin(), a.end(), b.end() - a.size());
+        }
+        if (suffix || (int)a.size() < prm.n_min) continue;
+        std::vector<int32_t> hits(a.rbegin(), a.rend());  // outermost first
+        double p[5], C[15], chi2;
+        auto no_align = [](int) -> const double* { return nullptr; };
+        if (!kf_fit<double>(y, z, row, sec.data(), hits.data(), (int)hits.size(), true, prm, no_align, p,
+                            C, chi2))
+            continue;
+        if (chi2 / (2.0 * (double)hits.size() - 5.0) <= chi2ndf_max) found.push_back(a);
+    }
+    int64_t total = 0;
+    for (auto& f : found) total += (int64_t)f.size();
+    if ((int64_t)found.size() > cap_chains || total > cap_hits)
+        return -std::max<int64_t>((int64_t)found.size(), total);
+    out_off[0] = 0;
+    int64_t o = 0;
+    for (size_t i = 0; i < found.size(); ++i) {
+        for (int32_t h : found[i]) out_hits[o++] = h;
+        out_off[i + 1] = (int32_t)o;
+    }
+    return (int64_t)found.size();
+}
+
+}  // extern "C"

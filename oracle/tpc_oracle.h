@@ -1,0 +1,138 @@
+/*
+ * TPC tracking oracle: a plain, slow, FP64 CPU restatement of the tracking
+ * path (row binning, cellular-automaton neighbour finding, chaining, segment
+ * merging, Kalman fit, alignment gradient).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the
+ * CPU-baseline leg of the benchmark may load this library.  It shares no code
+ * with the CUDA library and the CUDA library never calls it.
+ *
+ * The paper (ALICE O2 EPN farm, arXiv 2412.13755) states that TPC tracking
+ * runs on the GPUs and takes 99% of their compute (Sec. 4.2, Sec. 5) but
+ * gives no algorithm; every rule here is the build's stated reading, listed
+ * beside each function.  Arrays are host pointers owned by the caller.
+ */
+#ifndef TPC_ORACLE_H
+#define TPC_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+    float win_y;              /* |y_u - y_c| <= win_y |x_u - x_c|           */
+    float win_z;              /* |z_u - z_c| <= win_z |x_u - x_c|           */
+    float chi2_link;          /* triplet D^2 cut                            */
+    float sigma_y2, sigma_z2; /* measurement variances (cm^2)               */
+    int32_t max_gap;          /* rows searched on each side (1..max_gap)    */
+    int32_t n_seg;            /* minimum chain length kept as a segment     */
+    int32_t n_min;            /* minimum clusters of an output track        */
+    int32_t merge_max_row_gap;/* row gap allowed between merged segments    */
+    int32_t merge_max_overlap;/* row overlap allowed across a sector border */
+    float merge_z_slope;      /* z gate: |dz| <= slope * dx + margin        */
+    float merge_z_margin;
+    double chi2_merge;        /* 5-d merge chi2 cut                         */
+    double chi2_ext;          /* 2-d predicted-residual cut of extensions   */
+    int32_t ext_max_miss;     /* extension stops after this many empty rows */
+    double bz;                /* field (T)                                  */
+    double prior[5];          /* diagonal prior covariance of the fit seed  */
+    double seed_snp_max;      /* clamp of the seed |sin phi|                */
+    double seed_qpt_max;      /* clamp of the seed |q/pT| (c/GeV)           */
+    double snp_max;           /* transport fails when |sin phi| reaches it  */
+} orc_params;
+
+/* Fills the default parameter set of the build's reading. */
+void orc_default_params(orc_params* p);
+
+/* Per-cluster diagnostics of the neighbour step (input-order indices). */
+typedef struct {
+    int32_t* choice_dn;   /* [n] chosen down partner of each cluster or -1 */
+    int32_t* choice_up;   /* [n] chosen up partner or -1                    */
+    float*   d2;          /* [n] D^2 of the chosen triplet                  */
+    float*   d2_next;     /* [n] runner-up D^2 at the winning gap pair (inf)*/
+    int32_t* link_dn;     /* [n] final down link or -1                      */
+    int32_t* link_up;     /* [n] final up link or -1                        */
+    int32_t* seg_of;      /* [n] segment id (canonical order) or -1         */
+    double*  merge_margin;/* [n] relative margin of the merge decision that
+                             placed this cluster's segment (inf: none)      */
+} orc_diag;
+
+/* S1-S4: whole pipeline.  Inputs in input order, grouped per event*36+sector
+ * by evt_sector_off[n_events*36+1].  Outputs: track_of_cluster[n] (canonical
+ * track index or -1), trk_off[cap+1], trk_hits[n] (input-order indices,
+ * outermost first).  Returns the number of tracks, or -1 on bad input.
+ * diag may be NULL. */
+int64_t orc_find_tracks(const float* y, const float* z, const uint16_t* row,
+                        int64_t n, const int64_t* evt_sector_off,
+                        int32_t n_events, const orc_params* prm,
+                        int32_t* track_of_cluster, int32_t* trk_off,
+                        int32_t* trk_hits, orc_diag* diag);
+
+/* S5: FP64 Kalman fit of caller hit lists (outermost first).  The state is
+ * reported at the innermost cluster.  sector_of[n] gives each cluster's
+ * sector.  align[216] (or NULL) holds per-sector corrections applied to the
+ * cluster positions.  params[T*5], cov[T*15], chi2[T], ndf[T] (ndf = -1 when
+ * the transport fails).  Returns 0. */
+int orc_fit_tracks(const float* y, const float* z, const uint16_t* row,
+                   const int32_t* sector_of, const int32_t* trk_off,
+                   const int32_t* trk_hits, int32_t n_tracks,
+                   const double* align, const orc_params* prm,
+                   double* params, double* cov, double* chi2, int32_t* ndf);
+
+/* Same fit, hits consumed in the order given (reverse = 1: innermost first,
+ * state reported at the outermost cluster). */
+int orc_fit_tracks_dir(const float* y, const float* z, const uint16_t* row,
+                       const int32_t* sector_of, const int32_t* trk_off,
+                       const int32_t* trk_hits, int32_t n_tracks,
+                       const double* align, const orc_params* prm, int reverse,
+                       double* params, double* cov, double* chi2, int32_t* ndf);
+
+/* S6: total chi2 over tracks and (if grad != NULL) its exact derivative with
+ * respect to the 216 alignment parameters, by forward-mode dual numbers
+ * through the FP64 fit.  Failed fits contribute nothing. */
+int orc_fit_adjoint(const float* y, const float* z, const uint16_t* row,
+                    const int32_t* sector_of, const int32_t* trk_off,
+                    const int32_t* trk_hits, int32_t n_tracks,
+                    const double* align, const orc_params* prm,
+                    double* chi2_total, double* grad);
+
+/* Gauss-Newton matrix (216x216, row-major) of the total chi2 from the
+ * residual derivatives, for the alignment descent and null-mode analysis. */
+int orc_gauss_newton(const float* y, const float* z, const uint16_t* row,
+                     const int32_t* sector_of, const int32_t* trk_off,
+                     const int32_t* trk_hits, int32_t n_tracks,
+                     const double* align, const orc_params* prm, double* gn);
+
+/* The fit seed of a hit list given in fit order (first_is_outer = 1 for
+ * the inward fit): plane x0 and frame of the first cluster, state p[5]. */
+int orc_seed(const float* y, const float* z, const uint16_t* row, const int32_t* sector_of,
+             const int32_t* hits, int32_t n, int first_is_outer, const orc_params* prm,
+             double* x0, int32_t* frame, double* p);
+
+/* One propagation: state p (y, z, sin phi, tan lambda, q/pT) at plane x1 of
+ * sector s1 -> plane x2 of sector s2.  Writes p_out[5], jac[25] (row-major
+ * d p_out / d p) and dx1[5], dx2[5].  Returns 0, or 1 when it fails. */
+int orc_propagate(double x1, int s1, const double* p, double x2, int s2,
+                  const orc_params* prm, double* p_out, double* jac,
+                  double* dx1, double* dx2);
+
+/* C10: all admissible chains of one (event, sector) group: strictly rising
+ * rows, row steps <= max_gap, each interior triplet inside the windows with
+ * D^2 <= chi2_link, length >= n_min, and FP64 fit chi2/ndf <= chi2ndf_max.
+ * Writes chains innermost first into out_hits with offsets out_off.
+ * Returns the number of chains, or -(needed) when a capacity is too small. */
+int64_t orc_bruteforce_chains(const float* y, const float* z, const uint16_t* row,
+                              int64_t n, int32_t sector, const orc_params* prm,
+                              double chi2ndf_max, int64_t cap_chains,
+                              int64_t cap_hits, int32_t* out_off,
+                              int32_t* out_hits);
+
+/* Threads used by the OpenMP loops (0 = library default). */
+void orc_set_threads(int n);
+int orc_get_threads(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,389 @@
+"""Seeded synthetic TPC events: primary helices from the origin in a uniform Bz.
+
+This module is simulation only.  It draws charged tracks, intersects each
+helix with the pad-row planes of the 36 sectors in the *global* frame
+(circle / straight-line intersection of the transverse projection), smears
+the crossings, adds uniformly distributed noise clusters and lays the result
+out as the (event, sector)-grouped structure-of-arrays that the tracking
+library consumes.  It contains none of the reconstruction arithmetic (no
+neighbour rule, no chaining, no Kalman transport or update); the oracle and
+the CUDA path both read its output as plain data.
+
+Workload shapes follow the five benchmark configurations of the build
+(one sector; one central Pb-Pb-like event; a 50 kHz pile-up time frame;
+512 uneven events; the alignment sample).  The paper measures on ALICE Run-3
+Pb-Pb / pp time frames (Sec. 4, Sec. 4.3), which are not available here; these
+seeded events stand in for them.
+
+Geometry (the paper gives none; this is the build's stated reading):
+  * sector s in [0,36): phi-index i = s mod 18, side A (z>0) for s<18, C below;
+    sector centre angle alpha_i = (i + 1/2) * 20 deg;
+  * local frame x = X cos a + Y sin a, y = -X sin a + Y cos a, z = Z;
+  * pad row r in [0,152) is the plane x = 85 + r * 162/151 cm, accepted
+    |y| <= x tan(10 deg), |z| < 250 cm;
+  * curvature k = K * Bz * q/pT with K = 2.99792458e-3 (cm T GeV/c)^-1 and
+    the direction angle obeying dphi/ds = -k (positive charges bend clockwise
+    in +Bz).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+N_SECTORS = 36
+N_PHI = 18
+N_ROWS = 152
+X_FIRST = 85.0
+X_LAST = 247.0
+ROW_PITCH = (X_LAST - X_FIRST) / (N_ROWS - 1)
+SECTOR_WIDTH = math.radians(20.0)
+TAN_HALF_SECTOR = math.tan(math.radians(10.0))
+BZ = 0.5
+KAPPA = 2.99792458e-3
+Z_MAX = 250.0
+SIGMA_Y = 0.1
+SIGMA_Z = 0.15
+ROW_DROP = 0.05
+V_DRIFT = 2.58          # cm / us
+FRAME_US = 2000.0       # 100 collisions at 50 kHz
+SEED_BASE = 241213755
+
+ROW_X = X_FIRST + np.arange(N_ROWS, dtype=np.float64) * ROW_PITCH
+
+
+def sector_alpha(sector):
+    """Centre angle (rad) of a sector (array or scalar)."""
+    return ((np.asarray(sector) % N_PHI) + 0.5) * SECTOR_WIDTH
+
+
+def rotation_matrix(a, b, g):
+    """R = Rz(g) Ry(b) Rx(a) about the sector-local axes."""
+    ca, sa, cb, sb, cg, sg = (math.cos(a), math.sin(a), math.cos(b),
+                              math.sin(b), math.cos(g), math.sin(g))
+    rx = np.array([[1, 0, 0], [0, ca, -sa], [0, sa, ca]])
+    ry = np.array([[cb, 0, sb], [0, 1, 0], [-sb, 0, cb]])
+    rz = np.array([[cg, -sg, 0], [sg, cg, 0], [0, 0, 1]])
+    return rz @ ry @ rx
+
+
+@dataclasses.dataclass
+class Events:
+    """A batch of events, clusters grouped by (event, sector).
+
+    Cluster arrays are in *input order*: grouped by event*36+sector
+    (offsets in ``evt_sector_off``), shuffled inside each group.
+    """
+    y: np.ndarray               # f32 [n] local y (cm)
+    z: np.ndarray               # f32 [n] local z (cm), drift-shifted in frames
+    row: np.ndarray             # u16 [n]
+    charge: np.ndarray          # u16 [n]
+    evt_sector_off: np.ndarray  # i64 [E*36+1]
+    n_events: int
+    mc_track: np.ndarray        # i32 [n] global track id, -1 = noise
+    trk_q: np.ndarray           # f64 [T] charge sign
+    trk_pt: np.ndarray          # f64 [T]
+    trk_tgl: np.ndarray         # f64 [T]
+    trk_phi0: np.ndarray        # f64 [T]
+    trk_event: np.ndarray       # i32 [T]
+    trk_t0: np.ndarray          # f64 [T] drift-time offset (us), 0 outside frames
+    # per-cluster truth at the crossing (noise: NaN); only when truth=True
+    y_true: np.ndarray | None = None
+    z_true: np.ndarray | None = None
+    snp_true: np.ndarray | None = None
+    arc_true: np.ndarray | None = None
+    align: np.ndarray | None = None  # f64 [216] true correction parameters
+
+    @property
+    def n(self) -> int:
+        return int(self.y.shape[0])
+
+    def sector_of_cluster(self) -> np.ndarray:
+        grp = np.repeat(np.arange(self.n_events * N_SECTORS),
+                        np.diff(self.evt_sector_off))
+        return (grp % N_SECTORS).astype(np.int32)
+
+    def truth_tracks(self, n_min: int = 10):
+        """Truth hit lists: (trk_off, trk_hits, track ids) for tracks with
+        >= n_min clusters, hits in input-order indices, outermost first
+        (descending arc length along the helix)."""
+        sig = np.nonzero(self.mc_track >= 0)[0]
+        if self.arc_true is not None:
+            arc = self.arc_true[sig]
+        else:
+            arc = ROW_X[self.row[sig]]
+        order = np.lexsort((-arc, self.mc_track[sig]))
+        sig = sig[order]
+        tid = self.mc_track[sig]
+        ids, start, cnt = np.unique(tid, return_index=True, return_counts=True)
+        keep = cnt >= n_min
+        parts = [sig[s:s + c] for s, c, k in zip(start, cnt, keep) if k]
+        hits = np.concatenate(parts).astype(np.int32) if parts else np.zeros(0, np.int32)
+        off = np.zeros(int(keep.sum()) + 1, np.int32)
+        off[1:] = np.cumsum(cnt[keep])
+        return off, hits, ids[keep]
+
+
+def _crossings(phi0, k, tgl, wedge, misalign, want_truth):
+    """Intersect each helix with every accepted (sector, row) plane.
+
+    Works in the global transverse plane: the track circle has centre
+    C = (sin phi0, -cos phi0)/k and passes through the origin; the outgoing
+    crossing of the line n.P = x_r (n = (cos a, sin a)) has direction angle
+    psi = a - asin(k (x_r - n.C)).
+    Returns per-crossing arrays (track, sector, row, y, z, snp, arc).
+    """
+    T = phi0.shape[0]
+    cx = np.sin(phi0) / k
+    cy = -np.cos(phi0) / k
+    r_hi = X_LAST / math.cos(SECTOR_WIDTH / 2) + 1.0
+    th_a = phi0 - np.arcsin(np.clip(k * X_FIRST / 2, -1, 1))
+    th_b = phi0 - np.arcsin(np.clip(k * r_hi / 2, -1, 1))
+    i_lo = np.floor(np.minimum(th_a, th_b) / SECTOR_WIDTH).astype(np.int64)
+    i_hi = np.floor(np.maximum(th_a, th_b) / SECTOR_WIDTH).astype(np.int64)
+    side = np.where(tgl >= 0, 0, N_PHI)
+    out = []
+    xr = ROW_X[None, :]
+    for slot in range(6):
+        iphi = i_lo + slot
+        valid = iphi <= i_hi
+        if wedge is not None:
+            valid &= (iphi % N_PHI) == wedge
+        if not valid.any():
+            continue
+        t_idx = np.nonzero(valid)[0]
+        a = (iphi[t_idx] + 0.5) * SECTOR_WIDTH
+        ca, sa = np.cos(a)[:, None], np.sin(a)[:, None]
+        kk = k[t_idx][:, None]
+        nc = ca * cx[t_idx][:, None] + sa * cy[t_idx][:, None]
+        q = kk * (xr - nc)
+        ok = np.abs(q) < 1.0
+        qc = np.clip(q, -0.999999, 0.999999)
+        psi = a[:, None] - np.arcsin(qc)
+        dphi = phi0[t_idx][:, None] - psi
+        two_pi = 2 * math.pi
+        dpos = np.mod(dphi, two_pi)
+        dneg = -np.mod(-dphi, two_pi)
+        dd = np.where(kk > 0, dpos, dneg)
+        s = dd / kk
+        ok &= (s > 0) & (np.abs(dd) <= math.pi)
+        px = cx[t_idx][:, None] + (-np.sin(psi)) / kk
+        py = cy[t_idx][:, None] + np.cos(psi) / kk
+        yl = -sa * px + ca * py
+        zl = tgl[t_idx][:, None] * s
+        snp = np.sin(psi - a[:, None])
+        sector = (iphi[t_idx] % N_PHI + side[t_idx])[:, None] + np.zeros_like(s, dtype=np.int64)
+        xl = np.broadcast_to(xr, s.shape).copy()
+        if misalign is not None:
+            # measured point on the misaligned plane: x of R^T (P - D) = x_r
+            yl, zl, xl, s = _misaligned_crossing(phi0[t_idx], kk, tgl[t_idx], a,
+                                                 cx[t_idx], cy[t_idx], s,
+                                                 sector, misalign)
+        ok &= np.abs(yl) <= xr * TAN_HALF_SECTOR
+        ok &= np.abs(zl) < Z_MAX
+        ti, ri = np.nonzero(ok)
+        out.append((t_idx[ti], sector[ti, ri], ri, yl[ti, ri], zl[ti, ri],
+                    snp[ti, ri], s[ti, ri]))
+    if not out:
+        e = np.zeros(0)
+        return (e.astype(np.int64),) * 3 + (e,) * 4
+    return tuple(np.concatenate([o[j] for o in out]) for j in range(7))
+
+
+def _misaligned_crossing(phi0, kk, tgl, a, cx, cy, s, sector, misalign):
+    """Newton solve for the arc length where the helix meets the misaligned
+    row plane {R (x_r, y, z) + D}; returns measured (y, z) in that plane."""
+    ca, sa = np.cos(a)[:, None], np.sin(a)[:, None]
+    xr = ROW_X[None, :]
+    P = misalign.reshape(N_SECTORS, 6)[sector]          # [t, r, 6]
+    R = np.zeros(sector.shape + (3, 3))
+    for sec in np.unique(sector):
+        m = sector == sec
+        R[m] = rotation_matrix(*misalign.reshape(N_SECTORS, 6)[sec, 3:6])
+    D = P[..., 0:3]
+    s = s.copy()
+    for _ in range(6):
+        psi = phi0[:, None] - kk * s
+        px = cx[:, None] + (-np.sin(psi)) / kk
+        py = cy[:, None] + np.cos(psi) / kk
+        loc = np.stack([ca * px + sa * py, -sa * px + ca * py,
+                        tgl[:, None] * s], -1) - D
+        meas = np.einsum('...ji,...j->...i', R, loc)       # R^T (P - D)
+        dloc = np.stack([np.cos(psi - a[:, None]), np.sin(psi - a[:, None]),
+                         np.broadcast_to(tgl[:, None], s.shape)], -1)
+        dmeas = np.einsum('...ji,...j->...i', R, dloc)
+        s = s - (meas[..., 0] - xr) / dmeas[..., 0]
+    psi = phi0[:, None] - kk * s
+    px = cx[:, None] + (-np.sin(psi)) / kk
+    py = cy[:, None] + np.cos(psi) / kk
+    loc = np.stack([ca * px + sa * py, -sa * px + ca * py,
+                    tgl[:, None] * s], -1) - D
+    meas = np.einsum('...ji,...j->...i', R, loc)
+    return meas[..., 1], meas[..., 2], meas[..., 0], s
+
+
+def _draw_tracks(rng, n, pt_min, pt_slope, wedge):
+    pt = pt_min + rng.exponential(pt_slope, n)
+    eta = rng.uniform(-0.9, 0.9, n)
+    tgl = np.sinh(eta)
+    if wedge is None:
+        phi0 = rng.uniform(0.0, 2 * math.pi, n)
+    else:
+        phi0 = rng.uniform(wedge * SECTOR_WIDTH, (wedge + 1) * SECTOR_WIDTH, n)
+    q = np.where(rng.uniform(size=n) < 0.5, 1.0, -1.0)
+    return q, pt, tgl, phi0
+
+
+def _one_collision(rng, n_tracks, noise_frac, wedge, pt_min, pt_slope,
+                   misalign, want_truth, t0_us, tid0):
+    q, pt, tgl, phi0 = _draw_tracks(rng, n_tracks, pt_min, pt_slope, wedge)
+    k = KAPPA * BZ * q / pt
+    parts = []
+    CH = 8192
+    for c0 in range(0, n_tracks, CH):
+        sl = slice(c0, min(n_tracks, c0 + CH))
+        tr, sec, row, y, z, snp, arc = _crossings(phi0[sl], k[sl], tgl[sl], wedge,
+                                                  misalign, want_truth)
+        parts.append((tr + c0, sec, row, y, z, snp, arc))
+    tr, sec, row, yt, zt, snp, arc = (np.concatenate([p[j] for p in parts]) for j in range(7))
+    keep = rng.uniform(size=tr.shape[0]) >= ROW_DROP
+    tr, sec, row, yt, zt, snp, arc = (v[keep] for v in (tr, sec, row, yt, zt, snp, arc))
+    ym = yt + rng.normal(0.0, SIGMA_Y, yt.shape[0])
+    zm = zt + rng.normal(0.0, SIGMA_Z, zt.shape[0])
+    chg = np.minimum(20 + np.round(rng.exponential(60.0, yt.shape[0])), 65535)
+    n_sig = tr.shape[0]
+    n_noise = int(round(noise_frac / (1.0 - noise_frac) * n_sig)) if noise_frac > 0 else 0
+    if wedge is None:
+        nsec = rng.integers(0, N_SECTORS, n_noise)
+    else:
+        nsec = wedge + N_PHI * rng.integers(0, 2, n_noise)
+    nrow = rng.integers(0, N_ROWS, n_noise)
+    half = ROW_X[nrow] * TAN_HALF_SECTOR
+    ny = rng.uniform(-1.0, 1.0, n_noise) * half
+    nz = rng.uniform(0.0, Z_MAX, n_noise) * np.where(nsec < N_PHI, 1.0, -1.0)
+    nchg = rng.integers(1, 101, n_noise)
+    # drift-time shift (frames): A side z' = z - v t0, C side z' = z + v t0
+    if t0_us != 0.0:
+        shift = V_DRIFT * t0_us
+        zm = zm - np.where(sec < N_PHI, shift, -shift)
+        nz = nz - np.where(nsec < N_PHI, shift, -shift)
+    cl = dict(
+        sector=np.concatenate([sec, nsec]).astype(np.int64),
+        row=np.concatenate([row, nrow]).astype(np.uint16),
+        y=np.concatenate([ym, ny]),
+        z=np.concatenate([zm, nz]),
+        charge=np.concatenate([chg, nchg]).astype(np.uint16),
+        mc=np.concatenate([tr + tid0, np.full(n_noise, -1)]).astype(np.int32),
+        y_true=np.concatenate([yt, np.full(n_noise, np.nan)]),
+        z_true=np.concatenate([zt, np.full(n_noise, np.nan)]),
+        snp_true=np.concatenate([snp, np.full(n_noise, np.nan)]),
+        arc_true=np.concatenate([arc, np.full(n_noise, np.nan)]),
+    )
+    trk = dict(q=q, pt=pt, tgl=tgl, phi0=phi0)
+    return cl, trk
+
+
+def generate(events, seed, wedge=None, pt_min=0.2, pt_slope=0.5,
+             misalign=None, truth=False, frame=None):
+    """Generate a batch.
+
+    events: list of (n_tracks, noise_frac) per event.
+    frame:  None, or a list of (n_tracks, noise_frac) per collision; all
+            collisions then share one event with uniform drift-time offsets
+            over FRAME_US (z shifted by V_DRIFT * t0).
+    """
+    rng = np.random.default_rng(seed)
+    if frame is not None:
+        specs = [[(nt, nf, rng.uniform(0.0, FRAME_US)) for nt, nf in frame]]
+    else:
+        specs = [[(nt, nf, 0.0)] for nt, nf in events]
+    cls, trks = [], []
+    tid0 = 0
+    for ev, colls in enumerate(specs):
+        for nt, nf, t0 in colls:
+            cl, trk = _one_collision(rng, nt, nf, wedge, pt_min, pt_slope,
+                                     misalign, truth, t0, tid0)
+            cl['event'] = np.full(cl['row'].shape[0], ev, np.int64)
+            trk['event'] = np.full(nt, ev, np.int32)
+            trk['t0'] = np.full(nt, t0)
+            tid0 += nt
+            cls.append(cl)
+            trks.append(trk)
+    cat = {key: np.concatenate([c[key] for c in cls]) for key in cls[0]}
+    E = len(specs)
+    key = cat['event'] * N_SECTORS + cat['sector']
+    perm = rng.permutation(key.shape[0])
+    order = perm[np.argsort(key[perm], kind='stable')]
+    counts = np.bincount(key, minlength=E * N_SECTORS)
+    off = np.zeros(E * N_SECTORS + 1, np.int64)
+    off[1:] = np.cumsum(counts)
+    trk = {key_: np.concatenate([t[key_] for t in trks]) for key_ in trks[0]}
+    ev = Events(
+        y=cat['y'][order].astype(np.float32),
+        z=cat['z'][order].astype(np.float32),
+        row=cat['row'][order],
+        charge=cat['charge'][order],
+        evt_sector_off=off, n_events=E,
+        mc_track=cat['mc'][order],
+        trk_q=trk['q'], trk_pt=trk['pt'], trk_tgl=trk['tgl'],
+        trk_phi0=trk['phi0'], trk_event=trk['event'], trk_t0=trk['t0'],
+    )
+    ev.arc_true = cat['arc_true'][order]
+    if truth:
+        ev.y_true = cat['y_true'][order]
+        ev.z_true = cat['z_true'][order]
+        ev.snp_true = cat['snp_true'][order]
+    if misalign is not None:
+        ev.align = np.asarray(misalign, np.float64).copy()
+    return ev
+
+
+# --- the five workload shapes -------------------------------------------------
+
+def one_sector(n_tracks=200, noise=0.10, seed=SEED_BASE + 0, truth=False):
+    """One 20-degree wedge (sectors 0 and 18), 200 tracks, 10% noise."""
+    return generate([(n_tracks, noise)], seed, wedge=0, truth=truth)
+
+
+def central_event(n_tracks=10000, noise=0.20, seed=SEED_BASE + 1, truth=False):
+    """One central Pb-Pb-like event over 36 sectors, 1e4 tracks, 20% noise."""
+    return generate([(n_tracks, noise)], seed, truth=truth)
+
+
+def pileup_frame(n_collisions=100, n_tracks=10000, noise=0.20,
+                 seed=SEED_BASE + 2, truth=False):
+    """50 kHz frame: collisions at uniform drift-time offsets over 2 ms."""
+    return generate(None, seed, frame=[(n_tracks, noise)] * n_collisions,
+                    truth=truth)
+
+
+def uneven_batch(n_events=512, lo=10, hi=10000, seed=SEED_BASE + 3, truth=False):
+    """Events with log-uniform multiplicity in [lo, hi] and noise U[5%,30%]."""
+    rng = np.random.default_rng(seed + 1000003)
+    nt = np.exp(rng.uniform(math.log(lo), math.log(hi), n_events)).round().astype(int)
+    nf = rng.uniform(0.05, 0.30, n_events)
+    return generate(list(zip(nt.tolist(), nf.tolist())), seed, truth=truth)
+
+
+def draw_misalignment(seed=SEED_BASE + 4, shift_sigma=0.01, rot_sigma=1e-4):
+    """36 x (dx, dy, dz, a, b, g): shifts sigma 100 um, rotations 0.1 mrad."""
+    rng = np.random.default_rng(seed + 7777)
+    m = np.empty((N_SECTORS, 6))
+    m[:, 0:3] = rng.normal(0.0, shift_sigma, (N_SECTORS, 3))
+    m[:, 3:6] = rng.normal(0.0, rot_sigma, (N_SECTORS, 3))
+    return m.reshape(-1)
+
+
+def alignment_sample(n_tracks=200000, seed=SEED_BASE + 4, misalign=None,
+                     n_events=1):
+    """pT > 1 GeV/c tracks, no noise, clusters on misaligned row planes."""
+    if misalign is None:
+        misalign = draw_misalignment(seed)
+    per = [(n_tracks // n_events + (1 if i < n_tracks % n_events else 0), 0.0)
+           for i in range(n_events)]
+    return generate(per, seed, pt_min=1.0, pt_slope=0.5, misalign=misalign)
+
+
+CONFIG_NAMES = ("one_sector", "central_event", "pileup_frame", "uneven_batch",
+                "alignment_sample")
