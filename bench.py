@@ -1,0 +1,396 @@
+#!/usr/bin/env python3
+"""Benchmark of the TPC tracking path on GB300.
+
+One step = the whole tracking path over one central Pb-Pb-like event
+(36 sectors, 1e4 primary tracks, 20% noise, ~1.8e6 clusters): register the
+clusters (S0), bin (S1), neighbours (S2), chains and Kalman-guided tracklets
+(S3), merge (S4), and the Kalman fit of every found track (S5).  Metric:
+clusters per second.  The inputs (~22 MB) are smaller than L2, so L2 is
+flushed (512 MB write) between timed steps.  Synthetic seeded events stand in
+for ALICE Run-3 data.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+--impl reference times the FP64 CPU oracle (the reference arm of this build:
+the paper publishes no code) on the same workload, on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "TPC clusters/s tracked (CA+Kalman), 1 GB300"
+WORKLOAD = ("central_event: 1 event x 36 sectors, 1e4 primary tracks (pT exp slope 0.5 GeV/c "
+            "min 0.2, |eta|<0.9), 20% noise, ~1.8e6 clusters, Bz 0.5 T")
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
+# algorithmic traffic / work per unit, fixed before measuring
+NEIGHBOUR_BYTES_PER_CLUSTER = 20.0      # read y,z (8); write down, up, D^2 (12)
+FIT_BYTES_PER_HIT = 14.0                # hit index (4) + y, z (8) + row (2)
+FIT_BYTES_PER_TRACK = 88.0              # 5 params + 15 cov + chi2 + ndf
+FIT_FLOPS_PER_HIT = 290.0               # transport 55 + covariance 100 + update 135
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-profiler", action="store_true",
+                    help="skip the CUPTI launch count (when running under ncu)")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+# ----------------------------------------------------------------- clocks --
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx.append(float(f[2]))
+                except ValueError:
+                    continue
+                for name, v in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                                    "sw_power_cap"), f[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(name)
+        except OSError:
+            pass
+        finally:
+            if self.path and os.path.exists(self.path):
+                os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------- workload --
+def make_event(seed_offset=0):
+    from paper_2412_13755_gb300 import synth
+    return synth.central_event(seed=synth.SEED_BASE + 1 + seed_offset)
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def cpu_baseline(ev, target_s=15.0):
+    """The oracle, as it stands, on the host cores: find + fit of the event."""
+    import oracle
+    cores = host_cores()
+    oracle.set_threads(cores)
+    sec = ev.sector_of_cluster()
+    done, t0 = 0, time.perf_counter()
+    while True:
+        toc, off, hits = oracle.find_tracks(ev.y, ev.z, ev.row, ev.evt_sector_off, ev.n_events)
+        oracle.fit_tracks(ev.y, ev.z, ev.row, sec, off, hits)
+        done += 1
+        el = time.perf_counter() - t0
+        if el >= target_s or done >= 3:
+            break
+    return {"value": done * ev.n / el, "unit": "clusters/s", "cores": cores, "kind": "oracle",
+            "sample": f"{done} x the full central event ({ev.n} clusters), find + FP64 fit, "
+                      f"OpenMP over groups/tracks, {el:.1f} s"}
+
+
+# -------------------------------------------------------------- reference --
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    ev = make_event()
+    cores = host_cores()
+    oracle.set_threads(cores)
+    sec = ev.sector_of_cluster()
+
+    def step():
+        toc, off, hits = oracle.find_tracks(ev.y, ev.z, ev.row, ev.evt_sector_off, ev.n_events)
+        oracle.fit_tracks(ev.y, ev.z, ev.row, sec, off, hits)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    el = time.perf_counter() - t0
+    v = args.steps * ev.n / el
+    line = {"metric": METRIC, "value": v, "unit": "clusters/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": v, "unit": "clusters/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} x the full central event ({ev.n} clusters), "
+                                       f"find + FP64 fit"},
+            "e2e": {"value": v, "unit": "clusters/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# -------------------------------------------------------------------- ours --
+def count_launches(step, sync):
+    """Kernels of libtpctrack launched by one step (CUPTI via torch.profiler)."""
+    from torch.profiler import ProfilerActivity, profile
+    with profile(activities=[ProfilerActivity.CUDA]) as prof:
+        step()
+        sync()
+    n = 0
+    for e in prof.events():
+        name = getattr(e, "name", "") or ""
+        if "tpc" in name and ("k_" in name or "kernel" in name.lower()):
+            n += 1
+    return n
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2412_13755_gb300 import tpc
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    ev = make_event(seed_offset=rank)
+    n = ev.n
+    track_cap = 32768
+    tr = tpc.Tracker(n, 1, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    # host (pinned) and device copies of the inputs
+    h_y = torch.from_numpy(ev.y).pin_memory()
+    h_z = torch.from_numpy(ev.z).pin_memory()
+    h_row = torch.from_numpy(ev.row.view(np.int16)).pin_memory()
+    h_off = torch.from_numpy(ev.evt_sector_off).pin_memory()
+    d_y, d_z = h_y.to(dev), h_z.to(dev)
+    d_row = h_row.to(dev).view(torch.uint16)
+    d_off = h_off.to(dev)
+    find_out = (torch.empty(n, dtype=torch.int32, device=dev),
+                torch.empty(track_cap + 1, dtype=torch.int32, device=dev),
+                torch.empty(n, dtype=torch.int32, device=dev),
+                torch.empty(1, dtype=torch.int32, device=dev))
+    fit_out = (torch.empty(track_cap, 5, dtype=torch.float32, device=dev),
+               torch.empty(track_cap, 15, dtype=torch.float32, device=dev),
+               torch.empty(track_cap, dtype=torch.float32, device=dev),
+               torch.empty(track_cap, dtype=torch.int32, device=dev))
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    def step(y=d_y, z=d_z, row=d_row, off=d_off):
+        tr.load(y, z, row, off, 1)
+        tr.find(out=find_out)
+        tr.fit(find_out[1], find_out[2], track_cap, find_out[3], out=fit_out)
+
+    sync = torch.cuda.synchronize
+    for _ in range(max(args.warmup, 3)):
+        flush.zero_()
+        step()
+    sync()
+    st = tr.check()
+    launches_per_step = 0 if args.no_profiler else count_launches(step, sync)
+    tr.stage_timing(True)
+    stage_sum = {}
+    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    e1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    sync()
+    clocks.start()
+    for k in range(args.steps):
+        flush.zero_()
+        e0[k].record(stream)
+        step()
+        e1[k].record(stream)
+        sync()
+        for name, ms in tr.stage_times().items():
+            stage_sum[name] = stage_sum.get(name, 0.0) + ms
+    sync()
+    clk = clocks.stop()
+    tr.stage_timing(False)
+    step_ms = [a.elapsed_time(b) for a, b in zip(e0, e1)]
+    total_s = sum(step_ms) / 1e3
+    if world > 1:
+        t = torch.tensor([total_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    st = tr.check()
+    T = int(find_out[3].item())
+    units = n * world
+    value = units * args.steps / total_s
+
+    # end to end: host buffers -> device, step, results back to the host
+    h_toc = torch.empty(n, dtype=torch.int32).pin_memory()
+    h_par = torch.empty(track_cap, 5, dtype=torch.float32).pin_memory()
+    h_chi2 = torch.empty(track_cap, dtype=torch.float32).pin_memory()
+    h_nt = torch.empty(1, dtype=torch.int32).pin_memory()
+    b_y = torch.empty_like(d_y)
+    b_z = torch.empty_like(d_z)
+    b_row = torch.empty(n, dtype=torch.int16, device=dev)
+    b_off = torch.empty_like(d_off)
+
+    def e2e_step():
+        b_y.copy_(h_y, non_blocking=True)
+        b_z.copy_(h_z, non_blocking=True)
+        b_row.copy_(h_row, non_blocking=True)
+        b_off.copy_(h_off, non_blocking=True)
+        step(b_y, b_z, b_row.view(torch.uint16), b_off)
+        h_toc.copy_(find_out[0], non_blocking=True)
+        h_nt.copy_(find_out[3], non_blocking=True)
+        h_par.copy_(fit_out[0], non_blocking=True)
+        h_chi2.copy_(fit_out[2], non_blocking=True)
+
+    for _ in range(3):
+        e2e_step()
+    sync()
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()
+        e2e_step()
+    sync()
+    e2e_s = time.perf_counter() - t0
+    # the flushes are outside the metric: time them alone and subtract
+    t1 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()
+    sync()
+    e2e_s = max(e2e_s - (time.perf_counter() - t1), 1e-9)
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    h2d = 4 * n + 4 * n + 2 * n + 8 * ev.evt_sector_off.size
+    d2h = 4 * n + 4 + 20 * track_cap + 4 * track_cap
+
+    # roofline of the dominant kernel (single-kernel stages only)
+    per_step = {k: v / args.steps for k, v in stage_sum.items()}
+    hits_total = int(find_out[1][T].item()) if T > 0 else 0
+    kernels = {
+        "k_tracklets": per_step.get("tracklets", 0.0),
+        "k_neighbours": per_step.get("neighbours", 0.0),
+        "k_fit": per_step.get("fit", 0.0),
+    }
+    dom = max(kernels, key=kernels.get)
+    hbm_peak, peak_src = measured_peaks()
+    ms = kernels[dom]
+    if dom == "k_neighbours":
+        achieved = n * NEIGHBOUR_BYTES_PER_CLUSTER / (ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": None}
+    else:
+        # the Kalman kernels are FP32-ALU bound: per-hit flops at ~20 flop/byte
+        hits = hits_total if dom == "k_fit" else n
+        achieved = hits * FIT_FLOPS_PER_HIT / (ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None}
+    roof["kernel"] = dom
+    roof["kernel_ms"] = ms
+    roof["peak_source"] = peak_src if roof["unit"] == "GB/s" else "derived: 152 SM x 128 FP32 x 2 x 2070 MHz"
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": "clusters/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "events_per_gpu": 1, "clusters_per_gpu": n,
+                   "tracks_found": T, "l2": "flushed between timed steps (512 MB write)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "tracks_per_s": T * world * args.steps / total_s,
+        "stage_ms_per_step": per_step,
+        "e2e": {"value": units * args.steps / e2e_s, "unit": "clusters/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk,
+        "roofline": roof,
+        "status": {"fp64_updates": st.n_fp64_updates, "segments": st.n_segments,
+                   "tracklets": st.n_tracklets, "merges": st.n_merges},
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(ev)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

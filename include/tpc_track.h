@@ -1,0 +1,195 @@
+/*
+ * tpc_track.h -- C ABI of the GB300 TPC tracking library (libtpctrack.so).
+ *
+ * What it computes.  ALICE's online farm runs TPC track reconstruction on
+ * its GPUs; it is the step that loads them fully during data taking and
+ * takes 99% of their compute (arXiv 2412.13755, Sec. 4.2 and Sec. 5), and a
+ * whole time frame is processed in one operation inside GPU memory (Sec. 4).
+ * The paper names the step but does not describe it; this library implements
+ * it as cellular-automaton neighbour finding between pad rows, chaining and
+ * Kalman-guided extension into tracklets, merging across sector boundaries,
+ * a Kalman fit of the 5-parameter helix (y, z, sin phi, tan lambda, q/pT)
+ * with 5x5 covariance in a uniform Bz, and the exact gradient of the summed
+ * fit chi2 with respect to per-sector alignment corrections.
+ *
+ * Geometry: 36 sectors (phi-index s mod 18, side A for s < 18), centre angle
+ * (s mod 18 + 1/2) * 20 deg, local x = X cos a + Y sin a, y = -X sin a +
+ * Y cos a; 152 pad rows at x = 85 + r * 162/151 cm, accepted |y| <= x tan 10.
+ *
+ * Conventions for every entry point:
+ *  - Array arguments are DEVICE pointers owned by the caller unless the
+ *    comment says "host".  The library never allocates device memory: its
+ *    scratch lives in the caller's workspace (tpc_set_workspace).
+ *  - Calls are asynchronous on the given stream and never synchronise the
+ *    host (except tpc_last_error and tpc_get_stats, which read back).
+ *    Output counts stay on the device.
+ *  - Errors: a non-zero tpc_status for argument/launch errors.  Errors found
+ *    by kernels (capacity exceeded, bad cluster) are written to a device
+ *    status word; tpc_last_error reads it (synchronising the stream).
+ *  - No C++ exception crosses this boundary.  A context must not be used
+ *    from two host threads at once; calls on one context that overlap on the
+ *    GPU (different streams) race on its workspace.
+ *  - Cluster indices in inputs and outputs are input-order indices.
+ */
+#ifndef TPC_TRACK_H
+#define TPC_TRACK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* tpc_stream_t; /* = cudaStream_t, NULL = legacy default */
+typedef struct tpc_ctx tpc_ctx;
+
+typedef enum {
+    TPC_OK = 0,
+    TPC_ERR_ARG = 1,       /* bad argument (null pointer, size, order)        */
+    TPC_ERR_CUDA = 2,      /* a CUDA call failed; tpc_last_error has the text */
+    TPC_ERR_CAPACITY = 3,  /* workspace or output capacity exceeded           */
+    TPC_ERR_TIMEOUT = 4,   /* a bounded device wait gave up                   */
+    TPC_ERR_STATE = 5,     /* call out of order (no workspace, no clusters)   */
+    TPC_ERR_INPUT = 6      /* a cluster failed validation (row >= 152, NaN)   */
+} tpc_status;
+
+/* Reconstruction parameters (cuts, windows, fit prior).  The paper gives
+ * none; tpc_default_params fills the values this library is tested with. */
+typedef struct {
+    float win_y, win_z;        /* neighbour window |dy| <= win_y |dx| ...    */
+    float chi2_link;           /* triplet D^2 cut                            */
+    float sigma_y2, sigma_z2;  /* cluster variances (cm^2)                   */
+    int32_t max_gap;           /* pad rows searched above / below (1..3)     */
+    int32_t n_seg;             /* minimum chain length that seeds a tracklet */
+    int32_t n_min;             /* minimum clusters of an output track        */
+    int32_t merge_max_row_gap; /* rows allowed between merged tracklets      */
+    int32_t merge_max_overlap; /* row overlap allowed across a sector border */
+    float merge_z_slope, merge_z_margin; /* |dz| <= slope |dx| + margin      */
+    float chi2_merge;          /* 5-d merge chi2 cut                         */
+    float chi2_ext;            /* 2-d predicted-residual cut of extensions   */
+    int32_t ext_max_miss;      /* extension stops after this many empty rows */
+    float bz;                  /* field (T)                                  */
+    float prior[5];            /* diagonal prior covariance at the seed      */
+    float seed_snp_max;        /* clamp of the seed |sin phi|                */
+    float seed_qpt_max;        /* clamp of the seed |q/pT| (c/GeV)           */
+    float snp_max;             /* transport fails when |sin phi| reaches it  */
+    float fp64_ratio;          /* redo an update in FP64 when a posterior
+                                  variance drops below fp64_ratio x prior    */
+    float fp64_det;            /* ... or det S <= fp64_det S00 S11           */
+} tpc_params;
+
+/* Counters a call leaves in the workspace (read back by tpc_get_stats). */
+typedef struct {
+    int64_t n_clusters;
+    int32_t n_segments;       /* CA chains seeding tracklets                 */
+    int32_t n_tracklets;      /* tracklets kept after cluster ownership      */
+    int32_t n_merge_cand;     /* merge candidates passing the chi2 cut       */
+    int32_t n_merges;         /* accepted merges                             */
+    int32_t n_tracks;         /* output tracks                               */
+    int32_t n_fp64_updates;   /* Kalman updates redone in FP64 (all calls)   */
+    int32_t status;           /* device status word (tpc_status)            */
+    int32_t status_detail;
+} tpc_stats;
+
+/* Fills p with the library's default parameters. */
+void tpc_default_params(tpc_params* p);
+
+/* Creates a context (host object; no device memory).  params may be NULL
+ * for the defaults.  Returns TPC_ERR_ARG if ctx is NULL. */
+tpc_status tpc_create(tpc_ctx** ctx, const tpc_params* params);
+void tpc_destroy(tpc_ctx* ctx);
+
+/* Device bytes of scratch needed for batches of up to max_clusters clusters
+ * in up to max_events events (and fits / gradients of up to max_clusters
+ * hits).  Pure host computation. */
+size_t tpc_workspace_bytes(const tpc_ctx* ctx, int64_t max_clusters, int32_t max_events);
+
+/* Hands the library a caller-owned device buffer of `bytes` (256-byte
+ * aligned) sized by tpc_workspace_bytes for the same capacities.  The buffer
+ * must outlive every call that uses it.  TPC_ERR_CAPACITY if too small. */
+tpc_status tpc_set_workspace(tpc_ctx* ctx, void* dev_ptr, size_t bytes,
+                             int64_t max_clusters, int32_t max_events);
+
+/* S0 (the whole time frame resident in GPU memory, Sec. 4): registers the
+ * cluster arrays of a batch.  y, z: local coordinates (cm, FP32); row: pad
+ * row (u16, < 152); charge: u16 (may be NULL, unused by the reconstruction);
+ * n clusters in input order, grouped by event*36 + sector with device
+ * offsets evt_sector_off[n_events*36 + 1] (int64, non-decreasing, first 0,
+ * last n).  The arrays are read by later calls, not copied: keep them alive
+ * and unchanged until the last call that uses them.  Enqueues a validation
+ * kernel (bad rows / non-finite coordinates -> TPC_ERR_INPUT in the status
+ * word).  TPC_ERR_CAPACITY if n or n_events exceed the workspace. */
+tpc_status tpc_load_clusters(tpc_ctx* ctx, const float* y, const float* z,
+                             const uint16_t* row, const uint16_t* charge, int64_t n,
+                             const int64_t* evt_sector_off, int32_t n_events,
+                             tpc_stream_t stream);
+
+/* S1-S4: pattern recognition of the loaded batch.
+ * Outputs (device, caller-owned):
+ *   track_of_cluster[n]  track index of each input cluster, -1 = none;
+ *   trk_off[track_cap+1] CSR offsets of the tracks' hits;
+ *   trk_hits[n]          input-order cluster indices, each track outermost
+ *                        pad row first;
+ *   n_tracks_dev[1]      number of tracks.
+ * Tracks are ordered by their smallest input cluster index.  If more than
+ * track_cap tracks are found the status word gets TPC_ERR_CAPACITY and the
+ * outputs are truncated. */
+tpc_status tpc_find_tracks(tpc_ctx* ctx, int32_t* track_of_cluster, int32_t* trk_off,
+                           int32_t* trk_hits, int32_t* n_tracks_dev, int32_t track_cap,
+                           tpc_stream_t stream);
+
+/* S5: Kalman fit of caller-supplied hit lists over the loaded clusters.
+ * trk_off[n_tracks+1], trk_hits[...] as produced by tpc_find_tracks (input
+ * indices, outermost first).  n_tracks_dev (device int32, may be NULL)
+ * overrides n_tracks when it is smaller, so the output of tpc_find_tracks can
+ * be fed without a host round trip; n_tracks is then the capacity.  Outputs
+ * per track, state at the innermost cluster in that cluster's sector frame:
+ *   params[T*5]  (y, z, sin phi, tan lambda, q/pT);
+ *   cov[T*15]    upper triangle row-major (00 01 02 03 04 11 12 ... 44);
+ *   chi2[T]      predicted-residual chi2 (compensated FP32 sum);
+ *   ndf[T]       2 n - 5, or -1 when the transport failed (params zeroed).
+ * State and covariance are FP32; an update whose covariance cancels is
+ * redone in FP64 (see tpc_params.fp64_ratio). */
+tpc_status tpc_fit_tracks(tpc_ctx* ctx, const int32_t* trk_off, const int32_t* trk_hits,
+                          int32_t n_tracks, const int32_t* n_tracks_dev, float* params,
+                          float* cov, float* chi2, int32_t* ndf, tpc_stream_t stream);
+
+/* S6: alignment chi2 and gradient.  align[216] (device FP64) holds per-sector
+ * corrections (dx, dy, dz, a, b, g): a cluster's corrected position in its
+ * sector frame is R(a,b,g) (x_row, y, z) + (dx, dy, dz), R = Rz(g) Ry(b) Rx(a).
+ * Each track is fitted on the corrected positions (seeded from the
+ * uncorrected ones); chi2_total[1] (FP64) receives the sum of the track chi2
+ * and, if grad is not NULL, grad[216] (FP64) receives its exact derivative
+ * (hand-written reverse sweep, per-track recomputation from checkpoints,
+ * FP64 cross-track reduction).  Tracks whose transport fails contribute 0. */
+tpc_status tpc_fit_adjoint(tpc_ctx* ctx, const int32_t* trk_off, const int32_t* trk_hits,
+                           int32_t n_tracks, const double* align, double* chi2_total,
+                           double* grad, tpc_stream_t stream);
+
+/* Reads the device status word and counters of the last calls (synchronises
+ * the stream) into *out (may be NULL) and returns the status.  buf (host, may
+ * be NULL) receives a one-line description. */
+tpc_status tpc_get_stats(tpc_ctx* ctx, tpc_stats* out, tpc_stream_t stream);
+tpc_status tpc_last_error(tpc_ctx* ctx, char* buf, size_t len);
+
+/* Stage timing (no counterpart in the paper; a measurement aid).  When
+ * enabled, the library records CUDA events on the launch stream around its
+ * main kernels; tpc_stage_times then synchronises and writes, for the last
+ * call of each kind, the milliseconds of the stages listed in
+ * TPC_STAGE_NAMES (ms_out[TPC_N_STAGES]).  Disabled by default; enabling it
+ * creates the events (host-side CUDA objects, no device memory). */
+#define TPC_N_STAGES 12
+#define TPC_STAGE_NAMES                                                         \
+    "bin", "neighbours", "links", "chains", "tracklets", "select", "merge_cand", \
+        "match", "output", "fit", "adjoint", "find_total"
+tpc_status tpc_stage_timing(tpc_ctx* ctx, int enable);
+tpc_status tpc_stage_times(tpc_ctx* ctx, float* ms_out);
+
+/* Clears the device status word and counters (asynchronous). */
+tpc_status tpc_reset_status(tpc_ctx* ctx, tpc_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,327 @@
+// C ABI of libtpctrack: context, workspace layout, argument checks, and the
+// entry points declared in include/tpc_track.h.  No C++ exception leaves
+// these functions.
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "tpc_internal.h"
+
+using namespace tpc;
+
+namespace tpc {
+
+Layout make_layout(int64_t N, int32_t E) {
+    Layout L;
+    L.N = N;
+    L.E = E;
+    L.G = (int64_t)E * NSEC;
+    L.K = (int64_t)NROW * L.G + N / CELL_OCC + 16;
+    L.S = N / 16 + 4096;
+    L.T = N + 1;
+    const int64_t scan_items = std::max<int64_t>(std::max<int64_t>(N + 1, L.K + 1), L.G + 1);
+    L.scan_tmp = scan_items / 4096 + 64;
+    L.adj_tracks = 0;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o += (bytes + 255) & ~size_t(255);
+        return at;
+    };
+    const size_t n4 = 4 * (size_t)N, n8 = 8 * (size_t)N, s4 = 4 * (size_t)L.S, s8 = 8 * (size_t)L.S;
+    const size_t g4 = 4 * (size_t)(L.G + 1);
+    L.geo = take(sizeof(Geo));
+    L.status = take(4 * ST_N_SLOTS);
+    L.g_zmin_u = take(g4);
+    L.g_zmax_u = take(g4);
+    L.g_nz = take(g4);
+    L.g_inv = take(g4);
+    L.g_zmin = take(g4);
+    L.g_kbase = take(g4);
+    L.key_in = take(n4);
+    L.slot_in = take(n4);
+    L.cell_cnt = take(4 * (size_t)(L.K + 1));
+    L.cell_off = take(4 * (size_t)(L.K + 1));
+    L.yb = take(n4);
+    L.zb = take(n4);
+    L.orig = take(n4);
+    L.grpb = take(n4);
+    L.rowb = take((size_t)N);
+    L.choice_dn = take(n4);
+    L.choice_up = take(n4);
+    L.d2 = take(n4);
+    L.claim_up = take(n8);
+    L.claim_dn = take(n8);
+    L.link_dn = take(n4);
+    L.link_up = take(n4);
+    L.owner = take(n8);
+    L.seg_start = take(s4);
+    L.seg_len = take(s4);
+    L.seg_grp = take(s4);
+    L.seg_canon = take(s4);
+    L.tl_rowhit = take(s4 * NROW);
+    L.tl_n = take(s4);
+    L.tl_key = take(s8);
+    L.tl_keep = take(s4);
+    L.tl_canon = take(s4);
+    L.tl_rmin = take(s4);
+    L.tl_rmax = take(s4);
+    L.tl_zin = take(s4);
+    L.tl_zout = take(s4);
+    L.tl_state = take(s4 * 40);
+    L.tl_ok = take(s4);
+    L.grp_tl_cnt = take(g4);
+    L.grp_tl_off = take(g4 + 4);
+    L.grp_tl_cur = take(g4);
+    L.tl_sorted = take(s4);
+    L.cand_n = take(s4);
+    L.cand_a = take(s4 * MAX_CAND);
+    L.cand_c2 = take(s4 * MAX_CAND);
+    L.best_a = take(s8);
+    L.best_b = take(s8);
+    L.nxt = take(s4);
+    L.prv = take(s4);
+    L.trk_flag = take(n4);
+    L.trk_rank = take(n4 + 4);
+    L.trk_len_at = take(n4);
+    L.trk_head_at = take(n4);
+    L.len_by_rank = take(4 * (size_t)L.T);
+    L.scan_a = take(4 * (size_t)L.scan_tmp);
+    L.scan_b = take(4 * (size_t)L.scan_tmp);
+    L.adj_grad = take(8 * 216 * 2);
+    L.adj_chi2 = take(8 * 2);
+    L.adj_ckpt = take(0);
+    L.total = o;
+    return L;
+}
+
+}  // namespace tpc
+
+static tpc_status fail(tpc_ctx* c, tpc_status st, const char* msg) {
+    if (c) {
+        try {
+            c->last_error = msg;
+        } catch (...) {
+        }
+    }
+    return st;
+}
+
+static tpc_status cuda_fail(tpc_ctx* c, cudaError_t e, const char* where) {
+    char buf[256];
+    snprintf(buf, sizeof buf, "%s: %s", where, cudaGetErrorString(e));
+    return fail(c, TPC_ERR_CUDA, buf);
+}
+
+extern "C" {
+
+void tpc_default_params(tpc_params* p) {
+    if (!p) return;
+    p->win_y = 3.0f;
+    p->win_z = 3.5f;
+    p->chi2_link = 16.0f;
+    p->sigma_y2 = 0.01f;
+    p->sigma_z2 = 0.0225f;
+    p->max_gap = 3;
+    p->n_seg = 5;
+    p->n_min = 10;
+    p->merge_max_row_gap = 24;
+    p->merge_max_overlap = 8;
+    p->merge_z_slope = 3.5f;
+    p->merge_z_margin = 2.0f;
+    p->chi2_merge = 30.0f;
+    p->chi2_ext = 16.0f;
+    p->ext_max_miss = 3;
+    p->bz = 0.5f;
+    p->prior[0] = 4.0f;
+    p->prior[1] = 4.0f;
+    p->prior[2] = 0.25f;
+    p->prior[3] = 0.25f;
+    p->prior[4] = 25.0f;
+    p->seed_snp_max = 0.99f;
+    p->seed_qpt_max = 5.0f;
+    p->snp_max = 0.999f;
+    p->fp64_ratio = 1e-4f;
+    p->fp64_det = 1e-6f;
+}
+
+tpc_status tpc_create(tpc_ctx** ctx, const tpc_params* params) {
+    if (!ctx) return TPC_ERR_ARG;
+    tpc_ctx* c = new (std::nothrow) tpc_ctx();
+    if (!c) return TPC_ERR_ARG;
+    if (params) c->prm = *params; else tpc_default_params(&c->prm);
+    if (c->prm.max_gap < 1 || c->prm.max_gap > 3 || c->prm.n_seg < 3 || c->prm.n_min < 3 ||
+        c->prm.ext_max_miss < 1) {
+        delete c;
+        return TPC_ERR_ARG;
+    }
+    *ctx = c;
+    return TPC_OK;
+}
+
+void tpc_destroy(tpc_ctx* ctx) {
+    if (!ctx) return;
+    for (auto& e : ctx->marks)
+        if (e) cudaEventDestroy(e);
+    delete ctx;
+}
+
+tpc_status tpc_stage_timing(tpc_ctx* c, int enable) {
+    if (!c) return TPC_ERR_ARG;
+    if (enable && !c->marks[0]) {
+        for (auto& e : c->marks) {
+            cudaError_t r = cudaEventCreate(&e);
+            if (r != cudaSuccess) return cuda_fail(c, r, "tpc_stage_timing");
+        }
+    }
+    c->timing = enable != 0;
+    return TPC_OK;
+}
+
+tpc_status tpc_stage_times(tpc_ctx* c, float* ms) {
+    if (!c || !ms) return TPC_ERR_ARG;
+    if (!c->marks[0]) return fail(c, TPC_ERR_STATE, "stage timing was never enabled");
+    // pairs of marks per stage; a pair never recorded reads as 0
+    static const int pairs[TPC_N_STAGES][2] = {{0, 1}, {1, 2},  {2, 3},  {3, 4},  {4, 5},   {5, 6},
+                                               {6, 7}, {7, 8},  {8, 9},  {10, 11}, {12, 13}, {0, 9}};
+    for (int i = 0; i < TPC_N_STAGES; ++i) {
+        float v = 0.f;
+        if (cudaEventSynchronize(c->marks[pairs[i][1]]) == cudaSuccess &&
+            cudaEventElapsedTime(&v, c->marks[pairs[i][0]], c->marks[pairs[i][1]]) != cudaSuccess) {
+            v = 0.f;
+            cudaGetLastError();
+        }
+        ms[i] = v;
+    }
+    return TPC_OK;
+}
+
+size_t tpc_workspace_bytes(const tpc_ctx* ctx, int64_t max_clusters, int32_t max_events) {
+    (void)ctx;
+    if (max_clusters < 0 || max_events < 1) return 0;
+    return make_layout(max_clusters, max_events).total;
+}
+
+tpc_status tpc_set_workspace(tpc_ctx* c, void* dev_ptr, size_t bytes, int64_t max_clusters,
+                             int32_t max_events) {
+    if (!c || !dev_ptr || max_clusters < 0 || max_events < 1 || max_clusters > (int64_t)1 << 30)
+        return fail(c, TPC_ERR_ARG, "tpc_set_workspace: bad argument");
+    if (((uintptr_t)dev_ptr & 255) != 0) return fail(c, TPC_ERR_ARG, "workspace not 256-byte aligned");
+    Layout L = make_layout(max_clusters, max_events);
+    if (bytes < L.total) return fail(c, TPC_ERR_CAPACITY, "workspace too small");
+    c->ws.base = static_cast<char*>(dev_ptr);
+    c->ws.L = L;
+    c->have_ws = true;
+    c->have_clusters = false;
+    cudaError_t e = init_geo(c->ws, nullptr);
+    if (e == cudaSuccess) e = reset_status(c->ws, nullptr);
+    if (e != cudaSuccess) return cuda_fail(c, e, "tpc_set_workspace");
+    return TPC_OK;
+}
+
+tpc_status tpc_load_clusters(tpc_ctx* c, const float* y, const float* z, const uint16_t* row,
+                             const uint16_t* charge, int64_t n, const int64_t* evt_sector_off,
+                             int32_t n_events, tpc_stream_t stream) {
+    if (!c) return TPC_ERR_ARG;
+    if (!c->have_ws) return fail(c, TPC_ERR_STATE, "no workspace");
+    if (n < 0 || n_events < 1 || !evt_sector_off || (n > 0 && (!y || !z || !row)))
+        return fail(c, TPC_ERR_ARG, "tpc_load_clusters: bad argument");
+    if (n > c->ws.L.N || n_events > c->ws.L.E)
+        return fail(c, TPC_ERR_CAPACITY, "batch larger than the workspace");
+    c->y = y;
+    c->z = z;
+    c->row = row;
+    c->charge = charge;
+    c->n = n;
+    c->n_events = n_events;
+    c->evt_sector_off = evt_sector_off;
+    c->have_clusters = true;
+    cudaError_t e = validate_clusters(c, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "tpc_load_clusters");
+    return TPC_OK;
+}
+
+tpc_status tpc_find_tracks(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hits,
+                           int32_t* n_tracks_dev, int32_t track_cap, tpc_stream_t stream) {
+    if (!c) return TPC_ERR_ARG;
+    if (!c->have_ws || !c->have_clusters) return fail(c, TPC_ERR_STATE, "no workspace or clusters");
+    if (!toc || !trk_off || !trk_hits || !n_tracks_dev || track_cap < 0 || track_cap > c->ws.L.T - 1)
+        return fail(c, TPC_ERR_ARG, "tpc_find_tracks: bad argument");
+    cudaError_t e = run_find(c, toc, trk_off, trk_hits, n_tracks_dev, track_cap, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "tpc_find_tracks");
+    return TPC_OK;
+}
+
+tpc_status tpc_fit_tracks(tpc_ctx* c, const int32_t* trk_off, const int32_t* trk_hits,
+                          int32_t n_tracks, const int32_t* n_tracks_dev, float* params, float* cov,
+                          float* chi2, int32_t* ndf, tpc_stream_t stream) {
+    if (!c) return TPC_ERR_ARG;
+    if (!c->have_ws || !c->have_clusters) return fail(c, TPC_ERR_STATE, "no workspace or clusters");
+    if (n_tracks < 0 || (n_tracks > 0 && (!trk_off || !trk_hits || !params || !cov || !chi2 || !ndf)))
+        return fail(c, TPC_ERR_ARG, "tpc_fit_tracks: bad argument");
+    cudaError_t e = run_fit(c, trk_off, trk_hits, n_tracks, n_tracks_dev, params, cov, chi2, ndf,
+                            (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "tpc_fit_tracks");
+    return TPC_OK;
+}
+
+tpc_status tpc_fit_adjoint(tpc_ctx* c, const int32_t* trk_off, const int32_t* trk_hits,
+                           int32_t n_tracks, const double* align, double* chi2_total, double* grad,
+                           tpc_stream_t stream) {
+    if (!c) return TPC_ERR_ARG;
+    if (!c->have_ws || !c->have_clusters) return fail(c, TPC_ERR_STATE, "no workspace or clusters");
+    if (n_tracks < 0 || !align || !chi2_total || (n_tracks > 0 && (!trk_off || !trk_hits)))
+        return fail(c, TPC_ERR_ARG, "tpc_fit_adjoint: bad argument");
+    cudaError_t e = run_adjoint(c, trk_off, trk_hits, n_tracks, align, chi2_total, grad,
+                                (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "tpc_fit_adjoint");
+    return TPC_OK;
+}
+
+tpc_status tpc_get_stats(tpc_ctx* c, tpc_stats* out, tpc_stream_t stream) {
+    if (!c) return TPC_ERR_ARG;
+    if (!c->have_ws) return fail(c, TPC_ERR_STATE, "no workspace");
+    int32_t h[ST_N_SLOTS];
+    cudaError_t e = cudaMemcpyAsync(h, c->ws.at<int32_t>(c->ws.L.status), sizeof h,
+                                    cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "tpc_get_stats");
+    if (out) {
+        out->n_clusters = c->n;
+        out->n_segments = h[ST_NSEG];
+        out->n_tracklets = h[ST_NTL];
+        out->n_merge_cand = h[ST_NCAND];
+        out->n_merges = h[ST_NMERGE];
+        out->n_tracks = h[ST_NTRACKS];
+        out->n_fp64_updates = h[ST_FP64];
+        out->status = h[ST_STATUS];
+        out->status_detail = h[ST_DETAIL];
+    }
+    if (h[ST_STATUS] != 0) {
+        char buf[160];
+        snprintf(buf, sizeof buf, "device status %d (detail %d)", h[ST_STATUS], h[ST_DETAIL]);
+        fail(c, (tpc_status)h[ST_STATUS], buf);
+    }
+    return (tpc_status)h[ST_STATUS];
+}
+
+tpc_status tpc_last_error(tpc_ctx* c, char* buf, size_t len) {
+    if (!c) return TPC_ERR_ARG;
+    tpc_status st = TPC_OK;
+    if (c->have_ws) st = tpc_get_stats(c, nullptr, nullptr);
+    if (buf && len) {
+        snprintf(buf, len, "%s", c->last_error.c_str());
+    }
+    return st;
+}
+
+tpc_status tpc_reset_status(tpc_ctx* c, tpc_stream_t stream) {
+    if (!c) return TPC_ERR_ARG;
+    if (!c->have_ws) return fail(c, TPC_ERR_STATE, "no workspace");
+    cudaError_t e = reset_status(c->ws, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "tpc_reset_status");
+    c->last_error.clear();
+    return TPC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,909 @@
+// S1-S4 of the tracking path: row/z-cell binning, cellular-automaton
+// neighbour finding, chaining, Kalman-guided tracklet construction and
+// selection, segment merging across sectors, and the canonical track output.
+//
+// Integer decisions that floating point takes in the neighbour step (window
+// cuts, triplet D^2 and its comparisons) are evaluated in FP32 with explicit
+// round-to-nearest intrinsics (no contraction), so they are bit-identical to
+// an FP32 evaluation of the same formula on any IEEE machine.  Every tie is
+// broken by the clusters' input indices (canonical ids), so the output does
+// not depend on the order in which the GPU visits clusters.
+#include <algorithm>
+
+#include "tpc_dev.cuh"
+
+namespace tpc {
+
+namespace {
+
+constexpr int TPB = 256;
+constexpr uint64_t KEY_MAX = ~0ull;
+
+inline unsigned grid_for(int64_t n, int per = TPB) {
+    const int64_t b = (n + per - 1) / per;
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, 152LL * 64));
+}
+
+__device__ __forceinline__ uint32_t f2o(float f) {
+    const uint32_t u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float o2f(uint32_t o) {
+    return __uint_as_float((o & 0x80000000u) ? (o & 0x7fffffffu) : ~o);
+}
+
+struct Cells {  // per-group z-cell description
+    const float* zmin;
+    const float* inv;
+    const int32_t* nz;
+    const int32_t* kbase;
+    const int32_t* off;  // cell offsets into the binned arrays
+};
+
+__device__ __forceinline__ int zcell(const Cells& c, int g, float z) {
+    const int nz = c.nz[g];
+    const float f = (z - c.zmin[g]) * c.inv[g];
+    int k = f >= 0.f ? (int)f : 0;  // monotone in z
+    return k < nz - 1 ? k : nz - 1;
+}
+
+// ---------------------------------------------------------------- S1 ------
+__global__ void k_zrange(const float* __restrict__ z, int64_t n, const int64_t* __restrict__ off,
+                         int G, uint32_t* zmin_u, uint32_t* zmax_u) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int g = group_of(off, G, i);
+        const uint32_t o = f2o(z[i]);
+        // lanes of one group combine before the atomics
+        const unsigned act = __activemask();
+        const unsigned same = __match_any_sync(act, g);
+        const uint32_t mn = __reduce_min_sync(same, o);
+        const uint32_t mx = __reduce_max_sync(same, o);
+        if ((threadIdx.x & 31) == (__ffs(same) - 1)) {
+            atomicMin(&zmin_u[g], mn);
+            atomicMax(&zmax_u[g], mx);
+        }
+    }
+}
+
+// one block: z cells per group and their key bases
+__global__ void __launch_bounds__(1024) k_cells(const int64_t* __restrict__ off, int G,
+                                                const uint32_t* zmin_u, const uint32_t* zmax_u,
+                                                float* zmin, float* inv, int32_t* nz,
+                                                int32_t* kbase, int64_t Kcap, int32_t* st) {
+    __shared__ int32_t sh[32];
+    __shared__ int64_t carry_s;
+    if (threadIdx.x == 0) carry_s = 0;
+    __syncthreads();
+    for (int g0 = 0; g0 < G; g0 += blockDim.x) {
+        const int g = g0 + threadIdx.x;
+        int32_t cnt = 0;
+        if (g < G) {
+            const int64_t ng = off[g + 1] - off[g];
+            int64_t k = ng / (NROW * CELL_OCC);
+            k = k < 1 ? 1 : (k > NZ_MAX ? NZ_MAX : k);
+            float lo = 0.f, hi = 0.f;
+            if (ng > 0) {
+                lo = o2f(zmin_u[g]);
+                hi = o2f(zmax_u[g]);
+            }
+            const float w = hi - lo;
+            zmin[g] = lo;
+            inv[g] = w > 0.f ? (float)k / w : 0.f;
+            nz[g] = (int32_t)k;
+            cnt = (int32_t)(NROW * k);
+        }
+        // block exclusive scan of cnt
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        int32_t x = cnt;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) sh[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            int32_t s = sh[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                const int32_t y = __shfl_up_sync(0xffffffffu, s, o);
+                if (lane >= o) s += y;
+            }
+            sh[lane] = s;
+        }
+        __syncthreads();
+        const int64_t base = carry_s;
+        const int32_t ex = (wid > 0 ? sh[wid - 1] : 0) + x - cnt;
+        if (g < G) kbase[g] = (int32_t)(base + ex);
+        const int32_t tot = sh[31];
+        __syncthreads();
+        if (threadIdx.x == 0) carry_s = base + tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        kbase[G] = (int32_t)carry_s;
+        if (carry_s > Kcap) set_status(st, TPC_ERR_CAPACITY, 1);
+    }
+}
+
+__global__ void k_hist(const float* __restrict__ z, const uint16_t* __restrict__ row, int64_t n,
+                       const int64_t* __restrict__ off, int G, Cells cells, int32_t* cnt,
+                       int32_t* key_in, int32_t* slot_in, int64_t Kcap) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int g = group_of(off, G, i);
+        const int r = row[i];
+        const int key = cells.kbase[g] + r * cells.nz[g] + zcell(cells, g, z[i]);
+        int slot = 0;
+        if (key < Kcap) slot = atomicAdd(&cnt[key], 1);
+        key_in[i] = key;
+        slot_in[i] = slot;
+    }
+}
+
+__global__ void k_scatter(const float* __restrict__ y, const float* __restrict__ z,
+                          const uint16_t* __restrict__ row, int64_t n,
+                          const int64_t* __restrict__ off, int G,
+                          const int32_t* __restrict__ key_in, const int32_t* __restrict__ slot_in,
+                          const int32_t* __restrict__ cell_off, int64_t Kcap, float* yb, float* zb,
+                          int32_t* orig, int32_t* grpb, uint8_t* rowb) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int key = key_in[i];
+        if (key >= Kcap) continue;
+        const int64_t pos = cell_off[key] + slot_in[i];
+        yb[pos] = y[i];
+        zb[pos] = z[i];
+        orig[pos] = (int32_t)i;
+        grpb[pos] = group_of(off, G, i);
+        rowb[pos] = (uint8_t)row[i];
+    }
+}
+
+// ---------------------------------------------------------------- S2 ------
+struct NbPrm {
+    float win_y, win_z, chi2_link, sy2, sz2;
+    int max_gap;
+};
+
+// window test, FP32, one rounding per operation
+__device__ __forceinline__ bool in_win(float xa, float ya, float za, float xb, float yb, float zb,
+                                       float wy, float wz) {
+    const float dx = fabsf(__fsub_rn(xb, xa));
+    return fabsf(__fsub_rn(yb, ya)) <= __fmul_rn(wy, dx) &&
+           fabsf(__fsub_rn(zb, za)) <= __fmul_rn(wz, dx);
+}
+
+// triplet D^2 (straight-line interpolation of c between d and u), FP32
+__device__ __forceinline__ float triplet_d2(float xd, float yd, float zd, float xc, float yc,
+                                            float zc, float xu, float yu, float zu, float sy2,
+                                            float sz2) {
+    const float a = __fdiv_rn(__fsub_rn(xc, xd), __fsub_rn(xu, xd));
+    const float yh = __fadd_rn(yd, __fmul_rn(a, __fsub_rn(yu, yd)));
+    const float zh = __fadd_rn(zd, __fmul_rn(a, __fsub_rn(zu, zd)));
+    const float ry = __fsub_rn(yc, yh);
+    const float rz = __fsub_rn(zc, zh);
+    const float b = __fsub_rn(1.0f, a);
+    const float f = __fadd_rn(__fadd_rn(1.0f, __fmul_rn(a, a)), __fmul_rn(b, b));
+    return __fadd_rn(__fdiv_rn(__fmul_rn(ry, ry), __fmul_rn(sy2, f)),
+                     __fdiv_rn(__fmul_rn(rz, rz), __fmul_rn(sz2, f)));
+}
+
+// binned index range of the z cells of row r (group g) covering [zlo, zhi]
+__device__ __forceinline__ void cell_range(const Cells& cells, int g, int r, float zlo, float zhi,
+                                           int& b, int& e) {
+    const int base = cells.kbase[g] + r * cells.nz[g];
+    b = cells.off[base + zcell(cells, g, zlo)];
+    e = cells.off[base + zcell(cells, g, zhi) + 1];
+}
+
+// For each cluster: the (down, up) pair in rows r-gd, r+gu minimising D^2
+// with D^2 <= chi2_link, over gap pairs in order of increasing gd+gu, then
+// gu; ties by the canonical id of u, then of d.
+__global__ void __launch_bounds__(TPB) k_neighbours(
+    int64_t n, const float* __restrict__ yb, const float* __restrict__ zb,
+    const int32_t* __restrict__ orig, const int32_t* __restrict__ grpb,
+    const uint8_t* __restrict__ rowb, Cells cells, const Geo* __restrict__ geo, NbPrm P,
+    int32_t* choice_dn, int32_t* choice_up, float* d2out) {
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const int g = grpb[c], r = rowb[c];
+        const float xc = geo->row_xf[r], yc = yb[c], zc = zb[c];
+        int bd = -1, bu = -1;
+        float bd2 = 0.f;
+        for (int sum = 2; sum <= 2 * P.max_gap && bd < 0; ++sum) {
+            for (int gu = 1; gu <= P.max_gap && bd < 0; ++gu) {
+                const int gd = sum - gu;
+                if (gd < 1 || gd > P.max_gap) continue;
+                const int rd = r - gd, ru = r + gu;
+                if (rd < 0 || ru >= NROW) continue;
+                const float xd = geo->row_xf[rd], xu = geo->row_xf[ru];
+                const float wzd = __fmul_rn(P.win_z, fabsf(__fsub_rn(xd, xc)));
+                const float wzu = __fmul_rn(P.win_z, fabsf(__fsub_rn(xu, xc)));
+                // cell ranges: a superset of the exact window
+                int db, de, ub, ue;
+                cell_range(cells, g, rd, zc - wzd * 1.0001f - 1e-3f, zc + wzd * 1.0001f + 1e-3f, db, de);
+                cell_range(cells, g, ru, zc - wzu * 1.0001f - 1e-3f, zc + wzu * 1.0001f + 1e-3f, ub, ue);
+                int pd = -1, pu = -1;
+                float pd2 = 0.f;
+                int pod = 0, pou = 0;
+                for (int d = db; d < de; ++d) {
+                    const float ydd = yb[d], zdd = zb[d];
+                    if (!in_win(xc, yc, zc, xd, ydd, zdd, P.win_y, P.win_z)) continue;
+                    for (int u = ub; u < ue; ++u) {
+                        const float yuu = yb[u], zuu = zb[u];
+                        if (!in_win(xc, yc, zc, xu, yuu, zuu, P.win_y, P.win_z)) continue;
+                        const float d2 = triplet_d2(xd, ydd, zdd, xc, yc, zc, xu, yuu, zuu, P.sy2, P.sz2);
+                        if (!(d2 <= P.chi2_link)) continue;
+                        bool better = pd < 0 || d2 < pd2;
+                        if (!better && d2 == pd2) {
+                            const int ou = orig[u], od = orig[d];
+                            better = ou < pou || (ou == pou && od < pod);
+                        }
+                        if (better) {
+                            pd = d;
+                            pu = u;
+                            pd2 = d2;
+                            pod = orig[d];
+                            pou = orig[u];
+                        }
+                    }
+                }
+                if (pd >= 0) {
+                    bd = pd;
+                    bu = pu;
+                    bd2 = pd2;
+                }
+            }
+        }
+        choice_dn[c] = bd;
+        choice_up[c] = bu;
+        d2out[c] = bd2;
+    }
+}
+
+__device__ __forceinline__ uint64_t claim_key(float d2, int32_t orig) {
+    return ((uint64_t)__float_as_uint(d2) << 32) | (uint32_t)orig;
+}
+
+// endpoints without a triplet of their own accept their best claimant
+__global__ void k_claims(int64_t n, const int32_t* __restrict__ cdn, const int32_t* __restrict__ cup,
+                         const float* __restrict__ d2, const int32_t* __restrict__ orig,
+                         unsigned long long* claim_up, unsigned long long* claim_dn) {
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const int u = cup[c], d = cdn[c];
+        if (u < 0) continue;
+        const unsigned long long key = claim_key(d2[c], orig[c]);
+        if (cdn[u] < 0) atomicMin(&claim_up[u], key);
+        if (cup[d] < 0) atomicMin(&claim_dn[d], key);
+    }
+}
+
+// links: mutual choices, or the winning claim of an endpoint
+__global__ void k_links(int64_t n, const int32_t* __restrict__ cdn, const int32_t* __restrict__ cup,
+                        const float* __restrict__ d2, const int32_t* __restrict__ orig,
+                        const unsigned long long* __restrict__ claim_up,
+                        const unsigned long long* __restrict__ claim_dn, int32_t* link_dn,
+                        int32_t* link_up) {
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const int u = cup[c], d = cdn[c];
+        if (u < 0) continue;
+        const unsigned long long key = claim_key(d2[c], orig[c]);
+        const int cu = cdn[u];
+        if (cu == (int)c || (cu < 0 && claim_up[u] == key)) {
+            link_up[c] = u;
+            link_dn[u] = (int32_t)c;
+        }
+        const int cd = cup[d];
+        if (cd == (int)c || (cd < 0 && claim_dn[d] == key)) {
+            link_dn[c] = d;
+            link_up[d] = (int32_t)c;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- S3 ------
+__global__ void k_chains(int64_t n, const int32_t* __restrict__ link_dn,
+                         const int32_t* __restrict__ link_up, const int32_t* __restrict__ orig,
+                         const int32_t* __restrict__ grpb, int n_seg, int64_t Scap,
+                         int32_t* seg_start, int32_t* seg_grp, int32_t* seg_canon, int32_t* st) {
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        if (link_dn[c] >= 0 || link_up[c] < 0) continue;
+        int len = 0, cur = (int)c;
+        int32_t mn = 0x7fffffff;
+        while (cur >= 0 && len <= NROW) {
+            mn = min(mn, orig[cur]);
+            ++len;
+            cur = link_up[cur];
+        }
+        if (len < n_seg) continue;
+        const int slot = atomicAdd(&st[ST_NSEG], 1);
+        if (slot >= Scap) {
+            set_status(st, TPC_ERR_CAPACITY, 2);
+            continue;
+        }
+        seg_start[slot] = (int32_t)c;
+        seg_grp[slot] = grpb[c];
+        seg_canon[slot] = mn;
+    }
+}
+
+// ---------------------------------------------------------------- S3b -----
+struct TlPrm {
+    float sy2, sz2, chi2_ext, kb, snp_max, fp64_ratio, fp64_det;
+    int ext_max_miss, n_seg;
+    double bz, seed_snp, seed_qpt;
+    float prior[5];
+};
+
+// Fit the tracklet's hits (row-indexed slot, -1 = empty) in one direction:
+// inward (rows descending, seeded at the outermost) or outward.
+__device__ bool fit_slot(const int32_t* __restrict__ hit, int rmin, int rmax, bool inward,
+                         const float* __restrict__ yb, const float* __restrict__ zb, int sector,
+                         const Geo* __restrict__ geo, const TlPrm& P, KF& s, int* n_fp64) {
+    int n = 0;
+    for (int r = rmin; r <= rmax; ++r) n += hit[r] >= 0;
+    if (n < 3) return false;
+    // first, middle (n/2-th in fit order) and last hit
+    int rows[3], secs[3] = {sector, sector, sector};
+    float ys[3], zs[3];
+    int k = 0, want = n / 2;
+    for (int j = 0; j <= rmax - rmin; ++j) {
+        const int r = inward ? rmax - j : rmin + j;
+        const int h = hit[r];
+        if (h < 0) continue;
+        if (k == 0) { rows[0] = r; ys[0] = yb[h]; zs[0] = zb[h]; }
+        if (k == want) { rows[1] = r; ys[1] = yb[h]; zs[1] = zb[h]; }
+        if (k == n - 1) { rows[2] = r; ys[2] = yb[h]; zs[2] = zb[h]; }
+        ++k;
+    }
+    kf_seed(s, rows, secs, ys, zs, inward, geo, P.bz, P.seed_snp, P.seed_qpt, P.prior);
+    for (int j = 0; j <= rmax - rmin; ++j) {
+        const int r = inward ? rmax - j : rmin + j;
+        const int h = hit[r];
+        if (h < 0) continue;
+        MoveJ mj;
+        if (!kf_move<float>(s, geo->row_xd[r], sector, geo, P.kb, P.snp_max, &mj)) return false;
+        kf_update(s, yb[h], zb[h], P.sy2, P.sz2, P.fp64_ratio, P.fp64_det, n_fp64, &mj);
+    }
+    return true;
+}
+
+// Extend from the current state row by row (dir = -1 inward, +1 outward):
+// in each row take the cluster with the smallest predicted-residual chi2
+// (ties: smaller canonical id) if <= chi2_ext; stop after ext_max_miss empty
+// rows, at the last row, on a transport failure or when the prediction
+// leaves the sector's acceptance.  Returns the last row reached with a hit.
+__device__ int extend_slot(int32_t* __restrict__ hit, int r_last, int dir, KF& s, int g,
+                           const float* __restrict__ yb, const float* __restrict__ zb,
+                           const int32_t* __restrict__ orig, const Cells& cells,
+                           const Geo* __restrict__ geo, const TlPrm& P, int* n_fp64) {
+    const int sector = g % NSEC;
+    int misses = 0;
+    for (int r = r_last + dir; r >= 0 && r < NROW; r += dir) {
+        MoveJ mj;
+        if (!kf_move<float>(s, geo->row_xd[r], sector, geo, P.kb, P.snp_max, &mj)) break;
+        if (fabs((double)s.p[0] + (double)s.lo[0]) > geo->row_xd[r] * geo->tan_half_d) break;
+        const float S00 = s.C[0] + P.sy2, S01 = s.C[1], S11 = s.C[5] + P.sz2;
+        const float det = S00 * S11 - S01 * S01;
+        const float wz = sqrtf(P.chi2_ext * S11) * 1.001f + 1e-3f;
+        const float wy = sqrtf(P.chi2_ext * S00) * 1.001f + 1e-3f;
+        int b, e;
+        cell_range(cells, g, r, s.p[1] - wz, s.p[1] + wz, b, e);
+        int best = -1, bo = 0;
+        float bchi = 0.f;
+        for (int c = b; c < e; ++c) {
+            const float r1 = (zb[c] - s.p[1]) - s.lo[1];
+            if (fabsf(r1) > wz) continue;
+            const float r0 = (yb[c] - s.p[0]) - s.lo[0];
+            if (fabsf(r0) > wy) continue;
+            const float chi = (r0 * r0 * S11 - 2.f * r0 * r1 * S01 + r1 * r1 * S00) / det;
+            if (!(chi <= P.chi2_ext)) continue;
+            const int oc = orig[c];
+            if (best < 0 || chi < bchi || (chi == bchi && oc < bo)) {
+                best = c;
+                bchi = chi;
+                bo = oc;
+            }
+        }
+        if (best >= 0) {
+            kf_update(s, yb[best], zb[best], P.sy2, P.sz2, P.fp64_ratio, P.fp64_det, n_fp64, &mj);
+            hit[r] = best;
+            r_last = r;
+            misses = 0;
+        } else if (++misses >= P.ext_max_miss) {
+            break;
+        }
+    }
+    return r_last;
+}
+
+__global__ void __launch_bounds__(128) k_tracklets(
+    const int32_t* __restrict__ seg_start, const int32_t* __restrict__ seg_grp,
+    const int32_t* __restrict__ seg_canon, const int32_t* __restrict__ link_up,
+    const float* __restrict__ yb, const float* __restrict__ zb, const int32_t* __restrict__ orig,
+    const uint8_t* __restrict__ rowb, Cells cells, const Geo* __restrict__ geo, TlPrm P,
+    int64_t Scap, int32_t* st, int32_t* tl_rowhit, int32_t* tl_n, unsigned long long* tl_key) {
+    const int nseg = min((int64_t)st[ST_NSEG], Scap);
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nseg; s += gridDim.x * blockDim.x) {
+        int32_t* hit = tl_rowhit + (int64_t)s * NROW;
+        for (int r = 0; r < NROW; ++r) hit[r] = -1;
+        const int g = seg_grp[s];
+        const int sector = g % NSEC;
+        int rmin = NROW, rmax = -1;
+        for (int c = seg_start[s]; c >= 0; c = link_up[c]) {
+            const int r = rowb[c];
+            hit[r] = c;
+            rmin = min(rmin, r);
+            rmax = max(rmax, r);
+        }
+        KF kf;
+        if (fit_slot(hit, rmin, rmax, true, yb, zb, sector, geo, P, kf, &st[ST_FP64]))
+            rmin = extend_slot(hit, rmin, -1, kf, g, yb, zb, orig, cells, geo, P, &st[ST_FP64]);
+        if (fit_slot(hit, rmin, rmax, false, yb, zb, sector, geo, P, kf, &st[ST_FP64]))
+            rmax = extend_slot(hit, rmax, +1, kf, g, yb, zb, orig, cells, geo, P, &st[ST_FP64]);
+        int n = 0;
+        for (int r = rmin; r <= rmax; ++r) n += hit[r] >= 0;
+        tl_n[s] = n;
+        tl_key[s] = ((unsigned long long)(NROW * 4 - n) << 32) | (uint32_t)seg_canon[s];
+    }
+}
+
+// every cluster belongs to the best tracklet containing it
+__global__ void k_owner(const int32_t* __restrict__ tl_rowhit, const unsigned long long* __restrict__ tl_key,
+                        int64_t Scap, const int32_t* st, unsigned long long* owner) {
+    const int nseg = min((int64_t)st[ST_NSEG], Scap);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)nseg * NROW;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int h = tl_rowhit[i];
+        if (h >= 0) atomicMin(&owner[h], tl_key[i / NROW]);
+    }
+}
+
+// keep tracklets owning >= n_seg clusters; refit them both ways
+__global__ void __launch_bounds__(128) k_keep(
+    int32_t* tl_rowhit, const unsigned long long* __restrict__ tl_key,
+    const unsigned long long* __restrict__ owner, const int32_t* __restrict__ seg_grp,
+    const float* __restrict__ yb, const float* __restrict__ zb, const int32_t* __restrict__ orig,
+    const Geo* __restrict__ geo, TlPrm P, int64_t Scap, int32_t* st, int32_t* tl_keep,
+    int32_t* tl_canon, int32_t* tl_rmin, int32_t* tl_rmax, float* tl_zin, float* tl_zout,
+    float* tl_state, int32_t* tl_ok, int32_t* grp_tl_cnt) {
+    const int nseg = min((int64_t)st[ST_NSEG], Scap);
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nseg; s += gridDim.x * blockDim.x) {
+        int32_t* hit = tl_rowhit + (int64_t)s * NROW;
+        const unsigned long long key = tl_key[s];
+        int n = 0, rmin = NROW, rmax = -1;
+        int32_t canon = 0x7fffffff;
+        for (int r = 0; r < NROW; ++r) {
+            const int h = hit[r];
+            if (h < 0) continue;
+            if (owner[h] != key) {
+                hit[r] = -1;
+                continue;
+            }
+            ++n;
+            rmin = min(rmin, r);
+            rmax = max(rmax, r);
+            canon = min(canon, orig[h]);
+        }
+        if (n < P.n_seg) {
+            tl_keep[s] = 0;
+            continue;
+        }
+        const int g = seg_grp[s];
+        const int sector = g % NSEC;
+        tl_keep[s] = 1;
+        tl_canon[s] = canon;
+        tl_rmin[s] = rmin;
+        tl_rmax[s] = rmax;
+        tl_zin[s] = zb[hit[rmin]];
+        tl_zout[s] = zb[hit[rmax]];
+        float* out = tl_state + (int64_t)s * 40;
+        KF kf;
+        int ok = 0;
+        if (fit_slot(hit, rmin, rmax, true, yb, zb, sector, geo, P, kf, &st[ST_FP64])) {
+            ok |= 1;
+            for (int i = 0; i < 3; ++i) kf.p[i] += kf.lo[i];
+            for (int i = 0; i < 5; ++i) out[i] = kf.p[i];
+            for (int i = 0; i < 15; ++i) out[5 + i] = kf.C[i];
+        }
+        if (fit_slot(hit, rmin, rmax, false, yb, zb, sector, geo, P, kf, &st[ST_FP64])) {
+            ok |= 2;
+            for (int i = 0; i < 3; ++i) kf.p[i] += kf.lo[i];
+            for (int i = 0; i < 5; ++i) out[20 + i] = kf.p[i];
+            for (int i = 0; i < 15; ++i) out[25 + i] = kf.C[i];
+        }
+        tl_ok[s] = ok;
+        atomicAdd(&st[ST_NTL], 1);
+        atomicAdd(&grp_tl_cnt[g], 1);
+    }
+}
+
+__global__ void k_tl_scatter(const int32_t* __restrict__ tl_keep, const int32_t* __restrict__ seg_grp,
+                             const int32_t* __restrict__ grp_tl_off, int64_t Scap, const int32_t* st,
+                             int32_t* grp_tl_cur, int32_t* tl_sorted) {
+    const int nseg = min((int64_t)st[ST_NSEG], Scap);
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nseg; s += gridDim.x * blockDim.x) {
+        if (!tl_keep[s]) continue;
+        const int g = seg_grp[s];
+        tl_sorted[grp_tl_off[g] + atomicAdd(&grp_tl_cur[g], 1)] = s;
+    }
+}
+
+// ---------------------------------------------------------------- S4 ------
+struct MgPrm {
+    int merge_gap, merge_ov;
+    float mz_slope, mz_margin;
+    double chi2_merge, kb, snp_max;
+};
+
+// 5x5 SPD chi2 = dp^T M^-1 dp by Cholesky (FP64); false if not SPD
+__device__ bool chol_chi2(const double dp[5], const double M[15], double& out) {
+    double Lm[5][5];
+    for (int i = 0; i < 5; ++i)
+        for (int j = 0; j <= i; ++j) {
+            double s = M[sx(i, j)];
+            for (int l = 0; l < j; ++l) s -= Lm[i][l] * Lm[j][l];
+            if (i == j) {
+                if (!(s > 0.0)) return false;
+                Lm[i][i] = sqrt(s);
+            } else {
+                Lm[i][j] = s / Lm[j][j];
+            }
+        }
+    double v[5];
+    out = 0.0;
+    for (int i = 0; i < 5; ++i) {
+        double s = dp[i];
+        for (int l = 0; l < i; ++l) s -= Lm[i][l] * v[l];
+        v[i] = s / Lm[i][i];
+        out += v[i] * v[i];
+    }
+    return true;
+}
+
+// For tracklet B (inner end), candidates A (outer end) in the same or a
+// phi-adjacent sector of the same side and event: A's outward-fit state at
+// its outermost row is moved to B's innermost plane (FP64) and compared with
+// B's inward-fit state there.
+__global__ void __launch_bounds__(128) k_merge_cand(
+    const int32_t* __restrict__ tl_keep, const int32_t* __restrict__ tl_ok,
+    const int32_t* __restrict__ seg_grp, const int32_t* __restrict__ tl_rmin,
+    const int32_t* __restrict__ tl_rmax, const float* __restrict__ tl_zin,
+    const float* __restrict__ tl_zout, const float* __restrict__ tl_state,
+    const int32_t* __restrict__ grp_tl_off, const int32_t* __restrict__ tl_sorted,
+    const Geo* __restrict__ geo, MgPrm P, int64_t Scap, int32_t* st, int32_t* cand_n,
+    int32_t* cand_a, float* cand_c2) {
+    const int nseg = min((int64_t)st[ST_NSEG], Scap);
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nseg; b += gridDim.x * blockDim.x) {
+        cand_n[b] = 0;
+        if (!tl_keep[b] || !(tl_ok[b] & 1)) continue;
+        const int gb = seg_grp[b];
+        const int ev = gb / NSEC, sb = gb % NSEC, side = sb / NPHI, phb = sb % NPHI;
+        const int rb = tl_rmin[b];
+        const float zb_in = tl_zin[b];
+        const float* stb = tl_state + (int64_t)b * 40;
+        int nc = 0;
+        for (int dp = -1; dp <= 1; ++dp) {
+            const int sa = side * NPHI + (phb + dp + NPHI) % NPHI;
+            const int ga = ev * NSEC + sa;
+            for (int q = grp_tl_off[ga]; q < grp_tl_off[ga + 1]; ++q) {
+                const int a = tl_sorted[q];
+                if (a == b || !(tl_ok[a] & 2)) continue;
+                const int gap = rb - tl_rmax[a];
+                const int min_gap = dp == 0 ? 0 : -P.merge_ov;
+                if (gap < min_gap || gap > P.merge_gap) continue;
+                const float dxr = fabsf(__fsub_rn(geo->row_xf[rb], geo->row_xf[tl_rmax[a]]));
+                if (!(fabsf(__fsub_rn(zb_in, tl_zout[a])) <=
+                      __fadd_rn(__fmul_rn(P.mz_slope, dxr), P.mz_margin)))
+                    continue;
+                const float* sta = tl_state + (int64_t)a * 40;
+                KFD s;
+                s.x = geo->row_xd[tl_rmax[a]];
+                s.frame = sa;
+                for (int i = 0; i < 5; ++i) s.p[i] = sta[20 + i];
+                s.lo[0] = s.lo[1] = s.lo[2] = 0.0;
+                for (int i = 0; i < 15; ++i) s.C[i] = sta[25 + i];
+                if (!kf_move<double>(s, geo->row_xd[rb], sb, geo, P.kb, P.snp_max)) continue;
+                double d[5], M[15];
+                for (int i = 0; i < 5; ++i) d[i] = (double)stb[i] - s.p[i];
+                for (int i = 0; i < 15; ++i) M[i] = s.C[i] + (double)stb[5 + i];
+                double c2;
+                if (!chol_chi2(d, M, c2) || !(c2 <= P.chi2_merge)) continue;
+                if (nc < MAX_CAND) {
+                    cand_a[(int64_t)b * MAX_CAND + nc] = a;
+                    cand_c2[(int64_t)b * MAX_CAND + nc] = (float)c2;
+                } else {
+                    set_status(st, TPC_ERR_CAPACITY, 3);
+                }
+                ++nc;
+            }
+        }
+        cand_n[b] = min(nc, MAX_CAND);
+        if (nc) atomicAdd(&st[ST_NCAND], min(nc, MAX_CAND));
+    }
+}
+
+// Greedy matching in ascending chi2 (ties: canonical ids), computed as
+// rounds of locally dominant candidates: a candidate whose key is the best
+// among the live candidates of its A (outer end) and of its B (inner end) is
+// accepted; candidates touching an accepted end die.  One block.
+__global__ void __launch_bounds__(1024) k_match(
+    const int32_t* __restrict__ cand_n, const int32_t* __restrict__ cand_a,
+    const float* __restrict__ cand_c2, const int32_t* __restrict__ tl_canon, int64_t Scap,
+    int32_t* st, unsigned long long* best_a, unsigned long long* best_b, int32_t* nxt,
+    int32_t* prv) {
+    __shared__ int live;
+    const int nseg = min((int64_t)st[ST_NSEG], Scap);
+    for (int round = 0; round < 4096; ++round) {
+        if (threadIdx.x == 0) live = 0;
+        __syncthreads();
+        for (int b = threadIdx.x; b < nseg; b += blockDim.x) {
+            if (prv[b] >= 0) continue;
+            for (int i = 0; i < cand_n[b]; ++i) {
+                const int a = cand_a[(int64_t)b * MAX_CAND + i];
+                if (nxt[a] >= 0) continue;
+                const uint64_t c2 = __float_as_uint(cand_c2[(int64_t)b * MAX_CAND + i]);
+                atomicMin(&best_a[a], (c2 << 32) | (uint32_t)tl_canon[b]);
+                atomicMin(&best_b[b], (c2 << 32) | (uint32_t)tl_canon[a]);
+                live = 1;
+            }
+        }
+        __syncthreads();
+        if (!live) break;
+        for (int b = threadIdx.x; b < nseg; b += blockDim.x) {
+            if (prv[b] >= 0) continue;
+            for (int i = 0; i < cand_n[b]; ++i) {
+                const int a = cand_a[(int64_t)b * MAX_CAND + i];
+                if (nxt[a] >= 0) continue;
+                const uint64_t c2 = __float_as_uint(cand_c2[(int64_t)b * MAX_CAND + i]);
+                if (best_a[a] == ((c2 << 32) | (uint32_t)tl_canon[b]) &&
+                    best_b[b] == ((c2 << 32) | (uint32_t)tl_canon[a])) {
+                    nxt[a] = b;
+                    prv[b] = a;
+                    atomicAdd(&st[ST_NMERGE], 1);
+                }
+            }
+        }
+        __syncthreads();
+        for (int b = threadIdx.x; b < nseg; b += blockDim.x) {
+            best_b[b] = KEY_MAX;
+            best_a[b] = KEY_MAX;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- output --
+// Chains of merged tracklets (walk from the outermost, i.e. nxt < 0).
+__global__ void k_track_heads(const int32_t* __restrict__ tl_keep, const int32_t* __restrict__ nxt,
+                              const int32_t* __restrict__ prv, const int32_t* __restrict__ tl_canon,
+                              const int32_t* __restrict__ tl_rowhit, int n_min, int64_t Scap,
+                              const int32_t* st, int32_t* trk_flag, int32_t* trk_len_at,
+                              int32_t* trk_head_at) {
+    const int nseg = min((int64_t)st[ST_NSEG], Scap);
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nseg; s += gridDim.x * blockDim.x) {
+        if (!tl_keep[s] || nxt[s] >= 0) continue;
+        int len = 0, guard = 0;
+        int32_t canon = 0x7fffffff;
+        for (int t = s; t >= 0 && guard < 4096; t = prv[t], ++guard) {
+            const int32_t* hit = tl_rowhit + (int64_t)t * NROW;
+            for (int r = 0; r < NROW; ++r) len += hit[r] >= 0;
+            canon = min(canon, tl_canon[t]);
+        }
+        if (len < n_min) continue;
+        trk_flag[canon] = 1;
+        trk_len_at[canon] = len;
+        trk_head_at[canon] = s;
+    }
+}
+
+__global__ void k_track_len(int64_t n, const int32_t* __restrict__ trk_flag,
+                            const int32_t* __restrict__ trk_rank, const int32_t* __restrict__ trk_len_at,
+                            int32_t track_cap, int32_t* len_by_rank, int32_t* st, int32_t* n_tracks_dev) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (!trk_flag[i]) continue;
+        const int r = trk_rank[i];
+        if (r < track_cap) len_by_rank[r] = trk_len_at[i];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const int T = trk_rank[n];
+        st[ST_NTRACKS] = T;
+        *n_tracks_dev = min(T, track_cap);
+        if (T > track_cap) set_status(st, TPC_ERR_CAPACITY, 4);
+    }
+}
+
+__global__ void k_track_write(int64_t n, const int32_t* __restrict__ trk_flag,
+                              const int32_t* __restrict__ trk_rank,
+                              const int32_t* __restrict__ trk_head_at, const int32_t* __restrict__ prv,
+                              const int32_t* __restrict__ tl_rowhit, const int32_t* __restrict__ orig,
+                              const int32_t* __restrict__ trk_off, int32_t track_cap, int32_t* toc,
+                              int32_t* trk_hits) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (!trk_flag[i]) continue;
+        const int r = trk_rank[i];
+        if (r >= track_cap) continue;
+        int o = trk_off[r], guard = 0;
+        for (int t = trk_head_at[i]; t >= 0 && guard < 4096; t = prv[t], ++guard) {
+            const int32_t* hit = tl_rowhit + (int64_t)t * NROW;
+            for (int rr = NROW - 1; rr >= 0; --rr) {
+                const int h = hit[rr];
+                if (h < 0) continue;
+                const int oi = orig[h];
+                trk_hits[o++] = oi;
+                toc[oi] = r;
+            }
+        }
+    }
+}
+
+__global__ void k_fill_u64(unsigned long long* p, int64_t n, unsigned long long v) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
+__global__ void k_fill_u32(uint32_t* p, int64_t n, uint32_t v) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
+}  // namespace
+
+#define TPC_TRY(x)                                  \
+    do {                                            \
+        cudaError_t e_ = (x);                       \
+        if (e_ != cudaSuccess) return e_;           \
+    } while (0)
+
+cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hits,
+                     int32_t* n_tracks_dev, int32_t track_cap, cudaStream_t s) {
+    const Workspace& W = c->ws;
+    const Layout& L = W.L;
+    const tpc_params& p = c->prm;
+    const int64_t n = c->n;
+    const int G = c->n_events * NSEC;
+    int32_t* st = W.at<int32_t>(L.status);
+    const Geo* geo = W.at<Geo>(L.geo);
+    int32_t* scan_tmp = W.at<int32_t>(L.scan_a);
+
+    c->mark(0, s);
+    // per-call counters (the status word and the FP64 count are cumulative)
+    TPC_TRY(fill_i32(st + ST_NSEG, ST_NTRACKS - ST_NSEG + 1, 0, s));
+    // S1: z range per group, cells, histogram, scan, scatter
+    k_fill_u32<<<grid_for(G), TPB, 0, s>>>(W.at<uint32_t>(L.g_zmin_u), G, 0xffffffffu);
+    k_fill_u32<<<grid_for(G), TPB, 0, s>>>(W.at<uint32_t>(L.g_zmax_u), G, 0u);
+    k_zrange<<<grid_for(n), TPB, 0, s>>>(c->z, n, c->evt_sector_off, G, W.at<uint32_t>(L.g_zmin_u),
+                                         W.at<uint32_t>(L.g_zmax_u));
+    k_cells<<<1, 1024, 0, s>>>(c->evt_sector_off, G, W.at<uint32_t>(L.g_zmin_u),
+                               W.at<uint32_t>(L.g_zmax_u), W.at<float>(L.g_zmin), W.at<float>(L.g_inv),
+                               W.at<int32_t>(L.g_nz), W.at<int32_t>(L.g_kbase), L.K, st);
+    Cells cells{W.at<float>(L.g_zmin), W.at<float>(L.g_inv), W.at<int32_t>(L.g_nz),
+                W.at<int32_t>(L.g_kbase), W.at<int32_t>(L.cell_off)};
+    TPC_TRY(fill_i32(W.at<int32_t>(L.cell_cnt), L.K + 1, 0, s));
+    k_hist<<<grid_for(n), TPB, 0, s>>>(c->z, c->row, n, c->evt_sector_off, G, cells,
+                                       W.at<int32_t>(L.cell_cnt), W.at<int32_t>(L.key_in),
+                                       W.at<int32_t>(L.slot_in), L.K);
+    TPC_TRY(scan_i32(W.at<int32_t>(L.cell_cnt), W.at<int32_t>(L.cell_off), L.K, scan_tmp, s));
+    float* yb = W.at<float>(L.yb);
+    float* zb = W.at<float>(L.zb);
+    int32_t* orig = W.at<int32_t>(L.orig);
+    int32_t* grpb = W.at<int32_t>(L.grpb);
+    uint8_t* rowb = W.at<uint8_t>(L.rowb);
+    k_scatter<<<grid_for(n), TPB, 0, s>>>(c->y, c->z, c->row, n, c->evt_sector_off, G,
+                                          W.at<int32_t>(L.key_in), W.at<int32_t>(L.slot_in),
+                                          W.at<int32_t>(L.cell_off), L.K, yb, zb, orig, grpb, rowb);
+    TPC_TRY(cudaGetLastError());
+
+    c->mark(1, s);
+    // S2: neighbours, claims, links
+    int32_t* cdn = W.at<int32_t>(L.choice_dn);
+    int32_t* cup = W.at<int32_t>(L.choice_up);
+    float* d2 = W.at<float>(L.d2);
+    NbPrm nb{p.win_y, p.win_z, p.chi2_link, p.sigma_y2, p.sigma_z2, p.max_gap};
+    k_neighbours<<<grid_for(n), TPB, 0, s>>>(n, yb, zb, orig, grpb, rowb, cells, geo, nb, cdn, cup, d2);
+    c->mark(2, s);
+    auto* claim_up = W.at<unsigned long long>(L.claim_up);
+    auto* claim_dn = W.at<unsigned long long>(L.claim_dn);
+    k_fill_u64<<<grid_for(n), TPB, 0, s>>>(claim_up, n, KEY_MAX);
+    k_fill_u64<<<grid_for(n), TPB, 0, s>>>(claim_dn, n, KEY_MAX);
+    k_claims<<<grid_for(n), TPB, 0, s>>>(n, cdn, cup, d2, orig, claim_up, claim_dn);
+    int32_t* ldn = W.at<int32_t>(L.link_dn);
+    int32_t* lup = W.at<int32_t>(L.link_up);
+    TPC_TRY(fill_i32(ldn, n, -1, s));
+    TPC_TRY(fill_i32(lup, n, -1, s));
+    k_links<<<grid_for(n), TPB, 0, s>>>(n, cdn, cup, d2, orig, claim_up, claim_dn, ldn, lup);
+
+    c->mark(3, s);
+    // S3: chains
+    k_chains<<<grid_for(n), TPB, 0, s>>>(n, ldn, lup, orig, grpb, p.n_seg, L.S,
+                                         W.at<int32_t>(L.seg_start), W.at<int32_t>(L.seg_grp),
+                                         W.at<int32_t>(L.seg_canon), st);
+    c->mark(4, s);
+    // S3b: tracklets
+    TlPrm tp;
+    tp.sy2 = p.sigma_y2;
+    tp.sz2 = p.sigma_z2;
+    tp.chi2_ext = p.chi2_ext;
+    tp.kb = (float)(KAPPA * (double)p.bz);
+    tp.snp_max = p.snp_max;
+    tp.fp64_ratio = p.fp64_ratio;
+    tp.fp64_det = p.fp64_det;
+    tp.ext_max_miss = p.ext_max_miss;
+    tp.n_seg = p.n_seg;
+    tp.bz = p.bz;
+    tp.seed_snp = p.seed_snp_max;
+    tp.seed_qpt = p.seed_qpt_max;
+    for (int i = 0; i < 5; ++i) tp.prior[i] = p.prior[i];
+    const unsigned sgrid = grid_for(L.S, 128);
+    int32_t* tl_rowhit = W.at<int32_t>(L.tl_rowhit);
+    auto* tl_key = W.at<unsigned long long>(L.tl_key);
+    k_tracklets<<<sgrid, 128, 0, s>>>(W.at<int32_t>(L.seg_start), W.at<int32_t>(L.seg_grp),
+                                      W.at<int32_t>(L.seg_canon), lup, yb, zb, orig, rowb, cells, geo,
+                                      tp, L.S, st, tl_rowhit, W.at<int32_t>(L.tl_n), tl_key);
+    c->mark(5, s);
+    auto* owner = W.at<unsigned long long>(L.owner);
+    k_fill_u64<<<grid_for(n), TPB, 0, s>>>(owner, n, KEY_MAX);
+    k_owner<<<grid_for(L.S * NROW), TPB, 0, s>>>(tl_rowhit, tl_key, L.S, st, owner);
+    int32_t* grp_cnt = W.at<int32_t>(L.grp_tl_cnt);
+    TPC_TRY(fill_i32(grp_cnt, G + 1, 0, s));
+    k_keep<<<sgrid, 128, 0, s>>>(tl_rowhit, tl_key, owner, W.at<int32_t>(L.seg_grp), yb, zb, orig, geo,
+                                 tp, L.S, st, W.at<int32_t>(L.tl_keep), W.at<int32_t>(L.tl_canon),
+                                 W.at<int32_t>(L.tl_rmin), W.at<int32_t>(L.tl_rmax),
+                                 W.at<float>(L.tl_zin), W.at<float>(L.tl_zout),
+                                 W.at<float>(L.tl_state), W.at<int32_t>(L.tl_ok), grp_cnt);
+    TPC_TRY(scan_i32(grp_cnt, W.at<int32_t>(L.grp_tl_off), G, scan_tmp, s));
+    TPC_TRY(fill_i32(W.at<int32_t>(L.grp_tl_cur), G, 0, s));
+    k_tl_scatter<<<sgrid, 128, 0, s>>>(W.at<int32_t>(L.tl_keep), W.at<int32_t>(L.seg_grp),
+                                       W.at<int32_t>(L.grp_tl_off), L.S, st,
+                                       W.at<int32_t>(L.grp_tl_cur), W.at<int32_t>(L.tl_sorted));
+    c->mark(6, s);
+    // S4: merge candidates and greedy matching
+    MgPrm mp{p.merge_max_row_gap, p.merge_max_overlap, p.merge_z_slope, p.merge_z_margin,
+             (double)p.chi2_merge, KAPPA * (double)p.bz, (double)p.snp_max};
+    k_merge_cand<<<sgrid, 128, 0, s>>>(W.at<int32_t>(L.tl_keep), W.at<int32_t>(L.tl_ok),
+                                       W.at<int32_t>(L.seg_grp), W.at<int32_t>(L.tl_rmin),
+                                       W.at<int32_t>(L.tl_rmax), W.at<float>(L.tl_zin),
+                                       W.at<float>(L.tl_zout), W.at<float>(L.tl_state),
+                                       W.at<int32_t>(L.grp_tl_off), W.at<int32_t>(L.tl_sorted), geo, mp,
+                                       L.S, st, W.at<int32_t>(L.cand_n), W.at<int32_t>(L.cand_a),
+                                       W.at<float>(L.cand_c2));
+    c->mark(7, s);
+    int32_t* nxt = W.at<int32_t>(L.nxt);
+    int32_t* prv = W.at<int32_t>(L.prv);
+    TPC_TRY(fill_i32(nxt, L.S, -1, s));
+    TPC_TRY(fill_i32(prv, L.S, -1, s));
+    auto* best_a = W.at<unsigned long long>(L.best_a);
+    auto* best_b = W.at<unsigned long long>(L.best_b);
+    k_fill_u64<<<grid_for(L.S), TPB, 0, s>>>(best_a, L.S, KEY_MAX);
+    k_fill_u64<<<grid_for(L.S), TPB, 0, s>>>(best_b, L.S, KEY_MAX);
+    k_match<<<1, 1024, 0, s>>>(W.at<int32_t>(L.cand_n), W.at<int32_t>(L.cand_a), W.at<float>(L.cand_c2),
+                               W.at<int32_t>(L.tl_canon), L.S, st, best_a, best_b, nxt, prv);
+    c->mark(8, s);
+    // output: canonical order by smallest input index
+    int32_t* flag = W.at<int32_t>(L.trk_flag);
+    TPC_TRY(fill_i32(flag, n, 0, s));
+    k_track_heads<<<sgrid, 128, 0, s>>>(W.at<int32_t>(L.tl_keep), nxt, prv, W.at<int32_t>(L.tl_canon),
+                                        tl_rowhit, p.n_min, L.S, st, flag, W.at<int32_t>(L.trk_len_at),
+                                        W.at<int32_t>(L.trk_head_at));
+    int32_t* rank = W.at<int32_t>(L.trk_rank);
+    TPC_TRY(scan_i32(flag, rank, n, scan_tmp, s));
+    int32_t* len_by_rank = W.at<int32_t>(L.len_by_rank);
+    TPC_TRY(fill_i32(len_by_rank, track_cap, 0, s));
+    k_track_len<<<grid_for(n), TPB, 0, s>>>(n, flag, rank, W.at<int32_t>(L.trk_len_at), track_cap,
+                                            len_by_rank, st, n_tracks_dev);
+    TPC_TRY(scan_i32(len_by_rank, trk_off, track_cap, scan_tmp, s));
+    TPC_TRY(fill_i32(toc, n, -1, s));
+    k_track_write<<<grid_for(n), TPB, 0, s>>>(n, flag, rank, W.at<int32_t>(L.trk_head_at), prv,
+                                              tl_rowhit, orig, trk_off, track_cap, toc, trk_hits);
+    c->mark(9, s);
+    return cudaGetLastError();
+}
+
+}  // namespace tpc

@@ -1,0 +1,107 @@
+// Internal declarations shared by the translation units of libtpctrack.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/tpc_track.h"
+
+namespace tpc {
+
+constexpr int NSEC = 36;
+constexpr int NPHI = 18;
+constexpr int NROW = 152;
+constexpr int MAX_CAND = 16;     // merge candidates kept per tracklet
+constexpr int CELL_OCC = 8;      // target clusters per (row, z-cell)
+constexpr int NZ_MAX = 8192;     // z cells per row at most
+
+// Geometry table written into the workspace at set-up.
+struct Geo {
+    double row_xd[NROW];   // pad-row plane x (cm), FP64
+    float row_xf[NROW];    // the same rounded to FP32 (neighbour decisions)
+    float tan_half;        // tan(10 deg)
+    float pad0;
+    double tan_half_d;
+    double alpha[NPHI];    // sector centre angles
+    double da_cos[NPHI];   // cos / sin of the frame rotation from phi-index
+    double da_sin[NPHI];   // i to phi-index (i + k) mod 18, k = 0..17
+};
+
+// Device status word and counters (int32 slots in the workspace).
+enum StatusSlot {
+    ST_STATUS = 0, ST_DETAIL, ST_NSEG, ST_NTL, ST_NCAND, ST_NMERGE, ST_NTRACKS, ST_FP64,
+    ST_MATCH_LIVE, ST_N_SLOTS = 16
+};
+
+// Workspace layout: byte offsets of every buffer, computed from capacities.
+struct Layout {
+    int64_t N = 0;   // max clusters
+    int32_t E = 0;   // max events
+    int64_t G = 0;   // groups = E*36
+    int64_t K = 0;   // cell capacity
+    int64_t S = 0;   // segment / tracklet slots
+    int64_t T = 0;   // output tracks capacity used internally
+    int64_t scan_tmp = 0;
+    size_t total = 0;
+    // offsets
+    size_t geo, status, g_zmin_u, g_zmax_u, g_nz, g_inv, g_zmin, g_kbase, key_in, slot_in,
+        cell_cnt, cell_off, yb, zb, orig, grpb, rowb, choice_dn, choice_up, d2, claim_up,
+        claim_dn, link_dn, link_up, owner, seg_start, seg_len, seg_grp, seg_canon, tl_rowhit,
+        tl_n, tl_key, tl_keep, tl_canon, tl_rmin, tl_rmax, tl_zin, tl_zout, tl_state, tl_ok,
+        grp_tl_cnt, grp_tl_off, grp_tl_cur, tl_sorted, cand_n, cand_a, cand_c2, best_a, best_b,
+        nxt, prv, trk_flag, trk_rank, trk_len_at, trk_head_at, len_by_rank, scan_a, scan_b,
+        adj_grad, adj_chi2, adj_ckpt;
+    int64_t adj_tracks = 0;  // tracks the adjoint scratch holds per launch chunk
+};
+
+Layout make_layout(int64_t max_clusters, int32_t max_events);
+
+struct Workspace {
+    char* base = nullptr;
+    Layout L;
+    template <class T> T* at(size_t off) const { return reinterpret_cast<T*>(base + off); }
+};
+
+}  // namespace tpc
+
+struct tpc_ctx {
+    tpc_params prm;
+    tpc::Workspace ws;
+    bool have_ws = false;
+    // loaded batch
+    const float* y = nullptr;
+    const float* z = nullptr;
+    const uint16_t* row = nullptr;
+    const uint16_t* charge = nullptr;
+    const int64_t* evt_sector_off = nullptr;
+    int64_t n = 0;
+    int32_t n_events = 0;
+    bool have_clusters = false;
+    std::string last_error;
+    // stage timing: marks 0..9 around the find stages, 10/11 fit, 12/13 adjoint
+    bool timing = false;
+    cudaEvent_t marks[16] = {};
+    void mark(int i, cudaStream_t s) {
+        if (timing) cudaEventRecord(marks[i], s);
+    }
+};
+
+namespace tpc {
+// launchers (return cudaGetLastError of their launches)
+cudaError_t init_geo(const Workspace& ws, cudaStream_t s);
+cudaError_t reset_status(const Workspace& ws, cudaStream_t s);
+cudaError_t validate_clusters(const tpc_ctx* c, cudaStream_t s);
+cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hits,
+                     int32_t* n_tracks_dev, int32_t track_cap, cudaStream_t s);
+cudaError_t run_fit(tpc_ctx* c, const int32_t* trk_off, const int32_t* trk_hits, int32_t n_tracks,
+                    const int32_t* n_tracks_dev, float* params, float* cov, float* chi2,
+                    int32_t* ndf, cudaStream_t s);
+cudaError_t run_adjoint(tpc_ctx* c, const int32_t* trk_off, const int32_t* trk_hits,
+                        int32_t n_tracks, const double* align, double* chi2_total, double* grad,
+                        cudaStream_t s);
+cudaError_t fill_i32(int32_t* p, int64_t n, int32_t v, cudaStream_t s);
+// exclusive scan of in[0..L) into out[0..L] (out[L] = total); tmp from the workspace
+cudaError_t scan_i32(const int32_t* in, int32_t* out, int64_t L, int32_t* tmp, cudaStream_t s);
+}  // namespace tpc

@@ -1,0 +1,309 @@
+"""Thin Python binding of libtpctrack (include/tpc_track.h).
+
+Argument marshalling only: tensors are passed to the C ABI as device
+pointers, every step of the tracking path runs in the library's CUDA
+kernels.  PyTorch provides device memory and streams.  There is no fallback:
+if the library is not built, or no CUDA device is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+from . import build as _build
+
+TPC_OK, TPC_ERR_ARG, TPC_ERR_CUDA, TPC_ERR_CAPACITY, TPC_ERR_TIMEOUT, TPC_ERR_STATE, \
+    TPC_ERR_INPUT = range(7)
+STATUS_NAMES = {0: "TPC_OK", 1: "TPC_ERR_ARG", 2: "TPC_ERR_CUDA", 3: "TPC_ERR_CAPACITY",
+                4: "TPC_ERR_TIMEOUT", 5: "TPC_ERR_STATE", 6: "TPC_ERR_INPUT"}
+
+EXPORTS = ("tpc_default_params", "tpc_create", "tpc_destroy", "tpc_workspace_bytes",
+           "tpc_set_workspace", "tpc_load_clusters", "tpc_find_tracks", "tpc_fit_tracks",
+           "tpc_fit_adjoint", "tpc_get_stats", "tpc_last_error", "tpc_reset_status",
+           "tpc_stage_timing", "tpc_stage_times")
+STAGE_NAMES = ("bin", "neighbours", "links", "chains", "tracklets", "select", "merge_cand",
+               "match", "output", "fit", "adjoint", "find_total")
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("win_y", C.c_float), ("win_z", C.c_float), ("chi2_link", C.c_float),
+        ("sigma_y2", C.c_float), ("sigma_z2", C.c_float),
+        ("max_gap", C.c_int32), ("n_seg", C.c_int32), ("n_min", C.c_int32),
+        ("merge_max_row_gap", C.c_int32), ("merge_max_overlap", C.c_int32),
+        ("merge_z_slope", C.c_float), ("merge_z_margin", C.c_float),
+        ("chi2_merge", C.c_float), ("chi2_ext", C.c_float), ("ext_max_miss", C.c_int32),
+        ("bz", C.c_float), ("prior", C.c_float * 5), ("seed_snp_max", C.c_float),
+        ("seed_qpt_max", C.c_float), ("snp_max", C.c_float),
+        ("fp64_ratio", C.c_float), ("fp64_det", C.c_float),
+    ]
+
+
+class Stats(C.Structure):
+    _fields_ = [
+        ("n_clusters", C.c_int64), ("n_segments", C.c_int32), ("n_tracklets", C.c_int32),
+        ("n_merge_cand", C.c_int32), ("n_merges", C.c_int32), ("n_tracks", C.c_int32),
+        ("n_fp64_updates", C.c_int32), ("status", C.c_int32), ("status_detail", C.c_int32),
+    ]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library(build_if_missing: bool = True):
+    """Loads libtpctrack.so (building it first if asked)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError("libtpctrack.so is not built (run __graft_entry__.build())")
+    lib = C.CDLL(_build.LIB)
+    vp, i32, i64, sz = C.c_void_p, C.c_int32, C.c_int64, C.c_size_t
+    lib.tpc_default_params.argtypes = [vp]
+    lib.tpc_default_params.restype = None
+    lib.tpc_create.argtypes = [vp, vp]
+    lib.tpc_destroy.argtypes = [vp]
+    lib.tpc_destroy.restype = None
+    lib.tpc_workspace_bytes.argtypes = [vp, i64, i32]
+    lib.tpc_workspace_bytes.restype = sz
+    lib.tpc_set_workspace.argtypes = [vp, vp, sz, i64, i32]
+    lib.tpc_load_clusters.argtypes = [vp, vp, vp, vp, vp, i64, vp, i32, vp]
+    lib.tpc_find_tracks.argtypes = [vp, vp, vp, vp, vp, i32, vp]
+    lib.tpc_fit_tracks.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp, vp, vp]
+    lib.tpc_fit_adjoint.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp]
+    lib.tpc_get_stats.argtypes = [vp, vp, vp]
+    lib.tpc_last_error.argtypes = [vp, C.c_char_p, sz]
+    lib.tpc_reset_status.argtypes = [vp, vp]
+    lib.tpc_stage_timing.argtypes = [vp, C.c_int]
+    lib.tpc_stage_times.argtypes = [vp, vp]
+    for name in EXPORTS:
+        f = getattr(lib, name)
+        if name not in ("tpc_default_params", "tpc_destroy", "tpc_workspace_bytes"):
+            f.restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    load_library().tpc_default_params(C.byref(p))
+    for k, v in kw.items():
+        if k == "prior":
+            for i in range(5):
+                p.prior[i] = v[i]
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+class TPCError(RuntimeError):
+    pass
+
+
+def _check(ctx, rc, what):
+    if rc != TPC_OK:
+        buf = C.create_string_buffer(512)
+        load_library().tpc_last_error(ctx, buf, 512)
+        raise TPCError(f"{what}: {STATUS_NAMES.get(rc, rc)} {buf.value.decode(errors='replace')}")
+
+
+def _need(t, dtype, name):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous CUDA {dtype} tensor")
+
+
+# --- the C ABI, one Python function per entry point --------------------------
+
+def tpc_create(params: Params | None = None):
+    ctx = C.c_void_p()
+    rc = load_library().tpc_create(C.byref(ctx), C.byref(params) if params is not None else None)
+    if rc != TPC_OK:
+        raise TPCError(f"tpc_create: {STATUS_NAMES.get(rc, rc)}")
+    return ctx
+
+
+def tpc_destroy(ctx):
+    load_library().tpc_destroy(ctx)
+
+
+def tpc_workspace_bytes(ctx, max_clusters: int, max_events: int) -> int:
+    return int(load_library().tpc_workspace_bytes(ctx, int(max_clusters), int(max_events)))
+
+
+def tpc_set_workspace(ctx, ws: torch.Tensor, max_clusters: int, max_events: int):
+    _need(ws, torch.uint8, "workspace")
+    rc = load_library().tpc_set_workspace(ctx, _ptr(ws), ws.numel(), int(max_clusters),
+                                          int(max_events))
+    _check(ctx, rc, "tpc_set_workspace")
+
+
+def tpc_load_clusters(ctx, y, z, row, charge, evt_sector_off, n_events, stream=None):
+    _need(y, torch.float32, "y")
+    _need(z, torch.float32, "z")
+    _need(row, torch.uint16, "row")
+    if charge is not None:
+        _need(charge, torch.uint16, "charge")
+    _need(evt_sector_off, torch.int64, "evt_sector_off")
+    rc = load_library().tpc_load_clusters(ctx, _ptr(y), _ptr(z), _ptr(row), _ptr(charge),
+                                          y.numel(), _ptr(evt_sector_off), int(n_events),
+                                          _stream(stream))
+    _check(ctx, rc, "tpc_load_clusters")
+
+
+def tpc_find_tracks(ctx, track_of_cluster, trk_off, trk_hits, n_tracks_dev, stream=None):
+    for t, n in ((track_of_cluster, "track_of_cluster"), (trk_off, "trk_off"),
+                 (trk_hits, "trk_hits"), (n_tracks_dev, "n_tracks_dev")):
+        _need(t, torch.int32, n)
+    rc = load_library().tpc_find_tracks(ctx, _ptr(track_of_cluster), _ptr(trk_off), _ptr(trk_hits),
+                                        _ptr(n_tracks_dev), trk_off.numel() - 1, _stream(stream))
+    _check(ctx, rc, "tpc_find_tracks")
+
+
+def tpc_fit_tracks(ctx, trk_off, trk_hits, n_tracks, n_tracks_dev, params, cov, chi2, ndf,
+                   stream=None):
+    _need(trk_off, torch.int32, "trk_off")
+    _need(trk_hits, torch.int32, "trk_hits")
+    for t, n in ((params, "params"), (cov, "cov"), (chi2, "chi2")):
+        _need(t, torch.float32, n)
+    _need(ndf, torch.int32, "ndf")
+    if n_tracks_dev is not None:
+        _need(n_tracks_dev, torch.int32, "n_tracks_dev")
+    rc = load_library().tpc_fit_tracks(ctx, _ptr(trk_off), _ptr(trk_hits), int(n_tracks),
+                                       _ptr(n_tracks_dev), _ptr(params), _ptr(cov), _ptr(chi2),
+                                       _ptr(ndf), _stream(stream))
+    _check(ctx, rc, "tpc_fit_tracks")
+
+
+def tpc_fit_adjoint(ctx, trk_off, trk_hits, n_tracks, align, chi2_total, grad=None, stream=None):
+    _need(trk_off, torch.int32, "trk_off")
+    _need(trk_hits, torch.int32, "trk_hits")
+    _need(align, torch.float64, "align")
+    _need(chi2_total, torch.float64, "chi2_total")
+    if grad is not None:
+        _need(grad, torch.float64, "grad")
+    rc = load_library().tpc_fit_adjoint(ctx, _ptr(trk_off), _ptr(trk_hits), int(n_tracks),
+                                        _ptr(align), _ptr(chi2_total), _ptr(grad), _stream(stream))
+    _check(ctx, rc, "tpc_fit_adjoint")
+
+
+def tpc_get_stats(ctx, stream=None) -> Stats:
+    st = Stats()
+    load_library().tpc_get_stats(ctx, C.byref(st), _stream(stream))
+    return st
+
+
+def tpc_stage_timing(ctx, enable: bool):
+    _check(ctx, load_library().tpc_stage_timing(ctx, 1 if enable else 0), "tpc_stage_timing")
+
+
+def tpc_stage_times(ctx) -> dict:
+    ms = (C.c_float * len(STAGE_NAMES))()
+    _check(ctx, load_library().tpc_stage_times(ctx, ms), "tpc_stage_times")
+    return dict(zip(STAGE_NAMES, [float(v) for v in ms]))
+
+
+def tpc_reset_status(ctx, stream=None):
+    _check(ctx, load_library().tpc_reset_status(ctx, _stream(stream)), "tpc_reset_status")
+
+
+# --- convenience wrapper -------------------------------------------------------
+
+class Tracker:
+    """Owns a context and its workspace tensor for batches of up to
+    max_clusters clusters in max_events events."""
+
+    def __init__(self, max_clusters: int, max_events: int = 1, params: Params | None = None,
+                 device: str | torch.device = "cuda"):
+        if not torch.cuda.is_available():
+            raise RuntimeError("libtpctrack needs a CUDA device")
+        self.device = torch.device(device)
+        self.params = params or default_params()
+        self.ctx = tpc_create(self.params)
+        self.max_clusters = int(max_clusters)
+        self.max_events = int(max_events)
+        nbytes = tpc_workspace_bytes(self.ctx, self.max_clusters, self.max_events)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        tpc_set_workspace(self.ctx, self.workspace, self.max_clusters, self.max_events)
+        self.n = 0
+
+    def close(self):
+        if self.ctx is not None:
+            tpc_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load(self, y, z, row, evt_sector_off, n_events, charge=None, stream=None):
+        self._inputs = (y, z, row, charge, evt_sector_off)  # keep alive
+        self.n = y.numel()
+        tpc_load_clusters(self.ctx, y, z, row, charge, evt_sector_off, n_events, stream)
+
+    def alloc_find_outputs(self, track_cap=None):
+        cap = int(track_cap if track_cap is not None else max(1, self.n // 10 + 16))
+        dev = self.device
+        return (torch.empty(max(self.n, 1), dtype=torch.int32, device=dev),
+                torch.empty(cap + 1, dtype=torch.int32, device=dev),
+                torch.empty(max(self.n, 1), dtype=torch.int32, device=dev),
+                torch.empty(1, dtype=torch.int32, device=dev))
+
+    def find(self, out=None, track_cap=None, stream=None):
+        out = out or self.alloc_find_outputs(track_cap)
+        tpc_find_tracks(self.ctx, *out, stream=stream)
+        return out
+
+    def fit(self, trk_off, trk_hits, n_tracks, n_tracks_dev=None, out=None, stream=None):
+        dev = self.device
+        T = max(int(n_tracks), 1)
+        out = out or (torch.empty(T, 5, dtype=torch.float32, device=dev),
+                      torch.empty(T, 15, dtype=torch.float32, device=dev),
+                      torch.empty(T, dtype=torch.float32, device=dev),
+                      torch.empty(T, dtype=torch.int32, device=dev))
+        tpc_fit_tracks(self.ctx, trk_off, trk_hits, n_tracks, n_tracks_dev, *out, stream=stream)
+        return out
+
+    def adjoint(self, trk_off, trk_hits, n_tracks, align, want_grad=True, stream=None):
+        chi2 = torch.zeros(1, dtype=torch.float64, device=self.device)
+        grad = torch.zeros(216, dtype=torch.float64, device=self.device) if want_grad else None
+        tpc_fit_adjoint(self.ctx, trk_off, trk_hits, n_tracks, align, chi2, grad, stream=stream)
+        return chi2, grad
+
+    def stats(self, stream=None) -> Stats:
+        return tpc_get_stats(self.ctx, stream)
+
+    def check(self, stream=None):
+        st = self.stats(stream)
+        if st.status != TPC_OK:
+            raise TPCError(f"device status {STATUS_NAMES.get(st.status, st.status)} "
+                           f"(detail {st.status_detail})")
+        return st
+
+    def reset_status(self, stream=None):
+        tpc_reset_status(self.ctx, stream)
+
+    def stage_timing(self, enable: bool = True):
+        tpc_stage_timing(self.ctx, enable)
+
+    def stage_times(self) -> dict:
+        return tpc_stage_times(self.ctx)

@@ -1,0 +1,96 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+* Pattern recognition: cluster-to-track assignment must agree for >= 99.99%
+  of the clusters (decisions that depend on FP32 vs FP64 rounding are rare
+  near-ties); the neighbour step itself is bit-exact by construction.
+* Fit: on the same hit lists, FP32 GPU parameters agree with the FP64 oracle
+  within |dp_i| <= 1e-5 max(|p_i|, s_i), s = (1 cm, 1 cm, 0.1, 0.1, 0.1 c/GeV).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2412_13755_gb300 import synth, tpc  # noqa: E402
+from gpu_util import canon_of_cluster, gpu_find, to_dev  # noqa: E402
+
+SCALE = np.array([1.0, 1.0, 0.1, 0.1, 0.1])
+
+
+def _assign_parity(orc, ev, min_agree=0.9999):
+    g_toc, g_off, g_hits, st, _ = gpu_find(ev)
+    o_toc, o_off, o_hits = orc.find_tracks(ev.y, ev.z, ev.row, ev.evt_sector_off, ev.n_events)
+    gc = canon_of_cluster(g_toc, g_off, g_hits, ev.n)
+    oc = canon_of_cluster(o_toc, o_off, o_hits, ev.n)
+    agree = np.mean(gc == oc)
+    print(f"n={ev.n} tracks gpu={len(g_off)-1} oracle={len(o_off)-1} agreement={agree:.6f} "
+          f"segments={st.n_segments} tracklets={st.n_tracklets} merges={st.n_merges}")
+    assert agree >= min_agree, agree
+    return g_toc, g_off, g_hits
+
+
+def test_find_one_sector(orc):
+    ev = synth.one_sector()
+    g_toc, g_off, g_hits = _assign_parity(orc, ev)
+    assert len(g_off) > 100
+
+
+def test_find_central_event_small(orc):
+    _assign_parity(orc, synth.central_event(n_tracks=2000, seed=101))
+
+
+@pytest.mark.slow
+def test_find_central_event_full(orc):
+    _assign_parity(orc, synth.central_event())
+
+
+def test_find_multi_event_batch(orc):
+    _assign_parity(orc, synth.uneven_batch(n_events=6, lo=10, hi=800, seed=303))
+
+
+def test_fit_parity_truth_tracks(orc):
+    ev = synth.central_event(n_tracks=3000, noise=0.0, seed=202)
+    sec = ev.sector_of_cluster()
+    off, hits, _ = ev.truth_tracks()
+    tr = tpc.Tracker(ev.n, 1)
+    y, z, row, eo = to_dev(ev)
+    tr.load(y, z, row, eo, 1)
+    T = len(off) - 1
+    par, cov, chi2, ndf = tr.fit(torch.from_numpy(off).cuda(), torch.from_numpy(hits).cuda(), T)
+    torch.cuda.synchronize()
+    tr.check()
+    opar, ocov, ochi2, ondf = orc.fit_tracks(ev.y, ev.z, ev.row, sec, off, hits)
+    gpar = par.cpu().numpy().astype(np.float64)
+    ok = (ondf > 0) & (ndf.cpu().numpy() > 0)
+    assert ok.mean() > 0.999
+    rel = np.abs(gpar - opar) / np.maximum(np.abs(opar), SCALE)
+    sig = np.sqrt(ocov[:, [0, 5, 9, 12, 14]])
+    in_sigma = np.abs(gpar - opar) / sig
+    gcov = cov.cpu().numpy().astype(np.float64)
+    crel = np.abs(gcov - ocov) / np.maximum(np.abs(ocov), 1e-30)
+    print("per-quantity |GPU FP32 - oracle FP64| (relative, floors 1 cm/1 cm/0.1/0.1/0.1):")
+    for i, name in enumerate(("y", "z", "sin phi", "tan lambda", "q/pT")):
+        print(f"  {name:10s} median {np.median(rel[ok, i]):.2e} p99.9 "
+              f"{np.percentile(rel[ok, i], 99.9):.2e} max {rel[ok, i].max():.2e} "
+              f"max/sigma {in_sigma[ok, i].max():.2e}")
+    print(f"  cov diag max rel {crel[ok][:, [0, 5, 9, 12, 14]].max(0)}")
+    within = np.all(rel <= 1e-5, axis=1)
+    assert within[ok].mean() >= 0.999, within[ok].mean()
+    assert in_sigma[ok].max() <= 1e-3, in_sigma[ok].max(0)
+    gchi2 = chi2.cpu().numpy()
+    np.testing.assert_allclose(gchi2[ok], ochi2[ok], rtol=2e-3, atol=1e-3)
+    assert np.array_equal(ndf.cpu().numpy()[ok], ondf[ok])
+
+
+def test_empty_input():
+    tr = tpc.Tracker(16, 1)
+    y = torch.zeros(0, device="cuda")
+    z = torch.zeros(0, device="cuda")
+    row = torch.zeros(0, dtype=torch.int16, device="cuda").view(torch.uint16)
+    off = torch.zeros(37, dtype=torch.int64, device="cuda")
+    tr.load(y, z, row, off, 1)
+    toc, trk_off, hits, ntd = tr.find(track_cap=4)
+    torch.cuda.synchronize()
+    tr.check()
+    assert int(ntd.item()) == 0
