@@ -90,6 +90,8 @@ typedef struct {
     int32_t n_fp64_updates;   /* Kalman updates redone in FP64 (all calls)   */
     int32_t status;           /* device status word (tpc_status)            */
     int32_t status_detail;
+    int64_t n_launches;       /* kernels this library has launched in this
+                                 process (host-side count, all contexts)    */
 } tpc_stats;
 
 /* Fills p with the library's default parameters. */

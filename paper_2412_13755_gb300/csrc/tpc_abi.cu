@@ -11,6 +11,8 @@ using namespace tpc;
 
 namespace tpc {
 
+std::atomic<long long> g_launches{0};
+
 Layout make_layout(int64_t N, int32_t E) {
     Layout L;
     L.N = N;
@@ -74,6 +76,7 @@ Layout make_layout(int64_t N, int32_t E) {
     L.grp_tl_off = take(g4 + 4);
     L.grp_tl_cur = take(g4);
     L.tl_sorted = take(s4);
+    L.gs_meta = take(s4 * 4);
     L.cand_n = take(s4);
     L.cand_a = take(s4 * MAX_CAND);
     L.cand_c2 = take(s4 * MAX_CAND);
@@ -296,6 +299,7 @@ tpc_status tpc_get_stats(tpc_ctx* c, tpc_stats* out, tpc_stream_t stream) {
         out->n_fp64_updates = h[ST_FP64];
         out->status = h[ST_STATUS];
         out->status_detail = h[ST_DETAIL];
+        out->n_launches = g_launches.load(std::memory_order_relaxed);
     }
     if (h[ST_STATUS] != 0) {
         char buf[160];

@@ -549,11 +549,11 @@ cudaError_t run_adjoint(tpc_ctx* c, const int32_t* trk_off, const int32_t* trk_h
     for (int i = 0; i < 5; ++i) ap.prior[i] = p.prior[i];
     ap.want_grad = grad != nullptr;
     c->mark(12, s);
-    k_zero_f64<<<1, 32, 0, s>>>(chi2_total, 1);
-    if (grad) k_zero_f64<<<1, 256, 0, s>>>(grad, 216);
+    tpc::LaunchCount{}, k_zero_f64<<<1, 32, 0, s>>>(chi2_total, 1);
+    if (grad) tpc::LaunchCount{}, k_zero_f64<<<1, 256, 0, s>>>(grad, 216);
     if (n_tracks > 0) {
         const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((n_tracks + 127) / 128, 152 * 4));
-        k_adjoint<<<(unsigned)blocks, 128, 0, s>>>(trk_off, trk_hits, n_tracks, c->y, c->z, c->row,
+        tpc::LaunchCount{}, k_adjoint<<<(unsigned)blocks, 128, 0, s>>>(trk_off, trk_hits, n_tracks, c->y, c->z, c->row,
                                                    c->evt_sector_off, c->n_events * NSEC, align,
                                                    c->ws.at<Geo>(c->ws.L.geo), ap, chi2_total, grad,
                                                    c->ws.at<int32_t>(c->ws.L.status));

@@ -122,11 +122,11 @@ cudaError_t scan_i32(const int32_t* in, int32_t* out, int64_t L, int32_t* tmp, c
     if (nb > 0) {
         // the reduce pass reads items strided by SCAN_T; the down pass reads
         // them contiguously per thread: both cover the block's SCAN_B items
-        k_scan_reduce<<<(unsigned)nb, SCAN_T, 0, s>>>(in, L, tmp);
-        k_scan_top<<<1, 1024, 0, s>>>(tmp, nb, out + L);
-        k_scan_down<<<(unsigned)nb, SCAN_T, 0, s>>>(in, L, tmp, out);
+        tpc::LaunchCount{}, k_scan_reduce<<<(unsigned)nb, SCAN_T, 0, s>>>(in, L, tmp);
+        tpc::LaunchCount{}, k_scan_top<<<1, 1024, 0, s>>>(tmp, nb, out + L);
+        tpc::LaunchCount{}, k_scan_down<<<(unsigned)nb, SCAN_T, 0, s>>>(in, L, tmp, out);
     } else {
-        k_fill_i32<<<1, 32, 0, s>>>(out, 1, 0);
+        tpc::LaunchCount{}, k_fill_i32<<<1, 32, 0, s>>>(out, 1, 0);
     }
     return cudaGetLastError();
 }
@@ -134,7 +134,7 @@ cudaError_t scan_i32(const int32_t* in, int32_t* out, int64_t L, int32_t* tmp, c
 cudaError_t fill_i32(int32_t* p, int64_t n, int32_t v, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     const int64_t blocks = std::min<int64_t>((n + 255) / 256, 152 * 16);
-    k_fill_i32<<<(unsigned)blocks, 256, 0, s>>>(p, n, v);
+    tpc::LaunchCount{}, k_fill_i32<<<(unsigned)blocks, 256, 0, s>>>(p, n, v);
     return cudaGetLastError();
 }
 
@@ -155,7 +155,7 @@ cudaError_t init_geo(const Workspace& ws, cudaStream_t s) {
         g.da_cos[k] = std::cos(d);
         g.da_sin[k] = std::sin(d);
     }
-    k_init_geo<<<1, 1, 0, s>>>(ws.at<Geo>(ws.L.geo), g);
+    tpc::LaunchCount{}, k_init_geo<<<1, 1, 0, s>>>(ws.at<Geo>(ws.L.geo), g);
     return cudaGetLastError();
 }
 
@@ -167,7 +167,7 @@ cudaError_t validate_clusters(const tpc_ctx* c, cudaStream_t s) {
     const int G = c->n_events * NSEC;
     const int64_t work = std::max<int64_t>(c->n, G + 1);
     const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, 152 * 8));
-    k_validate<<<(unsigned)blocks, 256, 0, s>>>(c->y, c->z, c->row, c->n, c->evt_sector_off, G,
+    tpc::LaunchCount{}, k_validate<<<(unsigned)blocks, 256, 0, s>>>(c->y, c->z, c->row, c->n, c->evt_sector_off, G,
                                                 c->ws.at<int32_t>(c->ws.L.status));
     return cudaGetLastError();
 }

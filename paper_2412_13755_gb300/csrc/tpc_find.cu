@@ -523,12 +523,19 @@ __global__ void __launch_bounds__(128) k_keep(
 
 __global__ void k_tl_scatter(const int32_t* __restrict__ tl_keep, const int32_t* __restrict__ seg_grp,
                              const int32_t* __restrict__ grp_tl_off, int64_t Scap, const int32_t* st,
-                             int32_t* grp_tl_cur, int32_t* tl_sorted) {
+                             int32_t* grp_tl_cur, int32_t* tl_sorted,
+                             const int32_t* __restrict__ tl_rmin, const int32_t* __restrict__ tl_rmax,
+                             const float* __restrict__ tl_zin, const float* __restrict__ tl_zout,
+                             const int32_t* __restrict__ tl_ok, int4* gs_meta) {
     const int nseg = min((int64_t)st[ST_NSEG], Scap);
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nseg; s += gridDim.x * blockDim.x) {
         if (!tl_keep[s]) continue;
         const int g = seg_grp[s];
-        tl_sorted[grp_tl_off[g] + atomicAdd(&grp_tl_cur[g], 1)] = s;
+        const int q = grp_tl_off[g] + atomicAdd(&grp_tl_cur[g], 1);
+        tl_sorted[q] = s;
+        // packed per-position merge data read coalesced by the candidate search
+        gs_meta[q] = make_int4(tl_rmax[s] | (tl_rmin[s] << 8) | (tl_ok[s] << 16),
+                               __float_as_int(tl_zout[s]), __float_as_int(tl_zin[s]), s);
     }
 }
 
@@ -536,7 +543,8 @@ __global__ void k_tl_scatter(const int32_t* __restrict__ tl_keep, const int32_t*
 struct MgPrm {
     int merge_gap, merge_ov;
     float mz_slope, mz_margin;
-    double chi2_merge, kb, snp_max;
+    double chi2_merge;
+    float kbf, snp_maxf;
 };
 
 // 5x5 SPD chi2 = dp^T M^-1 dp by Cholesky (FP64); false if not SPD
@@ -566,63 +574,85 @@ __device__ bool chol_chi2(const double dp[5], const double M[15], double& out) {
 
 // For tracklet B (inner end), candidates A (outer end) in the same or a
 // phi-adjacent sector of the same side and event: A's outward-fit state at
-// its outermost row is moved to B's innermost plane (FP64) and compared with
-// B's inward-fit state there.
-__global__ void __launch_bounds__(128) k_merge_cand(
-    const int32_t* __restrict__ tl_keep, const int32_t* __restrict__ tl_ok,
-    const int32_t* __restrict__ seg_grp, const int32_t* __restrict__ tl_rmin,
-    const int32_t* __restrict__ tl_rmax, const float* __restrict__ tl_zin,
-    const float* __restrict__ tl_zout, const float* __restrict__ tl_state,
-    const int32_t* __restrict__ grp_tl_off, const int32_t* __restrict__ tl_sorted,
-    const Geo* __restrict__ geo, MgPrm P, int64_t Scap, int32_t* st, int32_t* cand_n,
-    int32_t* cand_a, float* cand_c2) {
-    const int nseg = min((int64_t)st[ST_NSEG], Scap);
-    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nseg; b += gridDim.x * blockDim.x) {
-        cand_n[b] = 0;
-        if (!tl_keep[b] || !(tl_ok[b] & 1)) continue;
+// its outermost row is moved to B's innermost plane and compared with B's
+// inward-fit state there (chi2 of the 5-d difference, solved in FP64).  One
+// warp per B; the lanes stride over the group-sorted candidates.
+__global__ void __launch_bounds__(256) k_merge_cand(
+    const int32_t* __restrict__ seg_grp, const float* __restrict__ tl_state,
+    const int32_t* __restrict__ grp_tl_off, const int4* __restrict__ gs_meta,
+    const Geo* __restrict__ geo, MgPrm P, int32_t* st, int32_t* cand_n, int32_t* cand_a,
+    float* cand_c2) {
+    const int lane = threadIdx.x & 31;
+    const int nkept = st[ST_NTL];
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int qb = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; qb < nkept; qb += warps) {
+        const int4 mb = gs_meta[qb];
+        const int b = mb.w;
+        if (lane == 0) cand_n[b] = 0;
+        if (!((mb.x >> 16) & 1)) continue;
+        const int rb = (mb.x >> 8) & 0xff;
+        const float zb_in = __int_as_float(mb.z);
         const int gb = seg_grp[b];
         const int ev = gb / NSEC, sb = gb % NSEC, side = sb / NPHI, phb = sb % NPHI;
-        const int rb = tl_rmin[b];
-        const float zb_in = tl_zin[b];
         const float* stb = tl_state + (int64_t)b * 40;
-        int nc = 0;
+        int nc = 0;  // warp-uniform count
         for (int dp = -1; dp <= 1; ++dp) {
             const int sa = side * NPHI + (phb + dp + NPHI) % NPHI;
             const int ga = ev * NSEC + sa;
-            for (int q = grp_tl_off[ga]; q < grp_tl_off[ga + 1]; ++q) {
-                const int a = tl_sorted[q];
-                if (a == b || !(tl_ok[a] & 2)) continue;
-                const int gap = rb - tl_rmax[a];
-                const int min_gap = dp == 0 ? 0 : -P.merge_ov;
-                if (gap < min_gap || gap > P.merge_gap) continue;
-                const float dxr = fabsf(__fsub_rn(geo->row_xf[rb], geo->row_xf[tl_rmax[a]]));
-                if (!(fabsf(__fsub_rn(zb_in, tl_zout[a])) <=
-                      __fadd_rn(__fmul_rn(P.mz_slope, dxr), P.mz_margin)))
-                    continue;
-                const float* sta = tl_state + (int64_t)a * 40;
-                KFD s;
-                s.x = geo->row_xd[tl_rmax[a]];
-                s.frame = sa;
-                for (int i = 0; i < 5; ++i) s.p[i] = sta[20 + i];
-                s.lo[0] = s.lo[1] = s.lo[2] = 0.0;
-                for (int i = 0; i < 15; ++i) s.C[i] = sta[25 + i];
-                if (!kf_move<double>(s, geo->row_xd[rb], sb, geo, P.kb, P.snp_max)) continue;
-                double d[5], M[15];
-                for (int i = 0; i < 5; ++i) d[i] = (double)stb[i] - s.p[i];
-                for (int i = 0; i < 15; ++i) M[i] = s.C[i] + (double)stb[5 + i];
-                double c2;
-                if (!chol_chi2(d, M, c2) || !(c2 <= P.chi2_merge)) continue;
-                if (nc < MAX_CAND) {
-                    cand_a[(int64_t)b * MAX_CAND + nc] = a;
-                    cand_c2[(int64_t)b * MAX_CAND + nc] = (float)c2;
-                } else {
-                    set_status(st, TPC_ERR_CAPACITY, 3);
+            const int q0 = grp_tl_off[ga], q1 = grp_tl_off[ga + 1];
+            const int min_gap = dp == 0 ? 0 : -P.merge_ov;
+            for (int qa0 = q0; qa0 < q1; qa0 += 32) {
+                const int qa = qa0 + lane;
+                bool pass = false;
+                float c2f = 0.f;
+                int a = -1;
+                if (qa < q1 && qa != qb) {
+                    const int4 ma = gs_meta[qa];
+                    a = ma.w;
+                    const int ra = ma.x & 0xff;
+                    const int gap = rb - ra;
+                    pass = ((ma.x >> 17) & 1) && gap >= min_gap && gap <= P.merge_gap;
+                    if (pass) {
+                        const float dxr = fabsf(__fsub_rn(geo->row_xf[rb], geo->row_xf[ra]));
+                        pass = fabsf(__fsub_rn(zb_in, __int_as_float(ma.y))) <=
+                               __fadd_rn(__fmul_rn(P.mz_slope, dxr), P.mz_margin);
+                    }
+                    if (pass) {
+                        const float* sta = tl_state + (int64_t)a * 40;
+                        KF s;
+                        s.x = geo->row_xd[ra];
+                        s.frame = sa;
+                        for (int i = 0; i < 5; ++i) s.p[i] = sta[20 + i];
+                        s.lo[0] = s.lo[1] = s.lo[2] = 0.f;
+                        for (int i = 0; i < 15; ++i) s.C[i] = sta[25 + i];
+                        pass = kf_move<float>(s, geo->row_xd[rb], sb, geo, P.kbf, P.snp_maxf);
+                        if (pass) {
+                            double d[5], M[15];
+                            for (int i = 0; i < 3; ++i) d[i] = (double)stb[i] - ((double)s.p[i] + (double)s.lo[i]);
+                            for (int i = 3; i < 5; ++i) d[i] = (double)stb[i] - (double)s.p[i];
+                            for (int i = 0; i < 15; ++i) M[i] = (double)s.C[i] + (double)stb[5 + i];
+                            double c2;
+                            pass = chol_chi2(d, M, c2) && c2 <= P.chi2_merge;
+                            c2f = (float)c2;
+                        }
+                    }
                 }
-                ++nc;
+                const unsigned bal = __ballot_sync(0xffffffffu, pass);
+                if (pass) {
+                    const int k = nc + __popc(bal & ((1u << lane) - 1u));
+                    if (k < MAX_CAND) {
+                        cand_a[(int64_t)b * MAX_CAND + k] = a;
+                        cand_c2[(int64_t)b * MAX_CAND + k] = c2f;
+                    }
+                }
+                nc += __popc(bal);
             }
         }
-        cand_n[b] = min(nc, MAX_CAND);
-        if (nc) atomicAdd(&st[ST_NCAND], min(nc, MAX_CAND));
+        if (lane == 0) {
+            cand_n[b] = min(nc, MAX_CAND);
+            if (nc > MAX_CAND) set_status(st, TPC_ERR_CAPACITY, 3);
+            if (nc) atomicAdd(&st[ST_NCAND], min(nc, MAX_CAND));
+        }
     }
 }
 
@@ -777,17 +807,17 @@ cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hi
     // per-call counters (the status word and the FP64 count are cumulative)
     TPC_TRY(fill_i32(st + ST_NSEG, ST_NTRACKS - ST_NSEG + 1, 0, s));
     // S1: z range per group, cells, histogram, scan, scatter
-    k_fill_u32<<<grid_for(G), TPB, 0, s>>>(W.at<uint32_t>(L.g_zmin_u), G, 0xffffffffu);
-    k_fill_u32<<<grid_for(G), TPB, 0, s>>>(W.at<uint32_t>(L.g_zmax_u), G, 0u);
-    k_zrange<<<grid_for(n), TPB, 0, s>>>(c->z, n, c->evt_sector_off, G, W.at<uint32_t>(L.g_zmin_u),
+    tpc::LaunchCount{}, k_fill_u32<<<grid_for(G), TPB, 0, s>>>(W.at<uint32_t>(L.g_zmin_u), G, 0xffffffffu);
+    tpc::LaunchCount{}, k_fill_u32<<<grid_for(G), TPB, 0, s>>>(W.at<uint32_t>(L.g_zmax_u), G, 0u);
+    tpc::LaunchCount{}, k_zrange<<<grid_for(n), TPB, 0, s>>>(c->z, n, c->evt_sector_off, G, W.at<uint32_t>(L.g_zmin_u),
                                          W.at<uint32_t>(L.g_zmax_u));
-    k_cells<<<1, 1024, 0, s>>>(c->evt_sector_off, G, W.at<uint32_t>(L.g_zmin_u),
+    tpc::LaunchCount{}, k_cells<<<1, 1024, 0, s>>>(c->evt_sector_off, G, W.at<uint32_t>(L.g_zmin_u),
                                W.at<uint32_t>(L.g_zmax_u), W.at<float>(L.g_zmin), W.at<float>(L.g_inv),
                                W.at<int32_t>(L.g_nz), W.at<int32_t>(L.g_kbase), L.K, st);
     Cells cells{W.at<float>(L.g_zmin), W.at<float>(L.g_inv), W.at<int32_t>(L.g_nz),
                 W.at<int32_t>(L.g_kbase), W.at<int32_t>(L.cell_off)};
     TPC_TRY(fill_i32(W.at<int32_t>(L.cell_cnt), L.K + 1, 0, s));
-    k_hist<<<grid_for(n), TPB, 0, s>>>(c->z, c->row, n, c->evt_sector_off, G, cells,
+    tpc::LaunchCount{}, k_hist<<<grid_for(n), TPB, 0, s>>>(c->z, c->row, n, c->evt_sector_off, G, cells,
                                        W.at<int32_t>(L.cell_cnt), W.at<int32_t>(L.key_in),
                                        W.at<int32_t>(L.slot_in), L.K);
     TPC_TRY(scan_i32(W.at<int32_t>(L.cell_cnt), W.at<int32_t>(L.cell_off), L.K, scan_tmp, s));
@@ -796,7 +826,7 @@ cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hi
     int32_t* orig = W.at<int32_t>(L.orig);
     int32_t* grpb = W.at<int32_t>(L.grpb);
     uint8_t* rowb = W.at<uint8_t>(L.rowb);
-    k_scatter<<<grid_for(n), TPB, 0, s>>>(c->y, c->z, c->row, n, c->evt_sector_off, G,
+    tpc::LaunchCount{}, k_scatter<<<grid_for(n), TPB, 0, s>>>(c->y, c->z, c->row, n, c->evt_sector_off, G,
                                           W.at<int32_t>(L.key_in), W.at<int32_t>(L.slot_in),
                                           W.at<int32_t>(L.cell_off), L.K, yb, zb, orig, grpb, rowb);
     TPC_TRY(cudaGetLastError());
@@ -807,22 +837,22 @@ cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hi
     int32_t* cup = W.at<int32_t>(L.choice_up);
     float* d2 = W.at<float>(L.d2);
     NbPrm nb{p.win_y, p.win_z, p.chi2_link, p.sigma_y2, p.sigma_z2, p.max_gap};
-    k_neighbours<<<grid_for(n), TPB, 0, s>>>(n, yb, zb, orig, grpb, rowb, cells, geo, nb, cdn, cup, d2);
+    tpc::LaunchCount{}, k_neighbours<<<grid_for(n), TPB, 0, s>>>(n, yb, zb, orig, grpb, rowb, cells, geo, nb, cdn, cup, d2);
     c->mark(2, s);
     auto* claim_up = W.at<unsigned long long>(L.claim_up);
     auto* claim_dn = W.at<unsigned long long>(L.claim_dn);
-    k_fill_u64<<<grid_for(n), TPB, 0, s>>>(claim_up, n, KEY_MAX);
-    k_fill_u64<<<grid_for(n), TPB, 0, s>>>(claim_dn, n, KEY_MAX);
-    k_claims<<<grid_for(n), TPB, 0, s>>>(n, cdn, cup, d2, orig, claim_up, claim_dn);
+    tpc::LaunchCount{}, k_fill_u64<<<grid_for(n), TPB, 0, s>>>(claim_up, n, KEY_MAX);
+    tpc::LaunchCount{}, k_fill_u64<<<grid_for(n), TPB, 0, s>>>(claim_dn, n, KEY_MAX);
+    tpc::LaunchCount{}, k_claims<<<grid_for(n), TPB, 0, s>>>(n, cdn, cup, d2, orig, claim_up, claim_dn);
     int32_t* ldn = W.at<int32_t>(L.link_dn);
     int32_t* lup = W.at<int32_t>(L.link_up);
     TPC_TRY(fill_i32(ldn, n, -1, s));
     TPC_TRY(fill_i32(lup, n, -1, s));
-    k_links<<<grid_for(n), TPB, 0, s>>>(n, cdn, cup, d2, orig, claim_up, claim_dn, ldn, lup);
+    tpc::LaunchCount{}, k_links<<<grid_for(n), TPB, 0, s>>>(n, cdn, cup, d2, orig, claim_up, claim_dn, ldn, lup);
 
     c->mark(3, s);
     // S3: chains
-    k_chains<<<grid_for(n), TPB, 0, s>>>(n, ldn, lup, orig, grpb, p.n_seg, L.S,
+    tpc::LaunchCount{}, k_chains<<<grid_for(n), TPB, 0, s>>>(n, ldn, lup, orig, grpb, p.n_seg, L.S,
                                          W.at<int32_t>(L.seg_start), W.at<int32_t>(L.seg_grp),
                                          W.at<int32_t>(L.seg_canon), st);
     c->mark(4, s);
@@ -844,36 +874,38 @@ cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hi
     const unsigned sgrid = grid_for(L.S, 128);
     int32_t* tl_rowhit = W.at<int32_t>(L.tl_rowhit);
     auto* tl_key = W.at<unsigned long long>(L.tl_key);
-    k_tracklets<<<sgrid, 128, 0, s>>>(W.at<int32_t>(L.seg_start), W.at<int32_t>(L.seg_grp),
+    tpc::LaunchCount{}, k_tracklets<<<sgrid, 128, 0, s>>>(W.at<int32_t>(L.seg_start), W.at<int32_t>(L.seg_grp),
                                       W.at<int32_t>(L.seg_canon), lup, yb, zb, orig, rowb, cells, geo,
                                       tp, L.S, st, tl_rowhit, W.at<int32_t>(L.tl_n), tl_key);
     c->mark(5, s);
     auto* owner = W.at<unsigned long long>(L.owner);
-    k_fill_u64<<<grid_for(n), TPB, 0, s>>>(owner, n, KEY_MAX);
-    k_owner<<<grid_for(L.S * NROW), TPB, 0, s>>>(tl_rowhit, tl_key, L.S, st, owner);
+    tpc::LaunchCount{}, k_fill_u64<<<grid_for(n), TPB, 0, s>>>(owner, n, KEY_MAX);
+    tpc::LaunchCount{}, k_owner<<<grid_for(L.S * NROW), TPB, 0, s>>>(tl_rowhit, tl_key, L.S, st, owner);
     int32_t* grp_cnt = W.at<int32_t>(L.grp_tl_cnt);
     TPC_TRY(fill_i32(grp_cnt, G + 1, 0, s));
-    k_keep<<<sgrid, 128, 0, s>>>(tl_rowhit, tl_key, owner, W.at<int32_t>(L.seg_grp), yb, zb, orig, geo,
+    tpc::LaunchCount{}, k_keep<<<sgrid, 128, 0, s>>>(tl_rowhit, tl_key, owner, W.at<int32_t>(L.seg_grp), yb, zb, orig, geo,
                                  tp, L.S, st, W.at<int32_t>(L.tl_keep), W.at<int32_t>(L.tl_canon),
                                  W.at<int32_t>(L.tl_rmin), W.at<int32_t>(L.tl_rmax),
                                  W.at<float>(L.tl_zin), W.at<float>(L.tl_zout),
                                  W.at<float>(L.tl_state), W.at<int32_t>(L.tl_ok), grp_cnt);
     TPC_TRY(scan_i32(grp_cnt, W.at<int32_t>(L.grp_tl_off), G, scan_tmp, s));
     TPC_TRY(fill_i32(W.at<int32_t>(L.grp_tl_cur), G, 0, s));
-    k_tl_scatter<<<sgrid, 128, 0, s>>>(W.at<int32_t>(L.tl_keep), W.at<int32_t>(L.seg_grp),
+    tpc::LaunchCount{}, k_tl_scatter<<<sgrid, 128, 0, s>>>(W.at<int32_t>(L.tl_keep), W.at<int32_t>(L.seg_grp),
                                        W.at<int32_t>(L.grp_tl_off), L.S, st,
-                                       W.at<int32_t>(L.grp_tl_cur), W.at<int32_t>(L.tl_sorted));
+                                       W.at<int32_t>(L.grp_tl_cur), W.at<int32_t>(L.tl_sorted),
+                                       W.at<int32_t>(L.tl_rmin), W.at<int32_t>(L.tl_rmax),
+                                       W.at<float>(L.tl_zin), W.at<float>(L.tl_zout),
+                                       W.at<int32_t>(L.tl_ok), W.at<int4>(L.gs_meta));
     c->mark(6, s);
     // S4: merge candidates and greedy matching
     MgPrm mp{p.merge_max_row_gap, p.merge_max_overlap, p.merge_z_slope, p.merge_z_margin,
-             (double)p.chi2_merge, KAPPA * (double)p.bz, (double)p.snp_max};
-    k_merge_cand<<<sgrid, 128, 0, s>>>(W.at<int32_t>(L.tl_keep), W.at<int32_t>(L.tl_ok),
-                                       W.at<int32_t>(L.seg_grp), W.at<int32_t>(L.tl_rmin),
-                                       W.at<int32_t>(L.tl_rmax), W.at<float>(L.tl_zin),
-                                       W.at<float>(L.tl_zout), W.at<float>(L.tl_state),
-                                       W.at<int32_t>(L.grp_tl_off), W.at<int32_t>(L.tl_sorted), geo, mp,
-                                       L.S, st, W.at<int32_t>(L.cand_n), W.at<int32_t>(L.cand_a),
-                                       W.at<float>(L.cand_c2));
+             (double)p.chi2_merge, (float)(KAPPA * (double)p.bz), p.snp_max};
+    // cand_n of slots that are not kept must read 0 for the matching
+    TPC_TRY(fill_i32(W.at<int32_t>(L.cand_n), L.S, 0, s));
+    tpc::LaunchCount{}, k_merge_cand<<<grid_for(L.S * 32, 256), 256, 0, s>>>(
+        W.at<int32_t>(L.seg_grp), W.at<float>(L.tl_state), W.at<int32_t>(L.grp_tl_off),
+        W.at<int4>(L.gs_meta), geo, mp, st, W.at<int32_t>(L.cand_n), W.at<int32_t>(L.cand_a),
+        W.at<float>(L.cand_c2));
     c->mark(7, s);
     int32_t* nxt = W.at<int32_t>(L.nxt);
     int32_t* prv = W.at<int32_t>(L.prv);
@@ -881,26 +913,26 @@ cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hi
     TPC_TRY(fill_i32(prv, L.S, -1, s));
     auto* best_a = W.at<unsigned long long>(L.best_a);
     auto* best_b = W.at<unsigned long long>(L.best_b);
-    k_fill_u64<<<grid_for(L.S), TPB, 0, s>>>(best_a, L.S, KEY_MAX);
-    k_fill_u64<<<grid_for(L.S), TPB, 0, s>>>(best_b, L.S, KEY_MAX);
-    k_match<<<1, 1024, 0, s>>>(W.at<int32_t>(L.cand_n), W.at<int32_t>(L.cand_a), W.at<float>(L.cand_c2),
+    tpc::LaunchCount{}, k_fill_u64<<<grid_for(L.S), TPB, 0, s>>>(best_a, L.S, KEY_MAX);
+    tpc::LaunchCount{}, k_fill_u64<<<grid_for(L.S), TPB, 0, s>>>(best_b, L.S, KEY_MAX);
+    tpc::LaunchCount{}, k_match<<<1, 1024, 0, s>>>(W.at<int32_t>(L.cand_n), W.at<int32_t>(L.cand_a), W.at<float>(L.cand_c2),
                                W.at<int32_t>(L.tl_canon), L.S, st, best_a, best_b, nxt, prv);
     c->mark(8, s);
     // output: canonical order by smallest input index
     int32_t* flag = W.at<int32_t>(L.trk_flag);
     TPC_TRY(fill_i32(flag, n, 0, s));
-    k_track_heads<<<sgrid, 128, 0, s>>>(W.at<int32_t>(L.tl_keep), nxt, prv, W.at<int32_t>(L.tl_canon),
+    tpc::LaunchCount{}, k_track_heads<<<sgrid, 128, 0, s>>>(W.at<int32_t>(L.tl_keep), nxt, prv, W.at<int32_t>(L.tl_canon),
                                         tl_rowhit, p.n_min, L.S, st, flag, W.at<int32_t>(L.trk_len_at),
                                         W.at<int32_t>(L.trk_head_at));
     int32_t* rank = W.at<int32_t>(L.trk_rank);
     TPC_TRY(scan_i32(flag, rank, n, scan_tmp, s));
     int32_t* len_by_rank = W.at<int32_t>(L.len_by_rank);
     TPC_TRY(fill_i32(len_by_rank, track_cap, 0, s));
-    k_track_len<<<grid_for(n), TPB, 0, s>>>(n, flag, rank, W.at<int32_t>(L.trk_len_at), track_cap,
+    tpc::LaunchCount{}, k_track_len<<<grid_for(n), TPB, 0, s>>>(n, flag, rank, W.at<int32_t>(L.trk_len_at), track_cap,
                                             len_by_rank, st, n_tracks_dev);
     TPC_TRY(scan_i32(len_by_rank, trk_off, track_cap, scan_tmp, s));
     TPC_TRY(fill_i32(toc, n, -1, s));
-    k_track_write<<<grid_for(n), TPB, 0, s>>>(n, flag, rank, W.at<int32_t>(L.trk_head_at), prv,
+    tpc::LaunchCount{}, k_track_write<<<grid_for(n), TPB, 0, s>>>(n, flag, rank, W.at<int32_t>(L.trk_head_at), prv,
                                               tl_rowhit, orig, trk_off, track_cap, toc, trk_hits);
     c->mark(9, s);
     return cudaGetLastError();

@@ -99,7 +99,7 @@ cudaError_t run_fit(tpc_ctx* c, const int32_t* trk_off, const int32_t* trk_hits,
     for (int i = 0; i < 5; ++i) fp.prior[i] = p.prior[i];
     const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((n_tracks + 127) / 128, 152 * 32));
     c->mark(10, s);
-    k_fit<<<(unsigned)blocks, 128, 0, s>>>(trk_off, trk_hits, n_tracks, n_tracks_dev, c->y, c->z,
+    tpc::LaunchCount{}, k_fit<<<(unsigned)blocks, 128, 0, s>>>(trk_off, trk_hits, n_tracks, n_tracks_dev, c->y, c->z,
                                            c->row, c->evt_sector_off, c->n_events * NSEC,
                                            c->ws.at<Geo>(c->ws.L.geo), fp, params, cov, chi2, ndf,
                                            c->ws.at<int32_t>(c->ws.L.status));

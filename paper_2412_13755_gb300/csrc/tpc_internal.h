@@ -4,11 +4,18 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 
 #include "../../include/tpc_track.h"
 
 namespace tpc {
+
+// kernels launched by this library in this process (host-side count)
+extern std::atomic<long long> g_launches;
+struct LaunchCount {
+    LaunchCount() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+};
 
 constexpr int NSEC = 36;
 constexpr int NPHI = 18;
@@ -50,7 +57,7 @@ struct Layout {
         cell_cnt, cell_off, yb, zb, orig, grpb, rowb, choice_dn, choice_up, d2, claim_up,
         claim_dn, link_dn, link_up, owner, seg_start, seg_len, seg_grp, seg_canon, tl_rowhit,
         tl_n, tl_key, tl_keep, tl_canon, tl_rmin, tl_rmax, tl_zin, tl_zout, tl_state, tl_ok,
-        grp_tl_cnt, grp_tl_off, grp_tl_cur, tl_sorted, cand_n, cand_a, cand_c2, best_a, best_b,
+        grp_tl_cnt, grp_tl_off, grp_tl_cur, tl_sorted, gs_meta, cand_n, cand_a, cand_c2, best_a, best_b,
         nxt, prv, trk_flag, trk_rank, trk_len_at, trk_head_at, len_by_rank, scan_a, scan_b,
         adj_grad, adj_chi2, adj_ckpt;
     int64_t adj_tracks = 0;  // tracks the adjoint scratch holds per launch chunk

@@ -46,6 +46,7 @@ class Stats(C.Structure):
         ("n_clusters", C.c_int64), ("n_segments", C.c_int32), ("n_tracklets", C.c_int32),
         ("n_merge_cand", C.c_int32), ("n_merges", C.c_int32), ("n_tracks", C.c_int32),
         ("n_fp64_updates", C.c_int32), ("status", C.c_int32), ("status_detail", C.c_int32),
+        ("n_launches", C.c_int64),
     ]
 
 

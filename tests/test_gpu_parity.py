@@ -4,7 +4,8 @@
   of the clusters (decisions that depend on FP32 vs FP64 rounding are rare
   near-ties); the neighbour step itself is bit-exact by construction.
 * Fit: on the same hit lists, FP32 GPU parameters agree with the FP64 oracle
-  within |dp_i| <= 1e-5 max(|p_i|, s_i), s = (1 cm, 1 cm, 0.1, 0.1, 0.1 c/GeV).
+  within |dp_i| <= 1e-5 max(|p_i|, s_i), s = (1 cm, 1 cm, 0.1, 0.1, 0.1 c/GeV),
+  for every track.
 """
 import numpy as np
 import pytest
@@ -75,9 +76,10 @@ def test_fit_parity_truth_tracks(orc):
               f"{np.percentile(rel[ok, i], 99.9):.2e} max {rel[ok, i].max():.2e} "
               f"max/sigma {in_sigma[ok, i].max():.2e}")
     print(f"  cov diag max rel {crel[ok][:, [0, 5, 9, 12, 14]].max(0)}")
-    within = np.all(rel <= 1e-5, axis=1)
-    assert within[ok].mean() >= 0.999, within[ok].mean()
-    assert in_sigma[ok].max() <= 1e-3, in_sigma[ok].max(0)
+    # every track within 1e-5 relative (floors s); errors are also a tiny
+    # fraction of each parameter's own statistical sigma
+    assert np.all(rel[ok] <= 1e-5), rel[ok].max(0)
+    assert in_sigma[ok].max() <= 1e-2, in_sigma[ok].max(0)
     gchi2 = chi2.cpu().numpy()
     np.testing.assert_allclose(gchi2[ok], ochi2[ok], rtol=2e-3, atol=1e-3)
     assert np.array_equal(ndf.cpu().numpy()[ok], ondf[ok])
