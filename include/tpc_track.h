@@ -188,6 +188,40 @@ tpc_status tpc_last_error(tpc_ctx* ctx, char* buf, size_t len);
 tpc_status tpc_stage_timing(tpc_ctx* ctx, int enable);
 tpc_status tpc_stage_times(tpc_ctx* ctx, float* ms_out);
 
+/* Pattern recognition without allocation (the paper has no counterpart;
+ * this is an interface for a kind of caller).  Some callers cannot allocate
+ * device memory at all: a host program or plugin whose device memory is
+ * owned entirely by another allocator and that may only pass the library its
+ * input and output buffers; or an online path that must not pay the implicit
+ * synchronisation of cudaMalloc.  For them this call runs the same S1-S4
+ * kernels as tpc_find_tracks with its scratch in a fixed device array of
+ * TPC_NOALLOC_SCRATCH_BYTES that is part of the library image: every GPU
+ * that loads libtpctrack holds that array until the process exits, and the
+ * call itself allocates nothing (no cudaMalloc/cudaFree, no context object).
+ *
+ * Limits: n <= TPC_NOALLOC_MAX_CLUSTERS, n_events <= TPC_NOALLOC_MAX_EVENTS,
+ * track_cap <= TPC_NOALLOC_MAX_CLUSTERS; larger requests return
+ * TPC_ERR_CAPACITY before anything is launched.  params may be NULL
+ * (defaults).  Inputs and outputs are as for tpc_load_clusters and
+ * tpc_find_tracks (device pointers, caller-owned); status_dev (device int32)
+ * receives the device status word of this call (TPC_OK, or e.g.
+ * TPC_ERR_INPUT / TPC_ERR_CAPACITY found by the kernels).
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the one array and it keeps the
+ * previous call's contents; the call re-initialises what it needs.  Calls
+ * whose work overlaps on the GPU (several streams or host threads at once)
+ * race on the array and corrupt each other's results: serialise them. */
+#define TPC_NOALLOC_MAX_CLUSTERS 65536
+#define TPC_NOALLOC_MAX_EVENTS 4
+#define TPC_NOALLOC_SCRATCH_BYTES (16u << 20)
+tpc_status tpc_find_tracks_noalloc(const tpc_params* params, const float* y, const float* z,
+                                   const uint16_t* row, int64_t n, const int64_t* evt_sector_off,
+                                   int32_t n_events, int32_t* track_of_cluster, int32_t* trk_off,
+                                   int32_t* trk_hits, int32_t* n_tracks_dev, int32_t* status_dev,
+                                   int32_t track_cap, tpc_stream_t stream);
+
 /* Clears the device status word and counters (asynchronous). */
 tpc_status tpc_reset_status(tpc_ctx* ctx, tpc_stream_t stream);
 

@@ -22,7 +22,7 @@ STATUS_NAMES = {0: "TPC_OK", 1: "TPC_ERR_ARG", 2: "TPC_ERR_CUDA", 3: "TPC_ERR_CA
 EXPORTS = ("tpc_default_params", "tpc_create", "tpc_destroy", "tpc_workspace_bytes",
            "tpc_set_workspace", "tpc_load_clusters", "tpc_find_tracks", "tpc_fit_tracks",
            "tpc_fit_adjoint", "tpc_get_stats", "tpc_last_error", "tpc_reset_status",
-           "tpc_stage_timing", "tpc_stage_times")
+           "tpc_stage_timing", "tpc_stage_times", "tpc_find_tracks_noalloc")
 STAGE_NAMES = ("bin", "neighbours", "links", "chains", "tracklets", "select", "merge_cand",
                "match", "output", "fit", "adjoint", "find_total")
 
