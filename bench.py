@@ -42,6 +42,147 @@ FIT_BYTES_PER_TRACK = 88.0              # 5 params + 15 cov + chi2 + ndf
 FIT_FLOPS_PER_HIT = 290.0               # transport 55 + covariance 100 + update 135
 
 
+def batched_vs_plain(torch, tpc, dev, steps):
+    """512 events of log-uniform multiplicity (10..1e4 tracks, noise 5-30%):
+    the whole batch as one autotuned, graph-captured call vs the plain path
+    (one load + find + fit per event).  Both give identical tracks."""
+    from paper_2412_13755_gb300 import synth
+    t0 = time.perf_counter()
+    ev = synth.uneven_batch_parallel()
+    gen_s = time.perf_counter() - t0
+    n, E = ev.n, ev.n_events
+    off = ev.evt_sector_off
+    y = torch.from_numpy(ev.y).to(dev)
+    z = torch.from_numpy(ev.z).to(dev)
+    row = torch.from_numpy(ev.row.view(np.int16)).to(dev).view(torch.uint16)
+    d_off = torch.from_numpy(off).to(dev)
+    cap = n // 10 + 16
+    # batched: one context over all events
+    trb = tpc.Tracker(n, E, device=dev)
+    outb = (torch.empty(n, dtype=torch.int32, device=dev), torch.empty(cap + 1, dtype=torch.int32, device=dev),
+            torch.empty(n, dtype=torch.int32, device=dev), torch.empty(1, dtype=torch.int32, device=dev))
+    fitb = (torch.empty(cap, 5, dtype=torch.float32, device=dev), torch.empty(cap, 15, dtype=torch.float32, device=dev),
+            torch.empty(cap, dtype=torch.float32, device=dev), torch.empty(cap, dtype=torch.int32, device=dev))
+    trb.load(y, z, row, d_off, E)
+    tune = trb.autotune(out=outb)
+
+    def step_b():
+        trb.load(y, z, row, d_off, E)
+        trb.find(out=outb)
+        trb.fit(outb[1], outb[2], cap, outb[3], out=fitb)
+
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(side):
+        step_b()
+    torch.cuda.current_stream(dev).wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    l0 = trb.stats().n_launches
+    with torch.cuda.graph(graph):
+        step_b()
+    graph_kernels = int(trb.stats().n_launches - l0)  # kernels captured in the graph
+    graph.replay()
+    torch.cuda.synchronize()
+    stb = trb.check()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        graph.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    batched_s = e0.elapsed_time(e1) / 1e3 / steps
+    # plain: one context sized for the largest event, one call sequence per event
+    sizes = off[36::36] - off[0:-1:36]
+    nmax = int(sizes.max())
+    trp = tpc.Tracker(nmax, 1, device=dev)
+    capp = nmax // 10 + 16
+    outp = (torch.empty(nmax, dtype=torch.int32, device=dev), torch.empty(capp + 1, dtype=torch.int32, device=dev),
+            torch.empty(nmax, dtype=torch.int32, device=dev), torch.empty(1, dtype=torch.int32, device=dev))
+    fitp = (torch.empty(capp, 5, dtype=torch.float32, device=dev), torch.empty(capp, 15, dtype=torch.float32, device=dev),
+            torch.empty(capp, dtype=torch.float32, device=dev), torch.empty(capp, dtype=torch.int32, device=dev))
+    ev_offs = [d_off[36 * e:36 * e + 37] - int(off[36 * e]) for e in range(E)]
+    starts = [int(off[36 * e]) for e in range(E)]
+    plain_toc = torch.empty(n, dtype=torch.int32, device=dev)
+
+    def step_p(record=False):
+        for e in range(E):
+            b, m = starts[e], int(sizes[e])
+            trp.load(y[b:b + m], z[b:b + m], row[b:b + m], ev_offs[e], 1)
+            trp.find(out=outp)
+            trp.fit(outp[1], outp[2], capp, outp[3], out=fitp)
+            if record:
+                plain_toc[b:b + m] = outp[0][:m]
+
+    step_p(record=True)
+    torch.cuda.synchronize()
+    trp.check()
+    # equal accuracy: per event, the plain track ids equal the batched ones
+    # shifted by the number of batched tracks of earlier events
+    bt = outb[0]
+    first = torch.full((E,), 0, dtype=torch.int32, device=dev)
+    for e in range(E):
+        b, m = starts[e], int(sizes[e])
+        seg = bt[b:b + m]
+        first[e] = seg[seg >= 0].min() if bool((seg >= 0).any()) else 0
+    ev_of = torch.repeat_interleave(torch.arange(E, device=dev), torch.from_numpy(sizes).to(dev))
+    shifted = torch.where(bt >= 0, bt - first[ev_of], bt)
+    identical = bool(torch.equal(shifted, plain_toc))
+    e0.record()
+    for _ in range(steps):
+        step_p()
+    e1.record()
+    torch.cuda.synchronize()
+    plain_s = e0.elapsed_time(e1) / 1e3 / steps
+    return {
+        "workload": f"uneven_batch: {E} events, log-uniform 10..1e4 tracks, noise U[5%,30%], {n} clusters",
+        "batched_clusters_per_s": n / batched_s, "plain_clusters_per_s": n / plain_s,
+        "speedup": plain_s / batched_s, "batched_ms": 1e3 * batched_s, "plain_ms": 1e3 * plain_s,
+        "identical_tracks": identical, "tracks": int(stb.n_tracks),
+        "tune": {"lane_blocks_per_sm": tune.lane_blocks_per_sm, "lane_tile": tune.lane_tile},
+        "graph_kernels_per_step": graph_kernels, "generation_s": gen_s,
+        "inputs_vs_l2": "1.5 GB of inputs, larger than L2 (no flush needed)",
+    }
+
+
+def adjoint_bench(torch, tpc, dev, steps):
+    """Alignment sample: 2e5 tracks pT > 1 GeV/c; chi2 + gradient per step."""
+    from paper_2412_13755_gb300 import synth
+    ev = synth.alignment_sample_parallel()
+    off_h, hits_h, _ = ev.truth_tracks(n_min=10)
+    T = len(off_h) - 1
+    tr = tpc.Tracker(ev.n, 1, device=dev)
+    y = torch.from_numpy(ev.y).to(dev)
+    z = torch.from_numpy(ev.z).to(dev)
+    row = torch.from_numpy(ev.row.view(np.int16)).to(dev).view(torch.uint16)
+    d_off = torch.from_numpy(ev.evt_sector_off).to(dev)
+    tr.load(y, z, row, d_off, 1)
+    trk_off = torch.from_numpy(off_h).to(dev)
+    trk_hits = torch.from_numpy(hits_h).to(dev)
+    align = torch.from_numpy(0.5 * ev.align).to(dev)
+    for _ in range(2):
+        tr.adjoint(trk_off, trk_hits, T, align)
+    torch.cuda.synchronize()
+    tr.check()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        chi2, grad = tr.adjoint(trk_off, trk_hits, T, align)
+    e1.record()
+    torch.cuda.synchronize()
+    s_grad = e0.elapsed_time(e1) / 1e3 / steps
+    e0.record()
+    for _ in range(steps):
+        tr.adjoint(trk_off, trk_hits, T, align, want_grad=False)
+    e1.record()
+    torch.cuda.synchronize()
+    s_fwd = e0.elapsed_time(e1) / 1e3 / steps
+    return {"workload": f"alignment_sample: {T} tracks pT>1 GeV/c, {ev.n} clusters, 216 parameters",
+            "tracks_per_s": T / s_grad, "forward_only_tracks_per_s": T / s_fwd,
+            "ms_per_step": 1e3 * s_grad, "chi2": float(chi2.item())}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -49,8 +190,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-profiler", action="store_true",
-                    help="skip the CUPTI launch count (when running under ncu)")
+    ap.add_argument("--no-profiler", action="store_true", help="(kept for compatibility)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched-vs-plain and adjoint measurements")
     return ap.parse_args()
 
 
@@ -380,6 +522,9 @@ def run_ours(args):
         "status": {"fp64_updates": st.n_fp64_updates, "segments": st.n_segments,
                    "tracklets": st.n_tracklets, "merges": st.n_merges},
     }
+    if not args.no_extras:
+        line["batched_vs_plain"] = batched_vs_plain(torch, tpc, dev, max(3, args.steps // 4))
+        line["adjoint"] = adjoint_bench(torch, tpc, dev, max(3, args.steps // 4))
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(ev)
     print(json.dumps(line), flush=True)

@@ -77,6 +77,9 @@ typedef struct {
     float fp64_ratio;          /* redo an update in FP64 when a posterior
                                   variance drops below fp64_ratio x prior    */
     float fp64_det;            /* ... or det S <= fp64_det S00 S11           */
+    float fp64_weak_qpt;       /* tpc_fit_tracks refits a track in FP64 when
+                                  its final q/pT variance exceeds this
+                                  fraction of the prior (weak curvature)     */
 } tpc_params;
 
 /* Counters a call leaves in the workspace (read back by tpc_get_stats). */
@@ -174,6 +177,27 @@ tpc_status tpc_fit_adjoint(tpc_ctx* ctx, const int32_t* trk_off, const int32_t* 
  * be NULL) receives a one-line description. */
 tpc_status tpc_get_stats(tpc_ctx* ctx, tpc_stats* out, tpc_stream_t stream);
 tpc_status tpc_last_error(tpc_ctx* ctx, char* buf, size_t len);
+
+/* Launch configuration of the persistent work-queue kernels (the tracklet
+ * lanes): persistent blocks per SM and the number of segments a lane takes
+ * from the queue per atomic ticket. */
+typedef struct {
+    int32_t lane_blocks_per_sm; /* 1..16                                   */
+    int32_t lane_tile;          /* 1..16                                   */
+} tpc_tune;
+
+/* Sets the configuration used by later calls (NULL restores the default
+ * 8 blocks/SM, tile 1). */
+tpc_status tpc_set_tune(tpc_ctx* ctx, const tpc_tune* tune);
+
+/* Autotuner: runs tpc_find_tracks on the loaded batch (outputs into the
+ * given buffers, as tpc_find_tracks) for each candidate configuration
+ * (blocks/SM in {4, 8, 16} x tile in {1, 4}), times each with CUDA events on
+ * the stream, keeps the fastest for later calls and writes it to *best (may
+ * be NULL).  Synchronises the stream; not for use during graph capture. */
+tpc_status tpc_autotune(tpc_ctx* ctx, int32_t* track_of_cluster, int32_t* trk_off,
+                        int32_t* trk_hits, int32_t* n_tracks_dev, int32_t track_cap,
+                        tpc_tune* best, tpc_stream_t stream);
 
 /* Stage timing (no counterpart in the paper; a measurement aid).  When
  * enabled, the library records CUDA events on the launch stream around its

@@ -84,6 +84,8 @@ Layout make_layout(int64_t N, int32_t E) {
     L.best_b = take(s8);
     L.nxt = take(s4);
     L.prv = take(s4);
+    L.hard = take(n4);
+    L.refit = take(4 * (size_t)L.T);
     L.trk_flag = take(n4);
     L.trk_rank = take(n4 + 4);
     L.trk_len_at = take(n4);
@@ -146,6 +148,7 @@ void tpc_default_params(tpc_params* p) {
     p->snp_max = 0.999f;
     p->fp64_ratio = 1e-4f;
     p->fp64_det = 1e-6f;
+    p->fp64_weak_qpt = 1e-3f;
 }
 
 tpc_status tpc_create(tpc_ctx** ctx, const tpc_params* params) {
@@ -262,6 +265,7 @@ tpc_status tpc_fit_tracks(tpc_ctx* c, const int32_t* trk_off, const int32_t* trk
     if (!c->have_ws || !c->have_clusters) return fail(c, TPC_ERR_STATE, "no workspace or clusters");
     if (n_tracks < 0 || (n_tracks > 0 && (!trk_off || !trk_hits || !params || !cov || !chi2 || !ndf)))
         return fail(c, TPC_ERR_ARG, "tpc_fit_tracks: bad argument");
+    if (n_tracks > c->ws.L.T - 1) return fail(c, TPC_ERR_CAPACITY, "tpc_fit_tracks: too many tracks");
     cudaError_t e = run_fit(c, trk_off, trk_hits, n_tracks, n_tracks_dev, params, cov, chi2, ndf,
                             (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "tpc_fit_tracks");
@@ -278,6 +282,62 @@ tpc_status tpc_fit_adjoint(tpc_ctx* c, const int32_t* trk_off, const int32_t* tr
     cudaError_t e = run_adjoint(c, trk_off, trk_hits, n_tracks, align, chi2_total, grad,
                                 (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "tpc_fit_adjoint");
+    return TPC_OK;
+}
+
+tpc_status tpc_set_tune(tpc_ctx* c, const tpc_tune* t) {
+    if (!c) return TPC_ERR_ARG;
+    if (!t) {
+        c->tune = tpc_tune{8, 1};
+        return TPC_OK;
+    }
+    if (t->lane_blocks_per_sm < 1 || t->lane_blocks_per_sm > 16 || t->lane_tile < 1 || t->lane_tile > 16)
+        return fail(c, TPC_ERR_ARG, "tpc_set_tune: out of range");
+    c->tune = *t;
+    return TPC_OK;
+}
+
+tpc_status tpc_autotune(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hits,
+                        int32_t* n_tracks_dev, int32_t track_cap, tpc_tune* best, tpc_stream_t stream) {
+    if (!c) return TPC_ERR_ARG;
+    if (!c->have_ws || !c->have_clusters) return fail(c, TPC_ERR_STATE, "no workspace or clusters");
+    if (!toc || !trk_off || !trk_hits || !n_tracks_dev || track_cap < 0 || track_cap > c->ws.L.T - 1)
+        return fail(c, TPC_ERR_ARG, "tpc_autotune: bad argument");
+    const cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "tpc_autotune");
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_fail(c, cudaGetLastError(), "tpc_autotune");
+    }
+    const bool timing = c->timing;
+    c->timing = false;
+    static const int bps[3] = {4, 8, 16};
+    static const int tiles[2] = {1, 4};
+    tpc_tune best_t = c->tune;
+    float best_ms = 1e30f;
+    cudaError_t err = cudaSuccess;
+    for (int rep = 0; rep < 2 && err == cudaSuccess; ++rep)  // first pass warms up
+        for (int bi = 0; bi < 3 && err == cudaSuccess; ++bi)
+            for (int ti = 0; ti < 2 && err == cudaSuccess; ++ti) {
+                c->tune = tpc_tune{bps[bi], tiles[ti]};
+                err = cudaEventRecord(e0, s);
+                if (err == cudaSuccess) err = run_find(c, toc, trk_off, trk_hits, n_tracks_dev, track_cap, s);
+                if (err == cudaSuccess) err = cudaEventRecord(e1, s);
+                if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+                float ms = 0.f;
+                if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+                if (err == cudaSuccess && rep == 1 && ms < best_ms) {
+                    best_ms = ms;
+                    best_t = c->tune;
+                }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->timing = timing;
+    c->tune = best_t;
+    if (err != cudaSuccess) return cuda_fail(c, err, "tpc_autotune");
+    if (best) *best = best_t;
     return TPC_OK;
 }
 

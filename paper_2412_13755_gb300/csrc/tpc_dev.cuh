@@ -119,7 +119,8 @@ struct MoveJ {
 // reach snp_max.
 template <class R>
 __device__ __forceinline__ bool kf_move(KFT<R>& s, double x_to, int to, const Geo* __restrict__ geo,
-                                        R kb, R snp_max, MoveJ* mj = nullptr) {
+                                        R kb, R snp_max, MoveJ* mj = nullptr,
+                                        const R* dx_same_frame = nullptr) {
     double xs = s.x;
     R ys = s.p[0], ss = s.p[2];
     R ys_lo = s.lo[0], ss_lo = s.lo[2];
@@ -144,7 +145,8 @@ __device__ __forceinline__ bool kf_move(KFT<R>& s, double x_to, int to, const Ge
         ss = sn;
         ss_lo = R(0);
     }
-    const R dx = (R)(x_to - xs);
+    // dx_same_frame: the caller's exact step between row planes of one frame
+    const R dx = (!rot && dx_same_frame) ? *dx_same_frame : (R)(x_to - xs);
     const R t = s.p[3], w = s.p[4];
     const R k = w * kb;
     const R s1 = ss;
@@ -296,6 +298,34 @@ __device__ __forceinline__ float kf_update(KF& s, float my, float mz, float sy2,
         for (int j = i; j < 5; ++j)
             s.C[sx(i, j)] = (float)(Cd[sx(i, j)] - (k0[i] * c0[j] + k1[i] * c1[j]));
     return (float)(dr0 * dr0 * e00 + 2.0 * dr0 * dr1 * e01 + dr1 * dr1 * e11);
+}
+
+// Plain FP64 update (used when a whole track is refit in FP64).
+__device__ __forceinline__ double kf_update_d(KFD& s, double my, double mz, double sy2, double sz2) {
+    const double r0 = my - (s.p[0] + s.lo[0]), r1 = mz - (s.p[1] + s.lo[1]);
+    const double S00 = s.C[0] + sy2, S01 = s.C[1], S11 = s.C[5] + sz2;
+    const double det = S00 * S11 - S01 * S01;
+    const double i00 = S11 / det, i01 = -S01 / det, i11 = S00 / det;
+    double C0[5], C1[5], K0[5], K1[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        C0[i] = s.C[sx(0, i)];
+        C1[i] = s.C[sx(1, i)];
+    }
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        K0[i] = C0[i] * i00 + C1[i] * i01;
+        K1[i] = C0[i] * i01 + C1[i] * i11;
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) add_comp(s.p[i], s.lo[i], K0[i] * r0 + K1[i] * r1);
+#pragma unroll
+    for (int i = 3; i < 5; ++i) s.p[i] += K0[i] * r0 + K1[i] * r1;
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+#pragma unroll
+        for (int j = i; j < 5; ++j) s.C[sx(i, j)] -= K0[i] * C0[j] + K1[i] * C1[j];
+    return r0 * r0 * i00 + 2.0 * r0 * r1 * i01 + r1 * r1 * i11;
 }
 
 // Neumaier-compensated FP32 accumulation.

@@ -198,66 +198,86 @@ __device__ __forceinline__ void cell_range(const Cells& cells, int g, int r, flo
 
 // For each cluster: the (down, up) pair in rows r-gd, r+gu minimising D^2
 // with D^2 <= chi2_link, over gap pairs in order of increasing gd+gu, then
-// gu; ties by the canonical id of u, then of d.
+// gu; ties by the canonical id of u, then of d.  Run in two passes with the
+// same result: pass 1 tries gd+gu = 2 for every cluster and queues the
+// clusters without a pair; pass 2 continues those from gd+gu = 3, so the
+// lanes of a warp do similar amounts of work.
 __global__ void __launch_bounds__(TPB) k_neighbours(
-    int64_t n, const float* __restrict__ yb, const float* __restrict__ zb,
+    int pass, int64_t n, const float* __restrict__ yb, const float* __restrict__ zb,
     const int32_t* __restrict__ orig, const int32_t* __restrict__ grpb,
     const uint8_t* __restrict__ rowb, Cells cells, const Geo* __restrict__ geo, NbPrm P,
-    int32_t* choice_dn, int32_t* choice_up, float* d2out) {
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
-         c += (int64_t)gridDim.x * blockDim.x) {
-        const int g = grpb[c], r = rowb[c];
-        const float xc = geo->row_xf[r], yc = yb[c], zc = zb[c];
+    int32_t* choice_dn, int32_t* choice_up, float* d2out, int32_t* hard, int32_t* st) {
+    const int64_t count = pass == 1 ? n : (int64_t)st[ST_NHARD];
+    const int sum_lo = pass == 1 ? 2 : 3, sum_hi = pass == 1 ? 2 : 2 * P.max_gap;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t i_end = ((count + stride - 1) / stride) * stride;  // warp-uniform trip count
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < i_end; i += stride) {
+        bool active = i < count;
+        const int64_t c = !active ? 0 : (pass == 1 ? i : (int64_t)hard[i]);
         int bd = -1, bu = -1;
         float bd2 = 0.f;
-        for (int sum = 2; sum <= 2 * P.max_gap && bd < 0; ++sum) {
-            for (int gu = 1; gu <= P.max_gap && bd < 0; ++gu) {
-                const int gd = sum - gu;
-                if (gd < 1 || gd > P.max_gap) continue;
-                const int rd = r - gd, ru = r + gu;
-                if (rd < 0 || ru >= NROW) continue;
-                const float xd = geo->row_xf[rd], xu = geo->row_xf[ru];
-                const float wzd = __fmul_rn(P.win_z, fabsf(__fsub_rn(xd, xc)));
-                const float wzu = __fmul_rn(P.win_z, fabsf(__fsub_rn(xu, xc)));
-                // cell ranges: a superset of the exact window
-                int db, de, ub, ue;
-                cell_range(cells, g, rd, zc - wzd * 1.0001f - 1e-3f, zc + wzd * 1.0001f + 1e-3f, db, de);
-                cell_range(cells, g, ru, zc - wzu * 1.0001f - 1e-3f, zc + wzu * 1.0001f + 1e-3f, ub, ue);
-                int pd = -1, pu = -1;
-                float pd2 = 0.f;
-                int pod = 0, pou = 0;
-                for (int d = db; d < de; ++d) {
-                    const float ydd = yb[d], zdd = zb[d];
-                    if (!in_win(xc, yc, zc, xd, ydd, zdd, P.win_y, P.win_z)) continue;
-                    for (int u = ub; u < ue; ++u) {
-                        const float yuu = yb[u], zuu = zb[u];
-                        if (!in_win(xc, yc, zc, xu, yuu, zuu, P.win_y, P.win_z)) continue;
-                        const float d2 = triplet_d2(xd, ydd, zdd, xc, yc, zc, xu, yuu, zuu, P.sy2, P.sz2);
-                        if (!(d2 <= P.chi2_link)) continue;
-                        bool better = pd < 0 || d2 < pd2;
-                        if (!better && d2 == pd2) {
-                            const int ou = orig[u], od = orig[d];
-                            better = ou < pou || (ou == pou && od < pod);
-                        }
-                        if (better) {
-                            pd = d;
-                            pu = u;
-                            pd2 = d2;
-                            pod = orig[d];
-                            pou = orig[u];
+        if (active) {
+            const int g = grpb[c], r = rowb[c];
+            const float xc = geo->row_xf[r], yc = yb[c], zc = zb[c];
+            for (int sum = sum_lo; sum <= sum_hi && bd < 0; ++sum) {
+                for (int gu = 1; gu <= P.max_gap && bd < 0; ++gu) {
+                    const int gd = sum - gu;
+                    if (gd < 1 || gd > P.max_gap) continue;
+                    const int rd = r - gd, ru = r + gu;
+                    if (rd < 0 || ru >= NROW) continue;
+                    const float xd = geo->row_xf[rd], xu = geo->row_xf[ru];
+                    const float wzd = __fmul_rn(P.win_z, fabsf(__fsub_rn(xd, xc)));
+                    const float wzu = __fmul_rn(P.win_z, fabsf(__fsub_rn(xu, xc)));
+                    // cell ranges: a superset of the exact window
+                    int db, de, ub, ue;
+                    cell_range(cells, g, rd, zc - wzd * 1.0001f - 1e-3f, zc + wzd * 1.0001f + 1e-3f, db, de);
+                    cell_range(cells, g, ru, zc - wzu * 1.0001f - 1e-3f, zc + wzu * 1.0001f + 1e-3f, ub, ue);
+                    int pd = -1, pu = -1;
+                    float pd2 = 0.f;
+                    int pod = 0, pou = 0;
+                    for (int d = db; d < de; ++d) {
+                        const float ydd = yb[d], zdd = zb[d];
+                        if (!in_win(xc, yc, zc, xd, ydd, zdd, P.win_y, P.win_z)) continue;
+                        for (int u = ub; u < ue; ++u) {
+                            const float yuu = yb[u], zuu = zb[u];
+                            if (!in_win(xc, yc, zc, xu, yuu, zuu, P.win_y, P.win_z)) continue;
+                            const float d2 = triplet_d2(xd, ydd, zdd, xc, yc, zc, xu, yuu, zuu, P.sy2, P.sz2);
+                            if (!(d2 <= P.chi2_link)) continue;
+                            bool better = pd < 0 || d2 < pd2;
+                            if (!better && d2 == pd2) {
+                                const int ou = orig[u], od = orig[d];
+                                better = ou < pou || (ou == pou && od < pod);
+                            }
+                            if (better) {
+                                pd = d;
+                                pu = u;
+                                pd2 = d2;
+                                pod = orig[d];
+                                pou = orig[u];
+                            }
                         }
                     }
-                }
-                if (pd >= 0) {
-                    bd = pd;
-                    bu = pu;
-                    bd2 = pd2;
+                    if (pd >= 0) {
+                        bd = pd;
+                        bu = pu;
+                        bd2 = pd2;
+                    }
                 }
             }
+            choice_dn[c] = bd;
+            choice_up[c] = bu;
+            d2out[c] = bd2;
         }
-        choice_dn[c] = bd;
-        choice_up[c] = bu;
-        d2out[c] = bd2;
+        if (pass == 1) {
+            // queue the clusters without a pair (warp-aggregated)
+            const bool q = active && bd < 0;
+            const unsigned bal = __ballot_sync(0xffffffffu, q);
+            int base = 0;
+            const int lane = threadIdx.x & 31;
+            if (lane == 0 && bal) base = atomicAdd(&st[ST_NHARD], __popc(bal));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (q) hard[base + __popc(bal & ((1u << lane) - 1u))] = (int32_t)c;
+        }
     }
 }
 
@@ -332,24 +352,21 @@ __global__ void k_chains(int64_t n, const int32_t* __restrict__ link_dn,
 
 // ---------------------------------------------------------------- S3b -----
 struct TlPrm {
-    float sy2, sz2, chi2_ext, kb, snp_max, fp64_ratio, fp64_det;
+    float sy2, sz2, chi2_ext, kb, snp_max, fp64_ratio, fp64_det, pitch;
     int ext_max_miss, n_seg;
     double bz, seed_snp, seed_qpt;
     float prior[5];
 };
 
-// Fit the tracklet's hits (row-indexed slot, -1 = empty) in one direction:
-// inward (rows descending, seeded at the outermost) or outward.
-__device__ bool fit_slot(const int32_t* __restrict__ hit, int rmin, int rmax, bool inward,
-                         const float* __restrict__ yb, const float* __restrict__ zb, int sector,
-                         const Geo* __restrict__ geo, const TlPrm& P, KF& s, int* n_fp64) {
-    int n = 0;
-    for (int r = rmin; r <= rmax; ++r) n += hit[r] >= 0;
-    if (n < 3) return false;
-    // first, middle (n/2-th in fit order) and last hit
+// Three-point seed of the hits in a tracklet slot for one fit direction:
+// first, middle (n/2-th in fit order) and last hit.
+__device__ void seed_slot(const int32_t* __restrict__ hit, int rmin, int rmax, int n, bool inward,
+                          const float* __restrict__ yb, const float* __restrict__ zb, int sector,
+                          const Geo* __restrict__ geo, const TlPrm& P, KF& s) {
     int rows[3], secs[3] = {sector, sector, sector};
     float ys[3], zs[3];
-    int k = 0, want = n / 2;
+    const int want = n / 2;
+    int k = 0;
     for (int j = 0; j <= rmax - rmin; ++j) {
         const int r = inward ? rmax - j : rmin + j;
         const int h = hit[r];
@@ -360,95 +377,192 @@ __device__ bool fit_slot(const int32_t* __restrict__ hit, int rmin, int rmax, bo
         ++k;
     }
     kf_seed(s, rows, secs, ys, zs, inward, geo, P.bz, P.seed_snp, P.seed_qpt, P.prior);
-    for (int j = 0; j <= rmax - rmin; ++j) {
-        const int r = inward ? rmax - j : rmin + j;
-        const int h = hit[r];
-        if (h < 0) continue;
-        MoveJ mj;
-        if (!kf_move<float>(s, geo->row_xd[r], sector, geo, P.kb, P.snp_max, &mj)) return false;
-        kf_update(s, yb[h], zb[h], P.sy2, P.sz2, P.fp64_ratio, P.fp64_det, n_fp64, &mj);
-    }
-    return true;
 }
 
-// Extend from the current state row by row (dir = -1 inward, +1 outward):
-// in each row take the cluster with the smallest predicted-residual chi2
-// (ties: smaller canonical id) if <= chi2_ext; stop after ext_max_miss empty
-// rows, at the last row, on a transport failure or when the prediction
-// leaves the sector's acceptance.  Returns the last row reached with a hit.
-__device__ int extend_slot(int32_t* __restrict__ hit, int r_last, int dir, KF& s, int g,
-                           const float* __restrict__ yb, const float* __restrict__ zb,
-                           const int32_t* __restrict__ orig, const Cells& cells,
-                           const Geo* __restrict__ geo, const TlPrm& P, int* n_fp64) {
-    const int sector = g % NSEC;
-    int misses = 0;
-    for (int r = r_last + dir; r >= 0 && r < NROW; r += dir) {
-        MoveJ mj;
-        if (!kf_move<float>(s, geo->row_xd[r], sector, geo, P.kb, P.snp_max, &mj)) break;
-        if (fabs((double)s.p[0] + (double)s.lo[0]) > geo->row_xd[r] * geo->tan_half_d) break;
-        const float S00 = s.C[0] + P.sy2, S01 = s.C[1], S11 = s.C[5] + P.sz2;
-        const float det = S00 * S11 - S01 * S01;
-        const float wz = sqrtf(P.chi2_ext * S11) * 1.001f + 1e-3f;
-        const float wy = sqrtf(P.chi2_ext * S00) * 1.001f + 1e-3f;
-        int b, e;
-        cell_range(cells, g, r, s.p[1] - wz, s.p[1] + wz, b, e);
-        int best = -1, bo = 0;
-        float bchi = 0.f;
-        for (int c = b; c < e; ++c) {
-            const float r1 = (zb[c] - s.p[1]) - s.lo[1];
-            if (fabsf(r1) > wz) continue;
-            const float r0 = (yb[c] - s.p[0]) - s.lo[0];
-            if (fabsf(r0) > wy) continue;
-            const float chi = (r0 * r0 * S11 - 2.f * r0 * r1 * S01 + r1 * r1 * S00) / det;
-            if (!(chi <= P.chi2_ext)) continue;
-            const int oc = orig[c];
-            if (best < 0 || chi < bchi || (chi == bchi && oc < bo)) {
-                best = c;
-                bchi = chi;
-                bo = oc;
-            }
-        }
-        if (best >= 0) {
-            kf_update(s, yb[best], zb[best], P.sy2, P.sz2, P.fp64_ratio, P.fp64_det, n_fp64, &mj);
-            hit[r] = best;
-            r_last = r;
-            misses = 0;
-        } else if (++misses >= P.ext_max_miss) {
-            break;
-        }
-    }
-    return r_last;
-}
+// Tracklet lanes.  Every lane owns one slot at a time and runs a small state
+// machine, one Kalman step per loop iteration, so that the lanes of a warp
+// execute the same transport / update code:
+//   build:  inward fit of the chain -> inward extension -> outward fit of all
+//           hits -> outward extension   (a failed fit skips its extension)
+//   refit:  inward fit (state at the innermost) -> outward fit (outermost)
+// Extension: in each row the cluster with the smallest predicted-residual
+// chi2 (ties: smaller canonical id) if <= chi2_ext; stop after ext_max_miss
+// empty rows, at the last row, on a transport failure, or when the
+// prediction leaves the row's acceptance.  Finished lanes take the next slot
+// from an atomic work queue.
+enum { PH_FIT_IN = 0, PH_EXT_IN = 1, PH_FIT_OUT = 2, PH_EXT_OUT = 3 };
 
-__global__ void __launch_bounds__(128) k_tracklets(
-    const int32_t* __restrict__ seg_start, const int32_t* __restrict__ seg_grp,
+__global__ void __launch_bounds__(128, 4) k_tracklet_lanes(
+    int refit, const int32_t* __restrict__ seg_start, const int32_t* __restrict__ seg_grp,
     const int32_t* __restrict__ seg_canon, const int32_t* __restrict__ link_up,
     const float* __restrict__ yb, const float* __restrict__ zb, const int32_t* __restrict__ orig,
     const uint8_t* __restrict__ rowb, Cells cells, const Geo* __restrict__ geo, TlPrm P,
-    int64_t Scap, int32_t* st, int32_t* tl_rowhit, int32_t* tl_n, unsigned long long* tl_key) {
+    int64_t Scap, int32_t* st, int32_t* tl_rowhit, int32_t* tl_n, unsigned long long* tl_key,
+    const int32_t* __restrict__ tl_keep, const int32_t* __restrict__ tl_rmin_in,
+    const int32_t* __restrict__ tl_rmax_in, float* tl_state, int32_t* tl_ok, int tile) {
     const int nseg = min((int64_t)st[ST_NSEG], Scap);
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nseg; s += gridDim.x * blockDim.x) {
-        int32_t* hit = tl_rowhit + (int64_t)s * NROW;
-        for (int r = 0; r < NROW; ++r) hit[r] = -1;
-        const int g = seg_grp[s];
-        const int sector = g % NSEC;
-        int rmin = NROW, rmax = -1;
-        for (int c = seg_start[s]; c >= 0; c = link_up[c]) {
-            const int r = rowb[c];
-            hit[r] = c;
-            rmin = min(rmin, r);
-            rmax = max(rmax, r);
+    int32_t* queue = &st[refit ? ST_Q_REFIT : ST_Q_BUILD];
+    int s = -1, phase = 0, r = 0, rmin = 0, rmax = 0, n = 0, misses = 0, g = 0, sector = 0, ok = 0;
+    int steps = 0;
+    int t_next = 0, t_end = 0;  // slots of the current ticket
+    int32_t* hit = nullptr;
+    KF kf;
+    for (;;) {
+        if (s < 0) {
+            // take the next slot (a ticket covers `tile` consecutive slots)
+            if (t_next >= t_end) {
+                t_next = atomicAdd(queue, tile);
+                t_end = t_next + tile;
+            }
+            s = t_next++;
+            if (s >= nseg) break;
+            hit = tl_rowhit + (int64_t)s * NROW;
+            g = seg_grp[s];
+            sector = g % NSEC;
+            ok = 0;
+            if (refit) {
+                if (!tl_keep[s]) {
+                    s = -1;
+                    continue;
+                }
+                rmin = tl_rmin_in[s];
+                rmax = tl_rmax_in[s];
+                n = 0;
+                for (int rr = rmin; rr <= rmax; ++rr) n += hit[rr] >= 0;
+            } else {
+                for (int rr = 0; rr < NROW; ++rr) hit[rr] = -1;
+                rmin = NROW;
+                rmax = -1;
+                n = 0;
+                for (int c = seg_start[s]; c >= 0; c = link_up[c]) {
+                    const int rr = rowb[c];
+                    hit[rr] = c;
+                    rmin = min(rmin, rr);
+                    rmax = max(rmax, rr);
+                    ++n;
+                }
+            }
+            phase = PH_FIT_IN;
+            seed_slot(hit, rmin, rmax, n, true, yb, zb, sector, geo, P, kf);
+            r = rmax + 1;
+            misses = 0;
         }
-        KF kf;
-        if (fit_slot(hit, rmin, rmax, true, yb, zb, sector, geo, P, kf, &st[ST_FP64]))
-            rmin = extend_slot(hit, rmin, -1, kf, g, yb, zb, orig, cells, geo, P, &st[ST_FP64]);
-        if (fit_slot(hit, rmin, rmax, false, yb, zb, sector, geo, P, kf, &st[ST_FP64]))
-            rmax = extend_slot(hit, rmax, +1, kf, g, yb, zb, orig, cells, geo, P, &st[ST_FP64]);
-        int n = 0;
-        for (int r = rmin; r <= rmax; ++r) n += hit[r] >= 0;
+        // ---- one step of the current phase
+        const bool fit = phase == PH_FIT_IN || phase == PH_FIT_OUT;
+        const int dir = (phase == PH_FIT_IN || phase == PH_EXT_IN) ? -1 : 1;
+        int target = r + dir;
+        if (fit) {
+            while (target >= rmin && target <= rmax && hit[target] < 0) target += dir;
+        }
+        bool end_phase;
+        if (fit) end_phase = target < rmin || target > rmax;
+        else end_phase = target < 0 || target >= NROW || misses >= P.ext_max_miss;
+        bool moved = false;
+        MoveJ mj;
+        if (!end_phase) {
+            // within one sector the planes are rows: the step is an exact
+            // multiple of the row pitch
+            const int from_row = (r >= 0 && r < NROW) ? r : (dir < 0 ? rmax : rmin);
+            const float dxr = (float)(target - from_row) * P.pitch;
+            moved = kf_move<float>(kf, geo->row_xd[target], sector, geo, P.kb, P.snp_max, &mj,
+                                   kf.x == geo->row_xd[from_row] ? &dxr : nullptr);
+            ++steps;
+            if (!moved) end_phase = true;
+            else if (!fit && fabsf(kf.p[0] + kf.lo[0]) > geo->row_xf[target] * geo->tan_half)
+                end_phase = true;
+        }
+        if (!end_phase) {
+            int c = -1;
+            if (fit) {
+                c = hit[target];
+            } else {
+                const float S00 = kf.C[0] + P.sy2, S01 = kf.C[1], S11 = kf.C[5] + P.sz2;
+                const float det = S00 * S11 - S01 * S01;
+                const float wz = sqrtf(P.chi2_ext * S11) * 1.001f + 1e-3f;
+                const float wy = sqrtf(P.chi2_ext * S00) * 1.001f + 1e-3f;
+                int b, e;
+                cell_range(cells, g, target, kf.p[1] - wz, kf.p[1] + wz, b, e);
+                int bo = 0;
+                float bchi = 0.f;
+                for (int q = b; q < e; ++q) {
+                    const float r1 = (zb[q] - kf.p[1]) - kf.lo[1];
+                    if (fabsf(r1) > wz) continue;
+                    const float r0 = (yb[q] - kf.p[0]) - kf.lo[0];
+                    if (fabsf(r0) > wy) continue;
+                    const float chi = (r0 * r0 * S11 - 2.f * r0 * r1 * S01 + r1 * r1 * S00) / det;
+                    if (!(chi <= P.chi2_ext)) continue;
+                    const int oq = orig[q];
+                    if (c < 0 || chi < bchi || (chi == bchi && oq < bo)) {
+                        c = q;
+                        bchi = chi;
+                        bo = oq;
+                    }
+                }
+                if (c >= 0) {
+                    hit[target] = c;
+                    ++n;
+                    if (dir < 0) rmin = target; else rmax = target;
+                    misses = 0;
+                } else {
+                    ++misses;
+                }
+            }
+            if (c >= 0) kf_update(kf, yb[c], zb[c], P.sy2, P.sz2, P.fp64_ratio, P.fp64_det, &st[ST_FP64], &mj);
+            r = target;
+            continue;
+        }
+        // ---- phase transitions
+        if (phase == PH_FIT_IN) {
+            if (moved || target < rmin || target > rmax) ok |= 1;  // fit completed
+            if (refit && (ok & 1)) {
+                float* out = tl_state + (int64_t)s * 40;
+                for (int i = 0; i < 3; ++i) out[i] = kf.p[i] + kf.lo[i];
+                for (int i = 3; i < 5; ++i) out[i] = kf.p[i];
+                for (int i = 0; i < 15; ++i) out[5 + i] = kf.C[i];
+            }
+            if (!refit && (ok & 1)) {
+                phase = PH_EXT_IN;
+                r = rmin;
+                misses = 0;
+                continue;
+            }
+            phase = PH_FIT_OUT;
+        } else if (phase == PH_EXT_IN) {
+            phase = PH_FIT_OUT;
+        } else if (phase == PH_FIT_OUT) {
+            if (moved || target < rmin || target > rmax) ok |= 2;
+            if (refit) {
+                if (ok & 2) {
+                    float* out = tl_state + (int64_t)s * 40;
+                    for (int i = 0; i < 3; ++i) out[20 + i] = kf.p[i] + kf.lo[i];
+                    for (int i = 3; i < 5; ++i) out[20 + i] = kf.p[i];
+                    for (int i = 0; i < 15; ++i) out[25 + i] = kf.C[i];
+                }
+                tl_ok[s] = ok;
+                s = -1;
+                continue;
+            }
+            if (ok & 2) {
+                phase = PH_EXT_OUT;
+                r = rmax;
+                misses = 0;
+                continue;
+            }
+            phase = PH_EXT_OUT + 1;  // finished
+        } else {
+            phase = PH_EXT_OUT + 1;
+        }
+        if (phase == PH_FIT_OUT) {
+            seed_slot(hit, rmin, rmax, n, false, yb, zb, sector, geo, P, kf);
+            r = rmin - 1;
+            continue;
+        }
+        // finished building this tracklet
         tl_n[s] = n;
         tl_key[s] = ((unsigned long long)(NROW * 4 - n) << 32) | (uint32_t)seg_canon[s];
+        s = -1;
     }
+    atomicAdd(&st[ST_KFSTEPS], steps);
 }
 
 // every cluster belongs to the best tracklet containing it
@@ -462,14 +576,14 @@ __global__ void k_owner(const int32_t* __restrict__ tl_rowhit, const unsigned lo
     }
 }
 
-// keep tracklets owning >= n_seg clusters; refit them both ways
-__global__ void __launch_bounds__(128) k_keep(
-    int32_t* tl_rowhit, const unsigned long long* __restrict__ tl_key,
-    const unsigned long long* __restrict__ owner, const int32_t* __restrict__ seg_grp,
-    const float* __restrict__ yb, const float* __restrict__ zb, const int32_t* __restrict__ orig,
-    const Geo* __restrict__ geo, TlPrm P, int64_t Scap, int32_t* st, int32_t* tl_keep,
-    int32_t* tl_canon, int32_t* tl_rmin, int32_t* tl_rmax, float* tl_zin, float* tl_zout,
-    float* tl_state, int32_t* tl_ok, int32_t* grp_tl_cnt) {
+// keep tracklets owning >= n_seg clusters (hits they do not own are
+// cleared); the refits of the kept ones run in k_tracklet_lanes
+__global__ void k_keep(int32_t* tl_rowhit, const unsigned long long* __restrict__ tl_key,
+                       const unsigned long long* __restrict__ owner, const int32_t* __restrict__ seg_grp,
+                       const float* __restrict__ zb, const int32_t* __restrict__ orig, int n_seg,
+                       int64_t Scap, int32_t* st, int32_t* tl_keep, int32_t* tl_canon,
+                       int32_t* tl_rmin, int32_t* tl_rmax, float* tl_zin, float* tl_zout,
+                       int32_t* tl_ok, int32_t* grp_tl_cnt) {
     const int nseg = min((int64_t)st[ST_NSEG], Scap);
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nseg; s += gridDim.x * blockDim.x) {
         int32_t* hit = tl_rowhit + (int64_t)s * NROW;
@@ -488,34 +602,18 @@ __global__ void __launch_bounds__(128) k_keep(
             rmax = max(rmax, r);
             canon = min(canon, orig[h]);
         }
-        if (n < P.n_seg) {
+        tl_ok[s] = 0;
+        if (n < n_seg) {
             tl_keep[s] = 0;
             continue;
         }
         const int g = seg_grp[s];
-        const int sector = g % NSEC;
         tl_keep[s] = 1;
         tl_canon[s] = canon;
         tl_rmin[s] = rmin;
         tl_rmax[s] = rmax;
         tl_zin[s] = zb[hit[rmin]];
         tl_zout[s] = zb[hit[rmax]];
-        float* out = tl_state + (int64_t)s * 40;
-        KF kf;
-        int ok = 0;
-        if (fit_slot(hit, rmin, rmax, true, yb, zb, sector, geo, P, kf, &st[ST_FP64])) {
-            ok |= 1;
-            for (int i = 0; i < 3; ++i) kf.p[i] += kf.lo[i];
-            for (int i = 0; i < 5; ++i) out[i] = kf.p[i];
-            for (int i = 0; i < 15; ++i) out[5 + i] = kf.C[i];
-        }
-        if (fit_slot(hit, rmin, rmax, false, yb, zb, sector, geo, P, kf, &st[ST_FP64])) {
-            ok |= 2;
-            for (int i = 0; i < 3; ++i) kf.p[i] += kf.lo[i];
-            for (int i = 0; i < 5; ++i) out[20 + i] = kf.p[i];
-            for (int i = 0; i < 15; ++i) out[25 + i] = kf.C[i];
-        }
-        tl_ok[s] = ok;
         atomicAdd(&st[ST_NTL], 1);
         atomicAdd(&grp_tl_cnt[g], 1);
     }
@@ -806,6 +904,7 @@ cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hi
     c->mark(0, s);
     // per-call counters (the status word and the FP64 count are cumulative)
     TPC_TRY(fill_i32(st + ST_NSEG, ST_NTRACKS - ST_NSEG + 1, 0, s));
+    TPC_TRY(fill_i32(st + ST_Q_BUILD, ST_NHARD - ST_Q_BUILD + 1, 0, s));
     // S1: z range per group, cells, histogram, scan, scatter
     tpc::LaunchCount{}, k_fill_u32<<<grid_for(G), TPB, 0, s>>>(W.at<uint32_t>(L.g_zmin_u), G, 0xffffffffu);
     tpc::LaunchCount{}, k_fill_u32<<<grid_for(G), TPB, 0, s>>>(W.at<uint32_t>(L.g_zmax_u), G, 0u);
@@ -837,7 +936,11 @@ cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hi
     int32_t* cup = W.at<int32_t>(L.choice_up);
     float* d2 = W.at<float>(L.d2);
     NbPrm nb{p.win_y, p.win_z, p.chi2_link, p.sigma_y2, p.sigma_z2, p.max_gap};
-    tpc::LaunchCount{}, k_neighbours<<<grid_for(n), TPB, 0, s>>>(n, yb, zb, orig, grpb, rowb, cells, geo, nb, cdn, cup, d2);
+    tpc::LaunchCount{}, k_neighbours<<<grid_for(n), TPB, 0, s>>>(1, n, yb, zb, orig, grpb, rowb, cells, geo, nb,
+                                                               cdn, cup, d2, W.at<int32_t>(L.hard), st);
+    tpc::LaunchCount{}, k_neighbours<<<grid_for(n / 4 + 1), TPB, 0, s>>>(2, n, yb, zb, orig, grpb, rowb, cells,
+                                                                       geo, nb, cdn, cup, d2,
+                                                                       W.at<int32_t>(L.hard), st);
     c->mark(2, s);
     auto* claim_up = W.at<unsigned long long>(L.claim_up);
     auto* claim_dn = W.at<unsigned long long>(L.claim_dn);
@@ -865,6 +968,7 @@ cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hi
     tp.snp_max = p.snp_max;
     tp.fp64_ratio = p.fp64_ratio;
     tp.fp64_det = p.fp64_det;
+    tp.pitch = (float)(162.0 / 151.0);
     tp.ext_max_miss = p.ext_max_miss;
     tp.n_seg = p.n_seg;
     tp.bz = p.bz;
@@ -872,22 +976,31 @@ cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hi
     tp.seed_qpt = p.seed_qpt_max;
     for (int i = 0; i < 5; ++i) tp.prior[i] = p.prior[i];
     const unsigned sgrid = grid_for(L.S, 128);
+    // persistent lanes: enough resident warps to fill the GPU
+    const unsigned lgrid = 152u * (unsigned)c->tune.lane_blocks_per_sm;
+    const int tile = c->tune.lane_tile;
     int32_t* tl_rowhit = W.at<int32_t>(L.tl_rowhit);
     auto* tl_key = W.at<unsigned long long>(L.tl_key);
-    tpc::LaunchCount{}, k_tracklets<<<sgrid, 128, 0, s>>>(W.at<int32_t>(L.seg_start), W.at<int32_t>(L.seg_grp),
-                                      W.at<int32_t>(L.seg_canon), lup, yb, zb, orig, rowb, cells, geo,
-                                      tp, L.S, st, tl_rowhit, W.at<int32_t>(L.tl_n), tl_key);
+    tpc::LaunchCount{}, k_tracklet_lanes<<<lgrid, 128, 0, s>>>(
+        0, W.at<int32_t>(L.seg_start), W.at<int32_t>(L.seg_grp), W.at<int32_t>(L.seg_canon), lup, yb,
+        zb, orig, rowb, cells, geo, tp, L.S, st, tl_rowhit, W.at<int32_t>(L.tl_n), tl_key, nullptr,
+        nullptr, nullptr, nullptr, nullptr, tile);
     c->mark(5, s);
     auto* owner = W.at<unsigned long long>(L.owner);
     tpc::LaunchCount{}, k_fill_u64<<<grid_for(n), TPB, 0, s>>>(owner, n, KEY_MAX);
     tpc::LaunchCount{}, k_owner<<<grid_for(L.S * NROW), TPB, 0, s>>>(tl_rowhit, tl_key, L.S, st, owner);
     int32_t* grp_cnt = W.at<int32_t>(L.grp_tl_cnt);
     TPC_TRY(fill_i32(grp_cnt, G + 1, 0, s));
-    tpc::LaunchCount{}, k_keep<<<sgrid, 128, 0, s>>>(tl_rowhit, tl_key, owner, W.at<int32_t>(L.seg_grp), yb, zb, orig, geo,
-                                 tp, L.S, st, W.at<int32_t>(L.tl_keep), W.at<int32_t>(L.tl_canon),
-                                 W.at<int32_t>(L.tl_rmin), W.at<int32_t>(L.tl_rmax),
-                                 W.at<float>(L.tl_zin), W.at<float>(L.tl_zout),
-                                 W.at<float>(L.tl_state), W.at<int32_t>(L.tl_ok), grp_cnt);
+    tpc::LaunchCount{}, k_keep<<<sgrid, 128, 0, s>>>(tl_rowhit, tl_key, owner, W.at<int32_t>(L.seg_grp), zb,
+                                 orig, p.n_seg, L.S, st, W.at<int32_t>(L.tl_keep),
+                                 W.at<int32_t>(L.tl_canon), W.at<int32_t>(L.tl_rmin),
+                                 W.at<int32_t>(L.tl_rmax), W.at<float>(L.tl_zin),
+                                 W.at<float>(L.tl_zout), W.at<int32_t>(L.tl_ok), grp_cnt);
+    tpc::LaunchCount{}, k_tracklet_lanes<<<lgrid, 128, 0, s>>>(
+        1, W.at<int32_t>(L.seg_start), W.at<int32_t>(L.seg_grp), W.at<int32_t>(L.seg_canon), lup, yb,
+        zb, orig, rowb, cells, geo, tp, L.S, st, tl_rowhit, W.at<int32_t>(L.tl_n), tl_key,
+        W.at<int32_t>(L.tl_keep), W.at<int32_t>(L.tl_rmin), W.at<int32_t>(L.tl_rmax),
+        W.at<float>(L.tl_state), W.at<int32_t>(L.tl_ok), tile);
     TPC_TRY(scan_i32(grp_cnt, W.at<int32_t>(L.grp_tl_off), G, scan_tmp, s));
     TPC_TRY(fill_i32(W.at<int32_t>(L.grp_tl_cur), G, 0, s));
     tpc::LaunchCount{}, k_tl_scatter<<<sgrid, 128, 0, s>>>(W.at<int32_t>(L.tl_keep), W.at<int32_t>(L.seg_grp),

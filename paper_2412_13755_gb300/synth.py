@@ -174,12 +174,19 @@ def _crossings(phi0, k, tgl, wedge, misalign, want_truth):
         zl = tgl[t_idx][:, None] * s
         snp = np.sin(psi - a[:, None])
         sector = (iphi[t_idx] % N_PHI + side[t_idx])[:, None] + np.zeros_like(s, dtype=np.int64)
-        xl = np.broadcast_to(xr, s.shape).copy()
         if misalign is not None:
-            # measured point on the misaligned plane: x of R^T (P - D) = x_r
-            yl, zl, xl, s = _misaligned_crossing(phi0[t_idx], kk, tgl[t_idx], a,
-                                                 cx[t_idx], cy[t_idx], s,
-                                                 sector, misalign)
+            # measured point on the misaligned plane: x of R^T (P - D) = x_r,
+            # solved only where the nominal crossing exists
+            ti0, ri0 = np.nonzero(ok)
+            ym, zm, sm = _misaligned_crossing(phi0[t_idx][ti0], kk[ti0, 0], tgl[t_idx][ti0],
+                                              a[ti0], cx[t_idx][ti0], cy[t_idx][ti0],
+                                              s[ti0, ri0], sector[ti0, ri0], ROW_X[ri0], misalign)
+            yl = np.zeros_like(s)
+            zl = np.zeros_like(s)
+            yl[ti0, ri0] = ym
+            zl[ti0, ri0] = zm
+            s = s.copy()
+            s[ti0, ri0] = sm
         ok &= np.abs(yl) <= xr * TAN_HALF_SECTOR
         ok &= np.abs(zl) < Z_MAX
         ti, ri = np.nonzero(ok)
@@ -191,36 +198,35 @@ def _crossings(phi0, k, tgl, wedge, misalign, want_truth):
     return tuple(np.concatenate([o[j] for o in out]) for j in range(7))
 
 
-def _misaligned_crossing(phi0, kk, tgl, a, cx, cy, s, sector, misalign):
-    """Newton solve for the arc length where the helix meets the misaligned
-    row plane {R (x_r, y, z) + D}; returns measured (y, z) in that plane."""
-    ca, sa = np.cos(a)[:, None], np.sin(a)[:, None]
-    xr = ROW_X[None, :]
-    P = misalign.reshape(N_SECTORS, 6)[sector]          # [t, r, 6]
-    R = np.zeros(sector.shape + (3, 3))
-    for sec in np.unique(sector):
-        m = sector == sec
-        R[m] = rotation_matrix(*misalign.reshape(N_SECTORS, 6)[sec, 3:6])
-    D = P[..., 0:3]
+def _misaligned_crossing(phi0, k, tgl, a, cx, cy, s, sector, xr, misalign):
+    """Newton solve (1-d arrays, one entry per crossing) for the arc length
+    where the helix meets the misaligned row plane {R (x_r, y, z) + D};
+    returns the measured (y, z) in that plane and the arc length."""
+    ca, sa = np.cos(a), np.sin(a)
+    par = misalign.reshape(N_SECTORS, 6)
+    Rs = np.stack([rotation_matrix(*par[i, 3:6]) for i in range(N_SECTORS)])
+    R = Rs[sector]                       # [m, 3, 3]
+    D = par[sector, 0:3]
     s = s.copy()
-    for _ in range(6):
-        psi = phi0[:, None] - kk * s
-        px = cx[:, None] + (-np.sin(psi)) / kk
-        py = cy[:, None] + np.cos(psi) / kk
-        loc = np.stack([ca * px + sa * py, -sa * px + ca * py,
-                        tgl[:, None] * s], -1) - D
-        meas = np.einsum('...ji,...j->...i', R, loc)       # R^T (P - D)
-        dloc = np.stack([np.cos(psi - a[:, None]), np.sin(psi - a[:, None]),
-                         np.broadcast_to(tgl[:, None], s.shape)], -1)
-        dmeas = np.einsum('...ji,...j->...i', R, dloc)
-        s = s - (meas[..., 0] - xr) / dmeas[..., 0]
-    psi = phi0[:, None] - kk * s
-    px = cx[:, None] + (-np.sin(psi)) / kk
-    py = cy[:, None] + np.cos(psi) / kk
-    loc = np.stack([ca * px + sa * py, -sa * px + ca * py,
-                    tgl[:, None] * s], -1) - D
-    meas = np.einsum('...ji,...j->...i', R, loc)
-    return meas[..., 1], meas[..., 2], meas[..., 0], s
+
+    def rt(v0, v1, v2):  # R^T v, component-wise
+        return (R[:, 0, 0] * v0 + R[:, 1, 0] * v1 + R[:, 2, 0] * v2,
+                R[:, 0, 1] * v0 + R[:, 1, 1] * v1 + R[:, 2, 1] * v2,
+                R[:, 0, 2] * v0 + R[:, 1, 2] * v1 + R[:, 2, 2] * v2)
+
+    def measured(s):
+        psi = phi0 - k * s
+        px = cx + (-np.sin(psi)) / k
+        py = cy + np.cos(psi) / k
+        m = rt(ca * px + sa * py - D[:, 0], -sa * px + ca * py - D[:, 1], tgl * s - D[:, 2])
+        return np.stack(m, -1), psi
+
+    for _ in range(4):
+        meas, psi = measured(s)
+        d0 = rt(np.cos(psi - a), np.sin(psi - a), tgl)[0]
+        s = s - (meas[:, 0] - xr) / d0
+    meas, _ = measured(s)
+    return meas[:, 1], meas[:, 2], s
 
 
 def _draw_tracks(rng, n, pt_min, pt_slope, wedge):
@@ -313,8 +319,18 @@ def generate(events, seed, wedge=None, pt_min=0.2, pt_slope=0.5,
     cat = {key: np.concatenate([c[key] for c in cls]) for key in cls[0]}
     E = len(specs)
     key = cat['event'] * N_SECTORS + cat['sector']
-    perm = rng.permutation(key.shape[0])
-    order = perm[np.argsort(key[perm], kind='stable')]
+    if E == 1:
+        perm = rng.permutation(key.shape[0])
+        order = perm[np.argsort(key[perm], kind='stable')]
+    else:
+        # events are contiguous in generation order: group and shuffle each
+        bounds = np.searchsorted(cat['event'], np.arange(E + 1))
+        parts = []
+        for e in range(E):
+            b0, b1 = bounds[e], bounds[e + 1]
+            perm = rng.permutation(b1 - b0)
+            parts.append(b0 + perm[np.argsort(cat['sector'][b0:b1][perm], kind='stable')])
+        order = np.concatenate(parts)
     counts = np.bincount(key, minlength=E * N_SECTORS)
     off = np.zeros(E * N_SECTORS + 1, np.int64)
     off[1:] = np.cumsum(counts)
@@ -337,6 +353,90 @@ def generate(events, seed, wedge=None, pt_min=0.2, pt_slope=0.5,
     if misalign is not None:
         ev.align = np.asarray(misalign, np.float64).copy()
     return ev
+
+
+# --- parallel generation ---------------------------------------------------------
+
+def _unit(args):
+    """One independently seeded generation unit (an event, or a chunk of the
+    tracks of one event) for generate_parallel."""
+    seed, n_tracks, noise, wedge, pt_min, pt_slope, misalign = args
+    rng = np.random.default_rng(seed)
+    cl, trk = _one_collision(rng, n_tracks, noise, wedge, pt_min, pt_slope, misalign, False, 0.0, 0)
+    keep = ("sector", "row", "y", "z", "charge", "mc", "arc_true")
+    cl = {k: cl[k] for k in keep}
+    cl["y"] = cl["y"].astype(np.float32)
+    cl["z"] = cl["z"].astype(np.float32)
+    return cl, trk
+
+
+def generate_parallel(units, seed, workers=None, wedge=None, pt_min=0.2, pt_slope=0.5,
+                      misalign=None):
+    """Like generate() for many units, in a spawn-context process pool.
+
+    units: list of (event index, n_tracks, noise_frac); units of one event
+    are merged into that event.  Unit u draws from PCG64 seeded with
+    (seed, u), so the result does not depend on the number of workers (it
+    differs from generate() with the same seed)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    import os
+    if workers is None:
+        workers = max(1, len(os.sched_getaffinity(0)))
+    jobs = [((seed, u), nt, nf, wedge, pt_min, pt_slope, misalign)
+            for u, (_, nt, nf) in enumerate(units)]
+    with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        res = list(ex.map(_unit, jobs, chunksize=max(1, len(jobs) // (4 * workers))))
+    E = max(u[0] for u in units) + 1
+    tid0 = 0
+    cls, trks = [], []
+    for (ev, nt, _), (cl, trk) in zip(units, res):
+        cl["mc"] = np.where(cl["mc"] >= 0, cl["mc"] + tid0, -1).astype(np.int32)
+        cl["event"] = np.full(cl["row"].shape[0], ev, np.int64)
+        trk["event"] = np.full(nt, ev, np.int32)
+        trk["t0"] = np.zeros(nt)
+        tid0 += nt
+        cls.append(cl)
+        trks.append(trk)
+    cat = {key: np.concatenate([c[key] for c in cls]) for key in cls[0]}
+    key = cat["event"] * N_SECTORS + cat["sector"]
+    rng = np.random.default_rng((seed, len(units)))
+    order = np.argsort(key * (1 << 31) + rng.integers(0, 1 << 31, key.shape[0]), kind="stable")
+    counts = np.bincount(key, minlength=E * N_SECTORS)
+    off = np.zeros(E * N_SECTORS + 1, np.int64)
+    off[1:] = np.cumsum(counts)
+    trk = {k: np.concatenate([t[k] for t in trks]) for k in trks[0]}
+    ev = Events(y=cat["y"][order], z=cat["z"][order], row=cat["row"][order],
+                charge=cat["charge"][order], evt_sector_off=off, n_events=E,
+                mc_track=cat["mc"][order], trk_q=trk["q"], trk_pt=trk["pt"], trk_tgl=trk["tgl"],
+                trk_phi0=trk["phi0"], trk_event=trk["event"], trk_t0=trk["t0"])
+    ev.arc_true = cat["arc_true"][order]
+    if misalign is not None:
+        ev.align = np.asarray(misalign, np.float64).copy()
+    return ev
+
+
+def uneven_batch_parallel(n_events=512, lo=10, hi=10000, seed=SEED_BASE + 3, workers=None):
+    """The uneven 512-event batch, generated in parallel (one unit per event)."""
+    rng = np.random.default_rng(seed + 1000003)
+    nt = np.exp(rng.uniform(math.log(lo), math.log(hi), n_events)).round().astype(int)
+    nf = rng.uniform(0.05, 0.30, n_events)
+    return generate_parallel([(e, int(nt[e]), float(nf[e])) for e in range(n_events)], seed,
+                             workers=workers)
+
+
+def alignment_sample_parallel(n_tracks=200000, seed=SEED_BASE + 4, misalign=None, chunk=5000,
+                              workers=None):
+    """The alignment sample (one event) generated in parallel track chunks."""
+    if misalign is None:
+        misalign = draw_misalignment(seed)
+    units = []
+    left = n_tracks
+    while left > 0:
+        units.append((0, min(chunk, left), 0.0))
+        left -= chunk
+    return generate_parallel(units, seed, workers=workers, pt_min=1.0, pt_slope=0.5,
+                             misalign=misalign)
 
 
 # --- the five workload shapes -------------------------------------------------

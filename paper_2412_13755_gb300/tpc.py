@@ -22,7 +22,8 @@ STATUS_NAMES = {0: "TPC_OK", 1: "TPC_ERR_ARG", 2: "TPC_ERR_CUDA", 3: "TPC_ERR_CA
 EXPORTS = ("tpc_default_params", "tpc_create", "tpc_destroy", "tpc_workspace_bytes",
            "tpc_set_workspace", "tpc_load_clusters", "tpc_find_tracks", "tpc_fit_tracks",
            "tpc_fit_adjoint", "tpc_get_stats", "tpc_last_error", "tpc_reset_status",
-           "tpc_stage_timing", "tpc_stage_times", "tpc_find_tracks_noalloc")
+           "tpc_stage_timing", "tpc_stage_times", "tpc_find_tracks_noalloc", "tpc_set_tune",
+           "tpc_autotune")
 STAGE_NAMES = ("bin", "neighbours", "links", "chains", "tracklets", "select", "merge_cand",
                "match", "output", "fit", "adjoint", "find_total")
 
@@ -37,8 +38,12 @@ class Params(C.Structure):
         ("chi2_merge", C.c_float), ("chi2_ext", C.c_float), ("ext_max_miss", C.c_int32),
         ("bz", C.c_float), ("prior", C.c_float * 5), ("seed_snp_max", C.c_float),
         ("seed_qpt_max", C.c_float), ("snp_max", C.c_float),
-        ("fp64_ratio", C.c_float), ("fp64_det", C.c_float),
+        ("fp64_ratio", C.c_float), ("fp64_det", C.c_float), ("fp64_weak_qpt", C.c_float),
     ]
+
+
+class Tune(C.Structure):
+    _fields_ = [("lane_blocks_per_sm", C.c_int32), ("lane_tile", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -84,6 +89,8 @@ def load_library(build_if_missing: bool = True):
     lib.tpc_last_error.argtypes = [vp, C.c_char_p, sz]
     lib.tpc_reset_status.argtypes = [vp, vp]
     lib.tpc_stage_timing.argtypes = [vp, C.c_int]
+    lib.tpc_set_tune.argtypes = [vp, vp]
+    lib.tpc_autotune.argtypes = [vp, vp, vp, vp, vp, i32, vp, vp]
     lib.tpc_stage_times.argtypes = [vp, vp]
     for name in EXPORTS:
         f = getattr(lib, name)
@@ -205,6 +212,20 @@ def tpc_fit_adjoint(ctx, trk_off, trk_hits, n_tracks, align, chi2_total, grad=No
     _check(ctx, rc, "tpc_fit_adjoint")
 
 
+def tpc_set_tune(ctx, tune: Tune | None):
+    _check(ctx, load_library().tpc_set_tune(ctx, C.byref(tune) if tune is not None else None),
+           "tpc_set_tune")
+
+
+def tpc_autotune(ctx, track_of_cluster, trk_off, trk_hits, n_tracks_dev, stream=None) -> Tune:
+    best = Tune()
+    rc = load_library().tpc_autotune(ctx, _ptr(track_of_cluster), _ptr(trk_off), _ptr(trk_hits),
+                                     _ptr(n_tracks_dev), trk_off.numel() - 1, C.byref(best),
+                                     _stream(stream))
+    _check(ctx, rc, "tpc_autotune")
+    return best
+
+
 def tpc_get_stats(ctx, stream=None) -> Stats:
     st = Stats()
     load_library().tpc_get_stats(ctx, C.byref(st), _stream(stream))
@@ -302,6 +323,13 @@ class Tracker:
 
     def reset_status(self, stream=None):
         tpc_reset_status(self.ctx, stream)
+
+    def autotune(self, out=None, stream=None) -> Tune:
+        out = out or self.alloc_find_outputs()
+        return tpc_autotune(self.ctx, *out, stream=stream)
+
+    def set_tune(self, tune: Tune | None):
+        tpc_set_tune(self.ctx, tune)
 
     def stage_timing(self, enable: bool = True):
         tpc_stage_timing(self.ctx, enable)
