@@ -196,88 +196,176 @@ __device__ __forceinline__ void cell_range(const Cells& cells, int g, int r, flo
     e = cells.off[base + zcell(cells, g, zhi) + 1];
 }
 
-// For each cluster: the (down, up) pair in rows r-gd, r+gu minimising D^2
-// with D^2 <= chi2_link, over gap pairs in order of increasing gd+gu, then
-// gu; ties by the canonical id of u, then of d.  Run in two passes with the
-// same result: pass 1 tries gd+gu = 2 for every cluster and queues the
-// clusters without a pair; pass 2 continues those from gd+gu = 3, so the
-// lanes of a warp do similar amounts of work.
-__global__ void __launch_bounds__(TPB) k_neighbours(
-    int pass, int64_t n, const float* __restrict__ yb, const float* __restrict__ zb,
+// Serial evaluation of one gap pair (gd, gu) for cluster c; the reference
+// used by the warp kernel when a candidate list overflows.
+__device__ void pair_scan_serial(int64_t c, int gd, int gu, const float* __restrict__ yb,
+                                 const float* __restrict__ zb, const int32_t* __restrict__ orig,
+                                 int g, int r, float xc, float yc, float zc, const Cells& cells,
+                                 const Geo* __restrict__ geo, const NbPrm& P, int& bd, int& bu,
+                                 float& bd2) {
+    const int rd = r - gd, ru = r + gu;
+    const float xd = geo->row_xf[rd], xu = geo->row_xf[ru];
+    const float wzd = __fmul_rn(P.win_z, fabsf(__fsub_rn(xd, xc)));
+    const float wzu = __fmul_rn(P.win_z, fabsf(__fsub_rn(xu, xc)));
+    int db, de, ub, ue;
+    cell_range(cells, g, rd, zc - wzd * 1.0001f - 1e-3f, zc + wzd * 1.0001f + 1e-3f, db, de);
+    cell_range(cells, g, ru, zc - wzu * 1.0001f - 1e-3f, zc + wzu * 1.0001f + 1e-3f, ub, ue);
+    int pd = -1, pu = -1, pod = 0, pou = 0;
+    float pd2 = 0.f;
+    for (int d = db; d < de; ++d) {
+        const float ydd = yb[d], zdd = zb[d];
+        if (!in_win(xc, yc, zc, xd, ydd, zdd, P.win_y, P.win_z)) continue;
+        for (int u = ub; u < ue; ++u) {
+            const float yuu = yb[u], zuu = zb[u];
+            if (!in_win(xc, yc, zc, xu, yuu, zuu, P.win_y, P.win_z)) continue;
+            const float d2 = triplet_d2(xd, ydd, zdd, xc, yc, zc, xu, yuu, zuu, P.sy2, P.sz2);
+            if (!(d2 <= P.chi2_link)) continue;
+            bool better = pd < 0 || d2 < pd2;
+            if (!better && d2 == pd2) {
+                const int ou = orig[u], od = orig[d];
+                better = ou < pou || (ou == pou && od < pod);
+            }
+            if (better) {
+                pd = d; pu = u; pd2 = d2; pod = orig[d]; pou = orig[u];
+            }
+        }
+    }
+    bd = pd;
+    bu = pu;
+    bd2 = pd2;
+}
+
+constexpr int NB_LIST = 64;     // candidates kept per row and cluster
+constexpr int NB_WARPS = 8;     // warps per block
+struct NbLists {
+    float y[6][NB_LIST];
+    float z[6][NB_LIST];
+    int idx[6][NB_LIST];
+    int cnt[6];
+};
+
+// Warp-cooperative neighbour search (same rule and result as the serial
+// search): one warp per cluster; the window candidates of each needed row
+// offset are compacted into shared memory once, then the lanes evaluate the
+// (down, up) pairs of a gap pair in parallel and reduce to the best pair
+// (smallest D^2, then canonical id of u, then of d).
+__global__ void __launch_bounds__(NB_WARPS * 32) k_neighbours_warp(
+    int64_t n, const float* __restrict__ yb, const float* __restrict__ zb,
     const int32_t* __restrict__ orig, const int32_t* __restrict__ grpb,
     const uint8_t* __restrict__ rowb, Cells cells, const Geo* __restrict__ geo, NbPrm P,
-    int32_t* choice_dn, int32_t* choice_up, float* d2out, int32_t* hard, int32_t* st) {
-    const int64_t count = pass == 1 ? n : (int64_t)st[ST_NHARD];
-    const int sum_lo = pass == 1 ? 2 : 3, sum_hi = pass == 1 ? 2 : 2 * P.max_gap;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const int64_t i_end = ((count + stride - 1) / stride) * stride;  // warp-uniform trip count
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < i_end; i += stride) {
-        bool active = i < count;
-        const int64_t c = !active ? 0 : (pass == 1 ? i : (int64_t)hard[i]);
+    int32_t* choice_dn, int32_t* choice_up, float* d2out) {
+    __shared__ NbLists sh_all[NB_WARPS];
+    NbLists& sh = sh_all[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t c = wid; c < n; c += nw) {
+        const int g = grpb[c], r = rowb[c];
+        const float xc = geo->row_xf[r], yc = yb[c], zc = zb[c];
+        unsigned built = 0;  // bit k: list k (k < 3: down rows r-1-k, k >= 3: up rows r+k-2)
         int bd = -1, bu = -1;
         float bd2 = 0.f;
-        if (active) {
-            const int g = grpb[c], r = rowb[c];
-            const float xc = geo->row_xf[r], yc = yb[c], zc = zb[c];
-            for (int sum = sum_lo; sum <= sum_hi && bd < 0; ++sum) {
-                for (int gu = 1; gu <= P.max_gap && bd < 0; ++gu) {
-                    const int gd = sum - gu;
-                    if (gd < 1 || gd > P.max_gap) continue;
-                    const int rd = r - gd, ru = r + gu;
-                    if (rd < 0 || ru >= NROW) continue;
-                    const float xd = geo->row_xf[rd], xu = geo->row_xf[ru];
-                    const float wzd = __fmul_rn(P.win_z, fabsf(__fsub_rn(xd, xc)));
-                    const float wzu = __fmul_rn(P.win_z, fabsf(__fsub_rn(xu, xc)));
-                    // cell ranges: a superset of the exact window
-                    int db, de, ub, ue;
-                    cell_range(cells, g, rd, zc - wzd * 1.0001f - 1e-3f, zc + wzd * 1.0001f + 1e-3f, db, de);
-                    cell_range(cells, g, ru, zc - wzu * 1.0001f - 1e-3f, zc + wzu * 1.0001f + 1e-3f, ub, ue);
-                    int pd = -1, pu = -1;
-                    float pd2 = 0.f;
-                    int pod = 0, pou = 0;
-                    for (int d = db; d < de; ++d) {
-                        const float ydd = yb[d], zdd = zb[d];
-                        if (!in_win(xc, yc, zc, xd, ydd, zdd, P.win_y, P.win_z)) continue;
-                        for (int u = ub; u < ue; ++u) {
-                            const float yuu = yb[u], zuu = zb[u];
-                            if (!in_win(xc, yc, zc, xu, yuu, zuu, P.win_y, P.win_z)) continue;
-                            const float d2 = triplet_d2(xd, ydd, zdd, xc, yc, zc, xu, yuu, zuu, P.sy2, P.sz2);
-                            if (!(d2 <= P.chi2_link)) continue;
-                            bool better = pd < 0 || d2 < pd2;
-                            if (!better && d2 == pd2) {
-                                const int ou = orig[u], od = orig[d];
-                                better = ou < pou || (ou == pou && od < pod);
-                            }
-                            if (better) {
-                                pd = d;
-                                pu = u;
-                                pd2 = d2;
-                                pod = orig[d];
-                                pou = orig[u];
-                            }
+        for (int sum = 2; sum <= 2 * P.max_gap && bd < 0; ++sum) {
+            for (int gu = 1; gu <= P.max_gap && bd < 0; ++gu) {
+                const int gd = sum - gu;
+                if (gd < 1 || gd > P.max_gap) continue;
+                const int rd = r - gd, ru = r + gu;
+                if (rd < 0 || ru >= NROW) continue;
+                const int kd = gd - 1, ku = 2 + gu;
+                // build the two lists if needed
+#pragma unroll
+                for (int side = 0; side < 2; ++side) {
+                    const int k = side == 0 ? kd : ku;
+                    if (built & (1u << k)) continue;
+                    const int rr = side == 0 ? rd : ru;
+                    const float xr = geo->row_xf[rr];
+                    const float wz = __fmul_rn(P.win_z, fabsf(__fsub_rn(xr, xc)));
+                    int b, e;
+                    cell_range(cells, g, rr, zc - wz * 1.0001f - 1e-3f, zc + wz * 1.0001f + 1e-3f, b, e);
+                    int cnt = 0;
+                    for (int base = b; base < e; base += 32) {
+                        const int q = base + lane;
+                        float yq = 0.f, zq = 0.f;
+                        bool pass = false;
+                        if (q < e) {
+                            yq = yb[q];
+                            zq = zb[q];
+                            pass = in_win(xc, yc, zc, xr, yq, zq, P.win_y, P.win_z);
                         }
+                        const unsigned bal = __ballot_sync(0xffffffffu, pass);
+                        const int pos = cnt + __popc(bal & lt);
+                        if (pass && pos < NB_LIST) {
+                            sh.idx[k][pos] = q;
+                            sh.y[k][pos] = yq;
+                            sh.z[k][pos] = zq;
+                        }
+                        cnt += __popc(bal);
                     }
-                    if (pd >= 0) {
-                        bd = pd;
-                        bu = pu;
-                        bd2 = pd2;
+                    if (lane == 0) sh.cnt[k] = cnt;
+                    built |= 1u << k;
+                }
+                __syncwarp();
+                const int nd = sh.cnt[kd], nu = sh.cnt[ku];
+                if (nd == 0 || nu == 0) continue;
+                if (nd > NB_LIST || nu > NB_LIST) {
+                    // overflow: the serial scan of this gap pair
+                    int sd = -1, su = -1;
+                    float s2 = 0.f;
+                    if (lane == 0)
+                        pair_scan_serial(c, gd, gu, yb, zb, orig, g, r, xc, yc, zc, cells, geo, P, sd, su, s2);
+                    bd = __shfl_sync(0xffffffffu, sd, 0);
+                    bu = __shfl_sync(0xffffffffu, su, 0);
+                    bd2 = __shfl_sync(0xffffffffu, s2, 0);
+                    continue;
+                }
+                const float xd = geo->row_xf[rd], xu = geo->row_xf[ru];
+                int pd = -1, pu = -1, pod = 0, pou = 0;
+                float pd2 = 0.f;
+                const int total = nd * nu;
+                for (int p = lane; p < total; p += 32) {
+                    const int i = p / nu, j = p - i * nu;
+                    const float d2 = triplet_d2(xd, sh.y[kd][i], sh.z[kd][i], xc, yc, zc, xu,
+                                                sh.y[ku][j], sh.z[ku][j], P.sy2, P.sz2);
+                    if (!(d2 <= P.chi2_link)) continue;
+                    const int d = sh.idx[kd][i], u = sh.idx[ku][j];
+                    bool better = pd < 0 || d2 < pd2;
+                    if (!better && d2 == pd2) {
+                        const int ou = orig[u], od = orig[d];
+                        better = ou < pou || (ou == pou && od < pod);
+                    }
+                    if (better) {
+                        pd = d; pu = u; pd2 = d2; pod = orig[d]; pou = orig[u];
                     }
                 }
+                // warp argmin of (D^2, canonical u, canonical d)
+#pragma unroll
+                for (int o = 16; o >= 1; o >>= 1) {
+                    const int od_ = __shfl_xor_sync(0xffffffffu, pd, o);
+                    const int ou_ = __shfl_xor_sync(0xffffffffu, pu, o);
+                    const float o2 = __shfl_xor_sync(0xffffffffu, pd2, o);
+                    const int ood = __shfl_xor_sync(0xffffffffu, pod, o);
+                    const int oou = __shfl_xor_sync(0xffffffffu, pou, o);
+                    bool take = od_ >= 0 && (pd < 0 || o2 < pd2 ||
+                                             (o2 == pd2 && (oou < pou || (oou == pou && ood < pod))));
+                    if (take) {
+                        pd = od_; pu = ou_; pd2 = o2; pod = ood; pou = oou;
+                    }
+                }
+                if (pd >= 0) {
+                    bd = pd;
+                    bu = pu;
+                    bd2 = pd2;
+                }
+                __syncwarp();
             }
+        }
+        if (lane == 0) {
             choice_dn[c] = bd;
             choice_up[c] = bu;
             d2out[c] = bd2;
         }
-        if (pass == 1) {
-            // queue the clusters without a pair (warp-aggregated)
-            const bool q = active && bd < 0;
-            const unsigned bal = __ballot_sync(0xffffffffu, q);
-            int base = 0;
-            const int lane = threadIdx.x & 31;
-            if (lane == 0 && bal) base = atomicAdd(&st[ST_NHARD], __popc(bal));
-            base = __shfl_sync(0xffffffffu, base, 0);
-            if (q) hard[base + __popc(bal & ((1u << lane) - 1u))] = (int32_t)c;
-        }
+        __syncwarp();
     }
 }
 
@@ -724,6 +812,20 @@ __global__ void __launch_bounds__(256) k_merge_cand(
                         s.lo[0] = s.lo[1] = s.lo[2] = 0.f;
                         for (int i = 0; i < 15; ++i) s.C[i] = sta[25 + i];
                         pass = kf_move<float>(s, geo->row_xd[rb], sb, geo, P.kbf, P.snp_maxf);
+                        // each component's 1-d chi2 is a lower bound of the
+                        // 5-d chi2: reject in FP32 (1% margin) before the
+                        // FP64 solve
+                        if (pass) {
+                            const float lim = (float)P.chi2_merge * 1.01f;
+                            const int di[4] = {0, 1, 2, 3};
+                            const int ci[4] = {0, 5, 9, 12};
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) {
+                                const float d = stb[di[k]] - (s.p[di[k]] + (di[k] < 3 ? s.lo[di[k]] : 0.f));
+                                const float v = s.C[ci[k]] + stb[5 + ci[k]];
+                                pass = pass && d * d <= lim * v;
+                            }
+                        }
                         if (pass) {
                             double d[5], M[15];
                             for (int i = 0; i < 3; ++i) d[i] = (double)stb[i] - ((double)s.p[i] + (double)s.lo[i]);
@@ -904,7 +1006,7 @@ cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hi
     c->mark(0, s);
     // per-call counters (the status word and the FP64 count are cumulative)
     TPC_TRY(fill_i32(st + ST_NSEG, ST_NTRACKS - ST_NSEG + 1, 0, s));
-    TPC_TRY(fill_i32(st + ST_Q_BUILD, ST_NHARD - ST_Q_BUILD + 1, 0, s));
+    TPC_TRY(fill_i32(st + ST_Q_BUILD, ST_KFSTEPS - ST_Q_BUILD + 1, 0, s));
     // S1: z range per group, cells, histogram, scan, scatter
     tpc::LaunchCount{}, k_fill_u32<<<grid_for(G), TPB, 0, s>>>(W.at<uint32_t>(L.g_zmin_u), G, 0xffffffffu);
     tpc::LaunchCount{}, k_fill_u32<<<grid_for(G), TPB, 0, s>>>(W.at<uint32_t>(L.g_zmax_u), G, 0u);
@@ -936,11 +1038,8 @@ cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hi
     int32_t* cup = W.at<int32_t>(L.choice_up);
     float* d2 = W.at<float>(L.d2);
     NbPrm nb{p.win_y, p.win_z, p.chi2_link, p.sigma_y2, p.sigma_z2, p.max_gap};
-    tpc::LaunchCount{}, k_neighbours<<<grid_for(n), TPB, 0, s>>>(1, n, yb, zb, orig, grpb, rowb, cells, geo, nb,
-                                                               cdn, cup, d2, W.at<int32_t>(L.hard), st);
-    tpc::LaunchCount{}, k_neighbours<<<grid_for(n / 4 + 1), TPB, 0, s>>>(2, n, yb, zb, orig, grpb, rowb, cells,
-                                                                       geo, nb, cdn, cup, d2,
-                                                                       W.at<int32_t>(L.hard), st);
+    tpc::LaunchCount{}, k_neighbours_warp<<<152 * 8, NB_WARPS * 32, 0, s>>>(n, yb, zb, orig, grpb, rowb, cells,
+                                                                        geo, nb, cdn, cup, d2);
     c->mark(2, s);
     auto* claim_up = W.at<unsigned long long>(L.claim_up);
     auto* claim_dn = W.at<unsigned long long>(L.claim_dn);
