@@ -95,6 +95,8 @@ typedef struct {
     int32_t status_detail;
     int64_t n_launches;       /* kernels this library has launched in this
                                  process (host-side count, all contexts)    */
+    int64_t n_kf_steps;       /* Kalman steps of the tracklet kernel in the
+                                 last tpc_find_tracks (build + refit)       */
 } tpc_stats;
 
 /* Fills p with the library's default parameters. */

@@ -21,7 +21,9 @@ Layout make_layout(int64_t N, int32_t E) {
     L.K = (int64_t)NROW * L.G + N / CELL_OCC + 16;
     L.S = N / 16 + 4096;
     L.T = N + 1;
-    const int64_t scan_items = std::max<int64_t>(std::max<int64_t>(N + 1, L.K + 1), L.G + 1);
+    L.KT = L.G + N / 64 + 16;
+    const int64_t scan_items =
+        std::max<int64_t>(std::max<int64_t>(N + 1, L.K + 1), std::max<int64_t>(L.G + 1, L.KT + 1));
     L.scan_tmp = scan_items / 4096 + 64;
     L.adj_tracks = 0;
     size_t o = 0;
@@ -72,9 +74,15 @@ Layout make_layout(int64_t N, int32_t E) {
     L.tl_zout = take(s4);
     L.tl_state = take(s4 * 40);
     L.tl_ok = take(s4);
-    L.grp_tl_cnt = take(g4);
-    L.grp_tl_off = take(g4 + 4);
-    L.grp_tl_cur = take(g4);
+    const size_t kt4 = 4 * (size_t)(L.KT + 1);
+    L.grp_tl_cnt = take(kt4);
+    L.grp_tl_off = take(kt4 + 4);
+    L.grp_tl_cur = take(kt4);
+    L.tl_binkey = take(s4);
+    L.tb_zmin = take(g4);
+    L.tb_inv = take(g4);
+    L.tb_nb = take(g4);
+    L.tb_base = take(g4 + 4);
     L.tl_sorted = take(s4);
     L.gs_meta = take(s4 * 4);
     L.cand_n = take(s4);
@@ -359,6 +367,9 @@ tpc_status tpc_get_stats(tpc_ctx* c, tpc_stats* out, tpc_stream_t stream) {
         out->status = h[ST_STATUS];
         out->status_detail = h[ST_DETAIL];
         out->n_launches = g_launches.load(std::memory_order_relaxed);
+        long long ks;
+        memcpy(&ks, &h[ST_KFSTEPS], sizeof ks);
+        out->n_kf_steps = ks;
     }
     if (h[ST_STATUS] != 0) {
         char buf[160];

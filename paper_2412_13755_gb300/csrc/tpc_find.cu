@@ -38,7 +38,32 @@ struct Cells {  // per-group z-cell description
     const int32_t* nz;
     const int32_t* kbase;
     const int32_t* off;  // cell offsets into the binned arrays
+    int64_t K;           // cell capacity (self-check bound)
+    int64_t n;           // binned clusters (self-check bound)
+    int32_t* st;         // status word for self-check reports
 };
+
+// Self-check: an index outside [0, bound) is reported in the status word
+// (TPC_ERR_STATE, detail = site) and the caller skips the access.
+__device__ __forceinline__ bool in_range(int64_t i, int64_t bound, int32_t* st, int site) {
+    if (i >= 0 && i < bound) return true;
+    set_status(st, TPC_ERR_STATE, site);
+    return false;
+}
+
+struct TlBins {  // per-group z bins of the kept tracklets' outer ends
+    const float* zmin;
+    const float* inv;
+    const int32_t* nb;
+    const int32_t* base;
+};
+
+__device__ __forceinline__ int tl_bin(const TlBins& t, int g, float z) {
+    const int nb = t.nb[g];
+    const float f = (z - t.zmin[g]) * t.inv[g];
+    int k = f >= 0.f ? (int)f : 0;  // monotone in z
+    return k < nb - 1 ? k : nb - 1;
+}
 
 __device__ __forceinline__ int zcell(const Cells& c, int g, float z) {
     const int nz = c.nz[g];
@@ -125,6 +150,63 @@ __global__ void __launch_bounds__(1024) k_cells(const int64_t* __restrict__ off,
     }
 }
 
+// one block: tracklet z bins per group (<= 16 cm wide; at most
+// 1 + n_g/64 bins so that the total is bounded by the cluster count)
+__global__ void __launch_bounds__(1024) k_tl_bins(const int64_t* __restrict__ off, int G,
+                                                  const uint32_t* zmin_u, const uint32_t* zmax_u,
+                                                  float* zmin, float* inv, int32_t* nb,
+                                                  int32_t* base) {
+    __shared__ int32_t sh[32];
+    __shared__ int64_t carry_s;
+    if (threadIdx.x == 0) carry_s = 0;
+    __syncthreads();
+    for (int g0 = 0; g0 < G; g0 += blockDim.x) {
+        const int g = g0 + threadIdx.x;
+        int32_t cnt = 0;
+        if (g < G) {
+            const int64_t ng = off[g + 1] - off[g];
+            float lo = 0.f, hi = 0.f;
+            if (ng > 0) {
+                lo = o2f(zmin_u[g]);
+                hi = o2f(zmax_u[g]);
+            }
+            const float w = hi - lo;
+            int64_t k = (int64_t)ceilf(w / 16.f);
+            const int64_t kmax = 1 + ng / 64;
+            k = k < 1 ? 1 : (k > kmax ? kmax : k);
+            zmin[g] = lo;
+            inv[g] = w > 0.f ? (float)k / w : 0.f;
+            nb[g] = (int32_t)k;
+            cnt = (int32_t)k;
+        }
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        int32_t x = cnt;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) sh[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            int32_t v = sh[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                const int32_t y = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += y;
+            }
+            sh[lane] = v;
+        }
+        __syncthreads();
+        const int64_t b0 = carry_s;
+        const int32_t ex = (wid > 0 ? sh[wid - 1] : 0) + x - cnt;
+        if (g < G) base[g] = (int32_t)(b0 + ex);
+        const int32_t tot = sh[31];
+        __syncthreads();
+        if (threadIdx.x == 0) carry_s = b0 + tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) base[G] = (int32_t)carry_s;
+}
+
 __global__ void k_hist(const float* __restrict__ z, const uint16_t* __restrict__ row, int64_t n,
                        const int64_t* __restrict__ off, int G, Cells cells, int32_t* cnt,
                        int32_t* key_in, int32_t* slot_in, int64_t Kcap) {
@@ -192,8 +274,13 @@ __device__ __forceinline__ float triplet_d2(float xd, float yd, float zd, float 
 __device__ __forceinline__ void cell_range(const Cells& cells, int g, int r, float zlo, float zhi,
                                            int& b, int& e) {
     const int base = cells.kbase[g] + r * cells.nz[g];
-    b = cells.off[base + zcell(cells, g, zlo)];
-    e = cells.off[base + zcell(cells, g, zhi) + 1];
+    const int k0 = base + zcell(cells, g, zlo), k1 = base + zcell(cells, g, zhi) + 1;
+    b = e = 0;
+    if (!in_range(k0, cells.K + 1, cells.st, 101) || !in_range(k1, cells.K + 1, cells.st, 102)) return;
+    b = cells.off[k0];
+    e = cells.off[k1];
+    if (!in_range(b, cells.n + 1, cells.st, 103) || !in_range(e, cells.n + 1, cells.st, 104) || e < b)
+        b = e = 0;
 }
 
 // Serial evaluation of one gap pair (gd, gu) for cluster c; the reference
@@ -650,7 +737,7 @@ __global__ void __launch_bounds__(128, 4) k_tracklet_lanes(
         tl_key[s] = ((unsigned long long)(NROW * 4 - n) << 32) | (uint32_t)seg_canon[s];
         s = -1;
     }
-    atomicAdd(&st[ST_KFSTEPS], steps);
+    if (!refit) atomicAdd(reinterpret_cast<unsigned long long*>(&st[ST_KFSTEPS]), (unsigned long long)steps);
 }
 
 // every cluster belongs to the best tracklet containing it
@@ -671,7 +758,8 @@ __global__ void k_keep(int32_t* tl_rowhit, const unsigned long long* __restrict_
                        const float* __restrict__ zb, const int32_t* __restrict__ orig, int n_seg,
                        int64_t Scap, int32_t* st, int32_t* tl_keep, int32_t* tl_canon,
                        int32_t* tl_rmin, int32_t* tl_rmax, float* tl_zin, float* tl_zout,
-                       int32_t* tl_ok, int32_t* grp_tl_cnt) {
+                       int32_t* tl_ok, int32_t* grp_tl_cnt, TlBins tb, int32_t* tl_binkey,
+                       int64_t KT) {
     const int nseg = min((int64_t)st[ST_NSEG], Scap);
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nseg; s += gridDim.x * blockDim.x) {
         int32_t* hit = tl_rowhit + (int64_t)s * NROW;
@@ -702,8 +790,14 @@ __global__ void k_keep(int32_t* tl_rowhit, const unsigned long long* __restrict_
         tl_rmax[s] = rmax;
         tl_zin[s] = zb[hit[rmin]];
         tl_zout[s] = zb[hit[rmax]];
+        const int bkey = tb.base[g] + tl_bin(tb, g, zb[hit[rmax]]);
+        if (!in_range(bkey, KT, st, 301)) {
+            tl_keep[s] = 0;
+            continue;
+        }
+        tl_binkey[s] = bkey;
         atomicAdd(&st[ST_NTL], 1);
-        atomicAdd(&grp_tl_cnt[g], 1);
+        atomicAdd(&grp_tl_cnt[bkey], 1);
     }
 }
 
@@ -712,12 +806,14 @@ __global__ void k_tl_scatter(const int32_t* __restrict__ tl_keep, const int32_t*
                              int32_t* grp_tl_cur, int32_t* tl_sorted,
                              const int32_t* __restrict__ tl_rmin, const int32_t* __restrict__ tl_rmax,
                              const float* __restrict__ tl_zin, const float* __restrict__ tl_zout,
-                             const int32_t* __restrict__ tl_ok, int4* gs_meta) {
+                             const int32_t* __restrict__ tl_ok, int4* gs_meta,
+                             const int32_t* __restrict__ tl_binkey, int32_t* st_w) {
     const int nseg = min((int64_t)st[ST_NSEG], Scap);
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nseg; s += gridDim.x * blockDim.x) {
         if (!tl_keep[s]) continue;
-        const int g = seg_grp[s];
-        const int q = grp_tl_off[g] + atomicAdd(&grp_tl_cur[g], 1);
+        const int key = tl_binkey[s];
+        const int q = grp_tl_off[key] + atomicAdd(&grp_tl_cur[key], 1);
+        if (!in_range(q, Scap, st_w, 302)) continue;
         tl_sorted[q] = s;
         // packed per-position merge data read coalesced by the candidate search
         gs_meta[q] = make_int4(tl_rmax[s] | (tl_rmin[s] << 8) | (tl_ok[s] << 16),
@@ -730,7 +826,8 @@ struct MgPrm {
     int merge_gap, merge_ov;
     float mz_slope, mz_margin;
     double chi2_merge;
-    float kbf, snp_maxf;
+    float kbf, snp_maxf, pitch;
+    int64_t KT, S;
 };
 
 // 5x5 SPD chi2 = dp^T M^-1 dp by Cholesky (FP64); false if not SPD
@@ -758,6 +855,10 @@ __device__ bool chol_chi2(const double dp[5], const double M[15], double& out) {
     return true;
 }
 
+__device__ __forceinline__ bool ma_ok(const int4* __restrict__ gs_meta, int qa, int b) {
+    return gs_meta[qa].w != b;
+}
+
 // For tracklet B (inner end), candidates A (outer end) in the same or a
 // phi-adjacent sector of the same side and event: A's outward-fit state at
 // its outermost row is moved to B's innermost plane and compared with B's
@@ -767,7 +868,7 @@ __global__ void __launch_bounds__(256) k_merge_cand(
     const int32_t* __restrict__ seg_grp, const float* __restrict__ tl_state,
     const int32_t* __restrict__ grp_tl_off, const int4* __restrict__ gs_meta,
     const Geo* __restrict__ geo, MgPrm P, int32_t* st, int32_t* cand_n, int32_t* cand_a,
-    float* cand_c2) {
+    float* cand_c2, TlBins tb) {
     const int lane = threadIdx.x & 31;
     const int nkept = st[ST_NTL];
     const int warps = (gridDim.x * blockDim.x) >> 5;
@@ -785,16 +886,26 @@ __global__ void __launch_bounds__(256) k_merge_cand(
         for (int dp = -1; dp <= 1; ++dp) {
             const int sa = side * NPHI + (phb + dp + NPHI) % NPHI;
             const int ga = ev * NSEC + sa;
-            const int q0 = grp_tl_off[ga], q1 = grp_tl_off[ga + 1];
+            // the z gate |z_B - z_A| <= slope |dx| + margin with |dx| at
+            // most max(row gap, overlap) pitches bounds the bins to visit
+            const float wmax = P.mz_slope * P.pitch * (float)max(P.merge_gap, P.merge_ov) * 1.001f +
+                               P.mz_margin + 1e-3f;
+            const int k0 = tb.base[ga] + tl_bin(tb, ga, zb_in - wmax);
+            const int k1 = tb.base[ga] + tl_bin(tb, ga, zb_in + wmax);
+            if (!in_range(k0, P.KT + 1, st, 201) || !in_range(k1 + 1, P.KT + 1, st, 202)) continue;
+            int q0 = grp_tl_off[k0], q1 = grp_tl_off[k1 + 1];
+            if (!in_range(q0, nkept + 1, st, 203) || !in_range(q1, nkept + 1, st, 204) || q1 < q0)
+                q0 = q1 = 0;
             const int min_gap = dp == 0 ? 0 : -P.merge_ov;
             for (int qa0 = q0; qa0 < q1; qa0 += 32) {
                 const int qa = qa0 + lane;
                 bool pass = false;
                 float c2f = 0.f;
                 int a = -1;
-                if (qa < q1 && qa != qb) {
+                if (qa < q1 && qa != qb && ma_ok(gs_meta, qa, b)) {
                     const int4 ma = gs_meta[qa];
                     a = ma.w;
+                    if (!in_range(a, P.S, st, 205)) a = b;
                     const int ra = ma.x & 0xff;
                     const int gap = rb - ra;
                     pass = ((ma.x >> 17) & 1) && gap >= min_gap && gap <= P.merge_gap;
@@ -952,7 +1063,7 @@ __global__ void k_track_write(int64_t n, const int32_t* __restrict__ trk_flag,
                               const int32_t* __restrict__ trk_head_at, const int32_t* __restrict__ prv,
                               const int32_t* __restrict__ tl_rowhit, const int32_t* __restrict__ orig,
                               const int32_t* __restrict__ trk_off, int32_t track_cap, int32_t* toc,
-                              int32_t* trk_hits) {
+                              int32_t* trk_hits, int32_t* st_w) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         if (!trk_flag[i]) continue;
@@ -965,6 +1076,10 @@ __global__ void k_track_write(int64_t n, const int32_t* __restrict__ trk_flag,
                 const int h = hit[rr];
                 if (h < 0) continue;
                 const int oi = orig[h];
+                if (o >= n) {
+                    set_status(st_w, TPC_ERR_STATE, 401);
+                    break;
+                }
                 trk_hits[o++] = oi;
                 toc[oi] = r;
             }
@@ -1006,7 +1121,7 @@ cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hi
     c->mark(0, s);
     // per-call counters (the status word and the FP64 count are cumulative)
     TPC_TRY(fill_i32(st + ST_NSEG, ST_NTRACKS - ST_NSEG + 1, 0, s));
-    TPC_TRY(fill_i32(st + ST_Q_BUILD, ST_KFSTEPS - ST_Q_BUILD + 1, 0, s));
+    TPC_TRY(fill_i32(st + ST_Q_BUILD, ST_KFSTEPS + 2 - ST_Q_BUILD, 0, s));
     // S1: z range per group, cells, histogram, scan, scatter
     tpc::LaunchCount{}, k_fill_u32<<<grid_for(G), TPB, 0, s>>>(W.at<uint32_t>(L.g_zmin_u), G, 0xffffffffu);
     tpc::LaunchCount{}, k_fill_u32<<<grid_for(G), TPB, 0, s>>>(W.at<uint32_t>(L.g_zmax_u), G, 0u);
@@ -1016,7 +1131,7 @@ cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hi
                                W.at<uint32_t>(L.g_zmax_u), W.at<float>(L.g_zmin), W.at<float>(L.g_inv),
                                W.at<int32_t>(L.g_nz), W.at<int32_t>(L.g_kbase), L.K, st);
     Cells cells{W.at<float>(L.g_zmin), W.at<float>(L.g_inv), W.at<int32_t>(L.g_nz),
-                W.at<int32_t>(L.g_kbase), W.at<int32_t>(L.cell_off)};
+                W.at<int32_t>(L.g_kbase), W.at<int32_t>(L.cell_off), L.K, n, st};
     TPC_TRY(fill_i32(W.at<int32_t>(L.cell_cnt), L.K + 1, 0, s));
     tpc::LaunchCount{}, k_hist<<<grid_for(n), TPB, 0, s>>>(c->z, c->row, n, c->evt_sector_off, G, cells,
                                        W.at<int32_t>(L.cell_cnt), W.at<int32_t>(L.key_in),
@@ -1089,35 +1204,43 @@ cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hi
     tpc::LaunchCount{}, k_fill_u64<<<grid_for(n), TPB, 0, s>>>(owner, n, KEY_MAX);
     tpc::LaunchCount{}, k_owner<<<grid_for(L.S * NROW), TPB, 0, s>>>(tl_rowhit, tl_key, L.S, st, owner);
     int32_t* grp_cnt = W.at<int32_t>(L.grp_tl_cnt);
-    TPC_TRY(fill_i32(grp_cnt, G + 1, 0, s));
+    TlBins tb{W.at<float>(L.tb_zmin), W.at<float>(L.tb_inv), W.at<int32_t>(L.tb_nb), W.at<int32_t>(L.tb_base)};
+    tpc::LaunchCount{}, k_tl_bins<<<1, 1024, 0, s>>>(c->evt_sector_off, G, W.at<uint32_t>(L.g_zmin_u),
+                                                   W.at<uint32_t>(L.g_zmax_u), W.at<float>(L.tb_zmin),
+                                                   W.at<float>(L.tb_inv), W.at<int32_t>(L.tb_nb),
+                                                   W.at<int32_t>(L.tb_base));
+    TPC_TRY(fill_i32(grp_cnt, L.KT + 1, 0, s));
     tpc::LaunchCount{}, k_keep<<<sgrid, 128, 0, s>>>(tl_rowhit, tl_key, owner, W.at<int32_t>(L.seg_grp), zb,
                                  orig, p.n_seg, L.S, st, W.at<int32_t>(L.tl_keep),
                                  W.at<int32_t>(L.tl_canon), W.at<int32_t>(L.tl_rmin),
                                  W.at<int32_t>(L.tl_rmax), W.at<float>(L.tl_zin),
-                                 W.at<float>(L.tl_zout), W.at<int32_t>(L.tl_ok), grp_cnt);
+                                 W.at<float>(L.tl_zout), W.at<int32_t>(L.tl_ok), grp_cnt, tb,
+                                 W.at<int32_t>(L.tl_binkey), L.KT);
     tpc::LaunchCount{}, k_tracklet_lanes<<<lgrid, 128, 0, s>>>(
         1, W.at<int32_t>(L.seg_start), W.at<int32_t>(L.seg_grp), W.at<int32_t>(L.seg_canon), lup, yb,
         zb, orig, rowb, cells, geo, tp, L.S, st, tl_rowhit, W.at<int32_t>(L.tl_n), tl_key,
         W.at<int32_t>(L.tl_keep), W.at<int32_t>(L.tl_rmin), W.at<int32_t>(L.tl_rmax),
         W.at<float>(L.tl_state), W.at<int32_t>(L.tl_ok), tile);
-    TPC_TRY(scan_i32(grp_cnt, W.at<int32_t>(L.grp_tl_off), G, scan_tmp, s));
-    TPC_TRY(fill_i32(W.at<int32_t>(L.grp_tl_cur), G, 0, s));
+    TPC_TRY(scan_i32(grp_cnt, W.at<int32_t>(L.grp_tl_off), L.KT, scan_tmp, s));
+    TPC_TRY(fill_i32(W.at<int32_t>(L.grp_tl_cur), L.KT, 0, s));
     tpc::LaunchCount{}, k_tl_scatter<<<sgrid, 128, 0, s>>>(W.at<int32_t>(L.tl_keep), W.at<int32_t>(L.seg_grp),
                                        W.at<int32_t>(L.grp_tl_off), L.S, st,
                                        W.at<int32_t>(L.grp_tl_cur), W.at<int32_t>(L.tl_sorted),
                                        W.at<int32_t>(L.tl_rmin), W.at<int32_t>(L.tl_rmax),
                                        W.at<float>(L.tl_zin), W.at<float>(L.tl_zout),
-                                       W.at<int32_t>(L.tl_ok), W.at<int4>(L.gs_meta));
+                                       W.at<int32_t>(L.tl_ok), W.at<int4>(L.gs_meta),
+                                       W.at<int32_t>(L.tl_binkey), st);
     c->mark(6, s);
     // S4: merge candidates and greedy matching
     MgPrm mp{p.merge_max_row_gap, p.merge_max_overlap, p.merge_z_slope, p.merge_z_margin,
-             (double)p.chi2_merge, (float)(KAPPA * (double)p.bz), p.snp_max};
+             (double)p.chi2_merge, (float)(KAPPA * (double)p.bz), p.snp_max, (float)(162.0 / 151.0),
+             L.KT, L.S};
     // cand_n of slots that are not kept must read 0 for the matching
     TPC_TRY(fill_i32(W.at<int32_t>(L.cand_n), L.S, 0, s));
     tpc::LaunchCount{}, k_merge_cand<<<grid_for(L.S * 32, 256), 256, 0, s>>>(
         W.at<int32_t>(L.seg_grp), W.at<float>(L.tl_state), W.at<int32_t>(L.grp_tl_off),
         W.at<int4>(L.gs_meta), geo, mp, st, W.at<int32_t>(L.cand_n), W.at<int32_t>(L.cand_a),
-        W.at<float>(L.cand_c2));
+        W.at<float>(L.cand_c2), tb);
     c->mark(7, s);
     int32_t* nxt = W.at<int32_t>(L.nxt);
     int32_t* prv = W.at<int32_t>(L.prv);
@@ -1145,7 +1268,7 @@ cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hi
     TPC_TRY(scan_i32(len_by_rank, trk_off, track_cap, scan_tmp, s));
     TPC_TRY(fill_i32(toc, n, -1, s));
     tpc::LaunchCount{}, k_track_write<<<grid_for(n), TPB, 0, s>>>(n, flag, rank, W.at<int32_t>(L.trk_head_at), prv,
-                                              tl_rowhit, orig, trk_off, track_cap, toc, trk_hits);
+                                              tl_rowhit, orig, trk_off, track_cap, toc, trk_hits, st);
     c->mark(9, s);
     return cudaGetLastError();
 }

@@ -358,11 +358,11 @@ def generate(events, seed, wedge=None, pt_min=0.2, pt_slope=0.5,
 # --- parallel generation ---------------------------------------------------------
 
 def _unit(args):
-    """One independently seeded generation unit (an event, or a chunk of the
-    tracks of one event) for generate_parallel."""
-    seed, n_tracks, noise, wedge, pt_min, pt_slope, misalign = args
+    """One independently seeded generation unit (an event, a collision of a
+    frame, or a chunk of the tracks of one event) for generate_parallel."""
+    seed, n_tracks, noise, wedge, pt_min, pt_slope, misalign, t0 = args
     rng = np.random.default_rng(seed)
-    cl, trk = _one_collision(rng, n_tracks, noise, wedge, pt_min, pt_slope, misalign, False, 0.0, 0)
+    cl, trk = _one_collision(rng, n_tracks, noise, wedge, pt_min, pt_slope, misalign, False, t0, 0)
     keep = ("sector", "row", "y", "z", "charge", "mc", "arc_true")
     cl = {k: cl[k] for k in keep}
     cl["y"] = cl["y"].astype(np.float32)
@@ -374,8 +374,9 @@ def generate_parallel(units, seed, workers=None, wedge=None, pt_min=0.2, pt_slop
                       misalign=None):
     """Like generate() for many units, in a spawn-context process pool.
 
-    units: list of (event index, n_tracks, noise_frac); units of one event
-    are merged into that event.  Unit u draws from PCG64 seeded with
+    units: list of (event index, n_tracks, noise_frac[, t0_us]); units of
+    one event are merged into that event (t0_us: drift-time offset of a
+    collision in a frame).  Unit u draws from PCG64 seeded with
     (seed, u), so the result does not depend on the number of workers (it
     differs from generate() with the same seed)."""
     import concurrent.futures as cf
@@ -383,18 +384,19 @@ def generate_parallel(units, seed, workers=None, wedge=None, pt_min=0.2, pt_slop
     import os
     if workers is None:
         workers = max(1, len(os.sched_getaffinity(0)))
-    jobs = [((seed, u), nt, nf, wedge, pt_min, pt_slope, misalign)
-            for u, (_, nt, nf) in enumerate(units)]
+    units = [tuple(u) + (0.0,) * (4 - len(u)) for u in units]
+    jobs = [((seed, u), nt, nf, wedge, pt_min, pt_slope, misalign, t0)
+            for u, (_, nt, nf, t0) in enumerate(units)]
     with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
         res = list(ex.map(_unit, jobs, chunksize=max(1, len(jobs) // (4 * workers))))
     E = max(u[0] for u in units) + 1
     tid0 = 0
     cls, trks = [], []
-    for (ev, nt, _), (cl, trk) in zip(units, res):
+    for (ev, nt, _, t0), (cl, trk) in zip(units, res):
         cl["mc"] = np.where(cl["mc"] >= 0, cl["mc"] + tid0, -1).astype(np.int32)
         cl["event"] = np.full(cl["row"].shape[0], ev, np.int64)
         trk["event"] = np.full(nt, ev, np.int32)
-        trk["t0"] = np.zeros(nt)
+        trk["t0"] = np.full(nt, t0)
         tid0 += nt
         cls.append(cl)
         trks.append(trk)
@@ -414,6 +416,15 @@ def generate_parallel(units, seed, workers=None, wedge=None, pt_min=0.2, pt_slop
     if misalign is not None:
         ev.align = np.asarray(misalign, np.float64).copy()
     return ev
+
+
+def pileup_frame_parallel(n_collisions=100, n_tracks=10000, noise=0.20, seed=SEED_BASE + 2,
+                          workers=None):
+    """The 50 kHz frame generated in parallel (one unit per collision)."""
+    rng = np.random.default_rng(seed + 2000003)
+    t0 = rng.uniform(0.0, FRAME_US, n_collisions)
+    return generate_parallel([(0, n_tracks, noise, float(t0[i])) for i in range(n_collisions)],
+                             seed, workers=workers)
 
 
 def uneven_batch_parallel(n_events=512, lo=10, hi=10000, seed=SEED_BASE + 3, workers=None):

@@ -51,7 +51,7 @@ class Stats(C.Structure):
         ("n_clusters", C.c_int64), ("n_segments", C.c_int32), ("n_tracklets", C.c_int32),
         ("n_merge_cand", C.c_int32), ("n_merges", C.c_int32), ("n_tracks", C.c_int32),
         ("n_fp64_updates", C.c_int32), ("status", C.c_int32), ("status_detail", C.c_int32),
-        ("n_launches", C.c_int64),
+        ("n_launches", C.c_int64), ("n_kf_steps", C.c_int64),
     ]
 
 
@@ -292,6 +292,14 @@ class Tracker:
 
     def find(self, out=None, track_cap=None, stream=None):
         out = out or self.alloc_find_outputs(track_cap)
+        toc, trk_off, trk_hits, n_dev = out
+        # the library writes n entries of toc and trk_hits and track_cap+1 of
+        # trk_off: undersized buffers are refused here, before any launch
+        if toc.numel() < self.n or trk_hits.numel() < self.n or trk_off.numel() < 2 \
+                or n_dev.numel() < 1:
+            raise ValueError(f"find outputs too small for {self.n} clusters: "
+                             f"toc {toc.numel()}, trk_off {trk_off.numel()}, "
+                             f"trk_hits {trk_hits.numel()}")
         tpc_find_tracks(self.ctx, *out, stream=stream)
         return out
 

@@ -68,4 +68,4 @@ def test_struct_sizes_match_header(lib):
     from paper_2412_13755_gb300 import tpc
     # 5 floats, 5 int32, 2 floats, 2 floats, int32, float, 5 floats, 6 floats
     assert C.sizeof(tpc.Params) == 108
-    assert C.sizeof(tpc.Stats) == 48
+    assert C.sizeof(tpc.Stats) == 56

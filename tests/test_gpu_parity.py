@@ -46,6 +46,11 @@ def test_find_central_event_full(orc):
     _assign_parity(orc, synth.central_event())
 
 
+def test_find_pileup_frame_small(orc):
+    # 10 collisions at drift-time offsets over the 2 ms frame, one event
+    _assign_parity(orc, synth.pileup_frame(n_collisions=10, n_tracks=1000, seed=404))
+
+
 def test_find_multi_event_batch(orc):
     _assign_parity(orc, synth.uneven_batch(n_events=6, lo=10, hi=800, seed=303))
 
@@ -96,3 +101,18 @@ def test_empty_input():
     torch.cuda.synchronize()
     tr.check()
     assert int(ntd.item()) == 0
+
+
+def test_undersized_outputs_refused():
+    """Buffers smaller than the loaded cluster count are refused on the host,
+    before any kernel could write past them."""
+    ev = synth.one_sector()
+    tr = tpc.Tracker(ev.n, 1)
+    small = tr.alloc_find_outputs(8)  # allocated before load: sized for 0 clusters
+    tr.load(*to_dev(ev), 1)
+    with pytest.raises(ValueError):
+        tr.find(out=small)
+    out = tr.find(out=tr.alloc_find_outputs())
+    torch.cuda.synchronize()
+    tr.check()
+    assert int(out[3].item()) > 0
