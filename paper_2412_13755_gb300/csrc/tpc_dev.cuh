@@ -28,11 +28,17 @@ __device__ __forceinline__ int group_of(const int64_t* __restrict__ off, int G, 
     return lo;
 }
 
-// Packed symmetric 5x5: 00 01 02 03 04 11 12 13 14 22 23 24 33 34 44
-__host__ __device__ constexpr int sx(int i, int j) {
-    return i <= j ? (i == 0 ? j : i == 1 ? 4 + j : i == 2 ? 7 + j : i == 3 ? 9 + j : 14)
-                  : sx(j, i);
+// Packed symmetric 5x5: 00 01 02 03 04 11 12 13 14 22 23 24 33 34 44.
+// Closed form (row a of the upper triangle starts at 5a - a(a-1)/2), not
+// recursive, so that constant indices fold at compile time and the packed
+// arrays stay in registers.
+__host__ __device__ __forceinline__ constexpr int sx(int i, int j) {
+    return (i <= j ? i : j) * 5 - (i <= j ? i : j) * ((i <= j ? i : j) - 1) / 2 + (i <= j ? j : i) -
+           (i <= j ? i : j);
 }
+static_assert(sx(0, 0) == 0 && sx(0, 4) == 4 && sx(1, 1) == 5 && sx(2, 1) == 6 && sx(2, 2) == 9 &&
+                  sx(3, 3) == 12 && sx(4, 3) == 13 && sx(4, 4) == 14,
+              "packed index");
 
 __device__ __forceinline__ float t_sqrt(float v) { return sqrtf(v); }
 __device__ __forceinline__ double t_sqrt(double v) { return sqrt(v); }
@@ -116,16 +122,18 @@ struct MoveJ {
 //   z2 = z1 + t arc sign(dx), arc = chord * asin(u)/u, u = |k| chord / 2.
 // The covariance follows with the analytic Jacobian of the composition.
 // Returns false (state untouched or partially moved) when |sin phi| would
-// reach snp_max.
-template <class R>
+// reach snp_max.  CanRotate = false is the move between row planes of one
+// frame by the caller's step *dx_same_frame (required): no rotation code, no
+// FP64 plane arithmetic, and s.x is left to the caller.
+template <class R, bool CanRotate = true>
 __device__ __forceinline__ bool kf_move(KFT<R>& s, double x_to, int to, const Geo* __restrict__ geo,
                                         R kb, R snp_max, MoveJ* mj = nullptr,
                                         const R* dx_same_frame = nullptr) {
-    double xs = s.x;
+    double xs = CanRotate ? s.x : 0.0;
     R ys = s.p[0], ss = s.p[2];
     R ys_lo = s.lo[0], ss_lo = s.lo[2];
     R ca = R(1), sa = R(0), dsn = R(1);
-    const bool rot = to != s.frame;
+    const bool rot = CanRotate && to != s.frame;
     if (rot) {
         const int k = ((to % NPHI) - (s.frame % NPHI) + NPHI) % NPHI;
         const double cad = geo->da_cos[k], sad = geo->da_sin[k];
@@ -213,8 +221,10 @@ __device__ __forceinline__ bool kf_move(KFT<R>& s, double x_to, int to, const Ge
     add_comp(ss, ss_lo, -k * dx);
     s.p[2] = ss;
     s.lo[2] = ss_lo;
-    s.x = x_to;
-    s.frame = to;
+    if (CanRotate) {
+        s.x = x_to;
+        s.frame = to;
+    }
     return true;
 }
 
@@ -389,6 +399,55 @@ __device__ __forceinline__ void kf_seed(KF& s, const int rows[3], const int secs
     s.p[2] = (float)sn;
     s.p[3] = (float)t;
     s.p[4] = (float)w;
+    s.lo[0] = s.lo[1] = s.lo[2] = 0.f;
+#pragma unroll
+    for (int i = 0; i < 15; ++i) s.C[i] = 0.f;
+    s.C[sx(0, 0)] = prior[0];
+    s.C[sx(1, 1)] = prior[1];
+    s.C[sx(2, 2)] = prior[2];
+    s.C[sx(3, 3)] = prior[3];
+    s.C[sx(4, 4)] = prior[4];
+}
+
+// The same three-point seed in FP32 for clusters of one frame, with x of
+// the planes in FP32: sin phi at the first cluster is expanded as
+// sin(theta -/+ h) = sin theta cos h -/+ cos theta sin h, with
+// sin theta = cy/L, cos theta = cx/L, sin h = hk, cos h = sqrt(1 - hk^2), so
+// only the arc length needs an inverse sine.  The seed only sets the
+// linearisation point and the prior centre of the fit.
+__device__ __forceinline__ void kf_seed_f(KF& s, const int rows[3], int frame, const float ys[3],
+                                          const float zs[3], bool first_is_outer,
+                                          const Geo* __restrict__ geo, float kb_unit,
+                                          float snp_max_seed, float qpt_max, const float prior[5]) {
+    const int i0 = first_is_outer ? 2 : 0, i2 = first_is_outer ? 0 : 2;
+    const float x0 = geo->row_xf[rows[i0]], x1 = geo->row_xf[rows[1]], x2 = geo->row_xf[rows[i2]];
+    const float ax = x1 - x0, ay = ys[1] - ys[i0];
+    const float bx = x2 - x1, by = ys[i2] - ys[1];
+    const float cx = x2 - x0, cy = ys[i2] - ys[i0];
+    const float la = sqrtf(ax * ax + ay * ay), lb = sqrtf(bx * bx + by * by);
+    const float L = sqrtf(cx * cx + cy * cy);
+    const float cross = ax * by - ay * bx;
+    float k = 0.f;
+    if (la > 0.f && lb > 0.f && L > 0.f) k = -2.f * cross / (la * lb * L);
+    const float hk = fminf(0.999f, fmaxf(-0.999f, k * L * 0.5f));
+    float sn = 0.f;
+    if (L > 0.f) {
+        const float st = cy / L, ct = cx / L, ch = sqrtf(1.f - hk * hk);
+        sn = first_is_outer ? st * ch - ct * hk : st * ch + ct * hk;
+    }
+    sn = fminf(snp_max_seed, fmaxf(-snp_max_seed, sn));
+    const float au = fabsf(hk);
+    const float arc = (au < 1e-9f || k == 0.f) ? L : 2.f * asinf(au) / fabsf(k);
+    const float t = arc > 0.f ? (zs[i2] - zs[i0]) / arc : 0.f;
+    float w = kb_unit != 0.f ? k / kb_unit : 0.f;
+    w = fminf(qpt_max, fmaxf(-qpt_max, w));
+    s.x = geo->row_xd[rows[0]];
+    s.frame = frame;
+    s.p[0] = ys[0];
+    s.p[1] = zs[0];
+    s.p[2] = sn;
+    s.p[3] = t;
+    s.p[4] = w;
     s.lo[0] = s.lo[1] = s.lo[2] = 0.f;
 #pragma unroll
     for (int i = 0; i < 15; ++i) s.C[i] = 0.f;

@@ -38,9 +38,6 @@ struct Cells {  // per-group z-cell description
     const int32_t* nz;
     const int32_t* kbase;
     const int32_t* off;  // cell offsets into the binned arrays
-    int64_t K;           // cell capacity (self-check bound)
-    int64_t n;           // binned clusters (self-check bound)
-    int32_t* st;         // status word for self-check reports
 };
 
 // Self-check: an index outside [0, bound) is reported in the status word
@@ -273,14 +270,11 @@ __device__ __forceinline__ float triplet_d2(float xd, float yd, float zd, float 
 // binned index range of the z cells of row r (group g) covering [zlo, zhi]
 __device__ __forceinline__ void cell_range(const Cells& cells, int g, int r, float zlo, float zhi,
                                            int& b, int& e) {
+    // zcell clamps to the group's cells, and k_cells has checked that the
+    // groups' cells fit the table: both offsets are inside cell_off
     const int base = cells.kbase[g] + r * cells.nz[g];
-    const int k0 = base + zcell(cells, g, zlo), k1 = base + zcell(cells, g, zhi) + 1;
-    b = e = 0;
-    if (!in_range(k0, cells.K + 1, cells.st, 101) || !in_range(k1, cells.K + 1, cells.st, 102)) return;
-    b = cells.off[k0];
-    e = cells.off[k1];
-    if (!in_range(b, cells.n + 1, cells.st, 103) || !in_range(e, cells.n + 1, cells.st, 104) || e < b)
-        b = e = 0;
+    b = cells.off[base + zcell(cells, g, zlo)];
+    e = cells.off[base + zcell(cells, g, zhi) + 1];
 }
 
 // Serial evaluation of one gap pair (gd, gu) for cluster c; the reference
@@ -525,6 +519,26 @@ __global__ void k_chains(int64_t n, const int32_t* __restrict__ link_dn,
     }
 }
 
+// Processing order of the segments: by the binned position of their start
+// cluster, i.e. (group, row, z cell), so that the lanes of a warp tend to
+// follow tracks of similar extent and stay in the same phase.  The order
+// only schedules the work; no result depends on it.
+__global__ void k_seg_mark(const int32_t* __restrict__ seg_start, int64_t Scap, const int32_t* st,
+                           int32_t* flag, int32_t* slot_at) {
+    const int nseg = min((int64_t)st[ST_NSEG], Scap);
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nseg; s += gridDim.x * blockDim.x) {
+        flag[seg_start[s]] = 1;
+        slot_at[seg_start[s]] = s;
+    }
+}
+
+__global__ void k_seg_perm(int64_t n, const int32_t* __restrict__ flag, const int32_t* __restrict__ rank,
+                           const int32_t* __restrict__ slot_at, int32_t* perm) {
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
+         c += (int64_t)gridDim.x * blockDim.x)
+        if (flag[c]) perm[rank[c]] = slot_at[c];
+}
+
 // ---------------------------------------------------------------- S3b -----
 struct TlPrm {
     float sy2, sz2, chi2_ext, kb, snp_max, fp64_ratio, fp64_det, pitch;
@@ -533,12 +547,12 @@ struct TlPrm {
     float prior[5];
 };
 
-// Three-point seed of the hits in a tracklet slot for one fit direction:
-// first, middle (n/2-th in fit order) and last hit.
-__device__ void seed_slot(const int32_t* __restrict__ hit, int rmin, int rmax, int n, bool inward,
+// Three-point seed (FP32) of the hits in a tracklet slot for one fit
+// direction: first, middle (n/2-th in fit order) and last hit.
+__device__ __forceinline__ void seed_slot(const int32_t* __restrict__ hit, int rmin, int rmax, int n, bool inward,
                           const float* __restrict__ yb, const float* __restrict__ zb, int sector,
                           const Geo* __restrict__ geo, const TlPrm& P, KF& s) {
-    int rows[3], secs[3] = {sector, sector, sector};
+    int rows[3];
     float ys[3], zs[3];
     const int want = n / 2;
     int k = 0;
@@ -551,7 +565,7 @@ __device__ void seed_slot(const int32_t* __restrict__ hit, int rmin, int rmax, i
         if (k == n - 1) { rows[2] = r; ys[2] = yb[h]; zs[2] = zb[h]; }
         ++k;
     }
-    kf_seed(s, rows, secs, ys, zs, inward, geo, P.bz, P.seed_snp, P.seed_qpt, P.prior);
+    kf_seed_f(s, rows, sector, ys, zs, inward, geo, P.kb, (float)P.seed_snp, (float)P.seed_qpt, P.prior);
 }
 
 // Tracklet lanes.  Every lane owns one slot at a time and runs a small state
@@ -559,7 +573,8 @@ __device__ void seed_slot(const int32_t* __restrict__ hit, int rmin, int rmax, i
 // execute the same transport / update code:
 //   build:  inward fit of the chain -> inward extension -> outward fit of all
 //           hits -> outward extension   (a failed fit skips its extension)
-//   refit:  inward fit (state at the innermost) -> outward fit (outermost)
+//   refit:  inward fit (state at the innermost) and outward fit (state at
+//           the outermost) of the kept hits, as two independent work items
 // Extension: in each row the cluster with the smallest predicted-residual
 // chi2 (ties: smaller canonical id) if <= chi2_ext; stop after ext_max_miss
 // empty rows, at the last row, on a transport failure, or when the
@@ -572,13 +587,19 @@ __global__ void __launch_bounds__(128, 4) k_tracklet_lanes(
     const int32_t* __restrict__ seg_canon, const int32_t* __restrict__ link_up,
     const float* __restrict__ yb, const float* __restrict__ zb, const int32_t* __restrict__ orig,
     const uint8_t* __restrict__ rowb, Cells cells, const Geo* __restrict__ geo, TlPrm P,
-    int64_t Scap, int32_t* st, int32_t* tl_rowhit, int32_t* tl_n, unsigned long long* tl_key,
+    const int32_t* __restrict__ perm, int64_t Scap, int32_t* st, int32_t* tl_rowhit, int32_t* tl_n,
+    unsigned long long* tl_key,
     const int32_t* __restrict__ tl_keep, const int32_t* __restrict__ tl_rmin_in,
     const int32_t* __restrict__ tl_rmax_in, float* tl_state, int32_t* tl_ok, int tile) {
     const int nseg = min((int64_t)st[ST_NSEG], Scap);
+    const int nitems = refit ? 2 * nseg : nseg;  // refit: item = 2 slot + side
     int32_t* queue = &st[refit ? ST_Q_REFIT : ST_Q_BUILD];
     int s = -1, phase = 0, r = 0, rmin = 0, rmax = 0, n = 0, misses = 0, g = 0, sector = 0, ok = 0;
+    int xr = 0;  // row plane of the state (the state never leaves its sector)
     int steps = 0;
+    // z cells of the slot's group
+    float gz0 = 0.f, ginv = 0.f;
+    int gnz = 1, gkb = 0;
     int t_next = 0, t_end = 0;  // slots of the current ticket
     int32_t* hit = nullptr;
     KF kf;
@@ -589,12 +610,18 @@ __global__ void __launch_bounds__(128, 4) k_tracklet_lanes(
                 t_next = atomicAdd(queue, tile);
                 t_end = t_next + tile;
             }
-            s = t_next++;
-            if (s >= nseg) break;
+            const int item = t_next++;
+            if (item >= nitems) break;
+            s = perm[refit ? item >> 1 : item];
+            const bool outward_only = refit && (item & 1);
             hit = tl_rowhit + (int64_t)s * NROW;
             g = seg_grp[s];
             sector = g % NSEC;
             ok = 0;
+            gz0 = cells.zmin[g];
+            ginv = cells.inv[g];
+            gnz = cells.nz[g];
+            gkb = cells.kbase[g];
             if (refit) {
                 if (!tl_keep[s]) {
                     s = -1;
@@ -617,10 +644,18 @@ __global__ void __launch_bounds__(128, 4) k_tracklet_lanes(
                     ++n;
                 }
             }
-            phase = PH_FIT_IN;
-            seed_slot(hit, rmin, rmax, n, true, yb, zb, sector, geo, P, kf);
-            r = rmax + 1;
             misses = 0;
+            if (outward_only) {
+                phase = PH_FIT_OUT;
+                seed_slot(hit, rmin, rmax, n, false, yb, zb, sector, geo, P, kf);
+                xr = rmin;
+                r = rmin - 1;
+            } else {
+                phase = PH_FIT_IN;
+                seed_slot(hit, rmin, rmax, n, true, yb, zb, sector, geo, P, kf);
+                xr = rmax;
+                r = rmax + 1;
+            }
         }
         // ---- one step of the current phase
         const bool fit = phase == PH_FIT_IN || phase == PH_FIT_OUT;
@@ -633,15 +668,13 @@ __global__ void __launch_bounds__(128, 4) k_tracklet_lanes(
         if (fit) end_phase = target < rmin || target > rmax;
         else end_phase = target < 0 || target >= NROW || misses >= P.ext_max_miss;
         bool moved = false;
-        MoveJ mj;
         if (!end_phase) {
             // within one sector the planes are rows: the step is an exact
-            // multiple of the row pitch
-            const int from_row = (r >= 0 && r < NROW) ? r : (dir < 0 ? rmax : rmin);
-            const float dxr = (float)(target - from_row) * P.pitch;
-            moved = kf_move<float>(kf, geo->row_xd[target], sector, geo, P.kb, P.snp_max, &mj,
-                                   kf.x == geo->row_xd[from_row] ? &dxr : nullptr);
+            // multiple of the row pitch (zero for the first hit after a seed)
+            const float dxr = (float)(target - xr) * P.pitch;
+            moved = kf_move<float, false>(kf, 0.0, sector, geo, P.kb, P.snp_max, nullptr, &dxr);
             ++steps;
+            if (moved) xr = target;
             if (!moved) end_phase = true;
             else if (!fit && fabsf(kf.p[0] + kf.lo[0]) > geo->row_xf[target] * geo->tan_half)
                 end_phase = true;
@@ -655,10 +688,14 @@ __global__ void __launch_bounds__(128, 4) k_tracklet_lanes(
                 const float det = S00 * S11 - S01 * S01;
                 const float wz = sqrtf(P.chi2_ext * S11) * 1.001f + 1e-3f;
                 const float wy = sqrtf(P.chi2_ext * S00) * 1.001f + 1e-3f;
-                int b, e;
-                cell_range(cells, g, target, kf.p[1] - wz, kf.p[1] + wz, b, e);
+                const int cb = gkb + target * gnz;
+                const float f0 = (kf.p[1] - wz - gz0) * ginv, f1 = (kf.p[1] + wz - gz0) * ginv;
+                const int k0 = min(f0 >= 0.f ? (int)f0 : 0, gnz - 1);
+                const int k1 = min(f1 >= 0.f ? (int)f1 : 0, gnz - 1);
+                const int b = cells.off[cb + k0], e = cells.off[cb + k1 + 1];
                 int bo = 0;
                 float bchi = 0.f;
+#pragma unroll 4
                 for (int q = b; q < e; ++q) {
                     const float r1 = (zb[q] - kf.p[1]) - kf.lo[1];
                     if (fabsf(r1) > wz) continue;
@@ -682,20 +719,25 @@ __global__ void __launch_bounds__(128, 4) k_tracklet_lanes(
                     ++misses;
                 }
             }
-            if (c >= 0) kf_update(kf, yb[c], zb[c], P.sy2, P.sz2, P.fp64_ratio, P.fp64_det, &st[ST_FP64], &mj);
+            if (c >= 0) kf_update(kf, yb[c], zb[c], P.sy2, P.sz2, P.fp64_ratio, P.fp64_det, &st[ST_FP64], nullptr);
             r = target;
             continue;
         }
         // ---- phase transitions
         if (phase == PH_FIT_IN) {
             if (moved || target < rmin || target > rmax) ok |= 1;  // fit completed
-            if (refit && (ok & 1)) {
-                float* out = tl_state + (int64_t)s * 40;
-                for (int i = 0; i < 3; ++i) out[i] = kf.p[i] + kf.lo[i];
-                for (int i = 3; i < 5; ++i) out[i] = kf.p[i];
-                for (int i = 0; i < 15; ++i) out[5 + i] = kf.C[i];
+            if (refit) {
+                if (ok & 1) {
+                    float* out = tl_state + (int64_t)s * 40;
+                    for (int i = 0; i < 3; ++i) out[i] = kf.p[i] + kf.lo[i];
+                    for (int i = 3; i < 5; ++i) out[i] = kf.p[i];
+                    for (int i = 0; i < 15; ++i) out[5 + i] = kf.C[i];
+                    atomicOr(&tl_ok[s], 1);
+                }
+                s = -1;
+                continue;
             }
-            if (!refit && (ok & 1)) {
+            if (ok & 1) {
                 phase = PH_EXT_IN;
                 r = rmin;
                 misses = 0;
@@ -712,8 +754,8 @@ __global__ void __launch_bounds__(128, 4) k_tracklet_lanes(
                     for (int i = 0; i < 3; ++i) out[20 + i] = kf.p[i] + kf.lo[i];
                     for (int i = 3; i < 5; ++i) out[20 + i] = kf.p[i];
                     for (int i = 0; i < 15; ++i) out[25 + i] = kf.C[i];
+                    atomicOr(&tl_ok[s], 2);
                 }
-                tl_ok[s] = ok;
                 s = -1;
                 continue;
             }
@@ -729,6 +771,7 @@ __global__ void __launch_bounds__(128, 4) k_tracklet_lanes(
         }
         if (phase == PH_FIT_OUT) {
             seed_slot(hit, rmin, rmax, n, false, yb, zb, sector, geo, P, kf);
+            xr = rmin;
             r = rmin - 1;
             continue;
         }
@@ -1131,7 +1174,7 @@ cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hi
                                W.at<uint32_t>(L.g_zmax_u), W.at<float>(L.g_zmin), W.at<float>(L.g_inv),
                                W.at<int32_t>(L.g_nz), W.at<int32_t>(L.g_kbase), L.K, st);
     Cells cells{W.at<float>(L.g_zmin), W.at<float>(L.g_inv), W.at<int32_t>(L.g_nz),
-                W.at<int32_t>(L.g_kbase), W.at<int32_t>(L.cell_off), L.K, n, st};
+                W.at<int32_t>(L.g_kbase), W.at<int32_t>(L.cell_off)};
     TPC_TRY(fill_i32(W.at<int32_t>(L.cell_cnt), L.K + 1, 0, s));
     tpc::LaunchCount{}, k_hist<<<grid_for(n), TPB, 0, s>>>(c->z, c->row, n, c->evt_sector_off, G, cells,
                                        W.at<int32_t>(L.cell_cnt), W.at<int32_t>(L.key_in),
@@ -1172,6 +1215,18 @@ cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hi
     tpc::LaunchCount{}, k_chains<<<grid_for(n), TPB, 0, s>>>(n, ldn, lup, orig, grpb, p.n_seg, L.S,
                                          W.at<int32_t>(L.seg_start), W.at<int32_t>(L.seg_grp),
                                          W.at<int32_t>(L.seg_canon), st);
+    // processing order of the segments (start clusters are unique)
+    {
+        int32_t* flag = W.at<int32_t>(L.trk_flag);
+        int32_t* rank = W.at<int32_t>(L.trk_rank);
+        int32_t* slot_at = W.at<int32_t>(L.trk_head_at);
+        TPC_TRY(fill_i32(flag, n, 0, s));
+        tpc::LaunchCount{}, k_seg_mark<<<grid_for(L.S, 128), 128, 0, s>>>(W.at<int32_t>(L.seg_start), L.S, st,
+                                                                           flag, slot_at);
+        TPC_TRY(scan_i32(flag, rank, n, scan_tmp, s));
+        tpc::LaunchCount{}, k_seg_perm<<<grid_for(n), TPB, 0, s>>>(n, flag, rank, slot_at,
+                                                                W.at<int32_t>(L.seg_perm));
+    }
     c->mark(4, s);
     // S3b: tracklets
     TlPrm tp;
@@ -1197,7 +1252,7 @@ cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hi
     auto* tl_key = W.at<unsigned long long>(L.tl_key);
     tpc::LaunchCount{}, k_tracklet_lanes<<<lgrid, 128, 0, s>>>(
         0, W.at<int32_t>(L.seg_start), W.at<int32_t>(L.seg_grp), W.at<int32_t>(L.seg_canon), lup, yb,
-        zb, orig, rowb, cells, geo, tp, L.S, st, tl_rowhit, W.at<int32_t>(L.tl_n), tl_key, nullptr,
+        zb, orig, rowb, cells, geo, tp, W.at<int32_t>(L.seg_perm), L.S, st, tl_rowhit, W.at<int32_t>(L.tl_n), tl_key, nullptr,
         nullptr, nullptr, nullptr, nullptr, tile);
     c->mark(5, s);
     auto* owner = W.at<unsigned long long>(L.owner);
@@ -1218,7 +1273,7 @@ cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hi
                                  W.at<int32_t>(L.tl_binkey), L.KT);
     tpc::LaunchCount{}, k_tracklet_lanes<<<lgrid, 128, 0, s>>>(
         1, W.at<int32_t>(L.seg_start), W.at<int32_t>(L.seg_grp), W.at<int32_t>(L.seg_canon), lup, yb,
-        zb, orig, rowb, cells, geo, tp, L.S, st, tl_rowhit, W.at<int32_t>(L.tl_n), tl_key,
+        zb, orig, rowb, cells, geo, tp, W.at<int32_t>(L.seg_perm), L.S, st, tl_rowhit, W.at<int32_t>(L.tl_n), tl_key,
         W.at<int32_t>(L.tl_keep), W.at<int32_t>(L.tl_rmin), W.at<int32_t>(L.tl_rmax),
         W.at<float>(L.tl_state), W.at<int32_t>(L.tl_ok), tile);
     TPC_TRY(scan_i32(grp_cnt, W.at<int32_t>(L.grp_tl_off), L.KT, scan_tmp, s));

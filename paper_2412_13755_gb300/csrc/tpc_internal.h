@@ -21,7 +21,7 @@ constexpr int NSEC = 36;
 constexpr int NPHI = 18;
 constexpr int NROW = 152;
 constexpr int MAX_CAND = 16;     // merge candidates kept per tracklet
-constexpr int CELL_OCC = 8;      // target clusters per (row, z-cell)
+constexpr int CELL_OCC = 2;      // target clusters per (row, z-cell)
 constexpr int NZ_MAX = 8192;     // z cells per row at most
 
 // Geometry table written into the workspace at set-up.
@@ -57,7 +57,7 @@ struct Layout {
     // offsets
     size_t geo, status, g_zmin_u, g_zmax_u, g_nz, g_inv, g_zmin, g_kbase, key_in, slot_in,
         cell_cnt, cell_off, yb, zb, orig, grpb, rowb, choice_dn, choice_up, d2, claim_up,
-        claim_dn, link_dn, link_up, owner, seg_start, seg_len, seg_grp, seg_canon, tl_rowhit,
+        claim_dn, link_dn, link_up, owner, seg_start, seg_perm, seg_grp, seg_canon, tl_rowhit,
         tl_n, tl_key, tl_keep, tl_canon, tl_rmin, tl_rmax, tl_zin, tl_zout, tl_state, tl_ok,
         grp_tl_cnt, grp_tl_off, grp_tl_cur, tl_sorted, gs_meta, tl_binkey, tb_zmin, tb_inv, tb_nb, tb_base, cand_n, cand_a, cand_c2, best_a, best_b,
         nxt, prv, refit, trk_flag, trk_rank, trk_len_at, trk_head_at, len_by_rank, scan_a, scan_b,
