@@ -578,6 +578,17 @@ bool chi2_5(const double dp[5], const double M[15], double& out) {
     return true;
 }
 
+// Moves a filtered state (p, C at plane x of `sector`) to the plane of row r
+// of the same sector: helix transport with the covariance J C J^T.  Returns
+// false (state untouched) when the transport fails.
+bool move_to_row(double& x, double p[5], double C[15], int sector, int r, const orc_params& prm) {
+    double J[25], dX[5];
+    int frame = sector;
+    if (!move_state<double>(x, p, frame, row_x(r), sector, J, dX, prm)) return false;
+    cov_transform(C, J);
+    return true;
+}
+
 // S3b: Kalman-guided extension.  From the state at plane x (frame =
 // sector), visit rows r_start, r_start+dir, ... ; in each row take the
 // cluster of the group with the smallest predicted-residual chi2
@@ -593,10 +604,12 @@ void extend_tracklet(const float* y, const float* z, const std::vector<std::vect
         double J[25], dX[5];
         int frame = sector;
         if (!move_state<double>(x, p, frame, row_x(r), sector, J, dX, prm)) break;
+        // the state and its covariance move together, so that the state the
+        // extension ends with is consistent at its plane
+        cov_transform(C, J);
         // the track has left the sector when its prediction is outside the
         // row's acceptance |y| <= x tan(10 deg)
         if (std::fabs(p[0]) > row_x(r) * TAN_HALF) break;
-        cov_transform(C, J);
         const double S00 = C[sidx(0, 0)] + prm.sigma_y2, S01 = C[sidx(0, 1)], S11 = C[sidx(1, 1)] + prm.sigma_z2;
         const double det = S00 * S11 - S01 * S01;
         int32_t best = -1;
@@ -727,8 +740,12 @@ int64_t orc_find_tracks(const float* y, const float* z, const uint16_t* row, int
     for (int g = 0; g < G; ++g)
         for (int64_t i = off[g]; i < off[g + 1]; ++i) sec[i] = g % NSEC;
     auto no_align = [](int) -> const double* { return nullptr; };
-    // S3b: each segment seeds a tracklet: inward fit + inward extension, then
-    // outward fit over everything + outward extension.
+    // S3b: each segment seeds a tracklet: inward fit + inward extension; the
+    // final inward-filtered state, moved to the outermost hit row, starts the
+    // outward extension.  Without process noise that state carries every hit
+    // (the move is exact), so it stands for an outward fit over all of them;
+    // the outward fit itself is used only when the inward fit or that move
+    // fails.
     std::vector<std::vector<int32_t>> tl_hits(S0);
 #pragma omp parallel for schedule(dynamic, 16) num_threads(nt)
     for (int i = 0; i < S0; ++i) {
@@ -736,15 +753,20 @@ int64_t orc_find_tracks(const float* y, const float* z, const uint16_t* row, int
         const auto& rows = grp_rows[sg.event * NSEC + sg.sector];
         std::vector<int32_t> H = sg.hits;
         double p[5], C[15], chi2, x;
+        bool have_out = false;
         if (kf_fit<double>(y, z, row, sec.data(), H.data(), (int)H.size(), true, prm, no_align, p, C,
                            chi2, &x)) {
             std::vector<int32_t> add;
             extend_tracklet(y, z, rows, sg.sector, x, p, C, row[H.back()] - 1, -1, prm, add);
             H.insert(H.end(), add.begin(), add.end());
+            have_out = move_to_row(x, p, C, sg.sector, row[H.front()], prm);
         }
-        std::vector<int32_t> rev(H.rbegin(), H.rend());
-        if (kf_fit<double>(y, z, row, sec.data(), rev.data(), (int)rev.size(), false, prm, no_align, p, C,
-                           chi2, &x)) {
+        if (!have_out) {
+            std::vector<int32_t> rev(H.rbegin(), H.rend());
+            have_out = kf_fit<double>(y, z, row, sec.data(), rev.data(), (int)rev.size(), false, prm, no_align,
+                                      p, C, chi2, &x);
+        }
+        if (have_out) {
             std::vector<int32_t> add;
             extend_tracklet(y, z, rows, sg.sector, x, p, C, row[H.front()] + 1, +1, prm, add);
             std::vector<int32_t> H2(add.rbegin(), add.rend());
@@ -778,16 +800,26 @@ int64_t orc_find_tracks(const float* y, const float* z, const uint16_t* row, int
     }
     std::sort(segs.begin(), segs.end(), [](const Segment& a, const Segment& b) { return a.canon < b.canon; });
     const int S = (int)segs.size();
-    // S5 on tracklets: inward fit (state at innermost), outward fit (outermost)
+    // S5 on tracklets: inward fit (state at the innermost hit); the state at
+    // the outermost hit is that state moved there (the outward fit only when
+    // the inward fit or the move fails)
 #pragma omp parallel for schedule(dynamic, 16) num_threads(nt)
     for (int i = 0; i < S; ++i) {
         Segment& s = segs[i];
-        double chi2;
+        double chi2, x;
         s.ok_in = kf_fit<double>(y, z, row, sec.data(), s.hits.data(), (int)s.hits.size(), true, prm,
-                                 no_align, s.p_in, s.c_in, chi2);
-        std::vector<int32_t> rev(s.hits.rbegin(), s.hits.rend());
-        s.ok_out = kf_fit<double>(y, z, row, sec.data(), rev.data(), (int)rev.size(), false, prm,
-                                  no_align, s.p_out, s.c_out, chi2);
+                                 no_align, s.p_in, s.c_in, chi2, &x);
+        s.ok_out = false;
+        if (s.ok_in) {
+            for (int k = 0; k < 5; ++k) s.p_out[k] = s.p_in[k];
+            for (int k = 0; k < 15; ++k) s.c_out[k] = s.c_in[k];
+            s.ok_out = move_to_row(x, s.p_out, s.c_out, s.sector, row[s.hits.front()], prm);
+        }
+        if (!s.ok_out) {
+            std::vector<int32_t> rev(s.hits.rbegin(), s.hits.rend());
+            s.ok_out = kf_fit<double>(y, z, row, sec.data(), rev.data(), (int)rev.size(), false, prm,
+                                      no_align, s.p_out, s.c_out, chi2);
+        }
     }
     // S4 candidates
     std::vector<std::vector<MergePair>> cand_b(S);

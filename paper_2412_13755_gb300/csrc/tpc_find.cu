@@ -325,13 +325,154 @@ struct NbLists {
     int cnt[6];
 };
 
-// Warp-cooperative neighbour search (same rule and result as the serial
-// search): one warp per cluster; the window candidates of each needed row
+// Neighbour search by sub-warps of NG lanes, one cluster per sub-warp
+// (same rule and result as the serial search).  The admissible window
+// candidates of each needed row offset (down rows r-1..r-3 -> lists 0..2, up
+// rows r+1..r+3 -> lists 3..5) are compacted into the sub-warp's shared
+// memory lists once; the lanes then evaluate the (down, up) pairs of each gap
+// pair in order and reduce to the best pair (smallest D^2, then canonical id
+// of u, then of d).  A cluster whose needed list exceeds NS_CAP entries is
+// queued for the full-warp kernel below, which redoes it.
+constexpr int NG = 8;          // lanes per cluster
+constexpr int NS_CAP = 16;     // list capacity per row offset (<= 254)
+constexpr int NS_WARPS = 8;    // warps per block
+struct NsLists {
+    float y[6][NS_CAP];
+    float z[6][NS_CAP];
+    int idx[6][NS_CAP];
+};
+__global__ void __launch_bounds__(NS_WARPS * 32) k_neighbours_sub(
+    int64_t n, const float* __restrict__ yb, const float* __restrict__ zb,
+    const int32_t* __restrict__ orig, const int32_t* __restrict__ grpb,
+    const uint8_t* __restrict__ rowb, Cells cells, const Geo* __restrict__ geo, NbPrm P,
+    int32_t* choice_dn, int32_t* choice_up, float* d2out, int32_t* st, int32_t* ovf_queue) {
+    constexpr int GPW = 32 / NG;  // clusters per warp
+    __shared__ NsLists sh_all[NS_WARPS * GPW];
+    const int lane = threadIdx.x & 31;
+    const int gq = lane / NG, li = lane % NG;
+    const unsigned gm = ((1u << NG) - 1u) << (gq * NG);
+    const unsigned lt = (1u << li) - 1u;
+    NsLists& sh = sh_all[(threadIdx.x >> 5) * GPW + gq];
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t c0 = wid * GPW; c0 < n; c0 += nw * GPW) {
+        const int64_t c = c0 + gq;
+        if (c >= n) continue;  // the whole sub-warp leaves together
+        const int g = grpb[c], r = rowb[c];
+        const float xc = geo->row_xf[r], yc = yb[c], zc = zb[c];
+        // list k: bit k of `built`; its count (capped at NS_CAP + 1) in bits 8k..8k+7 of `cnts`
+        unsigned built = 0;
+        uint64_t cnts = 0;
+        int bd = -1, bu = -1;
+        float bd2 = 0.f;
+        bool ovf = false;
+        for (int sum = 2; sum <= 2 * P.max_gap && bd < 0 && !ovf; ++sum) {
+            for (int gu = 1; gu <= P.max_gap && bd < 0 && !ovf; ++gu) {
+                const int gd = sum - gu;
+                if (gd < 1 || gd > P.max_gap) continue;
+                const int rd = r - gd, ru = r + gu;
+                if (rd < 0 || ru >= NROW) continue;
+                const int kd = gd - 1, ku = 2 + gu;
+#pragma unroll
+                for (int side = 0; side < 2; ++side) {
+                    const int k = side == 0 ? kd : ku;
+                    if (built & (1u << k)) continue;
+                    const int rr = side == 0 ? rd : ru;
+                    const float xr = geo->row_xf[rr];
+                    const float wz = __fmul_rn(P.win_z, fabsf(__fsub_rn(xr, xc)));
+                    int b, e;
+                    cell_range(cells, g, rr, zc - wz * 1.0001f - 1e-3f, zc + wz * 1.0001f + 1e-3f, b, e);
+                    int cnt = 0;
+                    for (int base = b; base < e; base += NG) {
+                        const int q = base + li;
+                        float yq = 0.f, zq = 0.f;
+                        bool pass = false;
+                        if (q < e) {
+                            yq = yb[q];
+                            zq = zb[q];
+                            pass = in_win(xc, yc, zc, xr, yq, zq, P.win_y, P.win_z);
+                        }
+                        const unsigned bal = (__ballot_sync(gm, pass) >> (gq * NG)) & ((1u << NG) - 1u);
+                        const int pos = cnt + __popc(bal & lt);
+                        if (pass && pos < NS_CAP) {
+                            sh.idx[k][pos] = q;
+                            sh.y[k][pos] = yq;
+                            sh.z[k][pos] = zq;
+                        }
+                        cnt += __popc(bal);
+                    }
+                    built |= 1u << k;
+                    cnts |= (uint64_t)min(cnt, NS_CAP + 1) << (8 * k);
+                }
+                __syncwarp(gm);
+                const int nd = (int)((cnts >> (8 * kd)) & 255u), nu = (int)((cnts >> (8 * ku)) & 255u);
+                if (nd == 0 || nu == 0) continue;
+                if (nd > NS_CAP || nu > NS_CAP) {
+                    ovf = true;
+                    break;
+                }
+                const float xd = geo->row_xf[rd], xu = geo->row_xf[ru];
+                int pd = -1, pu = -1, pod = 0, pou = 0;
+                float pd2 = 0.f;
+                const int total = nd * nu;
+                for (int pp = li; pp < total; pp += NG) {
+                    const int i = pp / nu, j = pp - i * nu;
+                    const float d2 = triplet_d2(xd, sh.y[kd][i], sh.z[kd][i], xc, yc, zc, xu,
+                                                sh.y[ku][j], sh.z[ku][j], P.sy2, P.sz2);
+                    if (!(d2 <= P.chi2_link)) continue;
+                    const int d = sh.idx[kd][i], u = sh.idx[ku][j];
+                    bool better = pd < 0 || d2 < pd2;
+                    if (!better && d2 == pd2) {
+                        const int ou = orig[u], od = orig[d];
+                        better = ou < pou || (ou == pou && od < pod);
+                    }
+                    if (better) {
+                        pd = d; pu = u; pd2 = d2; pod = orig[d]; pou = orig[u];
+                    }
+                }
+                // sub-warp argmin of (D^2, canonical u, canonical d)
+#pragma unroll
+                for (int o = NG / 2; o >= 1; o >>= 1) {
+                    const int od_ = __shfl_xor_sync(gm, pd, o);
+                    const int ou_ = __shfl_xor_sync(gm, pu, o);
+                    const float o2 = __shfl_xor_sync(gm, pd2, o);
+                    const int ood = __shfl_xor_sync(gm, pod, o);
+                    const int oou = __shfl_xor_sync(gm, pou, o);
+                    const bool take = od_ >= 0 && (pd < 0 || o2 < pd2 ||
+                                                   (o2 == pd2 && (oou < pou || (oou == pou && ood < pod))));
+                    if (take) {
+                        pd = od_; pu = ou_; pd2 = o2; pod = ood; pou = oou;
+                    }
+                }
+                if (pd >= 0) {
+                    bd = pd;
+                    bu = pu;
+                    bd2 = pd2;
+                }
+                __syncwarp(gm);
+            }
+        }
+        if (li == 0) {
+            if (ovf) {
+                ovf_queue[atomicAdd(&st[ST_NB_OVF], 1)] = (int32_t)c;
+            } else {
+                choice_dn[c] = bd;
+                choice_up[c] = bu;
+                d2out[c] = bd2;
+            }
+        }
+        __syncwarp(gm);
+    }
+}
+
+// Warp-cooperative neighbour search for the queued clusters (same rule and
+// result): one warp per cluster; the window candidates of each needed row
 // offset are compacted into shared memory once, then the lanes evaluate the
 // (down, up) pairs of a gap pair in parallel and reduce to the best pair
 // (smallest D^2, then canonical id of u, then of d).
 __global__ void __launch_bounds__(NB_WARPS * 32) k_neighbours_warp(
-    int64_t n, const float* __restrict__ yb, const float* __restrict__ zb,
+    const int32_t* __restrict__ queue, const int32_t* __restrict__ st,
+    const float* __restrict__ yb, const float* __restrict__ zb,
     const int32_t* __restrict__ orig, const int32_t* __restrict__ grpb,
     const uint8_t* __restrict__ rowb, Cells cells, const Geo* __restrict__ geo, NbPrm P,
     int32_t* choice_dn, int32_t* choice_up, float* d2out) {
@@ -341,7 +482,9 @@ __global__ void __launch_bounds__(NB_WARPS * 32) k_neighbours_warp(
     const unsigned lt = (1u << lane) - 1u;
     const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t c = wid; c < n; c += nw) {
+    const int64_t nq = st[ST_NB_OVF];
+    for (int64_t qi = wid; qi < nq; qi += nw) {
+        const int64_t c = queue[qi];
         const int g = grpb[c], r = rowb[c];
         const float xc = geo->row_xf[r], yc = yb[c], zc = zb[c];
         unsigned built = 0;  // bit k: list k (k < 3: down rows r-1-k, k >= 3: up rows r+k-2)
@@ -571,10 +714,12 @@ __device__ __forceinline__ void seed_slot(const int32_t* __restrict__ hit, int r
 // Tracklet lanes.  Every lane owns one slot at a time and runs a small state
 // machine, one Kalman step per loop iteration, so that the lanes of a warp
 // execute the same transport / update code:
-//   build:  inward fit of the chain -> inward extension -> outward fit of all
-//           hits -> outward extension   (a failed fit skips its extension)
-//   refit:  inward fit (state at the innermost) and outward fit (state at
-//           the outermost) of the kept hits, as two independent work items
+//   build:  inward fit of the chain -> inward extension -> the state moved
+//           to the outermost hit row -> outward extension
+//   refit:  inward fit of the kept hits (state at the innermost) -> the
+//           state moved to the outermost hit row (state there)
+// An outward fit of all hits stands in for the moved state only when the
+// inward fit or the move fails; a failed fit skips its extension.
 // Extension: in each row the cluster with the smallest predicted-residual
 // chi2 (ties: smaller canonical id) if <= chi2_ext; stop after ext_max_miss
 // empty rows, at the last row, on a transport failure, or when the
@@ -592,7 +737,7 @@ __global__ void __launch_bounds__(128, 4) k_tracklet_lanes(
     const int32_t* __restrict__ tl_keep, const int32_t* __restrict__ tl_rmin_in,
     const int32_t* __restrict__ tl_rmax_in, float* tl_state, int32_t* tl_ok, int tile) {
     const int nseg = min((int64_t)st[ST_NSEG], Scap);
-    const int nitems = refit ? 2 * nseg : nseg;  // refit: item = 2 slot + side
+    const int nitems = nseg;
     int32_t* queue = &st[refit ? ST_Q_REFIT : ST_Q_BUILD];
     int s = -1, phase = 0, r = 0, rmin = 0, rmax = 0, n = 0, misses = 0, g = 0, sector = 0, ok = 0;
     int xr = 0;  // row plane of the state (the state never leaves its sector)
@@ -612,8 +757,7 @@ __global__ void __launch_bounds__(128, 4) k_tracklet_lanes(
             }
             const int item = t_next++;
             if (item >= nitems) break;
-            s = perm[refit ? item >> 1 : item];
-            const bool outward_only = refit && (item & 1);
+            s = perm[item];
             hit = tl_rowhit + (int64_t)s * NROW;
             g = seg_grp[s];
             sector = g % NSEC;
@@ -645,17 +789,10 @@ __global__ void __launch_bounds__(128, 4) k_tracklet_lanes(
                 }
             }
             misses = 0;
-            if (outward_only) {
-                phase = PH_FIT_OUT;
-                seed_slot(hit, rmin, rmax, n, false, yb, zb, sector, geo, P, kf);
-                xr = rmin;
-                r = rmin - 1;
-            } else {
-                phase = PH_FIT_IN;
-                seed_slot(hit, rmin, rmax, n, true, yb, zb, sector, geo, P, kf);
-                xr = rmax;
-                r = rmax + 1;
-            }
+            phase = PH_FIT_IN;
+            seed_slot(hit, rmin, rmax, n, true, yb, zb, sector, geo, P, kf);
+            xr = rmax;
+            r = rmax + 1;
         }
         // ---- one step of the current phase
         const bool fit = phase == PH_FIT_IN || phase == PH_FIT_OUT;
@@ -724,38 +861,54 @@ __global__ void __launch_bounds__(128, 4) k_tracklet_lanes(
             continue;
         }
         // ---- phase transitions
+        // After the inward pass the filtered state, moved to the outermost
+        // hit row, carries every hit (exact transport, no process noise): it
+        // is the outward state; an outward fit only replaces it when the
+        // inward fit or that move failed.
+        bool to_outer = false;
         if (phase == PH_FIT_IN) {
             if (moved || target < rmin || target > rmax) ok |= 1;  // fit completed
-            if (refit) {
-                if (ok & 1) {
-                    float* out = tl_state + (int64_t)s * 40;
-                    for (int i = 0; i < 3; ++i) out[i] = kf.p[i] + kf.lo[i];
-                    for (int i = 3; i < 5; ++i) out[i] = kf.p[i];
-                    for (int i = 0; i < 15; ++i) out[5 + i] = kf.C[i];
-                    atomicOr(&tl_ok[s], 1);
-                }
-                s = -1;
-                continue;
+            if (refit && (ok & 1)) {
+                float* out = tl_state + (int64_t)s * 40;
+                for (int i = 0; i < 3; ++i) out[i] = kf.p[i] + kf.lo[i];
+                for (int i = 3; i < 5; ++i) out[i] = kf.p[i];
+                for (int i = 0; i < 15; ++i) out[5 + i] = kf.C[i];
             }
-            if (ok & 1) {
+            if (!refit && (ok & 1)) {
                 phase = PH_EXT_IN;
                 r = rmin;
                 misses = 0;
                 continue;
             }
+            to_outer = (ok & 1) != 0;
             phase = PH_FIT_OUT;
         } else if (phase == PH_EXT_IN) {
+            to_outer = true;
             phase = PH_FIT_OUT;
         } else if (phase == PH_FIT_OUT) {
             if (moved || target < rmin || target > rmax) ok |= 2;
+            phase = PH_EXT_OUT + 1;  // outward state ready (or the fit failed)
+        } else {
+            phase = PH_EXT_OUT + 2;  // finished
+        }
+        if (to_outer) {
+            const float dxl = (float)(rmax - xr) * P.pitch;
+            if (kf_move<float, false>(kf, 0.0, sector, geo, P.kb, P.snp_max, nullptr, &dxl)) {
+                ++steps;
+                xr = rmax;
+                ok |= 2;
+                phase = PH_EXT_OUT + 1;
+            }
+        }
+        if (phase == PH_EXT_OUT + 1) {
             if (refit) {
                 if (ok & 2) {
                     float* out = tl_state + (int64_t)s * 40;
                     for (int i = 0; i < 3; ++i) out[20 + i] = kf.p[i] + kf.lo[i];
                     for (int i = 3; i < 5; ++i) out[20 + i] = kf.p[i];
                     for (int i = 0; i < 15; ++i) out[25 + i] = kf.C[i];
-                    atomicOr(&tl_ok[s], 2);
                 }
+                tl_ok[s] = ok;
                 s = -1;
                 continue;
             }
@@ -765,9 +918,6 @@ __global__ void __launch_bounds__(128, 4) k_tracklet_lanes(
                 misses = 0;
                 continue;
             }
-            phase = PH_EXT_OUT + 1;  // finished
-        } else {
-            phase = PH_EXT_OUT + 1;
         }
         if (phase == PH_FIT_OUT) {
             seed_slot(hit, rmin, rmax, n, false, yb, zb, sector, geo, P, kf);
@@ -1164,7 +1314,7 @@ cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hi
     c->mark(0, s);
     // per-call counters (the status word and the FP64 count are cumulative)
     TPC_TRY(fill_i32(st + ST_NSEG, ST_NTRACKS - ST_NSEG + 1, 0, s));
-    TPC_TRY(fill_i32(st + ST_Q_BUILD, ST_KFSTEPS + 2 - ST_Q_BUILD, 0, s));
+    TPC_TRY(fill_i32(st + ST_Q_BUILD, ST_NB_OVF + 1 - ST_Q_BUILD, 0, s));
     // S1: z range per group, cells, histogram, scan, scatter
     tpc::LaunchCount{}, k_fill_u32<<<grid_for(G), TPB, 0, s>>>(W.at<uint32_t>(L.g_zmin_u), G, 0xffffffffu);
     tpc::LaunchCount{}, k_fill_u32<<<grid_for(G), TPB, 0, s>>>(W.at<uint32_t>(L.g_zmax_u), G, 0u);
@@ -1196,8 +1346,11 @@ cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hi
     int32_t* cup = W.at<int32_t>(L.choice_up);
     float* d2 = W.at<float>(L.d2);
     NbPrm nb{p.win_y, p.win_z, p.chi2_link, p.sigma_y2, p.sigma_z2, p.max_gap};
-    tpc::LaunchCount{}, k_neighbours_warp<<<152 * 8, NB_WARPS * 32, 0, s>>>(n, yb, zb, orig, grpb, rowb, cells,
-                                                                        geo, nb, cdn, cup, d2);
+    int32_t* nb_queue = W.at<int32_t>(L.key_in);  // free after S1
+    tpc::LaunchCount{}, k_neighbours_sub<<<grid_for(n, NS_WARPS * 32 / NG * 4), NS_WARPS * 32, 0, s>>>(
+        n, yb, zb, orig, grpb, rowb, cells, geo, nb, cdn, cup, d2, st, nb_queue);
+    tpc::LaunchCount{}, k_neighbours_warp<<<152 * 8, NB_WARPS * 32, 0, s>>>(nb_queue, st, yb, zb, orig, grpb,
+                                                                        rowb, cells, geo, nb, cdn, cup, d2);
     c->mark(2, s);
     auto* claim_up = W.at<unsigned long long>(L.claim_up);
     auto* claim_dn = W.at<unsigned long long>(L.claim_dn);

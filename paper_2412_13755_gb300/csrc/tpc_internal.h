@@ -40,7 +40,7 @@ struct Geo {
 enum StatusSlot {
     ST_STATUS = 0, ST_DETAIL, ST_NSEG, ST_NTL, ST_NCAND, ST_NMERGE, ST_NTRACKS, ST_FP64,
     ST_MATCH_LIVE, ST_Q_BUILD, ST_Q_REFIT, ST_NREFIT, ST_KFSTEPS = 12 /* 64-bit: slots 12-13 */,
-    ST_N_SLOTS = 16
+    ST_NB_OVF = 14, ST_N_SLOTS = 16
 };
 
 // Workspace layout: byte offsets of every buffer, computed from capacities.
