@@ -35,7 +35,7 @@ METRIC = "TPC clusters/s tracked (CA+Kalman), 1 GB300"
 WORKLOAD = ("central_event: 1 event x 36 sectors, 1e4 primary tracks (pT exp slope 0.5 GeV/c "
             "min 0.2, |eta|<0.9), 20% noise, ~1.8e6 clusters, Bz 0.5 T")
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
-# algorithmic traffic / work per unit, fixed before measuring (see DESIGN.md)
+# algorithmic traffic / work per unit, fixed before measuring
 NEIGHBOUR_BYTES_PER_CLUSTER = 20.0      # read y,z (8); write down, up, D^2 (12)
 FIT_BYTES_PER_HIT = 14.0                # hit index (4) + y, z (8) + row (2)
 FIT_BYTES_PER_TRACK = 88.0              # 5 params + 15 cov + chi2 + ndf
@@ -245,6 +245,28 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x, dist, device):
+    """The largest of the ranks' values of x (the job's time is its slowest
+    rank's); x itself when there is one rank."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_value(units_per_rank, world, steps, total_s):
+    """Whole-job throughput: the units every rank processed over the
+    slowest rank's time (weak scaling: per-rank work is fixed)."""
+    return units_per_rank * world * steps / total_s
+
+
+def rank_seed_offset(rank):
+    """Each rank tracks its own event (seed offset = rank)."""
+    return rank
+
+
 def host_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -377,20 +399,6 @@ def run_reference(args):
 
 
 # -------------------------------------------------------------------- ours --
-def count_launches(step, sync):
-    """Kernels of libtpctrack launched by one step (CUPTI via torch.profiler)."""
-    from torch.profiler import ProfilerActivity, profile
-    with profile(activities=[ProfilerActivity.CUDA]) as prof:
-        step()
-        sync()
-    n = 0
-    for e in prof.events():
-        name = getattr(e, "name", "") or ""
-        if "tpc" in name and ("k_" in name or "kernel" in name.lower()):
-            n += 1
-    return n
-
-
 def run_ours(args):
     import torch
 
@@ -402,7 +410,7 @@ def run_ours(args):
         dist.init_process_group("nccl")
     dev = torch.device(f"cuda:{local}")
     torch.cuda.set_device(dev)
-    ev = make_event(seed_offset=rank)
+    ev = make_event(seed_offset=rank_seed_offset(rank))
     n = ev.n
     track_cap = 32768
     tr = tpc.Tracker(n, 1, device=dev)
@@ -462,15 +470,10 @@ def run_ours(args):
     clk = clocks.stop()
     tr.stage_timing(False)
     step_ms = [a.elapsed_time(b) for a, b in zip(e0, e1)]
-    total_s = sum(step_ms) / 1e3
-    if world > 1:
-        t = torch.tensor([total_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
+    total_s = max_over_ranks(sum(step_ms) / 1e3, dist if world > 1 else None, dev)
     st = tr.check()
     T = int(find_out[3].item())
-    units = n * world
-    value = units * args.steps / total_s
+    value = weak_value(n, world, args.steps, total_s)
 
     # end to end: host buffers -> device, step, results back to the host
     h_toc = torch.empty(n, dtype=torch.int32).pin_memory()
@@ -510,10 +513,7 @@ def run_ours(args):
         flush.zero_()
     sync()
     e2e_s = max(e2e_s - (time.perf_counter() - t1), 1e-9)
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, dist if world > 1 else None, dev)
     h2d = 4 * n + 4 * n + 2 * n + 8 * ev.evt_sector_off.size
     d2h = 4 * n + 4 + 20 * track_cap + 4 * track_cap
 
@@ -558,7 +558,7 @@ def run_ours(args):
                    "parallelism": "replicas" if world > 1 else "single"},
         "tracks_per_s": T * world * args.steps / total_s,
         "stage_ms_per_step": per_step,
-        "e2e": {"value": units * args.steps / e2e_s, "unit": "clusters/s",
+        "e2e": {"value": weak_value(n, world, args.steps, e2e_s), "unit": "clusters/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
