@@ -74,12 +74,13 @@ typedef struct {
     float seed_snp_max;        /* clamp of the seed |sin phi|                */
     float seed_qpt_max;        /* clamp of the seed |q/pT| (c/GeV)           */
     float snp_max;             /* transport fails when |sin phi| reaches it  */
-    float fp64_ratio;          /* redo an update in FP64 when a posterior
-                                  variance drops below fp64_ratio x prior    */
+    float fp64_ratio;          /* tracklet building: redo an update in FP64
+                                  when a posterior variance drops below
+                                  fp64_ratio x prior                         */
     float fp64_det;            /* ... or det S <= fp64_det S00 S11           */
-    float fp64_weak_qpt;       /* tpc_fit_tracks refits a track in FP64 when
-                                  its final q/pT variance exceeds this
-                                  fraction of the prior (weak curvature)     */
+    float fp64_weak_qpt;       /* reserved (not read): tpc_fit_tracks keeps
+                                  its covariance in float-float for every
+                                  track                                      */
 } tpc_params;
 
 /* Counters a call leaves in the workspace (read back by tpc_get_stats). */
@@ -156,8 +157,10 @@ tpc_status tpc_find_tracks(tpc_ctx* ctx, int32_t* track_of_cluster, int32_t* trk
  *   cov[T*15]    upper triangle row-major (00 01 02 03 04 11 12 ... 44);
  *   chi2[T]      predicted-residual chi2 (compensated FP32 sum);
  *   ndf[T]       2 n - 5, or -1 when the transport failed (params zeroed).
- * State and covariance are FP32; an update whose covariance cancels is
- * redone in FP64 (see tpc_params.fp64_ratio). */
+ * The state is FP32 with compensated y, z, sin phi; the covariance is kept
+ * in float-float (hi + lo FP32 pairs, error-free transformations) through
+ * every transport and update, so that C - K H C keeps its small directions
+ * without FP64 arithmetic. */
 tpc_status tpc_fit_tracks(tpc_ctx* ctx, const int32_t* trk_off, const int32_t* trk_hits,
                           int32_t n_tracks, const int32_t* n_tracks_dev, float* params,
                           float* cov, float* chi2, int32_t* ndf, tpc_stream_t stream);

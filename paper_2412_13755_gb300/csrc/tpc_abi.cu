@@ -92,7 +92,7 @@ Layout make_layout(int64_t N, int32_t E) {
     L.best_b = take(s8);
     L.nxt = take(s4);
     L.prv = take(s4);
-    L.refit = take(4 * (size_t)L.T);
+    L.match_act = take(2 * s4);
     L.trk_flag = take(n4);
     L.trk_rank = take(n4 + 4);
     L.trk_len_at = take(n4);

@@ -124,8 +124,10 @@ struct MoveJ {
 // Returns false (state untouched or partially moved) when |sin phi| would
 // reach snp_max.  CanRotate = false is the move between row planes of one
 // frame by the caller's step *dx_same_frame (required): no rotation code, no
-// FP64 plane arithmetic, and s.x is left to the caller.
-template <class R, bool CanRotate = true>
+// FP64 plane arithmetic, and s.x is left to the caller.  MoveCov = false
+// leaves s.C alone (for a caller that transforms its own covariance with the
+// Jacobian returned in mj).
+template <class R, bool CanRotate = true, bool MoveCov = true>
 __device__ __forceinline__ bool kf_move(KFT<R>& s, double x_to, int to, const Geo* __restrict__ geo,
                                         R kb, R snp_max, MoveJ* mj = nullptr,
                                         const R* dx_same_frame = nullptr) {
@@ -213,7 +215,7 @@ __device__ __forceinline__ bool kf_move(KFT<R>& s, double x_to, int to, const Ge
         for (int i = 0; i < 15; ++i) mj->Cpre[i] = (float)s.C[i];
         mj->valid = true;
     }
-    cov_jct<R>(s.C, j00, j02, dy_w, j10, j12, dz_t, dz_w, j20, j22, ds2_w);
+    if (MoveCov) cov_jct<R>(s.C, j00, j02, dy_w, j10, j12, dz_t, dz_w, j20, j22, ds2_w);
     add_comp(ys, ys_lo, dx * tn);
     s.p[0] = ys;
     s.lo[0] = ys_lo;
@@ -226,6 +228,203 @@ __device__ __forceinline__ bool kf_move(KFT<R>& s, double x_to, int to, const Ge
         s.frame = to;
     }
     return true;
+}
+
+// The update with the covariance step in FP64: the transport J C J^T of
+// the preceding move (when mj carries it) and the update itself, the state
+// increment applied in FP64 to the compensated state.  Returns the
+// predicted-residual chi2 term.
+__device__ __forceinline__ float kf_update_cov_d(KF& s, float my, float mz, float sy2, float sz2,
+                                                 const MoveJ* mj) {
+    double Cd[15];
+    if (mj && mj->valid) {
+#pragma unroll
+        for (int i = 0; i < 15; ++i) Cd[i] = mj->Cpre[i];
+        cov_jct<double>(Cd, mj->j00, mj->j02, mj->j04, mj->j10, mj->j12, mj->j13, mj->j14, mj->j20,
+                        mj->j22, mj->j24);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 15; ++i) Cd[i] = s.C[i];
+    }
+    const double dr0 = (double)my - ((double)s.p[0] + (double)s.lo[0]);
+    const double dr1 = (double)mz - ((double)s.p[1] + (double)s.lo[1]);
+    const double D00 = Cd[0] + (double)sy2, D01 = Cd[1], D11 = Cd[5] + (double)sz2;
+    const double ddet = D00 * D11 - D01 * D01;
+    const double e00 = D11 / ddet, e01 = -D01 / ddet, e11 = D00 / ddet;
+    double c0[5], c1[5], k0[5], k1[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        c0[i] = Cd[sx(0, i)];
+        c1[i] = Cd[sx(1, i)];
+        k0[i] = c0[i] * e00 + c1[i] * e01;
+        k1[i] = c0[i] * e01 + c1[i] * e11;
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const double v = (double)s.p[i] + (double)s.lo[i] + k0[i] * dr0 + k1[i] * dr1;
+        s.p[i] = (float)v;
+        s.lo[i] = (float)(v - (double)s.p[i]);
+    }
+#pragma unroll
+    for (int i = 3; i < 5; ++i) s.p[i] = (float)((double)s.p[i] + k0[i] * dr0 + k1[i] * dr1);
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+#pragma unroll
+        for (int j = i; j < 5; ++j)
+            s.C[sx(i, j)] = (float)(Cd[sx(i, j)] - (k0[i] * c0[j] + k1[i] * c1[j]));
+    return (float)(dr0 * dr0 * e00 + 2.0 * dr0 * dr1 * e01 + dr1 * dr1 * e11);
+}
+
+// Update with a covariance carried in FP64 across the whole fit (Cd, the
+// covariance of the FP32 state s): FP64 gain and covariance step, the state
+// increment applied in FP64 to the compensated state.  Returns the
+// predicted-residual chi2 term.
+__device__ __forceinline__ double kf_update_dcov(KF& s, double Cd[15], float my, float mz, double sy2,
+                                                 double sz2) {
+    const double dr0 = (double)my - ((double)s.p[0] + (double)s.lo[0]);
+    const double dr1 = (double)mz - ((double)s.p[1] + (double)s.lo[1]);
+    const double D00 = Cd[0] + sy2, D01 = Cd[1], D11 = Cd[5] + sz2;
+    const double idet = 1.0 / (D00 * D11 - D01 * D01);
+    const double e00 = D11 * idet, e01 = -D01 * idet, e11 = D00 * idet;
+    double c0[5], c1[5], k0[5], k1[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        c0[i] = Cd[sx(0, i)];
+        c1[i] = Cd[sx(1, i)];
+        k0[i] = c0[i] * e00 + c1[i] * e01;
+        k1[i] = c0[i] * e01 + c1[i] * e11;
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const double v = (double)s.p[i] + (double)s.lo[i] + k0[i] * dr0 + k1[i] * dr1;
+        s.p[i] = (float)v;
+        s.lo[i] = (float)(v - (double)s.p[i]);
+    }
+#pragma unroll
+    for (int i = 3; i < 5; ++i) s.p[i] = (float)((double)s.p[i] + k0[i] * dr0 + k1[i] * dr1);
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+#pragma unroll
+        for (int j = i; j < 5; ++j) Cd[sx(i, j)] -= k0[i] * c0[j] + k1[i] * c1[j];
+    return dr0 * dr0 * e00 + 2.0 * dr0 * dr1 * e01 + dr1 * dr1 * e11;
+}
+
+// ---- float-float covariance --------------------------------------------
+// A covariance entry as an unevaluated sum hi + lo of two FP32 numbers
+// (about 48 significant bits), updated with error-free transformations:
+// TwoSum (Knuth) for sums and TwoProduct through the fused multiply-add for
+// products.  Every operation is an explicitly rounded intrinsic, so the
+// compiler cannot contract them into other fused operations.  The Kalman update C - K H C cancels by orders of magnitude once
+// a track is well measured; FP32 storage loses the small directions there,
+// while GB300's FP64 rate is a small fraction of its FP32 rate.
+struct ff {
+    float hi, lo;
+};
+__device__ __forceinline__ ff ff_from(float a) { return ff{a, 0.f}; }
+// a + b exactly as s + e (Knuth's TwoSum)
+__device__ __forceinline__ ff two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float v = __fsub_rn(s, a);
+    return ff{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, v)), __fsub_rn(b, v))};
+}
+// a + b = s + e for |a| >= |b| (Dekker's FastTwoSum)
+__device__ __forceinline__ ff fast_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return ff{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+// x + y (the lo parts added in FP32, then renormalised)
+__device__ __forceinline__ ff ff_add(ff x, ff y) {
+    ff s = two_sum(x.hi, y.hi);
+    s.lo = __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo));
+    return fast_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ ff ff_neg(ff x) { return ff{-x.hi, -x.lo}; }
+// x * f for an FP32 f: TwoProduct of the hi part (exact through the FMA)
+__device__ __forceinline__ ff ff_mul_f(ff x, float f) {
+    const float p = __fmul_rn(x.hi, f);
+    const float e = __fmaf_rn(x.lo, f, __fmaf_rn(x.hi, f, -p));
+    return fast_two_sum(p, e);
+}
+__device__ __forceinline__ ff ff_mul(ff x, ff y) {
+    const float p = __fmul_rn(x.hi, y.hi);
+    float e = __fmaf_rn(x.hi, y.hi, -p);
+    e = __fmaf_rn(x.hi, y.lo, e);
+    e = __fmaf_rn(x.lo, y.hi, e);
+    return fast_two_sum(p, e);
+}
+// 1 / x: an FP32 reciprocal refined by one Newton step r + r (1 - x r)
+// carried in float-float
+__device__ __forceinline__ ff ff_rcp(ff x) {
+    const float r = __frcp_rn(x.hi);
+    const ff xr = ff_mul_f(x, r);
+    const ff one_minus = ff_add(ff_from(1.f), ff_neg(xr));
+    return ff_add(ff_from(r), ff_mul_f(one_minus, r));
+}
+// acc + x * f
+__device__ __forceinline__ ff ff_fma_f(ff acc, ff x, float f) { return ff_add(acc, ff_mul_f(x, f)); }
+
+// Covariance transform C <- J C J^T in float-float for the Jacobian of
+// cov_jct (J exact in FP32).
+__device__ __forceinline__ void cov_jct_ff(ff C[15], float j00, float j02, float j04, float j10,
+                                           float j12, float j13, float j14, float j20, float j22,
+                                           float j24) {
+    ff c[5][5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+#pragma unroll
+        for (int j = 0; j < 5; ++j) c[i][j] = C[sx(i, j)];
+    ff A0[5], A1[5], A2[5];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+        A0[j] = ff_fma_f(ff_fma_f(ff_mul_f(c[0][j], j00), c[2][j], j02), c[4][j], j04);
+        A1[j] = ff_fma_f(ff_fma_f(ff_fma_f(ff_fma_f(c[1][j], c[0][j], j10), c[2][j], j12), c[3][j], j13),
+                         c[4][j], j14);
+        A2[j] = ff_fma_f(ff_fma_f(ff_mul_f(c[0][j], j20), c[2][j], j22), c[4][j], j24);
+    }
+    C[sx(0, 0)] = ff_fma_f(ff_fma_f(ff_mul_f(A0[0], j00), A0[2], j02), A0[4], j04);
+    C[sx(0, 1)] = ff_fma_f(ff_fma_f(ff_fma_f(ff_fma_f(A0[1], A0[0], j10), A0[2], j12), A0[3], j13), A0[4], j14);
+    C[sx(0, 2)] = ff_fma_f(ff_fma_f(ff_mul_f(A0[0], j20), A0[2], j22), A0[4], j24);
+    C[sx(0, 3)] = A0[3];
+    C[sx(0, 4)] = A0[4];
+    C[sx(1, 1)] = ff_fma_f(ff_fma_f(ff_fma_f(ff_fma_f(A1[1], A1[0], j10), A1[2], j12), A1[3], j13), A1[4], j14);
+    C[sx(1, 2)] = ff_fma_f(ff_fma_f(ff_mul_f(A1[0], j20), A1[2], j22), A1[4], j24);
+    C[sx(1, 3)] = A1[3];
+    C[sx(1, 4)] = A1[4];
+    C[sx(2, 2)] = ff_fma_f(ff_fma_f(ff_mul_f(A2[0], j20), A2[2], j22), A2[4], j24);
+    C[sx(2, 3)] = A2[3];
+    C[sx(2, 4)] = A2[4];
+}
+
+// Kalman update with the covariance in float-float: S, its inverse, the
+// gain and C - K H C in float-float; the state increment from the gain in
+// FP32 on the compensated state.  Returns the predicted-residual chi2 term.
+__device__ __forceinline__ float kf_update_ff(KF& s, ff C[15], float my, float mz, float sy2, float sz2) {
+    const float r0 = (my - s.p[0]) - s.lo[0], r1 = (mz - s.p[1]) - s.lo[1];
+    const ff S00 = ff_add(C[0], ff_from(sy2)), S01 = C[1], S11 = ff_add(C[5], ff_from(sz2));
+    const ff det = ff_add(ff_mul(S00, S11), ff_neg(ff_mul(S01, S01)));
+    const ff idet = ff_rcp(det);
+    const ff i00 = ff_mul(S11, idet), i01 = ff_neg(ff_mul(S01, idet)), i11 = ff_mul(S00, idet);
+    ff C0[5], C1[5], K0[5], K1[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        C0[i] = C[sx(0, i)];
+        C1[i] = C[sx(1, i)];
+    }
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        K0[i] = ff_add(ff_mul(C0[i], i00), ff_mul(C1[i], i01));
+        K1[i] = ff_add(ff_mul(C0[i], i01), ff_mul(C1[i], i11));
+    }
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+#pragma unroll
+        for (int j = i; j < 5; ++j)
+            C[sx(i, j)] = ff_add(C[sx(i, j)], ff_neg(ff_add(ff_mul(K0[i], C0[j]), ff_mul(K1[i], C1[j]))));
+#pragma unroll
+    for (int i = 0; i < 3; ++i) add_comp(s.p[i], s.lo[i], K0[i].hi * r0 + K1[i].hi * r1);
+#pragma unroll
+    for (int i = 3; i < 5; ++i) s.p[i] += K0[i].hi * r0 + K1[i].hi * r1;
+    return r0 * r0 * i00.hi + 2.f * r0 * r1 * i01.hi + r1 * r1 * i11.hi;
 }
 
 // Kalman update with cluster (my, mz): S = C_yz + R, K = C H^T S^-1,
@@ -271,51 +470,15 @@ __device__ __forceinline__ float kf_update(KF& s, float my, float mz, float sy2,
     }
     // FP64 redo of the covariance step
     if (n_fp64) atomicAdd(n_fp64, 1);
-    double Cd[15];
-    if (mj && mj->valid) {
-#pragma unroll
-        for (int i = 0; i < 15; ++i) Cd[i] = mj->Cpre[i];
-        cov_jct<double>(Cd, mj->j00, mj->j02, mj->j04, mj->j10, mj->j12, mj->j13, mj->j14, mj->j20,
-                        mj->j22, mj->j24);
-    } else {
-#pragma unroll
-        for (int i = 0; i < 15; ++i) Cd[i] = s.C[i];
-    }
-    const double dr0 = (double)my - ((double)s.p[0] + (double)s.lo[0]);
-    const double dr1 = (double)mz - ((double)s.p[1] + (double)s.lo[1]);
-    const double D00 = Cd[0] + (double)sy2, D01 = Cd[1], D11 = Cd[5] + (double)sz2;
-    const double ddet = D00 * D11 - D01 * D01;
-    const double e00 = D11 / ddet, e01 = -D01 / ddet, e11 = D00 / ddet;
-    double c0[5], c1[5], k0[5], k1[5];
-#pragma unroll
-    for (int i = 0; i < 5; ++i) {
-        c0[i] = Cd[sx(0, i)];
-        c1[i] = Cd[sx(1, i)];
-        k0[i] = c0[i] * e00 + c1[i] * e01;
-        k1[i] = c0[i] * e01 + c1[i] * e11;
-    }
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        const double v = (double)s.p[i] + (double)s.lo[i] + k0[i] * dr0 + k1[i] * dr1;
-        s.p[i] = (float)v;
-        s.lo[i] = (float)(v - (double)s.p[i]);
-    }
-#pragma unroll
-    for (int i = 3; i < 5; ++i) s.p[i] = (float)((double)s.p[i] + k0[i] * dr0 + k1[i] * dr1);
-#pragma unroll
-    for (int i = 0; i < 5; ++i)
-#pragma unroll
-        for (int j = i; j < 5; ++j)
-            s.C[sx(i, j)] = (float)(Cd[sx(i, j)] - (k0[i] * c0[j] + k1[i] * c1[j]));
-    return (float)(dr0 * dr0 * e00 + 2.0 * dr0 * dr1 * e01 + dr1 * dr1 * e11);
+    return kf_update_cov_d(s, my, mz, sy2, sz2, mj);
 }
 
 // Plain FP64 update (used when a whole track is refit in FP64).
 __device__ __forceinline__ double kf_update_d(KFD& s, double my, double mz, double sy2, double sz2) {
     const double r0 = my - (s.p[0] + s.lo[0]), r1 = mz - (s.p[1] + s.lo[1]);
     const double S00 = s.C[0] + sy2, S01 = s.C[1], S11 = s.C[5] + sz2;
-    const double det = S00 * S11 - S01 * S01;
-    const double i00 = S11 / det, i01 = -S01 / det, i11 = S00 / det;
+    const double idet = 1.0 / (S00 * S11 - S01 * S01);
+    const double i00 = S11 * idet, i01 = -S01 * idet, i11 = S00 * idet;
     double C0[5], C1[5], K0[5], K1[5];
 #pragma unroll
     for (int i = 0; i < 5; ++i) {

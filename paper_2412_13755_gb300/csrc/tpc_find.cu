@@ -945,7 +945,8 @@ __global__ void k_owner(const int32_t* __restrict__ tl_rowhit, const unsigned lo
 }
 
 // keep tracklets owning >= n_seg clusters (hits they do not own are
-// cleared); the refits of the kept ones run in k_tracklet_lanes
+// cleared); the refits of the kept ones run in k_tracklet_lanes.  One warp
+// per slot, the lanes over the rows.
 __global__ void k_keep(int32_t* tl_rowhit, const unsigned long long* __restrict__ tl_key,
                        const unsigned long long* __restrict__ owner, const int32_t* __restrict__ seg_grp,
                        const float* __restrict__ zb, const int32_t* __restrict__ orig, int n_seg,
@@ -954,23 +955,36 @@ __global__ void k_keep(int32_t* tl_rowhit, const unsigned long long* __restrict_
                        int32_t* tl_ok, int32_t* grp_tl_cnt, TlBins tb, int32_t* tl_binkey,
                        int64_t KT) {
     const int nseg = min((int64_t)st[ST_NSEG], Scap);
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nseg; s += gridDim.x * blockDim.x) {
-        int32_t* hit = tl_rowhit + (int64_t)s * NROW;
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t s = w0; s < nseg; s += nw) {
+        int32_t* hit = tl_rowhit + s * NROW;
         const unsigned long long key = tl_key[s];
         int n = 0, rmin = NROW, rmax = -1;
         int32_t canon = 0x7fffffff;
-        for (int r = 0; r < NROW; ++r) {
-            const int h = hit[r];
-            if (h < 0) continue;
-            if (owner[h] != key) {
-                hit[r] = -1;
-                continue;
+        for (int r0 = 0; r0 < NROW; r0 += 32) {
+            const int r = r0 + lane;
+            bool own = false;
+            if (r < NROW) {
+                const int h = hit[r];
+                if (h >= 0) {
+                    if (owner[h] != key) hit[r] = -1;
+                    else {
+                        own = true;
+                        canon = min(canon, orig[h]);
+                    }
+                }
             }
-            ++n;
-            rmin = min(rmin, r);
-            rmax = max(rmax, r);
-            canon = min(canon, orig[h]);
+            const unsigned m = __ballot_sync(0xffffffffu, own);
+            if (m) {
+                n += __popc(m);
+                rmin = min(rmin, r0 + __ffs(m) - 1);
+                rmax = max(rmax, r0 + 31 - __clz(m));
+            }
         }
+        canon = __reduce_min_sync(0xffffffffu, canon);
+        if (lane != 0) continue;
         tl_ok[s] = 0;
         if (n < n_seg) {
             tl_keep[s] = 0;
@@ -1168,18 +1182,55 @@ __global__ void __launch_bounds__(1024) k_match(
     const int32_t* __restrict__ cand_n, const int32_t* __restrict__ cand_a,
     const float* __restrict__ cand_c2, const int32_t* __restrict__ tl_canon, int64_t Scap,
     int32_t* st, unsigned long long* best_a, unsigned long long* best_b, int32_t* nxt,
-    int32_t* prv) {
-    __shared__ int live;
+    int32_t* prv, int32_t* act) {
+    // Rounds of locally dominant candidates: an (a, b) pair whose key
+    // (chi2, canonical ids) is the smallest of every live pair at a and of
+    // every live pair at b is matched; both ends are then used.  The rounds
+    // run over a compacted list of the B ends that still have a live
+    // candidate; best_a / best_b hold KEY_MAX between rounds.
+    __shared__ int n_act, n_next, live;
+    __shared__ int32_t wsum[32];
     const int nseg = min((int64_t)st[ST_NSEG], Scap);
-    for (int round = 0; round < 4096; ++round) {
-        if (threadIdx.x == 0) live = 0;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    // B ends with candidates (prv is -1 for all before the first round)
+    if (threadIdx.x == 0) n_act = 0;
+    __syncthreads();
+    for (int b0 = 0; b0 < nseg; b0 += blockDim.x) {
+        const int b = b0 + threadIdx.x;
+        const bool has = b < nseg && cand_n[b] > 0;
+        const unsigned m = __ballot_sync(0xffffffffu, has);
+        if (lane == 0) wsum[wid] = __popc(m);
         __syncthreads();
-        for (int b = threadIdx.x; b < nseg; b += blockDim.x) {
+        if (threadIdx.x == 0) {
+            int o = n_act;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+                const int c = wsum[w];
+                wsum[w] = o;
+                o += c;
+            }
+            n_act = o;
+        }
+        __syncthreads();
+        if (has) act[wsum[wid] + __popc(m & ((1u << lane) - 1u))] = b;
+        __syncthreads();
+    }
+    int32_t* cur = act;
+    int32_t* nx = act + Scap;
+    for (int round = 0; round < 4096; ++round) {
+        const int na = n_act;
+        if (na == 0) break;
+        if (threadIdx.x == 0) {
+            live = 0;
+            n_next = 0;
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < na; i += blockDim.x) {
+            const int b = cur[i];
             if (prv[b] >= 0) continue;
-            for (int i = 0; i < cand_n[b]; ++i) {
-                const int a = cand_a[(int64_t)b * MAX_CAND + i];
+            for (int k = 0; k < cand_n[b]; ++k) {
+                const int a = cand_a[(int64_t)b * MAX_CAND + k];
                 if (nxt[a] >= 0) continue;
-                const uint64_t c2 = __float_as_uint(cand_c2[(int64_t)b * MAX_CAND + i]);
+                const uint64_t c2 = __float_as_uint(cand_c2[(int64_t)b * MAX_CAND + k]);
                 atomicMin(&best_a[a], (c2 << 32) | (uint32_t)tl_canon[b]);
                 atomicMin(&best_b[b], (c2 << 32) | (uint32_t)tl_canon[a]);
                 live = 1;
@@ -1187,12 +1238,13 @@ __global__ void __launch_bounds__(1024) k_match(
         }
         __syncthreads();
         if (!live) break;
-        for (int b = threadIdx.x; b < nseg; b += blockDim.x) {
+        for (int i = threadIdx.x; i < na; i += blockDim.x) {
+            const int b = cur[i];
             if (prv[b] >= 0) continue;
-            for (int i = 0; i < cand_n[b]; ++i) {
-                const int a = cand_a[(int64_t)b * MAX_CAND + i];
+            for (int k = 0; k < cand_n[b]; ++k) {
+                const int a = cand_a[(int64_t)b * MAX_CAND + k];
                 if (nxt[a] >= 0) continue;
-                const uint64_t c2 = __float_as_uint(cand_c2[(int64_t)b * MAX_CAND + i]);
+                const uint64_t c2 = __float_as_uint(cand_c2[(int64_t)b * MAX_CAND + k]);
                 if (best_a[a] == ((c2 << 32) | (uint32_t)tl_canon[b]) &&
                     best_b[b] == ((c2 << 32) | (uint32_t)tl_canon[a])) {
                     nxt[a] = b;
@@ -1202,35 +1254,54 @@ __global__ void __launch_bounds__(1024) k_match(
             }
         }
         __syncthreads();
-        for (int b = threadIdx.x; b < nseg; b += blockDim.x) {
+        // reset the keys that were touched; keep the B ends still unmatched
+        for (int i = threadIdx.x; i < na; i += blockDim.x) {
+            const int b = cur[i];
             best_b[b] = KEY_MAX;
-            best_a[b] = KEY_MAX;
+            bool keep = false;
+            for (int k = 0; k < cand_n[b]; ++k) {
+                const int a = cand_a[(int64_t)b * MAX_CAND + k];
+                best_a[a] = KEY_MAX;
+                keep |= nxt[a] < 0;
+            }
+            if (keep && prv[b] < 0) nx[atomicAdd(&n_next, 1)] = b;
         }
+        __syncthreads();
+        if (threadIdx.x == 0) n_act = n_next;
+        int32_t* t = cur;
+        cur = nx;
+        nx = t;
         __syncthreads();
     }
 }
 
 // ---------------------------------------------------------------- output --
 // Chains of merged tracklets (walk from the outermost, i.e. nxt < 0).
+// One warp per track head (the outermost kept tracklet of a merge chain,
+// nxt < 0): length and canonical id (smallest input index) of the chain.
 __global__ void k_track_heads(const int32_t* __restrict__ tl_keep, const int32_t* __restrict__ nxt,
                               const int32_t* __restrict__ prv, const int32_t* __restrict__ tl_canon,
                               const int32_t* __restrict__ tl_rowhit, int n_min, int64_t Scap,
                               const int32_t* st, int32_t* trk_flag, int32_t* trk_len_at,
                               int32_t* trk_head_at) {
     const int nseg = min((int64_t)st[ST_NSEG], Scap);
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nseg; s += gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t s = w0; s < nseg; s += nw) {
         if (!tl_keep[s] || nxt[s] >= 0) continue;
         int len = 0, guard = 0;
         int32_t canon = 0x7fffffff;
-        for (int t = s; t >= 0 && guard < 4096; t = prv[t], ++guard) {
+        for (int t = (int)s; t >= 0 && guard < 4096; t = prv[t], ++guard) {
             const int32_t* hit = tl_rowhit + (int64_t)t * NROW;
-            for (int r = 0; r < NROW; ++r) len += hit[r] >= 0;
+            for (int r0 = 0; r0 < NROW; r0 += 32)
+                len += __popc(__ballot_sync(0xffffffffu, r0 + lane < NROW && hit[r0 + lane] >= 0));
             canon = min(canon, tl_canon[t]);
         }
-        if (len < n_min) continue;
+        if (len < n_min || lane != 0) continue;
         trk_flag[canon] = 1;
         trk_len_at[canon] = len;
-        trk_head_at[canon] = s;
+        trk_head_at[canon] = (int32_t)s;
     }
 }
 
@@ -1251,30 +1322,40 @@ __global__ void k_track_len(int64_t n, const int32_t* __restrict__ trk_flag,
     }
 }
 
+// One warp per output track: the hits of its chain of tracklets, outermost
+// first, in the track's slice of the CSR, and the track index per cluster.
 __global__ void k_track_write(int64_t n, const int32_t* __restrict__ trk_flag,
                               const int32_t* __restrict__ trk_rank,
                               const int32_t* __restrict__ trk_head_at, const int32_t* __restrict__ prv,
                               const int32_t* __restrict__ tl_rowhit, const int32_t* __restrict__ orig,
                               const int32_t* __restrict__ trk_off, int32_t track_cap, int32_t* toc,
                               int32_t* trk_hits, int32_t* st_w) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = w0; i < n; i += nw) {
         if (!trk_flag[i]) continue;
         const int r = trk_rank[i];
         if (r >= track_cap) continue;
         int o = trk_off[r], guard = 0;
         for (int t = trk_head_at[i]; t >= 0 && guard < 4096; t = prv[t], ++guard) {
             const int32_t* hit = tl_rowhit + (int64_t)t * NROW;
-            for (int rr = NROW - 1; rr >= 0; --rr) {
-                const int h = hit[rr];
-                if (h < 0) continue;
-                const int oi = orig[h];
-                if (o >= n) {
-                    set_status(st_w, TPC_ERR_STATE, 401);
-                    break;
+            // rows from the outermost down, 32 at a time
+            for (int r0 = NROW - 1; r0 >= 0; r0 -= 32) {
+                const int rr = r0 - lane;
+                const int h = rr >= 0 ? hit[rr] : -1;
+                const unsigned m = __ballot_sync(0xffffffffu, h >= 0);
+                if (h >= 0) {
+                    const int pos = o + __popc(m & ((1u << lane) - 1u));
+                    if (pos < n) {
+                        const int oi = orig[h];
+                        trk_hits[pos] = oi;
+                        toc[oi] = r;
+                    } else {
+                        set_status(st_w, TPC_ERR_STATE, 401);
+                    }
                 }
-                trk_hits[o++] = oi;
-                toc[oi] = r;
+                o += __popc(m);
             }
         }
     }
@@ -1418,7 +1499,7 @@ cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hi
                                                    W.at<float>(L.tb_inv), W.at<int32_t>(L.tb_nb),
                                                    W.at<int32_t>(L.tb_base));
     TPC_TRY(fill_i32(grp_cnt, L.KT + 1, 0, s));
-    tpc::LaunchCount{}, k_keep<<<sgrid, 128, 0, s>>>(tl_rowhit, tl_key, owner, W.at<int32_t>(L.seg_grp), zb,
+    tpc::LaunchCount{}, k_keep<<<grid_for(L.S * 32, 128), 128, 0, s>>>(tl_rowhit, tl_key, owner, W.at<int32_t>(L.seg_grp), zb,
                                  orig, p.n_seg, L.S, st, W.at<int32_t>(L.tl_keep),
                                  W.at<int32_t>(L.tl_canon), W.at<int32_t>(L.tl_rmin),
                                  W.at<int32_t>(L.tl_rmax), W.at<float>(L.tl_zin),
@@ -1459,12 +1540,13 @@ cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hi
     tpc::LaunchCount{}, k_fill_u64<<<grid_for(L.S), TPB, 0, s>>>(best_a, L.S, KEY_MAX);
     tpc::LaunchCount{}, k_fill_u64<<<grid_for(L.S), TPB, 0, s>>>(best_b, L.S, KEY_MAX);
     tpc::LaunchCount{}, k_match<<<1, 1024, 0, s>>>(W.at<int32_t>(L.cand_n), W.at<int32_t>(L.cand_a), W.at<float>(L.cand_c2),
-                               W.at<int32_t>(L.tl_canon), L.S, st, best_a, best_b, nxt, prv);
+                               W.at<int32_t>(L.tl_canon), L.S, st, best_a, best_b, nxt, prv,
+                               W.at<int32_t>(L.match_act));
     c->mark(8, s);
     // output: canonical order by smallest input index
     int32_t* flag = W.at<int32_t>(L.trk_flag);
     TPC_TRY(fill_i32(flag, n, 0, s));
-    tpc::LaunchCount{}, k_track_heads<<<sgrid, 128, 0, s>>>(W.at<int32_t>(L.tl_keep), nxt, prv, W.at<int32_t>(L.tl_canon),
+    tpc::LaunchCount{}, k_track_heads<<<grid_for(L.S * 32, 128), 128, 0, s>>>(W.at<int32_t>(L.tl_keep), nxt, prv, W.at<int32_t>(L.tl_canon),
                                         tl_rowhit, p.n_min, L.S, st, flag, W.at<int32_t>(L.trk_len_at),
                                         W.at<int32_t>(L.trk_head_at));
     int32_t* rank = W.at<int32_t>(L.trk_rank);
@@ -1475,7 +1557,7 @@ cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hi
                                             len_by_rank, st, n_tracks_dev);
     TPC_TRY(scan_i32(len_by_rank, trk_off, track_cap, scan_tmp, s));
     TPC_TRY(fill_i32(toc, n, -1, s));
-    tpc::LaunchCount{}, k_track_write<<<grid_for(n), TPB, 0, s>>>(n, flag, rank, W.at<int32_t>(L.trk_head_at), prv,
+    tpc::LaunchCount{}, k_track_write<<<grid_for(n * 32), TPB, 0, s>>>(n, flag, rank, W.at<int32_t>(L.trk_head_at), prv,
                                               tl_rowhit, orig, trk_off, track_cap, toc, trk_hits, st);
     c->mark(9, s);
     return cudaGetLastError();

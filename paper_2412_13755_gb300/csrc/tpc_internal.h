@@ -39,7 +39,7 @@ struct Geo {
 // Device status word and counters (int32 slots in the workspace).
 enum StatusSlot {
     ST_STATUS = 0, ST_DETAIL, ST_NSEG, ST_NTL, ST_NCAND, ST_NMERGE, ST_NTRACKS, ST_FP64,
-    ST_MATCH_LIVE, ST_Q_BUILD, ST_Q_REFIT, ST_NREFIT, ST_KFSTEPS = 12 /* 64-bit: slots 12-13 */,
+    ST_MATCH_LIVE, ST_Q_BUILD, ST_Q_REFIT, ST_SPARE11, ST_KFSTEPS = 12 /* 64-bit: slots 12-13 */,
     ST_NB_OVF = 14, ST_N_SLOTS = 16
 };
 
@@ -60,7 +60,7 @@ struct Layout {
         claim_dn, link_dn, link_up, owner, seg_start, seg_perm, seg_grp, seg_canon, tl_rowhit,
         tl_n, tl_key, tl_keep, tl_canon, tl_rmin, tl_rmax, tl_zin, tl_zout, tl_state, tl_ok,
         grp_tl_cnt, grp_tl_off, grp_tl_cur, tl_sorted, gs_meta, tl_binkey, tb_zmin, tb_inv, tb_nb, tb_base, cand_n, cand_a, cand_c2, best_a, best_b,
-        nxt, prv, refit, trk_flag, trk_rank, trk_len_at, trk_head_at, len_by_rank, scan_a, scan_b,
+        nxt, prv, match_act, trk_flag, trk_rank, trk_len_at, trk_head_at, len_by_rank, scan_a, scan_b,
         adj_grad, adj_chi2, adj_ckpt;
     int64_t adj_tracks = 0;  // tracks the adjoint scratch holds per launch chunk
 };

@@ -90,6 +90,26 @@ def test_fit_parity_truth_tracks(orc):
     assert np.array_equal(ndf.cpu().numpy()[ok], ondf[ok])
 
 
+def test_fit_parity_found_tracks(orc):
+    """The fit of every track the pipeline finds in a noisy event (fakes and
+    low-pT tracks included) against the FP64 oracle on the same hit lists."""
+    ev = synth.central_event(n_tracks=2000, seed=101)
+    toc, off, hits, st, tr = gpu_find(ev)
+    T = len(off) - 1
+    par, cov, chi2, ndf = tr.fit(torch.from_numpy(off.astype(np.int32)).cuda(),
+                                 torch.from_numpy(hits.astype(np.int32)).cuda(), T)
+    torch.cuda.synchronize()
+    tr.check()
+    opar, ocov, ochi2, ondf = orc.fit_tracks(ev.y, ev.z, ev.row, ev.sector_of_cluster(), off, hits)
+    gndf = ndf.cpu().numpy()
+    # transport failures agree
+    assert np.array_equal(gndf <= 0, ondf <= 0)
+    ok = ondf > 0
+    rel = np.abs(par.cpu().numpy().astype(np.float64) - opar) / np.maximum(np.abs(opar), SCALE)
+    print(f"{T} tracks, max relative error per parameter {rel[ok].max(0)}")
+    assert np.all(rel[ok] <= 1e-5), rel[ok].max(0)
+
+
 def test_empty_input():
     tr = tpc.Tracker(16, 1)
     y = torch.zeros(0, device="cuda")
