@@ -18,7 +18,7 @@ Layout make_layout(int64_t N, int32_t E) {
     L.N = N;
     L.E = E;
     L.G = (int64_t)E * NSEC;
-    L.K = (int64_t)NROW * L.G + N / CELL_OCC + 16;
+    L.K = (int64_t)NROW * CELL_NY * L.G + N / CELL_OCC + 16;
     L.S = N / 16 + 4096;
     L.T = N + 1;
     L.KT = L.G + N / 64 + 16;

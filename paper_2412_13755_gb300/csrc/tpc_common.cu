@@ -146,6 +146,8 @@ cudaError_t init_geo(const Workspace& ws, cudaStream_t s) {
         g.row_xf[r] = (float)g.row_xd[r];
     }
     g.tan_half = (float)std::tan(10.0 * pi / 180.0);
+    for (int r = 0; r < NROW; ++r)
+        g.ycell_inv[r] = (float)(CELL_NY / (2.0 * g.row_xd[r] * std::tan(10.0 * pi / 180.0)));
     g.tan_half_d = std::tan(10.0 * pi / 180.0);
     for (int i = 0; i < NPHI; ++i) g.alpha[i] = (i + 0.5) * (20.0 * pi / 180.0);
     for (int k = 0; k < NPHI; ++k) {

@@ -69,6 +69,36 @@ __device__ __forceinline__ int zcell(const Cells& c, int g, float z) {
     return k < nz - 1 ? k : nz - 1;
 }
 
+// y cell of row r: uniform in y / (x_r tan 10 deg) over the acceptance,
+// clamped (monotone in y)
+__device__ __forceinline__ int ycell(const Geo* __restrict__ geo, int r, float y) {
+    const float f = y * geo->ycell_inv[r] + 0.5f * CELL_NY;
+    const int k = f >= 0.f ? (int)f : 0;
+    return k < CELL_NY - 1 ? k : CELL_NY - 1;
+}
+
+// The cells of row r (group g) covering z in [zlo, zhi] and y in [ylo, yhi]:
+// one contiguous run of binned clusters per z cell,
+// [off[base + iz * CELL_NY + iy0], off[base + iz * CELL_NY + iy1 + 1]) for
+// iz0 <= iz <= iz1.
+struct CellWin {
+    int base, iz0, iz1, iy0, iy1;
+};
+__device__ __forceinline__ CellWin cell_win(const Cells& cells, const Geo* __restrict__ geo, int g, int r,
+                                            float zlo, float zhi, float ylo, float yhi) {
+    CellWin w;
+    w.base = cells.kbase[g] + r * cells.nz[g] * CELL_NY;
+    w.iz0 = zcell(cells, g, zlo);
+    w.iz1 = zcell(cells, g, zhi);
+    w.iy0 = ycell(geo, r, ylo);
+    w.iy1 = ycell(geo, r, yhi);
+    return w;
+}
+__device__ __forceinline__ void cell_run(const Cells& cells, const CellWin& w, int iz, int& b, int& e) {
+    b = cells.off[w.base + iz * CELL_NY + w.iy0];
+    e = cells.off[w.base + iz * CELL_NY + w.iy1 + 1];
+}
+
 // ---------------------------------------------------------------- S1 ------
 __global__ void k_zrange(const float* __restrict__ z, int64_t n, const int64_t* __restrict__ off,
                          int G, uint32_t* zmin_u, uint32_t* zmax_u) {
@@ -102,7 +132,7 @@ __global__ void __launch_bounds__(1024) k_cells(const int64_t* __restrict__ off,
         int32_t cnt = 0;
         if (g < G) {
             const int64_t ng = off[g + 1] - off[g];
-            int64_t k = ng / (NROW * CELL_OCC);
+            int64_t k = ng / (NROW * CELL_OCC * CELL_NY);
             k = k < 1 ? 1 : (k > NZ_MAX ? NZ_MAX : k);
             float lo = 0.f, hi = 0.f;
             if (ng > 0) {
@@ -113,7 +143,7 @@ __global__ void __launch_bounds__(1024) k_cells(const int64_t* __restrict__ off,
             zmin[g] = lo;
             inv[g] = w > 0.f ? (float)k / w : 0.f;
             nz[g] = (int32_t)k;
-            cnt = (int32_t)(NROW * k);
+            cnt = (int32_t)(NROW * CELL_NY * k);
         }
         // block exclusive scan of cnt
         const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -204,14 +234,15 @@ __global__ void __launch_bounds__(1024) k_tl_bins(const int64_t* __restrict__ of
     if (threadIdx.x == 0) base[G] = (int32_t)carry_s;
 }
 
-__global__ void k_hist(const float* __restrict__ z, const uint16_t* __restrict__ row, int64_t n,
-                       const int64_t* __restrict__ off, int G, Cells cells, int32_t* cnt,
-                       int32_t* key_in, int32_t* slot_in, int64_t Kcap) {
+__global__ void k_hist(const float* __restrict__ y, const float* __restrict__ z,
+                       const uint16_t* __restrict__ row, int64_t n,
+                       const int64_t* __restrict__ off, int G, Cells cells, const Geo* __restrict__ geo,
+                       int32_t* cnt, int32_t* key_in, int32_t* slot_in, int64_t Kcap) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int g = group_of(off, G, i);
         const int r = row[i];
-        const int key = cells.kbase[g] + r * cells.nz[g] + zcell(cells, g, z[i]);
+        const int key = cells.kbase[g] + (r * cells.nz[g] + zcell(cells, g, z[i])) * CELL_NY + ycell(geo, r, y[i]);
         int slot = 0;
         if (key < Kcap) slot = atomicAdd(&cnt[key], 1);
         key_in[i] = key;
@@ -267,14 +298,15 @@ __device__ __forceinline__ float triplet_d2(float xd, float yd, float zd, float 
                      __fdiv_rn(__fmul_rn(rz, rz), __fmul_rn(sz2, f)));
 }
 
-// binned index range of the z cells of row r (group g) covering [zlo, zhi]
-__device__ __forceinline__ void cell_range(const Cells& cells, int g, int r, float zlo, float zhi,
-                                           int& b, int& e) {
-    // zcell clamps to the group's cells, and k_cells has checked that the
-    // groups' cells fit the table: both offsets are inside cell_off
-    const int base = cells.kbase[g] + r * cells.nz[g];
-    b = cells.off[base + zcell(cells, g, zlo)];
-    e = cells.off[base + zcell(cells, g, zhi) + 1];
+// The cells holding every candidate of row rr that can pass in_win for the
+// cluster at (xc, yc, zc): the window half-widths win_y |dx|, win_z |dx|
+// widened by a relative 1e-4 and 1e-3 cm against rounding.
+__device__ __forceinline__ CellWin nb_win(const Cells& cells, const Geo* __restrict__ geo, int g, int rr,
+                                          float xr, float xc, float yc, float zc, const NbPrm& P) {
+    const float dx = fabsf(__fsub_rn(xr, xc));
+    const float wz = __fmul_rn(P.win_z, dx) * 1.0001f + 1e-3f;
+    const float wy = __fmul_rn(P.win_y, dx) * 1.0001f + 1e-3f;
+    return cell_win(cells, geo, g, rr, zc - wz, zc + wz, yc - wy, yc + wy);
 }
 
 // Serial evaluation of one gap pair (gd, gu) for cluster c; the reference
@@ -286,17 +318,20 @@ __device__ void pair_scan_serial(int64_t c, int gd, int gu, const float* __restr
                                  float& bd2) {
     const int rd = r - gd, ru = r + gu;
     const float xd = geo->row_xf[rd], xu = geo->row_xf[ru];
-    const float wzd = __fmul_rn(P.win_z, fabsf(__fsub_rn(xd, xc)));
-    const float wzu = __fmul_rn(P.win_z, fabsf(__fsub_rn(xu, xc)));
-    int db, de, ub, ue;
-    cell_range(cells, g, rd, zc - wzd * 1.0001f - 1e-3f, zc + wzd * 1.0001f + 1e-3f, db, de);
-    cell_range(cells, g, ru, zc - wzu * 1.0001f - 1e-3f, zc + wzu * 1.0001f + 1e-3f, ub, ue);
+    const CellWin wd = nb_win(cells, geo, g, rd, xd, xc, yc, zc, P);
+    const CellWin wu = nb_win(cells, geo, g, ru, xu, xc, yc, zc, P);
     int pd = -1, pu = -1, pod = 0, pou = 0;
     float pd2 = 0.f;
-    for (int d = db; d < de; ++d) {
+    for (int izd = wd.iz0; izd <= wd.iz1; ++izd) {
+      int db, de;
+      cell_run(cells, wd, izd, db, de);
+      for (int d = db; d < de; ++d) {
         const float ydd = yb[d], zdd = zb[d];
         if (!in_win(xc, yc, zc, xd, ydd, zdd, P.win_y, P.win_z)) continue;
-        for (int u = ub; u < ue; ++u) {
+        for (int izu = wu.iz0; izu <= wu.iz1; ++izu) {
+          int ub, ue;
+          cell_run(cells, wu, izu, ub, ue);
+          for (int u = ub; u < ue; ++u) {
             const float yuu = yb[u], zuu = zb[u];
             if (!in_win(xc, yc, zc, xu, yuu, zuu, P.win_y, P.win_z)) continue;
             const float d2 = triplet_d2(xd, ydd, zdd, xc, yc, zc, xu, yuu, zuu, P.sy2, P.sz2);
@@ -309,7 +344,9 @@ __device__ void pair_scan_serial(int64_t c, int gd, int gu, const float* __restr
             if (better) {
                 pd = d; pu = u; pd2 = d2; pod = orig[d]; pou = orig[u];
             }
+          }
         }
+      }
     }
     bd = pd;
     bu = pu;
@@ -333,21 +370,33 @@ struct NbLists {
 // pair in order and reduce to the best pair (smallest D^2, then canonical id
 // of u, then of d).  A cluster whose needed list exceeds NS_CAP entries is
 // queued for the full-warp kernel below, which redoes it.
-constexpr int NG = 8;          // lanes per cluster
+constexpr int NG1 = 8;         // lanes per cluster, first gap pair
+constexpr int NG2 = 8;         // lanes per cluster, later gap pairs
+constexpr int NB_GAP_MAX = 3;  // largest gap of the neighbour search (tpc_params.max_gap <= 3)
 constexpr int NS_CAP = 16;     // list capacity per row offset (<= 254)
-constexpr int NS_WARPS = 8;    // warps per block
+// warps per block of the sub-warp kernel: NG, so that the lists of its
+// 32 clusters per block take the same shared memory for every NG
+template <int NG> __host__ __device__ constexpr int ns_warps() { return NG; }
 struct NsLists {
     float y[6][NS_CAP];
     float z[6][NS_CAP];
     int idx[6][NS_CAP];
 };
-__global__ void __launch_bounds__(NS_WARPS * 32) k_neighbours_sub(
-    int64_t n, const float* __restrict__ yb, const float* __restrict__ zb,
+// Two passes share this kernel: pass 1 (in_queue null) tries only the first
+// gap pair (1, 1) for every cluster and queues the clusters it leaves
+// without a pair in next_queue; pass 2 takes that queue and tries the gap
+// pairs from sum 3 on.  The gap pairs keep their order, so the result is the
+// one of a single pass, while the sub-warps of a warp do similar work.
+template <int NG>
+__global__ void __launch_bounds__(ns_warps<NG>() * 32) k_neighbours_sub(
+    int64_t n, const int32_t* __restrict__ in_queue, int in_slot, int sum_lo, int sum_hi,
+    const float* __restrict__ yb, const float* __restrict__ zb,
     const int32_t* __restrict__ orig, const int32_t* __restrict__ grpb,
     const uint8_t* __restrict__ rowb, Cells cells, const Geo* __restrict__ geo, NbPrm P,
-    int32_t* choice_dn, int32_t* choice_up, float* d2out, int32_t* st, int32_t* ovf_queue) {
+    int32_t* choice_dn, int32_t* choice_up, float* d2out, int32_t* st, int32_t* ovf_queue,
+    int32_t* next_queue, int next_slot) {
     constexpr int GPW = 32 / NG;  // clusters per warp
-    __shared__ NsLists sh_all[NS_WARPS * GPW];
+    __shared__ NsLists sh_all[ns_warps<NG>() * GPW];
     const int lane = threadIdx.x & 31;
     const int gq = lane / NG, li = lane % NG;
     const unsigned gm = ((1u << NG) - 1u) << (gq * NG);
@@ -355,9 +404,11 @@ __global__ void __launch_bounds__(NS_WARPS * 32) k_neighbours_sub(
     NsLists& sh = sh_all[(threadIdx.x >> 5) * GPW + gq];
     const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t c0 = wid * GPW; c0 < n; c0 += nw * GPW) {
-        const int64_t c = c0 + gq;
-        if (c >= n) continue;  // the whole sub-warp leaves together
+    const int64_t nin = in_queue ? (int64_t)st[in_slot] : n;
+    const int sum_end = min(sum_hi, 2 * P.max_gap);
+    for (int64_t c0 = wid * GPW; c0 < nin; c0 += nw * GPW) {
+        if (c0 + gq >= nin) continue;  // the whole sub-warp leaves together
+        const int64_t c = in_queue ? in_queue[c0 + gq] : c0 + gq;
         const int g = grpb[c], r = rowb[c];
         const float xc = geo->row_xf[r], yc = yb[c], zc = zb[c];
         // list k: bit k of `built`; its count (capped at NS_CAP + 1) in bits 8k..8k+7 of `cnts`
@@ -366,7 +417,7 @@ __global__ void __launch_bounds__(NS_WARPS * 32) k_neighbours_sub(
         int bd = -1, bu = -1;
         float bd2 = 0.f;
         bool ovf = false;
-        for (int sum = 2; sum <= 2 * P.max_gap && bd < 0 && !ovf; ++sum) {
+        for (int sum = sum_lo; sum <= sum_end && bd < 0 && !ovf; ++sum) {
             for (int gu = 1; gu <= P.max_gap && bd < 0 && !ovf; ++gu) {
                 const int gd = sum - gu;
                 if (gd < 1 || gd > P.max_gap) continue;
@@ -379,27 +430,29 @@ __global__ void __launch_bounds__(NS_WARPS * 32) k_neighbours_sub(
                     if (built & (1u << k)) continue;
                     const int rr = side == 0 ? rd : ru;
                     const float xr = geo->row_xf[rr];
-                    const float wz = __fmul_rn(P.win_z, fabsf(__fsub_rn(xr, xc)));
-                    int b, e;
-                    cell_range(cells, g, rr, zc - wz * 1.0001f - 1e-3f, zc + wz * 1.0001f + 1e-3f, b, e);
+                    const CellWin w = nb_win(cells, geo, g, rr, xr, xc, yc, zc, P);
                     int cnt = 0;
-                    for (int base = b; base < e; base += NG) {
-                        const int q = base + li;
-                        float yq = 0.f, zq = 0.f;
-                        bool pass = false;
-                        if (q < e) {
-                            yq = yb[q];
-                            zq = zb[q];
-                            pass = in_win(xc, yc, zc, xr, yq, zq, P.win_y, P.win_z);
+                    for (int iz = w.iz0; iz <= w.iz1; ++iz) {
+                        int b, e;
+                        cell_run(cells, w, iz, b, e);
+                        for (int base = b; base < e; base += NG) {
+                            const int q = base + li;
+                            float yq = 0.f, zq = 0.f;
+                            bool pass = false;
+                            if (q < e) {
+                                yq = yb[q];
+                                zq = zb[q];
+                                pass = in_win(xc, yc, zc, xr, yq, zq, P.win_y, P.win_z);
+                            }
+                            const unsigned bal = (__ballot_sync(gm, pass) >> (gq * NG)) & ((1u << NG) - 1u);
+                            const int pos = cnt + __popc(bal & lt);
+                            if (pass && pos < NS_CAP) {
+                                sh.idx[k][pos] = q;
+                                sh.y[k][pos] = yq;
+                                sh.z[k][pos] = zq;
+                            }
+                            cnt += __popc(bal);
                         }
-                        const unsigned bal = (__ballot_sync(gm, pass) >> (gq * NG)) & ((1u << NG) - 1u);
-                        const int pos = cnt + __popc(bal & lt);
-                        if (pass && pos < NS_CAP) {
-                            sh.idx[k][pos] = q;
-                            sh.y[k][pos] = yq;
-                            sh.z[k][pos] = zq;
-                        }
-                        cnt += __popc(bal);
                     }
                     built |= 1u << k;
                     cnts |= (uint64_t)min(cnt, NS_CAP + 1) << (8 * k);
@@ -455,6 +508,8 @@ __global__ void __launch_bounds__(NS_WARPS * 32) k_neighbours_sub(
         if (li == 0) {
             if (ovf) {
                 ovf_queue[atomicAdd(&st[ST_NB_OVF], 1)] = (int32_t)c;
+            } else if (bd < 0 && next_queue && sum_end < 2 * P.max_gap) {
+                next_queue[atomicAdd(&st[next_slot], 1)] = (int32_t)c;  // later gap pairs
             } else {
                 choice_dn[c] = bd;
                 choice_up[c] = bu;
@@ -504,27 +559,29 @@ __global__ void __launch_bounds__(NB_WARPS * 32) k_neighbours_warp(
                     if (built & (1u << k)) continue;
                     const int rr = side == 0 ? rd : ru;
                     const float xr = geo->row_xf[rr];
-                    const float wz = __fmul_rn(P.win_z, fabsf(__fsub_rn(xr, xc)));
-                    int b, e;
-                    cell_range(cells, g, rr, zc - wz * 1.0001f - 1e-3f, zc + wz * 1.0001f + 1e-3f, b, e);
+                    const CellWin w = nb_win(cells, geo, g, rr, xr, xc, yc, zc, P);
                     int cnt = 0;
-                    for (int base = b; base < e; base += 32) {
-                        const int q = base + lane;
-                        float yq = 0.f, zq = 0.f;
-                        bool pass = false;
-                        if (q < e) {
-                            yq = yb[q];
-                            zq = zb[q];
-                            pass = in_win(xc, yc, zc, xr, yq, zq, P.win_y, P.win_z);
+                    for (int iz = w.iz0; iz <= w.iz1; ++iz) {
+                        int b, e;
+                        cell_run(cells, w, iz, b, e);
+                        for (int base = b; base < e; base += 32) {
+                            const int q = base + lane;
+                            float yq = 0.f, zq = 0.f;
+                            bool pass = false;
+                            if (q < e) {
+                                yq = yb[q];
+                                zq = zb[q];
+                                pass = in_win(xc, yc, zc, xr, yq, zq, P.win_y, P.win_z);
+                            }
+                            const unsigned bal = __ballot_sync(0xffffffffu, pass);
+                            const int pos = cnt + __popc(bal & lt);
+                            if (pass && pos < NB_LIST) {
+                                sh.idx[k][pos] = q;
+                                sh.y[k][pos] = yq;
+                                sh.z[k][pos] = zq;
+                            }
+                            cnt += __popc(bal);
                         }
-                        const unsigned bal = __ballot_sync(0xffffffffu, pass);
-                        const int pos = cnt + __popc(bal & lt);
-                        if (pass && pos < NB_LIST) {
-                            sh.idx[k][pos] = q;
-                            sh.y[k][pos] = yq;
-                            sh.z[k][pos] = zq;
-                        }
-                        cnt += __popc(bal);
                     }
                     if (lane == 0) sh.cnt[k] = cnt;
                     built |= 1u << k;
@@ -825,26 +882,31 @@ __global__ void __launch_bounds__(128, 4) k_tracklet_lanes(
                 const float det = S00 * S11 - S01 * S01;
                 const float wz = sqrtf(P.chi2_ext * S11) * 1.001f + 1e-3f;
                 const float wy = sqrtf(P.chi2_ext * S00) * 1.001f + 1e-3f;
-                const int cb = gkb + target * gnz;
+                // cells of the window: z cells k0..k1, y cells y0..y1 of the row
+                const int cb = gkb + target * gnz * CELL_NY;
                 const float f0 = (kf.p[1] - wz - gz0) * ginv, f1 = (kf.p[1] + wz - gz0) * ginv;
                 const int k0 = min(f0 >= 0.f ? (int)f0 : 0, gnz - 1);
                 const int k1 = min(f1 >= 0.f ? (int)f1 : 0, gnz - 1);
-                const int b = cells.off[cb + k0], e = cells.off[cb + k1 + 1];
+                const float yp = kf.p[0] + kf.lo[0];
+                const int y0 = ycell(geo, target, yp - wy - 1e-3f), y1 = ycell(geo, target, yp + wy + 1e-3f);
                 int bo = 0;
                 float bchi = 0.f;
+                for (int kz = k0; kz <= k1; ++kz) {
+                    const int b = cells.off[cb + kz * CELL_NY + y0], e = cells.off[cb + kz * CELL_NY + y1 + 1];
 #pragma unroll 4
-                for (int q = b; q < e; ++q) {
-                    const float r1 = (zb[q] - kf.p[1]) - kf.lo[1];
-                    if (fabsf(r1) > wz) continue;
-                    const float r0 = (yb[q] - kf.p[0]) - kf.lo[0];
-                    if (fabsf(r0) > wy) continue;
-                    const float chi = (r0 * r0 * S11 - 2.f * r0 * r1 * S01 + r1 * r1 * S00) / det;
-                    if (!(chi <= P.chi2_ext)) continue;
-                    const int oq = orig[q];
-                    if (c < 0 || chi < bchi || (chi == bchi && oq < bo)) {
-                        c = q;
-                        bchi = chi;
-                        bo = oq;
+                    for (int q = b; q < e; ++q) {
+                        const float r1 = (zb[q] - kf.p[1]) - kf.lo[1];
+                        if (fabsf(r1) > wz) continue;
+                        const float r0 = (yb[q] - kf.p[0]) - kf.lo[0];
+                        if (fabsf(r0) > wy) continue;
+                        const float chi = (r0 * r0 * S11 - 2.f * r0 * r1 * S01 + r1 * r1 * S00) / det;
+                        if (!(chi <= P.chi2_ext)) continue;
+                        const int oq = orig[q];
+                        if (c < 0 || chi < bchi || (chi == bchi && oq < bo)) {
+                            c = q;
+                            bchi = chi;
+                            bo = oq;
+                        }
                     }
                 }
                 if (c >= 0) {
@@ -1395,7 +1457,7 @@ cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hi
     c->mark(0, s);
     // per-call counters (the status word and the FP64 count are cumulative)
     TPC_TRY(fill_i32(st + ST_NSEG, ST_NTRACKS - ST_NSEG + 1, 0, s));
-    TPC_TRY(fill_i32(st + ST_Q_BUILD, ST_NB_OVF + 1 - ST_Q_BUILD, 0, s));
+    TPC_TRY(fill_i32(st + ST_Q_BUILD, ST_NB_Q2 + 1 - ST_Q_BUILD, 0, s));
     // S1: z range per group, cells, histogram, scan, scatter
     tpc::LaunchCount{}, k_fill_u32<<<grid_for(G), TPB, 0, s>>>(W.at<uint32_t>(L.g_zmin_u), G, 0xffffffffu);
     tpc::LaunchCount{}, k_fill_u32<<<grid_for(G), TPB, 0, s>>>(W.at<uint32_t>(L.g_zmax_u), G, 0u);
@@ -1407,7 +1469,7 @@ cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hi
     Cells cells{W.at<float>(L.g_zmin), W.at<float>(L.g_inv), W.at<int32_t>(L.g_nz),
                 W.at<int32_t>(L.g_kbase), W.at<int32_t>(L.cell_off)};
     TPC_TRY(fill_i32(W.at<int32_t>(L.cell_cnt), L.K + 1, 0, s));
-    tpc::LaunchCount{}, k_hist<<<grid_for(n), TPB, 0, s>>>(c->z, c->row, n, c->evt_sector_off, G, cells,
+    tpc::LaunchCount{}, k_hist<<<grid_for(n), TPB, 0, s>>>(c->y, c->z, c->row, n, c->evt_sector_off, G, cells, geo,
                                        W.at<int32_t>(L.cell_cnt), W.at<int32_t>(L.key_in),
                                        W.at<int32_t>(L.slot_in), L.K);
     TPC_TRY(scan_i32(W.at<int32_t>(L.cell_cnt), W.at<int32_t>(L.cell_off), L.K, scan_tmp, s));
@@ -1427,9 +1489,15 @@ cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hi
     int32_t* cup = W.at<int32_t>(L.choice_up);
     float* d2 = W.at<float>(L.d2);
     NbPrm nb{p.win_y, p.win_z, p.chi2_link, p.sigma_y2, p.sigma_z2, p.max_gap};
-    int32_t* nb_queue = W.at<int32_t>(L.key_in);  // free after S1
-    tpc::LaunchCount{}, k_neighbours_sub<<<grid_for(n, NS_WARPS * 32 / NG * 4), NS_WARPS * 32, 0, s>>>(
-        n, yb, zb, orig, grpb, rowb, cells, geo, nb, cdn, cup, d2, st, nb_queue);
+    int32_t* nb_queue = W.at<int32_t>(L.key_in);    // free after S1
+    int32_t* nb_queue2 = W.at<int32_t>(L.slot_in);  // free after S1
+    // pass 1: gap pair (1, 1) for all; pass 2: the later gap pairs for the rest
+    tpc::LaunchCount{}, k_neighbours_sub<NG1><<<grid_for(n, 32 * 4), ns_warps<NG1>() * 32, 0, s>>>(
+        n, nullptr, 0, 2, 2, yb, zb, orig, grpb, rowb, cells, geo, nb, cdn, cup, d2, st, nb_queue, nb_queue2,
+        ST_NB_Q2);
+    tpc::LaunchCount{}, k_neighbours_sub<NG2><<<grid_for(n / 4, 32 * 4), ns_warps<NG2>() * 32, 0, s>>>(
+        n, nb_queue2, ST_NB_Q2, 3, 2 * NB_GAP_MAX, yb, zb, orig, grpb, rowb, cells, geo, nb, cdn, cup, d2, st,
+        nb_queue, nullptr, 0);
     tpc::LaunchCount{}, k_neighbours_warp<<<152 * 8, NB_WARPS * 32, 0, s>>>(nb_queue, st, yb, zb, orig, grpb,
                                                                         rowb, cells, geo, nb, cdn, cup, d2);
     c->mark(2, s);

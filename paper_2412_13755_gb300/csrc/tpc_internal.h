@@ -21,13 +21,15 @@ constexpr int NSEC = 36;
 constexpr int NPHI = 18;
 constexpr int NROW = 152;
 constexpr int MAX_CAND = 16;     // merge candidates kept per tracklet
-constexpr int CELL_OCC = 2;      // target clusters per (row, z-cell)
+constexpr int CELL_OCC = 2;      // target clusters per (row, z-cell, y-cell)
+constexpr int CELL_NY = 8;       // y cells per (row, z-cell), uniform in y / (x tan 10 deg)
 constexpr int NZ_MAX = 8192;     // z cells per row at most
 
 // Geometry table written into the workspace at set-up.
 struct Geo {
     double row_xd[NROW];   // pad-row plane x (cm), FP64
     float row_xf[NROW];    // the same rounded to FP32 (neighbour decisions)
+    float ycell_inv[NROW]; // CELL_NY / (2 x tan 10 deg): y-cell index scale per row
     float tan_half;        // tan(10 deg)
     float pad0;
     double tan_half_d;
@@ -40,7 +42,7 @@ struct Geo {
 enum StatusSlot {
     ST_STATUS = 0, ST_DETAIL, ST_NSEG, ST_NTL, ST_NCAND, ST_NMERGE, ST_NTRACKS, ST_FP64,
     ST_MATCH_LIVE, ST_Q_BUILD, ST_Q_REFIT, ST_SPARE11, ST_KFSTEPS = 12 /* 64-bit: slots 12-13 */,
-    ST_NB_OVF = 14, ST_N_SLOTS = 16
+    ST_NB_OVF = 14, ST_NB_Q2 = 15, ST_N_SLOTS = 16
 };
 
 // Workspace layout: byte offsets of every buffer, computed from capacities.
