@@ -363,6 +363,49 @@ __device__ __forceinline__ ff ff_rcp(ff x) {
 // acc + x * f
 __device__ __forceinline__ ff ff_fma_f(ff acc, ff x, float f) { return ff_add(acc, ff_mul_f(x, f)); }
 
+// sqrt(x) for x > 0: the FP32 root refined by one Newton (Heron) step
+// s + (x - s^2) / (2 s), the residual x - s^2 formed exactly with TwoProduct
+__device__ __forceinline__ ff ff_sqrt(ff x) {
+    const float s = __fsqrt_rn(x.hi);
+    const float p = __fmul_rn(s, s);
+    const float pe = __fmaf_rn(s, s, -p);
+    const ff r = ff_add(x, ff{-p, -pe});
+    return fast_two_sum(s, __fdiv_rn(r.hi, __fmul_rn(2.f, s)));
+}
+
+// chi2 = d^T M^-1 d for a 5x5 symmetric positive definite M (packed upper
+// triangle) by Cholesky factorisation and forward substitution, in
+// float-float.  Returns false when a pivot is not positive.
+__device__ __forceinline__ bool chol_chi2_ff(const ff d[5], const ff M[15], ff& out) {
+    ff Lm[5][5], inv[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+#pragma unroll
+        for (int j = 0; j <= i; ++j) {
+            ff acc = M[sx(i, j)];
+#pragma unroll
+            for (int l = 0; l < j; ++l) acc = ff_add(acc, ff_neg(ff_mul(Lm[i][l], Lm[j][l])));
+            if (i == j) {
+                if (!(acc.hi > 0.f)) return false;
+                Lm[i][i] = ff_sqrt(acc);
+                inv[i] = ff_rcp(Lm[i][i]);
+            } else {
+                Lm[i][j] = ff_mul(acc, inv[j]);
+            }
+        }
+    ff v[5], c2 = ff_from(0.f);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        ff acc = d[i];
+#pragma unroll
+        for (int l = 0; l < i; ++l) acc = ff_add(acc, ff_neg(ff_mul(Lm[i][l], v[l])));
+        v[i] = ff_mul(acc, inv[i]);
+        c2 = ff_add(c2, ff_mul(v[i], v[i]));
+    }
+    out = c2;
+    return true;
+}
+
 // Covariance transform C <- J C J^T in float-float for the Jacobian of
 // cov_jct (J exact in FP32).
 __device__ __forceinline__ void cov_jct_ff(ff C[15], float j00, float j02, float j04, float j10,

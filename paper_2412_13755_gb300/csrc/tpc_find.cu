@@ -1100,29 +1100,6 @@ struct MgPrm {
 };
 
 // 5x5 SPD chi2 = dp^T M^-1 dp by Cholesky (FP64); false if not SPD
-__device__ bool chol_chi2(const double dp[5], const double M[15], double& out) {
-    double Lm[5][5];
-    for (int i = 0; i < 5; ++i)
-        for (int j = 0; j <= i; ++j) {
-            double s = M[sx(i, j)];
-            for (int l = 0; l < j; ++l) s -= Lm[i][l] * Lm[j][l];
-            if (i == j) {
-                if (!(s > 0.0)) return false;
-                Lm[i][i] = sqrt(s);
-            } else {
-                Lm[i][j] = s / Lm[j][j];
-            }
-        }
-    double v[5];
-    out = 0.0;
-    for (int i = 0; i < 5; ++i) {
-        double s = dp[i];
-        for (int l = 0; l < i; ++l) s -= Lm[i][l] * v[l];
-        v[i] = s / Lm[i][i];
-        out += v[i] * v[i];
-    }
-    return true;
-}
 
 __device__ __forceinline__ bool ma_ok(const int4* __restrict__ gs_meta, int qa, int b) {
     return gs_meta[qa].w != b;
@@ -1183,8 +1160,17 @@ __global__ void __launch_bounds__(256) k_merge_cand(
                         pass = fabsf(__fsub_rn(zb_in, __int_as_float(ma.y))) <=
                                __fadd_rn(__fmul_rn(P.mz_slope, dxr), P.mz_margin);
                     }
+                    const float* sta = tl_state + (int64_t)a * 40;
                     if (pass) {
-                        const float* sta = tl_state + (int64_t)a * 40;
+                        // tan lambda and q/pT are unchanged by the transport
+                        // and the frame rotation: their 1-d chi2 (lower
+                        // bounds of the 5-d chi2) reject before the move
+                        const float lim = (float)P.chi2_merge * 1.01f;
+                        const float dt = stb[3] - sta[23], dw = stb[4] - sta[24];
+                        pass = dt * dt <= lim * (sta[25 + 12] + stb[5 + 12]) &&
+                               dw * dw <= lim * (sta[25 + 14] + stb[5 + 14]);
+                    }
+                    if (pass) {
                         KF s;
                         s.x = geo->row_xd[ra];
                         s.frame = sa;
@@ -1207,13 +1193,22 @@ __global__ void __launch_bounds__(256) k_merge_cand(
                             }
                         }
                         if (pass) {
-                            double d[5], M[15];
-                            for (int i = 0; i < 3; ++i) d[i] = (double)stb[i] - ((double)s.p[i] + (double)s.lo[i]);
-                            for (int i = 3; i < 5; ++i) d[i] = (double)stb[i] - (double)s.p[i];
-                            for (int i = 0; i < 15; ++i) M[i] = (double)s.C[i] + (double)stb[5 + i];
-                            double c2;
-                            pass = chol_chi2(d, M, c2) && c2 <= P.chi2_merge;
-                            c2f = (float)c2;
+                            // float-float: the differences and sums of the FP32
+                            // states are exact, the solve carries ~48 bits
+                            ff d[5], M[15];
+#pragma unroll
+                            for (int i = 0; i < 3; ++i)
+                                d[i] = ff_add(ff_from(stb[i]), ff_neg(two_sum(s.p[i], s.lo[i])));
+#pragma unroll
+                            for (int i = 3; i < 5; ++i) d[i] = two_sum(stb[i], -s.p[i]);
+#pragma unroll
+                            for (int i = 0; i < 15; ++i) M[i] = two_sum(s.C[i], stb[5 + i]);
+                            ff c2;
+                            pass = chol_chi2_ff(d, M, c2);
+                            // c2 <= chi2_merge on the float-float value
+                            const double lim2 = P.chi2_merge;
+                            pass = pass && ((double)c2.hi + (double)c2.lo) <= lim2;
+                            c2f = c2.hi + c2.lo;
                         }
                     }
                 }
