@@ -520,6 +520,91 @@ __global__ void __launch_bounds__(ns_warps<NG>() * 32) k_neighbours_sub(
     }
 }
 
+// First gap pair (1, 1), one lane per cluster.  The admissible up
+// candidates (row r+1) go into a register list of NF entries; the down
+// candidates (row r-1) stream from their cells, each paired with the list.
+// A cluster without a pair here is queued for the later gap pairs
+// (k_neighbours_sub, pass 2); one whose up list would overflow is queued for
+// the warp-cooperative kernel (full search).
+constexpr int NF = 6;
+__global__ void __launch_bounds__(256) k_neighbours_first(
+    int64_t n, const float* __restrict__ yb, const float* __restrict__ zb,
+    const int32_t* __restrict__ orig, const int32_t* __restrict__ grpb,
+    const uint8_t* __restrict__ rowb, Cells cells, const Geo* __restrict__ geo, NbPrm P,
+    int32_t* choice_dn, int32_t* choice_up, float* d2out, int32_t* st, int32_t* ovf_queue,
+    int32_t* next_queue, int next_slot) {
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const int g = grpb[c], r = rowb[c];
+        if (r < 1 || r + 1 >= NROW) {
+            next_queue[atomicAdd(&st[next_slot], 1)] = (int32_t)c;
+            continue;
+        }
+        const float xc = geo->row_xf[r], yc = yb[c], zc = zb[c];
+        const float xd = geo->row_xf[r - 1], xu = geo->row_xf[r + 1];
+        // up list
+        float uy[NF], uz[NF];
+        int ui[NF];
+        int nu = 0;
+        const CellWin wu = nb_win(cells, geo, g, r + 1, xu, xc, yc, zc, P);
+        for (int iz = wu.iz0; iz <= wu.iz1; ++iz) {
+            int b, e;
+            cell_run(cells, wu, iz, b, e);
+            for (int q = b; q < e; ++q) {
+                const float yq = yb[q], zq = zb[q];
+                if (!in_win(xc, yc, zc, xu, yq, zq, P.win_y, P.win_z)) continue;
+#pragma unroll
+                for (int k = 0; k < NF; ++k)
+                    if (k == nu) {
+                        uy[k] = yq;
+                        uz[k] = zq;
+                        ui[k] = q;
+                    }
+                ++nu;
+            }
+        }
+        if (nu > NF) {
+            ovf_queue[atomicAdd(&st[ST_NB_OVF], 1)] = (int32_t)c;
+            continue;
+        }
+        int bd = -1, bu = -1, pod = 0, pou = 0;
+        float bd2 = 0.f;
+        if (nu > 0) {
+            const CellWin wd = nb_win(cells, geo, g, r - 1, xd, xc, yc, zc, P);
+            for (int iz = wd.iz0; iz <= wd.iz1; ++iz) {
+                int b, e;
+                cell_run(cells, wd, iz, b, e);
+                for (int d = b; d < e; ++d) {
+                    const float ydd = yb[d], zdd = zb[d];
+                    if (!in_win(xc, yc, zc, xd, ydd, zdd, P.win_y, P.win_z)) continue;
+#pragma unroll
+                    for (int k = 0; k < NF; ++k) {
+                        if (k >= nu) break;
+                        const float d2 = triplet_d2(xd, ydd, zdd, xc, yc, zc, xu, uy[k], uz[k], P.sy2, P.sz2);
+                        if (!(d2 <= P.chi2_link)) continue;
+                        const int u = ui[k];
+                        bool better = bd < 0 || d2 < bd2;
+                        if (!better && d2 == bd2) {
+                            const int ou = orig[u], od = orig[d];
+                            better = ou < pou || (ou == pou && od < pod);
+                        }
+                        if (better) {
+                            bd = d; bu = u; bd2 = d2; pod = orig[d]; pou = orig[u];
+                        }
+                    }
+                }
+            }
+        }
+        if (bd < 0 && 2 * P.max_gap > 2) {
+            next_queue[atomicAdd(&st[next_slot], 1)] = (int32_t)c;
+            continue;
+        }
+        choice_dn[c] = bd;
+        choice_up[c] = bu;
+        d2out[c] = bd2;
+    }
+}
+
 // Warp-cooperative neighbour search for the queued clusters (same rule and
 // result): one warp per cluster; the window candidates of each needed row
 // offset are compacted into shared memory once, then the lanes evaluate the
@@ -1487,9 +1572,8 @@ cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hi
     int32_t* nb_queue = W.at<int32_t>(L.key_in);    // free after S1
     int32_t* nb_queue2 = W.at<int32_t>(L.slot_in);  // free after S1
     // pass 1: gap pair (1, 1) for all; pass 2: the later gap pairs for the rest
-    tpc::LaunchCount{}, k_neighbours_sub<NG1><<<grid_for(n, 32 * 4), ns_warps<NG1>() * 32, 0, s>>>(
-        n, nullptr, 0, 2, 2, yb, zb, orig, grpb, rowb, cells, geo, nb, cdn, cup, d2, st, nb_queue, nb_queue2,
-        ST_NB_Q2);
+    tpc::LaunchCount{}, k_neighbours_first<<<grid_for(n), TPB, 0, s>>>(
+        n, yb, zb, orig, grpb, rowb, cells, geo, nb, cdn, cup, d2, st, nb_queue, nb_queue2, ST_NB_Q2);
     tpc::LaunchCount{}, k_neighbours_sub<NG2><<<grid_for(n / 4, 32 * 4), ns_warps<NG2>() * 32, 0, s>>>(
         n, nb_queue2, ST_NB_Q2, 3, 2 * NB_GAP_MAX, yb, zb, orig, grpb, rowb, cells, geo, nb, cdn, cup, d2, st,
         nb_queue, nullptr, 0);
