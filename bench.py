@@ -40,6 +40,10 @@ NEIGHBOUR_BYTES_PER_CLUSTER = 20.0      # read y,z (8); write down, up, D^2 (12)
 FIT_BYTES_PER_HIT = 14.0                # hit index (4) + y, z (8) + row (2)
 FIT_BYTES_PER_TRACK = 88.0              # 5 params + 15 cov + chi2 + ndf
 KF_FLOPS_PER_STEP = 350.0               # transport ~60 + covariance J C J^T ~160 + update ~130
+# DRAM bytes (read + write) of one build launch of k_tracklet_lanes on the
+# central event, from an ncu capture of this kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum); None for a kernel without a capture
+TRAFFIC_BYTES_PER_LAUNCH = {"k_tracklet_lanes": 35.419e6 + 3.320e6}
 
 
 def batched_vs_plain(torch, tpc, dev, steps):
@@ -291,10 +295,22 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+
+    def wait_first(self, timeout_s=3.0):
+        """Blocks until the sampler has written its first line (or gives up),
+        so that the samples that follow cover the timed region."""
+        t0 = time.perf_counter()
+        while self.proc is not None and time.perf_counter() - t0 < timeout_s:
+            try:
+                if os.path.getsize(self.path) > 0:
+                    return
+            except OSError:
+                return
+            time.sleep(0.01)
 
     def stop(self):
         if self.proc is not None:
@@ -344,7 +360,7 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def cpu_baseline(ev, target_s=15.0):
+def cpu_baseline(ev, target_s=12.0):
     """The oracle, as it stands, on the host cores: find + fit of the event."""
     import oracle
     cores = host_cores()
@@ -356,7 +372,7 @@ def cpu_baseline(ev, target_s=15.0):
         oracle.fit_tracks(ev.y, ev.z, ev.row, sec, off, hits)
         done += 1
         el = time.perf_counter() - t0
-        if el >= target_s or done >= 3:
+        if el >= target_s:
             break
     return {"value": done * ev.n / el, "unit": "clusters/s", "cores": cores, "kind": "oracle",
             "sample": f"{done} x the full central event ({ev.n} clusters), find + FP64 fit, "
@@ -440,6 +456,10 @@ def run_ours(args):
         tr.fit(find_out[1], find_out[2], track_cap, find_out[3], out=fit_out)
 
     sync = torch.cuda.synchronize
+    # clocks: sampled from the warm-up through the timed steps
+    clocks = ClockSampler(local)
+    clocks.start()
+    clocks.wait_first()
     for _ in range(max(args.warmup, 3)):
         flush.zero_()
         step()
@@ -453,11 +473,9 @@ def run_ours(args):
     stage_sum = {}
     e0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     e1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    clocks = ClockSampler(local)
     if world > 1:
         dist.barrier()
     sync()
-    clocks.start()
     for k in range(args.steps):
         flush.zero_()
         e0[k].record(stream)
@@ -537,8 +555,8 @@ def run_ours(args):
         work_steps = st.n_kf_steps if dom == "k_tracklet_lanes" else hits_total
         achieved = work_steps * KF_FLOPS_PER_STEP / (ms * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
-                "kf_steps_per_launch": int(work_steps)}
+                "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                "traffic": TRAFFIC_BYTES_PER_LAUNCH.get(dom), "kf_steps_per_launch": int(work_steps)}
     roof["kernel"] = dom
     roof["kernel_ms"] = ms
     roof["peak_source"] = (peak_src + " (MEASURED_PEAKS.json hbm_gbs)" if roof["unit"] == "GB/s"

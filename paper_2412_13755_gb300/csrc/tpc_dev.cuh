@@ -438,6 +438,37 @@ __device__ __forceinline__ void cov_jct_ff(ff C[15], float j00, float j02, float
     C[sx(2, 4)] = A2[4];
 }
 
+// The same transform for a move inside one frame, where J = I except for
+// j02, j04, j12, j13, j14, j24 (j00 = j22 = 1, j10 = j20 = 0): the products
+// with the unit and zero entries are skipped.
+__device__ __forceinline__ void cov_jct_ff_frame(ff C[15], float j02, float j04, float j12, float j13,
+                                                 float j14, float j24) {
+    ff c[5][5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+#pragma unroll
+        for (int j = 0; j < 5; ++j) c[i][j] = C[sx(i, j)];
+    ff A0[5], A1[5], A2[5];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+        A0[j] = ff_fma_f(ff_fma_f(c[0][j], c[2][j], j02), c[4][j], j04);
+        A1[j] = ff_fma_f(ff_fma_f(ff_fma_f(c[1][j], c[2][j], j12), c[3][j], j13), c[4][j], j14);
+        A2[j] = ff_fma_f(c[2][j], c[4][j], j24);
+    }
+    C[sx(0, 0)] = ff_fma_f(ff_fma_f(A0[0], A0[2], j02), A0[4], j04);
+    C[sx(0, 1)] = ff_fma_f(ff_fma_f(ff_fma_f(A0[1], A0[2], j12), A0[3], j13), A0[4], j14);
+    C[sx(0, 2)] = ff_fma_f(A0[2], A0[4], j24);
+    C[sx(0, 3)] = A0[3];
+    C[sx(0, 4)] = A0[4];
+    C[sx(1, 1)] = ff_fma_f(ff_fma_f(ff_fma_f(A1[1], A1[2], j12), A1[3], j13), A1[4], j14);
+    C[sx(1, 2)] = ff_fma_f(A1[2], A1[4], j24);
+    C[sx(1, 3)] = A1[3];
+    C[sx(1, 4)] = A1[4];
+    C[sx(2, 2)] = ff_fma_f(A2[2], A2[4], j24);
+    C[sx(2, 3)] = A2[3];
+    C[sx(2, 4)] = A2[4];
+}
+
 // Kalman update with the covariance in float-float: S, its inverse, the
 // gain and C - K H C in float-float; the state increment from the gain in
 // FP32 on the compensated state.  Returns the predicted-residual chi2 term.

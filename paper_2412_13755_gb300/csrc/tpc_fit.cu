@@ -57,8 +57,11 @@ __global__ void __launch_bounds__(128) k_fit(
                 MoveJ mj;
                 ok = kf_move<float, true, false>(s, geo->row_xd[row[c]], g % NSEC, geo, P.kb, P.snp_max, &mj);
                 if (ok) {
-                    cov_jct_ff(Cf, mj.j00, mj.j02, mj.j04, mj.j10, mj.j12, mj.j13, mj.j14, mj.j20, mj.j22,
-                               mj.j24);
+                    if (mj.j00 == 1.f && mj.j22 == 1.f && mj.j10 == 0.f && mj.j20 == 0.f)
+                        cov_jct_ff_frame(Cf, mj.j02, mj.j04, mj.j12, mj.j13, mj.j14, mj.j24);
+                    else
+                        cov_jct_ff(Cf, mj.j00, mj.j02, mj.j04, mj.j10, mj.j12, mj.j13, mj.j14, mj.j20, mj.j22,
+                                   mj.j24);
                     chi2.add(kf_update_ff(s, Cf, y[c], z[c], P.sy2, P.sz2));
                 }
             }
