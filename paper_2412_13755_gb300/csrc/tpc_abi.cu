@@ -102,6 +102,7 @@ Layout make_layout(int64_t N, int32_t E) {
     L.scan_b = take(4 * (size_t)L.scan_tmp);
     L.adj_grad = take(8 * 216 * 2);
     L.adj_chi2 = take(8 * 2);
+    L.adj_rot = take(4 * NSEC * 39);
     L.adj_ckpt = take(0);
     L.total = o;
     return L;

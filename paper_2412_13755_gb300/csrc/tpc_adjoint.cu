@@ -231,13 +231,67 @@ __device__ __forceinline__ void rot_grad(const double* __restrict__ th, double x
     out[2] = xb * (-sg * x2 - cg * y1) + yb * (cg * x2 - sg * y1);
 }
 
+// Per-sector tables of the alignment correction, from the 216 parameters
+// (once per call): R - I, dR/da, dR/db, dR/dg (3x3 each, acting on
+// (x_row, y, z)) and the shift t.  The per-hit correction is then the small
+// FP32 increment (R - I) p + t, and the angle gradient a 27-term FP32
+// contraction, instead of six FP64 sines and cosines per hit.
+constexpr int ROT_TAB = 39;  // floats per sector: R - I (9), dR (27), t (3)
+__global__ void k_adj_tables(const double* __restrict__ align, float* tab) {
+    const int sec = threadIdx.x;
+    if (sec >= NSEC) return;
+    const double* th = align + 6 * sec;
+    float* o = tab + sec * ROT_TAB;
+    const double e[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+    double th0[6] = {0.0, 0.0, 0.0, th[3], th[4], th[5]};
+    for (int col = 0; col < 3; ++col) {
+        double xo, yo, zo;
+        corrected_pos(th0, e[col][0], e[col][1], e[col][2], xo, yo, zo);
+        o[0 * 3 + col] = (float)(xo - e[col][0]);
+        o[1 * 3 + col] = (float)(yo - e[col][1]);
+        o[2 * 3 + col] = (float)(zo - e[col][2]);
+        for (int r = 0; r < 3; ++r) {
+            double g3[3];
+            rot_grad(th0, e[col][0], e[col][1], e[col][2], e[r][0], e[r][1], e[r][2], g3);
+            for (int k = 0; k < 3; ++k) o[9 + k * 9 + r * 3 + col] = (float)g3[k];  // dR_k[r][col]
+        }
+    }
+    for (int i = 0; i < 3; ++i) o[36 + i] = (float)th[i];
+}
+
+// corrected position of (x_row, y, z) in sector table o: x as FP64 (a
+// plane position), y and z as FP32
+__device__ __forceinline__ void corr_tab(const float* o, double xr, float y, float z, double& xc,
+                                         float& yc, float& zc) {
+    const float xf = (float)xr;
+    const float dx = o[0] * xf + o[1] * y + o[2] * z + o[36];
+    const float dy = o[3] * xf + o[4] * y + o[5] * z + o[37];
+    const float dz = o[6] * xf + o[7] * y + o[8] * z + o[38];
+    xc = xr + (double)dx;
+    yc = y + dy;
+    zc = z + dz;
+}
+
+// the angle gradient: (xb, yb, zb) . dR_k (x_row, y, z) for k = a, b, g
+__device__ __forceinline__ void rot_grad_tab(const float* o, float xr, float y, float z, float xb,
+                                             float yb, float zb, float out[3]) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float* d = o + 9 + 9 * k;
+        out[k] = xb * (d[0] * xr + d[1] * y + d[2] * z) + yb * (d[3] * xr + d[4] * y + d[5] * z) +
+                 zb * (d[6] * xr + d[7] * y + d[8] * z);
+    }
+}
+
 __global__ void __launch_bounds__(128) k_adjoint(
     const int32_t* __restrict__ trk_off, const int32_t* __restrict__ trk_hits, int32_t T,
     const float* __restrict__ yin, const float* __restrict__ zin, const uint16_t* __restrict__ row,
-    const int64_t* __restrict__ evt_off, int G, const double* __restrict__ align,
+    const int64_t* __restrict__ evt_off, int G, const float* __restrict__ rot_tab,
     const Geo* __restrict__ geo, AdjPrm P, double* chi2_total, double* grad, int32_t* st) {
     __shared__ double sg[216];
     __shared__ double schi2;
+    __shared__ float tab[NSEC * ROT_TAB];
+    for (int i = threadIdx.x; i < NSEC * ROT_TAB; i += blockDim.x) tab[i] = rot_tab[i];
     for (int i = threadIdx.x; i < 216; i += blockDim.x) sg[i] = 0.0;
     if (threadIdx.x == 0) schi2 = 0.0;
     __syncthreads();
@@ -268,6 +322,8 @@ __global__ void __launch_bounds__(128) k_adjoint(
         }
         NSum chi2;
         bool ok = true;
+        int gcur = -1;
+        int64_t gb = 0, ge = 0;
         for (int j = 0; j < n && ok; ++j) {
             if (j % CK == 0) {
                 Pre& q = ck[j / CK];
@@ -277,13 +333,18 @@ __global__ void __launch_bounds__(128) k_adjoint(
                 for (int i = 0; i < 15; ++i) q.C[i] = s.C[i];
             }
             const int c = h[j];
-            const int sec = group_of(evt_off, G, c) % NSEC;
-            double xc, yc, zc;
-            corrected_pos(align + 6 * sec, geo->row_xd[row[c]], yin[c], zin[c], xc, yc, zc);
+            if (c < gb || c >= ge) {  // group lookup, cached while hits stay in one group
+                gcur = group_of(evt_off, G, c);
+                gb = evt_off[gcur];
+                ge = evt_off[gcur + 1];
+            }
+            const int sec = gcur % NSEC;
+            double xc;
+            float yc, zc;
+            corr_tab(tab + sec * ROT_TAB, geo->row_xd[row[c]], yin[c], zin[c], xc, yc, zc);
             MoveJ mj;
             ok = kf_move<float>(s, xc, sec, geo, P.kb, P.snp_max, &mj);
-            if (ok) chi2.add(kf_update(s, (float)yc, (float)zc, P.sy2, P.sz2, P.fp64_ratio,
-                                       P.fp64_det, nullptr, &mj));
+            if (ok) chi2.add(kf_update(s, yc, zc, P.sy2, P.sz2, P.fp64_ratio, P.fp64_det, nullptr, &mj));
         }
         if (!ok) continue;
         atomicAdd(&schi2, (double)chi2.value());
@@ -313,21 +374,33 @@ __global__ void __launch_bounds__(128) k_adjoint(
                 for (int i = 0; i < 3; ++i) q.lo[i] = r.lo[i];
                 for (int i = 0; i < 15; ++i) q.C[i] = r.C[i];
                 const int c = h[j];
-                const int sec = group_of(evt_off, G, c) % NSEC;
-                double xc, yc, zc;
-                corrected_pos(align + 6 * sec, geo->row_xd[row[c]], yin[c], zin[c], xc, yc, zc);
+                if (c < gb || c >= ge) {
+                    gcur = group_of(evt_off, G, c);
+                    gb = evt_off[gcur];
+                    ge = evt_off[gcur + 1];
+                }
+                const int sec = gcur % NSEC;
+                double xc;
+                float yc, zc;
+                corr_tab(tab + sec * ROT_TAB, geo->row_xd[row[c]], yin[c], zin[c], xc, yc, zc);
                 MoveJ mj;
                 kf_move<float>(r, xc, sec, geo, P.kb, P.snp_max, &mj);
-                kf_update(r, (float)yc, (float)zc, P.sy2, P.sz2, P.fp64_ratio, P.fp64_det, nullptr, &mj);
+                kf_update(r, yc, zc, P.sy2, P.sz2, P.fp64_ratio, P.fp64_det, nullptr, &mj);
             }
             for (int j = j1 - 1; j >= j0; --j) {
                 const Pre& q = seg[j - j0];
                 const int c = h[j];
-                const int sec = group_of(evt_off, G, c) % NSEC;
-                const double* th = align + 6 * sec;
+                if (c < gb || c >= ge) {
+                    gcur = group_of(evt_off, G, c);
+                    gb = evt_off[gcur];
+                    ge = evt_off[gcur + 1];
+                }
+                const int sec = gcur % NSEC;
+                const float* tb = tab + sec * ROT_TAB;
                 const double xr = geo->row_xd[row[c]];
-                double xc, yc, zc;
-                corrected_pos(th, xr, yin[c], zin[c], xc, yc, zc);
+                double xc;
+                float yc, zc;
+                corr_tab(tb, xr, yin[c], zin[c], xc, yc, zc);
                 // forward of this step again: transport, then update pieces
                 KF m;
                 m.x = q.x; m.frame = q.frame;
@@ -338,8 +411,8 @@ __global__ void __launch_bounds__(128) k_adjoint(
                 float Cm[5][5];
                 for (int a = 0; a < 5; ++a)
                     for (int bb = 0; bb < 5; ++bb) Cm[a][bb] = m.C[sx(a, bb)];
-                const float r0 = ((float)yc - m.p[0]) - m.lo[0];
-                const float r1 = ((float)zc - m.p[1]) - m.lo[1];
+                const float r0 = (yc - m.p[0]) - m.lo[0];
+                const float r1 = (zc - m.p[1]) - m.lo[1];
                 const float S00 = Cm[0][0] + P.sy2, S01 = Cm[0][1], S11 = Cm[1][1] + P.sz2;
                 const float det = S00 * S11 - S01 * S01;
                 const float W00 = S11 / det, W01 = -S01 / det, W11 = S00 / det;
@@ -492,8 +565,8 @@ __global__ void __launch_bounds__(128) k_adjoint(
                 // plus the departure of step j+1 (x_from)
                 const double xb = (double)xbar_to + (double)xbar_from_next;
                 xbar_from_next = xbar_from;
-                double gr[3];
-                rot_grad(th, xr, yin[c], zin[c], xb, ybar, zbar, gr);
+                float gr[3];
+                rot_grad_tab(tb, (float)xr, yin[c], zin[c], (float)xb, ybar, zbar, gr);
                 int sl = 0;
                 while (sl < nslot && slot_sec[sl] != sec) ++sl;
                 if (sl == nslot) {
@@ -552,9 +625,11 @@ cudaError_t run_adjoint(tpc_ctx* c, const int32_t* trk_off, const int32_t* trk_h
     tpc::LaunchCount{}, k_zero_f64<<<1, 32, 0, s>>>(chi2_total, 1);
     if (grad) tpc::LaunchCount{}, k_zero_f64<<<1, 256, 0, s>>>(grad, 216);
     if (n_tracks > 0) {
+        float* rot_tab = c->ws.at<float>(c->ws.L.adj_rot);
+        tpc::LaunchCount{}, k_adj_tables<<<1, 64, 0, s>>>(align, rot_tab);
         const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((n_tracks + 127) / 128, 152 * 4));
         tpc::LaunchCount{}, k_adjoint<<<(unsigned)blocks, 128, 0, s>>>(trk_off, trk_hits, n_tracks, c->y, c->z, c->row,
-                                                   c->evt_sector_off, c->n_events * NSEC, align,
+                                                   c->evt_sector_off, c->n_events * NSEC, rot_tab,
                                                    c->ws.at<Geo>(c->ws.L.geo), ap, chi2_total, grad,
                                                    c->ws.at<int32_t>(c->ws.L.status));
     }
