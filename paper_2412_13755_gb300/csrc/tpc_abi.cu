@@ -98,6 +98,7 @@ Layout make_layout(int64_t N, int32_t E) {
     L.trk_len_at = take(n4);
     L.trk_head_at = take(n4);
     L.len_by_rank = take(4 * (size_t)L.T);
+    L.head_by_rank = take(4 * (size_t)L.T);
     L.scan_a = take(4 * (size_t)L.scan_tmp);
     L.scan_b = take(4 * (size_t)L.scan_tmp);
     L.adj_grad = take(8 * 216 * 2);

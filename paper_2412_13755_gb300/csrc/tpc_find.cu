@@ -101,10 +101,11 @@ __device__ __forceinline__ void cell_run(const Cells& cells, const CellWin& w, i
 
 // ---------------------------------------------------------------- S1 ------
 __global__ void k_zrange(const float* __restrict__ z, int64_t n, const int64_t* __restrict__ off,
-                         int G, uint32_t* zmin_u, uint32_t* zmax_u) {
+                         int G, uint32_t* zmin_u, uint32_t* zmax_u, int32_t* grp_of) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int g = group_of(off, G, i);
+        grp_of[i] = g;
         const uint32_t o = f2o(z[i]);
         // lanes of one group combine before the atomics
         const unsigned act = __activemask();
@@ -236,11 +237,11 @@ __global__ void __launch_bounds__(1024) k_tl_bins(const int64_t* __restrict__ of
 
 __global__ void k_hist(const float* __restrict__ y, const float* __restrict__ z,
                        const uint16_t* __restrict__ row, int64_t n,
-                       const int64_t* __restrict__ off, int G, Cells cells, const Geo* __restrict__ geo,
+                       const int32_t* __restrict__ grp_of, Cells cells, const Geo* __restrict__ geo,
                        int32_t* cnt, int32_t* key_in, int32_t* slot_in, int64_t Kcap) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const int g = group_of(off, G, i);
+        const int g = grp_of[i];
         const int r = row[i];
         const int key = cells.kbase[g] + (r * cells.nz[g] + zcell(cells, g, z[i])) * CELL_NY + ycell(geo, r, y[i]);
         int slot = 0;
@@ -252,7 +253,7 @@ __global__ void k_hist(const float* __restrict__ y, const float* __restrict__ z,
 
 __global__ void k_scatter(const float* __restrict__ y, const float* __restrict__ z,
                           const uint16_t* __restrict__ row, int64_t n,
-                          const int64_t* __restrict__ off, int G,
+                          const int32_t* __restrict__ grp_of,
                           const int32_t* __restrict__ key_in, const int32_t* __restrict__ slot_in,
                           const int32_t* __restrict__ cell_off, int64_t Kcap, float* yb, float* zb,
                           int32_t* orig, int32_t* grpb, uint8_t* rowb) {
@@ -264,7 +265,7 @@ __global__ void k_scatter(const float* __restrict__ y, const float* __restrict__
         yb[pos] = y[i];
         zb[pos] = z[i];
         orig[pos] = (int32_t)i;
-        grpb[pos] = group_of(off, G, i);
+        grpb[pos] = grp_of[i];
         rowb[pos] = (uint8_t)row[i];
     }
 }
@@ -1449,12 +1450,17 @@ __global__ void k_track_heads(const int32_t* __restrict__ tl_keep, const int32_t
 
 __global__ void k_track_len(int64_t n, const int32_t* __restrict__ trk_flag,
                             const int32_t* __restrict__ trk_rank, const int32_t* __restrict__ trk_len_at,
-                            int32_t track_cap, int32_t* len_by_rank, int32_t* st, int32_t* n_tracks_dev) {
+                            const int32_t* __restrict__ trk_head_at, int32_t track_cap,
+                            int32_t* len_by_rank, int32_t* head_by_rank, int32_t* st,
+                            int32_t* n_tracks_dev) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         if (!trk_flag[i]) continue;
         const int r = trk_rank[i];
-        if (r < track_cap) len_by_rank[r] = trk_len_at[i];
+        if (r < track_cap) {
+            len_by_rank[r] = trk_len_at[i];
+            head_by_rank[r] = trk_head_at[i];
+        }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         const int T = trk_rank[n];
@@ -1466,21 +1472,18 @@ __global__ void k_track_len(int64_t n, const int32_t* __restrict__ trk_flag,
 
 // One warp per output track: the hits of its chain of tracklets, outermost
 // first, in the track's slice of the CSR, and the track index per cluster.
-__global__ void k_track_write(int64_t n, const int32_t* __restrict__ trk_flag,
-                              const int32_t* __restrict__ trk_rank,
-                              const int32_t* __restrict__ trk_head_at, const int32_t* __restrict__ prv,
+__global__ void k_track_write(const int32_t* __restrict__ st_r, int32_t track_cap,
+                              const int32_t* __restrict__ head_by_rank, const int32_t* __restrict__ prv,
                               const int32_t* __restrict__ tl_rowhit, const int32_t* __restrict__ orig,
-                              const int32_t* __restrict__ trk_off, int32_t track_cap, int32_t* toc,
+                              const int32_t* __restrict__ trk_off, int64_t n, int32_t* toc,
                               int32_t* trk_hits, int32_t* st_w) {
     const int lane = threadIdx.x & 31;
     const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t i = w0; i < n; i += nw) {
-        if (!trk_flag[i]) continue;
-        const int r = trk_rank[i];
-        if (r >= track_cap) continue;
+    const int T = min(st_r[ST_NTRACKS], track_cap);
+    for (int64_t r = w0; r < T; r += nw) {
         int o = trk_off[r], guard = 0;
-        for (int t = trk_head_at[i]; t >= 0 && guard < 4096; t = prv[t], ++guard) {
+        for (int t = head_by_rank[r]; t >= 0 && guard < 4096; t = prv[t], ++guard) {
             const int32_t* hit = tl_rowhit + (int64_t)t * NROW;
             // rows from the outermost down, 32 at a time
             for (int r0 = NROW - 1; r0 >= 0; r0 -= 32) {
@@ -1492,7 +1495,7 @@ __global__ void k_track_write(int64_t n, const int32_t* __restrict__ trk_flag,
                     if (pos < n) {
                         const int oi = orig[h];
                         trk_hits[pos] = oi;
-                        toc[oi] = r;
+                        toc[oi] = (int32_t)r;
                     } else {
                         set_status(st_w, TPC_ERR_STATE, 401);
                     }
@@ -1541,15 +1544,16 @@ cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hi
     // S1: z range per group, cells, histogram, scan, scatter
     tpc::LaunchCount{}, k_fill_u32<<<grid_for(G), TPB, 0, s>>>(W.at<uint32_t>(L.g_zmin_u), G, 0xffffffffu);
     tpc::LaunchCount{}, k_fill_u32<<<grid_for(G), TPB, 0, s>>>(W.at<uint32_t>(L.g_zmax_u), G, 0u);
+    int32_t* grp_of = W.at<int32_t>(L.d2);  // group of every input cluster (d2 is free in S1)
     tpc::LaunchCount{}, k_zrange<<<grid_for(n), TPB, 0, s>>>(c->z, n, c->evt_sector_off, G, W.at<uint32_t>(L.g_zmin_u),
-                                         W.at<uint32_t>(L.g_zmax_u));
+                                         W.at<uint32_t>(L.g_zmax_u), grp_of);
     tpc::LaunchCount{}, k_cells<<<1, 1024, 0, s>>>(c->evt_sector_off, G, W.at<uint32_t>(L.g_zmin_u),
                                W.at<uint32_t>(L.g_zmax_u), W.at<float>(L.g_zmin), W.at<float>(L.g_inv),
                                W.at<int32_t>(L.g_nz), W.at<int32_t>(L.g_kbase), L.K, st);
     Cells cells{W.at<float>(L.g_zmin), W.at<float>(L.g_inv), W.at<int32_t>(L.g_nz),
                 W.at<int32_t>(L.g_kbase), W.at<int32_t>(L.cell_off)};
     TPC_TRY(fill_i32(W.at<int32_t>(L.cell_cnt), L.K + 1, 0, s));
-    tpc::LaunchCount{}, k_hist<<<grid_for(n), TPB, 0, s>>>(c->y, c->z, c->row, n, c->evt_sector_off, G, cells, geo,
+    tpc::LaunchCount{}, k_hist<<<grid_for(n), TPB, 0, s>>>(c->y, c->z, c->row, n, grp_of, cells, geo,
                                        W.at<int32_t>(L.cell_cnt), W.at<int32_t>(L.key_in),
                                        W.at<int32_t>(L.slot_in), L.K);
     TPC_TRY(scan_i32(W.at<int32_t>(L.cell_cnt), W.at<int32_t>(L.cell_off), L.K, scan_tmp, s));
@@ -1558,7 +1562,7 @@ cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hi
     int32_t* orig = W.at<int32_t>(L.orig);
     int32_t* grpb = W.at<int32_t>(L.grpb);
     uint8_t* rowb = W.at<uint8_t>(L.rowb);
-    tpc::LaunchCount{}, k_scatter<<<grid_for(n), TPB, 0, s>>>(c->y, c->z, c->row, n, c->evt_sector_off, G,
+    tpc::LaunchCount{}, k_scatter<<<grid_for(n), TPB, 0, s>>>(c->y, c->z, c->row, n, grp_of,
                                           W.at<int32_t>(L.key_in), W.at<int32_t>(L.slot_in),
                                           W.at<int32_t>(L.cell_off), L.K, yb, zb, orig, grpb, rowb);
     TPC_TRY(cudaGetLastError());
@@ -1700,12 +1704,14 @@ cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hi
     TPC_TRY(scan_i32(flag, rank, n, scan_tmp, s));
     int32_t* len_by_rank = W.at<int32_t>(L.len_by_rank);
     TPC_TRY(fill_i32(len_by_rank, track_cap, 0, s));
-    tpc::LaunchCount{}, k_track_len<<<grid_for(n), TPB, 0, s>>>(n, flag, rank, W.at<int32_t>(L.trk_len_at), track_cap,
-                                            len_by_rank, st, n_tracks_dev);
+    int32_t* head_by_rank = W.at<int32_t>(L.head_by_rank);
+    tpc::LaunchCount{}, k_track_len<<<grid_for(n), TPB, 0, s>>>(n, flag, rank, W.at<int32_t>(L.trk_len_at),
+                                            W.at<int32_t>(L.trk_head_at), track_cap, len_by_rank,
+                                            head_by_rank, st, n_tracks_dev);
     TPC_TRY(scan_i32(len_by_rank, trk_off, track_cap, scan_tmp, s));
     TPC_TRY(fill_i32(toc, n, -1, s));
-    tpc::LaunchCount{}, k_track_write<<<grid_for(n * 32), TPB, 0, s>>>(n, flag, rank, W.at<int32_t>(L.trk_head_at), prv,
-                                              tl_rowhit, orig, trk_off, track_cap, toc, trk_hits, st);
+    tpc::LaunchCount{}, k_track_write<<<grid_for((int64_t)track_cap * 32), TPB, 0, s>>>(
+        st, track_cap, head_by_rank, prv, tl_rowhit, orig, trk_off, n, toc, trk_hits, st);
     c->mark(9, s);
     return cudaGetLastError();
 }
