@@ -37,6 +37,9 @@ WORKLOAD = ("central_event: 1 event x 36 sectors, 1e4 primary tracks (pT exp slo
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
 # algorithmic traffic / work per unit, fixed before measuring
 NEIGHBOUR_BYTES_PER_CLUSTER = 20.0      # read y,z (8); write down, up, D^2 (12)
+# the whole find + fit path, every intermediate product written once and read
+# once: binning 22, neighbours 16, chains and tracks 16, fit 12.7, scatter 12
+PATH_BYTES_PER_CLUSTER = 78.7
 FIT_BYTES_PER_HIT = 14.0                # hit index (4) + y, z (8) + row (2)
 FIT_BYTES_PER_TRACK = 88.0              # 5 params + 15 cov + chi2 + ndf
 KF_FLOPS_PER_STEP = 350.0               # transport ~60 + covariance J C J^T ~160 + update ~130
@@ -581,6 +584,9 @@ def run_ours(args):
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
         "roofline": roof,
+        "path_roofline": {"bound": "hbm", "bytes_per_cluster": PATH_BYTES_PER_CLUSTER,
+                          "achieved": value * PATH_BYTES_PER_CLUSTER / 1e9, "peak": hbm_peak,
+                          "unit": "GB/s", "frac": value * PATH_BYTES_PER_CLUSTER / 1e9 / hbm_peak},
         "status": {"fp64_updates": st.n_fp64_updates, "segments": st.n_segments,
                    "tracklets": st.n_tracklets, "merges": st.n_merges},
     }

@@ -136,3 +136,43 @@ def test_undersized_outputs_refused():
     torch.cuda.synchronize()
     tr.check()
     assert int(out[3].item()) > 0
+
+
+def test_pileup_drift_offsets_recovered():
+    """Pile-up frame: the collision time of every found track follows from
+    its fitted z at the vertex, z_vertex = -v_d t0 (A side) or +v_d t0
+    (C side); it matches the generated drift-time offset of its collision."""
+    ev = synth.pileup_frame(n_collisions=5, n_tracks=2000, noise=0.1, seed=synth.SEED_BASE + 17)
+    toc, off, hits, st, tr = gpu_find(ev)
+    T = len(off) - 1
+    par, cov, chi2, ndf = tr.fit(torch.from_numpy(off.astype(np.int32)).cuda(),
+                                 torch.from_numpy(hits.astype(np.int32)).cuda(), T)
+    torch.cuda.synchronize()
+    tr.check()
+    p = par.cpu().numpy().astype(np.float64)
+    ok = ndf.cpu().numpy() > 0
+    inner = hits[off[1:] - 1]                       # innermost cluster of each track
+    sec = ev.sector_of_cluster()[inner]
+    x = synth.ROW_X[ev.row[inner]]
+    y, z, tgl, w = p[:, 0], p[:, 1], p[:, 3], p[:, 4]
+    # transverse arc from the vertex (origin) to the innermost cluster
+    chord = np.hypot(x, y)
+    k = np.abs(synth.KAPPA * synth.BZ * w)
+    arc = np.where(k * chord > 1e-9, 2.0 / np.maximum(k, 1e-30) * np.arcsin(np.minimum(k * chord / 2, 1.0)), chord)
+    zv = z - tgl * arc
+    t0_reco = np.where(sec < 18, -zv, zv) / synth.V_DRIFT
+    # truth: the majority generated track of each found track
+    mc = ev.mc_track[hits]
+    maj = np.array([np.bincount(mc[off[t]:off[t + 1]][mc[off[t]:off[t + 1]] >= 0]).argmax()
+                    if np.any(mc[off[t]:off[t + 1]] >= 0) else -1 for t in range(T)])
+    good = ok & (maj >= 0)
+    res = t0_reco[good] - ev.trk_t0[maj[good]]
+    print(f"{good.sum()} tracks: t0 residual median {np.median(np.abs(res)):.3f} us, "
+          f"within 0.5 us {np.mean(np.abs(res) < 0.5):.4f}")
+    assert np.median(np.abs(res)) < 0.1
+    assert np.mean(np.abs(res) < 0.5) > 0.95
+    # per collision, the mean over its tracks recovers the offset
+    coll_t0 = np.unique(ev.trk_t0)
+    for t0 in coll_t0:
+        sel = np.abs(ev.trk_t0[maj[good]] - t0) < 1e-9
+        assert abs(np.median(t0_reco[good][sel]) - t0) < 0.05
