@@ -46,8 +46,7 @@ Layout make_layout(int64_t N, int32_t E) {
     L.slot_in = take(n4);
     L.cell_cnt = take(4 * (size_t)(L.K + 1));
     L.cell_off = take(4 * (size_t)(L.K + 1));
-    L.yb = take(n4);
-    L.zb = take(n4);
+    L.yzb = take(n8);
     L.orig = take(n4);
     L.grpb = take(n4);
     L.rowb = take((size_t)N);
@@ -64,6 +63,7 @@ Layout make_layout(int64_t N, int32_t E) {
     L.seg_grp = take(s4);
     L.seg_canon = take(s4);
     L.tl_rowhit = take(s4 * NROW);
+    L.tl_mask = take(s8 * 4);
     L.tl_n = take(s4);
     L.tl_key = take(s8);
     L.tl_keep = take(s4);

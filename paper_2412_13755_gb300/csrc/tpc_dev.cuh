@@ -656,11 +656,14 @@ __device__ __forceinline__ void kf_seed_f(KF& s, const int rows[3], int frame, c
                                           const float zs[3], bool first_is_outer,
                                           const Geo* __restrict__ geo, float kb_unit,
                                           float snp_max_seed, float qpt_max, const float prior[5]) {
-    const int i0 = first_is_outer ? 2 : 0, i2 = first_is_outer ? 0 : 2;
-    const float x0 = geo->row_xf[rows[i0]], x1 = geo->row_xf[rows[1]], x2 = geo->row_xf[rows[i2]];
-    const float ax = x1 - x0, ay = ys[1] - ys[i0];
-    const float bx = x2 - x1, by = ys[i2] - ys[1];
-    const float cx = x2 - x0, cy = ys[i2] - ys[i0];
+    // points in increasing x (selects, not indices: the arrays stay in registers)
+    const int r0 = first_is_outer ? rows[2] : rows[0], r2 = first_is_outer ? rows[0] : rows[2];
+    const float y0 = first_is_outer ? ys[2] : ys[0], y2 = first_is_outer ? ys[0] : ys[2];
+    const float z0 = first_is_outer ? zs[2] : zs[0], z2 = first_is_outer ? zs[0] : zs[2];
+    const float x0 = geo->row_xf[r0], x1 = geo->row_xf[rows[1]], x2 = geo->row_xf[r2];
+    const float ax = x1 - x0, ay = ys[1] - y0;
+    const float bx = x2 - x1, by = y2 - ys[1];
+    const float cx = x2 - x0, cy = y2 - y0;
     const float la = sqrtf(ax * ax + ay * ay), lb = sqrtf(bx * bx + by * by);
     const float L = sqrtf(cx * cx + cy * cy);
     const float cross = ax * by - ay * bx;
@@ -675,7 +678,7 @@ __device__ __forceinline__ void kf_seed_f(KF& s, const int rows[3], int frame, c
     sn = fminf(snp_max_seed, fmaxf(-snp_max_seed, sn));
     const float au = fabsf(hk);
     const float arc = (au < 1e-9f || k == 0.f) ? L : 2.f * asinf(au) / fabsf(k);
-    const float t = arc > 0.f ? (zs[i2] - zs[i0]) / arc : 0.f;
+    const float t = arc > 0.f ? (z2 - z0) / arc : 0.f;
     float w = kb_unit != 0.f ? k / kb_unit : 0.f;
     w = fminf(qpt_max, fmaxf(-qpt_max, w));
     s.x = geo->row_xd[rows[0]];

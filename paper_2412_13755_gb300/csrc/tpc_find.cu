@@ -255,15 +255,14 @@ __global__ void k_scatter(const float* __restrict__ y, const float* __restrict__
                           const uint16_t* __restrict__ row, int64_t n,
                           const int32_t* __restrict__ grp_of,
                           const int32_t* __restrict__ key_in, const int32_t* __restrict__ slot_in,
-                          const int32_t* __restrict__ cell_off, int64_t Kcap, float* yb, float* zb,
+                          const int32_t* __restrict__ cell_off, int64_t Kcap, float2* yzb,
                           int32_t* orig, int32_t* grpb, uint8_t* rowb) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int key = key_in[i];
         if (key >= Kcap) continue;
         const int64_t pos = cell_off[key] + slot_in[i];
-        yb[pos] = y[i];
-        zb[pos] = z[i];
+        yzb[pos] = make_float2(y[i], z[i]);
         orig[pos] = (int32_t)i;
         grpb[pos] = grp_of[i];
         rowb[pos] = (uint8_t)row[i];
@@ -312,8 +311,8 @@ __device__ __forceinline__ CellWin nb_win(const Cells& cells, const Geo* __restr
 
 // Serial evaluation of one gap pair (gd, gu) for cluster c; the reference
 // used by the warp kernel when a candidate list overflows.
-__device__ void pair_scan_serial(int64_t c, int gd, int gu, const float* __restrict__ yb,
-                                 const float* __restrict__ zb, const int32_t* __restrict__ orig,
+__device__ void pair_scan_serial(int64_t c, int gd, int gu, const float2* __restrict__ yzb,
+                                 const int32_t* __restrict__ orig,
                                  int g, int r, float xc, float yc, float zc, const Cells& cells,
                                  const Geo* __restrict__ geo, const NbPrm& P, int& bd, int& bu,
                                  float& bd2) {
@@ -327,13 +326,15 @@ __device__ void pair_scan_serial(int64_t c, int gd, int gu, const float* __restr
       int db, de;
       cell_run(cells, wd, izd, db, de);
       for (int d = db; d < de; ++d) {
-        const float ydd = yb[d], zdd = zb[d];
+        const float2 vd = yzb[d];
+        const float ydd = vd.x, zdd = vd.y;
         if (!in_win(xc, yc, zc, xd, ydd, zdd, P.win_y, P.win_z)) continue;
         for (int izu = wu.iz0; izu <= wu.iz1; ++izu) {
           int ub, ue;
           cell_run(cells, wu, izu, ub, ue);
           for (int u = ub; u < ue; ++u) {
-            const float yuu = yb[u], zuu = zb[u];
+            const float2 vu = yzb[u];
+            const float yuu = vu.x, zuu = vu.y;
             if (!in_win(xc, yc, zc, xu, yuu, zuu, P.win_y, P.win_z)) continue;
             const float d2 = triplet_d2(xd, ydd, zdd, xc, yc, zc, xu, yuu, zuu, P.sy2, P.sz2);
             if (!(d2 <= P.chi2_link)) continue;
@@ -391,7 +392,7 @@ struct NsLists {
 template <int NG>
 __global__ void __launch_bounds__(ns_warps<NG>() * 32) k_neighbours_sub(
     int64_t n, const int32_t* __restrict__ in_queue, int in_slot, int sum_lo, int sum_hi,
-    const float* __restrict__ yb, const float* __restrict__ zb,
+    const float2* __restrict__ yzb,
     const int32_t* __restrict__ orig, const int32_t* __restrict__ grpb,
     const uint8_t* __restrict__ rowb, Cells cells, const Geo* __restrict__ geo, NbPrm P,
     int32_t* choice_dn, int32_t* choice_up, float* d2out, int32_t* st, int32_t* ovf_queue,
@@ -411,7 +412,8 @@ __global__ void __launch_bounds__(ns_warps<NG>() * 32) k_neighbours_sub(
         if (c0 + gq >= nin) continue;  // the whole sub-warp leaves together
         const int64_t c = in_queue ? in_queue[c0 + gq] : c0 + gq;
         const int g = grpb[c], r = rowb[c];
-        const float xc = geo->row_xf[r], yc = yb[c], zc = zb[c];
+        const float2 vc = yzb[c];
+        const float xc = geo->row_xf[r], yc = vc.x, zc = vc.y;
         // list k: bit k of `built`; its count (capped at NS_CAP + 1) in bits 8k..8k+7 of `cnts`
         unsigned built = 0;
         uint64_t cnts = 0;
@@ -441,8 +443,9 @@ __global__ void __launch_bounds__(ns_warps<NG>() * 32) k_neighbours_sub(
                             float yq = 0.f, zq = 0.f;
                             bool pass = false;
                             if (q < e) {
-                                yq = yb[q];
-                                zq = zb[q];
+                                const float2 vq = yzb[q];
+                                yq = vq.x;
+                                zq = vq.y;
                                 pass = in_win(xc, yc, zc, xr, yq, zq, P.win_y, P.win_z);
                             }
                             const unsigned bal = (__ballot_sync(gm, pass) >> (gq * NG)) & ((1u << NG) - 1u);
@@ -529,7 +532,7 @@ __global__ void __launch_bounds__(ns_warps<NG>() * 32) k_neighbours_sub(
 // the warp-cooperative kernel (full search).
 constexpr int NF = 6;
 __global__ void __launch_bounds__(256) k_neighbours_first(
-    int64_t n, const float* __restrict__ yb, const float* __restrict__ zb,
+    int64_t n, const float2* __restrict__ yzb,
     const int32_t* __restrict__ orig, const int32_t* __restrict__ grpb,
     const uint8_t* __restrict__ rowb, Cells cells, const Geo* __restrict__ geo, NbPrm P,
     int32_t* choice_dn, int32_t* choice_up, float* d2out, int32_t* st, int32_t* ovf_queue,
@@ -541,7 +544,8 @@ __global__ void __launch_bounds__(256) k_neighbours_first(
             next_queue[atomicAdd(&st[next_slot], 1)] = (int32_t)c;
             continue;
         }
-        const float xc = geo->row_xf[r], yc = yb[c], zc = zb[c];
+        const float2 vc = yzb[c];
+        const float xc = geo->row_xf[r], yc = vc.x, zc = vc.y;
         const float xd = geo->row_xf[r - 1], xu = geo->row_xf[r + 1];
         // up list
         float uy[NF], uz[NF];
@@ -552,7 +556,8 @@ __global__ void __launch_bounds__(256) k_neighbours_first(
             int b, e;
             cell_run(cells, wu, iz, b, e);
             for (int q = b; q < e; ++q) {
-                const float yq = yb[q], zq = zb[q];
+                const float2 vq = yzb[q];
+                const float yq = vq.x, zq = vq.y;
                 if (!in_win(xc, yc, zc, xu, yq, zq, P.win_y, P.win_z)) continue;
 #pragma unroll
                 for (int k = 0; k < NF; ++k)
@@ -576,7 +581,8 @@ __global__ void __launch_bounds__(256) k_neighbours_first(
                 int b, e;
                 cell_run(cells, wd, iz, b, e);
                 for (int d = b; d < e; ++d) {
-                    const float ydd = yb[d], zdd = zb[d];
+                    const float2 vd = yzb[d];
+                    const float ydd = vd.x, zdd = vd.y;
                     if (!in_win(xc, yc, zc, xd, ydd, zdd, P.win_y, P.win_z)) continue;
 #pragma unroll
                     for (int k = 0; k < NF; ++k) {
@@ -613,7 +619,7 @@ __global__ void __launch_bounds__(256) k_neighbours_first(
 // (smallest D^2, then canonical id of u, then of d).
 __global__ void __launch_bounds__(NB_WARPS * 32) k_neighbours_warp(
     const int32_t* __restrict__ queue, const int32_t* __restrict__ st,
-    const float* __restrict__ yb, const float* __restrict__ zb,
+    const float2* __restrict__ yzb,
     const int32_t* __restrict__ orig, const int32_t* __restrict__ grpb,
     const uint8_t* __restrict__ rowb, Cells cells, const Geo* __restrict__ geo, NbPrm P,
     int32_t* choice_dn, int32_t* choice_up, float* d2out) {
@@ -627,7 +633,8 @@ __global__ void __launch_bounds__(NB_WARPS * 32) k_neighbours_warp(
     for (int64_t qi = wid; qi < nq; qi += nw) {
         const int64_t c = queue[qi];
         const int g = grpb[c], r = rowb[c];
-        const float xc = geo->row_xf[r], yc = yb[c], zc = zb[c];
+        const float2 vc = yzb[c];
+        const float xc = geo->row_xf[r], yc = vc.x, zc = vc.y;
         unsigned built = 0;  // bit k: list k (k < 3: down rows r-1-k, k >= 3: up rows r+k-2)
         int bd = -1, bu = -1;
         float bd2 = 0.f;
@@ -655,8 +662,9 @@ __global__ void __launch_bounds__(NB_WARPS * 32) k_neighbours_warp(
                             float yq = 0.f, zq = 0.f;
                             bool pass = false;
                             if (q < e) {
-                                yq = yb[q];
-                                zq = zb[q];
+                                const float2 vq = yzb[q];
+                                yq = vq.x;
+                                zq = vq.y;
                                 pass = in_win(xc, yc, zc, xr, yq, zq, P.win_y, P.win_z);
                             }
                             const unsigned bal = __ballot_sync(0xffffffffu, pass);
@@ -680,7 +688,7 @@ __global__ void __launch_bounds__(NB_WARPS * 32) k_neighbours_warp(
                     int sd = -1, su = -1;
                     float s2 = 0.f;
                     if (lane == 0)
-                        pair_scan_serial(c, gd, gu, yb, zb, orig, g, r, xc, yc, zc, cells, geo, P, sd, su, s2);
+                        pair_scan_serial(c, gd, gu, yzb, orig, g, r, xc, yc, zc, cells, geo, P, sd, su, s2);
                     bd = __shfl_sync(0xffffffffu, sd, 0);
                     bu = __shfl_sync(0xffffffffu, su, 0);
                     bd2 = __shfl_sync(0xffffffffu, s2, 0);
@@ -779,10 +787,14 @@ __global__ void k_links(int64_t n, const int32_t* __restrict__ cdn, const int32_
 }
 
 // ---------------------------------------------------------------- S3 ------
+// Chains of links from their lower ends; each one of at least n_seg
+// clusters takes a segment slot, whose row table (the chain's cluster per
+// row, -1 elsewhere) and row mask it writes for the tracklet lanes.
 __global__ void k_chains(int64_t n, const int32_t* __restrict__ link_dn,
                          const int32_t* __restrict__ link_up, const int32_t* __restrict__ orig,
-                         const int32_t* __restrict__ grpb, int n_seg, int64_t Scap,
-                         int32_t* seg_start, int32_t* seg_grp, int32_t* seg_canon, int32_t* st) {
+                         const int32_t* __restrict__ grpb, const uint8_t* __restrict__ rowb, int n_seg,
+                         int64_t Scap, int32_t* seg_start, int32_t* seg_grp, int32_t* seg_canon,
+                         int32_t* tl_rowhit, uint4* tl_mask, int32_t* st) {
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
          c += (int64_t)gridDim.x * blockDim.x) {
         if (link_dn[c] >= 0 || link_up[c] < 0) continue;
@@ -802,6 +814,25 @@ __global__ void k_chains(int64_t n, const int32_t* __restrict__ link_dn,
         seg_start[slot] = (int32_t)c;
         seg_grp[slot] = grpb[c];
         seg_canon[slot] = mn;
+        int32_t* hit = tl_rowhit + (int64_t)slot * NROW;
+        int4* h4 = reinterpret_cast<int4*>(hit);  // NROW * 4 bytes per slot: 16-byte aligned
+        for (int i = 0; i < NROW / 4; ++i) h4[i] = make_int4(-1, -1, -1, -1);
+        uint32_t m0 = 0, m1 = 0, m2 = 0, m3 = 0, m4 = 0;
+        cur = (int)c;
+        for (int k = 0; k < len; ++k) {
+            const int rr = rowb[cur];
+            hit[rr] = cur;
+            const uint32_t bit = 1u << (rr & 31);
+            const int w = rr >> 5;
+            m0 |= w == 0 ? bit : 0u;
+            m1 |= w == 1 ? bit : 0u;
+            m2 |= w == 2 ? bit : 0u;
+            m3 |= w == 3 ? bit : 0u;
+            m4 |= w == 4 ? bit : 0u;
+            cur = link_up[cur];
+        }
+        tl_mask[2 * (int64_t)slot] = make_uint4(m0, m1, m2, m3);
+        tl_mask[2 * (int64_t)slot + 1] = make_uint4(m4, 0u, 0u, 0u);
     }
 }
 
@@ -833,23 +864,81 @@ struct TlPrm {
     float prior[5];
 };
 
-// Three-point seed (FP32) of the hits in a tracklet slot for one fit
-// direction: first, middle (n/2-th in fit order) and last hit.
-__device__ __forceinline__ void seed_slot(const int32_t* __restrict__ hit, int rmin, int rmax, int n, bool inward,
-                          const float* __restrict__ yb, const float* __restrict__ zb, int sector,
-                          const Geo* __restrict__ geo, const TlPrm& P, KF& s) {
+// Rows holding a hit of a tracklet: bit r of the 152-bit mask m[0..4].  The
+// word loops below are unrolled, so that the mask stays in registers.
+constexpr int MASK_W = 5;
+// highest row below r with a hit, -1 if none
+__device__ __forceinline__ int mask_below(const uint32_t (&m)[MASK_W], int r) {
+    int best = -1;
+#pragma unroll
+    for (int w = 0; w < MASK_W; ++w) {
+        const int k = r - 32 * w;  // bits 0..k-1 of word w lie below r
+        const uint32_t b = k <= 0 ? 0u : k >= 32 ? m[w] : m[w] & ((1u << k) - 1u);
+        if (b) best = 32 * w + 31 - __clz(b);
+    }
+    return best;
+}
+// lowest row above r with a hit, NROW if none
+__device__ __forceinline__ int mask_above(const uint32_t (&m)[MASK_W], int r) {
+    int best = NROW;
+#pragma unroll
+    for (int w = MASK_W - 1; w >= 0; --w) {
+        const int k = r + 1 - 32 * w;  // bits k..31 of word w lie above r
+        const uint32_t b = k <= 0 ? m[w] : k >= 32 ? 0u : m[w] & ~((1u << k) - 1u);
+        if (b) best = 32 * w + __ffs(b) - 1;
+    }
+    return best;
+}
+// row of the j-th hit (from 0) counted from the top or from the bottom
+__device__ __forceinline__ int mask_nth(const uint32_t (&m)[MASK_W], int j, bool from_top) {
+    int row = -1, left = j;
+#pragma unroll
+    for (int i = 0; i < MASK_W; ++i) {
+        const int w = from_top ? MASK_W - 1 - i : i;
+        const uint32_t mw = from_top ? m[MASK_W - 1 - i] : m[i];  // static indices only
+        const int c = __popc(mw);
+        if (row < 0) {
+            if (left < c) {
+                uint32_t b = mw;
+                if (from_top) {
+                    for (int t = 0; t < left; ++t) b &= ~(1u << (31 - __clz(b)));
+                    row = 32 * w + 31 - __clz(b);
+                } else {
+                    for (int t = 0; t < left; ++t) b &= b - 1u;
+                    row = 32 * w + __ffs(b) - 1;
+                }
+            } else {
+                left -= c;
+            }
+        }
+    }
+    return row;
+}
+__device__ __forceinline__ void mask_set(uint32_t (&m)[MASK_W], int r) {
+    const uint32_t bit = 1u << (r & 31);
+    const int wr = r >> 5;
+#pragma unroll
+    for (int w = 0; w < MASK_W; ++w) m[w] |= wr == w ? bit : 0u;
+}
+
+// Three-point seed (FP32) of a tracklet's hits for one fit direction:
+// first, middle (n/2-th in fit order) and last hit.
+__device__ __forceinline__ void seed_mask(const int32_t* hit, const uint32_t (&m)[MASK_W], int rmin, int rmax,
+                                          int n, bool inward, const float2* __restrict__ yzb, int sector,
+                                          const Geo* __restrict__ geo, const TlPrm& P, KF& s) {
     int rows[3];
+    rows[0] = inward ? rmax : rmin;
+    rows[1] = mask_nth(m, n / 2, inward);
+    rows[2] = inward ? rmin : rmax;
+    int h[3];
     float ys[3], zs[3];
-    const int want = n / 2;
-    int k = 0;
-    for (int j = 0; j <= rmax - rmin; ++j) {
-        const int r = inward ? rmax - j : rmin + j;
-        const int h = hit[r];
-        if (h < 0) continue;
-        if (k == 0) { rows[0] = r; ys[0] = yb[h]; zs[0] = zb[h]; }
-        if (k == want) { rows[1] = r; ys[1] = yb[h]; zs[1] = zb[h]; }
-        if (k == n - 1) { rows[2] = r; ys[2] = yb[h]; zs[2] = zb[h]; }
-        ++k;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) h[i] = hit[rows[i]];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const float2 v = __ldg(&yzb[h[i]]);
+        ys[i] = v.x;
+        zs[i] = v.y;
     }
     kf_seed_f(s, rows, sector, ys, zs, inward, geo, P.kb, (float)P.seed_snp, (float)P.seed_qpt, P.prior);
 }
@@ -868,21 +957,23 @@ __device__ __forceinline__ void seed_slot(const int32_t* __restrict__ hit, int r
 // empty rows, at the last row, on a transport failure, or when the
 // prediction leaves the row's acceptance.  Finished lanes take the next slot
 // from an atomic work queue.
+// The slot's row table and row mask are prepared before the launch (by the
+// chain kernel for the build, by the keep kernel for the refit); a lane
+// keeps the mask in registers, so that the next hit row of a fit is known
+// without a load and the hit's coordinates are fetched before the transport.
 enum { PH_FIT_IN = 0, PH_EXT_IN = 1, PH_FIT_OUT = 2, PH_EXT_OUT = 3 };
+constexpr int EXT_ZB = 2;  // z cells of an extension window read in one batch
+constexpr int EXT_CH = 4;  // candidate loads in flight per lane
 
 __global__ void __launch_bounds__(128, 4) k_tracklet_lanes(
-    int refit, const int32_t* __restrict__ seg_start, const int32_t* __restrict__ seg_grp,
-    const int32_t* __restrict__ seg_canon, const int32_t* __restrict__ link_up,
-    const float* __restrict__ yb, const float* __restrict__ zb, const int32_t* __restrict__ orig,
-    const uint8_t* __restrict__ rowb, Cells cells, const Geo* __restrict__ geo, TlPrm P,
-    const int32_t* __restrict__ perm, int64_t Scap, int32_t* st, int32_t* tl_rowhit, int32_t* tl_n,
-    unsigned long long* tl_key,
-    const int32_t* __restrict__ tl_keep, const int32_t* __restrict__ tl_rmin_in,
-    const int32_t* __restrict__ tl_rmax_in, float* tl_state, int32_t* tl_ok, int tile) {
-    const int nseg = min((int64_t)st[ST_NSEG], Scap);
-    const int nitems = nseg;
+    int refit, const int32_t* __restrict__ items, int count_slot, const int32_t* __restrict__ seg_grp,
+    const int32_t* __restrict__ seg_canon, const float2* __restrict__ yzb, const int32_t* __restrict__ orig,
+    Cells cells, const Geo* __restrict__ geo, TlPrm P, int64_t Scap, int32_t* st, int32_t* tl_rowhit,
+    const uint4* __restrict__ tl_mask, int32_t* tl_n, unsigned long long* tl_key, float* tl_state,
+    int32_t* tl_ok, int4* gs_meta, int tile) {
+    const int nitems = min((int64_t)st[count_slot], Scap);
     int32_t* queue = &st[refit ? ST_Q_REFIT : ST_Q_BUILD];
-    int s = -1, phase = 0, r = 0, rmin = 0, rmax = 0, n = 0, misses = 0, g = 0, sector = 0, ok = 0;
+    int s = -1, item = 0, phase = 0, r = 0, rmin = 0, rmax = 0, n = 0, misses = 0, g = 0, sector = 0, ok = 0;
     int xr = 0;  // row plane of the state (the state never leaves its sector)
     int steps = 0;
     // z cells of the slot's group
@@ -890,17 +981,18 @@ __global__ void __launch_bounds__(128, 4) k_tracklet_lanes(
     int gnz = 1, gkb = 0;
     int t_next = 0, t_end = 0;  // slots of the current ticket
     int32_t* hit = nullptr;
+    uint32_t m[MASK_W];
     KF kf;
     for (;;) {
         if (s < 0) {
-            // take the next slot (a ticket covers `tile` consecutive slots)
+            // take the next slot (a ticket covers `tile` consecutive items)
             if (t_next >= t_end) {
                 t_next = atomicAdd(queue, tile);
                 t_end = t_next + tile;
             }
-            const int item = t_next++;
+            item = t_next++;
             if (item >= nitems) break;
-            s = perm[item];
+            s = items[item];
             hit = tl_rowhit + (int64_t)s * NROW;
             g = seg_grp[s];
             sector = g % NSEC;
@@ -909,31 +1001,18 @@ __global__ void __launch_bounds__(128, 4) k_tracklet_lanes(
             ginv = cells.inv[g];
             gnz = cells.nz[g];
             gkb = cells.kbase[g];
-            if (refit) {
-                if (!tl_keep[s]) {
-                    s = -1;
-                    continue;
-                }
-                rmin = tl_rmin_in[s];
-                rmax = tl_rmax_in[s];
-                n = 0;
-                for (int rr = rmin; rr <= rmax; ++rr) n += hit[rr] >= 0;
-            } else {
-                for (int rr = 0; rr < NROW; ++rr) hit[rr] = -1;
-                rmin = NROW;
-                rmax = -1;
-                n = 0;
-                for (int c = seg_start[s]; c >= 0; c = link_up[c]) {
-                    const int rr = rowb[c];
-                    hit[rr] = c;
-                    rmin = min(rmin, rr);
-                    rmax = max(rmax, rr);
-                    ++n;
-                }
-            }
+            const uint4 ma = tl_mask[2 * (int64_t)s], mb = tl_mask[2 * (int64_t)s + 1];
+            m[0] = ma.x;
+            m[1] = ma.y;
+            m[2] = ma.z;
+            m[3] = ma.w;
+            m[4] = mb.x;
+            n = __popc(m[0]) + __popc(m[1]) + __popc(m[2]) + __popc(m[3]) + __popc(m[4]);
+            rmin = mask_above(m, -1);
+            rmax = mask_below(m, NROW);
             misses = 0;
             phase = PH_FIT_IN;
-            seed_slot(hit, rmin, rmax, n, true, yb, zb, sector, geo, P, kf);
+            seed_mask(hit, m, rmin, rmax, n, true, yzb, sector, geo, P, kf);
             xr = rmax;
             r = rmax + 1;
         }
@@ -941,12 +1020,17 @@ __global__ void __launch_bounds__(128, 4) k_tracklet_lanes(
         const bool fit = phase == PH_FIT_IN || phase == PH_FIT_OUT;
         const int dir = (phase == PH_FIT_IN || phase == PH_EXT_IN) ? -1 : 1;
         int target = r + dir;
-        if (fit) {
-            while (target >= rmin && target <= rmax && hit[target] < 0) target += dir;
-        }
+        if (fit) target = dir < 0 ? mask_below(m, r) : mask_above(m, r);
         bool end_phase;
         if (fit) end_phase = target < rmin || target > rmax;
         else end_phase = target < 0 || target >= NROW || misses >= P.ext_max_miss;
+        // a fit step's hit, fetched before the transport
+        int c = -1;
+        float2 cv = make_float2(0.f, 0.f);
+        if (fit && !end_phase) {
+            c = hit[target];
+            cv = __ldg(&yzb[c]);
+        }
         bool moved = false;
         if (!end_phase) {
             // within one sector the planes are rows: the step is an exact
@@ -960,10 +1044,7 @@ __global__ void __launch_bounds__(128, 4) k_tracklet_lanes(
                 end_phase = true;
         }
         if (!end_phase) {
-            int c = -1;
-            if (fit) {
-                c = hit[target];
-            } else {
+            if (!fit) {
                 const float S00 = kf.C[0] + P.sy2, S01 = kf.C[1], S11 = kf.C[5] + P.sz2;
                 const float det = S00 * S11 - S01 * S01;
                 const float wz = sqrtf(P.chi2_ext * S11) * 1.001f + 1e-3f;
@@ -975,28 +1056,62 @@ __global__ void __launch_bounds__(128, 4) k_tracklet_lanes(
                 const int k1 = min(f1 >= 0.f ? (int)f1 : 0, gnz - 1);
                 const float yp = kf.p[0] + kf.lo[0];
                 const int y0 = ycell(geo, target, yp - wy - 1e-3f), y1 = ycell(geo, target, yp + wy + 1e-3f);
-                int bo = 0;
                 float bchi = 0.f;
-                for (int kz = k0; kz <= k1; ++kz) {
-                    const int b = cells.off[cb + kz * CELL_NY + y0], e = cells.off[cb + kz * CELL_NY + y1 + 1];
-#pragma unroll 4
-                    for (int q = b; q < e; ++q) {
-                        const float r1 = (zb[q] - kf.p[1]) - kf.lo[1];
-                        if (fabsf(r1) > wz) continue;
-                        const float r0 = (yb[q] - kf.p[0]) - kf.lo[0];
-                        if (fabsf(r0) > wy) continue;
-                        const float chi = (r0 * r0 * S11 - 2.f * r0 * r1 * S01 + r1 * r1 * S00) / det;
-                        if (!(chi <= P.chi2_ext)) continue;
-                        const int oq = orig[q];
-                        if (c < 0 || chi < bchi || (chi == bchi && oq < bo)) {
-                            c = q;
-                            bchi = chi;
-                            bo = oq;
-                        }
+                // best candidate so far: smallest chi2, then smaller
+                // canonical id (read only on an exact tie)
+                auto consider = [&](int q, float2 vq) {
+                    const float r1 = (vq.y - kf.p[1]) - kf.lo[1];
+                    const float r0 = (vq.x - kf.p[0]) - kf.lo[0];
+                    if (fabsf(r1) > wz || fabsf(r0) > wy) return;
+                    const float chi = (r0 * r0 * S11 - 2.f * r0 * r1 * S01 + r1 * r1 * S00) / det;
+                    if (!(chi <= P.chi2_ext)) return;
+                    if (c < 0 || chi < bchi || (chi == bchi && __ldg(&orig[q]) < __ldg(&orig[c]))) {
+                        c = q;
+                        cv = vq;
+                        bchi = chi;
                     }
+                };
+                // The runs of the first EXT_ZB z cells: their offsets are
+                // loaded in one batch and their candidates walked as one
+                // list, EXT_CH loads in flight at a time.
+                int qb[EXT_ZB], qe[EXT_ZB];
+#pragma unroll
+                for (int i = 0; i < EXT_ZB; ++i) {
+                    const int at = cb + (k0 + i) * CELL_NY;
+                    const bool in = k0 + i <= k1;
+                    qb[i] = in ? __ldg(&cells.off[at + y0]) : 0;
+                    qe[i] = in ? __ldg(&cells.off[at + y1 + 1]) : 0;
+                }
+                int pre[EXT_ZB + 1];
+                pre[0] = 0;
+#pragma unroll
+                for (int i = 0; i < EXT_ZB; ++i) pre[i + 1] = pre[i] + (qe[i] - qb[i]);
+                for (int t0 = 0; t0 < pre[EXT_ZB]; t0 += EXT_CH) {
+                    int qq[EXT_CH];
+                    float2 vv[EXT_CH];
+#pragma unroll
+                    for (int j = 0; j < EXT_CH; ++j) {
+                        const int t = t0 + j;
+                        int q = qb[EXT_ZB - 1] + (t - pre[EXT_ZB - 1]);
+#pragma unroll
+                        for (int i = EXT_ZB - 2; i >= 0; --i)
+                            if (t < pre[i + 1]) q = qb[i] + (t - pre[i]);
+                        qq[j] = q;
+                        if (t < pre[EXT_ZB]) vv[j] = __ldg(&yzb[q]);
+                    }
+#pragma unroll
+                    for (int j = 0; j < EXT_CH; ++j)
+                        if (t0 + j < pre[EXT_ZB]) consider(qq[j], vv[j]);
+                }
+                for (int kz = k0 + EXT_ZB; kz <= k1; ++kz) {
+                    const int b = __ldg(&cells.off[cb + kz * CELL_NY + y0]);
+                    const int e = __ldg(&cells.off[cb + kz * CELL_NY + y1 + 1]);
+#pragma unroll 4
+                    for (int q = b; q < e; ++q) consider(q, __ldg(&yzb[q]));
                 }
                 if (c >= 0) {
                     hit[target] = c;
+                    mask_set(m, target);
                     ++n;
                     if (dir < 0) rmin = target; else rmax = target;
                     misses = 0;
@@ -1004,7 +1119,7 @@ __global__ void __launch_bounds__(128, 4) k_tracklet_lanes(
                     ++misses;
                 }
             }
-            if (c >= 0) kf_update(kf, yb[c], zb[c], P.sy2, P.sz2, P.fp64_ratio, P.fp64_det, &st[ST_FP64], nullptr);
+            if (c >= 0) kf_update(kf, cv.x, cv.y, P.sy2, P.sz2, P.fp64_ratio, P.fp64_det, &st[ST_FP64], nullptr);
             r = target;
             continue;
         }
@@ -1057,6 +1172,8 @@ __global__ void __launch_bounds__(128, 4) k_tracklet_lanes(
                     for (int i = 0; i < 15; ++i) out[25 + i] = kf.C[i];
                 }
                 tl_ok[s] = ok;
+                // the fit flags of the merge's per-position record
+                gs_meta[item].x = rmax | (rmin << 8) | (ok << 16);
                 s = -1;
                 continue;
             }
@@ -1068,7 +1185,7 @@ __global__ void __launch_bounds__(128, 4) k_tracklet_lanes(
             }
         }
         if (phase == PH_FIT_OUT) {
-            seed_slot(hit, rmin, rmax, n, false, yb, zb, sector, geo, P, kf);
+            seed_mask(hit, m, rmin, rmax, n, false, yzb, sector, geo, P, kf);
             xr = rmin;
             r = rmin - 1;
             continue;
@@ -1097,11 +1214,11 @@ __global__ void k_owner(const int32_t* __restrict__ tl_rowhit, const unsigned lo
 // per slot, the lanes over the rows.
 __global__ void k_keep(int32_t* tl_rowhit, const unsigned long long* __restrict__ tl_key,
                        const unsigned long long* __restrict__ owner, const int32_t* __restrict__ seg_grp,
-                       const float* __restrict__ zb, const int32_t* __restrict__ orig, int n_seg,
+                       const float2* __restrict__ yzb, const int32_t* __restrict__ orig, int n_seg,
                        int64_t Scap, int32_t* st, int32_t* tl_keep, int32_t* tl_canon,
                        int32_t* tl_rmin, int32_t* tl_rmax, float* tl_zin, float* tl_zout,
                        int32_t* tl_ok, int32_t* grp_tl_cnt, TlBins tb, int32_t* tl_binkey,
-                       int64_t KT) {
+                       int64_t KT, uint4* tl_mask) {
     const int nseg = min((int64_t)st[ST_NSEG], Scap);
     const int lane = threadIdx.x & 31;
     const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -1111,7 +1228,10 @@ __global__ void k_keep(int32_t* tl_rowhit, const unsigned long long* __restrict_
         const unsigned long long key = tl_key[s];
         int n = 0, rmin = NROW, rmax = -1;
         int32_t canon = 0x7fffffff;
-        for (int r0 = 0; r0 < NROW; r0 += 32) {
+        uint32_t mw[MASK_W];
+#pragma unroll
+        for (int w = 0; w < MASK_W; ++w) {
+            const int r0 = 32 * w;
             const int r = r0 + lane;
             bool own = false;
             if (r < NROW) {
@@ -1125,6 +1245,7 @@ __global__ void k_keep(int32_t* tl_rowhit, const unsigned long long* __restrict_
                 }
             }
             const unsigned m = __ballot_sync(0xffffffffu, own);
+            mw[w] = m;
             if (m) {
                 n += __popc(m);
                 rmin = min(rmin, r0 + __ffs(m) - 1);
@@ -1140,12 +1261,14 @@ __global__ void k_keep(int32_t* tl_rowhit, const unsigned long long* __restrict_
         }
         const int g = seg_grp[s];
         tl_keep[s] = 1;
+        tl_mask[2 * s] = make_uint4(mw[0], mw[1], mw[2], mw[3]);
+        tl_mask[2 * s + 1] = make_uint4(mw[4], 0u, 0u, 0u);
         tl_canon[s] = canon;
         tl_rmin[s] = rmin;
         tl_rmax[s] = rmax;
-        tl_zin[s] = zb[hit[rmin]];
-        tl_zout[s] = zb[hit[rmax]];
-        const int bkey = tb.base[g] + tl_bin(tb, g, zb[hit[rmax]]);
+        tl_zin[s] = yzb[hit[rmin]].y;
+        tl_zout[s] = yzb[hit[rmax]].y;
+        const int bkey = tb.base[g] + tl_bin(tb, g, yzb[hit[rmax]].y);
         if (!in_range(bkey, KT, st, 301)) {
             tl_keep[s] = 0;
             continue;
@@ -1161,7 +1284,7 @@ __global__ void k_tl_scatter(const int32_t* __restrict__ tl_keep, const int32_t*
                              int32_t* grp_tl_cur, int32_t* tl_sorted,
                              const int32_t* __restrict__ tl_rmin, const int32_t* __restrict__ tl_rmax,
                              const float* __restrict__ tl_zin, const float* __restrict__ tl_zout,
-                             const int32_t* __restrict__ tl_ok, int4* gs_meta,
+                             int4* gs_meta,
                              const int32_t* __restrict__ tl_binkey, int32_t* st_w) {
     const int nseg = min((int64_t)st[ST_NSEG], Scap);
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nseg; s += gridDim.x * blockDim.x) {
@@ -1171,7 +1294,8 @@ __global__ void k_tl_scatter(const int32_t* __restrict__ tl_keep, const int32_t*
         if (!in_range(q, Scap, st_w, 302)) continue;
         tl_sorted[q] = s;
         // packed per-position merge data read coalesced by the candidate search
-        gs_meta[q] = make_int4(tl_rmax[s] | (tl_rmin[s] << 8) | (tl_ok[s] << 16),
+        // (the refit adds its fit flags in bits 16-17)
+        gs_meta[q] = make_int4(tl_rmax[s] | (tl_rmin[s] << 8),
                                __float_as_int(tl_zout[s]), __float_as_int(tl_zin[s]), s);
     }
 }
@@ -1184,8 +1308,6 @@ struct MgPrm {
     float kbf, snp_maxf, pitch;
     int64_t KT, S;
 };
-
-// 5x5 SPD chi2 = dp^T M^-1 dp by Cholesky (FP64); false if not SPD
 
 __device__ __forceinline__ bool ma_ok(const int4* __restrict__ gs_meta, int qa, int b) {
     return gs_meta[qa].w != b;
@@ -1557,14 +1679,13 @@ cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hi
                                        W.at<int32_t>(L.cell_cnt), W.at<int32_t>(L.key_in),
                                        W.at<int32_t>(L.slot_in), L.K);
     TPC_TRY(scan_i32(W.at<int32_t>(L.cell_cnt), W.at<int32_t>(L.cell_off), L.K, scan_tmp, s));
-    float* yb = W.at<float>(L.yb);
-    float* zb = W.at<float>(L.zb);
+    float2* yzb = W.at<float2>(L.yzb);
     int32_t* orig = W.at<int32_t>(L.orig);
     int32_t* grpb = W.at<int32_t>(L.grpb);
     uint8_t* rowb = W.at<uint8_t>(L.rowb);
     tpc::LaunchCount{}, k_scatter<<<grid_for(n), TPB, 0, s>>>(c->y, c->z, c->row, n, grp_of,
                                           W.at<int32_t>(L.key_in), W.at<int32_t>(L.slot_in),
-                                          W.at<int32_t>(L.cell_off), L.K, yb, zb, orig, grpb, rowb);
+                                          W.at<int32_t>(L.cell_off), L.K, yzb, orig, grpb, rowb);
     TPC_TRY(cudaGetLastError());
 
     c->mark(1, s);
@@ -1577,11 +1698,11 @@ cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hi
     int32_t* nb_queue2 = W.at<int32_t>(L.slot_in);  // free after S1
     // pass 1: gap pair (1, 1) for all; pass 2: the later gap pairs for the rest
     tpc::LaunchCount{}, k_neighbours_first<<<grid_for(n), TPB, 0, s>>>(
-        n, yb, zb, orig, grpb, rowb, cells, geo, nb, cdn, cup, d2, st, nb_queue, nb_queue2, ST_NB_Q2);
+        n, yzb, orig, grpb, rowb, cells, geo, nb, cdn, cup, d2, st, nb_queue, nb_queue2, ST_NB_Q2);
     tpc::LaunchCount{}, k_neighbours_sub<NG2><<<grid_for(n / 4, 32 * 4), ns_warps<NG2>() * 32, 0, s>>>(
-        n, nb_queue2, ST_NB_Q2, 3, 2 * NB_GAP_MAX, yb, zb, orig, grpb, rowb, cells, geo, nb, cdn, cup, d2, st,
+        n, nb_queue2, ST_NB_Q2, 3, 2 * NB_GAP_MAX, yzb, orig, grpb, rowb, cells, geo, nb, cdn, cup, d2, st,
         nb_queue, nullptr, 0);
-    tpc::LaunchCount{}, k_neighbours_warp<<<152 * 8, NB_WARPS * 32, 0, s>>>(nb_queue, st, yb, zb, orig, grpb,
+    tpc::LaunchCount{}, k_neighbours_warp<<<152 * 8, NB_WARPS * 32, 0, s>>>(nb_queue, st, yzb, orig, grpb,
                                                                         rowb, cells, geo, nb, cdn, cup, d2);
     c->mark(2, s);
     auto* claim_up = W.at<unsigned long long>(L.claim_up);
@@ -1597,9 +1718,11 @@ cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hi
 
     c->mark(3, s);
     // S3: chains
-    tpc::LaunchCount{}, k_chains<<<grid_for(n), TPB, 0, s>>>(n, ldn, lup, orig, grpb, p.n_seg, L.S,
+    int32_t* tl_rowhit = W.at<int32_t>(L.tl_rowhit);
+    auto* tl_mask = W.at<uint4>(L.tl_mask);
+    tpc::LaunchCount{}, k_chains<<<grid_for(n), TPB, 0, s>>>(n, ldn, lup, orig, grpb, rowb, p.n_seg, L.S,
                                          W.at<int32_t>(L.seg_start), W.at<int32_t>(L.seg_grp),
-                                         W.at<int32_t>(L.seg_canon), st);
+                                         W.at<int32_t>(L.seg_canon), tl_rowhit, tl_mask, st);
     // processing order of the segments (start clusters are unique)
     {
         int32_t* flag = W.at<int32_t>(L.trk_flag);
@@ -1633,12 +1756,11 @@ cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hi
     // persistent lanes: enough resident warps to fill the GPU
     const unsigned lgrid = 152u * (unsigned)c->tune.lane_blocks_per_sm;
     const int tile = c->tune.lane_tile;
-    int32_t* tl_rowhit = W.at<int32_t>(L.tl_rowhit);
     auto* tl_key = W.at<unsigned long long>(L.tl_key);
     tpc::LaunchCount{}, k_tracklet_lanes<<<lgrid, 128, 0, s>>>(
-        0, W.at<int32_t>(L.seg_start), W.at<int32_t>(L.seg_grp), W.at<int32_t>(L.seg_canon), lup, yb,
-        zb, orig, rowb, cells, geo, tp, W.at<int32_t>(L.seg_perm), L.S, st, tl_rowhit, W.at<int32_t>(L.tl_n), tl_key, nullptr,
-        nullptr, nullptr, nullptr, nullptr, tile);
+        0, W.at<int32_t>(L.seg_perm), ST_NSEG, W.at<int32_t>(L.seg_grp), W.at<int32_t>(L.seg_canon), yzb,
+        orig, cells, geo, tp, L.S, st, tl_rowhit, tl_mask, W.at<int32_t>(L.tl_n), tl_key, nullptr, nullptr,
+        nullptr, tile);
     c->mark(5, s);
     auto* owner = W.at<unsigned long long>(L.owner);
     tpc::LaunchCount{}, k_fill_u64<<<grid_for(n), TPB, 0, s>>>(owner, n, KEY_MAX);
@@ -1650,17 +1772,12 @@ cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hi
                                                    W.at<float>(L.tb_inv), W.at<int32_t>(L.tb_nb),
                                                    W.at<int32_t>(L.tb_base));
     TPC_TRY(fill_i32(grp_cnt, L.KT + 1, 0, s));
-    tpc::LaunchCount{}, k_keep<<<grid_for(L.S * 32, 128), 128, 0, s>>>(tl_rowhit, tl_key, owner, W.at<int32_t>(L.seg_grp), zb,
+    tpc::LaunchCount{}, k_keep<<<grid_for(L.S * 32, 128), 128, 0, s>>>(tl_rowhit, tl_key, owner, W.at<int32_t>(L.seg_grp), yzb,
                                  orig, p.n_seg, L.S, st, W.at<int32_t>(L.tl_keep),
                                  W.at<int32_t>(L.tl_canon), W.at<int32_t>(L.tl_rmin),
                                  W.at<int32_t>(L.tl_rmax), W.at<float>(L.tl_zin),
                                  W.at<float>(L.tl_zout), W.at<int32_t>(L.tl_ok), grp_cnt, tb,
-                                 W.at<int32_t>(L.tl_binkey), L.KT);
-    tpc::LaunchCount{}, k_tracklet_lanes<<<lgrid, 128, 0, s>>>(
-        1, W.at<int32_t>(L.seg_start), W.at<int32_t>(L.seg_grp), W.at<int32_t>(L.seg_canon), lup, yb,
-        zb, orig, rowb, cells, geo, tp, W.at<int32_t>(L.seg_perm), L.S, st, tl_rowhit, W.at<int32_t>(L.tl_n), tl_key,
-        W.at<int32_t>(L.tl_keep), W.at<int32_t>(L.tl_rmin), W.at<int32_t>(L.tl_rmax),
-        W.at<float>(L.tl_state), W.at<int32_t>(L.tl_ok), tile);
+                                 W.at<int32_t>(L.tl_binkey), L.KT, tl_mask);
     TPC_TRY(scan_i32(grp_cnt, W.at<int32_t>(L.grp_tl_off), L.KT, scan_tmp, s));
     TPC_TRY(fill_i32(W.at<int32_t>(L.grp_tl_cur), L.KT, 0, s));
     tpc::LaunchCount{}, k_tl_scatter<<<sgrid, 128, 0, s>>>(W.at<int32_t>(L.tl_keep), W.at<int32_t>(L.seg_grp),
@@ -1668,8 +1785,12 @@ cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hi
                                        W.at<int32_t>(L.grp_tl_cur), W.at<int32_t>(L.tl_sorted),
                                        W.at<int32_t>(L.tl_rmin), W.at<int32_t>(L.tl_rmax),
                                        W.at<float>(L.tl_zin), W.at<float>(L.tl_zout),
-                                       W.at<int32_t>(L.tl_ok), W.at<int4>(L.gs_meta),
-                                       W.at<int32_t>(L.tl_binkey), st);
+                                       W.at<int4>(L.gs_meta), W.at<int32_t>(L.tl_binkey), st);
+    // refit of the kept tracklets, in their merge order
+    tpc::LaunchCount{}, k_tracklet_lanes<<<lgrid, 128, 0, s>>>(
+        1, W.at<int32_t>(L.tl_sorted), ST_NTL, W.at<int32_t>(L.seg_grp), W.at<int32_t>(L.seg_canon), yzb,
+        orig, cells, geo, tp, L.S, st, tl_rowhit, tl_mask, W.at<int32_t>(L.tl_n), tl_key,
+        W.at<float>(L.tl_state), W.at<int32_t>(L.tl_ok), W.at<int4>(L.gs_meta), tile);
     c->mark(6, s);
     // S4: merge candidates and greedy matching
     MgPrm mp{p.merge_max_row_gap, p.merge_max_overlap, p.merge_z_slope, p.merge_z_margin,
