@@ -283,19 +283,36 @@ __device__ __forceinline__ bool in_win(float xa, float ya, float za, float xb, f
            fabsf(__fsub_rn(zb, za)) <= __fmul_rn(wz, dx);
 }
 
-// triplet D^2 (straight-line interpolation of c between d and u), FP32
-__device__ __forceinline__ float triplet_d2(float xd, float yd, float zd, float xc, float yc,
-                                            float zc, float xu, float yu, float zu, float sy2,
-                                            float sz2) {
-    const float a = __fdiv_rn(__fsub_rn(xc, xd), __fsub_rn(xu, xd));
-    const float yh = __fadd_rn(yd, __fmul_rn(a, __fsub_rn(yu, yd)));
-    const float zh = __fadd_rn(zd, __fmul_rn(a, __fsub_rn(zu, zd)));
-    const float ry = __fsub_rn(yc, yh);
-    const float rz = __fsub_rn(zc, zh);
-    const float b = __fsub_rn(1.0f, a);
-    const float f = __fadd_rn(__fadd_rn(1.0f, __fmul_rn(a, a)), __fmul_rn(b, b));
-    return __fadd_rn(__fdiv_rn(__fmul_rn(ry, ry), __fmul_rn(sy2, f)),
-                     __fdiv_rn(__fmul_rn(rz, rz), __fmul_rn(sz2, f)));
+// Triplet D^2, FP32 with one rounding per operation: c is compared with
+// the straight line from d to u at x_c, a = (x_c - x_d) / (x_u - x_d),
+//   D^2 = ry^2 / (sy2 f) + rz^2 / (sz2 f),  f = 1 + a^2 + (1 - a)^2.
+// The row-dependent part (a, f) is computed once per gap pair.  A pair with
+// D^2 <= chi2 has ry^2 <= chi2 sy2 f and rz^2 <= chi2 sz2 f; tested with a
+// relative margin of 1e-5 over the rounding, these bounds reject most pairs
+// before the two divisions, and leave D^2 unchanged for the others.
+struct TripletRows {
+    float a, dy, dz, ty, tz;
+};
+__device__ __forceinline__ TripletRows triplet_rows(float xd, float xc, float xu, float sy2, float sz2,
+                                                    float chi2) {
+    TripletRows t;
+    t.a = __fdiv_rn(__fsub_rn(xc, xd), __fsub_rn(xu, xd));
+    const float b = __fsub_rn(1.0f, t.a);
+    const float f = __fadd_rn(__fadd_rn(1.0f, __fmul_rn(t.a, t.a)), __fmul_rn(b, b));
+    t.dy = __fmul_rn(sy2, f);
+    t.dz = __fmul_rn(sz2, f);
+    t.ty = __fmul_rn(__fmul_rn(chi2, t.dy), 1.00001f);
+    t.tz = __fmul_rn(__fmul_rn(chi2, t.dz), 1.00001f);
+    return t;
+}
+// D^2 of the triplet (d, c, u), or +inf where the bounds show D^2 > chi2
+__device__ __forceinline__ float triplet_d2_cut(const TripletRows& t, float yd, float zd, float yc, float zc,
+                                                float yu, float zu) {
+    const float ry = __fsub_rn(yc, __fadd_rn(yd, __fmul_rn(t.a, __fsub_rn(yu, yd))));
+    const float rz = __fsub_rn(zc, __fadd_rn(zd, __fmul_rn(t.a, __fsub_rn(zu, zd))));
+    const float ry2 = __fmul_rn(ry, ry), rz2 = __fmul_rn(rz, rz);
+    if (ry2 > t.ty || rz2 > t.tz) return INFINITY;
+    return __fadd_rn(__fdiv_rn(ry2, t.dy), __fdiv_rn(rz2, t.dz));
 }
 
 // The cells holding every candidate of row rr that can pass in_win for the
@@ -320,6 +337,7 @@ __device__ void pair_scan_serial(int64_t c, int gd, int gu, const float2* __rest
     const float xd = geo->row_xf[rd], xu = geo->row_xf[ru];
     const CellWin wd = nb_win(cells, geo, g, rd, xd, xc, yc, zc, P);
     const CellWin wu = nb_win(cells, geo, g, ru, xu, xc, yc, zc, P);
+    const TripletRows tr = triplet_rows(xd, xc, xu, P.sy2, P.sz2, P.chi2_link);
     int pd = -1, pu = -1, pod = 0, pou = 0;
     float pd2 = 0.f;
     for (int izd = wd.iz0; izd <= wd.iz1; ++izd) {
@@ -336,7 +354,7 @@ __device__ void pair_scan_serial(int64_t c, int gd, int gu, const float2* __rest
             const float2 vu = yzb[u];
             const float yuu = vu.x, zuu = vu.y;
             if (!in_win(xc, yc, zc, xu, yuu, zuu, P.win_y, P.win_z)) continue;
-            const float d2 = triplet_d2(xd, ydd, zdd, xc, yc, zc, xu, yuu, zuu, P.sy2, P.sz2);
+            const float d2 = triplet_d2_cut(tr, ydd, zdd, yc, zc, yuu, zuu);
             if (!(d2 <= P.chi2_link)) continue;
             bool better = pd < 0 || d2 < pd2;
             if (!better && d2 == pd2) {
@@ -469,13 +487,15 @@ __global__ void __launch_bounds__(ns_warps<NG>() * 32) k_neighbours_sub(
                     break;
                 }
                 const float xd = geo->row_xf[rd], xu = geo->row_xf[ru];
+                const TripletRows tr = triplet_rows(xd, xc, xu, P.sy2, P.sz2, P.chi2_link);
                 int pd = -1, pu = -1, pod = 0, pou = 0;
                 float pd2 = 0.f;
                 const int total = nd * nu;
+                const float rnu = 1.f / (float)nu;
                 for (int pp = li; pp < total; pp += NG) {
-                    const int i = pp / nu, j = pp - i * nu;
-                    const float d2 = triplet_d2(xd, sh.y[kd][i], sh.z[kd][i], xc, yc, zc, xu,
-                                                sh.y[ku][j], sh.z[ku][j], P.sy2, P.sz2);
+                    // pp / nu: pp < 2^16, so the rounded quotient is exact
+                    const int i = (int)(((float)pp + 0.5f) * rnu), j = pp - i * nu;
+                    const float d2 = triplet_d2_cut(tr, sh.y[kd][i], sh.z[kd][i], yc, zc, sh.y[ku][j], sh.z[ku][j]);
                     if (!(d2 <= P.chi2_link)) continue;
                     const int d = sh.idx[kd][i], u = sh.idx[ku][j];
                     bool better = pd < 0 || d2 < pd2;
@@ -576,6 +596,7 @@ __global__ void __launch_bounds__(256) k_neighbours_first(
         int bd = -1, bu = -1, pod = 0, pou = 0;
         float bd2 = 0.f;
         if (nu > 0) {
+            const TripletRows tr = triplet_rows(xd, xc, xu, P.sy2, P.sz2, P.chi2_link);
             const CellWin wd = nb_win(cells, geo, g, r - 1, xd, xc, yc, zc, P);
             for (int iz = wd.iz0; iz <= wd.iz1; ++iz) {
                 int b, e;
@@ -587,7 +608,7 @@ __global__ void __launch_bounds__(256) k_neighbours_first(
 #pragma unroll
                     for (int k = 0; k < NF; ++k) {
                         if (k >= nu) break;
-                        const float d2 = triplet_d2(xd, ydd, zdd, xc, yc, zc, xu, uy[k], uz[k], P.sy2, P.sz2);
+                        const float d2 = triplet_d2_cut(tr, ydd, zdd, yc, zc, uy[k], uz[k]);
                         if (!(d2 <= P.chi2_link)) continue;
                         const int u = ui[k];
                         bool better = bd < 0 || d2 < bd2;
@@ -695,13 +716,13 @@ __global__ void __launch_bounds__(NB_WARPS * 32) k_neighbours_warp(
                     continue;
                 }
                 const float xd = geo->row_xf[rd], xu = geo->row_xf[ru];
+                const TripletRows tr = triplet_rows(xd, xc, xu, P.sy2, P.sz2, P.chi2_link);
                 int pd = -1, pu = -1, pod = 0, pou = 0;
                 float pd2 = 0.f;
                 const int total = nd * nu;
                 for (int p = lane; p < total; p += 32) {
                     const int i = p / nu, j = p - i * nu;
-                    const float d2 = triplet_d2(xd, sh.y[kd][i], sh.z[kd][i], xc, yc, zc, xu,
-                                                sh.y[ku][j], sh.z[ku][j], P.sy2, P.sz2);
+                    const float d2 = triplet_d2_cut(tr, sh.y[kd][i], sh.z[kd][i], yc, zc, sh.y[ku][j], sh.z[ku][j]);
                     if (!(d2 <= P.chi2_link)) continue;
                     const int d = sh.idx[kd][i], u = sh.idx[ku][j];
                     bool better = pd < 0 || d2 < pd2;
@@ -1057,13 +1078,14 @@ __global__ void __launch_bounds__(128, 4) k_tracklet_lanes(
                 const float yp = kf.p[0] + kf.lo[0];
                 const int y0 = ycell(geo, target, yp - wy - 1e-3f), y1 = ycell(geo, target, yp + wy + 1e-3f);
                 float bchi = 0.f;
+                const float idet = 1.f / det;
                 // best candidate so far: smallest chi2, then smaller
                 // canonical id (read only on an exact tie)
                 auto consider = [&](int q, float2 vq) {
                     const float r1 = (vq.y - kf.p[1]) - kf.lo[1];
                     const float r0 = (vq.x - kf.p[0]) - kf.lo[0];
                     if (fabsf(r1) > wz || fabsf(r0) > wy) return;
-                    const float chi = (r0 * r0 * S11 - 2.f * r0 * r1 * S01 + r1 * r1 * S00) / det;
+                    const float chi = (r0 * r0 * S11 - 2.f * r0 * r1 * S01 + r1 * r1 * S00) * idet;
                     if (!(chi <= P.chi2_ext)) return;
                     if (c < 0 || chi < bchi || (chi == bchi && __ldg(&orig[q]) < __ldg(&orig[c]))) {
                         c = q;
