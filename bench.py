@@ -36,7 +36,6 @@ WORKLOAD = ("central_event: 1 event x 36 sectors, 1e4 primary tracks (pT exp slo
             "min 0.2, |eta|<0.9), 20% noise, ~1.8e6 clusters, Bz 0.5 T")
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
 # algorithmic traffic / work per unit, fixed before measuring
-NEIGHBOUR_BYTES_PER_CLUSTER = 20.0      # read y,z (8); write down, up, D^2 (12)
 # the whole find + fit path, every intermediate product written once and read
 # once: binning 22, neighbours 16, chains and tracks 16, fit 12.7, scatter 12
 PATH_BYTES_PER_CLUSTER = 78.7
@@ -46,7 +45,7 @@ KF_FLOPS_PER_STEP = 350.0               # transport ~60 + covariance J C J^T ~16
 # DRAM bytes (read + write) of one build launch of k_tracklet_lanes on the
 # central event, from an ncu capture of this kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum); None for a kernel without a capture
-TRAFFIC_BYTES_PER_LAUNCH = {"k_tracklet_lanes": 35.419e6 + 3.320e6}
+TRAFFIC_BYTES_PER_LAUNCH = {"k_tracklet_lanes": 35.685e6 + 2.391e6}
 
 
 def batched_vs_plain(torch, tpc, dev, steps):
@@ -538,32 +537,26 @@ def run_ours(args):
     h2d = 4 * n + 4 * n + 2 * n + 8 * ev.evt_sector_off.size
     d2h = 4 * n + 4 + 20 * track_cap + 4 * track_cap
 
-    # roofline of the dominant kernel (single-kernel stages only)
+    # roofline of the dominant kernel: the longest launch among the stages
+    # that are one kernel each (the tracklet build, the fit); the neighbour
+    # stage is three kernels (first pass, later gap pairs, overflow)
     per_step = {k: v / args.steps for k, v in stage_sum.items()}
     hits_total = int(find_out[1][T].item()) if T > 0 else 0
     kernels = {
         "k_tracklet_lanes": per_step.get("tracklets", 0.0),
-        "k_neighbours_warp": per_step.get("neighbours", 0.0),
         "k_fit": per_step.get("fit", 0.0),
     }
     dom = max(kernels, key=kernels.get)
     hbm_peak, peak_src = measured_peaks()
     ms = kernels[dom]
-    if dom == "k_neighbours_warp":
-        achieved = n * NEIGHBOUR_BYTES_PER_CLUSTER / (ms * 1e-3) / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": None}
-    else:
-        # Kalman kernels are FP32-ALU work: counted steps x flops per step
-        work_steps = st.n_kf_steps if dom == "k_tracklet_lanes" else hits_total
-        achieved = work_steps * KF_FLOPS_PER_STEP / (ms * 1e-3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
-                "traffic": TRAFFIC_BYTES_PER_LAUNCH.get(dom), "kf_steps_per_launch": int(work_steps)}
-    roof["kernel"] = dom
-    roof["kernel_ms"] = ms
-    roof["peak_source"] = (peak_src + " (MEASURED_PEAKS.json hbm_gbs)" if roof["unit"] == "GB/s"
-                           else "derived: 152 SM x 128 FP32 lanes x 2 (FMA) x 2070 MHz")
+    # Kalman kernels are FP32-ALU work: counted steps x flops per step
+    work_steps = st.n_kf_steps if dom == "k_tracklet_lanes" else hits_total
+    achieved = work_steps * KF_FLOPS_PER_STEP / (ms * 1e-3) / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+            "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+            "traffic": TRAFFIC_BYTES_PER_LAUNCH.get(dom), "kf_steps_per_launch": int(work_steps),
+            "kernel": dom, "kernel_ms": ms,
+            "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 (FMA) x 2070 MHz"}
 
     if rank != 0:
         if world > 1:
@@ -586,7 +579,8 @@ def run_ours(args):
         "roofline": roof,
         "path_roofline": {"bound": "hbm", "bytes_per_cluster": PATH_BYTES_PER_CLUSTER,
                           "achieved": value * PATH_BYTES_PER_CLUSTER / 1e9, "peak": hbm_peak,
-                          "unit": "GB/s", "frac": value * PATH_BYTES_PER_CLUSTER / 1e9 / hbm_peak},
+                          "unit": "GB/s", "frac": value * PATH_BYTES_PER_CLUSTER / 1e9 / hbm_peak,
+                          "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)"},
         "status": {"fp64_updates": st.n_fp64_updates, "segments": st.n_segments,
                    "tracklets": st.n_tracklets, "merges": st.n_merges},
     }
