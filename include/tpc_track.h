@@ -244,7 +244,7 @@ tpc_status tpc_stage_times(tpc_ctx* ctx, float* ms_out);
  * race on the array and corrupt each other's results: serialise them. */
 #define TPC_NOALLOC_MAX_CLUSTERS 65536
 #define TPC_NOALLOC_MAX_EVENTS 4
-#define TPC_NOALLOC_SCRATCH_BYTES (16u << 20)
+#define TPC_NOALLOC_SCRATCH_BYTES (20u << 20)
 tpc_status tpc_find_tracks_noalloc(const tpc_params* params, const float* y, const float* z,
                                    const uint16_t* row, int64_t n, const int64_t* evt_sector_off,
                                    int32_t n_events, int32_t* track_of_cluster, int32_t* trk_off,

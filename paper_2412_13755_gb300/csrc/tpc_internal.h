@@ -21,8 +21,8 @@ constexpr int NSEC = 36;
 constexpr int NPHI = 18;
 constexpr int NROW = 152;
 constexpr int MAX_CAND = 16;     // merge candidates kept per tracklet
-constexpr int CELL_OCC = 2;      // target clusters per (row, z-cell, y-cell)
-constexpr int CELL_NY = 8;       // y cells per (row, z-cell), uniform in y / (x tan 10 deg)
+constexpr int CELL_OCC = 1;      // target clusters per (row, z-cell, y-cell)
+constexpr int CELL_NY = 16;      // y cells per (row, z-cell), uniform in y / (x tan 10 deg)
 constexpr int NZ_MAX = 8192;     // z cells per row at most
 
 // Geometry table written into the workspace at set-up.
