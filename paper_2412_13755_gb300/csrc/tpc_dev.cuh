@@ -360,8 +360,24 @@ __device__ __forceinline__ ff ff_rcp(ff x) {
     const ff one_minus = ff_add(ff_from(1.f), ff_neg(xr));
     return ff_add(ff_from(r), ff_mul_f(one_minus, r));
 }
-// acc + x * f
-__device__ __forceinline__ ff ff_fma_f(ff acc, ff x, float f) { return ff_add(acc, ff_mul_f(x, f)); }
+// acc + x * f: the product's error term joins the sum's low part, with one
+// renormalisation at the end
+__device__ __forceinline__ ff ff_fma_f(ff acc, ff x, float f) {
+    const float p = __fmul_rn(x.hi, f);
+    const float e = __fmaf_rn(x.lo, f, __fmaf_rn(x.hi, f, -p));
+    const ff s = two_sum(acc.hi, p);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(acc.lo, e)));
+}
+// x1 y1 + x2 y2 in float-float: both products as (p, e) with p = fl(x.hi
+// y.hi) and e the rest (TwoProduct through the FMA, plus the cross terms),
+// the two p summed exactly and the errors added to the low part
+__device__ __forceinline__ ff ff_dot2(ff x1, ff y1, ff x2, ff y2) {
+    const float p1 = __fmul_rn(x1.hi, y1.hi), p2 = __fmul_rn(x2.hi, y2.hi);
+    const float e1 = __fmaf_rn(x1.lo, y1.hi, __fmaf_rn(x1.hi, y1.lo, __fmaf_rn(x1.hi, y1.hi, -p1)));
+    const float e2 = __fmaf_rn(x2.lo, y2.hi, __fmaf_rn(x2.hi, y2.lo, __fmaf_rn(x2.hi, y2.hi, -p2)));
+    const ff s = two_sum(p1, p2);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(e1, e2)));
+}
 
 // sqrt(x) for x > 0: the FP32 root refined by one Newton (Heron) step
 // s + (x - s^2) / (2 s), the residual x - s^2 formed exactly with TwoProduct
@@ -486,14 +502,14 @@ __device__ __forceinline__ float kf_update_ff(KF& s, ff C[15], float my, float m
     }
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
-        K0[i] = ff_add(ff_mul(C0[i], i00), ff_mul(C1[i], i01));
-        K1[i] = ff_add(ff_mul(C0[i], i01), ff_mul(C1[i], i11));
+        K0[i] = ff_dot2(C0[i], i00, C1[i], i01);
+        K1[i] = ff_dot2(C0[i], i01, C1[i], i11);
     }
 #pragma unroll
     for (int i = 0; i < 5; ++i)
 #pragma unroll
         for (int j = i; j < 5; ++j)
-            C[sx(i, j)] = ff_add(C[sx(i, j)], ff_neg(ff_add(ff_mul(K0[i], C0[j]), ff_mul(K1[i], C1[j]))));
+            C[sx(i, j)] = ff_add(C[sx(i, j)], ff_neg(ff_dot2(K0[i], C0[j], K1[i], C1[j])));
 #pragma unroll
     for (int i = 0; i < 3; ++i) add_comp(s.p[i], s.lo[i], K0[i].hi * r0 + K1[i].hi * r1);
 #pragma unroll
