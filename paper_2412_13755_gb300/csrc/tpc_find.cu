@@ -390,10 +390,9 @@ struct NbLists {
 // pair in order and reduce to the best pair (smallest D^2, then canonical id
 // of u, then of d).  A cluster whose needed list exceeds NS_CAP entries is
 // queued for the full-warp kernel below, which redoes it.
-constexpr int NG1 = 8;         // lanes per cluster, first gap pair
 constexpr int NG2 = 8;         // lanes per cluster, later gap pairs
 constexpr int NB_GAP_MAX = 3;  // largest gap of the neighbour search (tpc_params.max_gap <= 3)
-constexpr int NS_CAP = 16;     // list capacity per row offset (<= 254)
+constexpr int NS_CAP = 24;     // list capacity per row offset (<= 254)
 // warps per block of the sub-warp kernel: NG, so that the lists of its
 // 32 clusters per block take the same shared memory for every NG
 template <int NG> __host__ __device__ constexpr int ns_warps() { return NG; }
@@ -1344,7 +1343,7 @@ __global__ void __launch_bounds__(256) k_merge_cand(
     const int32_t* __restrict__ seg_grp, const float* __restrict__ tl_state,
     const int32_t* __restrict__ grp_tl_off, const int4* __restrict__ gs_meta,
     const Geo* __restrict__ geo, MgPrm P, int32_t* st, int32_t* cand_n, int32_t* cand_a,
-    float* cand_c2, TlBins tb) {
+    float* cand_c2, TlBins tb, int32_t* match_act) {
     const int lane = threadIdx.x & 31;
     const int nkept = st[ST_NTL];
     const int warps = (gridDim.x * blockDim.x) >> 5;
@@ -1456,7 +1455,11 @@ __global__ void __launch_bounds__(256) k_merge_cand(
         if (lane == 0) {
             cand_n[b] = min(nc, MAX_CAND);
             if (nc > MAX_CAND) set_status(st, TPC_ERR_CAPACITY, 3);
-            if (nc) atomicAdd(&st[ST_NCAND], min(nc, MAX_CAND));
+            if (nc) {
+                atomicAdd(&st[ST_NCAND], min(nc, MAX_CAND));
+                // the B ends with candidates, the first list of the matching
+                match_act[atomicAdd(&st[ST_MATCH_LIVE], 1)] = b;
+            }
         }
     }
 }
@@ -1476,31 +1479,9 @@ __global__ void __launch_bounds__(1024) k_match(
     // run over a compacted list of the B ends that still have a live
     // candidate; best_a / best_b hold KEY_MAX between rounds.
     __shared__ int n_act, n_next, live;
-    __shared__ int32_t wsum[32];
-    const int nseg = min((int64_t)st[ST_NSEG], Scap);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    // B ends with candidates (prv is -1 for all before the first round)
-    if (threadIdx.x == 0) n_act = 0;
+    // the B ends with candidates, listed by the candidate search
+    if (threadIdx.x == 0) n_act = min((int64_t)st[ST_MATCH_LIVE], Scap);
     __syncthreads();
-    for (int b0 = 0; b0 < nseg; b0 += blockDim.x) {
-        const int b = b0 + threadIdx.x;
-        const bool has = b < nseg && cand_n[b] > 0;
-        const unsigned m = __ballot_sync(0xffffffffu, has);
-        if (lane == 0) wsum[wid] = __popc(m);
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int o = n_act;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-                const int c = wsum[w];
-                wsum[w] = o;
-                o += c;
-            }
-            n_act = o;
-        }
-        __syncthreads();
-        if (has) act[wsum[wid] + __popc(m & ((1u << lane) - 1u))] = b;
-        __syncthreads();
-    }
     int32_t* cur = act;
     int32_t* nx = act + Scap;
     for (int round = 0; round < 4096; ++round) {
@@ -1684,7 +1665,7 @@ cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hi
     c->mark(0, s);
     // per-call counters (the status word and the FP64 count are cumulative)
     TPC_TRY(fill_i32(st + ST_NSEG, ST_NTRACKS - ST_NSEG + 1, 0, s));
-    TPC_TRY(fill_i32(st + ST_Q_BUILD, ST_NB_Q2 + 1 - ST_Q_BUILD, 0, s));
+    TPC_TRY(fill_i32(st + ST_MATCH_LIVE, ST_NB_Q2 + 1 - ST_MATCH_LIVE, 0, s));
     // S1: z range per group, cells, histogram, scan, scatter
     tpc::LaunchCount{}, k_fill_u32<<<grid_for(G), TPB, 0, s>>>(W.at<uint32_t>(L.g_zmin_u), G, 0xffffffffu);
     tpc::LaunchCount{}, k_fill_u32<<<grid_for(G), TPB, 0, s>>>(W.at<uint32_t>(L.g_zmax_u), G, 0u);
@@ -1823,7 +1804,7 @@ cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hi
     tpc::LaunchCount{}, k_merge_cand<<<grid_for(L.S * 32, 256), 256, 0, s>>>(
         W.at<int32_t>(L.seg_grp), W.at<float>(L.tl_state), W.at<int32_t>(L.grp_tl_off),
         W.at<int4>(L.gs_meta), geo, mp, st, W.at<int32_t>(L.cand_n), W.at<int32_t>(L.cand_a),
-        W.at<float>(L.cand_c2), tb);
+        W.at<float>(L.cand_c2), tb, W.at<int32_t>(L.match_act));
     c->mark(7, s);
     int32_t* nxt = W.at<int32_t>(L.nxt);
     int32_t* prv = W.at<int32_t>(L.prv);
