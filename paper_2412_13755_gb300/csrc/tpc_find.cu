@@ -10,6 +10,8 @@
 // not depend on the order in which the GPU visits clusters.
 #include <algorithm>
 
+#include <cooperative_groups.h>
+
 #include "tpc_dev.cuh"
 
 namespace tpc {
@@ -1467,32 +1469,49 @@ __global__ void __launch_bounds__(256) k_merge_cand(
 // Greedy matching in ascending chi2 (ties: canonical ids), computed as
 // rounds of locally dominant candidates: a candidate whose key is the best
 // among the live candidates of its A (outer end) and of its B (inner end) is
-// accepted; candidates touching an accepted end die.  One block.
-__global__ void __launch_bounds__(1024) k_match(
+// accepted; candidates touching an accepted end die.  One thread-block
+// cluster of MATCH_CTAS blocks: a thread per live B end, the three phases of
+// a round separated by cluster barriers, the round counters in the shared
+// memory of block 0 (distributed shared memory).
+constexpr int MATCH_CTAS = 8;
+__global__ void __cluster_dims__(MATCH_CTAS, 1, 1) __launch_bounds__(1024) k_match(
     const int32_t* __restrict__ cand_n, const int32_t* __restrict__ cand_a,
     const float* __restrict__ cand_c2, const int32_t* __restrict__ tl_canon, int64_t Scap,
     int32_t* st, unsigned long long* best_a, unsigned long long* best_b, int32_t* nxt,
     int32_t* prv, int32_t* act) {
-    // Rounds of locally dominant candidates: an (a, b) pair whose key
-    // (chi2, canonical ids) is the smallest of every live pair at a and of
-    // every live pair at b is matched; both ends are then used.  The rounds
-    // run over a compacted list of the B ends that still have a live
-    // candidate; best_a / best_b hold KEY_MAX between rounds.
-    __shared__ int n_act, n_next, live;
-    // the B ends with candidates, listed by the candidate search
-    if (threadIdx.x == 0) n_act = min((int64_t)st[ST_MATCH_LIVE], Scap);
-    __syncthreads();
+    // An (a, b) pair whose key (chi2, canonical ids) is the smallest of every
+    // live pair at a and of every live pair at b is matched; both ends are
+    // then used.  The rounds run over a compacted list of the B ends that
+    // still have a live candidate (first written by the candidate search);
+    // best_a / best_b hold KEY_MAX between rounds.  Counters of round r:
+    // list length cnt[r & 1], next list length cnt[(r & 1) ^ 1], live flag
+    // live[r & 1]; each is cleared a round before it is written.
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    __shared__ int sh_cnt[2], sh_live[2];
+    int* cnt = cl.map_shared_rank(sh_cnt, 0);
+    int* live = cl.map_shared_rank(sh_live, 0);
+    const int tid = (int)cl.block_rank() * blockDim.x + threadIdx.x;
+    const int nthreads = MATCH_CTAS * blockDim.x;
+    const bool lead = cl.block_rank() == 0 && threadIdx.x == 0;
+    if (lead) {
+        cnt[0] = (int)min((int64_t)st[ST_MATCH_LIVE], Scap);
+        cnt[1] = 0;
+        live[0] = live[1] = 0;
+    }
+    cl.sync();
     int32_t* cur = act;
     int32_t* nx = act + Scap;
     for (int round = 0; round < 4096; ++round) {
-        const int na = n_act;
+        const int ra = round & 1, rb = ra ^ 1;
+        const int na = cnt[ra];
         if (na == 0) break;
-        if (threadIdx.x == 0) {
-            live = 0;
-            n_next = 0;
+        if (lead) {
+            cnt[rb] = 0;
+            live[rb] = 0;
         }
-        __syncthreads();
-        for (int i = threadIdx.x; i < na; i += blockDim.x) {
+        bool any = false;
+        for (int i = tid; i < na; i += nthreads) {
             const int b = cur[i];
             if (prv[b] >= 0) continue;
             for (int k = 0; k < cand_n[b]; ++k) {
@@ -1501,12 +1520,13 @@ __global__ void __launch_bounds__(1024) k_match(
                 const uint64_t c2 = __float_as_uint(cand_c2[(int64_t)b * MAX_CAND + k]);
                 atomicMin(&best_a[a], (c2 << 32) | (uint32_t)tl_canon[b]);
                 atomicMin(&best_b[b], (c2 << 32) | (uint32_t)tl_canon[a]);
-                live = 1;
+                any = true;
             }
         }
-        __syncthreads();
-        if (!live) break;
-        for (int i = threadIdx.x; i < na; i += blockDim.x) {
+        if (any) live[ra] = 1;
+        cl.sync();
+        if (!live[ra]) break;
+        for (int i = tid; i < na; i += nthreads) {
             const int b = cur[i];
             if (prv[b] >= 0) continue;
             for (int k = 0; k < cand_n[b]; ++k) {
@@ -1521,9 +1541,9 @@ __global__ void __launch_bounds__(1024) k_match(
                 }
             }
         }
-        __syncthreads();
+        cl.sync();
         // reset the keys that were touched; keep the B ends still unmatched
-        for (int i = threadIdx.x; i < na; i += blockDim.x) {
+        for (int i = tid; i < na; i += nthreads) {
             const int b = cur[i];
             best_b[b] = KEY_MAX;
             bool keep = false;
@@ -1532,15 +1552,15 @@ __global__ void __launch_bounds__(1024) k_match(
                 best_a[a] = KEY_MAX;
                 keep |= nxt[a] < 0;
             }
-            if (keep && prv[b] < 0) nx[atomicAdd(&n_next, 1)] = b;
+            if (keep && prv[b] < 0) nx[atomicAdd(&cnt[rb], 1)] = b;
         }
-        __syncthreads();
-        if (threadIdx.x == 0) n_act = n_next;
+        cl.sync();
         int32_t* t = cur;
         cur = nx;
         nx = t;
-        __syncthreads();
     }
+    // block 0 keeps its shared memory until every block has read it
+    cl.sync();
 }
 
 // ---------------------------------------------------------------- output --
@@ -1814,7 +1834,7 @@ cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hi
     auto* best_b = W.at<unsigned long long>(L.best_b);
     tpc::LaunchCount{}, k_fill_u64<<<grid_for(L.S), TPB, 0, s>>>(best_a, L.S, KEY_MAX);
     tpc::LaunchCount{}, k_fill_u64<<<grid_for(L.S), TPB, 0, s>>>(best_b, L.S, KEY_MAX);
-    tpc::LaunchCount{}, k_match<<<1, 1024, 0, s>>>(W.at<int32_t>(L.cand_n), W.at<int32_t>(L.cand_a), W.at<float>(L.cand_c2),
+    tpc::LaunchCount{}, k_match<<<MATCH_CTAS, 1024, 0, s>>>(W.at<int32_t>(L.cand_n), W.at<int32_t>(L.cand_a), W.at<float>(L.cand_c2),
                                W.at<int32_t>(L.tl_canon), L.S, st, best_a, best_b, nxt, prv,
                                W.at<int32_t>(L.match_act));
     c->mark(8, s);
