@@ -21,7 +21,7 @@ Layout make_layout(int64_t N, int32_t E) {
     L.K = (int64_t)NROW * CELL_NY * L.G + N / CELL_OCC + 16;
     L.S = N / 16 + 4096;
     L.T = N + 1;
-    L.KT = L.G + N / 64 + 16;
+    L.KT = NMRB * (L.G + N / 64) + 16;  // (group, outer row bucket, z bin) keys
     const int64_t scan_items =
         std::max<int64_t>(std::max<int64_t>(N + 1, L.K + 1), std::max<int64_t>(L.G + 1, L.KT + 1));
     L.scan_tmp = scan_items / 4096 + 64;

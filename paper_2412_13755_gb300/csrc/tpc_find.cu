@@ -50,7 +50,9 @@ __device__ __forceinline__ bool in_range(int64_t i, int64_t bound, int32_t* st, 
     return false;
 }
 
-struct TlBins {  // per-group z bins of the kept tracklets' outer ends
+// Kept tracklets are binned per group by the row bucket of their outer end
+// (MRB rows per bucket) and, within it, by the z of their outer end.
+struct TlBins {  // per-group (outer row bucket, z) bins of the kept tracklets' outer ends
     const float* zmin;
     const float* inv;
     const int32_t* nb;
@@ -207,7 +209,7 @@ __global__ void __launch_bounds__(1024) k_tl_bins(const int64_t* __restrict__ of
             zmin[g] = lo;
             inv[g] = w > 0.f ? (float)k / w : 0.f;
             nb[g] = (int32_t)k;
-            cnt = (int32_t)k;
+            cnt = (int32_t)(NMRB * k);
         }
         const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
         int32_t x = cnt;
@@ -1291,7 +1293,7 @@ __global__ void k_keep(int32_t* tl_rowhit, const unsigned long long* __restrict_
         tl_rmax[s] = rmax;
         tl_zin[s] = yzb[hit[rmin]].y;
         tl_zout[s] = yzb[hit[rmax]].y;
-        const int bkey = tb.base[g] + tl_bin(tb, g, yzb[hit[rmax]].y);
+        const int bkey = tb.base[g] + (rmax / MRB) * tb.nb[g] + tl_bin(tb, g, yzb[hit[rmax]].y);
         if (!in_range(bkey, KT, st, 301)) {
             tl_keep[s] = 0;
             continue;
@@ -1361,19 +1363,25 @@ __global__ void __launch_bounds__(256) k_merge_cand(
         const float* stb = tl_state + (int64_t)b * 40;
         int nc = 0;  // warp-uniform count
         for (int dp = -1; dp <= 1; ++dp) {
-            const int sa = side * NPHI + (phb + dp + NPHI) % NPHI;
-            const int ga = ev * NSEC + sa;
-            // the z gate |z_B - z_A| <= slope |dx| + margin with |dx| at
-            // most max(row gap, overlap) pitches bounds the bins to visit
-            const float wmax = P.mz_slope * P.pitch * (float)max(P.merge_gap, P.merge_ov) * 1.001f +
-                               P.mz_margin + 1e-3f;
-            const int k0 = tb.base[ga] + tl_bin(tb, ga, zb_in - wmax);
-            const int k1 = tb.base[ga] + tl_bin(tb, ga, zb_in + wmax);
+          const int sa = side * NPHI + (phb + dp + NPHI) % NPHI;
+          const int ga = ev * NSEC + sa;
+          const int min_gap = dp == 0 ? 0 : -P.merge_ov;
+          // outer rows ra with rb - merge_gap <= ra <= rb - min_gap, by bucket
+          const int ra_lo = max(rb - P.merge_gap, 0), ra_hi = min(rb - min_gap, NROW - 1);
+          for (int j = ra_lo / MRB; ra_lo <= ra_hi && j <= ra_hi / MRB; ++j) {
+            // the z gate |z_B - z_A| <= slope |dx| + margin, with |dx| at
+            // most that of the bucket's farthest allowed row, bounds the bins
+            const int r0 = max(j * MRB, ra_lo), r1 = min(j * MRB + MRB - 1, ra_hi);
+            const float xb = geo->row_xf[rb];
+            const float dxm = fmaxf(fabsf(xb - geo->row_xf[r0]), fabsf(xb - geo->row_xf[r1]));
+            const float wmax = P.mz_slope * dxm * 1.001f + P.mz_margin + 1e-3f;
+            const int kb = tb.base[ga] + j * tb.nb[ga];
+            const int k0 = kb + tl_bin(tb, ga, zb_in - wmax);
+            const int k1 = kb + tl_bin(tb, ga, zb_in + wmax);
             if (!in_range(k0, P.KT + 1, st, 201) || !in_range(k1 + 1, P.KT + 1, st, 202)) continue;
             int q0 = grp_tl_off[k0], q1 = grp_tl_off[k1 + 1];
             if (!in_range(q0, nkept + 1, st, 203) || !in_range(q1, nkept + 1, st, 204) || q1 < q0)
                 q0 = q1 = 0;
-            const int min_gap = dp == 0 ? 0 : -P.merge_ov;
             for (int qa0 = q0; qa0 < q1; qa0 += 32) {
                 const int qa = qa0 + lane;
                 bool pass = false;
@@ -1453,6 +1461,7 @@ __global__ void __launch_bounds__(256) k_merge_cand(
                 }
                 nc += __popc(bal);
             }
+          }
         }
         if (lane == 0) {
             cand_n[b] = min(nc, MAX_CAND);

@@ -23,6 +23,8 @@ constexpr int NROW = 152;
 constexpr int MAX_CAND = 16;     // merge candidates kept per tracklet
 constexpr int CELL_OCC = 1;      // target clusters per (row, z-cell, y-cell)
 constexpr int CELL_NY = 16;      // y cells per (row, z-cell), uniform in y / (x tan 10 deg)
+constexpr int MRB = 8;           // outer-row bucket of the merge's tracklet bins (rows)
+constexpr int NMRB = (NROW + MRB - 1) / MRB;
 constexpr int NZ_MAX = 8192;     // z cells per row at most
 
 // Geometry table written into the workspace at set-up.
