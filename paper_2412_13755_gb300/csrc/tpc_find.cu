@@ -1348,9 +1348,18 @@ __global__ void __launch_bounds__(256) k_merge_cand(
     const int32_t* __restrict__ grp_tl_off, const int4* __restrict__ gs_meta,
     const Geo* __restrict__ geo, MgPrm P, int32_t* st, int32_t* cand_n, int32_t* cand_a,
     float* cand_c2, TlBins tb, int32_t* match_act) {
+    // The cheap gates (row gap, z, and the 1-d chi2 of tan lambda and q/pT,
+    // which the transport and the frame rotation leave unchanged) run over
+    // every A in the bins; the A that pass are collected in the warp's list
+    // and taken 32 at a time through the transport, the 1-d chi2 of y, z,
+    // sin phi and the 5-d chi2, so that those run on full warps.
+    __shared__ int sh_q[8][64];
+    int* wq = sh_q[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
     const int nkept = st[ST_NTL];
     const int warps = (gridDim.x * blockDim.x) >> 5;
+    const float lim = (float)P.chi2_merge * 1.01f;
     for (int qb = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; qb < nkept; qb += warps) {
         const int4 mb = gs_meta[qb];
         const int b = mb.w;
@@ -1361,7 +1370,70 @@ __global__ void __launch_bounds__(256) k_merge_cand(
         const int gb = seg_grp[b];
         const int ev = gb / NSEC, sb = gb % NSEC, side = sb / NPHI, phb = sb % NPHI;
         const float* stb = tl_state + (int64_t)b * 40;
-        int nc = 0;  // warp-uniform count
+        const float tb3 = stb[3], tb4 = stb[4], vb3 = stb[5 + 12], vb4 = stb[5 + 14];
+        int nc = 0;    // warp-uniform count of candidates
+        int nbuf = 0;  // warp-uniform length of the list
+        // the expensive test of the first k entries of the list (lane i: entry i)
+        auto flush = [&](int k) {
+            bool pass = false;
+            float c2f = 0.f;
+            int a = -1;
+            if (lane < k) {
+                const int qa = wq[lane];
+                const int4 ma = gs_meta[qa];
+                a = ma.w;
+                if (!in_range(a, P.S, st, 205)) a = b;
+                const int ra = ma.x & 0xff;
+                const int sa = seg_grp[a] % NSEC;
+                const float* sta = tl_state + (int64_t)a * 40;
+                KF s;
+                s.x = geo->row_xd[ra];
+                s.frame = sa;
+                for (int i = 0; i < 5; ++i) s.p[i] = sta[20 + i];
+                s.lo[0] = s.lo[1] = s.lo[2] = 0.f;
+                for (int i = 0; i < 15; ++i) s.C[i] = sta[25 + i];
+                pass = kf_move<float>(s, geo->row_xd[rb], sb, geo, P.kbf, P.snp_maxf);
+                // each component's 1-d chi2 is a lower bound of the 5-d
+                // chi2: reject in FP32 (1% margin) before the solve
+                if (pass) {
+                    const int di[4] = {0, 1, 2, 3};
+                    const int ci[4] = {0, 5, 9, 12};
+#pragma unroll
+                    for (int k2 = 0; k2 < 4; ++k2) {
+                        const float d = stb[di[k2]] - (s.p[di[k2]] + (di[k2] < 3 ? s.lo[di[k2]] : 0.f));
+                        const float v = s.C[ci[k2]] + stb[5 + ci[k2]];
+                        pass = pass && d * d <= lim * v;
+                    }
+                }
+                if (pass) {
+                    // float-float: the differences and sums of the FP32
+                    // states are exact, the solve carries ~48 bits
+                    ff d[5], M[15];
+#pragma unroll
+                    for (int i = 0; i < 3; ++i)
+                        d[i] = ff_add(ff_from(stb[i]), ff_neg(two_sum(s.p[i], s.lo[i])));
+#pragma unroll
+                    for (int i = 3; i < 5; ++i) d[i] = two_sum(stb[i], -s.p[i]);
+#pragma unroll
+                    for (int i = 0; i < 15; ++i) M[i] = two_sum(s.C[i], stb[5 + i]);
+                    ff c2;
+                    pass = chol_chi2_ff(d, M, c2);
+                    // c2 <= chi2_merge on the float-float value
+                    const double lim2 = P.chi2_merge;
+                    pass = pass && ((double)c2.hi + (double)c2.lo) <= lim2;
+                    c2f = c2.hi + c2.lo;
+                }
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, pass);
+            if (pass) {
+                const int kk = nc + __popc(bal & lt);
+                if (kk < MAX_CAND) {
+                    cand_a[(int64_t)b * MAX_CAND + kk] = a;
+                    cand_c2[(int64_t)b * MAX_CAND + kk] = c2f;
+                }
+            }
+            nc += __popc(bal);
+        };
         for (int dp = -1; dp <= 1; ++dp) {
           const int sa = side * NPHI + (phb + dp + NPHI) % NPHI;
           const int ga = ev * NSEC + sa;
@@ -1385,11 +1457,9 @@ __global__ void __launch_bounds__(256) k_merge_cand(
             for (int qa0 = q0; qa0 < q1; qa0 += 32) {
                 const int qa = qa0 + lane;
                 bool pass = false;
-                float c2f = 0.f;
-                int a = -1;
                 if (qa < q1 && qa != qb && ma_ok(gs_meta, qa, b)) {
                     const int4 ma = gs_meta[qa];
-                    a = ma.w;
+                    int a = ma.w;
                     if (!in_range(a, P.S, st, 205)) a = b;
                     const int ra = ma.x & 0xff;
                     const int gap = rb - ra;
@@ -1399,70 +1469,34 @@ __global__ void __launch_bounds__(256) k_merge_cand(
                         pass = fabsf(__fsub_rn(zb_in, __int_as_float(ma.y))) <=
                                __fadd_rn(__fmul_rn(P.mz_slope, dxr), P.mz_margin);
                     }
-                    const float* sta = tl_state + (int64_t)a * 40;
                     if (pass) {
                         // tan lambda and q/pT are unchanged by the transport
                         // and the frame rotation: their 1-d chi2 (lower
                         // bounds of the 5-d chi2) reject before the move
-                        const float lim = (float)P.chi2_merge * 1.01f;
-                        const float dt = stb[3] - sta[23], dw = stb[4] - sta[24];
-                        pass = dt * dt <= lim * (sta[25 + 12] + stb[5 + 12]) &&
-                               dw * dw <= lim * (sta[25 + 14] + stb[5 + 14]);
-                    }
-                    if (pass) {
-                        KF s;
-                        s.x = geo->row_xd[ra];
-                        s.frame = sa;
-                        for (int i = 0; i < 5; ++i) s.p[i] = sta[20 + i];
-                        s.lo[0] = s.lo[1] = s.lo[2] = 0.f;
-                        for (int i = 0; i < 15; ++i) s.C[i] = sta[25 + i];
-                        pass = kf_move<float>(s, geo->row_xd[rb], sb, geo, P.kbf, P.snp_maxf);
-                        // each component's 1-d chi2 is a lower bound of the
-                        // 5-d chi2: reject in FP32 (1% margin) before the
-                        // FP64 solve
-                        if (pass) {
-                            const float lim = (float)P.chi2_merge * 1.01f;
-                            const int di[4] = {0, 1, 2, 3};
-                            const int ci[4] = {0, 5, 9, 12};
-#pragma unroll
-                            for (int k = 0; k < 4; ++k) {
-                                const float d = stb[di[k]] - (s.p[di[k]] + (di[k] < 3 ? s.lo[di[k]] : 0.f));
-                                const float v = s.C[ci[k]] + stb[5 + ci[k]];
-                                pass = pass && d * d <= lim * v;
-                            }
-                        }
-                        if (pass) {
-                            // float-float: the differences and sums of the FP32
-                            // states are exact, the solve carries ~48 bits
-                            ff d[5], M[15];
-#pragma unroll
-                            for (int i = 0; i < 3; ++i)
-                                d[i] = ff_add(ff_from(stb[i]), ff_neg(two_sum(s.p[i], s.lo[i])));
-#pragma unroll
-                            for (int i = 3; i < 5; ++i) d[i] = two_sum(stb[i], -s.p[i]);
-#pragma unroll
-                            for (int i = 0; i < 15; ++i) M[i] = two_sum(s.C[i], stb[5 + i]);
-                            ff c2;
-                            pass = chol_chi2_ff(d, M, c2);
-                            // c2 <= chi2_merge on the float-float value
-                            const double lim2 = P.chi2_merge;
-                            pass = pass && ((double)c2.hi + (double)c2.lo) <= lim2;
-                            c2f = c2.hi + c2.lo;
-                        }
+                        const float* sta = tl_state + (int64_t)a * 40;
+                        const float dt = tb3 - sta[23], dw = tb4 - sta[24];
+                        pass = dt * dt <= lim * (sta[25 + 12] + vb3) && dw * dw <= lim * (sta[25 + 14] + vb4);
                     }
                 }
                 const unsigned bal = __ballot_sync(0xffffffffu, pass);
-                if (pass) {
-                    const int k = nc + __popc(bal & ((1u << lane) - 1u));
-                    if (k < MAX_CAND) {
-                        cand_a[(int64_t)b * MAX_CAND + k] = a;
-                        cand_c2[(int64_t)b * MAX_CAND + k] = c2f;
-                    }
+                if (pass) wq[nbuf + __popc(bal & lt)] = qa;
+                nbuf += __popc(bal);
+                __syncwarp();
+                if (nbuf >= 32) {
+                    flush(32);
+                    // keep the entries beyond the first 32
+                    const int rest = nbuf - 32;
+                    const int v = lane < rest ? wq[32 + lane] : 0;
+                    __syncwarp();
+                    if (lane < rest) wq[lane] = v;
+                    nbuf = rest;
+                    __syncwarp();
                 }
-                nc += __popc(bal);
             }
           }
         }
+        if (nbuf > 0) flush(nbuf);
+        __syncwarp();
         if (lane == 0) {
             cand_n[b] = min(nc, MAX_CAND);
             if (nc > MAX_CAND) set_status(st, TPC_ERR_CAPACITY, 3);
