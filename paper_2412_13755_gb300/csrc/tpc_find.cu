@@ -985,7 +985,9 @@ __device__ __forceinline__ void seed_mask(const int32_t* hit, const uint32_t (&m
 // chain kernel for the build, by the keep kernel for the refit); a lane
 // keeps the mask in registers, so that the next hit row of a fit is known
 // without a load and the hit's coordinates are fetched before the transport.
-enum { PH_FIT_IN = 0, PH_EXT_IN = 1, PH_FIT_OUT = 2, PH_EXT_OUT = 3 };
+// PH_TO_OUTER is the move of the inward state to the outermost hit row, run
+// as a step so that it shares the transport with the other lanes' steps.
+enum { PH_FIT_IN = 0, PH_EXT_IN = 1, PH_FIT_OUT = 2, PH_EXT_OUT = 3, PH_TO_OUTER = 6 };
 constexpr int EXT_ZB = 2;  // z cells of an extension window read in one batch
 constexpr int EXT_CH = 4;  // candidate loads in flight per lane
 
@@ -1042,11 +1044,14 @@ __global__ void __launch_bounds__(128, 4) k_tracklet_lanes(
         }
         // ---- one step of the current phase
         const bool fit = phase == PH_FIT_IN || phase == PH_FIT_OUT;
+        const bool to_outer_step = phase == PH_TO_OUTER;
         const int dir = (phase == PH_FIT_IN || phase == PH_EXT_IN) ? -1 : 1;
         int target = r + dir;
         if (fit) target = dir < 0 ? mask_below(m, r) : mask_above(m, r);
+        if (to_outer_step) target = rmax;
         bool end_phase;
         if (fit) end_phase = target < rmin || target > rmax;
+        else if (to_outer_step) end_phase = false;
         else end_phase = target < 0 || target >= NROW || misses >= P.ext_max_miss;
         // a fit step's hit, fetched before the transport
         int c = -1;
@@ -1064,10 +1069,10 @@ __global__ void __launch_bounds__(128, 4) k_tracklet_lanes(
             ++steps;
             if (moved) xr = target;
             if (!moved) end_phase = true;
-            else if (!fit && fabsf(kf.p[0] + kf.lo[0]) > geo->row_xf[target] * geo->tan_half)
+            else if (!fit && !to_outer_step && fabsf(kf.p[0] + kf.lo[0]) > geo->row_xf[target] * geo->tan_half)
                 end_phase = true;
         }
-        if (!end_phase) {
+        if (!end_phase && !to_outer_step) {
             if (!fit) {
                 const float S00 = kf.C[0] + P.sy2, S01 = kf.C[1], S11 = kf.C[5] + P.sz2;
                 const float det = S00 * S11 - S01 * S01;
@@ -1154,7 +1159,16 @@ __global__ void __launch_bounds__(128, 4) k_tracklet_lanes(
         // is the outward state; an outward fit only replaces it when the
         // inward fit or that move failed.
         bool to_outer = false;
-        if (phase == PH_FIT_IN) {
+        if (to_outer_step) {
+            // the moved state is the outward state; if the move failed, an
+            // outward fit stands in
+            if (moved) {
+                ok |= 2;
+                phase = PH_EXT_OUT + 1;
+            } else {
+                phase = PH_FIT_OUT;
+            }
+        } else if (phase == PH_FIT_IN) {
             if (moved || target < rmin || target > rmax) ok |= 1;  // fit completed
             if (refit && (ok & 1)) {
                 float* out = tl_state + (int64_t)s * 40;
@@ -1180,13 +1194,8 @@ __global__ void __launch_bounds__(128, 4) k_tracklet_lanes(
             phase = PH_EXT_OUT + 2;  // finished
         }
         if (to_outer) {
-            const float dxl = (float)(rmax - xr) * P.pitch;
-            if (kf_move<float, false>(kf, 0.0, sector, geo, P.kb, P.snp_max, nullptr, &dxl)) {
-                ++steps;
-                xr = rmax;
-                ok |= 2;
-                phase = PH_EXT_OUT + 1;
-            }
+            phase = PH_TO_OUTER;
+            continue;
         }
         if (phase == PH_EXT_OUT + 1) {
             if (refit) {
