@@ -47,22 +47,34 @@ __global__ void __launch_bounds__(128) k_fit(
             for (int i = 0; i < 15; ++i) Cf[i] = ff_from(s.C[i]);
             int g = -1;
             int64_t gb = 0, ge = 0;
+            // the next hit's index and data are read a step ahead, so that
+            // their loads overlap the current step's arithmetic
+            int cn = h[0];
+            int rn = row[cn];
+            float yn = y[cn], zn = z[cn];
             for (int j = 0; j < n && ok; ++j) {
-                const int c = h[j];
+                const int c = cn, rc = rn;
+                const float yc = yn, zc = zn;
+                if (j + 1 < n) cn = h[j + 1];
                 if (c < gb || c >= ge) {  // group lookup, cached while hits stay in one group
                     g = group_of(evt_off, G, c);
                     gb = evt_off[g];
                     ge = evt_off[g + 1];
                 }
                 MoveJ mj;
-                ok = kf_move<float, true, false>(s, geo->row_xd[row[c]], g % NSEC, geo, P.kb, P.snp_max, &mj);
+                ok = kf_move<float, true, false>(s, geo->row_xd[rc], g % NSEC, geo, P.kb, P.snp_max, &mj);
+                if (j + 1 < n) {
+                    rn = row[cn];
+                    yn = y[cn];
+                    zn = z[cn];
+                }
                 if (ok) {
                     if (mj.j00 == 1.f && mj.j22 == 1.f && mj.j10 == 0.f && mj.j20 == 0.f)
                         cov_jct_ff_frame(Cf, mj.j02, mj.j04, mj.j12, mj.j13, mj.j14, mj.j24);
                     else
                         cov_jct_ff(Cf, mj.j00, mj.j02, mj.j04, mj.j10, mj.j12, mj.j13, mj.j14, mj.j20, mj.j22,
                                    mj.j24);
-                    chi2.add(kf_update_ff(s, Cf, y[c], z[c], P.sy2, P.sz2));
+                    chi2.add(kf_update_ff(s, Cf, yc, zc, P.sy2, P.sz2));
                 }
             }
         }
