@@ -59,7 +59,6 @@ Layout make_layout(int64_t N, int32_t E) {
     L.link_up = take(n4);
     L.owner = take(n8);
     L.seg_start = take(s4);
-    L.seg_perm = take(s4);
     L.seg_grp = take(s4);
     L.seg_canon = take(s4);
     L.tl_rowhit = take(s4 * NROW);

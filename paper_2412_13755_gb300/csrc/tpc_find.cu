@@ -819,18 +819,31 @@ __global__ void k_chains(int64_t n, const int32_t* __restrict__ link_dn,
                          const int32_t* __restrict__ grpb, const uint8_t* __restrict__ rowb, int n_seg,
                          int64_t Scap, int32_t* seg_start, int32_t* seg_grp, int32_t* seg_canon,
                          int32_t* tl_rowhit, uint4* tl_mask, int32_t* st) {
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
-         c += (int64_t)gridDim.x * blockDim.x) {
-        if (link_dn[c] >= 0 || link_up[c] < 0) continue;
+    // warp-uniform loop: a warp takes 32 consecutive clusters, and the
+    // slots of its chains are consecutive (one atomic per warp), so the slot
+    // order follows the binned order of the chain starts within a warp
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    for (int64_t c0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); c0 < n;
+         c0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = c0 + lane;
+        const bool start = c < n && link_dn[c] < 0 && link_up[c] >= 0;
         int len = 0, cur = (int)c;
         int32_t mn = 0x7fffffff;
-        while (cur >= 0 && len <= NROW) {
-            mn = min(mn, orig[cur]);
-            ++len;
-            cur = link_up[cur];
+        if (start) {
+            while (cur >= 0 && len <= NROW) {
+                mn = min(mn, orig[cur]);
+                ++len;
+                cur = link_up[cur];
+            }
         }
-        if (len < n_seg) continue;
-        const int slot = atomicAdd(&st[ST_NSEG], 1);
+        const bool qual = start && len >= n_seg;
+        const unsigned bal = __ballot_sync(0xffffffffu, qual);
+        int base = 0;
+        if (lane == 0 && bal) base = atomicAdd(&st[ST_NSEG], __popc(bal));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (!qual) continue;
+        const int slot = base + __popc(bal & lt);
         if (slot >= Scap) {
             set_status(st, TPC_ERR_CAPACITY, 2);
             continue;
@@ -858,26 +871,6 @@ __global__ void k_chains(int64_t n, const int32_t* __restrict__ link_dn,
         tl_mask[2 * (int64_t)slot] = make_uint4(m0, m1, m2, m3);
         tl_mask[2 * (int64_t)slot + 1] = make_uint4(m4, 0u, 0u, 0u);
     }
-}
-
-// Processing order of the segments: by the binned position of their start
-// cluster, i.e. (group, row, z cell), so that the lanes of a warp tend to
-// follow tracks of similar extent and stay in the same phase.  The order
-// only schedules the work; no result depends on it.
-__global__ void k_seg_mark(const int32_t* __restrict__ seg_start, int64_t Scap, const int32_t* st,
-                           int32_t* flag, int32_t* slot_at) {
-    const int nseg = min((int64_t)st[ST_NSEG], Scap);
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nseg; s += gridDim.x * blockDim.x) {
-        flag[seg_start[s]] = 1;
-        slot_at[seg_start[s]] = s;
-    }
-}
-
-__global__ void k_seg_perm(int64_t n, const int32_t* __restrict__ flag, const int32_t* __restrict__ rank,
-                           const int32_t* __restrict__ slot_at, int32_t* perm) {
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
-         c += (int64_t)gridDim.x * blockDim.x)
-        if (flag[c]) perm[rank[c]] = slot_at[c];
 }
 
 // ---------------------------------------------------------------- S3b -----
@@ -1018,7 +1011,7 @@ __global__ void __launch_bounds__(128, 4) k_tracklet_lanes(
             }
             item = t_next++;
             if (item >= nitems) break;
-            s = items[item];
+            s = items ? items[item] : item;
             hit = tl_rowhit + (int64_t)s * NROW;
             g = seg_grp[s];
             sector = g % NSEC;
@@ -1798,18 +1791,6 @@ cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hi
     tpc::LaunchCount{}, k_chains<<<grid_for(n), TPB, 0, s>>>(n, ldn, lup, orig, grpb, rowb, p.n_seg, L.S,
                                          W.at<int32_t>(L.seg_start), W.at<int32_t>(L.seg_grp),
                                          W.at<int32_t>(L.seg_canon), tl_rowhit, tl_mask, st);
-    // processing order of the segments (start clusters are unique)
-    {
-        int32_t* flag = W.at<int32_t>(L.trk_flag);
-        int32_t* rank = W.at<int32_t>(L.trk_rank);
-        int32_t* slot_at = W.at<int32_t>(L.trk_head_at);
-        TPC_TRY(fill_i32(flag, n, 0, s));
-        tpc::LaunchCount{}, k_seg_mark<<<grid_for(L.S, 128), 128, 0, s>>>(W.at<int32_t>(L.seg_start), L.S, st,
-                                                                           flag, slot_at);
-        TPC_TRY(scan_i32(flag, rank, n, scan_tmp, s));
-        tpc::LaunchCount{}, k_seg_perm<<<grid_for(n), TPB, 0, s>>>(n, flag, rank, slot_at,
-                                                                W.at<int32_t>(L.seg_perm));
-    }
     c->mark(4, s);
     // S3b: tracklets
     TlPrm tp;
@@ -1833,7 +1814,7 @@ cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hi
     const int tile = c->tune.lane_tile;
     auto* tl_key = W.at<unsigned long long>(L.tl_key);
     tpc::LaunchCount{}, k_tracklet_lanes<<<lgrid, 128, 0, s>>>(
-        0, W.at<int32_t>(L.seg_perm), ST_NSEG, W.at<int32_t>(L.seg_grp), W.at<int32_t>(L.seg_canon), yzb,
+        0, nullptr, ST_NSEG, W.at<int32_t>(L.seg_grp), W.at<int32_t>(L.seg_canon), yzb,
         orig, cells, geo, tp, L.S, st, tl_rowhit, tl_mask, W.at<int32_t>(L.tl_n), tl_key, nullptr, nullptr,
         nullptr, tile);
     c->mark(5, s);

@@ -61,7 +61,7 @@ struct Layout {
     // offsets
     size_t geo, status, g_zmin_u, g_zmax_u, g_nz, g_inv, g_zmin, g_kbase, key_in, slot_in,
         cell_cnt, cell_off, yzb, orig, grpb, rowb, choice_dn, choice_up, d2, claim_up,
-        claim_dn, link_dn, link_up, owner, seg_start, seg_perm, seg_grp, seg_canon, tl_rowhit, tl_mask,
+        claim_dn, link_dn, link_up, owner, seg_start, seg_grp, seg_canon, tl_rowhit, tl_mask,
         tl_n, tl_key, tl_keep, tl_canon, tl_rmin, tl_rmax, tl_zin, tl_zout, tl_state, tl_ok,
         grp_tl_cnt, grp_tl_off, grp_tl_cur, tl_sorted, gs_meta, tl_binkey, tb_zmin, tb_inv, tb_nb, tb_base, cand_n, cand_a, cand_c2, best_a, best_b,
         nxt, prv, match_act, trk_flag, trk_rank, trk_len_at, trk_head_at, len_by_rank, head_by_rank, scan_a, scan_b,
