@@ -45,7 +45,7 @@ KF_FLOPS_PER_STEP = 350.0               # transport ~60 + covariance J C J^T ~16
 # DRAM bytes (read + write) of one build launch of k_tracklet_lanes on the
 # central event, from an ncu capture of this kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum); None for a kernel without a capture
-TRAFFIC_BYTES_PER_LAUNCH = {"k_tracklet_lanes": 35.685e6 + 2.391e6}
+TRAFFIC_BYTES_PER_LAUNCH = {"k_tracklet_lanes": 38.144e6 + 2.447e6, "k_fit": 23.837e6}
 
 
 def batched_vs_plain(torch, tpc, dev, steps):
