@@ -145,6 +145,10 @@ __global__ void __launch_bounds__(1024) k_cells(const int64_t* __restrict__ off,
                 hi = o2f(zmax_u[g]);
             }
             const float w = hi - lo;
+            // z cells of at least ZCELL_MIN cm: a dense group (a pile-up
+            // frame) gets fuller cells rather than windows over many runs
+            const int64_t kz = (int64_t)(w / ZCELL_MIN) + 1;
+            k = k < kz ? k : kz;
             zmin[g] = lo;
             inv[g] = w > 0.f ? (float)k / w : 0.f;
             nz[g] = (int32_t)k;

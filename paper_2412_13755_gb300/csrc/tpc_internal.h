@@ -26,6 +26,7 @@ constexpr int CELL_NY = 16;      // y cells per (row, z-cell), uniform in y / (x
 constexpr int MRB = 8;           // outer-row bucket of the merge's tracklet bins (rows)
 constexpr int NMRB = (NROW + MRB - 1) / MRB;
 constexpr int NZ_MAX = 8192;     // z cells per row at most
+constexpr float ZCELL_MIN = 8.f;  // shortest z cell (cm)
 
 // Geometry table written into the workspace at set-up.
 struct Geo {
