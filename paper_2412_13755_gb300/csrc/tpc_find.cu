@@ -556,7 +556,7 @@ __global__ void __launch_bounds__(ns_warps<NG>() * 32) k_neighbours_sub(
 // candidates (row r-1) stream from their cells, each paired with the list.
 // A cluster without a pair here is queued for the later gap pairs
 // (k_neighbours_sub, pass 2); one whose up list would overflow is queued for
-// the warp-cooperative kernel (full search).
+// the sub-warp kernel from the first gap pair on (longer lists).
 constexpr int NF = 6;
 __global__ void __launch_bounds__(256) k_neighbours_first(
     int64_t n, const float2* __restrict__ yzb,
@@ -597,7 +597,7 @@ __global__ void __launch_bounds__(256) k_neighbours_first(
             }
         }
         if (nu > NF) {
-            ovf_queue[atomicAdd(&st[ST_NB_OVF], 1)] = (int32_t)c;
+            ovf_queue[atomicAdd(&st[ST_NB_Q3], 1)] = (int32_t)c;
             continue;
         }
         int bd = -1, bu = -1, pod = 0, pou = 0;
@@ -1768,9 +1768,14 @@ cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hi
     NbPrm nb{p.win_y, p.win_z, p.chi2_link, p.sigma_y2, p.sigma_z2, p.max_gap};
     int32_t* nb_queue = W.at<int32_t>(L.key_in);    // free after S1
     int32_t* nb_queue2 = W.at<int32_t>(L.slot_in);  // free after S1
-    // pass 1: gap pair (1, 1) for all; pass 2: the later gap pairs for the rest
+    int32_t* nb_queue3 = reinterpret_cast<int32_t*>(W.at<unsigned long long>(L.claim_up));  // free until the claims
+    // pass 1: gap pair (1, 1) for all; pass 2: the later gap pairs for the
+    // rest, and every gap pair for the clusters whose pass-1 list overflowed
     tpc::LaunchCount{}, k_neighbours_first<<<grid_for(n), TPB, 0, s>>>(
-        n, yzb, orig, grpb, rowb, cells, geo, nb, cdn, cup, d2, st, nb_queue, nb_queue2, ST_NB_Q2);
+        n, yzb, orig, grpb, rowb, cells, geo, nb, cdn, cup, d2, st, nb_queue3, nb_queue2, ST_NB_Q2);
+    tpc::LaunchCount{}, k_neighbours_sub<NG2><<<152 * 8, ns_warps<NG2>() * 32, 0, s>>>(
+        n, nb_queue3, ST_NB_Q3, 2, 2 * NB_GAP_MAX, yzb, orig, grpb, rowb, cells, geo, nb, cdn, cup, d2, st,
+        nb_queue, nullptr, 0);
     tpc::LaunchCount{}, k_neighbours_sub<NG2><<<grid_for(n / 4, 32 * 4), ns_warps<NG2>() * 32, 0, s>>>(
         n, nb_queue2, ST_NB_Q2, 3, 2 * NB_GAP_MAX, yzb, orig, grpb, rowb, cells, geo, nb, cdn, cup, d2, st,
         nb_queue, nullptr, 0);

@@ -44,7 +44,7 @@ struct Geo {
 // Device status word and counters (int32 slots in the workspace).
 enum StatusSlot {
     ST_STATUS = 0, ST_DETAIL, ST_NSEG, ST_NTL, ST_NCAND, ST_NMERGE, ST_NTRACKS, ST_FP64,
-    ST_MATCH_LIVE, ST_Q_BUILD, ST_Q_REFIT, ST_SPARE11, ST_KFSTEPS = 12 /* 64-bit: slots 12-13 */,
+    ST_MATCH_LIVE, ST_Q_BUILD, ST_Q_REFIT, ST_NB_Q3, ST_KFSTEPS = 12 /* 64-bit: slots 12-13 */,
     ST_NB_OVF = 14, ST_NB_Q2 = 15, ST_N_SLOTS = 16
 };
 
