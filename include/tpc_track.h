@@ -96,8 +96,17 @@ typedef struct {
     int32_t status_detail;
     int64_t n_launches;       /* kernels this library has launched in this
                                  process (host-side count, all contexts)    */
-    int64_t n_kf_steps;       /* Kalman steps of the tracklet kernel in the
-                                 last tpc_find_tracks (build + refit)       */
+    int64_t n_kf_steps;       /* Kalman steps of the tracklet build in the
+                                 last tpc_find_tracks                       */
+    /* neighbour search of the last tpc_find_tracks: clusters without a pair
+     * at the first gap pair (1,1), searched from gap sum 3 on by the 8-lane
+     * kernel; clusters whose first-pass up list overflowed, searched from
+     * (1,1) on by the 8-lane kernel; clusters whose 8-lane list overflowed,
+     * searched again by the full-warp kernel */
+    int32_t n_nb_second;
+    int32_t n_nb_dense;
+    int32_t n_nb_full;
+    int32_t reserved;
 } tpc_stats;
 
 /* Fills p with the library's default parameters. */

@@ -371,6 +371,10 @@ tpc_status tpc_get_stats(tpc_ctx* c, tpc_stats* out, tpc_stream_t stream) {
         long long ks;
         memcpy(&ks, &h[ST_KFSTEPS], sizeof ks);
         out->n_kf_steps = ks;
+        out->n_nb_second = h[ST_NB_Q2];
+        out->n_nb_dense = h[ST_NB_Q3];
+        out->n_nb_full = h[ST_NB_OVF];
+        out->reserved = 0;
     }
     if (h[ST_STATUS] != 0) {
         char buf[160];

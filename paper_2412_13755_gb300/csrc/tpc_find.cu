@@ -562,7 +562,7 @@ __global__ void __launch_bounds__(256) k_neighbours_first(
     int64_t n, const float2* __restrict__ yzb,
     const int32_t* __restrict__ orig, const int32_t* __restrict__ grpb,
     const uint8_t* __restrict__ rowb, Cells cells, const Geo* __restrict__ geo, NbPrm P,
-    int32_t* choice_dn, int32_t* choice_up, float* d2out, int32_t* st, int32_t* ovf_queue,
+    int32_t* choice_dn, int32_t* choice_up, float* d2out, int32_t* st, int32_t* dense_queue,
     int32_t* next_queue, int next_slot) {
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
          c += (int64_t)gridDim.x * blockDim.x) {
@@ -597,7 +597,7 @@ __global__ void __launch_bounds__(256) k_neighbours_first(
             }
         }
         if (nu > NF) {
-            ovf_queue[atomicAdd(&st[ST_NB_Q3], 1)] = (int32_t)c;
+            dense_queue[atomicAdd(&st[ST_NB_Q3], 1)] = (int32_t)c;
             continue;
         }
         int bd = -1, bu = -1, pod = 0, pou = 0;

@@ -52,6 +52,8 @@ class Stats(C.Structure):
         ("n_merge_cand", C.c_int32), ("n_merges", C.c_int32), ("n_tracks", C.c_int32),
         ("n_fp64_updates", C.c_int32), ("status", C.c_int32), ("status_detail", C.c_int32),
         ("n_launches", C.c_int64), ("n_kf_steps", C.c_int64),
+        ("n_nb_second", C.c_int32), ("n_nb_dense", C.c_int32), ("n_nb_full", C.c_int32),
+        ("reserved", C.c_int32),
     ]
 
 

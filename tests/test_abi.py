@@ -64,8 +64,21 @@ def test_host_only_calls(lib):
     assert lib.tpc_create(None, None) == tpc.TPC_ERR_ARG
 
 
-def test_struct_sizes_match_header(lib):
+def test_struct_sizes_match_header(lib, tmp_path):
+    # the binding's ctypes structures against the C header, compiled here
+    import shutil
+    import subprocess
     from paper_2412_13755_gb300 import tpc
-    # 5 floats, 5 int32, 2 floats, 2 floats, int32, float, 5 floats, 6 floats
-    assert C.sizeof(tpc.Params) == 108
-    assert C.sizeof(tpc.Stats) == 56
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    src = tmp_path / "sizes.c"
+    src.write_text('#include <stdio.h>\n#include "tpc_track.h"\n'
+                   'int main(void) { printf("%zu %zu %zu\\n", sizeof(tpc_params), sizeof(tpc_stats), '
+                   'sizeof(tpc_tune)); return 0; }\n')
+    exe = tmp_path / "sizes"
+    subprocess.run([cc, "-I", inc, str(src), "-o", str(exe)], check=True)
+    sizes = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True,
+                                            text=True).stdout.split()]
+    assert sizes == [C.sizeof(tpc.Params), C.sizeof(tpc.Stats), C.sizeof(tpc.Tune)]

@@ -51,6 +51,17 @@ def test_find_pileup_frame_small(orc):
     _assign_parity(orc, synth.pileup_frame(n_collisions=10, n_tracks=1000, seed=404))
 
 
+def test_find_dense_event(orc):
+    # 3x the central event's tracks in one event: many first-pass up lists
+    # and second-pass lists overflow, so every tier of the neighbour search
+    # (lane, 8-lane from the first gap pair, full warp) decides some clusters
+    ev = synth.central_event(n_tracks=30000, seed=505)
+    g_toc, g_off, g_hits, st, _ = gpu_find(ev)
+    print(f"second pass {st.n_nb_second}, dense {st.n_nb_dense}, full warp {st.n_nb_full}")
+    assert st.n_nb_second > 0 and st.n_nb_dense > 0 and st.n_nb_full > 0
+    _assign_parity(orc, ev)
+
+
 def test_find_multi_event_batch(orc):
     _assign_parity(orc, synth.uneven_batch(n_events=6, lo=10, hi=800, seed=303))
 
