@@ -11,8 +11,8 @@ for ALICE Run-3 data.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
---impl reference times the FP64 CPU oracle (the reference arm of this build:
-the paper publishes no code) on the same workload, on the host cores.
+--impl reference times the FP64 CPU oracle (the paper publishes no code to
+compare with) on the same workload, on the host cores.
 """
 from __future__ import annotations
 
