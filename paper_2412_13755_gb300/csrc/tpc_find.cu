@@ -421,7 +421,8 @@ __global__ void __launch_bounds__(ns_warps<NG>() * 32) k_neighbours_sub(
     const int32_t* __restrict__ orig, const int32_t* __restrict__ grpb,
     const uint8_t* __restrict__ rowb, Cells cells, const Geo* __restrict__ geo, NbPrm P,
     int32_t* choice_dn, int32_t* choice_up, float* d2out, int32_t* st, int32_t* ovf_queue,
-    int32_t* next_queue, int next_slot) {
+    int32_t* next_queue, int next_slot, const int32_t* __restrict__ in_queue_b, int in_slot_b,
+    int sum_lo_b) {
     constexpr int GPW = 32 / NG;  // clusters per warp
     __shared__ NsLists sh_all[ns_warps<NG>() * GPW];
     const int lane = threadIdx.x & 31;
@@ -431,11 +432,17 @@ __global__ void __launch_bounds__(ns_warps<NG>() * 32) k_neighbours_sub(
     NsLists& sh = sh_all[(threadIdx.x >> 5) * GPW + gq];
     const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int64_t nin = in_queue ? (int64_t)st[in_slot] : n;
+    // items: the first queue, then (optionally) a second queue that starts
+    // at gap sum sum_lo_b
+    const int64_t nin_a = in_queue ? (int64_t)st[in_slot] : n;
+    const int64_t nin = nin_a + (in_queue_b ? (int64_t)st[in_slot_b] : 0);
     const int sum_end = min(sum_hi, 2 * P.max_gap);
     for (int64_t c0 = wid * GPW; c0 < nin; c0 += nw * GPW) {
         if (c0 + gq >= nin) continue;  // the whole sub-warp leaves together
-        const int64_t c = in_queue ? in_queue[c0 + gq] : c0 + gq;
+        const int64_t item = c0 + gq;
+        const bool from_b = item >= nin_a;
+        const int64_t c = from_b ? in_queue_b[item - nin_a] : in_queue ? in_queue[item] : item;
+        const int s_lo = from_b ? sum_lo_b : sum_lo;
         const int g = grpb[c], r = rowb[c];
         const float2 vc = yzb[c];
         const float xc = geo->row_xf[r], yc = vc.x, zc = vc.y;
@@ -445,7 +452,7 @@ __global__ void __launch_bounds__(ns_warps<NG>() * 32) k_neighbours_sub(
         int bd = -1, bu = -1;
         float bd2 = 0.f;
         bool ovf = false;
-        for (int sum = sum_lo; sum <= sum_end && bd < 0 && !ovf; ++sum) {
+        for (int sum = s_lo; sum <= sum_end && bd < 0 && !ovf; ++sum) {
             for (int gu = 1; gu <= P.max_gap && bd < 0 && !ovf; ++gu) {
                 const int gd = sum - gu;
                 if (gd < 1 || gd > P.max_gap) continue;
@@ -1773,12 +1780,11 @@ cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hi
     // rest, and every gap pair for the clusters whose pass-1 list overflowed
     tpc::LaunchCount{}, k_neighbours_first<<<grid_for(n), TPB, 0, s>>>(
         n, yzb, orig, grpb, rowb, cells, geo, nb, cdn, cup, d2, st, nb_queue3, nb_queue2, ST_NB_Q2);
-    tpc::LaunchCount{}, k_neighbours_sub<NG2><<<152 * 8, ns_warps<NG2>() * 32, 0, s>>>(
-        n, nb_queue3, ST_NB_Q3, 2, 2 * NB_GAP_MAX, yzb, orig, grpb, rowb, cells, geo, nb, cdn, cup, d2, st,
-        nb_queue, nullptr, 0);
+    // one launch over both queues: the dense ones from (1, 1), then the rest
+    // from gap sum 3
     tpc::LaunchCount{}, k_neighbours_sub<NG2><<<grid_for(n / 4, 32 * 4), ns_warps<NG2>() * 32, 0, s>>>(
-        n, nb_queue2, ST_NB_Q2, 3, 2 * NB_GAP_MAX, yzb, orig, grpb, rowb, cells, geo, nb, cdn, cup, d2, st,
-        nb_queue, nullptr, 0);
+        n, nb_queue3, ST_NB_Q3, 2, 2 * NB_GAP_MAX, yzb, orig, grpb, rowb, cells, geo, nb, cdn, cup, d2, st,
+        nb_queue, nullptr, 0, nb_queue2, ST_NB_Q2, 3);
     tpc::LaunchCount{}, k_neighbours_warp<<<152 * 8, NB_WARPS * 32, 0, s>>>(nb_queue, st, yzb, orig, grpb,
                                                                         rowb, cells, geo, nb, cdn, cup, d2);
     c->mark(2, s);
