@@ -409,11 +409,13 @@ struct NsLists {
     float z[6][NS_CAP];
     int idx[6][NS_CAP];
 };
-// Two passes share this kernel: pass 1 (in_queue null) tries only the first
-// gap pair (1, 1) for every cluster and queues the clusters it leaves
-// without a pair in next_queue; pass 2 takes that queue and tries the gap
-// pairs from sum 3 on.  The gap pairs keep their order, so the result is the
-// one of a single pass, while the sub-warps of a warp do similar work.
+// The kernel takes the clusters of one or two queues, each from its own
+// first gap sum (sum_lo, sum_lo_b) up to sum_hi: the clusters whose
+// first-pass up list overflowed from (1, 1) on, and those the first pass
+// left without a pair from sum 3 on.  The gap pairs keep their order, so the
+// result is the one of a single serial search.  With next_queue set, a
+// cluster still without a pair after sum_hi is queued there instead of being
+// written.
 template <int NG>
 __global__ void __launch_bounds__(ns_warps<NG>() * 32) k_neighbours_sub(
     int64_t n, const int32_t* __restrict__ in_queue, int in_slot, int sum_lo, int sum_hi,
