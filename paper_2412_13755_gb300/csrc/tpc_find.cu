@@ -1,4 +1,4 @@
-// S1-S4 of the tracking path: row/z-cell binning, cellular-automaton
+// S1-S4 of the tracking path: (row, z cell, y cell) binning, cellular-automaton
 // neighbour finding, chaining, Kalman-guided tracklet construction and
 // selection, segment merging across sectors, and the canonical track output.
 //
