@@ -567,7 +567,7 @@ __global__ void __launch_bounds__(ns_warps<NG>() * 32) k_neighbours_sub(
 // (k_neighbours_sub, pass 2); one whose up list would overflow is queued for
 // the sub-warp kernel from the first gap pair on (longer lists).
 constexpr int NF = 6;
-__global__ void __launch_bounds__(256) k_neighbours_first(
+__global__ void __launch_bounds__(256, 4) k_neighbours_first(
     int64_t n, const float2* __restrict__ yzb,
     const int32_t* __restrict__ orig, const int32_t* __restrict__ grpb,
     const uint8_t* __restrict__ rowb, Cells cells, const Geo* __restrict__ geo, NbPrm P,
