@@ -1358,7 +1358,7 @@ __device__ __forceinline__ bool ma_ok(const int4* __restrict__ gs_meta, int qa, 
 // its outermost row is moved to B's innermost plane and compared with B's
 // inward-fit state there (chi2 of the 5-d difference, solved in FP64).  One
 // warp per B; the lanes stride over the group-sorted candidates.
-__global__ void __launch_bounds__(256) k_merge_cand(
+__global__ void __launch_bounds__(256, 4) k_merge_cand(
     const int32_t* __restrict__ seg_grp, const float* __restrict__ tl_state,
     const int32_t* __restrict__ grp_tl_off, const int4* __restrict__ gs_meta,
     const Geo* __restrict__ geo, MgPrm P, int32_t* st, int32_t* cand_n, int32_t* cand_a,
