@@ -12,6 +12,7 @@
 
 #include <cooperative_groups.h>
 
+#include "tpc_bits.cuh"
 #include "tpc_dev.cuh"
 
 namespace tpc {
@@ -282,46 +283,6 @@ struct NbPrm {
     float win_y, win_z, chi2_link, sy2, sz2;
     int max_gap;
 };
-
-// window test, FP32, one rounding per operation
-__device__ __forceinline__ bool in_win(float xa, float ya, float za, float xb, float yb, float zb,
-                                       float wy, float wz) {
-    const float dx = fabsf(__fsub_rn(xb, xa));
-    return fabsf(__fsub_rn(yb, ya)) <= __fmul_rn(wy, dx) &&
-           fabsf(__fsub_rn(zb, za)) <= __fmul_rn(wz, dx);
-}
-
-// Triplet D^2, FP32 with one rounding per operation: c is compared with
-// the straight line from d to u at x_c, a = (x_c - x_d) / (x_u - x_d),
-//   D^2 = ry^2 / (sy2 f) + rz^2 / (sz2 f),  f = 1 + a^2 + (1 - a)^2.
-// The row-dependent part (a, f) is computed once per gap pair.  A pair with
-// D^2 <= chi2 has ry^2 <= chi2 sy2 f and rz^2 <= chi2 sz2 f; tested with a
-// relative margin of 1e-5 over the rounding, these bounds reject most pairs
-// before the two divisions, and leave D^2 unchanged for the others.
-struct TripletRows {
-    float a, dy, dz, ty, tz;
-};
-__device__ __forceinline__ TripletRows triplet_rows(float xd, float xc, float xu, float sy2, float sz2,
-                                                    float chi2) {
-    TripletRows t;
-    t.a = __fdiv_rn(__fsub_rn(xc, xd), __fsub_rn(xu, xd));
-    const float b = __fsub_rn(1.0f, t.a);
-    const float f = __fadd_rn(__fadd_rn(1.0f, __fmul_rn(t.a, t.a)), __fmul_rn(b, b));
-    t.dy = __fmul_rn(sy2, f);
-    t.dz = __fmul_rn(sz2, f);
-    t.ty = __fmul_rn(__fmul_rn(chi2, t.dy), 1.00001f);
-    t.tz = __fmul_rn(__fmul_rn(chi2, t.dz), 1.00001f);
-    return t;
-}
-// D^2 of the triplet (d, c, u), or +inf where the bounds show D^2 > chi2
-__device__ __forceinline__ float triplet_d2_cut(const TripletRows& t, float yd, float zd, float yc, float zc,
-                                                float yu, float zu) {
-    const float ry = __fsub_rn(yc, __fadd_rn(yd, __fmul_rn(t.a, __fsub_rn(yu, yd))));
-    const float rz = __fsub_rn(zc, __fadd_rn(zd, __fmul_rn(t.a, __fsub_rn(zu, zd))));
-    const float ry2 = __fmul_rn(ry, ry), rz2 = __fmul_rn(rz, rz);
-    if (ry2 > t.ty || rz2 > t.tz) return INFINITY;
-    return __fadd_rn(__fdiv_rn(ry2, t.dy), __fdiv_rn(rz2, t.dz));
-}
 
 // The cells holding every candidate of row rr that can pass in_win for the
 // cluster at (xc, yc, zc): the window half-widths win_y |dx|, win_z |dx|
@@ -893,63 +854,6 @@ struct TlPrm {
     double bz, seed_snp, seed_qpt;
     float prior[5];
 };
-
-// Rows holding a hit of a tracklet: bit r of the 152-bit mask m[0..4].  The
-// word loops below are unrolled, so that the mask stays in registers.
-constexpr int MASK_W = 5;
-// highest row below r with a hit, -1 if none
-__device__ __forceinline__ int mask_below(const uint32_t (&m)[MASK_W], int r) {
-    int best = -1;
-#pragma unroll
-    for (int w = 0; w < MASK_W; ++w) {
-        const int k = r - 32 * w;  // bits 0..k-1 of word w lie below r
-        const uint32_t b = k <= 0 ? 0u : k >= 32 ? m[w] : m[w] & ((1u << k) - 1u);
-        if (b) best = 32 * w + 31 - __clz(b);
-    }
-    return best;
-}
-// lowest row above r with a hit, NROW if none
-__device__ __forceinline__ int mask_above(const uint32_t (&m)[MASK_W], int r) {
-    int best = NROW;
-#pragma unroll
-    for (int w = MASK_W - 1; w >= 0; --w) {
-        const int k = r + 1 - 32 * w;  // bits k..31 of word w lie above r
-        const uint32_t b = k <= 0 ? m[w] : k >= 32 ? 0u : m[w] & ~((1u << k) - 1u);
-        if (b) best = 32 * w + __ffs(b) - 1;
-    }
-    return best;
-}
-// row of the j-th hit (from 0) counted from the top or from the bottom
-__device__ __forceinline__ int mask_nth(const uint32_t (&m)[MASK_W], int j, bool from_top) {
-    int row = -1, left = j;
-#pragma unroll
-    for (int i = 0; i < MASK_W; ++i) {
-        const int w = from_top ? MASK_W - 1 - i : i;
-        const uint32_t mw = from_top ? m[MASK_W - 1 - i] : m[i];  // static indices only
-        const int c = __popc(mw);
-        if (row < 0) {
-            if (left < c) {
-                uint32_t b = mw;
-                if (from_top) {
-                    for (int t = 0; t < left; ++t) b &= ~(1u << (31 - __clz(b)));
-                    row = 32 * w + 31 - __clz(b);
-                } else {
-                    for (int t = 0; t < left; ++t) b &= b - 1u;
-                    row = 32 * w + __ffs(b) - 1;
-                }
-            } else {
-                left -= c;
-            }
-        }
-    }
-    return row;
-}
-__device__ __forceinline__ void mask_set(uint32_t (&m)[MASK_W], int r) {
-    const uint32_t bit = 1u << (r & 31);
-    const int wr = r >> 5;
-#pragma unroll
-    for (int w = 0; w < MASK_W; ++w) m[w] |= wr == w ? bit : 0u;
-}
 
 // Three-point seed (FP32) of a tracklet's hits for one fit direction:
 // first, middle (n/2-th in fit order) and last hit.
