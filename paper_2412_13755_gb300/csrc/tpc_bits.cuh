@@ -26,6 +26,9 @@ TPC_HD float add(float a, float b) { return __fadd_rn(a, b); }
 TPC_HD float sub(float a, float b) { return __fsub_rn(a, b); }
 TPC_HD float mul(float a, float b) { return __fmul_rn(a, b); }
 TPC_HD float div(float a, float b) { return __fdiv_rn(a, b); }
+TPC_HD float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+TPC_HD float rcp(float a) { return __frcp_rn(a); }
+TPC_HD float sqrt(float a) { return __fsqrt_rn(a); }
 #else
 TPC_HD int clz32(uint32_t x) { return x ? __builtin_clz(x) : 32; }
 TPC_HD int ffs32(uint32_t x) { return __builtin_ffs((int)x); }
@@ -34,6 +37,9 @@ TPC_HD float add(float a, float b) { return a + b; }
 TPC_HD float sub(float a, float b) { return a - b; }
 TPC_HD float mul(float a, float b) { return a * b; }
 TPC_HD float div(float a, float b) { return a / b; }
+TPC_HD float fma(float a, float b, float c) { return fmaf(a, b, c); }
+TPC_HD float rcp(float a) { return 1.0f / a; }
+TPC_HD float sqrt(float a) { return sqrtf(a); }
 #endif
 
 }  // namespace bits

@@ -8,6 +8,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "tpc_ff.cuh"
 #include "tpc_internal.h"
 
 namespace tpc {
@@ -27,18 +28,6 @@ __device__ __forceinline__ int group_of(const int64_t* __restrict__ off, int G, 
     }
     return lo;
 }
-
-// Packed symmetric 5x5: 00 01 02 03 04 11 12 13 14 22 23 24 33 34 44.
-// Closed form (row a of the upper triangle starts at 5a - a(a-1)/2), not
-// recursive, so that constant indices fold at compile time and the packed
-// arrays stay in registers.
-__host__ __device__ __forceinline__ constexpr int sx(int i, int j) {
-    return (i <= j ? i : j) * 5 - (i <= j ? i : j) * ((i <= j ? i : j) - 1) / 2 + (i <= j ? j : i) -
-           (i <= j ? i : j);
-}
-static_assert(sx(0, 0) == 0 && sx(0, 4) == 4 && sx(1, 1) == 5 && sx(2, 1) == 6 && sx(2, 2) == 9 &&
-                  sx(3, 3) == 12 && sx(4, 3) == 13 && sx(4, 4) == 14,
-              "packed index");
 
 __device__ __forceinline__ float t_sqrt(float v) { return sqrtf(v); }
 __device__ __forceinline__ double t_sqrt(double v) { return sqrt(v); }
@@ -307,119 +296,6 @@ __device__ __forceinline__ double kf_update_dcov(KF& s, double Cd[15], float my,
 #pragma unroll
         for (int j = i; j < 5; ++j) Cd[sx(i, j)] -= k0[i] * c0[j] + k1[i] * c1[j];
     return dr0 * dr0 * e00 + 2.0 * dr0 * dr1 * e01 + dr1 * dr1 * e11;
-}
-
-// ---- float-float covariance --------------------------------------------
-// A covariance entry as an unevaluated sum hi + lo of two FP32 numbers
-// (about 48 significant bits), updated with error-free transformations:
-// TwoSum (Knuth) for sums and TwoProduct through the fused multiply-add for
-// products.  Every operation is an explicitly rounded intrinsic, so the
-// compiler cannot contract them into other fused operations.  The Kalman update C - K H C cancels by orders of magnitude once
-// a track is well measured; FP32 storage loses the small directions there,
-// while GB300's FP64 rate is a small fraction of its FP32 rate.
-struct ff {
-    float hi, lo;
-};
-__device__ __forceinline__ ff ff_from(float a) { return ff{a, 0.f}; }
-// a + b exactly as s + e (Knuth's TwoSum)
-__device__ __forceinline__ ff two_sum(float a, float b) {
-    const float s = __fadd_rn(a, b);
-    const float v = __fsub_rn(s, a);
-    return ff{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, v)), __fsub_rn(b, v))};
-}
-// a + b = s + e for |a| >= |b| (Dekker's FastTwoSum)
-__device__ __forceinline__ ff fast_two_sum(float a, float b) {
-    const float s = __fadd_rn(a, b);
-    return ff{s, __fsub_rn(b, __fsub_rn(s, a))};
-}
-// x + y (the lo parts added in FP32, then renormalised)
-__device__ __forceinline__ ff ff_add(ff x, ff y) {
-    ff s = two_sum(x.hi, y.hi);
-    s.lo = __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo));
-    return fast_two_sum(s.hi, s.lo);
-}
-__device__ __forceinline__ ff ff_neg(ff x) { return ff{-x.hi, -x.lo}; }
-// x * f for an FP32 f: TwoProduct of the hi part (exact through the FMA)
-__device__ __forceinline__ ff ff_mul_f(ff x, float f) {
-    const float p = __fmul_rn(x.hi, f);
-    const float e = __fmaf_rn(x.lo, f, __fmaf_rn(x.hi, f, -p));
-    return fast_two_sum(p, e);
-}
-__device__ __forceinline__ ff ff_mul(ff x, ff y) {
-    const float p = __fmul_rn(x.hi, y.hi);
-    float e = __fmaf_rn(x.hi, y.hi, -p);
-    e = __fmaf_rn(x.hi, y.lo, e);
-    e = __fmaf_rn(x.lo, y.hi, e);
-    return fast_two_sum(p, e);
-}
-// 1 / x: an FP32 reciprocal refined by one Newton step r + r (1 - x r)
-// carried in float-float
-__device__ __forceinline__ ff ff_rcp(ff x) {
-    const float r = __frcp_rn(x.hi);
-    const ff xr = ff_mul_f(x, r);
-    const ff one_minus = ff_add(ff_from(1.f), ff_neg(xr));
-    return ff_add(ff_from(r), ff_mul_f(one_minus, r));
-}
-// acc + x * f: the product's error term joins the sum's low part, with one
-// renormalisation at the end
-__device__ __forceinline__ ff ff_fma_f(ff acc, ff x, float f) {
-    const float p = __fmul_rn(x.hi, f);
-    const float e = __fmaf_rn(x.lo, f, __fmaf_rn(x.hi, f, -p));
-    const ff s = two_sum(acc.hi, p);
-    return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(acc.lo, e)));
-}
-// x1 y1 + x2 y2 in float-float: both products as (p, e) with p = fl(x.hi
-// y.hi) and e the rest (TwoProduct through the FMA, plus the cross terms),
-// the two p summed exactly and the errors added to the low part
-__device__ __forceinline__ ff ff_dot2(ff x1, ff y1, ff x2, ff y2) {
-    const float p1 = __fmul_rn(x1.hi, y1.hi), p2 = __fmul_rn(x2.hi, y2.hi);
-    const float e1 = __fmaf_rn(x1.lo, y1.hi, __fmaf_rn(x1.hi, y1.lo, __fmaf_rn(x1.hi, y1.hi, -p1)));
-    const float e2 = __fmaf_rn(x2.lo, y2.hi, __fmaf_rn(x2.hi, y2.lo, __fmaf_rn(x2.hi, y2.hi, -p2)));
-    const ff s = two_sum(p1, p2);
-    return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(e1, e2)));
-}
-
-// sqrt(x) for x > 0: the FP32 root refined by one Newton (Heron) step
-// s + (x - s^2) / (2 s), the residual x - s^2 formed exactly with TwoProduct
-__device__ __forceinline__ ff ff_sqrt(ff x) {
-    const float s = __fsqrt_rn(x.hi);
-    const float p = __fmul_rn(s, s);
-    const float pe = __fmaf_rn(s, s, -p);
-    const ff r = ff_add(x, ff{-p, -pe});
-    return fast_two_sum(s, __fdiv_rn(r.hi, __fmul_rn(2.f, s)));
-}
-
-// chi2 = d^T M^-1 d for a 5x5 symmetric positive definite M (packed upper
-// triangle) by Cholesky factorisation and forward substitution, in
-// float-float.  Returns false when a pivot is not positive.
-__device__ __forceinline__ bool chol_chi2_ff(const ff d[5], const ff M[15], ff& out) {
-    ff Lm[5][5], inv[5];
-#pragma unroll
-    for (int i = 0; i < 5; ++i)
-#pragma unroll
-        for (int j = 0; j <= i; ++j) {
-            ff acc = M[sx(i, j)];
-#pragma unroll
-            for (int l = 0; l < j; ++l) acc = ff_add(acc, ff_neg(ff_mul(Lm[i][l], Lm[j][l])));
-            if (i == j) {
-                if (!(acc.hi > 0.f)) return false;
-                Lm[i][i] = ff_sqrt(acc);
-                inv[i] = ff_rcp(Lm[i][i]);
-            } else {
-                Lm[i][j] = ff_mul(acc, inv[j]);
-            }
-        }
-    ff v[5], c2 = ff_from(0.f);
-#pragma unroll
-    for (int i = 0; i < 5; ++i) {
-        ff acc = d[i];
-#pragma unroll
-        for (int l = 0; l < i; ++l) acc = ff_add(acc, ff_neg(ff_mul(Lm[i][l], v[l])));
-        v[i] = ff_mul(acc, inv[i]);
-        c2 = ff_add(c2, ff_mul(v[i], v[i]));
-    }
-    out = c2;
-    return true;
 }
 
 // Covariance transform C <- J C J^T in float-float for the Jacobian of

@@ -1,6 +1,9 @@
-"""The find kernels' exact helpers (row masks, window test, triplet D^2
-cut), compiled for the host and checked bit for bit against brute force and
-against the D^2 definition; no GPU needed."""
+"""Kernel helpers compiled for the host and checked without a GPU:
+- the find kernels' exact helpers (row masks, window test, triplet D^2 cut),
+  bit for bit against brute force and the D^2 definition;
+- the float-float arithmetic of the fit and the merge, against long double
+  within counted error bounds (TwoSum exact, each operation a few u^2, the
+  Cholesky chi2 within 64 kappa u^2)."""
 import os
 import shutil
 import subprocess
@@ -10,14 +13,15 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def test_kernel_helpers_on_host(tmp_path):
+@pytest.mark.parametrize("program", ["kernel_helpers_host", "ff_host"])
+def test_kernel_helpers_on_host(tmp_path, program):
     cxx = shutil.which("g++") or shutil.which("c++")
     if cxx is None:
         pytest.skip("no C++ compiler")
-    exe = tmp_path / "kernel_helpers"
+    exe = tmp_path / program
     subprocess.run([cxx, "-std=c++17", "-O2", "-ffp-contract=off",
                     "-I", os.path.join(ROOT, "paper_2412_13755_gb300", "csrc"),
-                    os.path.join(ROOT, "tests", "kernel_helpers_host.cpp"), "-o", str(exe)],
+                    os.path.join(ROOT, "tests", program + ".cpp"), "-o", str(exe)],
                    check=True)
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=300)
     print(r.stdout)
