@@ -1,0 +1,119 @@
+"""Parity at the benchmark's full sizes, in the launch configuration the
+benchmark times:
+
+* the 512-event uneven batch (about 1e8 clusters) as one autotuned context:
+  the whole track list passes the structural checks; sampled events (the
+  smallest, the largest and six drawn with a fixed seed) are found again by
+  the oracle one by one (events are independent) and their cluster-to-track
+  assignment must agree for >= 99.99% of the clusters; the fit of every
+  track of those events must match the oracle's fit of the same hit list
+  within |dp_i| <= 1e-5 max(|p_i|, s_i);
+* the 100-collision pile-up frame (about 1.8e8 clusters, one event): the
+  whole track list passes the structural checks, and the fit of 5000 tracks
+  drawn with a fixed seed matches the oracle's fit of their hit lists.
+
+The oracle cannot find a whole frame in seconds; for it the assignment is
+covered by the smaller pile-up parity test and, at full size, by the
+structural properties that hold at any size.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+from paper_2412_13755_gb300 import synth, tpc  # noqa: E402
+import track_checks as tc  # noqa: E402
+
+SCALE = np.array([1.0, 1.0, 0.1, 0.1, 0.1])
+
+
+def _device_inputs(ev, dev="cuda"):
+    y = torch.from_numpy(ev.y).to(dev)
+    z = torch.from_numpy(ev.z).to(dev)
+    row = torch.from_numpy(ev.row.view(np.int16)).to(dev).view(torch.uint16)
+    off = torch.from_numpy(ev.evt_sector_off).to(dev)
+    return y, z, row, off
+
+
+def _fit_outputs(cap, dev="cuda"):
+    return (torch.empty(cap, 5, dtype=torch.float32, device=dev),
+            torch.empty(cap, 15, dtype=torch.float32, device=dev),
+            torch.empty(cap, dtype=torch.float32, device=dev),
+            torch.empty(cap, dtype=torch.int32, device=dev))
+
+
+def _to_host(out, fit):
+    T = int(out[3].item())
+    off = out[1][:T + 1].cpu().numpy()
+    hits = out[2][:int(off[-1])].cpu().numpy()
+    toc = out[0].cpu().numpy()
+    par, _, _, ndf = (f[:T].cpu().numpy() for f in fit)
+    return toc, off, hits, par, ndf
+
+
+def _fit_parity(orc, ev, off, hits, par, ndf, keep):
+    s_off, s_hits = tc.sub_tracks(off, hits, keep)
+    opar, _, _, ondf = orc.fit_tracks(ev.y, ev.z, ev.row, ev.sector_of_cluster(), s_off, s_hits)
+    gpar, gndf = par[keep].astype(np.float64), ndf[keep]
+    assert np.array_equal(gndf <= 0, ondf <= 0), "transport failures differ"
+    ok = ondf > 0
+    assert np.array_equal(gndf[ok], ondf[ok])
+    rel = np.abs(gpar - opar) / np.maximum(np.abs(opar), SCALE)
+    print(f"  fit of {len(keep)} tracks: max relative error per parameter {rel[ok].max(0)}")
+    assert np.all(rel[ok] <= 1e-5), rel[ok].max(0)
+
+
+def test_uneven_batch_full_size(orc):
+    ev = synth.uneven_batch_parallel()
+    n, E = ev.n, ev.n_events
+    cap = n // 10 + 16
+    tr = tpc.Tracker(n, E)
+    try:
+        y, z, row, off = _device_inputs(ev)
+        out = tr.alloc_find_outputs(cap)
+        fit = _fit_outputs(cap)
+        tr.load(y, z, row, off, E)
+        tr.autotune(out=out)
+        tr.find(out=out)
+        tr.fit(out[1], out[2], cap, out[3], out=fit)
+        torch.cuda.synchronize()
+        tr.check()
+        toc, t_off, hits, par, ndf = _to_host(out, fit)
+    finally:
+        tr.close()
+    print(f"\nbatch: {E} events, {n} clusters, {len(t_off) - 1} tracks")
+    tc.check_structure(ev, toc, t_off, hits)
+    canon = tc.canon_of_cluster(t_off, hits, n)
+    events = tc.sample_events(ev, 8, seed=11)
+    agree, total = tc.per_event_agreement(orc, ev, events, canon)
+    print(f"  events {events}: {total} clusters, agreement {agree / total:.6f}")
+    assert agree >= 0.9999 * total
+    evt = tc.event_of_cluster(ev.evt_sector_off, E)
+    keep = np.flatnonzero(np.isin(evt[hits[t_off[:-1]]], events))
+    assert len(keep) > 0
+    _fit_parity(orc, ev, t_off, hits, par, ndf, keep)
+
+
+def test_pileup_frame_full_size(orc):
+    ev = synth.pileup_frame_parallel()
+    n = ev.n
+    cap = n // 10 + 16
+    tr = tpc.Tracker(n, 1)
+    try:
+        y, z, row, off = _device_inputs(ev)
+        tr.load(y, z, row, off, 1)
+        out = tr.alloc_find_outputs(cap)
+        fit = _fit_outputs(cap)
+        tr.find(out=out)
+        tr.fit(out[1], out[2], cap, out[3], out=fit)
+        torch.cuda.synchronize()
+        tr.check()
+        toc, t_off, hits, par, ndf = _to_host(out, fit)
+    finally:
+        tr.close()
+    T = len(t_off) - 1
+    print(f"\npile-up frame: {n} clusters, {T} tracks")
+    tc.check_structure(ev, toc, t_off, hits)
+    keep = np.sort(np.random.default_rng(12).choice(T, min(T, 5000), replace=False))
+    _fit_parity(orc, ev, t_off, hits, par, ndf, keep)
