@@ -140,6 +140,53 @@ def _need(t, dtype, name):
         raise TypeError(f"{name} must be a contiguous CUDA {dtype} tensor")
 
 
+# The C ABI takes plain pointers: it cannot see how large a caller's buffer
+# is.  The binding records the cluster count of each context's last load and
+# refuses, before any launch, a buffer smaller than what the call writes.
+_loaded_n: dict[int, int] = {}
+
+
+def _need_len(t, n, name, what):
+    if t.numel() < n:
+        raise ValueError(f"{what}: {name} holds {t.numel()} entries, the call writes {n}")
+
+
+def check_find_outputs(n, track_of_cluster, trk_off, trk_hits, n_tracks_dev, what="tpc_find_tracks"):
+    """tpc_find_tracks and tpc_autotune write n entries of track_of_cluster
+    and trk_hits (n = clusters loaded), trk_off.numel() entries of trk_off
+    (the track capacity plus one) and one of n_tracks_dev."""
+    _need_len(track_of_cluster, n, "track_of_cluster", what)
+    _need_len(trk_hits, n, "trk_hits", what)
+    _need_len(trk_off, 2, "trk_off", what)
+    _need_len(n_tracks_dev, 1, "n_tracks_dev", what)
+
+
+def check_fit_buffers(n_tracks, trk_off, params, cov, chi2, ndf, what="tpc_fit_tracks"):
+    """tpc_fit_tracks reads trk_off[n_tracks + 1] and writes n_tracks rows of
+    params (5), cov (15), chi2 and ndf."""
+    T = int(n_tracks)
+    if T < 0:
+        raise ValueError(f"{what}: n_tracks {T} < 0")
+    _need_len(trk_off, T + 1, "trk_off", what)
+    _need_len(params, 5 * T, "params", what)
+    _need_len(cov, 15 * T, "cov", what)
+    _need_len(chi2, T, "chi2", what)
+    _need_len(ndf, T, "ndf", what)
+
+
+def check_adjoint_buffers(n_tracks, trk_off, align, chi2_total, grad, what="tpc_fit_adjoint"):
+    """tpc_fit_adjoint reads trk_off[n_tracks + 1] and align[216] and writes
+    chi2_total[1] and, when given, grad[216]."""
+    T = int(n_tracks)
+    if T < 0:
+        raise ValueError(f"{what}: n_tracks {T} < 0")
+    _need_len(trk_off, T + 1, "trk_off", what)
+    _need_len(align, 216, "align", what)
+    _need_len(chi2_total, 1, "chi2_total", what)
+    if grad is not None:
+        _need_len(grad, 216, "grad", what)
+
+
 # --- the C ABI, one Python function per entry point --------------------------
 
 def tpc_create(params: Params | None = None):
@@ -151,6 +198,7 @@ def tpc_create(params: Params | None = None):
 
 
 def tpc_destroy(ctx):
+    _loaded_n.pop(ctx.value, None)
     load_library().tpc_destroy(ctx)
 
 
@@ -176,12 +224,14 @@ def tpc_load_clusters(ctx, y, z, row, charge, evt_sector_off, n_events, stream=N
                                           y.numel(), _ptr(evt_sector_off), int(n_events),
                                           _stream(stream))
     _check(ctx, rc, "tpc_load_clusters")
+    _loaded_n[ctx.value] = y.numel()
 
 
 def tpc_find_tracks(ctx, track_of_cluster, trk_off, trk_hits, n_tracks_dev, stream=None):
     for t, n in ((track_of_cluster, "track_of_cluster"), (trk_off, "trk_off"),
                  (trk_hits, "trk_hits"), (n_tracks_dev, "n_tracks_dev")):
         _need(t, torch.int32, n)
+    check_find_outputs(_loaded_n.get(ctx.value, 0), track_of_cluster, trk_off, trk_hits, n_tracks_dev)
     rc = load_library().tpc_find_tracks(ctx, _ptr(track_of_cluster), _ptr(trk_off), _ptr(trk_hits),
                                         _ptr(n_tracks_dev), trk_off.numel() - 1, _stream(stream))
     _check(ctx, rc, "tpc_find_tracks")
@@ -196,6 +246,7 @@ def tpc_fit_tracks(ctx, trk_off, trk_hits, n_tracks, n_tracks_dev, params, cov, 
     _need(ndf, torch.int32, "ndf")
     if n_tracks_dev is not None:
         _need(n_tracks_dev, torch.int32, "n_tracks_dev")
+    check_fit_buffers(n_tracks, trk_off, params, cov, chi2, ndf)
     rc = load_library().tpc_fit_tracks(ctx, _ptr(trk_off), _ptr(trk_hits), int(n_tracks),
                                        _ptr(n_tracks_dev), _ptr(params), _ptr(cov), _ptr(chi2),
                                        _ptr(ndf), _stream(stream))
@@ -209,6 +260,7 @@ def tpc_fit_adjoint(ctx, trk_off, trk_hits, n_tracks, align, chi2_total, grad=No
     _need(chi2_total, torch.float64, "chi2_total")
     if grad is not None:
         _need(grad, torch.float64, "grad")
+    check_adjoint_buffers(n_tracks, trk_off, align, chi2_total, grad)
     rc = load_library().tpc_fit_adjoint(ctx, _ptr(trk_off), _ptr(trk_hits), int(n_tracks),
                                         _ptr(align), _ptr(chi2_total), _ptr(grad), _stream(stream))
     _check(ctx, rc, "tpc_fit_adjoint")
@@ -220,6 +272,11 @@ def tpc_set_tune(ctx, tune: Tune | None):
 
 
 def tpc_autotune(ctx, track_of_cluster, trk_off, trk_hits, n_tracks_dev, stream=None) -> Tune:
+    for t, n in ((track_of_cluster, "track_of_cluster"), (trk_off, "trk_off"),
+                 (trk_hits, "trk_hits"), (n_tracks_dev, "n_tracks_dev")):
+        _need(t, torch.int32, n)
+    check_find_outputs(_loaded_n.get(ctx.value, 0), track_of_cluster, trk_off, trk_hits, n_tracks_dev,
+                       "tpc_autotune")
     best = Tune()
     rc = load_library().tpc_autotune(ctx, _ptr(track_of_cluster), _ptr(trk_off), _ptr(trk_hits),
                                      _ptr(n_tracks_dev), trk_off.numel() - 1, C.byref(best),
@@ -281,27 +338,22 @@ class Tracker:
 
     def load(self, y, z, row, evt_sector_off, n_events, charge=None, stream=None):
         self._inputs = (y, z, row, charge, evt_sector_off)  # keep alive
-        self.n = y.numel()
         tpc_load_clusters(self.ctx, y, z, row, charge, evt_sector_off, n_events, stream)
+        self.n = y.numel()
 
     def alloc_find_outputs(self, track_cap=None):
-        cap = int(track_cap if track_cap is not None else max(1, self.n // 10 + 16))
+        """Outputs of find for the loaded batch; before a load, for the
+        largest batch the context takes (max_clusters)."""
+        m = max(self.n if self.n > 0 else self.max_clusters, 1)
+        cap = int(track_cap if track_cap is not None else m // 10 + 16)
         dev = self.device
-        return (torch.empty(max(self.n, 1), dtype=torch.int32, device=dev),
+        return (torch.empty(m, dtype=torch.int32, device=dev),
                 torch.empty(cap + 1, dtype=torch.int32, device=dev),
-                torch.empty(max(self.n, 1), dtype=torch.int32, device=dev),
+                torch.empty(m, dtype=torch.int32, device=dev),
                 torch.empty(1, dtype=torch.int32, device=dev))
 
     def find(self, out=None, track_cap=None, stream=None):
         out = out or self.alloc_find_outputs(track_cap)
-        toc, trk_off, trk_hits, n_dev = out
-        # the library writes n entries of toc and trk_hits and track_cap+1 of
-        # trk_off: undersized buffers are refused here, before any launch
-        if toc.numel() < self.n or trk_hits.numel() < self.n or trk_off.numel() < 2 \
-                or n_dev.numel() < 1:
-            raise ValueError(f"find outputs too small for {self.n} clusters: "
-                             f"toc {toc.numel()}, trk_off {trk_off.numel()}, "
-                             f"trk_hits {trk_hits.numel()}")
         tpc_find_tracks(self.ctx, *out, stream=stream)
         return out
 

@@ -135,18 +135,38 @@ def test_empty_input():
 
 
 def test_undersized_outputs_refused():
-    """Buffers smaller than the loaded cluster count are refused on the host,
-    before any kernel could write past them."""
+    """Buffers smaller than what a call writes are refused on the host,
+    before any kernel could write past them: find and autotune outputs
+    smaller than the loaded cluster count, fit outputs and adjoint buffers
+    smaller than the track count."""
     ev = synth.one_sector()
     tr = tpc.Tracker(ev.n, 1)
-    small = tr.alloc_find_outputs(8)  # allocated before load: sized for 0 clusters
     tr.load(*to_dev(ev), 1)
-    with pytest.raises(ValueError):
+    i32 = dict(dtype=torch.int32, device="cuda")
+    small = (torch.empty(ev.n - 1, **i32), torch.empty(9, **i32), torch.empty(ev.n, **i32),
+             torch.empty(1, **i32))
+    with pytest.raises(ValueError, match="track_of_cluster"):
         tr.find(out=small)
+    with pytest.raises(ValueError, match="track_of_cluster"):
+        tr.autotune(out=small)
+    short_hits = (small[2], small[1], small[0], small[3])
+    with pytest.raises(ValueError, match="trk_hits"):
+        tr.find(out=short_hits)
     out = tr.find(out=tr.alloc_find_outputs())
     torch.cuda.synchronize()
     tr.check()
-    assert int(out[3].item()) > 0
+    T = int(out[3].item())
+    assert T > 0
+    f32 = dict(dtype=torch.float32, device="cuda")
+    fit = (torch.empty(T, 5, **f32), torch.empty(T - 1, 15, **f32), torch.empty(T, **f32),
+           torch.empty(T, **i32))
+    with pytest.raises(ValueError, match="cov"):
+        tr.fit(out[1], out[2], T, out=fit)
+    with pytest.raises(ValueError, match="trk_off"):
+        tr.fit(out[1][:T], out[2], T)
+    with pytest.raises(ValueError, match="align"):
+        tr.adjoint(out[1], out[2], T, torch.zeros(215, dtype=torch.float64, device="cuda"))
+    tr.check()
 
 
 def test_pileup_drift_offsets_recovered():

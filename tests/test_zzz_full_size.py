@@ -71,9 +71,9 @@ def test_uneven_batch_full_size(orc):
     tr = tpc.Tracker(n, E)
     try:
         y, z, row, off = _device_inputs(ev)
+        tr.load(y, z, row, off, E)
         out = tr.alloc_find_outputs(cap)
         fit = _fit_outputs(cap)
-        tr.load(y, z, row, off, E)
         tr.autotune(out=out)
         tr.find(out=out)
         tr.fit(out[1], out[2], cap, out[3], out=fit)
