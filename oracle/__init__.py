@@ -45,6 +45,16 @@ class Diag(C.Structure):
     ]
 
 
+class FieldGrid(C.Structure):
+    """Voxel grid of a displacement field (orc_field_grid)."""
+    _fields_ = [("n_band", C.c_int32), ("n_y", C.c_int32), ("n_z", C.c_int32),
+                ("u_lo", C.c_float), ("u_inv", C.c_float), ("z_inv", C.c_float)]
+
+
+def field_grid(n_band, n_y, n_z, u_lo, u_inv, z_inv) -> FieldGrid:
+    return FieldGrid(int(n_band), int(n_y), int(n_z), float(u_lo), float(u_inv), float(z_inv))
+
+
 def build(force: bool = False) -> str:
     src = os.path.join(_HERE, "tpc_oracle.cpp")
     if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= max(
@@ -66,6 +76,7 @@ def lib():
         _lib = C.CDLL(_SO)
         _lib.orc_find_tracks.restype = C.c_int64
         _lib.orc_bruteforce_chains.restype = C.c_int64
+        _lib.orc_voxel_of.restype = C.c_int64
     return _lib
 
 
@@ -154,6 +165,42 @@ def fit_adjoint(y, z, row, sector_of, trk_off, trk_hits, align, params=None,
     g = np.zeros(216) if want_grad else None
     lib().orc_fit_adjoint(_p(y), _p(z), _p(row), _p(sec), _p(off), _p(hits),
                           C.c_int32(T), _p(al), C.byref(prm), C.byref(tot), _p(g))
+    return (tot.value, g) if want_grad else tot.value
+
+
+def voxel_of(y, z, row, sector_of, grid: FieldGrid):
+    """Voxel of each cluster; returns (vox[n], number of voxels)."""
+    y, z, row = _c(y, np.float32), _c(z, np.float32), _c(row, np.uint16)
+    sec = _c(sector_of, np.int32)
+    vox = np.empty(y.shape[0], np.int32)
+    nv = lib().orc_voxel_of(_p(y), _p(z), _p(row), _p(sec), C.c_int64(y.shape[0]),
+                            C.byref(grid), _p(vox))
+    if nv < 0:
+        raise ValueError("invalid field grid")
+    return vox, int(nv)
+
+
+def field_adjoint(y, z, row, sector_of, trk_off, trk_hits, grid: FieldGrid, field,
+                  align=None, params=None, want_grad=True):
+    """Total chi2 with the displacement field[n_vox, 3] added to the aligned
+    clusters, and d chi2 / d field (exact, dual numbers)."""
+    y, z, row = _c(y, np.float32), _c(z, np.float32), _c(row, np.uint16)
+    sec = _c(sector_of, np.int32)
+    off, hits = _c(trk_off, np.int32), _c(trk_hits, np.int32)
+    T = off.shape[0] - 1
+    prm = params or default_params()
+    fld = _c(field, np.float64)
+    nv = 36 * grid.n_band * grid.n_y * grid.n_z
+    if fld.size != 3 * nv:
+        raise ValueError(f"field holds {fld.size} values, the grid has {nv} voxels x 3")
+    al = _c(align, np.float64) if align is not None else None
+    tot = C.c_double(0.0)
+    g = np.zeros((nv, 3)) if want_grad else None
+    rc = lib().orc_field_adjoint(_p(y), _p(z), _p(row), _p(sec), _p(off), _p(hits),
+                                 C.c_int32(T), _p(al), C.byref(grid), _p(fld), C.byref(prm),
+                                 C.byref(tot), _p(g))
+    if rc != 0:
+        raise ValueError("invalid field grid")
     return (tot.value, g) if want_grad else tot.value
 
 

@@ -20,6 +20,7 @@
 #include "tpc_oracle.h"
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -360,12 +361,19 @@ void corrected(const T th[6], double xr, double y, double z, T& xo, T& yo, T& zo
     zo = z2 + th[2];
 }
 
+// No displacement field: the corrected position is the aligned one.
+struct NoDisp {
+    std::nullptr_t operator()(int) const { return nullptr; }
+};
+
 // One full fit.  th(i) returns the 6 correction parameters of cluster hit i's
-// sector as T (or null alignment).  Returns false when a transport fails.
-template <class T, class ThFn>
+// sector as T (or null alignment); disp(j) returns the displacement (x, y, z)
+// added to the j-th cluster of the list after the alignment (or null).
+// Returns false when a transport fails.
+template <class T, class ThFn, class DispFn = NoDisp>
 bool kf_fit(const float* y, const float* z, const uint16_t* row, const int32_t* sec,
             const int32_t* hits, int n, bool first_is_outer, const orc_params& prm,
-            ThFn th, T p[5], T C[15], T& chi2, T* xlast = nullptr) {
+            ThFn th, T p[5], T C[15], T& chi2, T* xlast = nullptr, DispFn disp = DispFn()) {
     const Seed sd = make_seed(y, z, row, sec, hits, n, first_is_outer, prm);
     for (int i = 0; i < 5; ++i) p[i] = T(sd.p[i]);
     for (int i = 0; i < 15; ++i) C[i] = T(0.0);
@@ -384,6 +392,12 @@ bool kf_fit(const float* y, const float* z, const uint16_t* row, const int32_t* 
             xc = T(row_x(row[h]));
             yc = T((double)y[h]);
             zc = T((double)z[h]);
+        }
+        const T* d3 = disp(j);
+        if (d3) {
+            xc = xc + d3[0];
+            yc = yc + d3[1];
+            zc = zc + d3[2];
         }
         if (!move_state(x, p, frame, xc, sec[h], J, dX, prm)) return false;
         cov_transform(C, J);
@@ -1002,6 +1016,111 @@ int orc_fit_adjoint(const float* y, const float* z, const uint16_t* row, const i
         for (int t = 0; t < T; ++t)
             if (!tgrad[t].empty())
                 for (int i = 0; i < 216; ++i) grad[i] += tgrad[t][i];
+    }
+    return 0;
+}
+
+// ---- distortion map (Sec. 4.2: the TPC space-charge distortion evaluation)
+// The paper names the task and gives no method.  Reading: a piecewise-
+// constant displacement per voxel of the sector frames, added to the aligned
+// cluster position; its gradient is the exact derivative of the summed fit
+// chi2, the same quantity as the alignment gradient with the per-sector
+// parameters replaced by per-voxel ones.
+static bool grid_ok(const orc_field_grid* g) {
+    return g && g->n_band >= 1 && g->n_band <= NROW && NROW % g->n_band == 0 && g->n_y >= 1 &&
+           g->n_z >= 1 && (int64_t)NSEC * g->n_band * g->n_y * g->n_z < (int64_t)1 << 30;
+}
+
+// bin of an FP32 coordinate f (already scaled to bin units): clamped to
+// [0, nbin - 1]; NaN goes to bin 0
+static int clamp_bin(float f, int nbin) {
+    if (!(f >= 1.0f)) return 0;
+    if (f >= (float)nbin) return nbin - 1;
+    return (int)f;
+}
+
+static int32_t voxel_of(float y, float z, int r, int s, const orc_field_grid& g) {
+    const int band = r * g.n_band / NROW;
+    const float u = y / row_xf(r);
+    const int iy = clamp_bin((u - g.u_lo) * g.u_inv, g.n_y);
+    const int iz = clamp_bin(std::fabs(z) * g.z_inv, g.n_z);
+    return ((s * g.n_band + band) * g.n_y + iy) * g.n_z + iz;
+}
+
+int64_t orc_voxel_of(const float* y, const float* z, const uint16_t* row, const int32_t* sec,
+                     int64_t n, const orc_field_grid* grid, int32_t* vox) {
+    if (!grid_ok(grid)) return -1;
+    for (int64_t i = 0; i < n; ++i) vox[i] = voxel_of(y[i], z[i], row[i], sec[i], *grid);
+    return (int64_t)NSEC * grid->n_band * grid->n_y * grid->n_z;
+}
+
+// eight voxels (3 components each) carry dual parts per pass
+constexpr int NVP = ND / 3;
+
+int orc_field_adjoint(const float* y, const float* z, const uint16_t* row, const int32_t* sec,
+                      const int32_t* trk_off, const int32_t* trk_hits, int32_t T,
+                      const double* align, const orc_field_grid* grid, const double* field,
+                      const orc_params* prm, double* chi2_total, double* grad_field) {
+    if (!grid_ok(grid)) return -1;
+    const int64_t NV = (int64_t)NSEC * grid->n_band * grid->n_y * grid->n_z;
+    const int nt = orc_get_threads();
+    std::vector<double> tchi2(T, 0.0);
+    // per track: (voxel, d chi2 / d field[voxel][0..2]) of its touched voxels
+    std::vector<std::vector<std::pair<int32_t, std::array<double, 3>>>> tgrad(grad_field ? T : 0);
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nt)
+    for (int t = 0; t < T; ++t) {
+        const int n = trk_off[t + 1] - trk_off[t];
+        const int32_t* hits = trk_hits + trk_off[t];
+        if (n < 3) continue;
+        std::vector<int32_t> vox(n);
+        for (int j = 0; j < n; ++j) vox[j] = voxel_of(y[hits[j]], z[hits[j]], row[hits[j]], sec[hits[j]], *grid);
+        if (!grad_field) {
+            double p[5], C[15], chi2;
+            auto th = [&](int h) -> const double* { return align ? align + 6 * sec[h] : nullptr; };
+            auto disp = [&](int j) -> const double* { return field + 3 * (int64_t)vox[j]; };
+            if (kf_fit<double>(y, z, row, sec, hits, n, true, *prm, th, p, C, chi2, nullptr, disp))
+                tchi2[t] = chi2;
+            continue;
+        }
+        std::vector<int32_t> touched;
+        for (int j = 0; j < n; ++j)
+            if (std::find(touched.begin(), touched.end(), vox[j]) == touched.end()) touched.push_back(vox[j]);
+        std::vector<std::pair<int32_t, std::array<double, 3>>> g;
+        std::vector<D24> th(align ? 36 * 6 : 0);
+        for (size_t i = 0; i < th.size(); ++i) th[i] = D24(align[i]);
+        bool ok = true;
+        double chi2v = 0.0;
+        for (size_t base = 0; base < touched.size() && ok; base += NVP) {
+            std::vector<D24> d(3 * (size_t)n);
+            for (int j = 0; j < n; ++j) {
+                for (int c = 0; c < 3; ++c) d[3 * j + c] = D24(field[3 * (int64_t)vox[j] + c]);
+                for (size_t k = base; k < touched.size() && k < base + NVP; ++k)
+                    if (touched[k] == vox[j])
+                        for (int c = 0; c < 3; ++c) d[3 * j + c].d[(k - base) * 3 + c] = 1.0;
+            }
+            D24 p[5], C[15], chi2;
+            auto thf = [&](int h) -> const D24* { return align ? th.data() + 6 * sec[h] : nullptr; };
+            auto disp = [&](int j) -> const D24* { return d.data() + 3 * j; };
+            ok = kf_fit<D24>(y, z, row, sec, hits, n, true, *prm, thf, p, C, chi2, nullptr, disp);
+            if (!ok) break;
+            chi2v = chi2.v;
+            for (size_t k = base; k < touched.size() && k < base + NVP; ++k)
+                g.push_back({touched[k], {chi2.d[(k - base) * 3 + 0], chi2.d[(k - base) * 3 + 1],
+                                          chi2.d[(k - base) * 3 + 2]}});
+        }
+        if (ok) {
+            tchi2[t] = chi2v;
+            tgrad[t] = std::move(g);
+        }
+    }
+    double tot = 0.0;
+    for (int t = 0; t < T; ++t) tot += tchi2[t];
+    *chi2_total = tot;
+    if (grad_field) {
+        for (int64_t i = 0; i < 3 * NV; ++i) grad_field[i] = 0.0;
+        for (int t = 0; t < T; ++t)
+            for (const auto& e : tgrad[t])
+                for (int c = 0; c < 3; ++c) grad_field[3 * (int64_t)e.first + c] += e.second[c];
     }
     return 0;
 }

@@ -128,6 +128,41 @@ int64_t orc_bruteforce_chains(const float* y, const float* z, const uint16_t* ro
                               int64_t cap_hits, int32_t* out_off,
                               int32_t* out_hits);
 
+/* Distortion map: a displacement field over voxels of the sector frames,
+ * the quantity the online TPC space-charge distortion evaluation estimates
+ * (Sec. 4.2, "Processing and calibration"; the paper gives no method).  The
+ * reading: a piecewise-constant 3-d displacement per voxel, added to the
+ * (aligned) cluster position, estimated by minimising the summed track chi2.
+ * A cluster of sector s on pad row r at local (y, z) lies in voxel
+ *   v = ((s n_band + band) n_y + iy) n_z + iz,   band = r n_band / 152,
+ *   iy = clamp(floor((y / x_r - u_lo) u_inv), 0, n_y - 1),
+ *   iz = clamp(floor(|z| z_inv), 0, n_z - 1),
+ * the quotient, the difference and both products each rounded to FP32
+ * (x_r the pad-row plane position rounded to FP32), so that membership is
+ * an exact function of the measured cluster. */
+typedef struct {
+    int32_t n_band, n_y, n_z;   /* row bands (divide 152 rows), y/x bins, |z| bins */
+    float u_lo, u_inv;          /* y/x bins: lower edge and inverse width          */
+    float z_inv;                /* |z| bins: inverse width (cm^-1)                 */
+} orc_field_grid;
+
+/* Voxel of each cluster (vox[n]); returns the number of voxels,
+ * 36 n_band n_y n_z, or -1 for an invalid grid. */
+int64_t orc_voxel_of(const float* y, const float* z, const uint16_t* row,
+                     const int32_t* sector_of, int64_t n, const orc_field_grid* grid,
+                     int32_t* vox);
+
+/* Summed fit chi2 with the corrected positions R (x_r, y, z) + D + field[v]
+ * (align[216] as in orc_fit_adjoint, may be NULL = none; field[3 v + c],
+ * c = x, y, z in the sector frame) and, if grad_field is not NULL, its exact
+ * derivative d chi2 / d field (forward-mode dual numbers, eight voxels of a
+ * track per pass).  Returns 0, or -1 for an invalid grid. */
+int orc_field_adjoint(const float* y, const float* z, const uint16_t* row,
+                      const int32_t* sector_of, const int32_t* trk_off,
+                      const int32_t* trk_hits, int32_t n_tracks, const double* align,
+                      const orc_field_grid* grid, const double* field,
+                      const orc_params* prm, double* chi2_total, double* grad_field);
+
 /* Threads used by the OpenMP loops (0 = library default). */
 void orc_set_threads(int n);
 int orc_get_threads(void);

@@ -486,6 +486,25 @@ def draw_misalignment(seed=SEED_BASE + 4, shift_sigma=0.01, rot_sigma=1e-4):
     return m.reshape(-1)
 
 
+# Voxel grid of the distortion map (the build's reading of the space-charge
+# distortion map of Sec. 4.2; the paper gives no grid): 8 bands of 19 pad
+# rows, 4 bins of y/x over the sector acceptance, 5 bins of |z| over the
+# drift length.  Plain numbers; each side builds its own grid record.
+FIELD_GRID = dict(n_band=8, n_y=4, n_z=5, u_lo=-TAN_HALF_SECTOR,
+                  u_inv=4 / (2 * TAN_HALF_SECTOR), z_inv=5 / Z_MAX)
+
+
+def n_voxels(grid=FIELD_GRID):
+    return N_SECTORS * grid["n_band"] * grid["n_y"] * grid["n_z"]
+
+
+def draw_field(seed=SEED_BASE + 5, sigma=0.02, grid=FIELD_GRID):
+    """A random displacement field [n_voxels, 3]: each (x, y, z) component of
+    each voxel N(0, sigma) cm."""
+    rng = np.random.default_rng(seed + 5555)
+    return rng.normal(0.0, sigma, (n_voxels(grid), 3))
+
+
 def alignment_sample(n_tracks=200000, seed=SEED_BASE + 4, misalign=None,
                      n_events=1):
     """pT > 1 GeV/c tracks, no noise, clusters on misaligned row planes."""

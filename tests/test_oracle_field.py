@@ -1,0 +1,138 @@
+"""Pins of the oracle's distortion-map gradient: the TPC space-charge
+distortion evaluation (Sec. 4.2) read as a piecewise-constant displacement
+per voxel of the sector frames, estimated from the summed track chi2.
+
+* Voxel membership: every index is in range and names the cluster's sector
+  and pad-row band; a cluster well inside a bin (y/x and |z| at least 1% of
+  a bin width from its edges, beyond any FP32 rounding) lies in the bin that
+  contains it in exact arithmetic; coordinates beyond the grid go to the
+  edge bins.
+* A field constant over each sector is a rigid translation of that sector:
+  its chi2 equals the alignment chi2 with the same shifts and no rotation,
+  bit for bit (the two corrected positions are the same FP64 numbers), and
+  the field gradient summed over a sector's voxels equals the alignment
+  gradient's shift components (the alignment gradient is itself pinned to
+  finite differences).
+* FP64 central finite differences of the summed chi2 with respect to
+  sampled voxel components (h = 1e-6 cm).
+* Voxels without clusters have zero gradient; a zero field gives the plain
+  fit sum; a rigid alignment and a field combine.
+"""
+import numpy as np
+import pytest
+
+from paper_2412_13755_gb300 import synth
+
+G = synth.FIELD_GRID
+
+
+@pytest.fixture(scope="module")
+def grid(orc):
+    return orc.field_grid(**G)
+
+
+def _sample(n_tracks=150, seed=41):
+    ev = synth.alignment_sample(n_tracks=n_tracks, seed=seed, misalign=np.zeros(216))
+    off, hits, _ = ev.truth_tracks(n_min=10)
+    return ev, ev.sector_of_cluster(), off, hits
+
+
+def test_voxel_membership(orc, grid):
+    ev = synth.central_event(n_tracks=2000, seed=42)
+    sec = ev.sector_of_cluster()
+    vox, nv = orc.voxel_of(ev.y, ev.z, ev.row, sec, grid)
+    nb, ny, nz = G["n_band"], G["n_y"], G["n_z"]
+    assert nv == 36 * nb * ny * nz
+    assert vox.min() >= 0 and vox.max() < nv
+    iz = vox % nz
+    iy = (vox // nz) % ny
+    band = (vox // (nz * ny)) % nb
+    s = vox // (nz * ny * nb)
+    assert np.array_equal(s, sec)
+    assert np.array_equal(band, ev.row.astype(np.int64) // (152 // nb))
+    # exact-arithmetic bins of the clusters well inside one
+    x = synth.ROW_X[ev.row]
+    fy = (ev.y.astype(np.float64) / x - G["u_lo"]) * G["u_inv"]
+    fz = np.abs(ev.z.astype(np.float64)) * G["z_inv"]
+    inside = (np.abs(fy - np.floor(fy) - 0.5) < 0.49) & (np.abs(fz - np.floor(fz) - 0.5) < 0.49)
+    inside &= (fy > 0) & (fy < ny) & (fz < nz)
+    assert inside.mean() > 0.9
+    assert np.array_equal(iy[inside], np.floor(fy[inside]).astype(np.int64))
+    assert np.array_equal(iz[inside], np.floor(fz[inside]).astype(np.int64))
+
+
+def test_out_of_range_coordinates_go_to_the_edge_bins(orc, grid):
+    row = np.array([0, 151, 75, 75, 10, 10], np.uint16)
+    x = synth.ROW_X[row]
+    y = np.array([-2.0, 2.0, 0.0, 0.0, np.nan, 0.0]) * x
+    z = np.array([0.0, 1e4, -1e4, 0.0, 0.0, np.inf])
+    sec = np.array([0, 35, 17, 18, 3, 3], np.int32)
+    vox, _ = orc.voxel_of(y.astype(np.float32), z.astype(np.float32), row, sec, grid)
+    ny, nz = G["n_y"], G["n_z"]
+    iz, iy = vox % nz, (vox // nz) % ny
+    assert list(iy[:2]) == [0, ny - 1] and list(iz[1:3]) == [nz - 1, nz - 1]
+    assert iy[4] == 0 and iz[5] == nz - 1
+
+
+def test_constant_field_is_a_rigid_translation(orc, grid):
+    ev, sec, off, hits = _sample()
+    rng = np.random.default_rng(5)
+    shift = rng.normal(0.0, 0.02, (36, 3))
+    align = np.zeros((36, 6))
+    align[:, :3] = shift
+    nv = synth.n_voxels()
+    field = np.repeat(shift, nv // 36, axis=0)
+    c_f, g_f = orc.field_adjoint(ev.y, ev.z, ev.row, sec, off, hits, grid, field)
+    c_a, g_a = orc.fit_adjoint(ev.y, ev.z, ev.row, sec, off, hits, align.reshape(-1))
+    assert c_f == c_a
+    per_sector = g_f.reshape(36, nv // 36, 3).sum(axis=1)
+    want = g_a.reshape(36, 6)[:, :3]
+    np.testing.assert_allclose(per_sector, want, rtol=1e-9, atol=1e-9 * np.abs(want).max())
+    assert np.abs(want).max() > 1.0
+
+
+def test_gradient_matches_central_differences(orc, grid):
+    ev, sec, off, hits = _sample(n_tracks=120, seed=43)
+    field = synth.draw_field(seed=43, sigma=0.02)
+    c, g = orc.field_adjoint(ev.y, ev.z, ev.row, sec, off, hits, grid, field)
+    vox, nv = orc.voxel_of(ev.y, ev.z, ev.row, sec, grid)
+    used = np.unique(vox[hits])
+    rng = np.random.default_rng(6)
+    pick = [(int(v), int(c_)) for v in rng.choice(used, 24, replace=False) for c_ in range(3)]
+    h = 1e-6
+    scale = np.abs(g).max()
+    assert scale > 1.0
+    for v, k in pick:
+        fp, fm = field.copy(), field.copy()
+        fp[v, k] += h
+        fm[v, k] -= h
+        cp = orc.field_adjoint(ev.y, ev.z, ev.row, sec, off, hits, grid, fp, want_grad=False)
+        cm = orc.field_adjoint(ev.y, ev.z, ev.row, sec, off, hits, grid, fm, want_grad=False)
+        fd = (cp - cm) / (2 * h)
+        assert abs(g[v, k] - fd) <= 1e-6 * abs(fd) + 1e-6 * scale, (v, k, g[v, k], fd)
+
+
+def test_empty_voxels_zero_field_and_combination(orc, grid):
+    ev, sec, off, hits = _sample(n_tracks=100, seed=44)
+    nv = synth.n_voxels()
+    vox, _ = orc.voxel_of(ev.y, ev.z, ev.row, sec, grid)
+    empty = np.setdiff1d(np.arange(nv), vox[hits])
+    field = synth.draw_field(seed=44)
+    c, g = orc.field_adjoint(ev.y, ev.z, ev.row, sec, off, hits, grid, field)
+    assert len(empty) > 0 and np.all(g[empty] == 0.0)
+    # zero field: the plain fit sum
+    c0 = orc.field_adjoint(ev.y, ev.z, ev.row, sec, off, hits, grid, np.zeros((nv, 3)), want_grad=False)
+    par, cov, c2, ndf = orc.fit_tracks(ev.y, ev.z, ev.row, sec, off, hits)
+    assert c0 == c2[ndf > 0].sum() or abs(c0 - c2[ndf > 0].sum()) <= 1e-12 * c0
+    # alignment and field together: a sector's rigid shift moves into the
+    # field without changing chi2
+    mis = synth.draw_misalignment(44)
+    al = mis.copy().reshape(36, 6)
+    moved = al[:, :3].copy()
+    al[:, :3] = 0.0
+    f2 = field + np.repeat(moved, nv // 36, axis=0)
+    c_both = orc.field_adjoint(ev.y, ev.z, ev.row, sec, off, hits, grid, field, align=mis,
+                               want_grad=False)
+    c_moved = orc.field_adjoint(ev.y, ev.z, ev.row, sec, off, hits, grid, f2, align=al.reshape(-1),
+                                want_grad=False)
+    assert abs(c_both - c_moved) <= 1e-9 * c_both
