@@ -186,6 +186,43 @@ tpc_status tpc_fit_adjoint(tpc_ctx* ctx, const int32_t* trk_off, const int32_t* 
                            int32_t n_tracks, const double* align, double* chi2_total,
                            double* grad, tpc_stream_t stream);
 
+/* Distortion map: the online TPC space-charge distortion evaluation
+ * (Sec. 4.2, "Processing and calibration"; the paper gives no method), read
+ * as a piecewise-constant 3-d displacement per voxel of the sector frames,
+ * added to the aligned cluster position and estimated from the summed track
+ * chi2.  A cluster of sector s on pad row r at local (y, z) lies in voxel
+ *   v = ((s n_band + band) n_y + iy) n_z + iz,   band = r n_band / 152,
+ *   iy = clamp(floor((y / x_r - u_lo) u_inv), 0, n_y - 1),
+ *   iz = clamp(floor(|z| z_inv), 0, n_z - 1),
+ * with the quotient, the difference and both products each rounded to FP32
+ * (x_r the pad-row plane position rounded to FP32; NaN goes to bin 0). */
+typedef struct {
+    int32_t n_band;  /* pad-row bands, a divisor of 152                  */
+    int32_t n_y;     /* bins of y / x_r                                  */
+    int32_t n_z;     /* bins of |z|                                      */
+    float u_lo;      /* lower edge of the y / x_r bins                   */
+    float u_inv;     /* inverse width of the y / x_r bins                */
+    float z_inv;     /* inverse width of the |z| bins (cm^-1)            */
+} tpc_field_grid;
+
+/* Host: number of voxels, 36 n_band n_y n_z, or -1 for an invalid grid
+ * (NULL, a non-positive count, n_band not dividing 152, 2^26 voxels or more). */
+int64_t tpc_field_voxels(const tpc_field_grid* grid);
+
+/* S6 with a displacement field: as tpc_fit_adjoint, with the corrected
+ * position R (x_r, y, z) + (dx, dy, dz) + field[v] (align[216] device FP64,
+ * all zeros for no rigid correction; field[3 v + c] device FP64, c = x, y, z
+ * in the sector frame).  chi2_total[1] receives the summed chi2; if not NULL,
+ * grad_align[216] receives its derivative with respect to align and
+ * grad_field[3 n_vox] its derivative with respect to the field (exact
+ * reverse sweep; voxels without clusters get 0).  Returns TPC_ERR_ARG for
+ * an invalid grid or a NULL align, field or chi2_total. */
+tpc_status tpc_fit_adjoint_field(tpc_ctx* ctx, const int32_t* trk_off, const int32_t* trk_hits,
+                                 int32_t n_tracks, const double* align,
+                                 const tpc_field_grid* grid, const double* field,
+                                 double* chi2_total, double* grad_align, double* grad_field,
+                                 tpc_stream_t stream);
+
 /* Reads the device status word and counters of the last calls (synchronises
  * the stream) into *out (may be NULL) and returns the status.  buf (host, may
  * be NULL) receives a one-line description. */

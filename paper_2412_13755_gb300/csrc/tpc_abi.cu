@@ -293,6 +293,30 @@ tpc_status tpc_fit_adjoint(tpc_ctx* c, const int32_t* trk_off, const int32_t* tr
     return TPC_OK;
 }
 
+int64_t tpc_field_voxels(const tpc_field_grid* g) {
+    if (!g || g->n_band < 1 || g->n_band > NROW || NROW % g->n_band != 0 || g->n_y < 1 ||
+        g->n_z < 1 || g->n_y >= (1 << 26) || g->n_z >= (1 << 26))
+        return -1;
+    const int64_t nv = (int64_t)NSEC * g->n_band * g->n_y * g->n_z;
+    return nv < ((int64_t)1 << 26) ? nv : -1;
+}
+
+tpc_status tpc_fit_adjoint_field(tpc_ctx* c, const int32_t* trk_off, const int32_t* trk_hits,
+                                 int32_t n_tracks, const double* align, const tpc_field_grid* grid,
+                                 const double* field, double* chi2_total, double* grad_align,
+                                 double* grad_field, tpc_stream_t stream) {
+    if (!c) return TPC_ERR_ARG;
+    if (!c->have_ws || !c->have_clusters) return fail(c, TPC_ERR_STATE, "no workspace or clusters");
+    if (n_tracks < 0 || !align || !field || !chi2_total || (n_tracks > 0 && (!trk_off || !trk_hits)) ||
+        tpc_field_voxels(grid) < 0)
+        return fail(c, TPC_ERR_ARG, "tpc_fit_adjoint_field: bad argument");
+    const FieldGridD fg{grid->n_band, grid->n_y, grid->n_z, grid->u_lo, grid->u_inv, grid->z_inv};
+    cudaError_t e = run_adjoint_field(c, trk_off, trk_hits, n_tracks, align, fg, field, chi2_total,
+                                      grad_align, grad_field, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "tpc_fit_adjoint_field");
+    return TPC_OK;
+}
+
 tpc_status tpc_set_tune(tpc_ctx* c, const tpc_tune* t) {
     if (!c) return TPC_ERR_ARG;
     if (!t) {

@@ -13,6 +13,13 @@
 // plane positions come from a forward-mode evaluation of the transport with
 // six tangent directions.  Per-track partials (FP32) are reduced across
 // tracks in FP64 (shared-memory block sums, then global atomics).
+//
+// Distortion map (the online space-charge distortion evaluation of Sec. 4.2,
+// read as a piecewise-constant displacement per voxel of the sector frames):
+// the same kernel, instantiated with a field, adds field[v] to each corrected
+// cluster and scatters the cluster's position adjoint into the gradient of
+// its voxel.  A track's consecutive clusters mostly share a voxel, so each
+// lane sums a run in registers and flushes it with three FP64 atomics.
 #include <algorithm>
 
 #include "tpc_dev.cuh"
@@ -283,11 +290,32 @@ __device__ __forceinline__ void rot_grad_tab(const float* o, float xr, float y, 
     }
 }
 
+// the displacement of the cluster's voxel added to its corrected position;
+// returns the voxel
+__device__ __forceinline__ int add_field(const double* __restrict__ field, const FieldGridD& fg,
+                                         const Geo* __restrict__ geo, int r, int sec, float y, float z,
+                                         double& xc, float& yc, float& zc) {
+    const int v = field_voxel(y, z, r, NROW, geo->row_xf[r], sec, fg);
+    const double* f = field + 3 * (int64_t)v;
+    xc += f[0];
+    yc = yc + (float)f[1];
+    zc = zc + (float)f[2];
+    return v;
+}
+
+__device__ __forceinline__ void flush_field(double* grad_field, int v, double acc[3]) {
+    if (v >= 0)
+        for (int i = 0; i < 3; ++i) atomicAdd(&grad_field[3 * (int64_t)v + i], acc[i]);
+    acc[0] = acc[1] = acc[2] = 0.0;
+}
+
+template <bool FIELD>
 __global__ void __launch_bounds__(128) k_adjoint(
     const int32_t* __restrict__ trk_off, const int32_t* __restrict__ trk_hits, int32_t T,
     const float* __restrict__ yin, const float* __restrict__ zin, const uint16_t* __restrict__ row,
     const int64_t* __restrict__ evt_off, int G, const float* __restrict__ rot_tab,
-    const Geo* __restrict__ geo, AdjPrm P, double* chi2_total, double* grad, int32_t* st) {
+    const Geo* __restrict__ geo, AdjPrm P, double* chi2_total, double* grad, int32_t* st,
+    const double* __restrict__ field, FieldGridD fg, double* grad_field) {
     __shared__ double sg[216];
     __shared__ double schi2;
     __shared__ float tab[NSEC * ROT_TAB];
@@ -342,6 +370,7 @@ __global__ void __launch_bounds__(128) k_adjoint(
             double xc;
             float yc, zc;
             corr_tab(tab + sec * ROT_TAB, geo->row_xd[row[c]], yin[c], zin[c], xc, yc, zc);
+            if constexpr (FIELD) add_field(field, fg, geo, row[c], sec, yin[c], zin[c], xc, yc, zc);
             MoveJ mj;
             ok = kf_move<float>(s, xc, sec, geo, P.kb, P.snp_max, &mj);
             if (ok) chi2.add(kf_update(s, yc, zc, P.sy2, P.sz2, P.fp64_ratio, P.fp64_det, nullptr, &mj));
@@ -358,6 +387,8 @@ __global__ void __launch_bounds__(128) k_adjoint(
         double slot_g[NSLOT][6];
         int nslot = 0;
         float xbar_from_next = 0.f;  // x_from adjoint of the step after the current one
+        int vcur = -1;               // voxel of the run of clusters being summed
+        double facc[3] = {0.0, 0.0, 0.0};
         Pre seg[CK];
         for (int k = nck - 1; k >= 0; --k) {
             const int j0 = k * CK, j1 = min(n, j0 + CK);
@@ -383,6 +414,7 @@ __global__ void __launch_bounds__(128) k_adjoint(
                 double xc;
                 float yc, zc;
                 corr_tab(tab + sec * ROT_TAB, geo->row_xd[row[c]], yin[c], zin[c], xc, yc, zc);
+                if constexpr (FIELD) add_field(field, fg, geo, row[c], sec, yin[c], zin[c], xc, yc, zc);
                 MoveJ mj;
                 kf_move<float>(r, xc, sec, geo, P.kb, P.snp_max, &mj);
                 kf_update(r, yc, zc, P.sy2, P.sz2, P.fp64_ratio, P.fp64_det, nullptr, &mj);
@@ -401,6 +433,8 @@ __global__ void __launch_bounds__(128) k_adjoint(
                 double xc;
                 float yc, zc;
                 corr_tab(tb, xr, yin[c], zin[c], xc, yc, zc);
+                int vox = -1;
+                if constexpr (FIELD) vox = add_field(field, fg, geo, row[c], sec, yin[c], zin[c], xc, yc, zc);
                 // forward of this step again: transport, then update pieces
                 KF m;
                 m.x = q.x; m.frame = q.frame;
@@ -587,13 +621,27 @@ __global__ void __launch_bounds__(128) k_adjoint(
                     slot_g[sl][4] += gr[1];
                     slot_g[sl][5] += gr[2];
                 }
+                if constexpr (FIELD) {
+                    if (grad_field) {
+                        if (vox != vcur) {
+                            flush_field(grad_field, vcur, facc);
+                            vcur = vox;
+                        }
+                        facc[0] += xb;
+                        facc[1] += ybar;
+                        facc[2] += zbar;
+                    }
+                }
             }
+        }
+        if constexpr (FIELD) {
+            if (grad_field) flush_field(grad_field, vcur, facc);
         }
         for (int sl = 0; sl < nslot; ++sl)
             for (int i = 0; i < 6; ++i) atomicAdd(&sg[slot_sec[sl] * 6 + i], slot_g[sl][i]);
     }
     __syncthreads();
-    if (P.want_grad)
+    if (P.want_grad && (!FIELD || grad != nullptr))
         for (int i = threadIdx.x; i < 216; i += blockDim.x)
             if (sg[i] != 0.0) atomicAdd(&grad[i], sg[i]);
     if (threadIdx.x == 0) atomicAdd(chi2_total, schi2);
@@ -605,10 +653,8 @@ __global__ void k_zero_f64(double* p, int n) {
 
 }  // namespace
 
-cudaError_t run_adjoint(tpc_ctx* c, const int32_t* trk_off, const int32_t* trk_hits,
-                        int32_t n_tracks, const double* align, double* chi2_total, double* grad,
-                        cudaStream_t s) {
-    const tpc_params& p = c->prm;
+namespace {
+AdjPrm adj_prm(const tpc_params& p, bool want_grad) {
     AdjPrm ap;
     ap.sy2 = p.sigma_y2;
     ap.sz2 = p.sigma_z2;
@@ -620,7 +666,15 @@ cudaError_t run_adjoint(tpc_ctx* c, const int32_t* trk_off, const int32_t* trk_h
     ap.seed_snp = p.seed_snp_max;
     ap.seed_qpt = p.seed_qpt_max;
     for (int i = 0; i < 5; ++i) ap.prior[i] = p.prior[i];
-    ap.want_grad = grad != nullptr;
+    ap.want_grad = want_grad;
+    return ap;
+}
+}  // namespace
+
+cudaError_t run_adjoint(tpc_ctx* c, const int32_t* trk_off, const int32_t* trk_hits,
+                        int32_t n_tracks, const double* align, double* chi2_total, double* grad,
+                        cudaStream_t s) {
+    const AdjPrm ap = adj_prm(c->prm, grad != nullptr);
     c->mark(12, s);
     tpc::LaunchCount{}, k_zero_f64<<<1, 32, 0, s>>>(chi2_total, 1);
     if (grad) tpc::LaunchCount{}, k_zero_f64<<<1, 256, 0, s>>>(grad, 216);
@@ -628,10 +682,37 @@ cudaError_t run_adjoint(tpc_ctx* c, const int32_t* trk_off, const int32_t* trk_h
         float* rot_tab = c->ws.at<float>(c->ws.L.adj_rot);
         tpc::LaunchCount{}, k_adj_tables<<<1, 64, 0, s>>>(align, rot_tab);
         const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((n_tracks + 127) / 128, 152 * 4));
-        tpc::LaunchCount{}, k_adjoint<<<(unsigned)blocks, 128, 0, s>>>(trk_off, trk_hits, n_tracks, c->y, c->z, c->row,
+        tpc::LaunchCount{}, k_adjoint<false><<<(unsigned)blocks, 128, 0, s>>>(trk_off, trk_hits, n_tracks, c->y, c->z, c->row,
                                                    c->evt_sector_off, c->n_events * NSEC, rot_tab,
                                                    c->ws.at<Geo>(c->ws.L.geo), ap, chi2_total, grad,
-                                                   c->ws.at<int32_t>(c->ws.L.status));
+                                                   c->ws.at<int32_t>(c->ws.L.status),
+                                                   nullptr, FieldGridD{}, nullptr);
+    }
+    c->mark(13, s);
+    return cudaGetLastError();
+}
+
+cudaError_t run_adjoint_field(tpc_ctx* c, const int32_t* trk_off, const int32_t* trk_hits,
+                              int32_t n_tracks, const double* align, const FieldGridD& fg,
+                              const double* field, double* chi2_total, double* grad_align,
+                              double* grad_field, cudaStream_t s) {
+    const AdjPrm ap = adj_prm(c->prm, grad_align != nullptr || grad_field != nullptr);
+    const int64_t nv = (int64_t)NSEC * fg.n_band * fg.n_y * fg.n_z;
+    c->mark(12, s);
+    tpc::LaunchCount{}, k_zero_f64<<<1, 32, 0, s>>>(chi2_total, 1);
+    if (grad_align) tpc::LaunchCount{}, k_zero_f64<<<1, 256, 0, s>>>(grad_align, 216);
+    if (grad_field) {
+        const cudaError_t e = cudaMemsetAsync(grad_field, 0, (size_t)(3 * nv) * sizeof(double), s);
+        if (e != cudaSuccess) return e;
+    }
+    if (n_tracks > 0) {
+        float* rot_tab = c->ws.at<float>(c->ws.L.adj_rot);
+        tpc::LaunchCount{}, k_adj_tables<<<1, 64, 0, s>>>(align, rot_tab);
+        const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((n_tracks + 127) / 128, 152 * 4));
+        tpc::LaunchCount{}, k_adjoint<true><<<(unsigned)blocks, 128, 0, s>>>(
+            trk_off, trk_hits, n_tracks, c->y, c->z, c->row, c->evt_sector_off, c->n_events * NSEC,
+            rot_tab, c->ws.at<Geo>(c->ws.L.geo), ap, chi2_total, grad_align,
+            c->ws.at<int32_t>(c->ws.L.status), field, fg, grad_field);
     }
     c->mark(13, s);
     return cudaGetLastError();

@@ -144,4 +144,32 @@ TPC_HD void mask_set(uint32_t (&m)[MASK_W], int r) {
     for (int w = 0; w < MASK_W; ++w) m[w] |= wr == w ? bit : 0u;
 }
 
+// ---- distortion map voxels
+
+// Voxel grid of a displacement field over the sector frames (the C ABI's
+// tpc_field_grid).
+struct FieldGridD {
+    int n_band, n_y, n_z;
+    float u_lo, u_inv, z_inv;
+};
+
+// bin of an FP32 coordinate already scaled to bin units, clamped to
+// [0, nbin - 1] (NaN to 0)
+TPC_HD int field_bin(float f, int nbin) {
+    if (!(f >= 1.0f)) return 0;
+    if (f >= (float)nbin) return nbin - 1;
+    return (int)f;
+}
+
+// voxel of a cluster of sector sec on pad row r of n_rows (plane position
+// rounded to FP32: xr) at local (y, z): the quotient y / xr, the difference
+// and both products each rounded once
+TPC_HD int field_voxel(float y, float z, int r, int n_rows, float xr, int sec, const FieldGridD& g) {
+    const int band = r * g.n_band / n_rows;
+    const float u = bits::div(y, xr);
+    const int iy = field_bin(bits::mul(bits::sub(u, g.u_lo), g.u_inv), g.n_y);
+    const int iz = field_bin(bits::mul(fabsf(z), g.z_inv), g.n_z);
+    return ((sec * g.n_band + band) * g.n_y + iy) * g.n_z + iz;
+}
+
 }  // namespace tpc

@@ -8,6 +8,7 @@
 #include <string>
 
 #include "../../include/tpc_track.h"
+#include "tpc_bits.cuh"
 
 namespace tpc {
 
@@ -116,6 +117,10 @@ cudaError_t run_fit(tpc_ctx* c, const int32_t* trk_off, const int32_t* trk_hits,
 cudaError_t run_adjoint(tpc_ctx* c, const int32_t* trk_off, const int32_t* trk_hits,
                         int32_t n_tracks, const double* align, double* chi2_total, double* grad,
                         cudaStream_t s);
+cudaError_t run_adjoint_field(tpc_ctx* c, const int32_t* trk_off, const int32_t* trk_hits,
+                              int32_t n_tracks, const double* align, const FieldGridD& fg,
+                              const double* field, double* chi2_total, double* grad_align,
+                              double* grad_field, cudaStream_t s);
 cudaError_t fill_i32(int32_t* p, int64_t n, int32_t v, cudaStream_t s);
 // exclusive scan of in[0..L) into out[0..L] (out[L] = total); tmp from the workspace
 cudaError_t scan_i32(const int32_t* in, int32_t* out, int64_t L, int32_t* tmp, cudaStream_t s);

@@ -23,7 +23,7 @@ EXPORTS = ("tpc_default_params", "tpc_create", "tpc_destroy", "tpc_workspace_byt
            "tpc_set_workspace", "tpc_load_clusters", "tpc_find_tracks", "tpc_fit_tracks",
            "tpc_fit_adjoint", "tpc_get_stats", "tpc_last_error", "tpc_reset_status",
            "tpc_stage_timing", "tpc_stage_times", "tpc_find_tracks_noalloc", "tpc_set_tune",
-           "tpc_autotune")
+           "tpc_autotune", "tpc_field_voxels", "tpc_fit_adjoint_field")
 STAGE_NAMES = ("bin", "neighbours", "links", "chains", "tracklets", "select", "merge_cand",
                "match", "output", "fit", "adjoint", "find_total")
 
@@ -44,6 +44,16 @@ class Params(C.Structure):
 
 class Tune(C.Structure):
     _fields_ = [("lane_blocks_per_sm", C.c_int32), ("lane_tile", C.c_int32)]
+
+
+class FieldGrid(C.Structure):
+    """Voxel grid of a displacement field (tpc_field_grid)."""
+    _fields_ = [("n_band", C.c_int32), ("n_y", C.c_int32), ("n_z", C.c_int32),
+                ("u_lo", C.c_float), ("u_inv", C.c_float), ("z_inv", C.c_float)]
+
+
+def field_grid(n_band, n_y, n_z, u_lo, u_inv, z_inv) -> FieldGrid:
+    return FieldGrid(int(n_band), int(n_y), int(n_z), float(u_lo), float(u_inv), float(z_inv))
 
 
 class Stats(C.Structure):
@@ -94,9 +104,13 @@ def load_library(build_if_missing: bool = True):
     lib.tpc_set_tune.argtypes = [vp, vp]
     lib.tpc_autotune.argtypes = [vp, vp, vp, vp, vp, i32, vp, vp]
     lib.tpc_stage_times.argtypes = [vp, vp]
+    lib.tpc_field_voxels.argtypes = [vp]
+    lib.tpc_field_voxels.restype = i64
+    lib.tpc_fit_adjoint_field.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp, vp, vp, vp]
     for name in EXPORTS:
         f = getattr(lib, name)
-        if name not in ("tpc_default_params", "tpc_destroy", "tpc_workspace_bytes"):
+        if name not in ("tpc_default_params", "tpc_destroy", "tpc_workspace_bytes",
+                        "tpc_field_voxels"):
             f.restype = C.c_int
     _lib = lib
     return lib
@@ -266,6 +280,39 @@ def tpc_fit_adjoint(ctx, trk_off, trk_hits, n_tracks, align, chi2_total, grad=No
     _check(ctx, rc, "tpc_fit_adjoint")
 
 
+def tpc_field_voxels(grid: FieldGrid) -> int:
+    return int(load_library().tpc_field_voxels(C.byref(grid)))
+
+
+def check_field_buffers(n_voxels, field, grad_field, what="tpc_fit_adjoint_field"):
+    """tpc_fit_adjoint_field reads field[3 n_voxels] and writes, when given,
+    grad_field[3 n_voxels]."""
+    if n_voxels < 0:
+        raise ValueError(f"{what}: invalid field grid")
+    _need_len(field, 3 * n_voxels, "field", what)
+    if grad_field is not None:
+        _need_len(grad_field, 3 * n_voxels, "grad_field", what)
+
+
+def tpc_fit_adjoint_field(ctx, trk_off, trk_hits, n_tracks, align, grid: FieldGrid, field,
+                          chi2_total, grad_align=None, grad_field=None, stream=None):
+    _need(trk_off, torch.int32, "trk_off")
+    _need(trk_hits, torch.int32, "trk_hits")
+    _need(align, torch.float64, "align")
+    _need(field, torch.float64, "field")
+    _need(chi2_total, torch.float64, "chi2_total")
+    for t, n in ((grad_align, "grad_align"), (grad_field, "grad_field")):
+        if t is not None:
+            _need(t, torch.float64, n)
+    check_adjoint_buffers(n_tracks, trk_off, align, chi2_total, grad_align, "tpc_fit_adjoint_field")
+    check_field_buffers(tpc_field_voxels(grid), field, grad_field)
+    rc = load_library().tpc_fit_adjoint_field(ctx, _ptr(trk_off), _ptr(trk_hits), int(n_tracks),
+                                              _ptr(align), C.byref(grid), _ptr(field),
+                                              _ptr(chi2_total), _ptr(grad_align), _ptr(grad_field),
+                                              _stream(stream))
+    _check(ctx, rc, "tpc_fit_adjoint_field")
+
+
 def tpc_set_tune(ctx, tune: Tune | None):
     _check(ctx, load_library().tpc_set_tune(ctx, C.byref(tune) if tune is not None else None),
            "tpc_set_tune")
@@ -276,7 +323,7 @@ def tpc_autotune(ctx, track_of_cluster, trk_off, trk_hits, n_tracks_dev, stream=
                  (trk_hits, "trk_hits"), (n_tracks_dev, "n_tracks_dev")):
         _need(t, torch.int32, n)
     check_find_outputs(_loaded_n.get(ctx.value, 0), track_of_cluster, trk_off, trk_hits, n_tracks_dev,
-                       "tpc_autotune")
+                       "tpc_autotune", "tpc_field_voxels", "tpc_fit_adjoint_field")
     best = Tune()
     rc = load_library().tpc_autotune(ctx, _ptr(track_of_cluster), _ptr(trk_off), _ptr(trk_hits),
                                      _ptr(n_tracks_dev), trk_off.numel() - 1, C.byref(best),
@@ -372,6 +419,22 @@ class Tracker:
         grad = torch.zeros(216, dtype=torch.float64, device=self.device) if want_grad else None
         tpc_fit_adjoint(self.ctx, trk_off, trk_hits, n_tracks, align, chi2, grad, stream=stream)
         return chi2, grad
+
+    def adjoint_field(self, trk_off, trk_hits, n_tracks, grid: FieldGrid, field, align=None,
+                      want_grad=True, stream=None):
+        """Summed chi2 with the displacement field[n_voxels, 3] added to the
+        aligned clusters, and its gradients with respect to the alignment
+        and the field (None when want_grad is false)."""
+        dev = self.device
+        if align is None:
+            align = torch.zeros(216, dtype=torch.float64, device=dev)
+        chi2 = torch.zeros(1, dtype=torch.float64, device=dev)
+        nv = tpc_field_voxels(grid)
+        g_al = torch.zeros(216, dtype=torch.float64, device=dev) if want_grad else None
+        g_f = torch.zeros(max(nv, 0), 3, dtype=torch.float64, device=dev) if want_grad else None
+        tpc_fit_adjoint_field(self.ctx, trk_off, trk_hits, n_tracks, align, grid, field, chi2,
+                              g_al, g_f, stream=stream)
+        return chi2, g_al, g_f
 
     def stats(self, stream=None) -> Stats:
         return tpc_get_stats(self.ctx, stream)

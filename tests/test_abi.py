@@ -75,10 +75,24 @@ def test_struct_sizes_match_header(lib, tmp_path):
     inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
     src = tmp_path / "sizes.c"
     src.write_text('#include <stdio.h>\n#include "tpc_track.h"\n'
-                   'int main(void) { printf("%zu %zu %zu\\n", sizeof(tpc_params), sizeof(tpc_stats), '
-                   'sizeof(tpc_tune)); return 0; }\n')
+                   'int main(void) { printf("%zu %zu %zu %zu\\n", sizeof(tpc_params), sizeof(tpc_stats), '
+                   'sizeof(tpc_tune), sizeof(tpc_field_grid)); return 0; }\n')
     exe = tmp_path / "sizes"
     subprocess.run([cc, "-I", inc, str(src), "-o", str(exe)], check=True)
     sizes = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True,
                                             text=True).stdout.split()]
-    assert sizes == [C.sizeof(tpc.Params), C.sizeof(tpc.Stats), C.sizeof(tpc.Tune)]
+    assert sizes == [C.sizeof(tpc.Params), C.sizeof(tpc.Stats), C.sizeof(tpc.Tune),
+                     C.sizeof(tpc.FieldGrid)]
+
+
+def test_field_voxels(lib):
+    """The voxel count of a field grid, and the refusal of invalid grids (host
+    only; tpc_fit_adjoint_field refuses the same grids with TPC_ERR_ARG)."""
+    from paper_2412_13755_gb300 import synth, tpc
+    assert tpc.tpc_field_voxels(tpc.field_grid(**synth.FIELD_GRID)) == synth.n_voxels()
+    assert tpc.tpc_field_voxels(tpc.field_grid(1, 1, 1, 0, 1, 1)) == 36
+    assert tpc.tpc_field_voxels(tpc.field_grid(152, 2, 3, 0, 1, 1)) == 36 * 152 * 6
+    for bad in ((0, 1, 1), (5, 1, 1), (8, 0, 1), (8, 1, 0), (8, -3, 2), (152, 1 << 13, 1 << 13),
+                (8, 1 << 26, 1)):
+        assert tpc.tpc_field_voxels(tpc.field_grid(*bad, 0, 1, 1)) == -1, bad
+    assert lib.tpc_field_voxels(None) == -1

@@ -53,3 +53,16 @@ def test_adjoint_buffers():
                        ((i32(11), f64(216), f64(1), f64(215)), "grad")):
         with pytest.raises(ValueError, match=name):
             tpc.check_adjoint_buffers(10, *args)
+
+
+def test_field_buffers():
+    f64 = lambda *s: torch.empty(*s, dtype=torch.float64)  # noqa: E731
+    nv = 5760
+    tpc.check_field_buffers(nv, f64(nv, 3), None)
+    tpc.check_field_buffers(nv, f64(nv, 3), f64(nv, 3))
+    with pytest.raises(ValueError, match="field holds"):
+        tpc.check_field_buffers(nv, f64(nv - 1, 3), None)
+    with pytest.raises(ValueError, match="grad_field"):
+        tpc.check_field_buffers(nv, f64(nv, 3), f64(nv, 2))
+    with pytest.raises(ValueError, match="invalid field grid"):
+        tpc.check_field_buffers(-1, f64(nv, 3), None)
