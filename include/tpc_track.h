@@ -135,8 +135,14 @@ tpc_status tpc_set_workspace(tpc_ctx* ctx, void* dev_ptr, size_t bytes,
  * offsets evt_sector_off[n_events*36 + 1] (int64, non-decreasing, first 0,
  * last n).  The arrays are read by later calls, not copied: keep them alive
  * and unchanged until the last call that uses them.  Enqueues a validation
- * kernel (bad rows / non-finite coordinates -> TPC_ERR_INPUT in the status
- * word).  TPC_ERR_CAPACITY if n or n_events exceed the workspace. */
+ * kernel: a row >= 152, a non-finite coordinate or offsets that are not
+ * non-decreasing from 0 to n set TPC_ERR_INPUT in the status word (detail:
+ * the cluster index, or -1 / -2 / -3 for the first offset, the last offset,
+ * the order).  The find kernels are not guarded against such input and may
+ * access memory out of bounds on it: a caller that cannot vouch for its
+ * input reads the status (tpc_get_stats) after this call and before
+ * tpc_find_tracks.  TPC_ERR_CAPACITY if n or n_events exceed the
+ * workspace. */
 tpc_status tpc_load_clusters(tpc_ctx* ctx, const float* y, const float* z,
                              const uint16_t* row, const uint16_t* charge, int64_t n,
                              const int64_t* evt_sector_off, int32_t n_events,

@@ -227,6 +227,19 @@ def tpc_set_workspace(ctx, ws: torch.Tensor, max_clusters: int, max_events: int)
     _check(ctx, rc, "tpc_set_workspace")
 
 
+def check_load_inputs(y, z, row, charge, evt_sector_off, n_events, what="tpc_load_clusters"):
+    """tpc_load_clusters reads n = y.numel() entries of y, z, row (and
+    charge) and 36 n_events + 1 entries of evt_sector_off."""
+    n = y.numel()
+    _need_len(z, n, "z", what)
+    _need_len(row, n, "row", what)
+    if charge is not None:
+        _need_len(charge, n, "charge", what)
+    if int(n_events) < 1:
+        raise ValueError(f"{what}: n_events {int(n_events)} < 1")
+    _need_len(evt_sector_off, 36 * int(n_events) + 1, "evt_sector_off", what)
+
+
 def tpc_load_clusters(ctx, y, z, row, charge, evt_sector_off, n_events, stream=None):
     _need(y, torch.float32, "y")
     _need(z, torch.float32, "z")
@@ -234,6 +247,7 @@ def tpc_load_clusters(ctx, y, z, row, charge, evt_sector_off, n_events, stream=N
     if charge is not None:
         _need(charge, torch.uint16, "charge")
     _need(evt_sector_off, torch.int64, "evt_sector_off")
+    check_load_inputs(y, z, row, charge, evt_sector_off, n_events)
     rc = load_library().tpc_load_clusters(ctx, _ptr(y), _ptr(z), _ptr(row), _ptr(charge),
                                           y.numel(), _ptr(evt_sector_off), int(n_events),
                                           _stream(stream))
@@ -383,10 +397,16 @@ class Tracker:
         except Exception:
             pass
 
-    def load(self, y, z, row, evt_sector_off, n_events, charge=None, stream=None):
+    def load(self, y, z, row, evt_sector_off, n_events, charge=None, stream=None, validate=False):
+        """Registers a batch.  The library checks it on the device (rows,
+        finite coordinates, offsets) into the status word; with validate the
+        status is read here (a synchronisation) and a batch that fails is
+        refused before any find kernel could run on it."""
         self._inputs = (y, z, row, charge, evt_sector_off)  # keep alive
         tpc_load_clusters(self.ctx, y, z, row, charge, evt_sector_off, n_events, stream)
         self.n = y.numel()
+        if validate:
+            self.check(stream)
 
     def alloc_find_outputs(self, track_cap=None):
         """Outputs of find for the loaded batch; before a load, for the

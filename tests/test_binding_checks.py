@@ -66,3 +66,19 @@ def test_field_buffers():
         tpc.check_field_buffers(nv, f64(nv, 3), f64(nv, 2))
     with pytest.raises(ValueError, match="invalid field grid"):
         tpc.check_field_buffers(-1, f64(nv, 3), None)
+
+
+def test_load_inputs():
+    f32 = lambda n: torch.empty(n, dtype=torch.float32)  # noqa: E731
+    u16 = lambda n: torch.empty(n, dtype=torch.int16)  # noqa: E731  (size only)
+    i64 = lambda n: torch.empty(n, dtype=torch.int64)  # noqa: E731
+    n = 100
+    tpc.check_load_inputs(f32(n), f32(n), u16(n), None, i64(37), 1)
+    tpc.check_load_inputs(f32(n), f32(n), u16(n), u16(n), i64(73), 2)
+    for args, name in (((f32(n), f32(n - 1), u16(n), None, i64(37), 1), "z"),
+                       ((f32(n), f32(n), u16(n - 1), None, i64(37), 1), "row"),
+                       ((f32(n), f32(n), u16(n), u16(n - 1), i64(37), 1), "charge"),
+                       ((f32(n), f32(n), u16(n), None, i64(37), 2), "evt_sector_off"),
+                       ((f32(n), f32(n), u16(n), None, i64(37), 0), "n_events")):
+        with pytest.raises(ValueError, match=name):
+            tpc.check_load_inputs(*args)

@@ -1,0 +1,106 @@
+"""Failure detection, determinism and input-order checks on the GPU.
+
+* Malformed batches (a row >= 152, a non-finite coordinate, offsets that do
+  not run non-decreasing from 0 to n) are caught by the load's validation
+  kernel into the status word; with validate=True the binding refuses them
+  before any find kernel runs.  The validation kernel only reads the batch's
+  own n clusters and 36 n_events + 1 offsets, so no step of these cases
+  reads or writes out of bounds.  After a status reset the same context
+  tracks a valid batch.
+* Determinism: find + fit twice on the same batch give bitwise-equal
+  outputs.
+* Input order: a batch shuffled within each (event, sector) group agrees
+  with the oracle on the same shuffled batch (track identities are input
+  indices, so only tie-breaks may move).
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2412_13755_gb300 import synth, tpc  # noqa: E402
+from gpu_util import canon_of_cluster, gpu_find, to_dev  # noqa: E402
+
+
+def _malformed(ev):
+    """(name, y, z, row, off, details) of malformed copies of ev: the status
+    detail is one of details (the first check to fail sets it; a last offset
+    below n also breaks the order of the last two)."""
+    y, z, row, off = (a.copy() for a in (ev.y, ev.z, ev.row, ev.evt_sector_off))
+    k = ev.n // 3
+    r = row.copy()
+    r[k] = 152
+    yield "row", y, z, r, off, {k}
+    yy = y.copy()
+    yy[k + 1] = np.nan
+    yield "nan", yy, z, row, off, {k + 1}
+    zz = z.copy()
+    zz[k + 2] = np.inf
+    yield "inf", y, zz, row, off, {k + 2}
+    o = off.copy()
+    o[0] = 1
+    yield "first offset", y, z, row, o, {-1}
+    o = off.copy()
+    o[-1] = ev.n - 1
+    yield "last offset", y, z, row, o, {-2, -3}
+    o = off.copy()
+    o[5], o[6] = o[6] + 1, o[5]
+    yield "order", y, z, row, o, {-3}
+
+
+def test_malformed_batches_refused_before_find():
+    ev = synth.one_sector()
+    tr = tpc.Tracker(ev.n, 1)
+    for name, y, z, row, off, details in _malformed(ev):
+        d = (torch.from_numpy(y).cuda(), torch.from_numpy(z).cuda(),
+             torch.from_numpy(row.view(np.int16)).cuda().view(torch.uint16), torch.from_numpy(off).cuda())
+        with pytest.raises(tpc.TPCError, match="TPC_ERR_INPUT"):
+            tr.load(*d, 1, validate=True)
+        st = tr.stats()
+        assert st.status == tpc.TPC_ERR_INPUT and st.status_detail in details, (name, st.status_detail)
+        tr.reset_status()
+        assert tr.stats().status == tpc.TPC_OK
+    # the context still tracks a valid batch
+    d = to_dev(ev)
+    tr.load(*d, 1, validate=True)
+    out = tr.find()
+    torch.cuda.synchronize()
+    tr.check()
+    assert int(out[3].item()) > 100
+
+
+def test_find_and_fit_are_deterministic():
+    ev = synth.central_event(n_tracks=2000, seed=606)
+    runs = []
+    tr = tpc.Tracker(ev.n, 1)
+    d = to_dev(ev)
+    for _ in range(2):
+        tr.load(*d, 1)
+        toc, off, hits, nt = tr.find()
+        T = int(nt.item())
+        par, cov, chi2, ndf = tr.fit(off, hits, T, nt)
+        torch.cuda.synchronize()
+        tr.check()
+        runs.append([t.cpu().numpy() for t in (toc, off[:T + 1], hits[:int(off[T].item())], par, cov,
+                                              chi2, ndf)])
+    for a, b in zip(*runs):
+        assert np.array_equal(a, b)
+
+
+def test_shuffled_groups_agree_with_oracle(orc):
+    ev = synth.central_event(n_tracks=1500, seed=707)
+    rng = np.random.default_rng(708)
+    perm = np.concatenate([ev.evt_sector_off[g] + rng.permutation(ev.evt_sector_off[g + 1] - ev.evt_sector_off[g])
+                           for g in range(len(ev.evt_sector_off) - 1)])
+    sh = dataclasses.replace(ev, y=ev.y[perm], z=ev.z[perm], row=ev.row[perm], charge=ev.charge[perm],
+                             mc_track=ev.mc_track[perm])
+    g_toc, g_off, g_hits, st, _ = gpu_find(sh)
+    o_toc, o_off, o_hits = orc.find_tracks(sh.y, sh.z, sh.row, sh.evt_sector_off, sh.n_events)
+    gc = canon_of_cluster(g_toc, g_off, g_hits, sh.n)
+    oc = canon_of_cluster(o_toc, o_off, o_hits, sh.n)
+    agree = np.mean(gc == oc)
+    print(f"shuffled: agreement {agree:.6f}")
+    assert agree >= 0.9999
