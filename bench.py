@@ -39,6 +39,9 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x m
 # the whole find + fit path, every intermediate product written once and read
 # once: binning 22, neighbours 16, chains and tracks 16, fit 12.7, scatter 12
 PATH_BYTES_PER_CLUSTER = 78.7
+# the fused lower bound: read y, z, row once (10), write each cluster's track
+# (4) and the per-track fit outputs (88 B per ~120 clusters, 0.7)
+PATH_FUSED_BYTES_PER_CLUSTER = 14.7
 FIT_BYTES_PER_HIT = 14.0                # hit index (4) + y, z (8) + row (2)
 FIT_BYTES_PER_TRACK = 88.0              # 5 params + 15 cov + chi2 + ndf
 KF_FLOPS_PER_STEP = 350.0               # transport ~60 + covariance J C J^T ~160 + update ~130
@@ -619,6 +622,8 @@ def run_ours(args):
         "path_roofline": {"bound": "hbm", "bytes_per_cluster": PATH_BYTES_PER_CLUSTER,
                           "achieved": value * PATH_BYTES_PER_CLUSTER / 1e9, "peak": hbm_peak,
                           "unit": "GB/s", "frac": value * PATH_BYTES_PER_CLUSTER / 1e9 / hbm_peak,
+                          "fused_bytes_per_cluster": PATH_FUSED_BYTES_PER_CLUSTER,
+                          "fused_frac": value * PATH_FUSED_BYTES_PER_CLUSTER / 1e9 / hbm_peak,
                           "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)"},
         "status": {"fp64_updates": st.n_fp64_updates, "segments": st.n_segments,
                    "tracklets": st.n_tracklets, "merges": st.n_merges},
