@@ -125,7 +125,18 @@ class Events:
         return off, hits, ids[keep]
 
 
-def _crossings(phi0, k, tgl, wedge, misalign, want_truth):
+def _grid_voxel(sector, row, y, z, grid):
+    """Voxel of the distortion model (grid as in FIELD_GRID) at local (y, z)
+    on pad row `row` of `sector`, binned in FP64: the detector model's own
+    piecewise-constant field, independent of the reconstruction's binning."""
+    nb, ny, nz = grid["n_band"], grid["n_y"], grid["n_z"]
+    band = row * nb // N_ROWS
+    iy = np.clip(np.floor((y / ROW_X[row] - grid["u_lo"]) * grid["u_inv"]), 0, ny - 1).astype(np.int64)
+    iz = np.clip(np.floor(np.abs(z) * grid["z_inv"]), 0, nz - 1).astype(np.int64)
+    return ((sector * nb + band) * ny + iy) * nz + iz
+
+
+def _crossings(phi0, k, tgl, wedge, misalign, want_truth, distortion=None):
     """Intersect each helix with every accepted (sector, row) plane.
 
     Works in the global transverse plane: the track circle has centre
@@ -174,13 +185,32 @@ def _crossings(phi0, k, tgl, wedge, misalign, want_truth):
         zl = tgl[t_idx][:, None] * s
         snp = np.sin(psi - a[:, None])
         sector = (iphi[t_idx] % N_PHI + side[t_idx])[:, None] + np.zeros_like(s, dtype=np.int64)
-        if misalign is not None:
-            # measured point on the misaligned plane: x of R^T (P - D) = x_r,
+        if misalign is not None or distortion is not None:
+            # measured point on the displaced plane: x of R^T (P - D) = x_r,
             # solved only where the nominal crossing exists
             ti0, ri0 = np.nonzero(ok)
-            ym, zm, sm = _misaligned_crossing(phi0[t_idx][ti0], kk[ti0, 0], tgl[t_idx][ti0],
-                                              a[ti0], cx[t_idx][ti0], cy[t_idx][ti0],
-                                              s[ti0, ri0], sector[ti0, ri0], ROW_X[ri0], misalign)
+            args = (phi0[t_idx][ti0], kk[ti0, 0], tgl[t_idx][ti0], a[ti0], cx[t_idx][ti0],
+                    cy[t_idx][ti0], s[ti0, ri0], ROW_X[ri0])
+            sec0 = sector[ti0, ri0]
+            if misalign is not None:
+                par = misalign.reshape(N_SECTORS, 6)
+                Rs = np.stack([rotation_matrix(*par[i, 3:6]) for i in range(N_SECTORS)])
+                ym, zm, sm = _displaced_crossing(*args, Rs[sec0], par[sec0, 0:3])
+            else:
+                # distortion: the measured cluster is the true one moved by
+                # -F[v], v the voxel of the measured position (found from
+                # the nominal crossing, then once more from the result)
+                grid, field = distortion
+                eye = np.broadcast_to(np.eye(3), (len(ti0), 3, 3))
+                v = _grid_voxel(sec0, ri0, yl[ti0, ri0], zl[ti0, ri0], grid)
+                ym, zm, sm = _displaced_crossing(*args, eye, field[v])
+                v2 = _grid_voxel(sec0, ri0, ym, zm, grid)
+                moved = v2 != v
+                if moved.any():
+                    a2 = tuple(x[moved] for x in args)
+                    y2, z2, s2 = _displaced_crossing(*a2, eye[moved], field[v2[moved]])
+                    ym, zm, sm = ym.copy(), zm.copy(), sm.copy()
+                    ym[moved], zm[moved], sm[moved] = y2, z2, s2
             yl = np.zeros_like(s)
             zl = np.zeros_like(s)
             yl[ti0, ri0] = ym
@@ -198,15 +228,12 @@ def _crossings(phi0, k, tgl, wedge, misalign, want_truth):
     return tuple(np.concatenate([o[j] for o in out]) for j in range(7))
 
 
-def _misaligned_crossing(phi0, k, tgl, a, cx, cy, s, sector, xr, misalign):
+def _displaced_crossing(phi0, k, tgl, a, cx, cy, s, xr, R, D):
     """Newton solve (1-d arrays, one entry per crossing) for the arc length
-    where the helix meets the misaligned row plane {R (x_r, y, z) + D};
-    returns the measured (y, z) in that plane and the arc length."""
+    where the helix meets the displaced row plane {R (x_r, y, z) + D}
+    (R [m, 3, 3], D [m, 3] per crossing); returns the measured (y, z) in
+    that plane and the arc length."""
     ca, sa = np.cos(a), np.sin(a)
-    par = misalign.reshape(N_SECTORS, 6)
-    Rs = np.stack([rotation_matrix(*par[i, 3:6]) for i in range(N_SECTORS)])
-    R = Rs[sector]                       # [m, 3, 3]
-    D = par[sector, 0:3]
     s = s.copy()
 
     def rt(v0, v1, v2):  # R^T v, component-wise
@@ -242,7 +269,7 @@ def _draw_tracks(rng, n, pt_min, pt_slope, wedge):
 
 
 def _one_collision(rng, n_tracks, noise_frac, wedge, pt_min, pt_slope,
-                   misalign, want_truth, t0_us, tid0):
+                   misalign, want_truth, t0_us, tid0, distortion=None):
     q, pt, tgl, phi0 = _draw_tracks(rng, n_tracks, pt_min, pt_slope, wedge)
     k = KAPPA * BZ * q / pt
     parts = []
@@ -250,7 +277,7 @@ def _one_collision(rng, n_tracks, noise_frac, wedge, pt_min, pt_slope,
     for c0 in range(0, n_tracks, CH):
         sl = slice(c0, min(n_tracks, c0 + CH))
         tr, sec, row, y, z, snp, arc = _crossings(phi0[sl], k[sl], tgl[sl], wedge,
-                                                  misalign, want_truth)
+                                                  misalign, want_truth, distortion)
         parts.append((tr + c0, sec, row, y, z, snp, arc))
     tr, sec, row, yt, zt, snp, arc = (np.concatenate([p[j] for p in parts]) for j in range(7))
     keep = rng.uniform(size=tr.shape[0]) >= ROW_DROP
@@ -291,14 +318,20 @@ def _one_collision(rng, n_tracks, noise_frac, wedge, pt_min, pt_slope,
 
 
 def generate(events, seed, wedge=None, pt_min=0.2, pt_slope=0.5,
-             misalign=None, truth=False, frame=None):
+             misalign=None, truth=False, frame=None, distortion=None):
     """Generate a batch.
 
+    distortion: None, or (grid, field[n_voxels, 3]): each signal cluster is
+            measured displaced by -field[v] from the helix crossing (the
+            plane moved by field[v][0]), v its voxel; exclusive with
+            misalign.
     events: list of (n_tracks, noise_frac) per event.
     frame:  None, or a list of (n_tracks, noise_frac) per collision; all
             collisions then share one event with uniform drift-time offsets
             over FRAME_US (z shifted by V_DRIFT * t0).
     """
+    if misalign is not None and distortion is not None:
+        raise ValueError("misalign and distortion are exclusive")
     rng = np.random.default_rng(seed)
     if frame is not None:
         specs = [[(nt, nf, rng.uniform(0.0, FRAME_US)) for nt, nf in frame]]
@@ -309,7 +342,7 @@ def generate(events, seed, wedge=None, pt_min=0.2, pt_slope=0.5,
     for ev, colls in enumerate(specs):
         for nt, nf, t0 in colls:
             cl, trk = _one_collision(rng, nt, nf, wedge, pt_min, pt_slope,
-                                     misalign, truth, t0, tid0)
+                                     misalign, truth, t0, tid0, distortion)
             cl['event'] = np.full(cl['row'].shape[0], ev, np.int64)
             trk['event'] = np.full(nt, ev, np.int32)
             trk['t0'] = np.full(nt, t0)
@@ -352,6 +385,8 @@ def generate(events, seed, wedge=None, pt_min=0.2, pt_slope=0.5,
         ev.snp_true = cat['snp_true'][order]
     if misalign is not None:
         ev.align = np.asarray(misalign, np.float64).copy()
+    if distortion is not None:
+        ev.field = np.asarray(distortion[1], np.float64).copy()
     return ev
 
 
@@ -503,6 +538,14 @@ def draw_field(seed=SEED_BASE + 5, sigma=0.02, grid=FIELD_GRID):
     each voxel N(0, sigma) cm."""
     rng = np.random.default_rng(seed + 5555)
     return rng.normal(0.0, sigma, (n_voxels(grid), 3))
+
+
+def distortion_sample(n_tracks=2000, seed=SEED_BASE + 5, field=None, grid=FIELD_GRID):
+    """pT > 1 GeV/c tracks, no noise, clusters displaced by a voxel field
+    (default: draw_field(seed)); the field is kept as ev.field."""
+    if field is None:
+        field = draw_field(seed, grid=grid)
+    return generate([(n_tracks, 0.0)], seed, pt_min=1.0, pt_slope=0.5, distortion=(grid, field))
 
 
 def alignment_sample(n_tracks=200000, seed=SEED_BASE + 4, misalign=None,

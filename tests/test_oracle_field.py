@@ -136,3 +136,61 @@ def test_empty_voxels_zero_field_and_combination(orc, grid):
     c_moved = orc.field_adjoint(ev.y, ev.z, ev.row, sec, off, hits, grid, f2, align=al.reshape(-1),
                                 want_grad=False)
     assert abs(c_both - c_moved) <= 1e-9 * c_both
+
+
+def test_generated_distortion_lies_on_the_helix_once_undone():
+    """The generator's distortion model: a noiseless distorted cluster moved
+    back by +F[v] (v its voxel) lies on its track's helix: on the circle of
+    radius 1/|k| through the origin and at z = tan(lambda) times the arc
+    length."""
+    F = synth.draw_field(seed=61, sigma=0.05)
+    ev = synth.generate([(150, 0.0)], 61, pt_min=1.0, distortion=(G, F), truth=True)
+    sec = ev.sector_of_cluster().astype(np.int64)
+    row = ev.row.astype(np.int64)
+    v = synth._grid_voxel(sec, row, ev.y_true, ev.z_true, G)
+    x = synth.ROW_X[row] + F[v, 0]
+    y = ev.y_true + F[v, 1]
+    z = ev.z_true + F[v, 2]
+    a = synth.sector_alpha(sec)
+    X, Y = x * np.cos(a) - y * np.sin(a), x * np.sin(a) + y * np.cos(a)
+    t = ev.mc_track
+    k = synth.KAPPA * synth.BZ * ev.trk_q[t] / ev.trk_pt[t]
+    phi0 = ev.trk_phi0[t]
+    cx, cy = np.sin(phi0) / k, -np.cos(phi0) / k
+    r_err = np.abs(np.hypot(X - cx, Y - cy) * np.abs(k) - 1.0)
+    psi = np.arctan2(-(X - cx) * k, (Y - cy) * k)
+    d = np.where(k > 0, np.mod(phi0 - psi, 2 * np.pi), -np.mod(psi - phi0, 2 * np.pi))
+    z_err = np.abs(z - ev.trk_tgl[t] * d / k)
+    on = (r_err < 1e-9) & (z_err < 1e-7)
+    # within one displacement of a y or |z| bin edge the voxel can flip
+    # between the nominal and the displaced crossing, and the cluster keep
+    # the other voxel's displacement; everywhere else it must be exact
+    fy = (ev.y_true / synth.ROW_X[row] - G["u_lo"]) * G["u_inv"]
+    fz = np.abs(ev.z_true) * G["z_inv"]
+    edge = (np.abs(fy - np.round(fy)) * synth.ROW_X[row] / G["u_inv"] < 0.5) | \
+           (np.abs(fz - np.round(fz)) / G["z_inv"] < 0.5)
+    assert np.all(on[~edge]), (r_err[~edge].max(), z_err[~edge].max())
+    assert edge.mean() < 0.15 and on.mean() > 0.99
+    assert np.abs(F[v]).max() > 0.1
+
+
+def test_field_that_undoes_the_distortion_minimises_chi2(orc, grid):
+    """Along the line t F from no correction to the generated field, the
+    summed chi2 is smallest at t = 1, and the field gradient there is small
+    along F compared with its value at t = 0."""
+    F = synth.draw_field(seed=62, sigma=0.05)
+    ev = synth.distortion_sample(n_tracks=300, seed=62, field=F)
+    off, hits, _ = ev.truth_tracks(n_min=10)
+    sec = ev.sector_of_cluster()
+    ts = np.array([0.0, 0.5, 1.0, 1.5, 2.0])
+    c = np.array([orc.field_adjoint(ev.y, ev.z, ev.row, sec, off, hits, grid, t * F, want_grad=False)
+                  for t in ts])
+    a2, a1, _ = np.polyfit(ts, c, 2)
+    t_min = -a1 / (2 * a2)
+    print(f"chi2 along t F: {c.round(1)}, vertex t = {t_min:.4f}")
+    assert a2 > 0 and abs(t_min - 1.0) < 0.05
+    assert c[2] == c.min()
+    _, g0 = orc.field_adjoint(ev.y, ev.z, ev.row, sec, off, hits, grid, 0 * F)
+    _, g1 = orc.field_adjoint(ev.y, ev.z, ev.row, sec, off, hits, grid, F)
+    d0, d1 = float(np.sum(g0 * F)), float(np.sum(g1 * F))
+    assert d0 < 0 and abs(d1) < 0.05 * abs(d0), (d0, d1)
