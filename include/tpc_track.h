@@ -119,12 +119,17 @@ void tpc_destroy(tpc_ctx* ctx);
 
 /* Device bytes of scratch needed for batches of up to max_clusters clusters
  * in up to max_events events (and fits / gradients of up to max_clusters
- * hits).  Pure host computation. */
+ * hits).  Pure host computation.  Returns 0 for capacities the library does
+ * not take: max_clusters < 0 or > 2^30, max_events < 1, or so many events
+ * that the binning's 32-bit cell keys would overflow (87,552 keys per event
+ * plus one per cluster must stay below 2^31 - 17: about 24,500 events of
+ * small batches, 12,300 at 2^30 clusters). */
 size_t tpc_workspace_bytes(const tpc_ctx* ctx, int64_t max_clusters, int32_t max_events);
 
 /* Hands the library a caller-owned device buffer of `bytes` (256-byte
  * aligned) sized by tpc_workspace_bytes for the same capacities.  The buffer
- * must outlive every call that uses it.  TPC_ERR_CAPACITY if too small. */
+ * must outlive every call that uses it.  TPC_ERR_CAPACITY if too small,
+ * TPC_ERR_ARG for capacities tpc_workspace_bytes refuses. */
 tpc_status tpc_set_workspace(tpc_ctx* ctx, void* dev_ptr, size_t bytes,
                              int64_t max_clusters, int32_t max_events);
 

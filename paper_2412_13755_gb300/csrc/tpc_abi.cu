@@ -108,6 +108,15 @@ Layout make_layout(int64_t N, int32_t E) {
     return L;
 }
 
+// capacities whose 32-bit indexed tables (cell keys, tracklet-bin keys,
+// cluster and track indices) fit
+static bool layout_ok(int64_t max_clusters, int32_t max_events) {
+    if (max_clusters < 0 || max_clusters > ((int64_t)1 << 30) || max_events < 1) return false;
+    const Layout L = make_layout(max_clusters, max_events);
+    const int64_t lim = ((int64_t)1 << 31) - 1;
+    return L.K + 1 < lim && L.KT + 1 < lim && L.T < lim && L.G + 1 < lim;
+}
+
 }  // namespace tpc
 
 static tpc_status fail(tpc_ctx* c, tpc_status st, const char* msg) {
@@ -212,13 +221,13 @@ tpc_status tpc_stage_times(tpc_ctx* c, float* ms) {
 
 size_t tpc_workspace_bytes(const tpc_ctx* ctx, int64_t max_clusters, int32_t max_events) {
     (void)ctx;
-    if (max_clusters < 0 || max_events < 1) return 0;
+    if (!layout_ok(max_clusters, max_events)) return 0;
     return make_layout(max_clusters, max_events).total;
 }
 
 tpc_status tpc_set_workspace(tpc_ctx* c, void* dev_ptr, size_t bytes, int64_t max_clusters,
                              int32_t max_events) {
-    if (!c || !dev_ptr || max_clusters < 0 || max_events < 1 || max_clusters > (int64_t)1 << 30)
+    if (!c || !dev_ptr || !layout_ok(max_clusters, max_events))
         return fail(c, TPC_ERR_ARG, "tpc_set_workspace: bad argument");
     if (((uintptr_t)dev_ptr & 255) != 0) return fail(c, TPC_ERR_ARG, "workspace not 256-byte aligned");
     Layout L = make_layout(max_clusters, max_events);

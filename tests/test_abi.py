@@ -96,3 +96,27 @@ def test_field_voxels(lib):
                 (8, 1 << 26, 1)):
         assert tpc.tpc_field_voxels(tpc.field_grid(*bad, 0, 1, 1)) == -1, bad
     assert lib.tpc_field_voxels(None) == -1
+
+
+def test_workspace_capacities_refused_on_the_host(lib):
+    """Capacities whose 32-bit keys or indices would overflow are refused
+    before any device memory is touched: the workspace size is 0 and
+    tpc_set_workspace returns TPC_ERR_ARG (the buffer is never used)."""
+    from paper_2412_13755_gb300 import tpc
+    ctx = tpc.tpc_create()
+    try:
+        keys = lambda n, e: 152 * 16 * 36 * e + n + 16  # noqa: E731  (cell keys of the layout)
+        lim = (1 << 31) - 1
+        e_max = (lim - 2 - 16 - 1000) // (152 * 16 * 36)
+        assert keys(1000, e_max) + 1 < lim <= keys(1000, e_max + 1) + 1
+        assert tpc.tpc_workspace_bytes(ctx, 1000, e_max) > 0
+        assert tpc.tpc_workspace_bytes(ctx, 1000, e_max + 1) == 0
+        assert tpc.tpc_workspace_bytes(ctx, 1 << 30, 1) > 0
+        assert tpc.tpc_workspace_bytes(ctx, (1 << 30) + 1, 1) == 0
+        assert tpc.tpc_workspace_bytes(ctx, 1 << 30, 13000) == 0
+        assert tpc.tpc_workspace_bytes(ctx, -1, 1) == 0
+        fake = C.c_void_p(256)  # aligned, never dereferenced: refused first
+        rc = lib.tpc_set_workspace(ctx, fake, C.c_size_t(1 << 62), C.c_int64(1000), C.c_int32(e_max + 1))
+        assert rc == tpc.TPC_ERR_ARG
+    finally:
+        tpc.tpc_destroy(ctx)
