@@ -162,7 +162,7 @@ _loaded_n: dict[int, int] = {}
 
 def _need_len(t, n, name, what):
     if t.numel() < n:
-        raise ValueError(f"{what}: {name} holds {t.numel()} entries, the call writes {n}")
+        raise ValueError(f"{what}: {name} holds {t.numel()} entries, the call needs {n}")
 
 
 def check_find_outputs(n, track_of_cluster, trk_off, trk_hits, n_tracks_dev, what="tpc_find_tracks"):
