@@ -204,6 +204,28 @@ def field_adjoint(y, z, row, sector_of, trk_off, trk_hits, grid: FieldGrid, fiel
     return (tot.value, g) if want_grad else tot.value
 
 
+def field_gn_blocks(y, z, row, sector_of, trk_off, trk_hits, grid: FieldGrid, field,
+                    align=None, params=None):
+    """Per-voxel 3x3 diagonal blocks [n_vox, 3, 3] of the field's
+    Gauss-Newton matrix (dual numbers through the fit)."""
+    y, z, row = _c(y, np.float32), _c(z, np.float32), _c(row, np.uint16)
+    sec = _c(sector_of, np.int32)
+    off, hits = _c(trk_off, np.int32), _c(trk_hits, np.int32)
+    T = off.shape[0] - 1
+    prm = params or default_params()
+    fld = _c(field, np.float64)
+    nv = 36 * grid.n_band * grid.n_y * grid.n_z
+    if fld.size != 3 * nv:
+        raise ValueError(f"field holds {fld.size} values, the grid has {nv} voxels x 3")
+    al = _c(align, np.float64) if align is not None else None
+    out = np.zeros((nv, 3, 3))
+    rc = lib().orc_field_gn_blocks(_p(y), _p(z), _p(row), _p(sec), _p(off), _p(hits), C.c_int32(T),
+                                   _p(al), C.byref(grid), _p(fld), C.byref(prm), _p(out))
+    if rc != 0:
+        raise ValueError("invalid field grid")
+    return out
+
+
 def gauss_newton(y, z, row, sector_of, trk_off, trk_hits, align, params=None):
     y, z, row = _c(y, np.float32), _c(z, np.float32), _c(row, np.uint16)
     sec = _c(sector_of, np.int32)

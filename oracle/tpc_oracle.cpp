@@ -1125,6 +1125,86 @@ int orc_field_adjoint(const float* y, const float* z, const uint16_t* row, const
     return 0;
 }
 
+// Per-voxel diagonal blocks of the field's Gauss-Newton matrix: the fit
+// loop of kf_fit, in passes of eight voxels whose components carry the dual
+// parts, accumulating 2 dr^T S^-1 dr of every predicted residual.
+int orc_field_gn_blocks(const float* y, const float* z, const uint16_t* row, const int32_t* sec,
+                        const int32_t* trk_off, const int32_t* trk_hits, int32_t T,
+                        const double* align, const orc_field_grid* grid, const double* field,
+                        const orc_params* prm, double* blocks) {
+    if (!grid_ok(grid)) return -1;
+    const int64_t NV = (int64_t)NSEC * grid->n_band * grid->n_y * grid->n_z;
+    const int nt = orc_get_threads();
+    std::vector<std::vector<std::pair<int32_t, std::array<double, 9>>>> tb(T);
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nt)
+    for (int t = 0; t < T; ++t) {
+        const int n = trk_off[t + 1] - trk_off[t];
+        const int32_t* hits = trk_hits + trk_off[t];
+        if (n < 3) continue;
+        std::vector<int32_t> vox(n);
+        for (int j = 0; j < n; ++j) vox[j] = voxel_of(y[hits[j]], z[hits[j]], row[hits[j]], sec[hits[j]], *grid);
+        std::vector<int32_t> touched;
+        for (int j = 0; j < n; ++j)
+            if (std::find(touched.begin(), touched.end(), vox[j]) == touched.end()) touched.push_back(vox[j]);
+        std::vector<D24> th(align ? 36 * 6 : 0);
+        for (size_t i = 0; i < th.size(); ++i) th[i] = D24(align[i]);
+        const Seed sd = make_seed(y, z, row, sec, hits, n, true, *prm);
+        std::vector<std::pair<int32_t, std::array<double, 9>>> out;
+        bool ok = true;
+        for (size_t base = 0; base < touched.size() && ok; base += NVP) {
+            const int kn = (int)std::min<size_t>(NVP, touched.size() - base);
+            D24 p[5], C[15], chi2(0.0), J[25], dX[5];
+            for (int i = 0; i < 5; ++i) p[i] = D24(sd.p[i]);
+            for (int i = 0; i < 15; ++i) C[i] = D24(0.0);
+            for (int i = 0; i < 5; ++i) C[sidx(i, i)] = D24(prm->prior[i]);
+            D24 x(sd.x);
+            int frame = sd.frame;
+            std::vector<std::array<double, 9>> acc(kn);
+            for (auto& a : acc) a.fill(0.0);
+            for (int j = 0; j < n && ok; ++j) {
+                const int h = hits[j];
+                D24 xc, yc, zc;
+                if (align) {
+                    corrected<D24>(th.data() + 6 * sec[h], row_x(row[h]), (double)y[h], (double)z[h], xc, yc, zc);
+                } else {
+                    xc = D24(row_x(row[h]));
+                    yc = D24((double)y[h]);
+                    zc = D24((double)z[h]);
+                }
+                D24 d3[3];
+                for (int c = 0; c < 3; ++c) d3[c] = D24(field[3 * (int64_t)vox[j] + c]);
+                for (int k = 0; k < kn; ++k)
+                    if (touched[base + k] == vox[j])
+                        for (int c = 0; c < 3; ++c) d3[c].d[k * 3 + c] = 1.0;
+                xc = xc + d3[0];
+                yc = yc + d3[1];
+                zc = zc + d3[2];
+                ok = move_state(x, p, frame, xc, sec[h], J, dX, *prm);
+                if (!ok) break;
+                cov_transform(C, J);
+                D24 res[2], si[3];
+                kf_update(p, C, yc, zc, prm->sigma_y2, prm->sigma_z2, chi2, res, si);
+                for (int k = 0; k < kn; ++k)
+                    for (int a = 0; a < 3; ++a)
+                        for (int b = 0; b < 3; ++b) {
+                            const int ia = k * 3 + a, ib = k * 3 + b;
+                            acc[k][3 * a + b] +=
+                                2.0 * (res[0].d[ia] * (si[0].v * res[0].d[ib] + si[1].v * res[1].d[ib]) +
+                                       res[1].d[ia] * (si[1].v * res[0].d[ib] + si[2].v * res[1].d[ib]));
+                        }
+            }
+            if (ok)
+                for (int k = 0; k < kn; ++k) out.push_back({touched[base + k], acc[k]});
+        }
+        if (ok) tb[t] = std::move(out);
+    }
+    for (int64_t i = 0; i < 9 * NV; ++i) blocks[i] = 0.0;
+    for (int t = 0; t < T; ++t)
+        for (const auto& e : tb[t])
+            for (int i = 0; i < 9; ++i) blocks[9 * (int64_t)e.first + i] += e.second[i];
+    return 0;
+}
+
 // Gauss-Newton matrix: sum over tracks and clusters of 2 dr^T S^-1 dr, with
 // dr the derivative of each predicted residual with respect to the
 // parameters of the track's touched sectors.

@@ -163,6 +163,18 @@ int orc_field_adjoint(const float* y, const float* z, const uint16_t* row,
                       const orc_field_grid* grid, const double* field,
                       const orc_params* prm, double* chi2_total, double* grad_field);
 
+/* Per-voxel 3x3 diagonal blocks of the Gauss-Newton matrix of the summed
+ * chi2 with respect to the field: sum over tracks and clusters of
+ * 2 dr^T S^-1 dr, dr the derivative of each predicted residual with respect
+ * to the voxel's three components (through the whole fit, dual numbers).
+ * blocks[9 v + 3 a + b]; voxels without clusters get 0.  Returns 0, or -1
+ * for an invalid grid.  The preconditioner of a block-Jacobi descent. */
+int orc_field_gn_blocks(const float* y, const float* z, const uint16_t* row,
+                        const int32_t* sector_of, const int32_t* trk_off,
+                        const int32_t* trk_hits, int32_t n_tracks, const double* align,
+                        const orc_field_grid* grid, const double* field,
+                        const orc_params* prm, double* blocks);
+
 /* Threads used by the OpenMP loops (0 = library default). */
 void orc_set_threads(int n);
 int orc_get_threads(void);
