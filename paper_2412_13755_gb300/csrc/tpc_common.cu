@@ -139,24 +139,7 @@ cudaError_t fill_i32(int32_t* p, int64_t n, int32_t v, cudaStream_t s) {
 }
 
 cudaError_t init_geo(const Workspace& ws, cudaStream_t s) {
-    Geo g;
-    const double pi = 3.14159265358979323846;
-    for (int r = 0; r < NROW; ++r) {
-        g.row_xd[r] = 85.0 + r * (162.0 / 151.0);
-        g.row_xf[r] = (float)g.row_xd[r];
-    }
-    g.tan_half = (float)std::tan(10.0 * pi / 180.0);
-    for (int r = 0; r < NROW; ++r)
-        g.ycell_inv[r] = (float)(CELL_NY / (2.0 * g.row_xd[r] * std::tan(10.0 * pi / 180.0)));
-    g.tan_half_d = std::tan(10.0 * pi / 180.0);
-    for (int i = 0; i < NPHI; ++i) g.alpha[i] = (i + 0.5) * (20.0 * pi / 180.0);
-    for (int k = 0; k < NPHI; ++k) {
-        double d = g.alpha[k] - g.alpha[0];
-        while (d > pi) d -= 2 * pi;
-        while (d <= -pi) d += 2 * pi;
-        g.da_cos[k] = std::cos(d);
-        g.da_sin[k] = std::sin(d);
-    }
+    const Geo g = make_geo();
     tpc::LaunchCount{}, k_init_geo<<<1, 1, 0, s>>>(ws.at<Geo>(ws.L.geo), g);
     return cudaGetLastError();
 }

@@ -29,12 +29,12 @@ __device__ __forceinline__ int group_of(const int64_t* __restrict__ off, int G, 
     return lo;
 }
 
-__device__ __forceinline__ float t_sqrt(float v) { return sqrtf(v); }
-__device__ __forceinline__ double t_sqrt(double v) { return sqrt(v); }
-__device__ __forceinline__ float t_asin(float v) { return asinf(v); }
-__device__ __forceinline__ double t_asin(double v) { return asin(v); }
-__device__ __forceinline__ float t_abs(float v) { return fabsf(v); }
-__device__ __forceinline__ double t_abs(double v) { return fabs(v); }
+TPC_HD float t_sqrt(float v) { return sqrtf(v); }
+TPC_HD double t_sqrt(double v) { return sqrt(v); }
+TPC_HD float t_asin(float v) { return asinf(v); }
+TPC_HD double t_asin(double v) { return asin(v); }
+TPC_HD float t_abs(float v) { return fabsf(v); }
+TPC_HD double t_abs(double v) { return fabs(v); }
 
 template <class R>
 struct KFT {
@@ -48,7 +48,7 @@ struct KFT {
 // hi + lo += d, exactly up to the final rounding of lo (TwoSum); the pair
 // is renormalised so that |lo| stays below half an ulp of hi.
 template <class R>
-__device__ __forceinline__ void add_comp(R& hi, R& lo, R d) {
+TPC_HD void add_comp(R& hi, R& lo, R d) {
     const R s = hi + d;
     const R bp = s - hi;
     const R err = (hi - (s - bp)) + (d - bp);
@@ -67,8 +67,8 @@ using KFD = KFT<double>;
 //        [0,   0, 0,   1,   0  ],
 //        [0,   0, 0,   0,   1  ]]
 template <class R>
-__device__ __forceinline__ void cov_jct(R C[15], R j00, R j02, R j04, R j10, R j12, R j13, R j14,
-                                        R j20, R j22, R j24) {
+TPC_HD void cov_jct(R C[15], R j00, R j02, R j04, R j10, R j12, R j13, R j14, R j20, R j22,
+                    R j24) {
     R c[5][5];
 #pragma unroll
     for (int i = 0; i < 5; ++i)
@@ -117,9 +117,8 @@ struct MoveJ {
 // leaves s.C alone (for a caller that transforms its own covariance with the
 // Jacobian returned in mj).
 template <class R, bool CanRotate = true, bool MoveCov = true>
-__device__ __forceinline__ bool kf_move(KFT<R>& s, double x_to, int to, const Geo* __restrict__ geo,
-                                        R kb, R snp_max, MoveJ* mj = nullptr,
-                                        const R* dx_same_frame = nullptr) {
+TPC_HD bool kf_move(KFT<R>& s, double x_to, int to, const Geo* __restrict__ geo, R kb, R snp_max,
+                    MoveJ* mj = nullptr, const R* dx_same_frame = nullptr) {
     double xs = CanRotate ? s.x : 0.0;
     R ys = s.p[0], ss = s.p[2];
     R ys_lo = s.lo[0], ss_lo = s.lo[2];

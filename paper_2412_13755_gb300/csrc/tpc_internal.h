@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <cmath>
 #include <string>
 
 #include "../../include/tpc_track.h"
@@ -41,6 +42,30 @@ struct Geo {
     double da_cos[NPHI];   // cos / sin of the frame rotation from phi-index
     double da_sin[NPHI];   // i to phi-index (i + k) mod 18, k = 0..17
 };
+
+// The geometry table (host computation; copied to the workspace once).
+inline Geo make_geo() {
+    Geo g;
+    const double pi = 3.14159265358979323846;
+    for (int r = 0; r < NROW; ++r) {
+        g.row_xd[r] = 85.0 + r * (162.0 / 151.0);
+        g.row_xf[r] = (float)g.row_xd[r];
+    }
+    g.tan_half = (float)std::tan(10.0 * pi / 180.0);
+    g.pad0 = 0.f;
+    for (int r = 0; r < NROW; ++r)
+        g.ycell_inv[r] = (float)(CELL_NY / (2.0 * g.row_xd[r] * std::tan(10.0 * pi / 180.0)));
+    g.tan_half_d = std::tan(10.0 * pi / 180.0);
+    for (int i = 0; i < NPHI; ++i) g.alpha[i] = (i + 0.5) * (20.0 * pi / 180.0);
+    for (int k = 0; k < NPHI; ++k) {
+        double d = g.alpha[k] - g.alpha[0];
+        while (d > pi) d -= 2 * pi;
+        while (d <= -pi) d += 2 * pi;
+        g.da_cos[k] = std::cos(d);
+        g.da_sin[k] = std::sin(d);
+    }
+    return g;
+}
 
 // Device status word and counters (int32 slots in the workspace).
 enum StatusSlot {
