@@ -20,11 +20,16 @@ __device__ __forceinline__ void set_status(int32_t* st, int code, int detail) {
 }
 
 // largest g with off[g] <= i (off non-decreasing, off[0] = 0)
-__device__ __forceinline__ int group_of(const int64_t* __restrict__ off, int G, int64_t i) {
+TPC_HD int group_of(const int64_t* __restrict__ off, int G, int64_t i) {
     int lo = 0, hi = G;  // answer in [lo, hi)
     while (hi - lo > 1) {
         const int mid = (lo + hi) >> 1;
-        if (__ldg(off + mid) <= i) lo = mid; else hi = mid;
+#if defined(__CUDA_ARCH__)
+        const int64_t o = __ldg(off + mid);
+#else
+        const int64_t o = off[mid];
+#endif
+        if (o <= i) lo = mid; else hi = mid;
     }
     return lo;
 }
@@ -299,9 +304,8 @@ __device__ __forceinline__ double kf_update_dcov(KF& s, double Cd[15], float my,
 
 // Covariance transform C <- J C J^T in float-float for the Jacobian of
 // cov_jct (J exact in FP32).
-__device__ __forceinline__ void cov_jct_ff(ff C[15], float j00, float j02, float j04, float j10,
-                                           float j12, float j13, float j14, float j20, float j22,
-                                           float j24) {
+TPC_HD void cov_jct_ff(ff C[15], float j00, float j02, float j04, float j10, float j12, float j13,
+                       float j14, float j20, float j22, float j24) {
     ff c[5][5];
 #pragma unroll
     for (int i = 0; i < 5; ++i)
@@ -332,8 +336,8 @@ __device__ __forceinline__ void cov_jct_ff(ff C[15], float j00, float j02, float
 // The same transform for a move inside one frame, where J = I except for
 // j02, j04, j12, j13, j14, j24 (j00 = j22 = 1, j10 = j20 = 0): the products
 // with the unit and zero entries are skipped.
-__device__ __forceinline__ void cov_jct_ff_frame(ff C[15], float j02, float j04, float j12, float j13,
-                                                 float j14, float j24) {
+TPC_HD void cov_jct_ff_frame(ff C[15], float j02, float j04, float j12, float j13, float j14,
+                             float j24) {
     ff c[5][5];
 #pragma unroll
     for (int i = 0; i < 5; ++i)
@@ -363,7 +367,7 @@ __device__ __forceinline__ void cov_jct_ff_frame(ff C[15], float j02, float j04,
 // Kalman update with the covariance in float-float: S, its inverse, the
 // gain and C - K H C in float-float; the state increment from the gain in
 // FP32 on the compensated state.  Returns the predicted-residual chi2 term.
-__device__ __forceinline__ float kf_update_ff(KF& s, ff C[15], float my, float mz, float sy2, float sz2) {
+TPC_HD float kf_update_ff(KF& s, ff C[15], float my, float mz, float sy2, float sz2) {
     const float r0 = (my - s.p[0]) - s.lo[0], r1 = (mz - s.p[1]) - s.lo[1];
     const ff S00 = ff_add(C[0], ff_from(sy2)), S01 = C[1], S11 = ff_add(C[5], ff_from(sz2));
     const ff det = ff_add(ff_mul(S00, S11), ff_neg(ff_mul(S01, S01)));
@@ -469,12 +473,12 @@ __device__ __forceinline__ double kf_update_d(KFD& s, double my, double mz, doub
 // Neumaier-compensated FP32 accumulation.
 struct NSum {
     float s = 0.f, c = 0.f;
-    __device__ __forceinline__ void add(float v) {
+    TPC_HD void add(float v) {
         const float t = s + v;
         if (fabsf(s) >= fabsf(v)) c += (s - t) + v; else c += (v - t) + s;
         s = t;
     }
-    __device__ __forceinline__ float value() const { return s + c; }
+    TPC_HD float value() const { return s + c; }
 };
 
 // Three-point seed (FP64): circle through the innermost, middle and
@@ -482,10 +486,9 @@ struct NSum {
 // in the frame of the first cluster in fit order gives q/pT and sin phi at
 // that cluster; tan lambda = dz / arc between the end clusters; (y, z) of the
 // first cluster.  Clamped to |sin phi| <= snp_max_seed, |q/pT| <= qpt_max.
-__device__ __forceinline__ void kf_seed(KF& s, const int rows[3], const int secs[3],
-                                        const float ys[3], const float zs[3], bool first_is_outer,
-                                        const Geo* __restrict__ geo, double bz, double snp_max_seed,
-                                        double qpt_max, const float prior[5]) {
+TPC_HD void kf_seed(KF& s, const int rows[3], const int secs[3], const float ys[3],
+                    const float zs[3], bool first_is_outer, const Geo* __restrict__ geo, double bz,
+                    double snp_max_seed, double qpt_max, const float prior[5]) {
     const int fr = secs[0];
     double px[3], py[3];
 #pragma unroll

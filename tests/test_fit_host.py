@@ -1,0 +1,91 @@
+"""The fit kernel's per-track function (fit_track in tpc_fit.cuh: seed,
+transport, float-float covariance, compensated update and chi2) compiled
+by nvcc for the host and run on the CPU, against the FP64 oracle on the
+same hit lists, with the GPU parity bars:
+* the same tracks fail (a transport reaching |sin phi| = snp_max);
+* parameters within 1e-5 max(|p_i|, s_i), s = (1 cm, 1 cm, 0.1, 0.1, 0.1);
+* chi2 within 2e-3 relative (1e-3 absolute), the covariance diagonal within
+  1e-4 relative, ndf equal.
+Run on every track the oracle finds in a noisy event (fakes and low-pT
+tracks included) and on the truth tracks of a noise-free one.  No GPU is
+needed; the program launches no kernel."""
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_2412_13755_gb300 import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
+SCALE = np.array([1.0, 1.0, 0.1, 0.1, 0.1])
+DIAG = [0, 5, 9, 12, 14]
+
+
+@pytest.fixture(scope="module")
+def fit_host(tmp_path_factory):
+    nvcc = NVCC if os.path.exists(NVCC) else shutil.which("nvcc")
+    if nvcc is None:
+        pytest.skip("no nvcc")
+    exe = tmp_path_factory.mktemp("fit") / "fit_host"
+    subprocess.run([nvcc, "-std=c++17", "-O2", "-Xcompiler", "-ffp-contract=off",
+                    "-gencode", "arch=compute_103a,code=sm_103a",
+                    "-I", os.path.join(ROOT, "paper_2412_13755_gb300", "csrc"),
+                    "-I", os.path.join(ROOT, "include"),
+                    os.path.join(ROOT, "tests", "fit_host.cu"), "-o", str(exe)],
+                   check=True, capture_output=True)
+    return exe
+
+
+def _library_params():
+    pytest.importorskip("torch")
+    from paper_2412_13755_gb300 import tpc
+    p = tpc.default_params()
+    return np.array([p.sigma_y2, p.sigma_z2, p.snp_max, p.bz, p.seed_snp_max, p.seed_qpt_max,
+                     *list(p.prior)], np.float32)
+
+
+def _run(exe, tmp_path, ev, off, hits):
+    inp, out = tmp_path / "in.bin", tmp_path / "out.bin"
+    G = ev.n_events * 36
+    T = len(off) - 1
+    with open(inp, "wb") as f:
+        f.write(np.array([ev.n, G, T], np.int64).tobytes())
+        for a, dt in ((ev.y, np.float32), (ev.z, np.float32), (ev.row, np.uint16),
+                      (ev.evt_sector_off, np.int64), (off, np.int32), (hits[:off[-1]], np.int32)):
+            f.write(np.ascontiguousarray(a, dt).tobytes())
+        f.write(_library_params().tobytes())
+    r = subprocess.run([str(exe), str(inp), str(out)], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stdout + r.stderr
+    raw = np.fromfile(out, np.float32).reshape(T, 22)
+    return raw[:, :5].astype(np.float64), raw[:, 5:20].astype(np.float64), raw[:, 20].astype(np.float64), \
+        raw[:, 21].copy().view(np.int32)
+
+
+def _compare(orc, ev, off, hits, got):
+    par, cov, chi2, ndf = got
+    opar, ocov, ochi2, ondf = orc.fit_tracks(ev.y, ev.z, ev.row, ev.sector_of_cluster(), off, hits)
+    assert np.array_equal(ndf <= 0, ondf <= 0), "transport failures differ"
+    ok = ondf > 0
+    assert np.array_equal(ndf[ok], ondf[ok])
+    rel = np.abs(par - opar) / np.maximum(np.abs(opar), SCALE)
+    crel = np.abs(cov[ok][:, DIAG] - ocov[ok][:, DIAG]) / np.abs(ocov[ok][:, DIAG])
+    print(f"{ok.sum()} tracks: parameters {rel[ok].max(0)}, cov diagonal {crel.max():.2e}")
+    assert np.all(rel[ok] <= 1e-5), rel[ok].max(0)
+    assert np.all(crel <= 1e-4), crel.max()
+    np.testing.assert_allclose(chi2[ok], ochi2[ok], rtol=2e-3, atol=1e-3)
+    return ok.sum()
+
+
+def test_fit_found_tracks_on_host(orc, fit_host, tmp_path):
+    ev = synth.central_event(n_tracks=1000, seed=101)
+    _, off, hits = orc.find_tracks(ev.y, ev.z, ev.row, ev.evt_sector_off, ev.n_events)
+    assert _compare(orc, ev, off, hits, _run(fit_host, tmp_path, ev, off, hits)) > 900
+
+
+def test_fit_truth_tracks_on_host(orc, fit_host, tmp_path):
+    ev = synth.central_event(n_tracks=1500, noise=0.0, seed=202)
+    off, hits, _ = ev.truth_tracks()
+    assert _compare(orc, ev, off, hits, _run(fit_host, tmp_path, ev, off, hits)) > 1400
