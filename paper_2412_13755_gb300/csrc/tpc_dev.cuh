@@ -227,8 +227,7 @@ TPC_HD bool kf_move(KFT<R>& s, double x_to, int to, const Geo* __restrict__ geo,
 // the preceding move (when mj carries it) and the update itself, the state
 // increment applied in FP64 to the compensated state.  Returns the
 // predicted-residual chi2 term.
-__device__ __forceinline__ float kf_update_cov_d(KF& s, float my, float mz, float sy2, float sz2,
-                                                 const MoveJ* mj) {
+TPC_HD float kf_update_cov_d(KF& s, float my, float mz, float sy2, float sz2, const MoveJ* mj) {
     double Cd[15];
     if (mj && mj->valid) {
 #pragma unroll
@@ -272,8 +271,7 @@ __device__ __forceinline__ float kf_update_cov_d(KF& s, float my, float mz, floa
 // covariance of the FP32 state s): FP64 gain and covariance step, the state
 // increment applied in FP64 to the compensated state.  Returns the
 // predicted-residual chi2 term.
-__device__ __forceinline__ double kf_update_dcov(KF& s, double Cd[15], float my, float mz, double sy2,
-                                                 double sz2) {
+TPC_HD double kf_update_dcov(KF& s, double Cd[15], float my, float mz, double sy2, double sz2) {
     const double dr0 = (double)my - ((double)s.p[0] + (double)s.lo[0]);
     const double dr1 = (double)mz - ((double)s.p[1] + (double)s.lo[1]);
     const double D00 = Cd[0] + sy2, D01 = Cd[1], D11 = Cd[5] + sz2;
@@ -402,9 +400,8 @@ TPC_HD float kf_update_ff(KF& s, ff C[15], float my, float mz, float sy2, float 
 // fp64_ratio x its prior, or det S <= fp64_det S00 S11) the covariance step
 // is redone in FP64 -- the transport J C J^T of the preceding move (when mj
 // carries it) and the update -- and counted.
-__device__ __forceinline__ float kf_update(KF& s, float my, float mz, float sy2, float sz2,
-                                           float fp64_ratio, float fp64_det, int* n_fp64,
-                                           const MoveJ* mj = nullptr) {
+TPC_HD float kf_update(KF& s, float my, float mz, float sy2, float sz2, float fp64_ratio,
+                       float fp64_det, int* n_fp64, const MoveJ* mj = nullptr) {
     const float r0 = (my - s.p[0]) - s.lo[0], r1 = (mz - s.p[1]) - s.lo[1];
     const float S00 = s.C[0] + sy2, S01 = s.C[1], S11 = s.C[5] + sz2;
     const float det = S00 * S11 - S01 * S01;
@@ -438,12 +435,16 @@ __device__ __forceinline__ float kf_update(KF& s, float my, float mz, float sy2,
         return r0 * r0 * i00 + 2.f * r0 * r1 * i01 + r1 * r1 * i11;
     }
     // FP64 redo of the covariance step
+#if defined(__CUDA_ARCH__)
     if (n_fp64) atomicAdd(n_fp64, 1);
+#else
+    if (n_fp64) ++*n_fp64;
+#endif
     return kf_update_cov_d(s, my, mz, sy2, sz2, mj);
 }
 
 // Plain FP64 update (used when a whole track is refit in FP64).
-__device__ __forceinline__ double kf_update_d(KFD& s, double my, double mz, double sy2, double sz2) {
+TPC_HD double kf_update_d(KFD& s, double my, double mz, double sy2, double sz2) {
     const double r0 = my - (s.p[0] + s.lo[0]), r1 = mz - (s.p[1] + s.lo[1]);
     const double S00 = s.C[0] + sy2, S01 = s.C[1], S11 = s.C[5] + sz2;
     const double idet = 1.0 / (S00 * S11 - S01 * S01);
