@@ -32,7 +32,21 @@ def test_kernel_helpers_on_host(tmp_path, program):
     assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stdout[-2000:]
 
 
-def test_field_voxel_matches_oracle(tmp_path, orc):
+def _grid(which):
+    """The default grid, or a seeded random one (band counts that divide
+    152, uneven y and |z| bins, edges inside and outside the acceptance)."""
+    from paper_2412_13755_gb300 import synth
+    if which == 0:
+        return synth.FIELD_GRID
+    rng = np.random.default_rng(500 + which)
+    n_y, n_z = int(rng.integers(1, 9)), int(rng.integers(1, 12))
+    u_lo = -synth.TAN_HALF_SECTOR * rng.uniform(0.5, 1.2)
+    return dict(n_band=int(rng.choice([1, 2, 4, 8, 19, 38, 76, 152])), n_y=n_y, n_z=n_z, u_lo=u_lo,
+                u_inv=n_y / (2 * abs(u_lo) * rng.uniform(0.8, 1.3)), z_inv=n_z / rng.uniform(150.0, 300.0))
+
+
+@pytest.mark.parametrize("which", [0, 1, 2, 3])
+def test_field_voxel_matches_oracle(tmp_path, orc, which):
     from paper_2412_13755_gb300 import synth
     cxx = shutil.which("g++") or shutil.which("c++")
     if cxx is None:
@@ -42,7 +56,7 @@ def test_field_voxel_matches_oracle(tmp_path, orc):
                     "-I", os.path.join(ROOT, "paper_2412_13755_gb300", "csrc"),
                     os.path.join(ROOT, "tests", "field_voxel_host.cpp"), "-o", str(exe)], check=True)
     ev = synth.central_event(n_tracks=1000, seed=77)
-    G = synth.FIELD_GRID
+    G = _grid(which)
     # clusters on the bin edges of y / x and |z| and up to two float steps
     # either side of them
     rng = np.random.default_rng(78)
