@@ -74,13 +74,16 @@ def test_out_of_range_coordinates_go_to_the_edge_bins(orc, grid):
     assert iy[4] == 0 and iz[5] == nz - 1
 
 
-def test_constant_field_is_a_rigid_translation(orc, grid):
+@pytest.mark.parametrize("g", [None, dict(n_band=4, n_y=2, n_z=3, u_lo=-0.2, u_inv=5.0, z_inv=0.012)])
+def test_constant_field_is_a_rigid_translation(orc, grid, g):
     ev, sec, off, hits = _sample()
     rng = np.random.default_rng(5)
     shift = rng.normal(0.0, 0.02, (36, 3))
     align = np.zeros((36, 6))
     align[:, :3] = shift
-    nv = synth.n_voxels()
+    if g is not None:
+        grid = orc.field_grid(**g)
+    nv = synth.n_voxels(G if g is None else g)
     field = np.repeat(shift, nv // 36, axis=0)
     c_f, g_f = orc.field_adjoint(ev.y, ev.z, ev.row, sec, off, hits, grid, field)
     c_a, g_a = orc.fit_adjoint(ev.y, ev.z, ev.row, sec, off, hits, align.reshape(-1))
