@@ -5,9 +5,8 @@
 // comparison with the FP64 oracle.  Host code only; no kernel is launched.
 //   input:  n, G, T (int64); y[n], z[n] (float); row[n] (uint16);
 //           evt_off[G+1] (int64); trk_off[T+1], trk_hits[...] (int32);
-//           sy2, sz2, snp_max, bz, seed_snp, seed_qpt, prior[5] (float,
-//           the library's parameters);
-//           (then fp64_ratio, fp64_det);
+//           sy2, sz2, snp_max, bz, seed_snp, seed_qpt, prior[5],
+//           fp64_ratio, fp64_det (float, the library's parameters);
 //   output: per track params[5], cov[15], chi2 (float), ndf (int32), then
 //           the number of FP64 redos (int32).
 #include <cstdio>
