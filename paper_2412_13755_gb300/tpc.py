@@ -107,6 +107,8 @@ def load_library(build_if_missing: bool = True):
     lib.tpc_field_voxels.argtypes = [vp]
     lib.tpc_field_voxels.restype = i64
     lib.tpc_fit_adjoint_field.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp, vp, vp, vp]
+    lib.tpc_find_tracks_noalloc.argtypes = [vp, vp, vp, vp, i64, vp, i32, vp, vp, vp, vp, vp, i32,
+                                            vp]
     for name in EXPORTS:
         f = getattr(lib, name)
         if name not in ("tpc_default_params", "tpc_destroy", "tpc_workspace_bytes",
@@ -327,6 +329,36 @@ def tpc_fit_adjoint_field(ctx, trk_off, trk_hits, n_tracks, align, grid: FieldGr
     _check(ctx, rc, "tpc_fit_adjoint_field")
 
 
+# Limits of tpc_find_tracks_noalloc (include/tpc_track.h).
+NOALLOC_MAX_CLUSTERS = 65536
+NOALLOC_MAX_EVENTS = 4
+
+
+def tpc_find_tracks_noalloc(y, z, row, evt_sector_off, n_events, track_of_cluster, trk_off,
+                            trk_hits, n_tracks_dev, status_dev, params: Params | None = None,
+                            stream=None):
+    """Load + find in one call whose scratch is the library's own fixed
+    device array: the call allocates nothing.  The device status word is
+    copied to status_dev[0]."""
+    _need(y, torch.float32, "y")
+    _need(z, torch.float32, "z")
+    _need(row, torch.uint16, "row")
+    _need(evt_sector_off, torch.int64, "evt_sector_off")
+    for t, nm in ((track_of_cluster, "track_of_cluster"), (trk_off, "trk_off"),
+                  (trk_hits, "trk_hits"), (n_tracks_dev, "n_tracks_dev"), (status_dev, "status_dev")):
+        _need(t, torch.int32, nm)
+    what = "tpc_find_tracks_noalloc"
+    check_load_inputs(y, z, row, None, evt_sector_off, n_events, what)
+    check_find_outputs(y.numel(), track_of_cluster, trk_off, trk_hits, n_tracks_dev, what)
+    _need_len(status_dev, 1, "status_dev", what)
+    rc = load_library().tpc_find_tracks_noalloc(
+        C.byref(params) if params is not None else None, _ptr(y), _ptr(z), _ptr(row), y.numel(),
+        _ptr(evt_sector_off), int(n_events), _ptr(track_of_cluster), _ptr(trk_off), _ptr(trk_hits),
+        _ptr(n_tracks_dev), _ptr(status_dev), trk_off.numel() - 1, _stream(stream))
+    if rc != TPC_OK:
+        raise TPCError(f"{what}: {STATUS_NAMES.get(rc, rc)}")
+
+
 def tpc_set_tune(ctx, tune: Tune | None):
     _check(ctx, load_library().tpc_set_tune(ctx, C.byref(tune) if tune is not None else None),
            "tpc_set_tune")
@@ -337,7 +369,7 @@ def tpc_autotune(ctx, track_of_cluster, trk_off, trk_hits, n_tracks_dev, stream=
                  (trk_hits, "trk_hits"), (n_tracks_dev, "n_tracks_dev")):
         _need(t, torch.int32, n)
     check_find_outputs(_loaded_n.get(ctx.value, 0), track_of_cluster, trk_off, trk_hits, n_tracks_dev,
-                       "tpc_autotune", "tpc_field_voxels", "tpc_fit_adjoint_field")
+                       what="tpc_autotune")
     best = Tune()
     rc = load_library().tpc_autotune(ctx, _ptr(track_of_cluster), _ptr(trk_off), _ptr(trk_hits),
                                      _ptr(n_tracks_dev), trk_off.numel() - 1, C.byref(best),
