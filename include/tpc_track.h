@@ -143,11 +143,13 @@ tpc_status tpc_set_workspace(tpc_ctx* ctx, void* dev_ptr, size_t bytes,
  * kernel: a row >= 152, a non-finite coordinate or offsets that are not
  * non-decreasing from 0 to n set TPC_ERR_INPUT in the status word (detail:
  * the cluster index, or -1 / -2 / -3 for the first offset, the last offset,
- * the order).  The find kernels are not guarded against such input and may
- * access memory out of bounds on it: a caller that cannot vouch for its
- * input reads the status (tpc_get_stats) after this call and before
- * tpc_find_tracks.  TPC_ERR_CAPACITY if n or n_events exceed the
- * workspace. */
+ * the order).  A rejected batch is never indexed: every later kernel that
+ * reads clusters or offsets checks the rejection on the device and returns
+ * at once, so tpc_find_tracks yields no tracks (n_tracks_dev 0, every
+ * track_of_cluster -1, trk_off all 0, trk_hits untouched), tpc_fit_tracks
+ * reports every track as a failed fit (ndf -1) and the adjoint calls add
+ * nothing.  The rejection holds until the next load.  TPC_ERR_CAPACITY if n
+ * or n_events exceed the workspace. */
 tpc_status tpc_load_clusters(tpc_ctx* ctx, const float* y, const float* z,
                              const uint16_t* row, const uint16_t* charge, int64_t n,
                              const int64_t* evt_sector_off, int32_t n_events,
@@ -291,7 +293,9 @@ tpc_status tpc_stage_times(tpc_ctx* ctx, float* ms_out);
  * (defaults).  Inputs and outputs are as for tpc_load_clusters and
  * tpc_find_tracks (device pointers, caller-owned); status_dev (device int32)
  * receives the device status word of this call (TPC_OK, or e.g.
- * TPC_ERR_INPUT / TPC_ERR_CAPACITY found by the kernels).
+ * TPC_ERR_INPUT / TPC_ERR_CAPACITY found by the kernels).  Input that fails
+ * validation is not indexed: the call then returns no tracks, as
+ * tpc_find_tracks does after a rejected load.
  *
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call

@@ -60,6 +60,7 @@ __global__ void __launch_bounds__(128) k_adjoint(
     const int64_t* __restrict__ evt_off, int G, const float* __restrict__ rot_tab,
     const Geo* __restrict__ geo, AdjPrm P, double* chi2_total, double* grad, int32_t* st,
     const double* __restrict__ field, FieldGridD fg, double* grad_field) {
+    if (input_rejected(st)) return;  // clusters that failed validation are not read
     __shared__ double sg[216];
     __shared__ double schi2;
     __shared__ float tab[NSEC * ROT_TAB];

@@ -44,6 +44,26 @@ TPC_HD float sqrt(float a) { return sqrtf(a); }
 
 }  // namespace bits
 
+// ---- input validation (S0)
+
+// One cluster is valid when its pad row exists (row < nrow) and both
+// coordinates are finite.
+TPC_HD bool cluster_valid(uint16_t row, float y, float z, int nrow) {
+    return (int)row < nrow && isfinite(y) && isfinite(z);
+}
+
+// Check g (0 <= g <= G) of the group offsets off[0..G] over n clusters: 0
+// when entry g is consistent, else -1 (off[0] != 0), -2 (off[G] != n) or -3
+// (off[g + 1] < off[g]).  The offsets are a valid partition of [0, n) iff
+// every g passes; then every group's range lies inside [0, n).
+TPC_HD int offset_check(const int64_t* off, int G, int64_t n, int g) {
+    const int64_t o = off[g];
+    if (g == 0 && o != 0) return -1;
+    if (g == G && o != n) return -2;
+    if (g < G && off[g + 1] < o) return -3;
+    return 0;
+}
+
 // ---- neighbour search (S2)
 
 // window test, FP32, one rounding per operation

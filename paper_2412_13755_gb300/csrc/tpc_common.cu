@@ -21,14 +21,11 @@ __global__ void k_validate(const float* __restrict__ y, const float* __restrict_
                            const int64_t* __restrict__ off, int G, int32_t* st) {
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (tid <= G) {
-        const int64_t o = off[tid];
-        if (tid == 0 && o != 0) set_status(st, TPC_ERR_INPUT, -1);
-        if (tid == G && o != n) set_status(st, TPC_ERR_INPUT, -2);
-        if (tid < G && off[tid + 1] < o) set_status(st, TPC_ERR_INPUT, -3);
+        const int bad = offset_check(off, G, n, (int)tid);
+        if (bad) reject_input(st, bad);
     }
     for (int64_t i = tid; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        if (row[i] >= NROW || !isfinite(y[i]) || !isfinite(z[i]))
-            set_status(st, TPC_ERR_INPUT, (int)(i & 0x7fffffff));
+        if (!cluster_valid(row[i], y[i], z[i], NROW)) reject_input(st, (int)(i & 0x7fffffff));
     }
 }
 
@@ -152,6 +149,8 @@ cudaError_t validate_clusters(const tpc_ctx* c, cudaStream_t s) {
     const int G = c->n_events * NSEC;
     const int64_t work = std::max<int64_t>(c->n, G + 1);
     const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, 152 * 8));
+    const cudaError_t e = fill_i32(c->ws.at<int32_t>(c->ws.L.status) + ST_INPUT_BAD, 1, 0, s);
+    if (e != cudaSuccess) return e;
     tpc::LaunchCount{}, k_validate<<<(unsigned)blocks, 256, 0, s>>>(c->y, c->z, c->row, c->n, c->evt_sector_off, G,
                                                 c->ws.at<int32_t>(c->ws.L.status));
     return cudaGetLastError();

@@ -19,6 +19,19 @@ __device__ __forceinline__ void set_status(int32_t* st, int code, int detail) {
     if (atomicCAS(&st[ST_STATUS], 0, code) == 0) atomicExch(&st[ST_DETAIL], detail);
 }
 
+// The loaded batch failed validation (rows, offsets, finite coordinates).
+// Every kernel that reads clusters or their offsets returns early on such
+// a batch, so that nothing is indexed from invalid input.  The flag is its
+// own slot: the status word keeps the first error of a context, which may
+// predate the load.
+__device__ __forceinline__ bool input_rejected(const int32_t* st) {
+    return *reinterpret_cast<const volatile int32_t*>(&st[ST_INPUT_BAD]) != 0;
+}
+__device__ __forceinline__ void reject_input(int32_t* st, int detail) {
+    set_status(st, TPC_ERR_INPUT, detail);
+    atomicExch(&st[ST_INPUT_BAD], 1);
+}
+
 // largest g with off[g] <= i (off non-decreasing, off[0] = 0)
 TPC_HD int group_of(const int64_t* __restrict__ off, int G, int64_t i) {
     int lo = 0, hi = G;  // answer in [lo, hi)

@@ -106,7 +106,9 @@ __device__ __forceinline__ void cell_run(const Cells& cells, const CellWin& w, i
 
 // ---------------------------------------------------------------- S1 ------
 __global__ void k_zrange(const float* __restrict__ z, int64_t n, const int64_t* __restrict__ off,
-                         int G, uint32_t* zmin_u, uint32_t* zmax_u, int32_t* grp_of) {
+                         int G, uint32_t* zmin_u, uint32_t* zmax_u, int32_t* grp_of,
+                        const int32_t* __restrict__ st) {
+    if (input_rejected(st)) return;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int g = group_of(off, G, i);
@@ -129,6 +131,7 @@ __global__ void __launch_bounds__(1024) k_cells(const int64_t* __restrict__ off,
                                                 const uint32_t* zmin_u, const uint32_t* zmax_u,
                                                 float* zmin, float* inv, int32_t* nz,
                                                 int32_t* kbase, int64_t Kcap, int32_t* st) {
+    if (input_rejected(st)) return;
     __shared__ int32_t sh[32];
     __shared__ int64_t carry_s;
     if (threadIdx.x == 0) carry_s = 0;
@@ -192,7 +195,9 @@ __global__ void __launch_bounds__(1024) k_cells(const int64_t* __restrict__ off,
 __global__ void __launch_bounds__(1024) k_tl_bins(const int64_t* __restrict__ off, int G,
                                                   const uint32_t* zmin_u, const uint32_t* zmax_u,
                                                   float* zmin, float* inv, int32_t* nb,
-                                                  int32_t* base) {
+                                                  int32_t* base,
+                        const int32_t* __restrict__ st) {
+    if (input_rejected(st)) return;
     __shared__ int32_t sh[32];
     __shared__ int64_t carry_s;
     if (threadIdx.x == 0) carry_s = 0;
@@ -247,14 +252,16 @@ __global__ void __launch_bounds__(1024) k_tl_bins(const int64_t* __restrict__ of
 __global__ void k_hist(const float* __restrict__ y, const float* __restrict__ z,
                        const uint16_t* __restrict__ row, int64_t n,
                        const int32_t* __restrict__ grp_of, Cells cells, const Geo* __restrict__ geo,
-                       int32_t* cnt, int32_t* key_in, int32_t* slot_in, int64_t Kcap) {
+                       int32_t* cnt, int32_t* key_in, int32_t* slot_in, int64_t Kcap,
+                        const int32_t* __restrict__ st) {
+    if (input_rejected(st)) return;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int g = grp_of[i];
         const int r = row[i];
         const int key = cells.kbase[g] + (r * cells.nz[g] + zcell(cells, g, z[i])) * CELL_NY + ycell(geo, r, y[i]);
         int slot = 0;
-        if (key < Kcap) slot = atomicAdd(&cnt[key], 1);
+        if (key >= 0 && key < Kcap) slot = atomicAdd(&cnt[key], 1);
         key_in[i] = key;
         slot_in[i] = slot;
     }
@@ -265,11 +272,13 @@ __global__ void k_scatter(const float* __restrict__ y, const float* __restrict__
                           const int32_t* __restrict__ grp_of,
                           const int32_t* __restrict__ key_in, const int32_t* __restrict__ slot_in,
                           const int32_t* __restrict__ cell_off, int64_t Kcap, float2* yzb,
-                          int32_t* orig, int32_t* grpb, uint8_t* rowb) {
+                          int32_t* orig, int32_t* grpb, uint8_t* rowb,
+                        const int32_t* __restrict__ st) {
+    if (input_rejected(st)) return;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int key = key_in[i];
-        if (key >= Kcap) continue;
+        if (key < 0 || key >= Kcap) continue;
         const int64_t pos = cell_off[key] + slot_in[i];
         yzb[pos] = make_float2(y[i], z[i]);
         orig[pos] = (int32_t)i;
@@ -386,6 +395,7 @@ __global__ void __launch_bounds__(ns_warps<NG>() * 32) k_neighbours_sub(
     int32_t* choice_dn, int32_t* choice_up, float* d2out, int32_t* st, int32_t* ovf_queue,
     int32_t* next_queue, int next_slot, const int32_t* __restrict__ in_queue_b, int in_slot_b,
     int sum_lo_b) {
+    if (input_rejected(st)) return;
     constexpr int GPW = 32 / NG;  // clusters per warp
     __shared__ NsLists sh_all[ns_warps<NG>() * GPW];
     const int lane = threadIdx.x & 31;
@@ -534,6 +544,7 @@ __global__ void __launch_bounds__(256, 4) k_neighbours_first(
     const uint8_t* __restrict__ rowb, Cells cells, const Geo* __restrict__ geo, NbPrm P,
     int32_t* choice_dn, int32_t* choice_up, float* d2out, int32_t* st, int32_t* dense_queue,
     int32_t* next_queue, int next_slot) {
+    if (input_rejected(st)) return;
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
          c += (int64_t)gridDim.x * blockDim.x) {
         const int g = grpb[c], r = rowb[c];
@@ -621,6 +632,7 @@ __global__ void __launch_bounds__(NB_WARPS * 32) k_neighbours_warp(
     const int32_t* __restrict__ orig, const int32_t* __restrict__ grpb,
     const uint8_t* __restrict__ rowb, Cells cells, const Geo* __restrict__ geo, NbPrm P,
     int32_t* choice_dn, int32_t* choice_up, float* d2out) {
+    if (input_rejected(st)) return;
     __shared__ NbLists sh_all[NB_WARPS];
     NbLists& sh = sh_all[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
@@ -749,7 +761,9 @@ __device__ __forceinline__ uint64_t claim_key(float d2, int32_t orig) {
 // endpoints without a triplet of their own accept their best claimant
 __global__ void k_claims(int64_t n, const int32_t* __restrict__ cdn, const int32_t* __restrict__ cup,
                          const float* __restrict__ d2, const int32_t* __restrict__ orig,
-                         unsigned long long* claim_up, unsigned long long* claim_dn) {
+                         unsigned long long* claim_up, unsigned long long* claim_dn,
+                        const int32_t* __restrict__ st) {
+    if (input_rejected(st)) return;
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
          c += (int64_t)gridDim.x * blockDim.x) {
         const int u = cup[c], d = cdn[c];
@@ -765,7 +779,9 @@ __global__ void k_links(int64_t n, const int32_t* __restrict__ cdn, const int32_
                         const float* __restrict__ d2, const int32_t* __restrict__ orig,
                         const unsigned long long* __restrict__ claim_up,
                         const unsigned long long* __restrict__ claim_dn, int32_t* link_dn,
-                        int32_t* link_up) {
+                        int32_t* link_up,
+                        const int32_t* __restrict__ st) {
+    if (input_rejected(st)) return;
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
          c += (int64_t)gridDim.x * blockDim.x) {
         const int u = cup[c], d = cdn[c];
@@ -793,6 +809,7 @@ __global__ void k_chains(int64_t n, const int32_t* __restrict__ link_dn,
                          const int32_t* __restrict__ grpb, const uint8_t* __restrict__ rowb, int n_seg,
                          int64_t Scap, int32_t* seg_start, int32_t* seg_grp, int32_t* seg_canon,
                          int32_t* tl_rowhit, uint4* tl_mask, int32_t* st) {
+    if (input_rejected(st)) return;
     // warp-uniform loop: a warp takes 32 consecutive clusters, and the
     // slots of its chains are consecutive (one atomic per warp), so the slot
     // order follows the binned order of the chain starts within a warp
@@ -907,6 +924,7 @@ __global__ void __launch_bounds__(128, 4) k_tracklet_lanes(
     Cells cells, const Geo* __restrict__ geo, TlPrm P, int64_t Scap, int32_t* st, int32_t* tl_rowhit,
     const uint4* __restrict__ tl_mask, int32_t* tl_n, unsigned long long* tl_key, float* tl_state,
     int32_t* tl_ok, int4* gs_meta, int tile) {
+    if (input_rejected(st)) return;
     const int nitems = min((int64_t)st[count_slot], Scap);
     int32_t* queue = &st[refit ? ST_Q_REFIT : ST_Q_BUILD];
     int s = -1, item = 0, phase = 0, r = 0, rmin = 0, rmax = 0, n = 0, misses = 0, g = 0, sector = 0, ok = 0;
@@ -1145,6 +1163,7 @@ __global__ void __launch_bounds__(128, 4) k_tracklet_lanes(
 // every cluster belongs to the best tracklet containing it
 __global__ void k_owner(const int32_t* __restrict__ tl_rowhit, const unsigned long long* __restrict__ tl_key,
                         int64_t Scap, const int32_t* st, unsigned long long* owner) {
+    if (input_rejected(st)) return;
     const int nseg = min((int64_t)st[ST_NSEG], Scap);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)nseg * NROW;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -1163,6 +1182,7 @@ __global__ void k_keep(int32_t* tl_rowhit, const unsigned long long* __restrict_
                        int32_t* tl_rmin, int32_t* tl_rmax, float* tl_zin, float* tl_zout,
                        int32_t* tl_ok, int32_t* grp_tl_cnt, TlBins tb, int32_t* tl_binkey,
                        int64_t KT, uint4* tl_mask) {
+    if (input_rejected(st)) return;
     const int nseg = min((int64_t)st[ST_NSEG], Scap);
     const int lane = threadIdx.x & 31;
     const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -1230,6 +1250,7 @@ __global__ void k_tl_scatter(const int32_t* __restrict__ tl_keep, const int32_t*
                              const float* __restrict__ tl_zin, const float* __restrict__ tl_zout,
                              int4* gs_meta,
                              const int32_t* __restrict__ tl_binkey, int32_t* st_w) {
+    if (input_rejected(st)) return;
     const int nseg = min((int64_t)st[ST_NSEG], Scap);
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nseg; s += gridDim.x * blockDim.x) {
         if (!tl_keep[s]) continue;
@@ -1267,6 +1288,7 @@ __global__ void __launch_bounds__(256, 4) k_merge_cand(
     const int32_t* __restrict__ grp_tl_off, const int4* __restrict__ gs_meta,
     const Geo* __restrict__ geo, MgPrm P, int32_t* st, int32_t* cand_n, int32_t* cand_a,
     float* cand_c2, TlBins tb, int32_t* match_act) {
+    if (input_rejected(st)) return;
     // The cheap gates (row gap, z, and the 1-d chi2 of tan lambda and q/pT,
     // which the transport and the frame rotation leave unchanged) run over
     // every A in the bins; the A that pass are collected in the warp's list
@@ -1441,6 +1463,7 @@ __global__ void __cluster_dims__(MATCH_CTAS, 1, 1) __launch_bounds__(1024) k_mat
     const float* __restrict__ cand_c2, const int32_t* __restrict__ tl_canon, int64_t Scap,
     int32_t* st, unsigned long long* best_a, unsigned long long* best_b, int32_t* nxt,
     int32_t* prv, int32_t* act) {
+    if (input_rejected(st)) return;
     // An (a, b) pair whose key (chi2, canonical ids) is the smallest of every
     // live pair at a and of every live pair at b is matched; both ends are
     // then used.  The rounds run over a compacted list of the B ends that
@@ -1534,6 +1557,7 @@ __global__ void k_track_heads(const int32_t* __restrict__ tl_keep, const int32_t
                               const int32_t* __restrict__ tl_rowhit, int n_min, int64_t Scap,
                               const int32_t* st, int32_t* trk_flag, int32_t* trk_len_at,
                               int32_t* trk_head_at) {
+    if (input_rejected(st)) return;
     const int nseg = min((int64_t)st[ST_NSEG], Scap);
     const int lane = threadIdx.x & 31;
     const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -1560,6 +1584,10 @@ __global__ void k_track_len(int64_t n, const int32_t* __restrict__ trk_flag,
                             const int32_t* __restrict__ trk_head_at, int32_t track_cap,
                             int32_t* len_by_rank, int32_t* head_by_rank, int32_t* st,
                             int32_t* n_tracks_dev) {
+    if (input_rejected(st)) {  // rejected input: no tracks
+        if (blockIdx.x == 0 && threadIdx.x == 0) *n_tracks_dev = 0;
+        return;
+    }
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         if (!trk_flag[i]) continue;
@@ -1584,6 +1612,7 @@ __global__ void k_track_write(const int32_t* __restrict__ st_r, int32_t track_ca
                               const int32_t* __restrict__ tl_rowhit, const int32_t* __restrict__ orig,
                               const int32_t* __restrict__ trk_off, int64_t n, int32_t* toc,
                               int32_t* trk_hits, int32_t* st_w) {
+    if (input_rejected(st_r)) return;
     const int lane = threadIdx.x & 31;
     const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -1653,7 +1682,7 @@ cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hi
     tpc::LaunchCount{}, k_fill_u32<<<grid_for(G), TPB, 0, s>>>(W.at<uint32_t>(L.g_zmax_u), G, 0u);
     int32_t* grp_of = W.at<int32_t>(L.d2);  // group of every input cluster (d2 is free in S1)
     tpc::LaunchCount{}, k_zrange<<<grid_for(n), TPB, 0, s>>>(c->z, n, c->evt_sector_off, G, W.at<uint32_t>(L.g_zmin_u),
-                                         W.at<uint32_t>(L.g_zmax_u), grp_of);
+                                         W.at<uint32_t>(L.g_zmax_u), grp_of, st);
     tpc::LaunchCount{}, k_cells<<<1, 1024, 0, s>>>(c->evt_sector_off, G, W.at<uint32_t>(L.g_zmin_u),
                                W.at<uint32_t>(L.g_zmax_u), W.at<float>(L.g_zmin), W.at<float>(L.g_inv),
                                W.at<int32_t>(L.g_nz), W.at<int32_t>(L.g_kbase), L.K, st);
@@ -1662,7 +1691,7 @@ cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hi
     TPC_TRY(fill_i32(W.at<int32_t>(L.cell_cnt), L.K + 1, 0, s));
     tpc::LaunchCount{}, k_hist<<<grid_for(n), TPB, 0, s>>>(c->y, c->z, c->row, n, grp_of, cells, geo,
                                        W.at<int32_t>(L.cell_cnt), W.at<int32_t>(L.key_in),
-                                       W.at<int32_t>(L.slot_in), L.K);
+                                       W.at<int32_t>(L.slot_in), L.K, st);
     TPC_TRY(scan_i32(W.at<int32_t>(L.cell_cnt), W.at<int32_t>(L.cell_off), L.K, scan_tmp, s));
     float2* yzb = W.at<float2>(L.yzb);
     int32_t* orig = W.at<int32_t>(L.orig);
@@ -1670,7 +1699,7 @@ cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hi
     uint8_t* rowb = W.at<uint8_t>(L.rowb);
     tpc::LaunchCount{}, k_scatter<<<grid_for(n), TPB, 0, s>>>(c->y, c->z, c->row, n, grp_of,
                                           W.at<int32_t>(L.key_in), W.at<int32_t>(L.slot_in),
-                                          W.at<int32_t>(L.cell_off), L.K, yzb, orig, grpb, rowb);
+                                          W.at<int32_t>(L.cell_off), L.K, yzb, orig, grpb, rowb, st);
     TPC_TRY(cudaGetLastError());
 
     c->mark(1, s);
@@ -1698,12 +1727,12 @@ cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hi
     auto* claim_dn = W.at<unsigned long long>(L.claim_dn);
     tpc::LaunchCount{}, k_fill_u64<<<grid_for(n), TPB, 0, s>>>(claim_up, n, KEY_MAX);
     tpc::LaunchCount{}, k_fill_u64<<<grid_for(n), TPB, 0, s>>>(claim_dn, n, KEY_MAX);
-    tpc::LaunchCount{}, k_claims<<<grid_for(n), TPB, 0, s>>>(n, cdn, cup, d2, orig, claim_up, claim_dn);
+    tpc::LaunchCount{}, k_claims<<<grid_for(n), TPB, 0, s>>>(n, cdn, cup, d2, orig, claim_up, claim_dn, st);
     int32_t* ldn = W.at<int32_t>(L.link_dn);
     int32_t* lup = W.at<int32_t>(L.link_up);
     TPC_TRY(fill_i32(ldn, n, -1, s));
     TPC_TRY(fill_i32(lup, n, -1, s));
-    tpc::LaunchCount{}, k_links<<<grid_for(n), TPB, 0, s>>>(n, cdn, cup, d2, orig, claim_up, claim_dn, ldn, lup);
+    tpc::LaunchCount{}, k_links<<<grid_for(n), TPB, 0, s>>>(n, cdn, cup, d2, orig, claim_up, claim_dn, ldn, lup, st);
 
     c->mark(3, s);
     // S3: chains
@@ -1747,7 +1776,7 @@ cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hi
     tpc::LaunchCount{}, k_tl_bins<<<1, 1024, 0, s>>>(c->evt_sector_off, G, W.at<uint32_t>(L.g_zmin_u),
                                                    W.at<uint32_t>(L.g_zmax_u), W.at<float>(L.tb_zmin),
                                                    W.at<float>(L.tb_inv), W.at<int32_t>(L.tb_nb),
-                                                   W.at<int32_t>(L.tb_base));
+                                                   W.at<int32_t>(L.tb_base), st);
     TPC_TRY(fill_i32(grp_cnt, L.KT + 1, 0, s));
     tpc::LaunchCount{}, k_keep<<<grid_for(L.S * 32, 128), 128, 0, s>>>(tl_rowhit, tl_key, owner, W.at<int32_t>(L.seg_grp), yzb,
                                  orig, p.n_seg, L.S, st, W.at<int32_t>(L.tl_keep),

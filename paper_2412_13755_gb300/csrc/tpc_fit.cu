@@ -14,7 +14,10 @@ __global__ void __launch_bounds__(128) k_fit(
     const int32_t* __restrict__ n_tracks_dev, const float* __restrict__ y,
     const float* __restrict__ z, const uint16_t* __restrict__ row,
     const int64_t* __restrict__ evt_off, int G, const Geo* __restrict__ geo, FitPrm P,
-    float* params, float* cov, float* chi2o, int32_t* ndfo) {
+    float* params, float* cov, float* chi2o, int32_t* ndfo, const int32_t* __restrict__ st) {
+    // clusters that failed validation are not read: every track reports a
+    // failed fit
+    const bool rejected = input_rejected(st);
     int T = n_tracks;
     if (n_tracks_dev) T = min(T, *n_tracks_dev);
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x) {
@@ -22,7 +25,7 @@ __global__ void __launch_bounds__(128) k_fit(
         KF s;
         NSum chi2;
         ff Cf[15];
-        const bool ok = fit_track(trk_hits + b, n, y, z, row, evt_off, G, geo, P, s, Cf, chi2);
+        const bool ok = !rejected && fit_track(trk_hits + b, n, y, z, row, evt_off, G, geo, P, s, Cf, chi2);
         float* po = params + (int64_t)t * 5;
         float* co = cov + (int64_t)t * 15;
         if (ok) {
@@ -65,7 +68,8 @@ cudaError_t run_fit(tpc_ctx* c, const int32_t* trk_off, const int32_t* trk_hits,
     c->mark(10, s);
     tpc::LaunchCount{}, k_fit<<<(unsigned)blocks, 128, 0, s>>>(trk_off, trk_hits, n_tracks, n_tracks_dev, c->y, c->z,
                                            c->row, c->evt_sector_off, c->n_events * NSEC,
-                                           c->ws.at<Geo>(c->ws.L.geo), fp, params, cov, chi2, ndf);
+                                           c->ws.at<Geo>(c->ws.L.geo), fp, params, cov, chi2, ndf,
+                                           c->ws.at<int32_t>(c->ws.L.status));
     c->mark(11, s);
     return cudaGetLastError();
 }

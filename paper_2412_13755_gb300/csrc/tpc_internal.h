@@ -71,7 +71,9 @@ inline Geo make_geo() {
 enum StatusSlot {
     ST_STATUS = 0, ST_DETAIL, ST_NSEG, ST_NTL, ST_NCAND, ST_NMERGE, ST_NTRACKS, ST_FP64,
     ST_MATCH_LIVE, ST_Q_BUILD, ST_Q_REFIT, ST_NB_Q3, ST_KFSTEPS = 12 /* 64-bit: slots 12-13 */,
-    ST_NB_OVF = 14, ST_NB_Q2 = 15, ST_N_SLOTS = 16
+    ST_NB_OVF = 14, ST_NB_Q2 = 15,
+    ST_INPUT_BAD = 16,  // nonzero when the last validated batch was rejected
+    ST_N_SLOTS = 17
 };
 
 // Workspace layout: byte offsets of every buffer, computed from capacities.

@@ -112,7 +112,45 @@ static void check_triplets() {
     CHECK(passed > 1000 && cut > 1000, "both outcomes exercised");
 }
 
+// S0 validation: the per-entry offset checks all pass exactly when the
+// offsets partition [0, n) (first 0, last n, non-decreasing), and a valid
+// partition keeps every group's range inside [0, n); the cluster check
+// rejects rows past the last and every non-finite coordinate.
+static void check_validation() {
+    for (int trial = 0; trial < 20000; ++trial) {
+        const int G = 1 + (int)(next_u64() % 40);
+        int64_t off[64];
+        int64_t n = 0;
+        off[0] = 0;
+        for (int g = 0; g < G; ++g) off[g + 1] = off[g] + (int64_t)(next_u64() % 5);
+        n = off[G];
+        const int kind = (int)(next_u64() % 4);  // 0: valid; 1-3: one entry perturbed
+        if (kind > 0) {
+            const int g = (int)(next_u64() % (G + 1));
+            off[g] += (int64_t)(next_u64() % 7) - 3;
+        }
+        if (next_u64() % 8 == 0) n += (int64_t)(next_u64() % 3) - 1;
+        bool def = off[0] == 0 && off[G] == n;
+        for (int g = 0; g < G; ++g) def = def && off[g + 1] >= off[g];
+        bool pass = true;
+        for (int g = 0; g <= G; ++g) pass = pass && offset_check(off, G, n, g) == 0;
+        CHECK(pass == def, "offset check %d vs definition %d (G %d)", (int)pass, (int)def, G);
+        if (pass)
+            for (int g = 0; g < G; ++g) CHECK(off[g] >= 0 && off[g + 1] <= n, "group %d outside [0, n)", g);
+    }
+    const float inf = INFINITY, nan = NAN;
+    CHECK(cluster_valid(0, 1.f, -2.f, 152), "row 0");
+    CHECK(cluster_valid(151, 1e30f, -1e30f, 152), "row 151");
+    CHECK(!cluster_valid(152, 1.f, 1.f, 152), "row 152");
+    CHECK(!cluster_valid(65535, 1.f, 1.f, 152), "row 65535");
+    CHECK(!cluster_valid(3, nan, 1.f, 152), "NaN y");
+    CHECK(!cluster_valid(3, 1.f, nan, 152), "NaN z");
+    CHECK(!cluster_valid(3, inf, 1.f, 152), "inf y");
+    CHECK(!cluster_valid(3, 1.f, -inf, 152), "-inf z");
+}
+
 int main() {
+    check_validation();
     check_masks();
     check_triplets();
     if (failures == 0) std::printf("ok\n");

@@ -104,3 +104,37 @@ def test_shuffled_groups_agree_with_oracle(orc):
     agree = np.mean(gc == oc)
     print(f"shuffled: agreement {agree:.6f}")
     assert agree >= 0.9999
+
+
+def test_find_after_rejected_load_returns_no_tracks():
+    """Without the host-side check: every find and fit kernel sees the
+    load's rejection on the device and returns before reading the batch.
+    The validation reads only the batch's own n clusters and offsets, and
+    the guarded kernels read nothing derived from them, so these runs stay
+    in bounds by construction (the guard is checked on CPU first)."""
+    ev = synth.one_sector()
+    tr = tpc.Tracker(ev.n, 1)
+    cap = ev.n // 10 + 16
+    for name, y, z, row, off, details in _malformed(ev):
+        d = (torch.from_numpy(y).cuda(), torch.from_numpy(z).cuda(),
+             torch.from_numpy(row.view(np.int16)).cuda().view(torch.uint16), torch.from_numpy(off).cuda())
+        tr.load(*d, 1)
+        toc, trk_off, hits, ntd = tr.alloc_find_outputs(cap)
+        toc.fill_(7)
+        trk_off.fill_(7)
+        ntd.fill_(7)
+        tr.find(out=(toc, trk_off, hits, ntd))
+        par, cov, chi2, ndf = tr.fit(trk_off, hits, cap, None)
+        torch.cuda.synchronize()
+        st = tr.stats()
+        assert st.status == tpc.TPC_ERR_INPUT and st.status_detail in details, (name, st.status_detail)
+        assert int(ntd.item()) == 0, name
+        assert bool((toc == -1).all()) and bool((trk_off == 0).all()), name
+        assert bool((ndf == -1).all()), name
+        tr.reset_status()
+    d = to_dev(ev)
+    tr.load(*d, 1)
+    out = tr.find()
+    torch.cuda.synchronize()
+    tr.check()
+    assert int(out[3].item()) > 100

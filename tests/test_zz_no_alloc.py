@@ -3,10 +3,12 @@
 The no-allocation entry point is for callers that may not reserve device
 memory (their memory belongs to another allocator, or a cudaMalloc's implicit
 synchronisation is not acceptable); its scratch is a fixed array inside the
-library image.  Called twice in a row on different events through the C ABI,
+library image.  Called three times in a row on different events through the C ABI,
 it must return exactly what the regular entry point returns (integer outputs:
 assignment, offsets, hit lists and the track count are compared bit for bit),
-with a clean device status.  This file is collected last on purpose.
+with a clean device status.  A third, smaller call follows the larger one,
+so that contents a larger call leaves in the shared array cannot leak into a
+later result unnoticed.  This file is collected last on purpose.
 """
 import ctypes as C
 
@@ -45,14 +47,17 @@ def _noalloc(lib, ev, track_cap):
 def test_noalloc_matches_find_tracks_twice():
     lib = tpc.load_library()
     lib.tpc_find_tracks_noalloc.restype = C.c_int
+    # a larger batch followed by a smaller one: what the larger call left in
+    # the shared array must not leak into the smaller call's result
     events = [synth.one_sector(seed=synth.SEED_BASE + 50),
-              synth.uneven_batch(n_events=3, lo=20, hi=120, seed=synth.SEED_BASE + 51)]
+              synth.uneven_batch(n_events=3, lo=20, hi=120, seed=synth.SEED_BASE + 51),
+              synth.one_sector(n_tracks=20, seed=synth.SEED_BASE + 52)]
     for ev in events:
         assert ev.n <= 65536 and ev.n_events <= 4
         g_toc, g_off, g_hits, _, _ = gpu_find(ev)
         cap = max(16, ev.n // 10 + 16)
         n_toc, n_off, n_hits = _noalloc(lib, ev, cap)
-        assert len(g_off) > 20
+        assert len(g_off) > 3
         assert np.array_equal(n_toc, g_toc)
         assert np.array_equal(n_off, g_off)
         assert np.array_equal(n_hits, g_hits)
