@@ -444,7 +444,9 @@ class Tracker:
         """Outputs of find for the loaded batch; before a load, for the
         largest batch the context takes (max_clusters)."""
         m = max(self.n if self.n > 0 else self.max_clusters, 1)
-        cap = int(track_cap if track_cap is not None else m // 10 + 16)
+        # the context takes at most max_clusters tracks (a track has >= 1
+        # cluster); small batches get that bound instead of n/10 + 16
+        cap = int(track_cap if track_cap is not None else min(m // 10 + 16, max(self.max_clusters, 1)))
         dev = self.device
         return (torch.empty(m, dtype=torch.int32, device=dev),
                 torch.empty(cap + 1, dtype=torch.int32, device=dev),

@@ -196,3 +196,21 @@ def test_tracker_methods(stub):
     tr.stage_times()
     assert "tpc_autotune" in stub.calls and "tpc_fit_adjoint_field" in stub.calls
     tr.ctx = None  # nothing to destroy
+
+
+def test_default_track_capacity_fits_small_contexts(stub):
+    """The default track capacity never exceeds what the context takes
+    (max_clusters tracks): a 12-cluster batch gets 12, not 12 // 10 + 16."""
+    tr = object.__new__(tpc.Tracker)
+    tr.device = torch.device("cpu")
+    tr.ctx = CTX
+    tr.max_clusters = 12
+    tr.max_events = 1
+    tr.n = 0
+    tr.load(f32(12), f32(12), u16(12), i64(37), 1)
+    toc, trk_off, hits, ntd = tr.alloc_find_outputs()
+    assert trk_off.numel() - 1 <= 12
+    tr.max_clusters = 10_000
+    tr.n = 5000
+    assert tr.alloc_find_outputs()[1].numel() - 1 == 5000 // 10 + 16
+    tr.ctx = None
