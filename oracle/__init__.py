@@ -77,6 +77,7 @@ def lib():
         _lib.orc_find_tracks.restype = C.c_int64
         _lib.orc_bruteforce_chains.restype = C.c_int64
         _lib.orc_voxel_of.restype = C.c_int64
+        _lib.orc_tracklet.restype = C.c_int64
     return _lib
 
 
@@ -265,16 +266,51 @@ def bruteforce_chains(y, z, row, sector, params=None, chi2ndf_max=5.0,
     return [hits[off[i]:off[i + 1]].copy() for i in range(k)]
 
 
-def seed(y, z, row, sector_of, hits, first_is_outer=True, params=None):
-    """The fit seed: (x0, frame, p[5]) of a hit list in fit order."""
-    y, z, row = _c(y, np.float32), _c(z, np.float32), _c(row, np.uint16)
+def seed(y, z, row, sector_of, hits, first_is_outer=True, params=None, f64=False):
+    """The fit seed: (x0, frame, p[5]) of a hit list in fit order.  With f64
+    the points are passed in FP64 (pins with exact helix points)."""
+    dt = np.float64 if f64 else np.float32
+    y, z, row = _c(y, dt), _c(z, dt), _c(row, np.uint16)
     sec = _c(sector_of, np.int32)
     hits = _c(hits, np.int32)
     prm = params or default_params()
     x0 = C.c_double(0.0); fr = C.c_int32(0); p = np.empty(5)
-    rc = lib().orc_seed(_p(y), _p(z), _p(row), _p(sec), _p(hits), C.c_int32(hits.shape[0]),
+    fn = lib().orc_seed_f64 if f64 else lib().orc_seed
+    rc = fn(_p(y), _p(z), _p(row), _p(sec), _p(hits), C.c_int32(hits.shape[0]),
                         C.c_int(1 if first_is_outer else 0), C.byref(prm), C.byref(x0),
                         C.byref(fr), _p(p))
     if rc != 0:
         raise ValueError("seed needs >= 3 clusters")
     return x0.value, fr.value, p
+
+
+def tracklet(y, z, row, beg, end, sector, seg_hits, params=None):
+    """S3b of one segment (hits outermost first) inside the group [beg, end)
+    of one sector: the tracklet the find builds from it, outermost first."""
+    y, z, row = _c(y, np.float32), _c(z, np.float32), _c(row, np.uint16)
+    seg = _c(seg_hits, np.int32)
+    prm = params or default_params()
+    cap = 4 * 152
+    out = np.empty(cap, np.int32)
+    k = lib().orc_tracklet(_p(y), _p(z), _p(row), C.c_int64(beg), C.c_int64(end), C.c_int32(sector),
+                           _p(seg), C.c_int32(seg.shape[0]), C.byref(prm), _p(out), C.c_int32(cap))
+    if k < 0:
+        raise ValueError("orc_tracklet refused its arguments")
+    return out[:k].copy()
+
+
+def merge_chi2(y, z, row, hits_a, sec_a, hits_b, sec_b, params=None):
+    """S4 of an inner segment A and an outer segment B (hits outermost
+    first): (chi2_5, accepted by the merge's gates and cut), or None when a
+    fit or the move fails."""
+    y, z, row = _c(y, np.float32), _c(z, np.float32), _c(row, np.uint16)
+    a, b = _c(hits_a, np.int32), _c(hits_b, np.int32)
+    prm = params or default_params()
+    c2 = C.c_double(0.0)
+    ok = C.c_int32(0)
+    rc = lib().orc_merge_chi2(_p(y), _p(z), _p(row), _p(a), C.c_int32(a.shape[0]), C.c_int32(sec_a),
+                              _p(b), C.c_int32(b.shape[0]), C.c_int32(sec_b), C.byref(prm),
+                              C.byref(c2), C.byref(ok))
+    if rc == 1:
+        raise ValueError("orc_merge_chi2 refused its arguments")
+    return None if rc != 0 else (c2.value, bool(ok.value))

@@ -299,7 +299,8 @@ void local_to_frame(int from, double x, double y, int to, double& xo, double& yo
 }
 
 // hits in fit order (first = start of the fit)
-Seed make_seed(const float* y, const float* z, const uint16_t* row, const int32_t* sec,
+template <class F>
+Seed make_seed(const F* y, const F* z, const uint16_t* row, const int32_t* sec,
                const int32_t* hits, int n, bool first_is_outer, const orc_params& prm) {
     Seed sd;
     const int h0 = hits[0], hm = hits[n / 2], hl = hits[n - 1];
@@ -653,6 +654,81 @@ struct MergePair {
     int a, b;  // segment indices: a inner, b outer
 };
 
+// S3b for one segment (hits outermost first): inward fit and inward
+// extension; the final inward-filtered state, moved to the outermost hit
+// row, starts the outward extension.  Without process noise that state
+// carries every hit (the move is exact), so it stands for an outward fit
+// over all of them; the outward fit itself is used only when the inward fit
+// or that move fails.  Returns the tracklet's hits, outermost first.
+std::vector<int32_t> build_tracklet(const float* y, const float* z, const uint16_t* row,
+                                    const int32_t* sec, const std::vector<std::vector<int32_t>>& rows,
+                                    const Segment& sg, const orc_params& prm) {
+    auto no_align = [](int) -> const double* { return nullptr; };
+    std::vector<int32_t> H = sg.hits;
+    double p[5], C[15], chi2, x;
+    bool have_out = false;
+    if (kf_fit<double>(y, z, row, sec, H.data(), (int)H.size(), true, prm, no_align, p, C, chi2, &x)) {
+        std::vector<int32_t> add;
+        extend_tracklet(y, z, rows, sg.sector, x, p, C, row[H.back()] - 1, -1, prm, add);
+        H.insert(H.end(), add.begin(), add.end());
+        have_out = move_to_row(x, p, C, sg.sector, row[H.front()], prm);
+    }
+    if (!have_out) {
+        std::vector<int32_t> rev(H.rbegin(), H.rend());
+        have_out = kf_fit<double>(y, z, row, sec, rev.data(), (int)rev.size(), false, prm, no_align, p, C,
+                                  chi2, &x);
+    }
+    if (have_out) {
+        std::vector<int32_t> add;
+        extend_tracklet(y, z, rows, sg.sector, x, p, C, row[H.front()] + 1, +1, prm, add);
+        std::vector<int32_t> H2(add.rbegin(), add.rend());
+        H2.insert(H2.end(), H.begin(), H.end());
+        H.swap(H2);
+    }
+    return H;
+}
+
+// S5 on a tracklet (hits outermost first): inward fit, state at the
+// innermost hit; the state at the outermost hit is that state moved there
+// (the outward fit only when the inward fit or the move fails).
+void fit_segment(const float* y, const float* z, const uint16_t* row, const int32_t* sec, Segment& s,
+                 const orc_params& prm) {
+    auto no_align = [](int) -> const double* { return nullptr; };
+    double chi2, x;
+    s.ok_in = kf_fit<double>(y, z, row, sec, s.hits.data(), (int)s.hits.size(), true, prm, no_align, s.p_in,
+                             s.c_in, chi2, &x);
+    s.ok_out = false;
+    if (s.ok_in) {
+        for (int k = 0; k < 5; ++k) s.p_out[k] = s.p_in[k];
+        for (int k = 0; k < 15; ++k) s.c_out[k] = s.c_in[k];
+        s.ok_out = move_to_row(x, s.p_out, s.c_out, s.sector, row[s.hits.front()], prm);
+    }
+    if (!s.ok_out) {
+        std::vector<int32_t> rev(s.hits.rbegin(), s.hits.rend());
+        s.ok_out = kf_fit<double>(y, z, row, sec, rev.data(), (int)rev.size(), false, prm, no_align, s.p_out,
+                                  s.c_out, chi2);
+    }
+}
+
+// S4 compatibility of an inner segment A and an outer segment B: A's state
+// at its outermost cluster, moved to B's innermost plane (rotating on a
+// sector change), against B's state there:
+//   chi2_5 = dp^T (C_A + C_B)^-1 dp,  dp = p_B - p_A.
+bool merge_chi2_value(const Segment& A, const Segment& B, const orc_params& prm, double& chi2) {
+    if (!A.ok_out || !B.ok_in) return false;
+    double p[5], C[15], J[25], dX[5];
+    std::memcpy(p, A.p_out, sizeof p);
+    std::memcpy(C, A.c_out, sizeof C);
+    double x = row_x(A.row_max);
+    int frame = A.sector;
+    if (!move_state<double>(x, p, frame, row_x(B.row_min), B.sector, J, dX, prm)) return false;
+    cov_transform(C, J);
+    double dp[5], M[15];
+    for (int i = 0; i < 5; ++i) dp[i] = B.p_in[i] - p[i];
+    for (int i = 0; i < 15; ++i) M[i] = C[i] + B.c_in[i];
+    return chi2_5(dp, M, chi2);
+}
+
 // S4 candidate test: A's outward-fit state at its outermost cluster is moved
 // to B's innermost plane and compared with B's inward-fit state there.
 bool merge_chi2(const Segment& A, const Segment& B, const float* z, const orc_params& prm,
@@ -671,18 +747,7 @@ bool merge_chi2(const Segment& A, const Segment& B, const float* z, const orc_pa
     const float zb = z[B.hits.back()], za = z[A.hits.front()];
     const float dxr = std::fabs(row_xf(B.row_min) - row_xf(A.row_max));
     if (!(std::fabs(zb - za) <= prm.merge_z_slope * dxr + prm.merge_z_margin)) return false;
-    if (!A.ok_out || !B.ok_in) return false;
-    double p[5], C[15], J[25], dX[5];
-    std::memcpy(p, A.p_out, sizeof p);
-    std::memcpy(C, A.c_out, sizeof C);
-    double x = row_x(A.row_max);
-    int frame = A.sector;
-    if (!move_state<double>(x, p, frame, row_x(B.row_min), B.sector, J, dX, prm)) return false;
-    cov_transform(C, J);
-    double dp[5], M[15];
-    for (int i = 0; i < 5; ++i) dp[i] = B.p_in[i] - p[i];
-    for (int i = 0; i < 15; ++i) M[i] = C[i] + B.c_in[i];
-    if (!chi2_5(dp, M, chi2)) return false;
+    if (!merge_chi2_value(A, B, prm, chi2)) return false;
     return chi2 <= prm.chi2_merge;
 }
 
@@ -753,41 +818,12 @@ int64_t orc_find_tracks(const float* y, const float* z, const uint16_t* row, int
     std::vector<int32_t> sec(n);
     for (int g = 0; g < G; ++g)
         for (int64_t i = off[g]; i < off[g + 1]; ++i) sec[i] = g % NSEC;
-    auto no_align = [](int) -> const double* { return nullptr; };
-    // S3b: each segment seeds a tracklet: inward fit + inward extension; the
-    // final inward-filtered state, moved to the outermost hit row, starts the
-    // outward extension.  Without process noise that state carries every hit
-    // (the move is exact), so it stands for an outward fit over all of them;
-    // the outward fit itself is used only when the inward fit or that move
-    // fails.
+    // S3b: each segment seeds a tracklet (build_tracklet)
     std::vector<std::vector<int32_t>> tl_hits(S0);
 #pragma omp parallel for schedule(dynamic, 16) num_threads(nt)
     for (int i = 0; i < S0; ++i) {
         const Segment& sg = seeds[i];
-        const auto& rows = grp_rows[sg.event * NSEC + sg.sector];
-        std::vector<int32_t> H = sg.hits;
-        double p[5], C[15], chi2, x;
-        bool have_out = false;
-        if (kf_fit<double>(y, z, row, sec.data(), H.data(), (int)H.size(), true, prm, no_align, p, C,
-                           chi2, &x)) {
-            std::vector<int32_t> add;
-            extend_tracklet(y, z, rows, sg.sector, x, p, C, row[H.back()] - 1, -1, prm, add);
-            H.insert(H.end(), add.begin(), add.end());
-            have_out = move_to_row(x, p, C, sg.sector, row[H.front()], prm);
-        }
-        if (!have_out) {
-            std::vector<int32_t> rev(H.rbegin(), H.rend());
-            have_out = kf_fit<double>(y, z, row, sec.data(), rev.data(), (int)rev.size(), false, prm, no_align,
-                                      p, C, chi2, &x);
-        }
-        if (have_out) {
-            std::vector<int32_t> add;
-            extend_tracklet(y, z, rows, sg.sector, x, p, C, row[H.front()] + 1, +1, prm, add);
-            std::vector<int32_t> H2(add.rbegin(), add.rend());
-            H2.insert(H2.end(), H.begin(), H.end());
-            H.swap(H2);
-        }
-        tl_hits[i] = std::move(H);
+        tl_hits[i] = build_tracklet(y, z, row, sec.data(), grp_rows[sg.event * NSEC + sg.sector], sg, prm);
     }
     // S3c: every cluster belongs to the best tracklet containing it: more
     // clusters first, then the smaller canonical id of the seed segment.
@@ -819,21 +855,7 @@ int64_t orc_find_tracks(const float* y, const float* z, const uint16_t* row, int
     // the inward fit or the move fails)
 #pragma omp parallel for schedule(dynamic, 16) num_threads(nt)
     for (int i = 0; i < S; ++i) {
-        Segment& s = segs[i];
-        double chi2, x;
-        s.ok_in = kf_fit<double>(y, z, row, sec.data(), s.hits.data(), (int)s.hits.size(), true, prm,
-                                 no_align, s.p_in, s.c_in, chi2, &x);
-        s.ok_out = false;
-        if (s.ok_in) {
-            for (int k = 0; k < 5; ++k) s.p_out[k] = s.p_in[k];
-            for (int k = 0; k < 15; ++k) s.c_out[k] = s.c_in[k];
-            s.ok_out = move_to_row(x, s.p_out, s.c_out, s.sector, row[s.hits.front()], prm);
-        }
-        if (!s.ok_out) {
-            std::vector<int32_t> rev(s.hits.rbegin(), s.hits.rend());
-            s.ok_out = kf_fit<double>(y, z, row, sec.data(), rev.data(), (int)rev.size(), false, prm,
-                                      no_align, s.p_out, s.c_out, chi2);
-        }
+        fit_segment(y, z, row, sec.data(), segs[i], prm);
     }
     // S4 candidates
     std::vector<std::vector<MergePair>> cand_b(S);
@@ -1392,6 +1414,71 @@ int64_t orc_bruteforce_chains(const float* y, const float* z, const uint16_t* ro
         out_off[i + 1] = (int32_t)o;
     }
     return (int64_t)found.size();
+}
+
+int orc_seed_f64(const double* y, const double* z, const uint16_t* row, const int32_t* sector_of,
+                 const int32_t* hits, int32_t n, int first_is_outer, const orc_params* prm, double* x0,
+                 int32_t* frame, double* p) {
+    if (n < 3) return 1;
+    const Seed sd = make_seed(y, z, row, sector_of, hits, n, first_is_outer != 0, *prm);
+    *x0 = sd.x;
+    *frame = sd.frame;
+    for (int i = 0; i < 5; ++i) p[i] = sd.p[i];
+    return 0;
+}
+
+int64_t orc_tracklet(const float* y, const float* z, const uint16_t* row, int64_t beg, int64_t end,
+                     int32_t sector, const int32_t* seg_hits, int32_t nseg, const orc_params* prm,
+                     int32_t* out, int32_t cap) {
+    if (beg < 0 || end < beg || nseg < 3 || sector < 0 || sector >= NSEC) return -1;
+    std::vector<std::vector<int32_t>> rows(NROW);
+    for (int64_t i = beg; i < end; ++i) {
+        if (row[i] >= NROW) return -1;
+        rows[row[i]].push_back((int32_t)i);
+    }
+    std::vector<int32_t> sec((size_t)end, sector);
+    Segment sg;
+    sg.event = 0;
+    sg.sector = sector;
+    sg.hits.assign(seg_hits, seg_hits + nseg);
+    for (int32_t h : sg.hits)
+        if (h < beg || h >= end) return -1;
+    sg.canon = *std::min_element(sg.hits.begin(), sg.hits.end());
+    sg.row_max = row[sg.hits.front()];
+    sg.row_min = row[sg.hits.back()];
+    const std::vector<int32_t> H = build_tracklet(y, z, row, sec.data(), rows, sg, *prm);
+    if ((int64_t)H.size() > cap) return -(int64_t)H.size();
+    for (size_t i = 0; i < H.size(); ++i) out[i] = H[i];
+    return (int64_t)H.size();
+}
+
+int orc_merge_chi2(const float* y, const float* z, const uint16_t* row, const int32_t* hits_a, int32_t na,
+                   int32_t sec_a, const int32_t* hits_b, int32_t nb, int32_t sec_b, const orc_params* prm,
+                   double* chi2, int32_t* gates_pass) {
+    if (na < 3 || nb < 3 || sec_a < 0 || sec_a >= NSEC || sec_b < 0 || sec_b >= NSEC) return 1;
+    int32_t hmax = 0;
+    for (int i = 0; i < na; ++i) hmax = std::max(hmax, hits_a[i]);
+    for (int i = 0; i < nb; ++i) hmax = std::max(hmax, hits_b[i]);
+    std::vector<int32_t> sec((size_t)hmax + 1, 0);
+    Segment A, B;
+    for (int k = 0; k < 2; ++k) {
+        Segment& S = k == 0 ? A : B;
+        const int32_t* h = k == 0 ? hits_a : hits_b;
+        const int32_t m = k == 0 ? na : nb;
+        S.event = 0;
+        S.sector = k == 0 ? sec_a : sec_b;
+        S.hits.assign(h, h + m);
+        for (int32_t q : S.hits) sec[q] = S.sector;
+        S.canon = *std::min_element(S.hits.begin(), S.hits.end());
+        S.row_max = row[S.hits.front()];
+        S.row_min = row[S.hits.back()];
+    }
+    fit_segment(y, z, row, sec.data(), A, *prm);
+    fit_segment(y, z, row, sec.data(), B, *prm);
+    if (!merge_chi2_value(A, B, *prm, *chi2)) return 2;
+    double c2;
+    *gates_pass = merge_chi2(A, B, z, *prm, c2) ? 1 : 0;
+    return 0;
 }
 
 }  // extern "C"

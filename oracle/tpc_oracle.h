@@ -110,6 +110,28 @@ int orc_seed(const float* y, const float* z, const uint16_t* row, const int32_t*
              const int32_t* hits, int32_t n, int first_is_outer, const orc_params* prm,
              double* x0, int32_t* frame, double* p);
 
+/* The same seed for points given in FP64 (pins with exact helix points). */
+int orc_seed_f64(const double* y, const double* z, const uint16_t* row, const int32_t* sector_of,
+                 const int32_t* hits, int32_t n, int first_is_outer, const orc_params* prm,
+                 double* x0, int32_t* frame, double* p);
+
+/* S3b of one segment (seg_hits outermost first, all in the group [beg, end)
+ * of sector `sector`): the tracklet the find builds from it, outermost
+ * first, into out[cap].  Returns its length, -1 for a bad argument, or
+ * -(length) when cap is too small. */
+int64_t orc_tracklet(const float* y, const float* z, const uint16_t* row, int64_t beg,
+                     int64_t end, int32_t sector, const int32_t* seg_hits, int32_t nseg,
+                     const orc_params* prm, int32_t* out, int32_t cap);
+
+/* S4 of two segments (hits outermost first): inner A in sector sec_a,
+ * outer B in sec_b, each fitted as the find fits its tracklets.  Writes the
+ * chi2_5 of A's state moved to B's innermost plane against B's state there,
+ * and whether the merge's gates and cut accept the pair.  Returns 0, 1 for
+ * a bad argument, 2 when a fit or the move fails. */
+int orc_merge_chi2(const float* y, const float* z, const uint16_t* row, const int32_t* hits_a,
+                   int32_t na, int32_t sec_a, const int32_t* hits_b, int32_t nb, int32_t sec_b,
+                   const orc_params* prm, double* chi2, int32_t* gates_pass);
+
 /* One propagation: state p (y, z, sin phi, tan lambda, q/pT) at plane x1 of
  * sector s1 -> plane x2 of sector s2.  Writes p_out[5], jac[25] (row-major
  * d p_out / d p) and dx1[5], dx2[5].  Returns 0, or 1 when it fails. */
