@@ -4,8 +4,8 @@ by nvcc for the host and run on the CPU, against the FP64 oracle on the
 same hit lists, with the GPU parity bars:
 * the same tracks fail (a transport reaching |sin phi| = snp_max);
 * parameters within 1e-5 max(|p_i|, s_i), s = (1 cm, 1 cm, 0.1, 0.1, 0.1);
-* chi2 within 2e-3 relative (1e-3 absolute), the covariance diagonal within
-  1e-4 relative, ndf equal.
+* the 15 covariance terms within 1e-5 of sqrt(C_ii C_jj) (relative for
+  the diagonal), chi2 within 1e-5 max(chi2, 1), ndf equal.
 Run on every track the oracle finds in a noisy event (fakes and low-pT
 tracks included) and on the truth tracks of a noise-free one.  The tracklet
 lanes' FP32 Kalman step (with its FP64 redo) is checked the same way at an
@@ -72,11 +72,16 @@ def _compare(orc, ev, off, hits, got):
     ok = ondf > 0
     assert np.array_equal(ndf[ok], ondf[ok])
     rel = np.abs(par - opar) / np.maximum(np.abs(opar), SCALE)
-    crel = np.abs(cov[ok][:, DIAG] - ocov[ok][:, DIAG]) / np.abs(ocov[ok][:, DIAG])
-    print(f"{ok.sum()} tracks: parameters {rel[ok].max(0)}, cov diagonal {crel.max():.2e}")
+    d = ocov[:, DIAG]
+    iu = [(i, j) for i in range(5) for j in range(i, 5)]
+    cscale = np.stack([np.sqrt(d[:, i] * d[:, j]) for i, j in iu], 1)
+    crel = np.abs(cov - ocov) / np.maximum(cscale, 1e-300)
+    chrel = np.abs(chi2 - ochi2) / np.maximum(ochi2, 1.0)
+    print(f"{ok.sum()} tracks: parameters {rel[ok].max(0)}, cov terms {crel[ok].max():.2e}, "
+          f"chi2 {chrel[ok].max():.2e}")
     assert np.all(rel[ok] <= 1e-5), rel[ok].max(0)
-    assert np.all(crel <= 1e-4), crel.max()
-    np.testing.assert_allclose(chi2[ok], ochi2[ok], rtol=2e-3, atol=1e-3)
+    assert np.all(crel[ok] <= 1e-5), crel[ok].max(0)
+    assert np.all(chrel[ok] <= 1e-5), chrel[ok].max()
     return ok.sum()
 
 

@@ -66,6 +66,29 @@ def test_find_multi_event_batch(orc):
     _assign_parity(orc, synth.uneven_batch(n_events=6, lo=10, hi=800, seed=303))
 
 
+def _check_fit_parity(gpar, gcov, gchi2, gndf, opar, ocov, ochi2, ondf, ok):
+    """Fit bar per quantity, on the tracks that both sides fitted: the five
+    parameters within 1e-5 max(|p|, s); the 15 covariance terms within 1e-5
+    of sqrt(C_ii C_jj) (a relative error for the diagonal, on the scale of
+    the variances for the correlations); chi2 within 1e-5 max(chi2, 1);
+    identical ndf."""
+    rel = np.abs(gpar - opar) / np.maximum(np.abs(opar), SCALE)
+    d = ocov[:, [0, 5, 9, 12, 14]]
+    iu = [(i, j) for i in range(5) for j in range(i, 5)]
+    cscale = np.stack([np.sqrt(d[:, i] * d[:, j]) for i, j in iu], 1)
+    crel = np.abs(gcov - ocov) / np.maximum(cscale, 1e-300)
+    chrel = np.abs(gchi2 - ochi2) / np.maximum(ochi2, 1.0)
+    print("per-quantity |GPU FP32 - oracle FP64| over", int(ok.sum()), "tracks:")
+    for i, name in enumerate(("y", "z", "sin phi", "tan lambda", "q/pT")):
+        print(f"  {name:10s} median {np.median(rel[ok, i]):.2e} max {rel[ok, i].max():.2e}")
+    print(f"  cov terms max {crel[ok].max(0)}")
+    print(f"  chi2 median {np.median(chrel[ok]):.2e} max {chrel[ok].max():.2e}")
+    assert np.all(rel[ok] <= 1e-5), rel[ok].max(0)
+    assert np.all(crel[ok] <= 1e-5), crel[ok].max(0)
+    assert np.all(chrel[ok] <= 1e-5), chrel[ok].max()
+    assert np.array_equal(gndf[ok], ondf[ok])
+
+
 def test_fit_parity_truth_tracks(orc):
     ev = synth.central_event(n_tracks=3000, noise=0.0, seed=202)
     sec = ev.sector_of_cluster()
@@ -81,24 +104,40 @@ def test_fit_parity_truth_tracks(orc):
     gpar = par.cpu().numpy().astype(np.float64)
     ok = (ondf > 0) & (ndf.cpu().numpy() > 0)
     assert ok.mean() > 0.999
-    rel = np.abs(gpar - opar) / np.maximum(np.abs(opar), SCALE)
-    sig = np.sqrt(ocov[:, [0, 5, 9, 12, 14]])
-    in_sigma = np.abs(gpar - opar) / sig
-    gcov = cov.cpu().numpy().astype(np.float64)
-    crel = np.abs(gcov - ocov) / np.maximum(np.abs(ocov), 1e-30)
-    print("per-quantity |GPU FP32 - oracle FP64| (relative, floors 1 cm/1 cm/0.1/0.1/0.1):")
-    for i, name in enumerate(("y", "z", "sin phi", "tan lambda", "q/pT")):
-        print(f"  {name:10s} median {np.median(rel[ok, i]):.2e} p99.9 "
-              f"{np.percentile(rel[ok, i], 99.9):.2e} max {rel[ok, i].max():.2e} "
-              f"max/sigma {in_sigma[ok, i].max():.2e}")
-    print(f"  cov diag max rel {crel[ok][:, [0, 5, 9, 12, 14]].max(0)}")
-    # every track within 1e-5 relative (floors s); errors are also a tiny
-    # fraction of each parameter's own statistical sigma
-    assert np.all(rel[ok] <= 1e-5), rel[ok].max(0)
+    # errors are also a tiny fraction of each parameter's own sigma
+    in_sigma = np.abs(gpar - opar) / np.sqrt(ocov[:, [0, 5, 9, 12, 14]])
     assert in_sigma[ok].max() <= 1e-2, in_sigma[ok].max(0)
-    gchi2 = chi2.cpu().numpy()
-    np.testing.assert_allclose(gchi2[ok], ochi2[ok], rtol=2e-3, atol=1e-3)
-    assert np.array_equal(ndf.cpu().numpy()[ok], ondf[ok])
+    _check_fit_parity(gpar, cov.cpu().numpy().astype(np.float64), chi2.cpu().numpy().astype(np.float64),
+                      ndf.cpu().numpy(), opar, ocov, ochi2, ondf, ok)
+
+
+def test_fit_pulls_unit_width_on_gpu():
+    """The GPU fit's pulls against the generator's truth, with the oracle's
+    bar: over the tracks of chi2 probability > 1e-3, |mean| < 0.03 and
+    standard deviation in [0.97, 1.03] for each of the five parameters."""
+    from scipy.stats import chi2 as chi2_dist
+    ev = synth.central_event(n_tracks=10000, noise=0.0, truth=True, seed=11)
+    off, hits, tids = ev.truth_tracks(n_min=20)
+    tr = tpc.Tracker(ev.n, 1)
+    tr.load(*to_dev(ev), 1)
+    T = len(off) - 1
+    par, cov, chi2, ndf = tr.fit(torch.from_numpy(off).cuda(), torch.from_numpy(hits).cuda(), T)
+    torch.cuda.synchronize()
+    tr.check()
+    par = par.cpu().numpy().astype(np.float64)
+    cov = cov.cpu().numpy().astype(np.float64)
+    chi2, ndf = chi2.cpu().numpy().astype(np.float64), ndf.cpu().numpy()
+    ok = ndf > 0
+    inner = hits[off[1:] - 1]
+    truth = np.stack([ev.y_true[inner], ev.z_true[inner], ev.snp_true[inner], ev.trk_tgl[tids],
+                      ev.trk_q[tids] / ev.trk_pt[tids]], 1)
+    pull = ((par - truth) / np.sqrt(cov[:, [0, 5, 9, 12, 14]]))[ok]
+    good = chi2_dist.sf(chi2[ok], ndf[ok]) > 1e-3
+    assert good.mean() > 0.995, good.mean()
+    mu, sd = pull[good].mean(0), pull[good].std(0)
+    print("GPU pull mean", mu, "std", sd)
+    assert np.all(np.abs(mu) < 0.03), mu
+    assert np.all((sd > 0.97) & (sd < 1.03)), sd
 
 
 def test_fit_parity_found_tracks(orc):
@@ -116,9 +155,8 @@ def test_fit_parity_found_tracks(orc):
     # transport failures agree
     assert np.array_equal(gndf <= 0, ondf <= 0)
     ok = ondf > 0
-    rel = np.abs(par.cpu().numpy().astype(np.float64) - opar) / np.maximum(np.abs(opar), SCALE)
-    print(f"{T} tracks, max relative error per parameter {rel[ok].max(0)}")
-    assert np.all(rel[ok] <= 1e-5), rel[ok].max(0)
+    _check_fit_parity(par.cpu().numpy().astype(np.float64), cov.cpu().numpy().astype(np.float64),
+                      chi2.cpu().numpy().astype(np.float64), gndf, opar, ocov, ochi2, ondf, ok)
 
 
 def test_empty_input():

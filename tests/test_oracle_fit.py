@@ -6,7 +6,8 @@
   closed-form weighted least squares with the prior as pseudo-measurements
   (normal equations solved here independently), state and covariance.
 * Statistics: pulls of the five fitted parameters against the generator's
-  truth at the innermost cluster have zero mean and unit width, and
+  truth at the innermost cluster have |mean| < 0.03 and standard deviation
+  in [0.97, 1.03] over the tracks of chi2 probability > 1e-3, and
   chi2/ndf averages to one.
 """
 import numpy as np
@@ -84,15 +85,17 @@ def test_pulls_unit_width(orc):
     pull = (par - truth) / np.sqrt(cov[:, [0, 5, 9, 12, 14]])
     pull = pull[ok]
     assert pull.shape[0] > 8000
-    # a few steep pT~0.2 tracks seeded at a sector edge diverge in the first
-    # updates (extended Kalman filter from a diffuse prior); the core of the
-    # distribution is checked with robust estimators and the tail is bounded
-    outlier = np.abs(pull).max(1) > 6
-    assert outlier.mean() < 0.002
-    core = pull[~outlier]
-    mu = np.median(core, 0)
-    half68 = (np.percentile(core, 84.135, 0) - np.percentile(core, 15.865, 0)) / 2
+    # fit quality: the pulls are taken over the tracks whose chi2 probability
+    # is above 1e-3 (the usual cut; a correct fit loses 0.1% of its tracks
+    # to it).  It removes the rare steep pT ~ 0.2 GeV/c tracks that cross
+    # three or four sectors and on which the extended Kalman filter, started
+    # from the three-point seed, does not converge (chi2/ndf 2 to 35 here).
+    from scipy.stats import chi2 as chi2_dist
+    good = chi2_dist.sf(chi2[ok], ndf[ok]) > 1e-3
+    assert good.mean() > 0.995, good.mean()
+    core = pull[good]
+    mu, sd = core.mean(0), core.std(0)
+    print("pull mean", mu, "pull std", sd)
     assert np.all(np.abs(mu) < 0.03), mu
-    assert np.all((half68 > 0.95) & (half68 < 1.05)), half68
-    assert np.all(np.abs(core.std(0) - 1) < 0.05), core.std(0)
+    assert np.all((sd > 0.97) & (sd < 1.03)), sd
     assert abs(np.median(chi2[ok] / ndf[ok]) - 0.99) < 0.03
