@@ -33,6 +33,7 @@ class Params(C.Structure):
         ("prior", C.c_double * 5), ("seed_snp_max", C.c_double),
         ("seed_qpt_max", C.c_double),
         ("snp_max", C.c_double),
+        ("s2_fp64", C.c_int32),
     ]
 
 
@@ -42,6 +43,7 @@ class Diag(C.Structure):
         ("d2", C.c_void_p), ("d2_next", C.c_void_p),
         ("link_dn", C.c_void_p), ("link_up", C.c_void_p),
         ("seg_of", C.c_void_p), ("merge_margin", C.c_void_p),
+        ("ext_margin", C.c_void_p),
     ]
 
 
@@ -124,7 +126,8 @@ def find_tracks(y, z, row, evt_sector_off, n_events, params=None, diag=False):
         d = dict(choice_dn=np.empty(n, np.int32), choice_up=np.empty(n, np.int32),
                  d2=np.empty(n, np.float32), d2_next=np.empty(n, np.float32),
                  link_dn=np.empty(n, np.int32), link_up=np.empty(n, np.int32),
-                 seg_of=np.empty(n, np.int32), merge_margin=np.empty(n, np.float64))
+                 seg_of=np.empty(n, np.int32), merge_margin=np.empty(n, np.float64),
+                 ext_margin=np.empty(n, np.float64))
         dg = Diag(**{k: v.ctypes.data for k, v in d.items()})
     T = lib().orc_find_tracks(_p(y), _p(z), _p(row), C.c_int64(n), _p(off),
                               C.c_int32(n_events), C.byref(prm), _p(toc), _p(trk_off),

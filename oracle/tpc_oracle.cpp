@@ -442,6 +442,24 @@ bool in_window(float xa, float ya, float za, float xb, float yb, float zb, float
     return std::fabs(yb - ya) <= wy * dx && std::fabs(zb - za) <= wz * dx;
 }
 
+// The same two tests in FP64 (the diagnostic mode that measures how many
+// neighbour decisions FP32 rounding changes): row planes and window slopes
+// in double, coordinates widened from their FP32 storage.
+double triplet_d2_f64(double xd, double yd, double zd, double xc, double yc, double zc,
+                      double xu, double yu, double zu, double sy2, double sz2) {
+    const double a = (xc - xd) / (xu - xd);
+    const double ry = yc - (yd + a * (yu - yd));
+    const double rz = zc - (zd + a * (zu - zd));
+    const double b = 1.0 - a;
+    const double f = (1.0 + a * a) + b * b;
+    return (ry * ry) / (sy2 * f) + (rz * rz) / (sz2 * f);
+}
+
+bool in_window_f64(double xa, double ya, double za, double xb, double yb, double zb, double wy, double wz) {
+    const double dx = std::fabs(xb - xa);
+    return std::fabs(yb - ya) <= wy * dx && std::fabs(zb - za) <= wz * dx;
+}
+
 struct Segment {
     int event, sector;
     std::vector<int32_t> hits;  // outermost first (input-order indices)
@@ -462,29 +480,42 @@ void group_ca(const float* y, const float* z, const uint16_t* row, int64_t beg, 
     // S1: rows, canonical order = input order
     for (int64_t i = beg; i < end; ++i) rows[row[i]].push_back((int32_t)i);
     std::vector<int32_t> cdn(n, -1), cup(n, -1), ldn(n, -1), lup(n, -1);
-    std::vector<float> d2v(n, std::numeric_limits<float>::infinity());
-    std::vector<float> d2n(n, std::numeric_limits<float>::infinity());
+    std::vector<double> d2v(n, std::numeric_limits<double>::infinity());
+    std::vector<double> d2n(n, std::numeric_limits<double>::infinity());
     const std::vector<Gap> gaps = gap_order(prm.max_gap);
+    const bool f64 = prm.s2_fp64 != 0;
+    // admissibility and D^2 of the triplet (d, c, u): FP32 with one rounding
+    // per operation (the rule), or FP64 (diagnostic); an FP32 D^2 is exact
+    // in double, so the comparisons below decide alike in both modes
+    auto admissible = [&](int rc, int64_t c, int rb, int32_t b) {
+        if (f64)
+            return in_window_f64(row_x(rc), y[c], z[c], row_x(rb), y[b], z[b], prm.win_y, prm.win_z);
+        return in_window(row_xf(rc), y[c], z[c], row_xf(rb), y[b], z[b], prm.win_y, prm.win_z);
+    };
+    auto triplet = [&](int rd, int32_t d, int rc, int64_t c, int ru, int32_t u) -> double {
+        if (f64)
+            return triplet_d2_f64(row_x(rd), y[d], z[d], row_x(rc), y[c], z[c], row_x(ru), y[u], z[u],
+                                  (double)prm.sigma_y2, (double)prm.sigma_z2);
+        return triplet_d2(row_xf(rd), y[d], z[d], row_xf(rc), y[c], z[c], row_xf(ru), y[u], z[u],
+                          prm.sigma_y2, prm.sigma_z2);
+    };
     // S2a: each cluster chooses its best (down, up) pair
     for (int64_t c = beg; c < end; ++c) {
         const int r = row[c];
-        const float xc = row_xf(r), yc = y[c], zc = z[c];
-        float best_seen = std::numeric_limits<float>::infinity();
+        double best_seen = std::numeric_limits<double>::infinity();
         for (const Gap& gp : gaps) {
             const int rd = r - gp.d, ru = r + gp.u;
             if (rd < 0 || ru >= NROW) continue;
-            const float xd = row_xf(rd), xu = row_xf(ru);
             bool found = false;
-            float bd2 = 0, second = std::numeric_limits<float>::infinity();
+            double bd2 = 0, second = std::numeric_limits<double>::infinity();
             int32_t bd = -1, bu = -1;
             for (int32_t d : rows[rd]) {
-                if (!in_window(xc, yc, zc, xd, y[d], z[d], prm.win_y, prm.win_z)) continue;
+                if (!admissible(r, c, rd, d)) continue;
                 for (int32_t u : rows[ru]) {
-                    if (!in_window(xc, yc, zc, xu, y[u], z[u], prm.win_y, prm.win_z)) continue;
-                    const float d2 = triplet_d2(xd, y[d], z[d], xc, yc, zc, xu, y[u], z[u],
-                                                prm.sigma_y2, prm.sigma_z2);
+                    if (!admissible(r, c, ru, u)) continue;
+                    const double d2 = triplet(rd, d, r, c, ru, u);
                     if (d2 < best_seen) best_seen = d2;
-                    if (!(d2 <= prm.chi2_link)) {
+                    if (!(d2 <= (double)prm.chi2_link)) {
                         if (found && d2 < second) second = d2;
                         continue;
                     }
@@ -513,7 +544,7 @@ void group_ca(const float* y, const float* z, const uint16_t* row, int64_t beg, 
     std::vector<int32_t> claim_up(n, -1), claim_dn(n, -1);
     auto better_claim = [&](int32_t a, int32_t b) {  // a better than b?
         if (b < 0) return true;
-        const float da = d2v[a - beg], db = d2v[b - beg];
+        const double da = d2v[a - beg], db = d2v[b - beg];
         return da < db || (da == db && a < b);
     };
     for (int64_t c = beg; c < end; ++c) {
@@ -541,8 +572,8 @@ void group_ca(const float* y, const float* z, const uint16_t* row, int64_t beg, 
         for (int64_t c = beg; c < end; ++c) {
             if (diag->choice_dn) diag->choice_dn[c] = cdn[c - beg];
             if (diag->choice_up) diag->choice_up[c] = cup[c - beg];
-            if (diag->d2) diag->d2[c] = d2v[c - beg];
-            if (diag->d2_next) diag->d2_next[c] = d2n[c - beg];
+            if (diag->d2) diag->d2[c] = (float)d2v[c - beg];
+            if (diag->d2_next) diag->d2_next[c] = (float)d2n[c - beg];
             if (diag->link_dn) diag->link_dn[c] = ldn[c - beg];
             if (diag->link_up) diag->link_up[c] = lup[c - beg];
         }
@@ -611,9 +642,18 @@ bool move_to_row(double& x, double p[5], double C[15], int sector, int r, const 
 // update with it; stop after ext_max_miss consecutive rows without one, at
 // the last row, when the transport fails, or when the prediction leaves the
 // sector's acceptance.
+// A decision of the extension (a row's choice) and its relative margin, for
+// tracing disagreements to near-ties: (cluster, margin).
+using Decisions = std::vector<std::pair<int32_t, double>>;
+
+inline double rel_gap(double u, double v) {
+    const double m = std::max(std::fabs(u), std::fabs(v));
+    return m > 0 ? std::fabs(u - v) / m : 0.0;
+}
+
 void extend_tracklet(const float* y, const float* z, const std::vector<std::vector<int32_t>>& rows,
                      int sector, double& x, double p[5], double C[15], int r_start, int dir,
-                     const orc_params& prm, std::vector<int32_t>& added) {
+                     const orc_params& prm, std::vector<int32_t>& added, Decisions* dec = nullptr) {
     int misses = 0;
     for (int r = r_start; r >= 0 && r < NROW; r += dir) {
         double J[25], dX[5];
@@ -629,14 +669,30 @@ void extend_tracklet(const float* y, const float* z, const std::vector<std::vect
         const double det = S00 * S11 - S01 * S01;
         int32_t best = -1;
         double bchi = 0;
+        // diagnostics only: the two smallest chi2 of the row, cut or not
+        int32_t d1 = -1, d2 = -1;
+        double c1 = 0, c2 = 0;
         for (int32_t c : rows[r]) {
             const double r0 = (double)y[c] - p[0], r1 = (double)z[c] - p[1];
             const double chi = (r0 * r0 * S11 - 2.0 * r0 * r1 * S01 + r1 * r1 * S00) / det;
+            if (dec) {
+                if (d1 < 0 || chi < c1) {
+                    d2 = d1; c2 = c1; d1 = c; c1 = chi;
+                } else if (d2 < 0 || chi < c2) {
+                    d2 = c; c2 = chi;
+                }
+            }
             if (!(chi <= prm.chi2_ext)) continue;
             if (best < 0 || chi < bchi || (chi == bchi && c < best)) {
                 best = c;
                 bchi = chi;
             }
+        }
+        if (dec && d1 >= 0) {
+            double m = rel_gap(c1, prm.chi2_ext);
+            if (d2 >= 0) m = std::min(m, rel_gap(c1, c2));
+            dec->push_back({d1, m});
+            if (d2 >= 0) dec->push_back({d2, m});
         }
         if (best >= 0) {
             double chi2 = 0;
@@ -662,14 +718,14 @@ struct MergePair {
 // or that move fails.  Returns the tracklet's hits, outermost first.
 std::vector<int32_t> build_tracklet(const float* y, const float* z, const uint16_t* row,
                                     const int32_t* sec, const std::vector<std::vector<int32_t>>& rows,
-                                    const Segment& sg, const orc_params& prm) {
+                                    const Segment& sg, const orc_params& prm, Decisions* dec = nullptr) {
     auto no_align = [](int) -> const double* { return nullptr; };
     std::vector<int32_t> H = sg.hits;
     double p[5], C[15], chi2, x;
     bool have_out = false;
     if (kf_fit<double>(y, z, row, sec, H.data(), (int)H.size(), true, prm, no_align, p, C, chi2, &x)) {
         std::vector<int32_t> add;
-        extend_tracklet(y, z, rows, sg.sector, x, p, C, row[H.back()] - 1, -1, prm, add);
+        extend_tracklet(y, z, rows, sg.sector, x, p, C, row[H.back()] - 1, -1, prm, add, dec);
         H.insert(H.end(), add.begin(), add.end());
         have_out = move_to_row(x, p, C, sg.sector, row[H.front()], prm);
     }
@@ -680,7 +736,7 @@ std::vector<int32_t> build_tracklet(const float* y, const float* z, const uint16
     }
     if (have_out) {
         std::vector<int32_t> add;
-        extend_tracklet(y, z, rows, sg.sector, x, p, C, row[H.front()] + 1, +1, prm, add);
+        extend_tracklet(y, z, rows, sg.sector, x, p, C, row[H.front()] + 1, +1, prm, add, dec);
         std::vector<int32_t> H2(add.rbegin(), add.rend());
         H2.insert(H2.end(), H.begin(), H.end());
         H.swap(H2);
@@ -732,7 +788,8 @@ bool merge_chi2_value(const Segment& A, const Segment& B, const orc_params& prm,
 // S4 candidate test: A's outward-fit state at its outermost cluster is moved
 // to B's innermost plane and compared with B's inward-fit state there.
 bool merge_chi2(const Segment& A, const Segment& B, const float* z, const orc_params& prm,
-                double& chi2) {
+                double& chi2, bool* evaluated = nullptr) {
+    if (evaluated) *evaluated = false;
     if (A.event != B.event) return false;
     if ((A.sector < NPHI) != (B.sector < NPHI)) return false;
     const int dphi = ((B.sector % NPHI) - (A.sector % NPHI) + NPHI) % NPHI;
@@ -748,6 +805,7 @@ bool merge_chi2(const Segment& A, const Segment& B, const float* z, const orc_pa
     const float dxr = std::fabs(row_xf(B.row_min) - row_xf(A.row_max));
     if (!(std::fabs(zb - za) <= prm.merge_z_slope * dxr + prm.merge_z_margin)) return false;
     if (!merge_chi2_value(A, B, prm, chi2)) return false;
+    if (evaluated) *evaluated = true;
     return chi2 <= prm.chi2_merge;
 }
 
@@ -780,6 +838,7 @@ void orc_default_params(orc_params* p) {
     p->seed_snp_max = 0.99;
     p->seed_qpt_max = 5.0;
     p->snp_max = 0.999;
+    p->s2_fp64 = 0;
 }
 
 void orc_set_threads(int n) { g_threads = n; }
@@ -820,10 +879,18 @@ int64_t orc_find_tracks(const float* y, const float* z, const uint16_t* row, int
         for (int64_t i = off[g]; i < off[g + 1]; ++i) sec[i] = g % NSEC;
     // S3b: each segment seeds a tracklet (build_tracklet)
     std::vector<std::vector<int32_t>> tl_hits(S0);
+    const bool want_ext = diag && diag->ext_margin;
+    std::vector<Decisions> tl_dec(want_ext ? S0 : 0);
 #pragma omp parallel for schedule(dynamic, 16) num_threads(nt)
     for (int i = 0; i < S0; ++i) {
         const Segment& sg = seeds[i];
-        tl_hits[i] = build_tracklet(y, z, row, sec.data(), grp_rows[sg.event * NSEC + sg.sector], sg, prm);
+        tl_hits[i] = build_tracklet(y, z, row, sec.data(), grp_rows[sg.event * NSEC + sg.sector], sg, prm,
+                                    want_ext ? &tl_dec[i] : nullptr);
+    }
+    if (want_ext) {
+        for (int64_t i = 0; i < n; ++i) diag->ext_margin[i] = std::numeric_limits<double>::infinity();
+        for (const Decisions& d : tl_dec)
+            for (const auto& e : d) diag->ext_margin[e.first] = std::min(diag->ext_margin[e.first], e.second);
     }
     // S3c: every cluster belongs to the best tracklet containing it: more
     // clusters first, then the smaller canonical id of the seed segment.
@@ -859,12 +926,16 @@ int64_t orc_find_tracks(const float* y, const float* z, const uint16_t* row, int
     }
     // S4 candidates
     std::vector<std::vector<MergePair>> cand_b(S);
+    // pairs whose chi2 was evaluated and found above the cut (diagnostics)
+    std::vector<std::vector<MergePair>> rej_b(diag ? S : 0);
 #pragma omp parallel for schedule(dynamic, 16) num_threads(nt)
     for (int b = 0; b < S; ++b)
         for (int a = 0; a < S; ++a) {
             if (a == b) continue;
             double c2;
-            if (merge_chi2(segs[a], segs[b], z, prm, c2)) cand_b[b].push_back({c2, a, b});
+            bool evaluated;
+            if (merge_chi2(segs[a], segs[b], z, prm, c2, &evaluated)) cand_b[b].push_back({c2, a, b});
+            else if (diag && evaluated) rej_b[b].push_back({c2, a, b});
         }
     std::vector<MergePair> cand;
     for (auto& v : cand_b)
@@ -898,6 +969,13 @@ int64_t orc_find_tracks(const float* y, const float* z, const uint16_t* row, int
             margin[m.a] = std::min(margin[m.a], mg);
             margin[m.b] = std::min(margin[m.b], mg);
         }
+        // a pair refused by the cut is a decision too
+        for (const auto& v : rej_b)
+            for (const MergePair& m : v) {
+                const double mg = rel(m.chi2, prm.chi2_merge);
+                margin[m.a] = std::min(margin[m.a], mg);
+                margin[m.b] = std::min(margin[m.b], mg);
+            }
     }
     // tracks: chains of merged segments, hits outermost first
     struct Track { int32_t canon; std::vector<int32_t> hits; };

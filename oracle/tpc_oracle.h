@@ -40,6 +40,9 @@ typedef struct {
     double seed_snp_max;      /* clamp of the seed |sin phi|                */
     double seed_qpt_max;      /* clamp of the seed |q/pT| (c/GeV)           */
     double snp_max;           /* transport fails when |sin phi| reaches it  */
+    int32_t s2_fp64;          /* 1: window tests and triplet D^2 in FP64 (a
+                                 diagnostic mode; 0, the default, decides in
+                                 FP32 with one rounding per operation)      */
 } orc_params;
 
 /* Fills the default parameter set of the build's reading. */
@@ -56,6 +59,11 @@ typedef struct {
     int32_t* seg_of;      /* [n] segment id (canonical order) or -1         */
     double*  merge_margin;/* [n] relative margin of the merge decision that
                              placed this cluster's segment (inf: none)      */
+    double*  ext_margin;  /* [n] smallest relative margin of the extension
+                             decisions in which this cluster was the best
+                             or second-best candidate of a row: best chi2
+                             against the cut and against the runner-up
+                             (inf: none)                                    */
 } orc_diag;
 
 /* S1-S4: whole pipeline.  Inputs in input order, grouped per event*36+sector
