@@ -34,7 +34,7 @@ sys.path.insert(0, ROOT)
 METRIC = "TPC clusters/s tracked (CA+Kalman), 1 GB300"
 WORKLOAD = ("central_event: 1 event x 36 sectors, 1e4 primary tracks (pT exp slope 0.5 GeV/c "
             "min 0.2, |eta|<0.9), 20% noise, ~1.8e6 clusters, Bz 0.5 T")
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
+FP32_LANES_PER_SM = 128                 # Blackwell SM: 4 partitions x 32 FP32 lanes
 # algorithmic traffic / work per unit, fixed before measuring
 # the whole find + fit path, every intermediate product written once and read
 # once: binning 22, neighbours 16, chains and tracks 16, fit 12.7, scatter 12
@@ -44,7 +44,20 @@ PATH_BYTES_PER_CLUSTER = 78.7
 PATH_FUSED_BYTES_PER_CLUSTER = 14.7
 FIT_BYTES_PER_HIT = 14.0                # hit index (4) + y, z (8) + row (2)
 FIT_BYTES_PER_TRACK = 88.0              # 5 params + 15 cov + chi2 + ndf
-KF_FLOPS_PER_STEP = 350.0               # transport ~60 + covariance J C J^T ~160 + update ~130
+
+def kf_ops_per_step():
+    """Arithmetic operations of one Kalman step (transport, covariance
+    transport, update, chi2) as counted by the FP64 oracle over the central
+    event's truth tracks; stored in tests/golden/kf_ops_per_step.json by
+    tests/golden/make_kf_ops.py."""
+    with open(os.path.join(ROOT, "tests", "golden", "kf_ops_per_step.json")) as f:
+        return float(json.load(f)["ops_per_step"])
+
+
+def fp32_peak_tflops(torch, dev, sm_max_mhz):
+    """FP32 issue peak: SMs (queried) x 128 lanes x 2 (FMA) x max SM clock."""
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    return sms * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12, sms
 # DRAM bytes (read + write) of one build launch of k_tracklet_lanes on the
 # central event, from an ncu capture of this kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum); None for a kernel without a capture
@@ -365,6 +378,14 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+def measured_sm_max_mhz():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["sm_max_mhz"])
+    except (OSError, KeyError, ValueError):
+        return 2070.0
+
+
 def cpu_baseline(ev, target_s=12.0):
     """The oracle, as it stands, on the host cores: find + fit of the event."""
     import oracle
@@ -591,14 +612,18 @@ def run_ours(args):
     dom = max(kernels, key=kernels.get)
     hbm_peak, peak_src = measured_peaks()
     ms = kernels[dom]
-    # Kalman kernels are FP32-ALU work: counted steps x flops per step
+    # Kalman kernels are FP32-ALU work: counted steps x operations per step
     work_steps = st.n_kf_steps if dom == "k_tracklet_lanes" else hits_total
-    achieved = work_steps * KF_FLOPS_PER_STEP / (ms * 1e-3) / 1e12
-    roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-            "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+    ops_step = kf_ops_per_step()
+    sm_max = clk.get("sm_max_mhz") or measured_sm_max_mhz()
+    peak_tf, sms = fp32_peak_tflops(torch, dev, sm_max)
+    achieved = work_steps * ops_step / (ms * 1e-3) / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak_tf,
+            "unit": "TFLOP/s", "frac": achieved / peak_tf,
             "traffic": TRAFFIC_BYTES_PER_LAUNCH.get(dom), "kf_steps_per_launch": int(work_steps),
-            "kernel": dom, "kernel_ms": ms,
-            "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 (FMA) x 2070 MHz"}
+            "ops_per_kf_step": ops_step, "kernel": dom, "kernel_ms": ms,
+            "peak_source": f"derived: {sms} SMs (queried) x {FP32_LANES_PER_SM} FP32 lanes x 2 (FMA) x "
+                           f"{sm_max:.0f} MHz (max SM clock)"}
 
     if rank != 0:
         if world > 1:

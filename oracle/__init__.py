@@ -317,3 +317,17 @@ def merge_chi2(y, z, row, hits_a, sec_a, hits_b, sec_b, params=None):
     if rc == 1:
         raise ValueError("orc_merge_chi2 refused its arguments")
     return None if rc != 0 else (c2.value, bool(ok.value))
+
+
+def kf_ops(y, z, row, sector_of, trk_off, trk_hits, params=None):
+    """(operations, Kalman steps) of the FP64 fit of the given tracks; see
+    orc_kf_ops (structural zeros and ones of the Jacobians not counted)."""
+    y, z, row = _c(y, np.float32), _c(z, np.float32), _c(row, np.uint16)
+    sec = _c(sector_of, np.int32)
+    off, hits = _c(trk_off, np.int32), _c(trk_hits, np.int32)
+    prm = params or default_params()
+    ops = C.c_double(0.0)
+    steps = C.c_int64(0)
+    lib().orc_kf_ops(_p(y), _p(z), _p(row), _p(sec), _p(off), _p(hits), C.c_int32(off.shape[0] - 1),
+                     C.byref(prm), C.byref(ops), C.byref(steps))
+    return ops.value, steps.value

@@ -108,6 +108,41 @@ using std::cos;
 using std::sin;
 using std::sqrt;
 
+// ---- operation counting (the algorithmic work of a Kalman step) ---------
+// A double that counts the arithmetic performed on it: +, -, *, / and each
+// square root or arcsine count one operation, except an operation whose
+// operand is an exact 0 (or 1 for *, /): those are structural zeros and
+// ones of the Jacobians and cost an implementation that exploits the
+// structure nothing.  Used single-threaded (the counter is per thread).
+thread_local long long g_ops = 0;
+struct Cnt {
+    double v;
+    Cnt() : v(0) {}
+    Cnt(double x) : v(x) {}
+};
+inline bool triv_add(double a, double b) { return a == 0.0 || b == 0.0; }
+inline bool triv_mul(double a, double b) { return a == 0.0 || b == 0.0 || a == 1.0 || b == 1.0; }
+inline Cnt operator+(const Cnt& a, const Cnt& b) { if (!triv_add(a.v, b.v)) ++g_ops; return Cnt(a.v + b.v); }
+inline Cnt operator-(const Cnt& a, const Cnt& b) { if (!triv_add(a.v, b.v)) ++g_ops; return Cnt(a.v - b.v); }
+inline Cnt operator-(const Cnt& a) { return Cnt(-a.v); }
+inline Cnt operator*(const Cnt& a, const Cnt& b) { if (!triv_mul(a.v, b.v)) ++g_ops; return Cnt(a.v * b.v); }
+inline Cnt operator/(const Cnt& a, const Cnt& b) { if (b.v != 1.0 && a.v != 0.0) ++g_ops; return Cnt(a.v / b.v); }
+inline Cnt operator+(const Cnt& a, double b) { return a + Cnt(b); }
+inline Cnt operator+(double a, const Cnt& b) { return Cnt(a) + b; }
+inline Cnt operator-(const Cnt& a, double b) { return a - Cnt(b); }
+inline Cnt operator-(double a, const Cnt& b) { return Cnt(a) - b; }
+inline Cnt operator*(const Cnt& a, double b) { return a * Cnt(b); }
+inline Cnt operator*(double a, const Cnt& b) { return Cnt(a) * b; }
+inline Cnt operator/(const Cnt& a, double b) { return a / Cnt(b); }
+inline Cnt operator/(double a, const Cnt& b) { return Cnt(a) / b; }
+inline Cnt& operator+=(Cnt& a, const Cnt& b) { a = a + b; return a; }
+inline Cnt& operator-=(Cnt& a, const Cnt& b) { a = a - b; return a; }
+inline Cnt sqrt(const Cnt& a) { ++g_ops; return Cnt(std::sqrt(a.v)); }
+inline Cnt asin(const Cnt& a) { ++g_ops; return Cnt(std::asin(a.v)); }
+inline Cnt sin(const Cnt& a) { ++g_ops; return Cnt(std::sin(a.v)); }
+inline Cnt cos(const Cnt& a) { ++g_ops; return Cnt(std::cos(a.v)); }
+inline double val(const Cnt& a) { return a.v; }
+
 // ---- symmetric 5x5 storage ----------------------------------------------
 // order 00 01 02 03 04 11 12 13 14 22 23 24 33 34 44
 inline int sidx(int i, int j) {
@@ -1556,6 +1591,26 @@ int orc_merge_chi2(const float* y, const float* z, const uint16_t* row, const in
     if (!merge_chi2_value(A, B, *prm, *chi2)) return 2;
     double c2;
     *gates_pass = merge_chi2(A, B, z, *prm, c2) ? 1 : 0;
+    return 0;
+}
+
+int orc_kf_ops(const float* y, const float* z, const uint16_t* row, const int32_t* sec,
+               const int32_t* trk_off, const int32_t* trk_hits, int32_t T, const orc_params* prm,
+               double* ops, int64_t* steps) {
+    auto no_align = [](int) -> const Cnt* { return nullptr; };
+    long long total = 0;
+    int64_t n_steps = 0;
+    for (int t = 0; t < T; ++t) {
+        const int n = trk_off[t + 1] - trk_off[t];
+        if (n < 3) continue;
+        Cnt p[5], C[15], chi2;
+        g_ops = 0;
+        if (!kf_fit<Cnt>(y, z, row, sec, trk_hits + trk_off[t], n, true, *prm, no_align, p, C, chi2)) continue;
+        total += g_ops;
+        n_steps += n;
+    }
+    *ops = (double)total;
+    *steps = n_steps;
     return 0;
 }
 

@@ -140,6 +140,15 @@ int orc_merge_chi2(const float* y, const float* z, const uint16_t* row, const in
                    int32_t na, int32_t sec_a, const int32_t* hits_b, int32_t nb, int32_t sec_b,
                    const orc_params* prm, double* chi2, int32_t* gates_pass);
 
+/* Work of the fit: the arithmetic operations (+ - * /, square roots and
+ * arcsines; operations on exact zeros and multiplications by exact ones,
+ * the Jacobians' structure, not counted) that the FP64 fit of the given
+ * tracks performs, summed, and the number of Kalman steps (clusters)
+ * taken.  Single-threaded.  Returns 0. */
+int orc_kf_ops(const float* y, const float* z, const uint16_t* row, const int32_t* sec,
+               const int32_t* trk_off, const int32_t* trk_hits, int32_t T,
+               const orc_params* prm, double* ops, int64_t* steps);
+
 /* One propagation: state p (y, z, sin phi, tan lambda, q/pT) at plane x1 of
  * sector s1 -> plane x2 of sector s2.  Writes p_out[5], jac[25] (row-major
  * d p_out / d p) and dx1[5], dx2[5].  Returns 0, or 1 when it fails. */
