@@ -66,8 +66,9 @@ TRAFFIC_BYTES_PER_LAUNCH = {"k_tracklet_lanes": 38.144e6 + 2.447e6, "k_fit": 23.
 
 def batched_vs_plain(torch, tpc, dev, steps):
     """512 events of log-uniform multiplicity (10..1e4 tracks, noise 5-30%):
-    the whole batch as one autotuned, graph-captured call vs the plain path
-    (one load + find + fit per event).  Both give identical tracks."""
+    the whole batch as one autotuned call captured in the library's CUDA
+    graph (tpc_graph_capture / tpc_graph_launch) vs the plain path (one load
+    + find + fit per event).  Both give identical tracks."""
     from paper_2412_13755_gb300 import synth
     t0 = time.perf_counter()
     ev = synth.uneven_batch_parallel()
@@ -87,30 +88,18 @@ def batched_vs_plain(torch, tpc, dev, steps):
             torch.empty(cap, dtype=torch.float32, device=dev), torch.empty(cap, dtype=torch.int32, device=dev))
     trb.load(y, z, row, d_off, E)
     tune = trb.autotune(out=outb)
-
-    def step_b():
-        trb.load(y, z, row, d_off, E)
-        trb.find(out=outb)
-        trb.fit(outb[1], outb[2], cap, outb[3], out=fitb)
-
-    side = torch.cuda.Stream(dev)
-    side.wait_stream(torch.cuda.current_stream(dev))
-    with torch.cuda.stream(side):
-        step_b()
-    torch.cuda.current_stream(dev).wait_stream(side)
-    graph = torch.cuda.CUDAGraph()
+    # the library's own graph of the whole batch call (load, find, fit)
+    trb.capture(y, z, row, d_off, E, outb, fitb)
     l0 = trb.stats().n_launches
-    with torch.cuda.graph(graph):
-        step_b()
-    graph_kernels = int(trb.stats().n_launches - l0)  # kernels captured in the graph
-    graph.replay()
+    trb.replay()
     torch.cuda.synchronize()
+    graph_kernels = int(trb.stats().n_launches - l0)  # kernels of one replay
     stb = trb.check()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(steps):
-        graph.replay()
+        trb.replay()
     e1.record()
     torch.cuda.synchronize()
     batched_s = e0.elapsed_time(e1) / 1e3 / steps
@@ -161,7 +150,8 @@ def batched_vs_plain(torch, tpc, dev, steps):
         "batched_clusters_per_s": n / batched_s, "plain_clusters_per_s": n / plain_s,
         "speedup": plain_s / batched_s, "batched_ms": 1e3 * batched_s, "plain_ms": 1e3 * plain_s,
         "identical_tracks": identical, "tracks": int(stb.n_tracks),
-        "tune": {"lane_blocks_per_sm": tune.lane_blocks_per_sm, "lane_tile": tune.lane_tile},
+        "tune": {"lane_blocks_per_sm": tune.lane_blocks_per_sm, "lane_tile": tune.lane_tile,
+                 "nb_sub_lanes": tune.nb_sub_lanes},
         "graph_kernels_per_step": graph_kernels, "generation_s": gen_s,
         "inputs_vs_l2": "1.5 GB of inputs, larger than L2 (no flush needed)",
     }

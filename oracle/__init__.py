@@ -34,6 +34,7 @@ class Params(C.Structure):
         ("seed_qpt_max", C.c_double),
         ("snp_max", C.c_double),
         ("s2_fp64", C.c_int32),
+        ("mat_x_x0", C.c_double), ("mat_eloss", C.c_double), ("mass", C.c_double),
     ]
 
 
@@ -331,3 +332,20 @@ def kf_ops(y, z, row, sector_of, trk_off, trk_hits, params=None):
     lib().orc_kf_ops(_p(y), _p(z), _p(row), _p(sec), _p(off), _p(hits), C.c_int32(off.shape[0] - 1),
                      C.byref(prm), C.byref(ops), C.byref(steps))
     return ops.value, steps.value
+
+
+def smooth_tracks(y, z, row, sector_of, trk_off, trk_hits, params=None):
+    """Inward fit plus Rauch-Tung-Striebel smoother: (smoothed[n_hits, 20]
+    (state 5 + covariance 15 per hit of the lists, list order), chi2[T],
+    ndf[T])."""
+    y, z, row = _c(y, np.float32), _c(z, np.float32), _c(row, np.uint16)
+    sec = _c(sector_of, np.int32)
+    off, hits = _c(trk_off, np.int32), _c(trk_hits, np.int32)
+    T = off.shape[0] - 1
+    prm = params or default_params()
+    out = np.zeros((max(int(off[-1]), 1), 20))
+    chi2 = np.empty(T)
+    ndf = np.empty(T, np.int32)
+    lib().orc_smooth_tracks(_p(y), _p(z), _p(row), _p(sec), _p(off), _p(hits), C.c_int32(T),
+                            C.byref(prm), _p(out), _p(chi2), _p(ndf))
+    return out[:int(off[-1])], chi2, ndf

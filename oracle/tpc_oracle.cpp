@@ -27,6 +27,7 @@
 #include <functional>
 #include <limits>
 #include <vector>
+#include <type_traits>
 
 #ifdef _OPENMP
 #include <omp.h>
@@ -402,14 +403,101 @@ struct NoDisp {
     std::nullptr_t operator()(int) const { return nullptr; }
 };
 
+// ---- NEXT-3: material in the pad-row planes --------------------------------
+// The material of one plane acts on a track right after it crosses the
+// plane: a multiple-scattering deflection (two independent projected angles
+// of width theta0, the Highland formula for x/X0 = mat_x_x0 times the path
+// factor 1/(cos phi cos lambda)) and the mean energy loss mat_eloss times
+// the same factor.  A fit that moves against the motion (inward) undoes the
+// plane it arrives at: the energy is restored, then the deflection's
+// covariance is added, so the state is the one arriving at the plane.  A
+// fit along the motion applies the plane after its update.  With the angles
+// dphi = theta1 / cos(lambda), dlambda = theta2:
+//   Q_ss = theta0^2 cos^2(phi) (1 + t^2),  Q_tt = theta0^2 (1 + t^2)^2,
+//   Q_tw = theta0^2 (1 + t^2) w t,          Q_ww = theta0^2 w^2 t^2,
+// and the energy change maps w' = w p / p' (p^2 = (1 + t^2) / w^2), whose
+// Jacobian row d w'/d(t, w) transforms the covariance first.
+// The energy change of one plane: w' and its derivatives d w'/d w and
+// d w'/d t (the loss itself taken as fixed), and the momentum and energy
+// arriving at the plane (before the loss).
+template <class T>
+struct ElossMap {
+    T w2, dw_dw, dw_dt, p_arr, e_arr;
+};
+template <class T>
+ElossMap<T> eloss_map(const T p[5], const orc_params& prm, bool undo) {
+    const T s = p[2], t = p[3], w = p[4];
+    const T c2 = 1.0 - s * s;
+    const T tt = 1.0 + t * t;
+    const T path = sqrt(tt / c2);                      // 1 / (cos phi cos lambda)
+    const T pm = sqrt(tt) / (val(w) >= 0 ? w : -w);    // momentum before this step
+    const double m2 = prm.mass * prm.mass;
+    const T e = sqrt(pm * pm + m2);
+    ElossMap<T> m{w, T(1.0), T(0.0), pm, e};
+    if (prm.mat_eloss > 0.0) {
+        const T de = path * prm.mat_eloss;
+        const T e2 = undo ? e + de : e - de;
+        const T p2 = sqrt(e2 * e2 - m2);
+        const T r = e2 * pm * pm / (p2 * p2 * e);
+        m.w2 = w * pm / p2;
+        m.dw_dw = m.w2 / w * r;
+        m.dw_dt = m.w2 * t / tt * (1.0 - r);
+        if (undo) {
+            m.p_arr = p2;
+            m.e_arr = e2;
+        }
+    }
+    return m;
+}
+
+template <class T>
+void material_step(T p[5], T C[15], const orc_params& prm, bool undo) {
+    if (prm.mat_x_x0 <= 0.0 && prm.mat_eloss <= 0.0) return;
+    const ElossMap<T> m = eloss_map(p, prm, undo);
+    if (prm.mat_eloss > 0.0) {
+        // C' = J C J^T, J = identity except row 4 = (0, 0, 0, dw_dt, dw_dw)
+        T row4[5];
+        for (int i = 0; i < 5; ++i) row4[i] = m.dw_dt * C[sidx(3, i)] + m.dw_dw * C[sidx(4, i)];
+        const T c44 = m.dw_dt * row4[3] + m.dw_dw * row4[4];
+        for (int i = 0; i < 4; ++i) C[sidx(4, i)] = row4[i];
+        C[sidx(4, 4)] = c44;
+        p[4] = m.w2;
+    }
+    if (prm.mat_x_x0 > 0.0) {
+        const T s = p[2], t = p[3], wn = p[4];
+        const T c2 = 1.0 - s * s;
+        const T tt = 1.0 + t * t;
+        const T xx0 = sqrt(tt / c2) * prm.mat_x_x0;
+        const T beta = m.p_arr / m.e_arr;
+        // Highland: 13.6 MeV / (beta c p) sqrt(x/X0) (1 + 0.038 ln(x/X0))
+        const T lnx = T(std::log(val(xx0)));
+        const T th0 = 0.0136 / (beta * m.p_arr) * sqrt(xx0) * (1.0 + 0.038 * lnx);
+        const T q = th0 * th0;
+        C[sidx(2, 2)] += q * c2 * tt;
+        C[sidx(3, 3)] += q * tt * tt;
+        C[sidx(3, 4)] += q * tt * wn * t;
+        C[sidx(4, 4)] += q * wn * wn * t * t;
+    }
+}
+
+// What a recording fit hands out per hit j: the state predicted at the hit's
+// plane (after the transport and the material, before the update), the
+// filtered state after the update, and the Jacobian of the prediction with
+// respect to the previous filtered state (identity for j = 0).
+struct NoRec {
+    template <class T> void operator()(int, const T*, const T*, const T*, const T*, const T*) const {}
+};
+
 // One full fit.  th(i) returns the 6 correction parameters of cluster hit i's
 // sector as T (or null alignment); disp(j) returns the displacement (x, y, z)
 // added to the j-th cluster of the list after the alignment (or null).
 // Returns false when a transport fails.
-template <class T, class ThFn, class DispFn = NoDisp>
+template <class T, class ThFn, class DispFn = NoDisp, class RecFn = NoRec>
 bool kf_fit(const float* y, const float* z, const uint16_t* row, const int32_t* sec,
             const int32_t* hits, int n, bool first_is_outer, const orc_params& prm,
-            ThFn th, T p[5], T C[15], T& chi2, T* xlast = nullptr, DispFn disp = DispFn()) {
+            ThFn th, T p[5], T C[15], T& chi2, T* xlast = nullptr, DispFn disp = DispFn(),
+            RecFn rec = RecFn()) {
+    constexpr bool REC = !std::is_same<RecFn, NoRec>::value;
     const Seed sd = make_seed(y, z, row, sec, hits, n, first_is_outer, prm);
     for (int i = 0; i < 5; ++i) p[i] = T(sd.p[i]);
     for (int i = 0; i < 15; ++i) C[i] = T(0.0);
@@ -418,6 +506,37 @@ bool kf_fit(const float* y, const float* z, const uint16_t* row, const int32_t* 
     int frame = sd.frame;
     chi2 = T(0.0);
     T J[25], dX[5];
+    const bool mat = prm.mat_x_x0 > 0.0 || prm.mat_eloss > 0.0;
+    // composite Jacobian of one prediction (recording fits only)
+    T F[25];
+    auto f_reset = [&]() {
+        for (int i = 0; i < 25; ++i) F[i] = T(i % 6 == 0 ? 1.0 : 0.0);
+    };
+    auto f_chain = [&](const T* Js) {  // F <- Js F
+        T tmp[25];
+        for (int i = 0; i < 5; ++i)
+            for (int k = 0; k < 5; ++k) {
+                T acc(0.0);
+                for (int l = 0; l < 5; ++l) acc += Js[i * 5 + l] * F[l * 5 + k];
+                tmp[i * 5 + k] = acc;
+            }
+        for (int i = 0; i < 25; ++i) F[i] = tmp[i];
+    };
+    // material with its state Jacobian for the record (material_step moves
+    // the covariance itself; the recorded F needs the w row)
+    auto mat_step = [&](bool undo) {
+        if constexpr (REC) {
+            if (prm.mat_eloss > 0.0) {
+                const ElossMap<T> m = eloss_map(p, prm, undo);
+                T Jm[25];
+                for (int i = 0; i < 25; ++i) Jm[i] = T(i % 6 == 0 ? 1.0 : 0.0);
+                Jm[4 * 5 + 3] = m.dw_dt;
+                Jm[4 * 5 + 4] = m.dw_dw;
+                f_chain(Jm);
+            }
+        }
+        material_step(p, C, prm, undo);
+    };
     for (int j = 0; j < n; ++j) {
         const int h = hits[j];
         T xc, yc, zc;
@@ -435,9 +554,34 @@ bool kf_fit(const float* y, const float* z, const uint16_t* row, const int32_t* 
             yc = yc + d3[1];
             zc = zc + d3[2];
         }
+        if constexpr (REC) f_reset();
+        if (mat && j > 0) {
+            const int hp = hits[j - 1];
+            // along the motion: the previous plane acts after its update
+            if (!first_is_outer) mat_step(false);
+            // the planes crossed between the two hits (same sector)
+            if (sec[hp] == sec[h]) {
+                const int r0 = row[hp], r1 = row[h], step = r1 > r0 ? 1 : -1;
+                for (int r = r0 + step; r != r1; r += step) {
+                    if (!move_state(x, p, frame, T(row_x(r)), sec[h], J, dX, prm)) return false;
+                    cov_transform(C, J);
+                    if constexpr (REC) f_chain(J);
+                    mat_step(first_is_outer);
+                }
+            }
+        }
         if (!move_state(x, p, frame, xc, sec[h], J, dX, prm)) return false;
         cov_transform(C, J);
+        if constexpr (REC) f_chain(J);
+        // against the motion: undo the plane the track arrives at
+        if (mat && j > 0 && first_is_outer) mat_step(true);
+        T pp[5], Cp[15];
+        if constexpr (REC) {
+            for (int i = 0; i < 5; ++i) pp[i] = p[i];
+            for (int i = 0; i < 15; ++i) Cp[i] = C[i];
+        }
         kf_update(p, C, yc, zc, prm.sigma_y2, prm.sigma_z2, chi2);
+        if constexpr (REC) rec(j, pp, Cp, F, p, C);
     }
     if (xlast) *xlast = x;
     return true;
@@ -874,6 +1018,9 @@ void orc_default_params(orc_params* p) {
     p->seed_qpt_max = 5.0;
     p->snp_max = 0.999;
     p->s2_fp64 = 0;
+    p->mat_x_x0 = 0.0;
+    p->mat_eloss = 0.0;
+    p->mass = 0.13957;
 }
 
 void orc_set_threads(int n) { g_threads = n; }
@@ -1611,6 +1758,156 @@ int orc_kf_ops(const float* y, const float* z, const uint16_t* row, const int32_
     }
     *ops = (double)total;
     *steps = n_steps;
+    return 0;
+}
+
+// 5x5 SPD inverse by Cholesky (full matrix out, row-major); false when not
+// positive definite.
+static bool spd_inverse5(const double M[15], double inv[25]) {
+    double L[5][5] = {};
+    for (int i = 0; i < 5; ++i)
+        for (int j = 0; j <= i; ++j) {
+            double s = M[sidx(i, j)];
+            for (int l = 0; l < j; ++l) s -= L[i][l] * L[j][l];
+            if (i == j) {
+                if (!(s > 0)) return false;
+                L[i][i] = std::sqrt(s);
+            } else {
+                L[i][j] = s / L[j][j];
+            }
+        }
+    for (int c = 0; c < 5; ++c) {  // solve L L^T x = e_c
+        double v[5], x[5];
+        for (int i = 0; i < 5; ++i) {
+            double s = i == c ? 1.0 : 0.0;
+            for (int l = 0; l < i; ++l) s -= L[i][l] * v[l];
+            v[i] = s / L[i][i];
+        }
+        for (int i = 4; i >= 0; --i) {
+            double s = v[i];
+            for (int l = i + 1; l < 5; ++l) s -= L[l][i] * x[l];
+            x[i] = s / L[i][i];
+        }
+        for (int i = 0; i < 5; ++i) inv[i * 5 + c] = x[i];
+    }
+    return true;
+}
+
+int orc_smooth_tracks(const float* y, const float* z, const uint16_t* row, const int32_t* sec,
+                      const int32_t* trk_off, const int32_t* trk_hits, int32_t T, const orc_params* prm,
+                      double* out, double* chi2o, int32_t* ndf) {
+    const int nt = orc_get_threads();
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nt)
+    for (int t = 0; t < T; ++t) {
+        const int b = trk_off[t], n = trk_off[t + 1] - b;
+        struct Step { double pp[5], Cp[15], F[25], pf[5], Cf[15]; };
+        std::vector<Step> st((size_t)std::max(n, 0));
+        auto rec = [&](int j, const double* pp, const double* Cp, const double* F, const double* pf,
+                       const double* Cf) {
+            Step& q = st[j];
+            std::memcpy(q.pp, pp, sizeof q.pp);
+            std::memcpy(q.Cp, Cp, sizeof q.Cp);
+            std::memcpy(q.F, F, sizeof q.F);
+            std::memcpy(q.pf, pf, sizeof q.pf);
+            std::memcpy(q.Cf, Cf, sizeof q.Cf);
+        };
+        auto no_align = [](int) -> const double* { return nullptr; };
+        double p[5], C[15], chi2 = 0;
+        bool ok = n >= 3 && kf_fit<double>(y, z, row, sec, trk_hits + b, n, true, *prm, no_align, p, C, chi2,
+                                           nullptr, NoDisp(), rec);
+        // Rauch-Tung-Striebel: from the last filtered state back over the hits
+        double xs[5], Cs[15];
+        if (ok) {
+            std::memcpy(xs, st[n - 1].pf, sizeof xs);
+            std::memcpy(Cs, st[n - 1].Cf, sizeof Cs);
+            double* o = out + (size_t)(b + n - 1) * 20;
+            std::memcpy(o, xs, sizeof xs);
+            std::memcpy(o + 5, Cs, sizeof Cs);
+        }
+        for (int j = n - 2; j >= 0 && ok; --j) {
+            const Step &f = st[j], &nx = st[j + 1];
+            double Pinv[25];
+            if (!spd_inverse5(nx.Cp, Pinv)) {
+                ok = false;
+                break;
+            }
+            // A = Cf F^T Pinv
+            double CfF[25], A[25];
+            for (int i = 0; i < 5; ++i)
+                for (int k = 0; k < 5; ++k) {
+                    double acc = 0;
+                    for (int l = 0; l < 5; ++l) acc += f.Cf[sidx(i, l)] * nx.F[k * 5 + l];
+                    CfF[i * 5 + k] = acc;
+                }
+            for (int i = 0; i < 5; ++i)
+                for (int k = 0; k < 5; ++k) {
+                    double acc = 0;
+                    for (int l = 0; l < 5; ++l) acc += CfF[i * 5 + l] * Pinv[l * 5 + k];
+                    A[i * 5 + k] = acc;
+                }
+            // state: the smoothed state of hit j + 1 moved back to hit j
+            // along the motion (xb = f^-1(xs)), then
+            //   xn = xb + (I - A F) (pf - xb),
+            // which is the textbook pf + A (xs - f(pf)) for a linear f and
+            // exact for a deterministic segment (A F = I without material)
+            double xb[5], xq = row_x(row[trk_hits[b + j + 1]]);
+            std::memcpy(xb, xs, sizeof xb);
+            {
+                const int h1 = trk_hits[b + j + 1], h0 = trk_hits[b + j];
+                int frame = sec[h1];
+                double Cd[15] = {}, Jd[25], dX[5];
+                const bool mat = prm->mat_x_x0 > 0.0 || prm->mat_eloss > 0.0;
+                if (mat) material_step(xb, Cd, *prm, false);
+                if (mat && sec[h0] == sec[h1]) {
+                    const int r0 = row[h1], r1 = row[h0], stp = r1 > r0 ? 1 : -1;
+                    for (int r = r0 + stp; r != r1 && ok; r += stp) {
+                        ok = move_state<double>(xq, xb, frame, row_x(r), sec[h0], Jd, dX, *prm);
+                        if (ok) material_step(xb, Cd, *prm, false);
+                    }
+                }
+                if (ok) ok = move_state<double>(xq, xb, frame, row_x(row[h0]), sec[h0], Jd, dX, *prm);
+                if (!ok) break;
+            }
+            double AF[25];
+            for (int i = 0; i < 5; ++i)
+                for (int k = 0; k < 5; ++k) {
+                    double acc = 0;
+                    for (int l = 0; l < 5; ++l) acc += A[i * 5 + l] * nx.F[l * 5 + k];
+                    AF[i * 5 + k] = acc;
+                }
+            double D[25], xn[5], Cn[15];
+            for (int i = 0; i < 5; ++i) {
+                double acc = xb[i];
+                for (int l = 0; l < 5; ++l) acc += ((i == l ? 1.0 : 0.0) - AF[i * 5 + l]) * (f.pf[l] - xb[l]);
+                xn[i] = acc;
+            }
+            for (int i = 0; i < 5; ++i)
+                for (int k = 0; k < 5; ++k) D[i * 5 + k] = Cs[sidx(i, k)] - nx.Cp[sidx(i, k)];
+            double AD[25];
+            for (int i = 0; i < 5; ++i)
+                for (int k = 0; k < 5; ++k) {
+                    double acc = 0;
+                    for (int l = 0; l < 5; ++l) acc += A[i * 5 + l] * D[l * 5 + k];
+                    AD[i * 5 + k] = acc;
+                }
+            for (int i = 0; i < 5; ++i)
+                for (int k = i; k < 5; ++k) {
+                    double acc = f.Cf[sidx(i, k)];
+                    for (int l = 0; l < 5; ++l) acc += AD[i * 5 + l] * A[k * 5 + l];
+                    Cn[sidx(i, k)] = acc;
+                }
+            std::memcpy(xs, xn, sizeof xs);
+            std::memcpy(Cs, Cn, sizeof Cs);
+            double* o = out + (size_t)(b + j) * 20;
+            std::memcpy(o, xs, sizeof xs);
+            std::memcpy(o + 5, Cs, sizeof Cs);
+        }
+        if (!ok)
+            for (int j = 0; j < n; ++j)
+                for (int i = 0; i < 20; ++i) out[(size_t)(b + j) * 20 + i] = 0.0;
+        chi2o[t] = ok ? chi2 : 0.0;
+        ndf[t] = ok ? 2 * n - 5 : -1;
+    }
     return 0;
 }
 

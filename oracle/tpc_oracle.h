@@ -43,6 +43,11 @@ typedef struct {
     int32_t s2_fp64;          /* 1: window tests and triplet D^2 in FP64 (a
                                  diagnostic mode; 0, the default, decides in
                                  FP32 with one rounding per operation)      */
+    double mat_x_x0;          /* material of one pad-row plane, radiation
+                                 lengths at normal incidence (0: none)      */
+    double mat_eloss;         /* mean energy loss in one plane at normal
+                                 incidence (GeV; 0: none)                   */
+    double mass;              /* particle mass for the material (GeV)       */
 } orc_params;
 
 /* Fills the default parameter set of the build's reading. */
@@ -148,6 +153,17 @@ int orc_merge_chi2(const float* y, const float* z, const uint16_t* row, const in
 int orc_kf_ops(const float* y, const float* z, const uint16_t* row, const int32_t* sec,
                const int32_t* trk_off, const int32_t* trk_hits, int32_t T,
                const orc_params* prm, double* ops, int64_t* steps);
+
+/* NEXT-3: the fit with a Rauch-Tung-Striebel smoother.  The inward fit of
+ * each track (material per the orc_params) records, per hit, its predicted
+ * and filtered states and the prediction's Jacobian; the smoother then runs
+ * back from the innermost hit.  out[(trk_off[t] + j) * 20 ...] receives the
+ * smoothed state (5) and covariance (15) at the j-th hit of track t (list
+ * order, outermost first; the state arriving at that hit's plane).  chi2 and
+ * ndf as for orc_fit_tracks.  A failed track gets zeros and ndf -1. */
+int orc_smooth_tracks(const float* y, const float* z, const uint16_t* row, const int32_t* sector_of,
+                      const int32_t* trk_off, const int32_t* trk_hits, int32_t n_tracks,
+                      const orc_params* prm, double* out, double* chi2, int32_t* ndf);
 
 /* One propagation: state p (y, z, sin phi, tan lambda, q/pT) at plane x1 of
  * sector s1 -> plane x2 of sector s2.  Writes p_out[5], jac[25] (row-major

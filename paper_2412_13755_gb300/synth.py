@@ -560,3 +560,95 @@ def alignment_sample(n_tracks=200000, seed=SEED_BASE + 4, misalign=None,
 
 CONFIG_NAMES = ("one_sector", "central_event", "pileup_frame", "uneven_batch",
                 "alignment_sample")
+
+
+# --- tracks through material (Kalman-filter variants) ---------------------------
+
+PION_MASS = 0.13957      # GeV/c^2
+MAT_X_X0_ROW = 1e-4      # radiation lengths of one pad-row layer at normal incidence
+MAT_ELOSS_ROW = 2e-6     # GeV lost in one pad-row layer at normal incidence
+
+
+def highland_theta0(p, beta, x_x0):
+    """Width (rad) of the projected multiple-scattering angle after x_x0
+    radiation lengths for a unit-charge particle of momentum p (GeV/c) and
+    velocity beta (the Highland formula, PDG Review of Particle Physics)."""
+    x = np.maximum(x_x0, 1e-300)
+    return np.where(x_x0 > 0, 0.0136 / (beta * p) * np.sqrt(x) * (1.0 + 0.038 * np.log(x)), 0.0)
+
+
+def material_tracks(n_tracks=2000, seed=SEED_BASE + 6, x_x0_row=MAT_X_X0_ROW,
+                    eloss_row=MAT_ELOSS_ROW, mass=PION_MASS, pt_min=0.3, pt_slope=0.5,
+                    sector=0):
+    """Pions from the origin through the pad rows of one sector, with
+    material concentrated in the row planes: each plane the track crosses
+    deflects it by two independent Gaussian angles of width theta0 (Highland,
+    x/X0 = x_x0_row times the path factor 1/(cos phi cos lambda)) and takes
+    eloss_row times the same factor off its energy, after the crossing is
+    recorded.  Between planes the track is an exact helix in Bz.
+
+    Returns an Events batch of one event (clusters smeared as everywhere
+    else, no noise) whose truth arrays hold, per cluster, the state arriving
+    at its plane (before that plane's deflection and loss): y_true, z_true,
+    snp_true and, as attributes, tgl_true and qpt_true."""
+    rng = np.random.default_rng(seed)
+    q = np.where(rng.uniform(size=n_tracks) < 0.5, 1.0, -1.0)
+    pt = pt_min + rng.exponential(pt_slope, n_tracks)
+    lam = np.arctan(np.sinh(rng.uniform(-0.9, 0.9, n_tracks)))
+    phi = rng.uniform(-0.06, 0.06, n_tracks)           # local direction at the origin
+    lam0, phi0 = lam.copy(), phi.copy()
+    p = pt / np.cos(lam)
+    e = np.sqrt(p * p + mass * mass)
+    xs, ys, zs = np.zeros(n_tracks), np.zeros(n_tracks), np.zeros(n_tracks)
+    alive = np.ones(n_tracks, bool)
+    rec = []
+    for r in range(N_ROWS):
+        xr = ROW_X[r]
+        k = KAPPA * BZ * q / (p * np.cos(lam))
+        s0 = np.sin(phi)
+        s1 = s0 - k * (xr - xs)
+        alive &= np.abs(s1) < 0.9
+        s1 = np.clip(s1, -0.9, 0.9)
+        c0, c1 = np.sqrt(1 - s0 * s0), np.sqrt(1 - s1 * s1)
+        y1 = ys + (c1 - c0) / k
+        arc = (np.arcsin(s0) - np.arcsin(s1)) / k
+        z1 = zs + np.tan(lam) * arc
+        alive &= (np.abs(y1) <= xr * TAN_HALF_SECTOR) & (np.abs(z1) < Z_MAX)
+        idx = np.nonzero(alive)[0]
+        if idx.size == 0:
+            break
+        rec.append((idx, np.full(idx.size, r), y1[idx], z1[idx], s1[idx], np.tan(lam[idx]),
+                    (q / (p * np.cos(lam)))[idx]))
+        # the plane's material: deflection, then energy loss
+        phi = np.arcsin(s1)
+        path = 1.0 / (c1 * np.cos(lam))
+        beta = p / e
+        th0 = highland_theta0(p, beta, x_x0_row * path)
+        phi = phi + rng.normal(0.0, 1.0, n_tracks) * th0 / np.cos(lam)
+        lam = lam + rng.normal(0.0, 1.0, n_tracks) * th0
+        e = e - eloss_row * path
+        alive &= e > mass * 1.001
+        p = np.sqrt(np.maximum(e * e - mass * mass, 1e-12))
+        xs, ys, zs = np.full(n_tracks, xr), y1, z1
+    tr, row, yt, zt, st, tt, wt = (np.concatenate([a[j] for a in rec]) for j in range(7))
+    keep = rng.uniform(size=tr.shape[0]) >= ROW_DROP
+    tr, row, yt, zt, st, tt, wt = (v[keep] for v in (tr, row, yt, zt, st, tt, wt))
+    ym = yt + rng.normal(0.0, SIGMA_Y, yt.shape[0])
+    zm = zt + rng.normal(0.0, SIGMA_Z, zt.shape[0])
+    # a track's clusters go to the sector of its side at the origin (a
+    # scattering that carries a flat track across z = 0 does not move them)
+    sec = sector % N_PHI + N_PHI * (lam0[tr] < 0)
+    order = np.lexsort((tr, sec))
+    counts = np.bincount(sec, minlength=N_SECTORS)
+    off = np.zeros(N_SECTORS + 1, np.int64)
+    off[1:] = np.cumsum(counts)
+    ev = Events(y=ym[order].astype(np.float32), z=zm[order].astype(np.float32),
+                row=row[order].astype(np.uint16), charge=np.full(len(order), 50, np.uint16),
+                evt_sector_off=off, n_events=1, mc_track=tr[order].astype(np.int32),
+                trk_q=q, trk_pt=pt, trk_tgl=np.tan(lam0),
+                trk_phi0=phi0 + float(sector_alpha(sector)), trk_event=np.zeros(n_tracks, np.int32),
+                trk_t0=np.zeros(n_tracks))
+    ev.arc_true = ROW_X[row[order]]
+    ev.y_true, ev.z_true, ev.snp_true = yt[order], zt[order], st[order]
+    ev.tgl_true, ev.qpt_true = tt[order], wt[order]
+    return ev
