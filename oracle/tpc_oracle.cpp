@@ -832,17 +832,23 @@ inline double rel_gap(double u, double v) {
 
 void extend_tracklet(const float* y, const float* z, const std::vector<std::vector<int32_t>>& rows,
                      int sector, double& x, double p[5], double C[15], int r_start, int dir,
-                     const orc_params& prm, std::vector<int32_t>& added, Decisions* dec = nullptr) {
+                     const orc_params& prm, std::vector<int32_t>& added, Decisions* dec = nullptr,
+                     double* stop_margin = nullptr) {
     int misses = 0;
     for (int r = r_start; r >= 0 && r < NROW; r += dir) {
         double J[25], dX[5];
         int frame = sector;
+        if (stop_margin) {  // diagnostics: the transport's |sin phi| limit
+            const double s2 = p[2] - KAPPA * prm.bz * p[4] * (row_x(r) - x);
+            *stop_margin = std::min(*stop_margin, rel_gap(std::fabs(s2), prm.snp_max));
+        }
         if (!move_state<double>(x, p, frame, row_x(r), sector, J, dX, prm)) break;
         // the state and its covariance move together, so that the state the
         // extension ends with is consistent at its plane
         cov_transform(C, J);
         // the track has left the sector when its prediction is outside the
         // row's acceptance |y| <= x tan(10 deg)
+        if (stop_margin) *stop_margin = std::min(*stop_margin, rel_gap(std::fabs(p[0]), row_x(r) * TAN_HALF));
         if (std::fabs(p[0]) > row_x(r) * TAN_HALF) break;
         const double S00 = C[sidx(0, 0)] + prm.sigma_y2, S01 = C[sidx(0, 1)], S11 = C[sidx(1, 1)] + prm.sigma_z2;
         const double det = S00 * S11 - S01 * S01;
@@ -902,9 +908,13 @@ std::vector<int32_t> build_tracklet(const float* y, const float* z, const uint16
     std::vector<int32_t> H = sg.hits;
     double p[5], C[15], chi2, x;
     bool have_out = false;
+    // diagnostics: the smallest margin of the decisions that end the two
+    // extensions (acceptance edge, transport limit), charged to every hit
+    double stop = std::numeric_limits<double>::infinity();
+    double* stop_p = dec ? &stop : nullptr;
     if (kf_fit<double>(y, z, row, sec, H.data(), (int)H.size(), true, prm, no_align, p, C, chi2, &x)) {
         std::vector<int32_t> add;
-        extend_tracklet(y, z, rows, sg.sector, x, p, C, row[H.back()] - 1, -1, prm, add, dec);
+        extend_tracklet(y, z, rows, sg.sector, x, p, C, row[H.back()] - 1, -1, prm, add, dec, stop_p);
         H.insert(H.end(), add.begin(), add.end());
         have_out = move_to_row(x, p, C, sg.sector, row[H.front()], prm);
     }
@@ -915,11 +925,13 @@ std::vector<int32_t> build_tracklet(const float* y, const float* z, const uint16
     }
     if (have_out) {
         std::vector<int32_t> add;
-        extend_tracklet(y, z, rows, sg.sector, x, p, C, row[H.front()] + 1, +1, prm, add, dec);
+        extend_tracklet(y, z, rows, sg.sector, x, p, C, row[H.front()] + 1, +1, prm, add, dec, stop_p);
         std::vector<int32_t> H2(add.rbegin(), add.rend());
         H2.insert(H2.end(), H.begin(), H.end());
         H.swap(H2);
     }
+    if (dec && stop < std::numeric_limits<double>::infinity())
+        for (int32_t h : H) dec->push_back({h, stop});
     return H;
 }
 
