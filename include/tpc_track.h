@@ -242,23 +242,30 @@ tpc_status tpc_fit_adjoint_field(tpc_ctx* ctx, const int32_t* trk_off, const int
 tpc_status tpc_get_stats(tpc_ctx* ctx, tpc_stats* out, tpc_stream_t stream);
 tpc_status tpc_last_error(tpc_ctx* ctx, char* buf, size_t len);
 
-/* Launch configuration of the persistent work-queue kernels (the tracklet
- * lanes): persistent blocks per SM and the number of segments a lane takes
- * from the queue per atomic ticket. */
+/* Launch configuration of the work-queue kernels (S7, the batched path;
+ * the paper gives none).  Two stages consume device-side queues: the
+ * tracklet lanes (persistent blocks taking segments by atomic ticket) and
+ * the second neighbour pass (clusters queued by the first pass, one
+ * sub-warp each). */
 typedef struct {
-    int32_t lane_blocks_per_sm; /* 1..16                                   */
-    int32_t lane_tile;          /* 1..16                                   */
+    int32_t lane_blocks_per_sm; /* tracklet lanes: persistent blocks per SM, 1..16 */
+    int32_t lane_tile;          /* tracklet lanes: segments per ticket, 1..16       */
+    int32_t nb_sub_lanes;       /* second neighbour pass: lanes per queued cluster,
+                                   4, 8 or 16                                        */
 } tpc_tune;
 
 /* Sets the configuration used by later calls (NULL restores the default
- * 8 blocks/SM, tile 1). */
+ * 8 blocks/SM, tile 1, 8 lanes per queued cluster). */
 tpc_status tpc_set_tune(tpc_ctx* ctx, const tpc_tune* tune);
 
 /* Autotuner: runs tpc_find_tracks on the loaded batch (outputs into the
- * given buffers, as tpc_find_tracks) for each candidate configuration
- * (blocks/SM in {4, 8, 16} x tile in {1, 4}), times each with CUDA events on
- * the stream, keeps the fastest for later calls and writes it to *best (may
- * be NULL).  Synchronises the stream; not for use during graph capture. */
+ * given buffers, as tpc_find_tracks) per candidate configuration and times
+ * each with CUDA events on the stream (a warm-up pass, then a timed pass).
+ * Coordinate search: the second neighbour pass's lanes per queued cluster
+ * in {4, 8, 16}, then the tracklet lanes' blocks/SM in {4, 8, 16} x tile
+ * in {1, 4}.  Keeps the fastest for later calls and writes it to *best (may
+ * be NULL).  Every configuration gives the same tracks.  Synchronises the
+ * stream; not for use during graph capture. */
 tpc_status tpc_autotune(tpc_ctx* ctx, int32_t* track_of_cluster, int32_t* trk_off,
                         int32_t* trk_hits, int32_t* n_tracks_dev, int32_t track_cap,
                         tpc_tune* best, tpc_stream_t stream);
@@ -311,6 +318,74 @@ tpc_status tpc_find_tracks_noalloc(const tpc_params* params, const float* y, con
                                    int32_t n_events, int32_t* track_of_cluster, int32_t* trk_off,
                                    int32_t* trk_hits, int32_t* n_tracks_dev, int32_t* status_dev,
                                    int32_t track_cap, tpc_stream_t stream);
+
+/* S7: the whole tracking path over one batch in one call (paper Sec. 4: a
+ * time frame is processed in one operation inside GPU memory): S0 load and
+ * validation, S1-S4 find, and, when params is not NULL, the S5 fit of every
+ * found track, all enqueued on `stream` without a host synchronisation.
+ * Inputs as for tpc_load_clusters (the batch stays registered, as after
+ * that call); find outputs as for tpc_find_tracks; fit outputs have
+ * track_cap rows (params[5], cov[15], chi2, ndf per track), of which the
+ * first *n_tracks_dev are written.  Events of any size mix in one batch:
+ * every kernel runs over all events at once, and the two queued stages
+ * take their work from device-side queues (see tpc_tune). */
+typedef struct {
+    int32_t* track_of_cluster; /* [n]                                      */
+    int32_t* trk_off;          /* [track_cap + 1]                          */
+    int32_t* trk_hits;         /* [n]                                      */
+    int32_t* n_tracks_dev;     /* [1]                                      */
+    int32_t track_cap;
+    float* params;             /* [track_cap * 5] or NULL: no fit          */
+    float* cov;                /* [track_cap * 15]                         */
+    float* chi2;               /* [track_cap]                              */
+    int32_t* ndf;              /* [track_cap]                              */
+} tpc_batch_outputs;
+tpc_status tpc_track_batch(tpc_ctx* ctx, const float* y, const float* z, const uint16_t* row,
+                           const uint16_t* charge, int64_t n, const int64_t* evt_sector_off,
+                           int32_t n_events, const tpc_batch_outputs* out, tpc_stream_t stream);
+
+/* S7 as one CUDA graph held by the context: records tpc_track_batch with
+ * these arguments (every kernel of load, find and fit) into a graph on a
+ * stream of the library's own and instantiates it, replacing any graph the
+ * context held; nothing runs.  tpc_graph_launch then runs the whole batch
+ * as one graph launch on `stream`.  A replay reads the same input and
+ * output buffers, so refill the inputs in place between replays (the
+ * sizes n and n_events are fixed by the capture).  The stage timing is off
+ * inside the graph.  TPC_ERR_STATE from tpc_graph_launch if nothing was
+ * captured. */
+tpc_status tpc_graph_capture(tpc_ctx* ctx, const float* y, const float* z, const uint16_t* row,
+                             const uint16_t* charge, int64_t n, const int64_t* evt_sector_off,
+                             int32_t n_events, const tpc_batch_outputs* out);
+tpc_status tpc_graph_launch(tpc_ctx* ctx, tpc_stream_t stream);
+
+/* NEXT-3, Kalman-filter variants of the S5 fit (the paper is silent; the
+ * standard refinements of a track fit).  Material concentrated in the
+ * pad-row planes: a track crossing a plane is deflected by multiple
+ * scattering (two projected angles of the Highland width for mat_x_x0
+ * radiation lengths times the path factor 1/(cos phi cos lambda), as
+ * process noise in sin phi, tan lambda and q/pT) and loses mat_eloss GeV
+ * times the same factor (a deterministic map of q/pT); the fit crosses every
+ * plane between two clusters of one sector.  direction 0 fits inward (state
+ * arriving at the innermost cluster), 1 outward, along the motion (the
+ * outward refit: state arriving at the outermost cluster). */
+typedef struct {
+    float mat_x_x0;    /* radiation lengths of one plane at normal incidence (0: none) */
+    float mat_eloss;   /* mean energy loss in one plane at normal incidence, GeV (0: none) */
+    float mass;        /* particle mass, GeV (the pion's by default)                 */
+    int32_t direction; /* 0 inward, 1 outward                                        */
+} tpc_fit_options;
+
+/* tpc_fit_tracks with the options above (NULL: no material, inward), in
+ * FP64 per track; outputs as for tpc_fit_tracks.  smoothed (device, may be
+ * NULL; inward fits only, else TPC_ERR_ARG) receives for every cluster of
+ * every fitted track the Rauch-Tung-Striebel smoothed state (5) and
+ * covariance (15, packed as cov) at that cluster's plane, as doubles at
+ * smoothed[20 * (trk_off[t] + j) ...] for the j-th cluster of track t (list
+ * order); a failed track's entries are zero. */
+tpc_status tpc_fit_tracks_ex(tpc_ctx* ctx, const int32_t* trk_off, const int32_t* trk_hits,
+                             int32_t n_tracks, const int32_t* n_tracks_dev,
+                             const tpc_fit_options* options, float* params, float* cov,
+                             float* chi2, int32_t* ndf, double* smoothed, tpc_stream_t stream);
 
 /* Clears the device status word and counters (asynchronous). */
 tpc_status tpc_reset_status(tpc_ctx* ctx, tpc_stream_t stream);

@@ -186,6 +186,7 @@ void tpc_destroy(tpc_ctx* ctx) {
     if (!ctx) return;
     for (auto& e : ctx->marks)
         if (e) cudaEventDestroy(e);
+    if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
     delete ctx;
 }
 
@@ -236,6 +237,10 @@ tpc_status tpc_set_workspace(tpc_ctx* c, void* dev_ptr, size_t bytes, int64_t ma
     c->ws.L = L;
     c->have_ws = true;
     c->have_clusters = false;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
+        c->n_sm = sms;
     cudaError_t e = init_geo(c->ws, nullptr);
     if (e == cudaSuccess) e = reset_status(c->ws, nullptr);
     if (e != cudaSuccess) return cuda_fail(c, e, "tpc_set_workspace");
@@ -289,6 +294,23 @@ tpc_status tpc_fit_tracks(tpc_ctx* c, const int32_t* trk_off, const int32_t* trk
     return TPC_OK;
 }
 
+tpc_status tpc_fit_tracks_ex(tpc_ctx* c, const int32_t* trk_off, const int32_t* trk_hits, int32_t n_tracks,
+                             const int32_t* n_tracks_dev, const tpc_fit_options* o, float* params, float* cov,
+                             float* chi2, int32_t* ndf, double* smoothed, tpc_stream_t stream) {
+    if (!c) return TPC_ERR_ARG;
+    if (!c->have_ws || !c->have_clusters) return fail(c, TPC_ERR_STATE, "no workspace or clusters");
+    if (n_tracks < 0 || (n_tracks > 0 && (!trk_off || !trk_hits || !params || !cov || !chi2 || !ndf)))
+        return fail(c, TPC_ERR_ARG, "tpc_fit_tracks_ex: bad argument");
+    if (o && (o->mat_x_x0 < 0.f || o->mat_eloss < 0.f || !(o->mass > 0.f) || o->direction < 0 ||
+              o->direction > 1 || (o->direction == 1 && smoothed)))
+        return fail(c, TPC_ERR_ARG, "tpc_fit_tracks_ex: bad options");
+    if (n_tracks > c->ws.L.T - 1) return fail(c, TPC_ERR_CAPACITY, "tpc_fit_tracks_ex: too many tracks");
+    cudaError_t e = run_fit_ex(c, trk_off, trk_hits, n_tracks, n_tracks_dev, o, params, cov, chi2, ndf,
+                               smoothed, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "tpc_fit_tracks_ex");
+    return TPC_OK;
+}
+
 tpc_status tpc_fit_adjoint(tpc_ctx* c, const int32_t* trk_off, const int32_t* trk_hits,
                            int32_t n_tracks, const double* align, double* chi2_total, double* grad,
                            tpc_stream_t stream) {
@@ -329,10 +351,11 @@ tpc_status tpc_fit_adjoint_field(tpc_ctx* c, const int32_t* trk_off, const int32
 tpc_status tpc_set_tune(tpc_ctx* c, const tpc_tune* t) {
     if (!c) return TPC_ERR_ARG;
     if (!t) {
-        c->tune = tpc_tune{8, 1};
+        c->tune = tpc_tune{8, 1, 8};
         return TPC_OK;
     }
-    if (t->lane_blocks_per_sm < 1 || t->lane_blocks_per_sm > 16 || t->lane_tile < 1 || t->lane_tile > 16)
+    if (t->lane_blocks_per_sm < 1 || t->lane_blocks_per_sm > 16 || t->lane_tile < 1 || t->lane_tile > 16 ||
+        (t->nb_sub_lanes != 4 && t->nb_sub_lanes != 8 && t->nb_sub_lanes != 16))
         return fail(c, TPC_ERR_ARG, "tpc_set_tune: out of range");
     c->tune = *t;
     return TPC_OK;
@@ -353,32 +376,129 @@ tpc_status tpc_autotune(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk
     }
     const bool timing = c->timing;
     c->timing = false;
-    static const int bps[3] = {4, 8, 16};
-    static const int tiles[2] = {1, 4};
     tpc_tune best_t = c->tune;
     float best_ms = 1e30f;
     cudaError_t err = cudaSuccess;
-    for (int rep = 0; rep < 2 && err == cudaSuccess; ++rep)  // first pass warms up
-        for (int bi = 0; bi < 3 && err == cudaSuccess; ++bi)
-            for (int ti = 0; ti < 2 && err == cudaSuccess; ++ti) {
-                c->tune = tpc_tune{bps[bi], tiles[ti]};
-                err = cudaEventRecord(e0, s);
-                if (err == cudaSuccess) err = run_find(c, toc, trk_off, trk_hits, n_tracks_dev, track_cap, s);
-                if (err == cudaSuccess) err = cudaEventRecord(e1, s);
-                if (err == cudaSuccess) err = cudaEventSynchronize(e1);
-                float ms = 0.f;
-                if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
-                if (err == cudaSuccess && rep == 1 && ms < best_ms) {
-                    best_ms = ms;
-                    best_t = c->tune;
-                }
-            }
+    // one find per configuration, after a warm-up find of the same one
+    auto time_find = [&](const tpc_tune& t, float& ms) {
+        c->tune = t;
+        ms = 0.f;
+        for (int rep = 0; rep < 2 && err == cudaSuccess; ++rep) {
+            err = cudaEventRecord(e0, s);
+            if (err == cudaSuccess) err = run_find(c, toc, trk_off, trk_hits, n_tracks_dev, track_cap, s);
+            if (err == cudaSuccess) err = cudaEventRecord(e1, s);
+            if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+            if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+        }
+        if (err == cudaSuccess && ms < best_ms) {
+            best_ms = ms;
+            best_t = t;
+        }
+    };
+    // coordinate search: the second neighbour pass, then the tracklet lanes
+    static const int subs[3] = {4, 8, 16};
+    for (int i = 0; i < 3 && err == cudaSuccess; ++i) {
+        tpc_tune t = best_t;
+        t.nb_sub_lanes = subs[i];
+        float ms;
+        time_find(t, ms);
+    }
+    static const int bps[3] = {4, 8, 16};
+    static const int tiles[2] = {1, 4};
+    const tpc_tune base = best_t;
+    for (int bi = 0; bi < 3 && err == cudaSuccess; ++bi)
+        for (int ti = 0; ti < 2 && err == cudaSuccess; ++ti) {
+            tpc_tune t = base;
+            t.lane_blocks_per_sm = bps[bi];
+            t.lane_tile = tiles[ti];
+            float ms;
+            time_find(t, ms);
+        }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     c->timing = timing;
     c->tune = best_t;
     if (err != cudaSuccess) return cuda_fail(c, err, "tpc_autotune");
     if (best) *best = best_t;
+    return TPC_OK;
+}
+
+// S7: load, validation, find and fit of one batch, enqueued on one stream.
+static tpc_status enqueue_batch(tpc_ctx* c, const float* y, const float* z, const uint16_t* row,
+                                const uint16_t* charge, int64_t n, const int64_t* evt_sector_off,
+                                int32_t n_events, const tpc_batch_outputs* o, cudaStream_t s,
+                                const char* what) {
+    if (!c) return TPC_ERR_ARG;
+    if (!c->have_ws) return fail(c, TPC_ERR_STATE, "no workspace");
+    if (!o || n < 0 || n_events < 1 || !evt_sector_off || (n > 0 && (!y || !z || !row)) ||
+        !o->track_of_cluster || !o->trk_off || !o->trk_hits || !o->n_tracks_dev || o->track_cap < 0 ||
+        (o->params && (!o->cov || !o->chi2 || !o->ndf)))
+        return fail(c, TPC_ERR_ARG, what);
+    if (n > c->ws.L.N || n_events > c->ws.L.E || o->track_cap > c->ws.L.T - 1)
+        return fail(c, TPC_ERR_CAPACITY, "batch larger than the workspace");
+    c->y = y;
+    c->z = z;
+    c->row = row;
+    c->charge = charge;
+    c->n = n;
+    c->n_events = n_events;
+    c->evt_sector_off = evt_sector_off;
+    c->have_clusters = true;
+    cudaError_t e = validate_clusters(c, s);
+    if (e == cudaSuccess)
+        e = run_find(c, o->track_of_cluster, o->trk_off, o->trk_hits, o->n_tracks_dev, o->track_cap, s);
+    if (e == cudaSuccess && o->params)
+        e = run_fit(c, o->trk_off, o->trk_hits, o->track_cap, o->n_tracks_dev, o->params, o->cov, o->chi2,
+                    o->ndf, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, what);
+    return TPC_OK;
+}
+
+tpc_status tpc_track_batch(tpc_ctx* c, const float* y, const float* z, const uint16_t* row,
+                           const uint16_t* charge, int64_t n, const int64_t* evt_sector_off,
+                           int32_t n_events, const tpc_batch_outputs* out, tpc_stream_t stream) {
+    return enqueue_batch(c, y, z, row, charge, n, evt_sector_off, n_events, out, (cudaStream_t)stream,
+                         "tpc_track_batch");
+}
+
+tpc_status tpc_graph_capture(tpc_ctx* c, const float* y, const float* z, const uint16_t* row,
+                             const uint16_t* charge, int64_t n, const int64_t* evt_sector_off,
+                             int32_t n_events, const tpc_batch_outputs* out) {
+    if (!c) return TPC_ERR_ARG;
+    cudaStream_t cs = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(c, e, "tpc_graph_capture");
+    const bool timing = c->timing;
+    c->timing = false;
+    const long long l0 = g_launches.load(std::memory_order_relaxed);
+    tpc_status st = TPC_OK;
+    cudaGraph_t g = nullptr;
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        st = enqueue_batch(c, y, z, row, charge, n, evt_sector_off, n_events, out, cs, "tpc_graph_capture");
+        // the capture always ends, also after a failed enqueue
+        e = cudaStreamEndCapture(cs, &g);
+    }
+    c->timing = timing;
+    const long long kernels = g_launches.load(std::memory_order_relaxed) - l0;
+    cudaGraphExec_t x = nullptr;
+    if (st == TPC_OK && e == cudaSuccess) e = cudaGraphInstantiate(&x, g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    if (st != TPC_OK) return st;
+    if (e != cudaSuccess) return cuda_fail(c, e, "tpc_graph_capture");
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    c->graph = x;
+    c->graph_kernels = kernels;
+    return TPC_OK;
+}
+
+tpc_status tpc_graph_launch(tpc_ctx* c, tpc_stream_t stream) {
+    if (!c) return TPC_ERR_ARG;
+    if (!c->graph) return fail(c, TPC_ERR_STATE, "no graph captured");
+    const cudaError_t e = cudaGraphLaunch(c->graph, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "tpc_graph_launch");
+    g_launches.fetch_add(c->graph_kernels, std::memory_order_relaxed);
     return TPC_OK;
 }
 

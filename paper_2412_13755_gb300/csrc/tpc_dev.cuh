@@ -134,9 +134,10 @@ struct MoveJ {
 // FP64 plane arithmetic, and s.x is left to the caller.  MoveCov = false
 // leaves s.C alone (for a caller that transforms its own covariance with the
 // Jacobian returned in mj).
+// jfull (optional) receives the full Jacobian of the move, row-major 5x5.
 template <class R, bool CanRotate = true, bool MoveCov = true>
 TPC_HD bool kf_move(KFT<R>& s, double x_to, int to, const Geo* __restrict__ geo, R kb, R snp_max,
-                    MoveJ* mj = nullptr, const R* dx_same_frame = nullptr) {
+                    MoveJ* mj = nullptr, const R* dx_same_frame = nullptr, R* jfull = nullptr) {
     double xs = CanRotate ? s.x : 0.0;
     R ys = s.p[0], ss = s.p[2];
     R ys_lo = s.lo[0], ss_lo = s.lo[2];
@@ -220,6 +221,12 @@ TPC_HD bool kf_move(KFT<R>& s, double x_to, int to, const Geo* __restrict__ geo,
 #pragma unroll
         for (int i = 0; i < 15; ++i) mj->Cpre[i] = (float)s.C[i];
         mj->valid = true;
+    }
+    if (jfull) {
+        const R J[25] = {j00, R(0), j02, R(0), dy_w,  j10, R(1), j12, dz_t, dz_w,  j20, R(0), j22, R(0), ds2_w,
+                         R(0), R(0), R(0), R(1), R(0),  R(0), R(0), R(0), R(0), R(1)};
+#pragma unroll
+        for (int i = 0; i < 25; ++i) jfull[i] = J[i];
     }
     if (MoveCov) cov_jct<R>(s.C, j00, j02, dy_w, j10, j12, dz_t, dz_w, j20, j22, ds2_w);
     add_comp(ys, ys_lo, dx * tn);
@@ -500,7 +507,8 @@ struct NSum {
 // in the frame of the first cluster in fit order gives q/pT and sin phi at
 // that cluster; tan lambda = dz / arc between the end clusters; (y, z) of the
 // first cluster.  Clamped to |sin phi| <= snp_max_seed, |q/pT| <= qpt_max.
-TPC_HD void kf_seed(KF& s, const int rows[3], const int secs[3], const float ys[3],
+template <class R>
+TPC_HD void kf_seed(KFT<R>& s, const int rows[3], const int secs[3], const float ys[3],
                     const float zs[3], bool first_is_outer, const Geo* __restrict__ geo, double bz,
                     double snp_max_seed, double qpt_max, const float prior[5]) {
     const int fr = secs[0];
@@ -541,12 +549,12 @@ TPC_HD void kf_seed(KF& s, const int rows[3], const int secs[3], const float ys[
     s.frame = fr;
     s.p[0] = ys[0];
     s.p[1] = zs[0];
-    s.p[2] = (float)sn;
-    s.p[3] = (float)t;
-    s.p[4] = (float)w;
-    s.lo[0] = s.lo[1] = s.lo[2] = 0.f;
+    s.p[2] = (R)sn;
+    s.p[3] = (R)t;
+    s.p[4] = (R)w;
+    s.lo[0] = s.lo[1] = s.lo[2] = R(0);
 #pragma unroll
-    for (int i = 0; i < 15; ++i) s.C[i] = 0.f;
+    for (int i = 0; i < 15; ++i) s.C[i] = R(0);
     s.C[sx(0, 0)] = prior[0];
     s.C[sx(1, 1)] = prior[1];
     s.C[sx(2, 2)] = prior[2];

@@ -9,6 +9,7 @@
 // broken by the clusters' input indices (canonical ids), so the output does
 // not depend on the order in which the GPU visits clusters.
 #include <algorithm>
+#include <type_traits>
 
 #include <cooperative_groups.h>
 
@@ -1717,9 +1718,16 @@ cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hi
         n, yzb, orig, grpb, rowb, cells, geo, nb, cdn, cup, d2, st, nb_queue3, nb_queue2, ST_NB_Q2);
     // one launch over both queues: the dense ones from (1, 1), then the rest
     // from gap sum 3
-    tpc::LaunchCount{}, k_neighbours_sub<NG2><<<grid_for(n / 4, 32 * 4), ns_warps<NG2>() * 32, 0, s>>>(
-        n, nb_queue3, ST_NB_Q3, 2, 2 * NB_GAP_MAX, yzb, orig, grpb, rowb, cells, geo, nb, cdn, cup, d2, st,
-        nb_queue, nullptr, 0, nb_queue2, ST_NB_Q2, 3);
+    // lanes per queued cluster: a tuning knob of this queued stage
+    auto sub_pass = [&](auto ng) {
+        constexpr int NG = decltype(ng)::value;
+        tpc::LaunchCount{}, k_neighbours_sub<NG><<<grid_for(n / 4, 32 * 4), ns_warps<NG>() * 32, 0, s>>>(
+            n, nb_queue3, ST_NB_Q3, 2, 2 * NB_GAP_MAX, yzb, orig, grpb, rowb, cells, geo, nb, cdn, cup, d2, st,
+            nb_queue, nullptr, 0, nb_queue2, ST_NB_Q2, 3);
+    };
+    if (c->tune.nb_sub_lanes == 4) sub_pass(std::integral_constant<int, 4>{});
+    else if (c->tune.nb_sub_lanes == 16) sub_pass(std::integral_constant<int, 16>{});
+    else sub_pass(std::integral_constant<int, NG2>{});
     tpc::LaunchCount{}, k_neighbours_warp<<<152 * 8, NB_WARPS * 32, 0, s>>>(nb_queue, st, yzb, orig, grpb,
                                                                         rowb, cells, geo, nb, cdn, cup, d2);
     c->mark(2, s);
@@ -1760,7 +1768,7 @@ cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hi
     for (int i = 0; i < 5; ++i) tp.prior[i] = p.prior[i];
     const unsigned sgrid = grid_for(L.S, 128);
     // persistent lanes: enough resident warps to fill the GPU
-    const unsigned lgrid = 152u * (unsigned)c->tune.lane_blocks_per_sm;
+    const unsigned lgrid = (unsigned)c->n_sm * (unsigned)c->tune.lane_blocks_per_sm;
     const int tile = c->tune.lane_tile;
     auto* tl_key = W.at<unsigned long long>(L.tl_key);
     tpc::LaunchCount{}, k_tracklet_lanes<<<lgrid, 128, 0, s>>>(

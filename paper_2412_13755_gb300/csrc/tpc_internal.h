@@ -122,7 +122,10 @@ struct tpc_ctx {
     int32_t n_events = 0;
     bool have_clusters = false;
     std::string last_error;
-    tpc_tune tune{8, 1};
+    tpc_tune tune{8, 1, 8};
+    int n_sm = 152;                     // SMs of the device (queried at set-up)
+    cudaGraphExec_t graph = nullptr;    // S7 graph (tpc_graph_capture)
+    long long graph_kernels = 0;        // kernels in that graph
     // stage timing: marks 0..9 around the find stages, 10/11 fit, 12/13 adjoint
     bool timing = false;
     cudaEvent_t marks[16] = {};
@@ -141,6 +144,9 @@ cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hi
 cudaError_t run_fit(tpc_ctx* c, const int32_t* trk_off, const int32_t* trk_hits, int32_t n_tracks,
                     const int32_t* n_tracks_dev, float* params, float* cov, float* chi2,
                     int32_t* ndf, cudaStream_t s);
+cudaError_t run_fit_ex(tpc_ctx* c, const int32_t* trk_off, const int32_t* trk_hits, int32_t n_tracks,
+                       const int32_t* n_tracks_dev, const tpc_fit_options* o, float* params, float* cov,
+                       float* chi2, int32_t* ndf, double* smoothed, cudaStream_t s);
 cudaError_t run_adjoint(tpc_ctx* c, const int32_t* trk_off, const int32_t* trk_hits,
                         int32_t n_tracks, const double* align, double* chi2_total, double* grad,
                         cudaStream_t s);

@@ -23,7 +23,8 @@ EXPORTS = ("tpc_default_params", "tpc_create", "tpc_destroy", "tpc_workspace_byt
            "tpc_set_workspace", "tpc_load_clusters", "tpc_find_tracks", "tpc_fit_tracks",
            "tpc_fit_adjoint", "tpc_get_stats", "tpc_last_error", "tpc_reset_status",
            "tpc_stage_timing", "tpc_stage_times", "tpc_find_tracks_noalloc", "tpc_set_tune",
-           "tpc_autotune", "tpc_field_voxels", "tpc_fit_adjoint_field")
+           "tpc_autotune", "tpc_field_voxels", "tpc_fit_adjoint_field", "tpc_track_batch",
+           "tpc_graph_capture", "tpc_graph_launch", "tpc_fit_tracks_ex")
 STAGE_NAMES = ("bin", "neighbours", "links", "chains", "tracklets", "select", "merge_cand",
                "match", "output", "fit", "adjoint", "find_total")
 
@@ -43,7 +44,25 @@ class Params(C.Structure):
 
 
 class Tune(C.Structure):
-    _fields_ = [("lane_blocks_per_sm", C.c_int32), ("lane_tile", C.c_int32)]
+    _fields_ = [("lane_blocks_per_sm", C.c_int32), ("lane_tile", C.c_int32),
+                ("nb_sub_lanes", C.c_int32)]
+
+
+class FitOptions(C.Structure):
+    """Kalman-filter variants of the fit (tpc_fit_options)."""
+    _fields_ = [("mat_x_x0", C.c_float), ("mat_eloss", C.c_float), ("mass", C.c_float),
+                ("direction", C.c_int32)]
+
+
+def fit_options(mat_x_x0=0.0, mat_eloss=0.0, mass=0.13957, outward=False) -> FitOptions:
+    return FitOptions(float(mat_x_x0), float(mat_eloss), float(mass), 1 if outward else 0)
+
+
+class BatchOutputs(C.Structure):
+    """Outputs of one batch (tpc_batch_outputs): device pointers."""
+    _fields_ = [("track_of_cluster", C.c_void_p), ("trk_off", C.c_void_p), ("trk_hits", C.c_void_p),
+                ("n_tracks_dev", C.c_void_p), ("track_cap", C.c_int32), ("params", C.c_void_p),
+                ("cov", C.c_void_p), ("chi2", C.c_void_p), ("ndf", C.c_void_p)]
 
 
 class FieldGrid(C.Structure):
@@ -109,6 +128,10 @@ def load_library(build_if_missing: bool = True):
     lib.tpc_fit_adjoint_field.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp, vp, vp, vp]
     lib.tpc_find_tracks_noalloc.argtypes = [vp, vp, vp, vp, i64, vp, i32, vp, vp, vp, vp, vp, i32,
                                             vp]
+    lib.tpc_track_batch.argtypes = [vp, vp, vp, vp, vp, i64, vp, i32, vp, vp]
+    lib.tpc_graph_capture.argtypes = [vp, vp, vp, vp, vp, i64, vp, i32, vp]
+    lib.tpc_graph_launch.argtypes = [vp, vp]
+    lib.tpc_fit_tracks_ex.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp, vp, vp, vp, vp]
     for name in EXPORTS:
         f = getattr(lib, name)
         if name not in ("tpc_default_params", "tpc_destroy", "tpc_workspace_bytes",
@@ -283,6 +306,28 @@ def tpc_fit_tracks(ctx, trk_off, trk_hits, n_tracks, n_tracks_dev, params, cov, 
     _check(ctx, rc, "tpc_fit_tracks")
 
 
+def tpc_fit_tracks_ex(ctx, trk_off, trk_hits, n_tracks, n_tracks_dev, options, params, cov, chi2, ndf,
+                      smoothed=None, stream=None):
+    _need(trk_off, torch.int32, "trk_off")
+    _need(trk_hits, torch.int32, "trk_hits")
+    for t, n in ((params, "params"), (cov, "cov"), (chi2, "chi2")):
+        _need(t, torch.float32, n)
+    _need(ndf, torch.int32, "ndf")
+    if n_tracks_dev is not None:
+        _need(n_tracks_dev, torch.int32, "n_tracks_dev")
+    what = "tpc_fit_tracks_ex"
+    check_fit_buffers(n_tracks, trk_off, params, cov, chi2, ndf, what)
+    if smoothed is not None:
+        _need(smoothed, torch.float64, "smoothed")
+        # entries are written at 20 x (position in trk_hits)
+        _need_len(smoothed, 20 * trk_hits.numel(), "smoothed", what)
+    rc = load_library().tpc_fit_tracks_ex(ctx, _ptr(trk_off), _ptr(trk_hits), int(n_tracks),
+                                          _ptr(n_tracks_dev), C.byref(options) if options is not None else None,
+                                          _ptr(params), _ptr(cov), _ptr(chi2), _ptr(ndf), _ptr(smoothed),
+                                          _stream(stream))
+    _check(ctx, rc, what)
+
+
 def tpc_fit_adjoint(ctx, trk_off, trk_hits, n_tracks, align, chi2_total, grad=None, stream=None):
     _need(trk_off, torch.int32, "trk_off")
     _need(trk_hits, torch.int32, "trk_hits")
@@ -378,6 +423,56 @@ def tpc_autotune(ctx, track_of_cluster, trk_off, trk_hits, n_tracks_dev, stream=
     return best
 
 
+def _batch_args(ctx, y, z, row, charge, evt_sector_off, n_events, find_out, fit_out, what):
+    """Checks and marshals the arguments of tpc_track_batch /
+    tpc_graph_capture; returns the BatchOutputs structure."""
+    _need(y, torch.float32, "y")
+    _need(z, torch.float32, "z")
+    _need(row, torch.uint16, "row")
+    if charge is not None:
+        _need(charge, torch.uint16, "charge")
+    _need(evt_sector_off, torch.int64, "evt_sector_off")
+    check_load_inputs(y, z, row, charge, evt_sector_off, n_events, what)
+    toc, trk_off, trk_hits, ntd = find_out
+    for t, nm in ((toc, "track_of_cluster"), (trk_off, "trk_off"), (trk_hits, "trk_hits"),
+                  (ntd, "n_tracks_dev")):
+        _need(t, torch.int32, nm)
+    check_find_outputs(y.numel(), toc, trk_off, trk_hits, ntd, what)
+    cap = trk_off.numel() - 1
+    o = BatchOutputs(_ptr(toc), _ptr(trk_off), _ptr(trk_hits), _ptr(ntd), cap, None, None, None, None)
+    if fit_out is not None:
+        params, cov, chi2, ndf = fit_out
+        for t, nm in ((params, "params"), (cov, "cov"), (chi2, "chi2")):
+            _need(t, torch.float32, nm)
+        _need(ndf, torch.int32, "ndf")
+        check_fit_buffers(cap, trk_off, params, cov, chi2, ndf, what)
+        o.params, o.cov, o.chi2, o.ndf = _ptr(params), _ptr(cov), _ptr(chi2), _ptr(ndf)
+    return o
+
+
+def tpc_track_batch(ctx, y, z, row, charge, evt_sector_off, n_events, find_out, fit_out=None,
+                    stream=None):
+    o = _batch_args(ctx, y, z, row, charge, evt_sector_off, n_events, find_out, fit_out,
+                    "tpc_track_batch")
+    rc = load_library().tpc_track_batch(ctx, _ptr(y), _ptr(z), _ptr(row), _ptr(charge), y.numel(),
+                                        _ptr(evt_sector_off), int(n_events), C.byref(o), _stream(stream))
+    _check(ctx, rc, "tpc_track_batch")
+    _loaded_n[ctx.value] = y.numel()
+
+
+def tpc_graph_capture(ctx, y, z, row, charge, evt_sector_off, n_events, find_out, fit_out=None):
+    o = _batch_args(ctx, y, z, row, charge, evt_sector_off, n_events, find_out, fit_out,
+                    "tpc_graph_capture")
+    rc = load_library().tpc_graph_capture(ctx, _ptr(y), _ptr(z), _ptr(row), _ptr(charge), y.numel(),
+                                          _ptr(evt_sector_off), int(n_events), C.byref(o))
+    _check(ctx, rc, "tpc_graph_capture")
+    _loaded_n[ctx.value] = y.numel()
+
+
+def tpc_graph_launch(ctx, stream=None):
+    _check(ctx, load_library().tpc_graph_launch(ctx, _stream(stream)), "tpc_graph_launch")
+
+
 def tpc_get_stats(ctx, stream=None) -> Stats:
     st = Stats()
     load_library().tpc_get_stats(ctx, C.byref(st), _stream(stream))
@@ -468,6 +563,21 @@ class Tracker:
         tpc_fit_tracks(self.ctx, trk_off, trk_hits, n_tracks, n_tracks_dev, *out, stream=stream)
         return out
 
+    def fit_ex(self, trk_off, trk_hits, n_tracks, options=None, n_tracks_dev=None, smooth=False,
+               stream=None):
+        """The Kalman-filter variants (material, outward refit, smoother):
+        (params, cov, chi2, ndf, smoothed or None); smoothed holds 20
+        doubles (state, covariance) per entry of trk_hits."""
+        dev = self.device
+        T = max(int(n_tracks), 1)
+        out = (torch.empty(T, 5, dtype=torch.float32, device=dev),
+               torch.empty(T, 15, dtype=torch.float32, device=dev),
+               torch.empty(T, dtype=torch.float32, device=dev),
+               torch.empty(T, dtype=torch.int32, device=dev))
+        sm = torch.zeros(max(trk_hits.numel(), 1), 20, dtype=torch.float64, device=dev) if smooth else None
+        tpc_fit_tracks_ex(self.ctx, trk_off, trk_hits, n_tracks, n_tracks_dev, options, *out, sm, stream)
+        return (*out, sm)
+
     def adjoint(self, trk_off, trk_hits, n_tracks, align, want_grad=True, stream=None):
         chi2 = torch.zeros(1, dtype=torch.float64, device=self.device)
         grad = torch.zeros(216, dtype=torch.float64, device=self.device) if want_grad else None
@@ -502,6 +612,32 @@ class Tracker:
 
     def reset_status(self, stream=None):
         tpc_reset_status(self.ctx, stream)
+
+    def alloc_fit_outputs(self, track_cap):
+        dev = self.device
+        T = max(int(track_cap), 1)
+        return (torch.empty(T, 5, dtype=torch.float32, device=dev),
+                torch.empty(T, 15, dtype=torch.float32, device=dev),
+                torch.empty(T, dtype=torch.float32, device=dev),
+                torch.empty(T, dtype=torch.int32, device=dev))
+
+    def track_batch(self, y, z, row, evt_sector_off, n_events, find_out, fit_out=None, charge=None,
+                    stream=None):
+        """S7: load + find (+ fit when fit_out is given) of a whole batch in
+        one call."""
+        self._inputs = (y, z, row, charge, evt_sector_off)
+        tpc_track_batch(self.ctx, y, z, row, charge, evt_sector_off, n_events, find_out, fit_out, stream)
+        self.n = y.numel()
+
+    def capture(self, y, z, row, evt_sector_off, n_events, find_out, fit_out=None, charge=None):
+        """Records the batch call into the context's CUDA graph; replay()
+        runs it.  The buffers stay bound to the graph: keep them alive."""
+        self._graph_buffers = (y, z, row, charge, evt_sector_off, find_out, fit_out)
+        tpc_graph_capture(self.ctx, y, z, row, charge, evt_sector_off, n_events, find_out, fit_out)
+        self.n = y.numel()
+
+    def replay(self, stream=None):
+        tpc_graph_launch(self.ctx, stream)
 
     def autotune(self, out=None, stream=None) -> Tune:
         out = out or self.alloc_find_outputs()

@@ -120,3 +120,22 @@ def test_workspace_capacities_refused_on_the_host(lib):
         assert rc == tpc.TPC_ERR_ARG
     finally:
         tpc.tpc_destroy(ctx)
+
+
+def test_batch_calls_refused_without_device_work(lib):
+    """Host-side refusals of the S7 calls and the tuning knobs: nothing is
+    launched."""
+    from paper_2412_13755_gb300 import tpc
+    ctx = tpc.tpc_create(tpc.default_params())
+    try:
+        assert lib.tpc_graph_launch(ctx, None) == tpc.TPC_ERR_STATE
+        out = tpc.BatchOutputs()
+        assert lib.tpc_track_batch(ctx, None, None, None, None, 0, None, 1, C.byref(out), None) == \
+            tpc.TPC_ERR_STATE
+        for bad in ((0, 1, 8), (8, 0, 8), (8, 1, 5), (8, 1, 32), (17, 1, 8)):
+            assert lib.tpc_set_tune(ctx, C.byref(tpc.Tune(*bad))) == tpc.TPC_ERR_ARG, bad
+        for good in ((4, 1, 4), (16, 4, 16), (8, 1, 8)):
+            assert lib.tpc_set_tune(ctx, C.byref(tpc.Tune(*good))) == tpc.TPC_OK
+        assert lib.tpc_set_tune(ctx, None) == tpc.TPC_OK
+    finally:
+        tpc.tpc_destroy(ctx)

@@ -214,3 +214,54 @@ def test_default_track_capacity_fits_small_contexts(stub):
     tr.n = 5000
     assert tr.alloc_find_outputs()[1].numel() - 1 == 5000 // 10 + 16
     tr.ctx = None
+
+
+def test_batch_and_graph(stub):
+    n, cap = 300, 46
+    find = (i32(n), i32(cap + 1), i32(n), i32(1))
+    fit = (f32(cap, 5), f32(cap, 15), f32(cap), i32(cap))
+    tpc.tpc_track_batch(CTX, f32(n), f32(n), u16(n), None, i64(37), 1, find, fit)
+    assert stub.calls[-1] == "tpc_track_batch"
+    tpc.tpc_track_batch(CTX, f32(n), f32(n), u16(n), u16(n), i64(37), 1, find)
+    tpc.tpc_graph_capture(CTX, f32(n), f32(n), u16(n), None, i64(37), 1, find, fit)
+    assert stub.calls[-1] == "tpc_graph_capture"
+    tpc.tpc_graph_launch(CTX)
+    assert stub.calls[-1] == "tpc_graph_launch"
+    with pytest.raises(ValueError, match="trk_hits"):
+        tpc.tpc_track_batch(CTX, f32(n), f32(n), u16(n), None, i64(37), 1,
+                            (i32(n), i32(cap + 1), i32(n - 1), i32(1)), fit)
+    with pytest.raises(ValueError, match="cov"):
+        tpc.tpc_graph_capture(CTX, f32(n), f32(n), u16(n), None, i64(37), 1, find,
+                              (f32(cap, 5), f32(cap - 1, 15), f32(cap), i32(cap)))
+    tr = object.__new__(tpc.Tracker)
+    tr.device = torch.device("cpu")
+    tr.ctx = CTX
+    tr.max_clusters = n
+    tr.max_events = 1
+    tr.n = 0
+    tr.track_batch(f32(n), f32(n), u16(n), i64(37), 1, find, tr.alloc_fit_outputs(cap))
+    tr.capture(f32(n), f32(n), u16(n), i64(37), 1, find)
+    tr.replay()
+    assert stub.calls[-3:] == ["tpc_track_batch", "tpc_graph_capture", "tpc_graph_launch"]
+    tr.ctx = None
+
+
+def test_fit_ex(stub):
+    T = 6
+    o = tpc.fit_options(1e-4, 2e-6, 0.13957, outward=False)
+    tpc.tpc_fit_tracks_ex(CTX, i32(T + 1), i32(100), T, i32(1), o, f32(T, 5), f32(T, 15), f32(T), i32(T),
+                          f64(100, 20))
+    tpc.tpc_fit_tracks_ex(CTX, i32(T + 1), i32(100), T, None, None, f32(T, 5), f32(T, 15), f32(T), i32(T))
+    assert stub.calls[-1] == "tpc_fit_tracks_ex"
+    with pytest.raises(ValueError, match="smoothed"):
+        tpc.tpc_fit_tracks_ex(CTX, i32(T + 1), i32(100), T, None, o, f32(T, 5), f32(T, 15), f32(T), i32(T),
+                              f64(99, 20))
+    with pytest.raises(TypeError, match="smoothed"):
+        tpc.tpc_fit_tracks_ex(CTX, i32(T + 1), i32(100), T, None, o, f32(T, 5), f32(T, 15), f32(T), i32(T),
+                              f32(100, 20))
+    tr = object.__new__(tpc.Tracker)
+    tr.device = torch.device("cpu")
+    tr.ctx = CTX
+    par, cov, chi2, ndf, sm = tr.fit_ex(i32(T + 1), i32(100), T, o, smooth=True)
+    assert sm.shape == (100, 20) and par.shape == (T, 5)
+    tr.ctx = None
