@@ -119,3 +119,53 @@ def test_pileup_frame_full_size(orc):
     tc.check_structure(ev, toc, t_off, hits)
     keep = np.sort(np.random.default_rng(12).choice(T, min(T, 5000), replace=False))
     _fit_parity(orc, ev, t_off, hits, par, ndf, keep)
+
+
+def test_alignment_descent_full_size(orc):
+    """The alignment workload at its stated size: 2e5 tracks with pT > 1
+    GeV/c on 36 x 6 drawn misalignments, 50 descent steps
+    theta <- theta - P g(theta), g the library's adjoint gradient on the GPU,
+    P the pseudo-inverse of the oracle's FP64 Gauss-Newton matrix at
+    theta = 0 over its eigenvalues above 1e-9 of the largest.  Checks: chi2
+    falls; the end point is a stationary point of the oracle's FP64 chi2 in
+    every kept direction (gradient below 0.1 of its statistical sigma); and
+    recovery against the generated misalignment, reported per direction in
+    units of the target (10 um / 0.01 mrad) for the directions the sample
+    determines to better than the target."""
+    mis = synth.draw_misalignment(synth.SEED_BASE + 4)
+    ev = synth.alignment_sample_parallel(n_tracks=200000, misalign=mis)
+    off, hits, _ = ev.truth_tracks(n_min=10)
+    sec = ev.sector_of_cluster()
+    gn = orc.gauss_newton(ev.y, ev.z, ev.row, sec, off, hits, np.zeros(216))
+    w, V = np.linalg.eigh(gn)
+    keep = w > 1e-9 * w[-1]
+    P = (V[:, keep] / w[keep]) @ V[:, keep].T
+    tr = tpc.Tracker(ev.n, 1)
+    try:
+        y, z, row, eo = _device_inputs(ev)
+        tr.load(y, z, row, eo, 1)
+        d_off, d_hits = torch.from_numpy(off).cuda(), torch.from_numpy(hits).cuda()
+        T = len(off) - 1
+        theta = np.zeros(216)
+        chi2s = []
+        for _ in range(50):
+            chi2, g = tr.adjoint(d_off, d_hits, T, torch.from_numpy(theta).cuda())
+            chi2s.append(chi2.item())
+            theta = theta - P @ g.cpu().numpy()
+        tr.check()
+    finally:
+        tr.close()
+    _, go = orc.fit_adjoint(ev.y, ev.z, ev.row, sec, off, hits, theta)
+    stat = np.abs(V[:, keep].T @ go) / np.sqrt(2 * w[keep])
+    units = np.tile([1e-3, 1e-3, 1e-3, 1e-5, 1e-5, 1e-5], 36)
+    Hs = gn * np.outer(units, units)
+    ws, Vs = np.linalg.eigh(Hs)
+    sig = np.sqrt(2.0 / np.maximum(ws, 1e-300))
+    good = (ws > 1e-9 * ws[-1]) & (sig < 1.0)
+    err = Vs[:, good].T @ ((theta - mis) / units)
+    print(f"\nalignment: {T} tracks, chi2 {chi2s[0]:.6e} -> {chi2s[-1]:.6e}; oracle gradient at the end "
+          f"max {stat.max():.3f} sigma over {keep.sum()} directions; {good.sum()} directions determined "
+          f"to better than the target, {int(np.sum(np.abs(err) <= 1.0))} of them recovered within it "
+          f"(largest error {np.abs(err).max():.1f} target units)")
+    assert chi2s[-1] < chi2s[0]
+    assert stat.max() < 0.1
