@@ -81,6 +81,7 @@ def lib():
         _lib.orc_bruteforce_chains.restype = C.c_int64
         _lib.orc_voxel_of.restype = C.c_int64
         _lib.orc_tracklet.restype = C.c_int64
+        _lib.orc_find_clusters.restype = C.c_int64
     return _lib
 
 
@@ -349,3 +350,19 @@ def smooth_tracks(y, z, row, sector_of, trk_off, trk_hits, params=None):
     lib().orc_smooth_tracks(_p(y), _p(z), _p(row), _p(sec), _p(off), _p(hits), C.c_int32(T),
                             C.byref(prm), _p(out), _p(chi2), _p(ndf))
     return out[:int(off[-1])], chi2, ndf
+
+
+def find_clusters(digits, n_events, q_peak=8):
+    """Clusters of pad-time digits u16 [n_events*36*152, n_time, 160]:
+    (y, z, row, charge, evt_sector_off)."""
+    d = _c(digits, np.uint16)
+    n_time = d.shape[1]
+    cap = max(int(np.count_nonzero(d)), 1)
+    y = np.empty(cap, np.float32); z = np.empty(cap, np.float32)
+    row = np.empty(cap, np.uint16); ch = np.empty(cap, np.uint16)
+    off = np.empty(n_events * N_SECTORS + 1, np.int64)
+    k = lib().orc_find_clusters(_p(d), C.c_int32(n_events), C.c_int32(n_time), C.c_int32(q_peak),
+                                _p(y), _p(z), _p(row), _p(ch), _p(off), C.c_int64(cap))
+    if k < 0:
+        raise RuntimeError("cluster capacity too small")
+    return y[:k], z[:k], row[:k], ch[:k], off

@@ -1923,4 +1923,69 @@ int orc_smooth_tracks(const float* y, const float* z, const uint16_t* row, const
     return 0;
 }
 
+// ---- NEXT-2: clusterization of pad-time digits ------------------------------
+// A digit (t, p) of a pad-row plane is a peak when its count is at least
+// q_peak, above each of its four neighbours earlier in raster order and at
+// least each of the four later ones (outside the array: 0), so that a
+// plateau yields one peak.  Its cluster sums the 5 x 5 window around it
+// (clipped to the array): Q, and the count-weighted pad and time offsets,
+// all exact integers; the position follows in FP32, one rounding per
+// operation: cp = p + Sp/Q, y = (cp - 79.5) PAD_W; ct = t + St/Q,
+// |z| = (ct + 0.5) T_W (negative on the C side).  Clusters are written per
+// plane (event, sector, row) in raster order of their peaks.
+int64_t orc_find_clusters(const uint16_t* digits, int32_t n_events, int32_t n_time, int32_t q_peak,
+                          float* y, float* z, uint16_t* row, uint16_t* charge, int64_t* evt_sector_off,
+                          int64_t cap) {
+    constexpr int NP = 160;
+    const int64_t planes = (int64_t)n_events * NSEC * NROW;
+    std::vector<std::vector<std::array<float, 3>>> found((size_t)planes);
+    const int nt = orc_get_threads();
+#pragma omp parallel for schedule(dynamic, 64) num_threads(nt)
+    for (int64_t pl = 0; pl < planes; ++pl) {
+        const uint16_t* d = digits + (size_t)pl * n_time * NP;
+        auto at = [&](int t, int p) -> int {
+            return (t < 0 || t >= n_time || p < 0 || p >= NP) ? 0 : (int)d[(size_t)t * NP + p];
+        };
+        const bool side_c = (pl / NROW) % NSEC >= NPHI;
+        for (int t = 0; t < n_time; ++t)
+            for (int p = 0; p < NP; ++p) {
+                const int q = at(t, p);
+                if (q < q_peak) continue;
+                if (!(q > at(t - 1, p - 1) && q > at(t - 1, p) && q > at(t - 1, p + 1) && q > at(t, p - 1) &&
+                      q >= at(t, p + 1) && q >= at(t + 1, p - 1) && q >= at(t + 1, p) && q >= at(t + 1, p + 1)))
+                    continue;
+                int64_t Q = 0, Sp = 0, St = 0;
+                for (int dt = -2; dt <= 2; ++dt)
+                    for (int dp = -2; dp <= 2; ++dp) {
+                        const int v = at(t + dt, p + dp);
+                        Q += v;
+                        Sp += (int64_t)v * dp;
+                        St += (int64_t)v * dt;
+                    }
+                const float cp = (float)p + (float)Sp / (float)Q;
+                const float yy = (cp - 79.5f) * 0.6f;
+                const float ct = (float)t + (float)St / (float)Q;
+                const float az = (ct + 0.5f) * 0.5f;
+                found[(size_t)pl].push_back({yy, side_c ? -az : az, (float)std::min<int64_t>(Q, 65535)});
+            }
+    }
+    int64_t total = 0;
+    for (auto& f : found) total += (int64_t)f.size();
+    if (total > cap) return -total;
+    int64_t o = 0;
+    for (int64_t g = 0; g < (int64_t)n_events * NSEC; ++g) {
+        evt_sector_off[g] = o;
+        for (int r = 0; r < NROW; ++r)
+            for (const auto& c : found[(size_t)(g * NROW + r)]) {
+                y[o] = c[0];
+                z[o] = c[1];
+                row[o] = (uint16_t)r;
+                charge[o] = (uint16_t)c[2];
+                ++o;
+            }
+    }
+    evt_sector_off[(int64_t)n_events * NSEC] = o;
+    return total;
+}
+
 }  // extern "C"

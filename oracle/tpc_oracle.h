@@ -165,6 +165,16 @@ int orc_smooth_tracks(const float* y, const float* z, const uint16_t* row, const
                       const int32_t* trk_off, const int32_t* trk_hits, int32_t n_tracks,
                       const orc_params* prm, double* out, double* chi2, int32_t* ndf);
 
+/* NEXT-2: clusters of pad-time digits (u16 [n_events*36*152][n_time][160],
+ * planes ordered by event, sector, row): peaks by the raster rule, 5 x 5
+ * count-weighted centroids (see the source), written per plane in raster
+ * order of the peaks into y, z, row, charge (cap entries) with group
+ * offsets evt_sector_off[n_events*36 + 1].  Returns the number of
+ * clusters, or -(number) when cap is too small. */
+int64_t orc_find_clusters(const uint16_t* digits, int32_t n_events, int32_t n_time, int32_t q_peak,
+                          float* y, float* z, uint16_t* row, uint16_t* charge,
+                          int64_t* evt_sector_off, int64_t cap);
+
 /* One propagation: state p (y, z, sin phi, tan lambda, q/pT) at plane x1 of
  * sector s1 -> plane x2 of sector s2.  Writes p_out[5], jac[25] (row-major
  * d p_out / d p) and dx1[5], dx2[5].  Returns 0, or 1 when it fails. */

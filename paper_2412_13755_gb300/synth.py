@@ -652,3 +652,71 @@ def material_tracks(n_tracks=2000, seed=SEED_BASE + 6, x_x0_row=MAT_X_X0_ROW,
     ev.y_true, ev.z_true, ev.snp_true = yt[order], zt[order], st[order]
     ev.tgl_true, ev.qpt_true = tt[order], wt[order]
     return ev
+
+
+# --- pad-time digits (clusterization input) ----------------------------------------
+
+# The build's digit format (the paper gives none): per (event, sector, pad
+# row) a dense array of 10-bit ADC counts, u16 [N_TIME][N_PAD], pads
+# contiguous.  Pad p covers y in [(p - 80) PAD_W, (p - 79) PAD_W); time bin t
+# covers |z| in [t T_W, (t + 1) T_W) (z < 0 on the C side).
+N_PAD = 160
+N_TIME = 512
+PAD_W = 0.6          # cm
+T_W = 0.5            # cm of drift per time bin
+DIGIT_SIGMA_PAD = 0.7    # charge spread, pads
+DIGIT_SIGMA_TIME = 0.8   # charge spread, time bins
+DIGIT_GAIN = 4.0     # ADC counts per unit of cluster charge
+DIGIT_NOISE = 1.0    # ADC noise on digits with signal
+DIGIT_ZS = 3         # zero suppression: counts below are dropped
+ADC_MAX = 1023
+
+
+def _bin_fraction(c, sigma, k):
+    """Fraction of a Gaussian (centre c, width sigma, in bin units) inside
+    bin k = [k, k + 1)."""
+    from scipy.special import erf
+    a = (k - c) / (sigma * math.sqrt(2.0))
+    b = (k + 1 - c) / (sigma * math.sqrt(2.0))
+    return 0.5 * (erf(b) - erf(a))
+
+
+def digitize(ev, seed=SEED_BASE + 7, n_time=N_TIME):
+    """Pad-time digits of an Events batch: every cluster deposits
+    DIGIT_GAIN x its charge as a 2-d Gaussian over the 5 x 5 bins around its
+    (pad, time) centre; digits with signal get N(0, DIGIT_NOISE) noise, are
+    rounded down to integers, clamped to [0, ADC_MAX] and dropped below
+    DIGIT_ZS (zero suppression; digits without signal stay 0).  Returns
+    u16 [n_events * 36 * 152, n_time, N_PAD]."""
+    rng = np.random.default_rng(seed)
+    n_planes = ev.n_events * N_SECTORS * N_ROWS
+    grp = np.repeat(np.arange(ev.n_events * N_SECTORS), np.diff(ev.evt_sector_off))
+    plane = grp.astype(np.int64) * N_ROWS + ev.row.astype(np.int64)
+    cp = ev.y.astype(np.float64) / PAD_W + 80.0
+    ct = np.abs(ev.z.astype(np.float64)) / T_W
+    q = ev.charge.astype(np.float64) * DIGIT_GAIN
+    p0 = np.floor(cp).astype(np.int64)
+    t0 = np.floor(ct).astype(np.int64)
+    idxs, ws = [], []
+    for dp in range(-2, 3):
+        kp = p0 + dp
+        fp = _bin_fraction(cp, DIGIT_SIGMA_PAD, kp)
+        for dt in range(-2, 3):
+            kt = t0 + dt
+            ft = _bin_fraction(ct, DIGIT_SIGMA_TIME, kt)
+            ok = (kp >= 0) & (kp < N_PAD) & (kt >= 0) & (kt < n_time)
+            idxs.append((plane[ok] * n_time + kt[ok]) * N_PAD + kp[ok])
+            ws.append((q * fp * ft)[ok])
+    idx = np.concatenate(idxs)
+    w = np.concatenate(ws)
+    order = np.argsort(idx, kind="stable")
+    idx, w = idx[order], w[order]
+    start = np.flatnonzero(np.r_[True, idx[1:] != idx[:-1]])
+    uniq = idx[start]
+    acc = np.add.reduceat(w, start)
+    val = np.floor(acc + rng.normal(0.0, DIGIT_NOISE, uniq.size))
+    val = np.clip(val, 0, ADC_MAX)
+    val[val < DIGIT_ZS] = 0
+    out = np.zeros(n_planes * n_time * N_PAD, np.uint16)
+    out[uniq] = val.astype(np.uint16)
+    return out.reshape(n_planes, n_time, N_PAD)
