@@ -235,6 +235,43 @@ def pileup_bench(torch, tpc, dev, steps):
             "workspace_gb": tr.workspace.numel() / 1e9, "generation_s": gen_s}
 
 
+def clusterize_bench(torch, tpc, dev, steps, ev):
+    """NEXT-2: clusterization of the central event's pad-time digits
+    (36 x 152 planes x 512 time bins x 160 pads, u16: 0.9 GB, larger than
+    L2): digits/s and the HBM fraction of the clusterizer kernel, whose
+    algorithmic bytes are the digits read once plus 12 B per cluster
+    written (y, z, row, charge)."""
+    from paper_2412_13755_gb300 import synth
+    d = synth.digitize(ev)
+    d_dev = torch.from_numpy(d.view(np.int16)).to(dev).view(torch.uint16)
+    cap = int(np.count_nonzero(d))
+    cl = tpc.Clusterizer(1, d.shape[1], cap, device=dev)
+    for _ in range(3):
+        out = cl.run(d_dev)
+    torch.cuda.synchronize()
+    st = out[6].cpu().numpy()
+    if st[0] != 0:
+        raise RuntimeError(f"clusterizer status {st}")
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        cl.run(d_dev)
+    e1.record()
+    torch.cuda.synchronize()
+    sec = e0.elapsed_time(e1) / 1e3 / steps
+    n_cl = int(out[5].item())
+    algo = d.nbytes + 12 * n_cl
+    hbm_peak, src = measured_peaks()
+    return {"workload": f"central_event digits: {d.shape[0]} planes x {d.shape[1]} time bins x {d.shape[2]} pads "
+                        f"(u16, {d.nbytes / 1e9:.2f} GB), {n_cl} clusters",
+            "digits_per_s": d.size / sec, "clusters_per_s": n_cl / sec, "ms_per_step": 1e3 * sec,
+            "roofline": {"bound": "hbm", "achieved": algo / sec / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": algo / sec / 1e9 / hbm_peak, "algorithmic_bytes": algo,
+                         "peak_source": src + " (MEASURED_PEAKS.json hbm_gbs)"},
+            "inputs_vs_l2": "0.9 GB of digits, larger than L2 (no flush needed)"}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -650,7 +687,8 @@ def run_ours(args):
     extras = []
     if not args.no_extras:
         extras += [("batched_vs_plain", lambda: batched_vs_plain(torch, tpc, dev, max(3, args.steps // 4))),
-                   ("adjoint", lambda: adjoint_bench(torch, tpc, dev, max(3, args.steps // 4)))]
+                   ("adjoint", lambda: adjoint_bench(torch, tpc, dev, max(3, args.steps // 4))),
+                   ("clusterize", lambda: clusterize_bench(torch, tpc, dev, max(3, args.steps // 2), ev))]
     if args.pileup:
         extras.append(("pileup_frame", lambda: pileup_bench(torch, tpc, dev, 2)))
     for name, fn in extras:

@@ -387,6 +387,38 @@ tpc_status tpc_fit_tracks_ex(tpc_ctx* ctx, const int32_t* trk_off, const int32_t
                              const tpc_fit_options* options, float* params, float* cov,
                              float* chi2, int32_t* ndf, double* smoothed, tpc_stream_t stream);
 
+/* NEXT-2: clusterization of pad-time digits (paper Sec. 4.2: TPC
+ * clustering runs on the GPUs; the paper gives no digit format, this is the
+ * build's).  digits (device, 16-byte aligned): u16 ADC counts
+ * [n_events * 36 * 152][n_time][160], one dense array per pad-row plane
+ * (planes ordered by event, sector, row), pads contiguous; pad p covers
+ * local y in [(p - 80) 0.6, (p - 79) 0.6) cm, time bin t covers |z| in
+ * [0.5 t, 0.5 (t + 1)) cm (z < 0 on the C side).  A digit is a peak when its
+ * count is >= q_peak, greater than its four neighbours earlier in raster
+ * order (time, then pad) and at least its four later ones (outside the
+ * array: 0).  Its cluster sums the 5 x 5 window around it (clipped):
+ * charge Q, and in FP32 with one rounding per operation
+ * y = (p + Sp/Q - 79.5) 0.6, |z| = (t + St/Q + 0.5) 0.5, Sp and St the
+ * count-weighted pad and time offsets (exact integers).  Outputs (device,
+ * caller-owned, cap entries): y, z (f32), row, charge (u16, Q clamped to
+ * 65535), written per plane in raster order of the peaks, so that the
+ * result is the input of tpc_load_clusters with its group offsets
+ * evt_sector_off[n_events * 36 + 1] (i64); n_clusters_dev[1] the count;
+ * status_dev[2] (device int32) the status and detail of this call
+ * (TPC_ERR_CAPACITY when more than cap clusters, or more than 96 peaks in
+ * one 32-time-bin tile of a plane, were found: the excess is dropped;
+ * TPC_ERR_TIMEOUT when a tile's copy did not arrive).  workspace: device,
+ * 256-byte aligned, tpc_cluster_workspace_bytes(n_events, n_time) bytes
+ * (0 for n_events < 1 or n_time outside 1..4096).  Asynchronous on stream;
+ * TPC_ERR_ARG / TPC_ERR_CAPACITY for bad arguments or a small workspace,
+ * before anything is launched. */
+size_t tpc_cluster_workspace_bytes(int32_t n_events, int32_t n_time);
+tpc_status tpc_find_clusters(const uint16_t* digits, int32_t n_events, int32_t n_time,
+                             int32_t q_peak, void* workspace, size_t workspace_bytes, float* y,
+                             float* z, uint16_t* row, uint16_t* charge, int64_t* evt_sector_off,
+                             int64_t cap, int32_t* n_clusters_dev, int32_t* status_dev,
+                             tpc_stream_t stream);
+
 /* Clears the device status word and counters (asynchronous). */
 tpc_status tpc_reset_status(tpc_ctx* ctx, tpc_stream_t stream);
 

@@ -24,7 +24,8 @@ EXPORTS = ("tpc_default_params", "tpc_create", "tpc_destroy", "tpc_workspace_byt
            "tpc_fit_adjoint", "tpc_get_stats", "tpc_last_error", "tpc_reset_status",
            "tpc_stage_timing", "tpc_stage_times", "tpc_find_tracks_noalloc", "tpc_set_tune",
            "tpc_autotune", "tpc_field_voxels", "tpc_fit_adjoint_field", "tpc_track_batch",
-           "tpc_graph_capture", "tpc_graph_launch", "tpc_fit_tracks_ex")
+           "tpc_graph_capture", "tpc_graph_launch", "tpc_fit_tracks_ex", "tpc_cluster_workspace_bytes",
+           "tpc_find_clusters")
 STAGE_NAMES = ("bin", "neighbours", "links", "chains", "tracklets", "select", "merge_cand",
                "match", "output", "fit", "adjoint", "find_total")
 
@@ -132,10 +133,13 @@ def load_library(build_if_missing: bool = True):
     lib.tpc_graph_capture.argtypes = [vp, vp, vp, vp, vp, i64, vp, i32, vp]
     lib.tpc_graph_launch.argtypes = [vp, vp]
     lib.tpc_fit_tracks_ex.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.tpc_cluster_workspace_bytes.argtypes = [i32, i32]
+    lib.tpc_cluster_workspace_bytes.restype = sz
+    lib.tpc_find_clusters.argtypes = [vp, i32, i32, i32, vp, sz, vp, vp, vp, vp, vp, i64, vp, vp, vp]
     for name in EXPORTS:
         f = getattr(lib, name)
         if name not in ("tpc_default_params", "tpc_destroy", "tpc_workspace_bytes",
-                        "tpc_field_voxels"):
+                        "tpc_field_voxels", "tpc_cluster_workspace_bytes"):
             f.restype = C.c_int
     _lib = lib
     return lib
@@ -471,6 +475,74 @@ def tpc_graph_capture(ctx, y, z, row, charge, evt_sector_off, n_events, find_out
 
 def tpc_graph_launch(ctx, stream=None):
     _check(ctx, load_library().tpc_graph_launch(ctx, _stream(stream)), "tpc_graph_launch")
+
+
+# --- NEXT-2: clusterization ------------------------------------------------------
+
+N_PAD = 160
+
+
+def tpc_cluster_workspace_bytes(n_events: int, n_time: int) -> int:
+    return int(load_library().tpc_cluster_workspace_bytes(int(n_events), int(n_time)))
+
+
+def tpc_find_clusters(digits, n_events, workspace, outputs, q_peak=8, stream=None):
+    """outputs = (y f32[cap], z f32[cap], row u16[cap], charge u16[cap],
+    evt_sector_off i64[36 n_events + 1], n_clusters_dev i32[1],
+    status_dev i32[2])."""
+    what = "tpc_find_clusters"
+    _need(digits, torch.uint16, "digits")
+    _need(workspace, torch.uint8, "workspace")
+    y, z, row, charge, off, ncl, status = outputs
+    _need(y, torch.float32, "y")
+    _need(z, torch.float32, "z")
+    _need(row, torch.uint16, "row")
+    _need(charge, torch.uint16, "charge")
+    _need(off, torch.int64, "evt_sector_off")
+    _need(ncl, torch.int32, "n_clusters_dev")
+    _need(status, torch.int32, "status_dev")
+    if digits.dim() != 3 or digits.shape[0] != int(n_events) * 36 * 152 or digits.shape[2] != N_PAD:
+        raise ValueError(f"{what}: digits must be [n_events*36*152, n_time, {N_PAD}]")
+    cap = y.numel()
+    for t, nm in ((z, "z"), (row, "row"), (charge, "charge")):
+        _need_len(t, cap, nm, what)
+    _need_len(off, 36 * int(n_events) + 1, "evt_sector_off", what)
+    _need_len(ncl, 1, "n_clusters_dev", what)
+    _need_len(status, 2, "status_dev", what)
+    need = tpc_cluster_workspace_bytes(n_events, digits.shape[1])
+    if need == 0 or workspace.numel() < need:
+        raise ValueError(f"{what}: workspace holds {workspace.numel()} bytes, the call needs {need}")
+    rc = load_library().tpc_find_clusters(_ptr(digits), int(n_events), int(digits.shape[1]), int(q_peak),
+                                          _ptr(workspace), workspace.numel(), _ptr(y), _ptr(z), _ptr(row),
+                                          _ptr(charge), _ptr(off), cap, _ptr(ncl), _ptr(status),
+                                          _stream(stream))
+    if rc != TPC_OK:
+        raise TPCError(f"{what}: {STATUS_NAMES.get(rc, rc)}")
+
+
+class Clusterizer:
+    """Workspace and outputs for the clusterization of batches of up to
+    n_events events of n_time time bins."""
+
+    def __init__(self, n_events: int, n_time: int, cap: int, device="cuda"):
+        self.device = torch.device(device)
+        self.n_events, self.n_time, self.cap = int(n_events), int(n_time), int(cap)
+        nb = tpc_cluster_workspace_bytes(self.n_events, self.n_time)
+        if nb == 0:
+            raise ValueError("unsupported clusterization shape")
+        self.workspace = torch.empty(nb, dtype=torch.uint8, device=self.device)
+        d = self.device
+        self.out = (torch.empty(self.cap, dtype=torch.float32, device=d),
+                    torch.empty(self.cap, dtype=torch.float32, device=d),
+                    torch.empty(self.cap, dtype=torch.int16, device=d).view(torch.uint16),
+                    torch.empty(self.cap, dtype=torch.int16, device=d).view(torch.uint16),
+                    torch.empty(36 * self.n_events + 1, dtype=torch.int64, device=d),
+                    torch.empty(1, dtype=torch.int32, device=d),
+                    torch.empty(2, dtype=torch.int32, device=d))
+
+    def run(self, digits, q_peak=8, stream=None):
+        tpc_find_clusters(digits, self.n_events, self.workspace, self.out, q_peak, stream)
+        return self.out
 
 
 def tpc_get_stats(ctx, stream=None) -> Stats:

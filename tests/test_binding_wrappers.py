@@ -24,7 +24,7 @@ class StubLib:
 
     def __getattr__(self, name):
         real_f = getattr(self.real, name)
-        if name == "tpc_field_voxels":  # host-only arithmetic: use the real one
+        if name in ("tpc_field_voxels", "tpc_cluster_workspace_bytes"):  # host-only: the real one
             return real_f
 
         def f(*args):
@@ -265,3 +265,20 @@ def test_fit_ex(stub):
     par, cov, chi2, ndf, sm = tr.fit_ex(i32(T + 1), i32(100), T, o, smooth=True)
     assert sm.shape == (100, 20) and par.shape == (T, 5)
     tr.ctx = None
+
+
+def test_find_clusters(stub):
+    n_ev, n_time = 1, 32
+    nb = tpc.tpc_cluster_workspace_bytes(n_ev, n_time)
+    assert nb > 0 and tpc.tpc_cluster_workspace_bytes(0, 32) == 0 and tpc.tpc_cluster_workspace_bytes(1, 5000) == 0
+    d = torch.zeros(36 * 152, n_time, 160, dtype=torch.uint16)
+    outs = (f32(100), f32(100), u16(100), u16(100), i64(37), i32(1), i32(2))
+    tpc.tpc_find_clusters(d, n_ev, torch.zeros(nb, dtype=torch.uint8), outs)
+    assert stub.calls[-1] == "tpc_find_clusters"
+    with pytest.raises(ValueError, match="workspace"):
+        tpc.tpc_find_clusters(d, n_ev, torch.zeros(nb - 1, dtype=torch.uint8), outs)
+    with pytest.raises(ValueError, match="digits"):
+        tpc.tpc_find_clusters(torch.zeros(36 * 152, n_time, 150, dtype=torch.uint16), n_ev,
+                              torch.zeros(nb, dtype=torch.uint8), outs)
+    with pytest.raises(ValueError, match="status_dev"):
+        tpc.tpc_find_clusters(d, n_ev, torch.zeros(nb, dtype=torch.uint8), outs[:6] + (i32(1),))
