@@ -5,8 +5,8 @@
 // rows, pads contiguous.  A tile is TT time bins of one plane plus two halo
 // bins on each side: 36 consecutive time rows, one contiguous span of
 // memory, moved into shared memory by one bulk asynchronous copy (TMA,
-// cp.async.bulk with an mbarrier), two stages per block so that the next
-// tile's copy runs under the current tile's work.  Persistent blocks take
+// cp.async.bulk with an mbarrier), three stages per block so that two
+// tiles' copies run under the current tile's work.  Persistent blocks take
 // tiles round robin.  In a tile every digit is tested for the raster peak
 // rule; peaks are ranked in raster order by a block-wide ballot scan and
 // their 5 x 5 integer sums and FP32 positions written to the tile's slots
@@ -25,8 +25,13 @@ constexpr int CNP = 160;               // pads per row plane
 constexpr int CTT = 32;                // time bins per tile
 constexpr int CHALO = 2;               // 5 x 5 window
 constexpr int CTR = CTT + 2 * CHALO;   // time rows staged per tile
-constexpr int CTHREADS = 256;
+constexpr int CTHREADS = 128;
+constexpr int CSTAGES = 3;             // tiles in shared memory per block (2 in flight ahead)
 constexpr int CMAXP = 96;              // peak slots per tile
+constexpr int CGROUPS = CNP / 8;       // 8-pad groups per time row
+constexpr int CITEMS = CTT * CGROUPS;  // items (8 pads of one time row) per full tile
+constexpr int CPER = CITEMS / CTHREADS;  // consecutive items per thread
+static_assert(CITEMS % CTHREADS == 0, "whole items per thread");
 constexpr unsigned CWAIT_LIMIT = 1u << 22;  // mbarrier polls before giving up
 
 struct PeakRec {
@@ -79,15 +84,16 @@ __device__ __forceinline__ void fence_async_shared() {
 }
 
 struct TileGeom {
-    int64_t plane;
+    int plane;     // tiles number below 2^31 (checked at the call)
     int t0;        // first time bin of the tile
     int lo, hi;    // staged time rows [lo, hi) (clipped to [0, n_time))
 };
 
 __device__ __forceinline__ TileGeom tile_geom(int64_t tile, int n_tch, int n_time) {
     TileGeom g;
-    g.plane = tile / n_tch;
-    g.t0 = (int)(tile % n_tch) * CTT;
+    const int t32 = (int)tile;
+    g.plane = t32 / n_tch;
+    g.t0 = (t32 - g.plane * n_tch) * CTT;
     g.lo = max(g.t0 - CHALO, 0);
     g.hi = min(g.t0 + CTT + CHALO, n_time);
     return g;
@@ -97,115 +103,190 @@ __global__ void __launch_bounds__(CTHREADS) k_clusterize(const uint16_t* __restr
                                                          int64_t n_tiles, int n_tch, int q_peak,
                                                          PeakRec* __restrict__ recs, int32_t* __restrict__ cnt,
                                                          int32_t* st) {
-    __shared__ __align__(128) uint16_t buf[2][CTR * CNP];
-    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ __align__(128) uint16_t buf[CSTAGES][CTR * CNP];
+    __shared__ __align__(8) uint64_t bar[CSTAGES];
     __shared__ int32_t wsum[CTHREADS / 32];
+    __shared__ int32_t s_wc[CPER][CTHREADS / 32];
+    __shared__ int32_t s_cand[CITEMS];
+    __shared__ int16_t s_peak[CMAXP];
+    __shared__ int32_t s_ncand;
     __shared__ int32_t s_count;
-    __shared__ int32_t s_abort;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
-        s_abort = 0;
+        for (int k = 0; k < CSTAGES; ++k) mbar_init(&bar[k], 1);
         fence_async_shared();
     }
     __syncthreads();
     auto issue = [&](int64_t tile, int stage) {  // thread 0 only
         const TileGeom g = tile_geom(tile, n_tch, n_time);
         const unsigned bytes = (unsigned)(g.hi - g.lo) * CNP * 2u;
-        const uint16_t* src = digits + ((size_t)g.plane * n_time + g.lo) * CNP;
+        const uint16_t* src = digits + ((size_t)g.plane * (size_t)n_time + (size_t)g.lo) * CNP;
         uint16_t* dst = buf[stage] + (g.lo - (g.t0 - CHALO)) * CNP;
         fence_async_shared();
         mbar_expect_tx(&bar[stage], bytes);
         bulk_load(dst, src, bytes, &bar[stage]);
     };
     int64_t tile = blockIdx.x;
-    if (tid == 0 && tile < n_tiles) issue(tile, 0);
-    unsigned phase[2] = {0u, 0u};
+    // prologue: the first CSTAGES tiles of this block in flight
+    if (tid == 0)
+        for (int k = 0; k < CSTAGES; ++k) {
+            const int64_t tk = tile + (int64_t)k * gridDim.x;
+            if (tk < n_tiles) issue(tk, k);
+        }
+    unsigned phase[CSTAGES];
+    for (int k = 0; k < CSTAGES; ++k) phase[k] = 0u;
     for (int it = 0; tile < n_tiles; ++it, tile += gridDim.x) {
-        const int stage = it & 1;
-        const int64_t next = tile + gridDim.x;
-        // the other stage was released by the __syncthreads that ended the
-        // previous tile: its copy may start now
-        if (tid == 0 && next < n_tiles) issue(next, stage ^ 1);
+        const int stage = it % CSTAGES;
         if (!mbar_wait(&bar[stage], phase[stage])) {
             // give up: report, wait (bounded) for the copies in flight, leave
-            if (tid == 0) {
-                set_status(st, TPC_ERR_TIMEOUT, 10);
-                s_abort = 1;
+            if (tid == 0) set_status(st, TPC_ERR_TIMEOUT, 10);
+            for (int k = 1; k < CSTAGES; ++k) {
+                const int sk = (stage + k) % CSTAGES;
+                if (tile + (int64_t)k * gridDim.x < n_tiles) mbar_wait(&bar[sk], phase[sk]);
             }
-            mbar_wait(&bar[stage ^ 1], phase[stage ^ 1]);
             return;
         }
         phase[stage] ^= 1u;
         const TileGeom g = tile_geom(tile, n_tch, n_time);
         uint16_t* b = buf[stage];
-        // zero the halo rows outside the plane
-        for (int i = tid; i < CTR * CNP; i += CTHREADS) {
-            const int r = i / CNP, t = g.t0 - CHALO + r;
-            if (t < g.lo || t >= g.hi) b[i] = 0;
+        // zero the halo rows outside the plane (first and last tiles only):
+        // rows [0, lo - t0 + 2) and [hi - t0 + 2, CTR) of the stage
+        {
+            const int r_lo = g.lo - (g.t0 - CHALO), r_hi = g.hi - (g.t0 - CHALO);
+            const int n_lo = r_lo * CNP, n_hi = (CTR - r_hi) * CNP;
+            for (int i = tid; i < n_lo; i += CTHREADS) b[i] = 0;
+            for (int i = tid; i < n_hi; i += CTHREADS) b[r_hi * CNP + i] = 0;
         }
-        if (tid == 0) s_count = 0;
         __syncthreads();
         auto at = [&](int r, int p) -> int {  // r: staged row, p: pad (0 outside)
             return (p < 0 || p >= CNP) ? 0 : (int)b[r * CNP + p];
         };
         const int t_end = min(CTT, n_time - g.t0);
-        const int n_dig = t_end * CNP;
-        // raster order, CTHREADS digits per round
-        for (int base = 0; base < n_dig; base += CTHREADS) {
-            const int i = base + tid;
-            bool pk = false;
-            int r = 0, p = 0;
-            if (i < n_dig) {
-                r = i / CNP + CHALO;
-                p = i % CNP;
-                const int q = at(r, p);
-                pk = q >= q_peak && q > at(r - 1, p - 1) && q > at(r - 1, p) && q > at(r - 1, p + 1) &&
-                     q > at(r, p - 1) && q >= at(r, p + 1) && q >= at(r + 1, p - 1) && q >= at(r + 1, p) &&
-                     q >= at(r + 1, p + 1);
+        // items: 8 consecutive pads of one time row, raster order; thread
+        // tid takes the CPER consecutive items from tid * CPER, so that a
+        // scan of per-thread counts ranks the peaks in raster order
+        const int n_items = t_end * CGROUPS;
+        // phase 1: items (8 pads of one time row) with a digit at the
+        // threshold, compacted in raster order; item k * CTHREADS + tid
+        unsigned bal[CPER];
+#pragma unroll
+        for (int k = 0; k < CPER; ++k) {
+            const int item = k * CTHREADS + tid;
+            bool cand = false;
+            if (item < n_items) {
+                const int r = item / CGROUPS + CHALO, p0 = (item % CGROUPS) * 8;
+                const uint4 v = *reinterpret_cast<const uint4*>(b + r * CNP + p0);
+                const unsigned mx2 = __vmaxu2(__vmaxu2(v.x, v.y), __vmaxu2(v.z, v.w));
+                cand = (int)max(mx2 & 0xffffu, mx2 >> 16) >= q_peak;
             }
-            // block-wide rank of this round's peaks in raster order
-            const unsigned bal = __ballot_sync(0xffffffffu, pk);
-            if (lane == 0) wsum[wid] = __popc(bal);
+            bal[k] = __ballot_sync(0xffffffffu, cand);
+            if (lane == 0) s_wc[k][wid] = __popc(bal[k]);
+        }
+        __syncthreads();
+        {
+            int o = 0;
+#pragma unroll
+            for (int k = 0; k < CPER; ++k) {
+                int ok_ = o;
+#pragma unroll
+                for (int w = 0; w < CTHREADS / 32; ++w) {
+                    if (w < wid) ok_ += s_wc[k][w];
+                    o += s_wc[k][w];
+                }
+                if (bal[k] & (1u << lane)) s_cand[ok_ + __popc(bal[k] & ((1u << lane) - 1u))] = k * CTHREADS + tid;
+            }
+            if (tid == 0) s_ncand = o;
+        }
+        __syncthreads();
+        // phase 2: the peak test on the candidate items, one per thread;
+        // peaks ranked in raster order by a scan of the per-item counts
+        const int n_cand = s_ncand;
+        int peaks_before = 0;
+        for (int base = 0; base < n_cand; base += CTHREADS) {
+            const int j = base + tid;
+            unsigned mask = 0;
+            int item = 0;
+            if (j < n_cand) {
+                item = s_cand[j];
+                const int r = item / CGROUPS + CHALO, p0 = (item % CGROUPS) * 8;
+                int w[3][10];
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    const uint16_t* rp = b + (r - 1 + d) * CNP;
+                    const uint4 u = *reinterpret_cast<const uint4*>(rp + p0);
+                    const unsigned u4[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) w[d][e + 1] = (int)((u4[e >> 1] >> (16 * (e & 1))) & 0xffffu);
+                    w[d][0] = p0 > 0 ? (int)rp[p0 - 1] : 0;
+                    w[d][9] = p0 + 8 < CNP ? (int)rp[p0 + 8] : 0;
+                }
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const int q = w[1][e + 1];
+                    const bool pk = (q >= q_peak) & (q > w[0][e]) & (q > w[0][e + 1]) & (q > w[0][e + 2]) &
+                                    (q > w[1][e]) & (q >= w[1][e + 2]) & (q >= w[2][e]) & (q >= w[2][e + 1]) &
+                                    (q >= w[2][e + 2]);
+                    mask |= (unsigned)pk << e;
+                }
+            }
+            const int c = __popc(mask);
+            int incl = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            if (lane == 31) wsum[wid] = incl;
             __syncthreads();
-            int before = s_count, total = 0;
+            int before = peaks_before + incl - c, total = 0;
 #pragma unroll
             for (int w = 0; w < CTHREADS / 32; ++w) {
                 if (w < wid) before += wsum[w];
                 total += wsum[w];
             }
-            before += __popc(bal & ((1u << lane) - 1u));
-            if (pk) {
-                if (before < CMAXP) {
-                    int Q = 0, Sp = 0, St = 0;
-#pragma unroll
-                    for (int dt = -2; dt <= 2; ++dt)
-#pragma unroll
-                        for (int dp = -2; dp <= 2; ++dp) {
-                            const int v = at(r + dt, p + dp);
-                            Q += v;
-                            Sp += v * dp;
-                            St += v * dt;
-                        }
-                    const int t = g.t0 + r - CHALO;
-                    const float cp = __fadd_rn((float)p, __fdiv_rn((float)Sp, (float)Q));
-                    const float yy = __fmul_rn(__fsub_rn(cp, 79.5f), 0.6f);
-                    const float ct = __fadd_rn((float)t, __fdiv_rn((float)St, (float)Q));
-                    const float az = __fmul_rn(__fadd_rn(ct, 0.5f), 0.5f);
-                    const bool side_c = (g.plane / NROW) % NSEC >= NPHI;
-                    recs[tile * CMAXP + before] = PeakRec{yy, side_c ? -az : az, (uint32_t)min(Q, 65535)};
-                } else {
-                    set_status(st, TPC_ERR_CAPACITY, 11);
-                }
+            while (mask) {
+                const int e = __ffs(mask) - 1;
+                mask &= mask - 1;
+                if (before < CMAXP) s_peak[before] = (int16_t)(item * 8 + e);
+                ++before;
             }
+            peaks_before += total;
             __syncthreads();
-            if (tid == 0) s_count += total;
         }
+        if (peaks_before > CMAXP && tid == 0) set_status(st, TPC_ERR_CAPACITY, 11);
+        const int n_pk = min(peaks_before, CMAXP);
+        // phase 3: the 5 x 5 sums and positions of the peaks, one per thread
+        const bool side_c = (g.plane / NROW) % NSEC >= NPHI;  // 32-bit
+        for (int j = tid; j < n_pk; j += CTHREADS) {
+            const int code = s_peak[j];
+            const int item = code >> 3, e = code & 7;
+            const int r = item / CGROUPS + CHALO, p = (item % CGROUPS) * 8 + e;
+            int Q = 0, Sp = 0, St = 0;
+#pragma unroll
+            for (int dt = -2; dt <= 2; ++dt)
+#pragma unroll
+                for (int dp = -2; dp <= 2; ++dp) {
+                    const int v = at(r + dt, p + dp);
+                    Q += v;
+                    Sp += v * dp;
+                    St += v * dt;
+                }
+            const int t = g.t0 + r - CHALO;
+            const float cp = __fadd_rn((float)p, __fdiv_rn((float)Sp, (float)Q));
+            const float yy = __fmul_rn(__fsub_rn(cp, 79.5f), 0.6f);
+            const float ct = __fadd_rn((float)t, __fdiv_rn((float)St, (float)Q));
+            const float az = __fmul_rn(__fadd_rn(ct, 0.5f), 0.5f);
+            recs[tile * CMAXP + j] = PeakRec{yy, side_c ? -az : az, (uint32_t)min(Q, 65535)};
+        }
+        const int total = n_pk;
+        if (tid == 0) s_count = total;
         __syncthreads();
-        if (tid == 0) cnt[tile] = min(s_count, CMAXP);
-        // every thread is done with this stage before its next copy
-        __syncthreads();
+        if (tid == 0) {
+            cnt[tile] = min(s_count, CMAXP);
+            // every thread is done with this stage: its next tile may come
+            const int64_t ahead = tile + (int64_t)CSTAGES * gridDim.x;
+            if (ahead < n_tiles) issue(ahead, stage);
+        }
     }
 }
 
