@@ -235,6 +235,44 @@ def pileup_bench(torch, tpc, dev, steps):
             "workspace_gb": tr.workspace.numel() / 1e9, "generation_s": gen_s}
 
 
+def field_adjoint_bench(torch, tpc, dev, steps):
+    """NEXT-1: chi2 and its gradient with respect to the voxel displacement
+    field (36 x 160 voxels x 3) plus the alignment, on 2e5 pT > 1 GeV/c
+    tracks, at a drawn field (sigma 0.5 mm) added to every cluster in the
+    fit: tracks/s, forward + reverse sweep."""
+    from paper_2412_13755_gb300 import synth
+    grid = synth.FIELD_GRID
+    F = synth.draw_field(seed=synth.SEED_BASE + 5, sigma=0.05)
+    units = [(0, 5000, 0.0)] * 40
+    ev = synth.generate_parallel(units, synth.SEED_BASE + 5, pt_min=1.0, pt_slope=0.5, misalign=None)
+    off_h, hits_h, _ = ev.truth_tracks(n_min=10)
+    T = len(off_h) - 1
+    tr = tpc.Tracker(ev.n, 1, device=dev)
+    y = torch.from_numpy(ev.y).to(dev)
+    z = torch.from_numpy(ev.z).to(dev)
+    row = torch.from_numpy(ev.row.view(np.int16)).to(dev).view(torch.uint16)
+    d_off = torch.from_numpy(ev.evt_sector_off).to(dev)
+    tr.load(y, z, row, d_off, 1)
+    trk_off, trk_hits = torch.from_numpy(off_h).to(dev), torch.from_numpy(hits_h).to(dev)
+    g = tpc.field_grid(**grid)
+    field = torch.from_numpy(F).to(dev)
+    for _ in range(2):
+        tr.adjoint_field(trk_off, trk_hits, T, g, field)
+    torch.cuda.synchronize()
+    tr.check()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        tr.adjoint_field(trk_off, trk_hits, T, g, field)
+    e1.record()
+    torch.cuda.synchronize()
+    sec = e0.elapsed_time(e1) / 1e3 / steps
+    return {"workload": f"distortion map: {T} tracks pT>1 GeV/c, {ev.n} clusters, "
+                        f"{synth.n_voxels(grid)} voxels x 3 + 216 alignment parameters",
+            "tracks_per_s": T / sec, "ms_per_step": 1e3 * sec}
+
+
 def clusterize_bench(torch, tpc, dev, steps, ev):
     """NEXT-2: clusterization of the central event's pad-time digits
     (36 x 152 planes x 512 time bins x 160 pads, u16: 0.9 GB, larger than
@@ -688,7 +726,8 @@ def run_ours(args):
     if not args.no_extras:
         extras += [("batched_vs_plain", lambda: batched_vs_plain(torch, tpc, dev, max(3, args.steps // 4))),
                    ("adjoint", lambda: adjoint_bench(torch, tpc, dev, max(3, args.steps // 4))),
-                   ("clusterize", lambda: clusterize_bench(torch, tpc, dev, max(3, args.steps // 2), ev))]
+                   ("clusterize", lambda: clusterize_bench(torch, tpc, dev, max(3, args.steps // 2), ev)),
+                   ("field_adjoint", lambda: field_adjoint_bench(torch, tpc, dev, max(3, args.steps // 4)))]
     if args.pileup:
         extras.append(("pileup_frame", lambda: pileup_bench(torch, tpc, dev, 2)))
     for name, fn in extras:
