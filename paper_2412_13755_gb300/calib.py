@@ -20,10 +20,12 @@ from . import tpc
 
 def calibrate_field(tracker: tpc.Tracker, trk_off, trk_hits, n_tracks: int, grid: tpc.FieldGrid,
                     iters: int = 30, lam: float = 1.0, memory: int = 10, mask=None, field0=None,
-                    align=None):
+                    align=None, callback=None):
     """Field minimising sum(chi2) + lam |F|^2 over the components where
     `mask` (bool [n_voxels, 3], default all) is set, from field0 (default 0).
-    Returns (field [n_voxels, 3] float64 numpy, list of objective values)."""
+    callback(iteration, field, objective), when given, sees every accepted
+    iterate.  Returns (field [n_voxels, 3] float64 numpy, list of objective
+    values)."""
     nv = tpc.tpc_field_voxels(grid)
     dev = tracker.device
     F = np.zeros((nv, 3)) if field0 is None else np.array(field0, np.float64).reshape(nv, 3)
@@ -81,4 +83,6 @@ def calibrate_field(tracker: tpc.Tracker, trk_off, trk_hits, n_tracks: int, grid
                 Y.pop(0)
         F, f, g = Fn, fn, gn
         hist.append(f)
+        if callback is not None:
+            callback(len(hist) - 1, F, f)
     return F, hist

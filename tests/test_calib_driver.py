@@ -37,8 +37,12 @@ def test_lbfgs_reaches_the_regularised_minimum(monkeypatch):
     mask = np.ones((nv, 3), bool)
     mask[:, 0] = False                      # x components stay at zero
     lam = 0.5
-    F, hist = calib.calibrate_field(tr, None, None, 0, None, iters=80, lam=lam, mask=mask)
+    seen = []
+    F, hist = calib.calibrate_field(tr, None, None, 0, None, iters=80, lam=lam, mask=mask,
+                                    callback=lambda it, f_, obj: seen.append((it, obj)))
     assert all(b <= a + 1e-9 for a, b in zip(hist, hist[1:]))
+    # the callback sees every accepted iterate, numbered from 1
+    assert [it for it, _ in seen] == list(range(1, len(hist))) and [o for _, o in seen] == hist[1:]
     assert np.all(F[:, 0] == 0)
     # closed form on the free components: (A_ff + lam I) x = A_ff Fs_f (+ coupling to fixed x = 0)
     free = mask.reshape(-1)
