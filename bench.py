@@ -310,6 +310,9 @@ def clusterize_bench(torch, tpc, dev, steps, ev):
             "inputs_vs_l2": "0.9 GB of digits, larger than L2 (no flush needed)"}
 
 
+EXTRA_NAMES = ("batched_vs_plain", "adjoint", "clusterize", "field_adjoint", "pileup_frame")
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -322,6 +325,8 @@ def parse():
                     help="also time the 100-collision pile-up frame (~1.5e8 clusters)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-vs-plain and adjoint measurements")
+    ap.add_argument("--only", choices=sorted(EXTRA_NAMES),
+                    help="run one of the extra measurements alone and print its JSON (for profiling)")
     return ap.parse_args()
 
 
@@ -765,9 +770,26 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_only(args):
+    import torch
+
+    from paper_2412_13755_gb300 import tpc
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(dev)
+    k = max(3, args.steps // 4)
+    fns = {"batched_vs_plain": lambda: batched_vs_plain(torch, tpc, dev, k),
+           "adjoint": lambda: adjoint_bench(torch, tpc, dev, k),
+           "clusterize": lambda: clusterize_bench(torch, tpc, dev, max(3, args.steps // 2), make_event()),
+           "field_adjoint": lambda: field_adjoint_bench(torch, tpc, dev, k),
+           "pileup_frame": lambda: pileup_bench(torch, tpc, dev, 2)}
+    print(json.dumps({args.only: fns[args.only]()}), flush=True)
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.only:
+        run_only(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
