@@ -48,6 +48,13 @@ class Diag(C.Structure):
     ]
 
 
+class SidesParams(C.Structure):
+    """Parameters of the A/C-side association with t0 (orc_sides_params)."""
+    _fields_ = [("n_min", C.c_int32), ("gap_max", C.c_int32), ("chi2_junction", C.c_double),
+                ("z_membrane", C.c_double), ("chi2_joint", C.c_double), ("t0_prior", C.c_double),
+                ("v_drift", C.c_double)]
+
+
 class FieldGrid(C.Structure):
     """Voxel grid of a displacement field (orc_field_grid)."""
     _fields_ = [("n_band", C.c_int32), ("n_y", C.c_int32), ("n_z", C.c_int32),
@@ -82,6 +89,8 @@ def lib():
         _lib.orc_voxel_of.restype = C.c_int64
         _lib.orc_tracklet.restype = C.c_int64
         _lib.orc_find_clusters.restype = C.c_int64
+        _lib.orc_match_sides.restype = C.c_int64
+        _lib.orc_fit_t0.argtypes = [C.c_void_p] * 5 + [C.c_int32, C.c_int32, C.c_double] + [C.c_void_p] * 5
     return _lib
 
 
@@ -366,3 +375,52 @@ def find_clusters(digits, n_events, q_peak=8):
     if k < 0:
         raise RuntimeError("cluster capacity too small")
     return y[:k], z[:k], row[:k], ch[:k], off
+
+
+# --- NEXT-4: t0 as a sixth state parameter ------------------------------------
+
+def default_sides_params(**kw) -> SidesParams:
+    p = SidesParams()
+    lib().orc_default_sides_params(C.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def fit_t0(y, z, row, sector_of, hits, n_outer, t0_seed, params=None, sides=None):
+    """Six-parameter fit (y, z, sin phi, tan lambda, q/pT, t0) of hits
+    (outermost first; the first n_outer the outer segment).  Returns
+    (params6[6], cov6[21], chi2) or None when the fit fails."""
+    y, z, row = _c(y, np.float32), _c(z, np.float32), _c(row, np.uint16)
+    sec, h = _c(sector_of, np.int32), _c(hits, np.int32)
+    prm = params or default_params()
+    sp = sides or default_sides_params()
+    p6 = np.empty(6)
+    c6 = np.empty(21)
+    c2 = np.empty(1)
+    rc = lib().orc_fit_t0(_p(y), _p(z), _p(row), _p(sec), _p(h), len(h), int(n_outer), float(t0_seed),
+                          C.byref(prm), C.byref(sp), _p(p6), _p(c6), _p(c2))
+    return None if rc else (p6, c6, float(c2[0]))
+
+
+def match_sides(y, z, row, evt_sector_off, n_events, trk_off, trk_hits, params=None, sides=None):
+    """A/C-side association with t0.  Returns a dict of per-track arrays:
+    partner, t0, params6 [T,6], cov6 [T,21], chi2, ndf, dchi2, margin;
+    and n_pairs."""
+    y, z, row = _c(y, np.float32), _c(z, np.float32), _c(row, np.uint16)
+    off = _c(evt_sector_off, np.int64)
+    to, th = _c(trk_off, np.int32), _c(trk_hits, np.int32)
+    T = to.shape[0] - 1
+    prm = params or default_params()
+    sp = sides or default_sides_params()
+    out = dict(partner=np.empty(T, np.int32), t0=np.empty(T), params6=np.empty((T, 6)),
+               cov6=np.empty((T, 21)), chi2=np.empty(T), ndf=np.empty(T, np.int32),
+               dchi2=np.empty(T), margin=np.empty(T))
+    npairs = lib().orc_match_sides(_p(y), _p(z), _p(row), C.c_int64(y.shape[0]), _p(off),
+                                   C.c_int32(n_events), _p(to), _p(th), C.c_int32(T), C.byref(prm),
+                                   C.byref(sp), *[_p(out[k]) for k in ("partner", "t0", "params6", "cov6",
+                                                                        "chi2", "ndf", "dchi2", "margin")])
+    if npairs < 0:
+        raise ValueError("oracle rejected the input")
+    out["n_pairs"] = int(npairs)
+    return out

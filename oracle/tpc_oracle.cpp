@@ -26,6 +26,7 @@
 #include <cstring>
 #include <functional>
 #include <limits>
+#include <map>
 #include <vector>
 #include <type_traits>
 
@@ -1986,6 +1987,377 @@ int64_t orc_find_clusters(const uint16_t* digits, int32_t n_events, int32_t n_ti
     }
     evt_sector_off[(int64_t)n_events * NSEC] = o;
     return total;
+}
+
+}  // extern "C"
+
+// ---- NEXT-4: the drift-time offset t0 as a sixth state parameter ----------
+// A collision at drift-time offset t0 (us) is seen at z' = z - v t0 on side
+// A (sectors 0..17) and at z' = z + v t0 on side C (the time-frame
+// convention of the pile-up frame).  The state (y, z, sin phi, tan lambda,
+// q/pT, t0) carries the true z; the helix transport leaves t0 unchanged; a
+// cluster of side sgn (+1 A, -1 C) measures (y, z - sgn v t0).  Found tracks
+// never span both sides (the merge joins one side only), so a track that
+// crosses the central membrane is found as two: an inner segment and an
+// outer one, on opposite sides of one phi sector, with adjacent row ranges.
+namespace {
+
+// symmetric 6x6 storage, upper triangle row by row:
+// 00 01 02 03 04 05 11 12 13 14 15 22 23 24 25 33 34 35 44 45 55
+inline int s6(int i, int j) {
+    if (i > j) std::swap(i, j);
+    static const int base[6] = {0, 6, 11, 15, 18, 20};
+    return base[i] + (j - i);
+}
+
+inline int side_sign(int sector) { return sector < NPHI ? 1 : -1; }
+
+// SPD solve r^T M^-1 r by Cholesky for a dense n x n M (row-major); false
+// when M is not positive definite.
+bool chi2_dense(const double* r, const double* M, int n, double& out) {
+    double L[36] = {};
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j <= i; ++j) {
+            double s = M[i * n + j];
+            for (int l = 0; l < j; ++l) s -= L[i * 6 + l] * L[j * 6 + l];
+            if (i == j) {
+                if (!(s > 0)) return false;
+                L[i * 6 + i] = std::sqrt(s);
+            } else {
+                L[i * 6 + j] = s / L[j * 6 + j];
+            }
+        }
+    double v[6];
+    out = 0;
+    for (int i = 0; i < n; ++i) {
+        double s = r[i];
+        for (int l = 0; l < i; ++l) s -= L[i * 6 + l] * v[l];
+        v[i] = s / L[i * 6 + i];
+        out += v[i] * v[i];
+    }
+    return true;
+}
+
+// Kalman update of the six-parameter state with one cluster of side sgn:
+// H = [[1 0 0 0 0 0], [0 1 0 0 0 a]], a = -sgn v;  S = H C H^T + R,
+// K = C H^T S^-1, p += K r, C -= K H C, chi2 += r^T S^-1 r.
+void kf6_update(double p[6], double C[21], double my, double mz, double a, double sy2, double sz2,
+                double& chi2) {
+    double HC0[6], HC1[6];  // rows of H C
+    for (int i = 0; i < 6; ++i) {
+        HC0[i] = C[s6(0, i)];
+        HC1[i] = C[s6(1, i)] + a * C[s6(5, i)];
+    }
+    const double r0 = my - p[0], r1 = mz - (p[1] + a * p[5]);
+    const double S00 = HC0[0] + sy2, S01 = HC0[1] + a * HC0[5];
+    const double S11 = HC1[1] + a * HC1[5] + sz2;
+    const double det = S00 * S11 - S01 * S01;
+    const double i00 = S11 / det, i01 = -S01 / det, i11 = S00 / det;
+    double K0[6], K1[6];  // K = (H C)^T S^-1
+    for (int i = 0; i < 6; ++i) {
+        K0[i] = HC0[i] * i00 + HC1[i] * i01;
+        K1[i] = HC0[i] * i01 + HC1[i] * i11;
+    }
+    for (int i = 0; i < 6; ++i) p[i] += K0[i] * r0 + K1[i] * r1;
+    for (int i = 0; i < 6; ++i)
+        for (int j = i; j < 6; ++j) C[s6(i, j)] -= K0[i] * HC0[j] + K1[i] * HC1[j];
+    chi2 += r0 * r0 * i00 + 2.0 * r0 * r1 * i01 + r1 * r1 * i11;
+}
+
+// C6 <- J6 C6 J6^T with J6 = diag(J, 1): the t0 row and column follow the
+// five helix parameters' Jacobian, Var(t0) is unchanged.
+void cov6_transform(double C[21], const double J[25]) {
+    double full[36], tmp[36];
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j < 6; ++j) full[i * 6 + j] = C[s6(i, j)];
+    auto J6 = [&](int i, int l) { return i < 5 ? (l < 5 ? J[i * 5 + l] : 0.0) : (l == 5 ? 1.0 : 0.0); };
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j < 6; ++j) {
+            double acc = 0.0;
+            for (int l = 0; l < 6; ++l) acc += J6(i, l) * full[l * 6 + j];
+            tmp[i * 6 + j] = acc;
+        }
+    for (int i = 0; i < 6; ++i)
+        for (int j = i; j < 6; ++j) {
+            double acc = 0.0;
+            for (int l = 0; l < 6; ++l) acc += tmp[i * 6 + l] * J6(j, l);
+            C[s6(i, j)] = acc;
+        }
+}
+
+// The joint fit of a hit list whose first n_outer hits are the outer
+// segment (outermost first) and the rest the inner one, continuing inward.
+// Seed: the three-cluster seed of the outer segment alone (its first,
+// middle and last clusters, one side, so its z is the apparent z' of that
+// side), its z made the true z with t0_seed; prior covariance diagonal,
+// the helix parameters' prior as in the five-parameter fit and t0_prior^2
+// for t0.  State and covariance at the innermost cluster on return.
+bool fit_t0(const float* y, const float* z, const uint16_t* row, const int32_t* sec, const int32_t* hits,
+            int n, int n_outer, double t0_seed, const orc_params& prm, const orc_sides_params& sp, double p6[6],
+            double C6[21], double& chi2) {
+    if (n_outer < 3 || n <= n_outer) return false;
+    const Seed sd = make_seed(y, z, row, sec, hits, n_outer, true, prm);
+    double p[5];
+    for (int i = 0; i < 5; ++i) p[i] = sd.p[i];
+    double t0 = t0_seed;
+    p[1] = sd.p[1] + side_sign(sec[hits[0]]) * sp.v_drift * t0_seed;
+    for (int i = 0; i < 21; ++i) C6[i] = 0.0;
+    for (int i = 0; i < 5; ++i) C6[s6(i, i)] = prm.prior[i];
+    C6[s6(5, 5)] = sp.t0_prior * sp.t0_prior;
+    double x = sd.x;
+    int frame = sd.frame;
+    chi2 = 0.0;
+    for (int j = 0; j < n; ++j) {
+        const int h = hits[j];
+        double J[25], dX[5];
+        if (!move_state<double>(x, p, frame, row_x(row[h]), sec[h], J, dX, prm)) return false;
+        cov6_transform(C6, J);
+        double q[6] = {p[0], p[1], p[2], p[3], p[4], t0};
+        kf6_update(q, C6, (double)y[h], (double)z[h], -side_sign(sec[h]) * sp.v_drift, prm.sigma_y2,
+                   prm.sigma_z2, chi2);
+        for (int i = 0; i < 5; ++i) p[i] = q[i];
+        t0 = q[5];
+    }
+    for (int i = 0; i < 5; ++i) p6[i] = p[i];
+    p6[5] = t0;
+    return true;
+}
+
+// One found track as seen by the association.
+struct SideTrack {
+    bool usable = false;  // one side, >= n_min clusters, both fits done
+    int event = 0, sgn = 0;
+    int r_in = 0, r_out = 0;   // rows of the innermost and outermost clusters
+    int s_in = 0, s_out = 0;   // their sectors
+    double x_in = 0, p_in[5] = {}, C_in[15] = {}, chi2_in = 0;  // inward fit: state at the innermost cluster
+    double x_out = 0, p_out[5] = {}, C_out[15] = {};            // outward fit: state at the outermost cluster
+};
+
+struct SideCand {
+    int i, o;        // inner and outer track
+    double t0s;      // t0 from the two junction states
+    double dchi2;    // chi2 increase of the joint fit
+    double p6[6], C6[21], chi2;
+};
+
+inline double rel_m(double u, double v) {
+    const double m = std::max(std::fabs(u), std::fabs(v));
+    return m > 0 ? std::fabs(u - v) / m : 0.0;
+}
+
+}  // namespace
+
+extern "C" {
+
+void orc_default_sides_params(orc_sides_params* p) {
+    p->n_min = 10;
+    p->gap_max = 8;
+    p->chi2_junction = 30.0;
+    p->z_membrane = 3.0;
+    p->chi2_joint = 40.0;
+    p->t0_prior = 1.0;
+    p->v_drift = 2.58;
+}
+
+int orc_fit_t0(const float* y, const float* z, const uint16_t* row, const int32_t* sector_of,
+               const int32_t* hits, int32_t n, int32_t n_outer, double t0_seed, const orc_params* prm,
+               const orc_sides_params* sp, double* params6, double* cov6, double* chi2) {
+    return fit_t0(y, z, row, sector_of, hits, n, n_outer, t0_seed, *prm, *sp, params6, cov6, *chi2) ? 0 : 1;
+}
+
+// Association of the A- and C-side segments of membrane-crossing tracks.
+//  1. Per found track: usable when all its clusters lie on one side and it
+//     has >= n_min of them; the inward fit gives the state at its innermost
+//     cluster and the segment's chi2, the outward fit the state at its
+//     outermost cluster.
+//  2. Candidates (i inner, o outer): one event, opposite sides, the same
+//     or an adjacent phi sector at the junction (i's outermost cluster,
+//     o's innermost: a low-pT track may cross a sector border there too),
+//     1 <= row(o innermost) - row(i outermost) <= gap_max.
+//  3. Junction: i's outward state moved to o's innermost plane; the 4-d
+//     chi2 of (y, sin phi, tan lambda, q/pT) against o's inward state with
+//     the sum of both covariances must be <= chi2_junction; with z'_i and
+//     z'_o the two apparent z there, the true z at the junction,
+//     (z'_i + z'_o)/2, must lie within z_membrane of the membrane; t0 seed
+//     (z'_o - z'_i)/(2 sgn_i v).
+//  4. The joint fit (o's clusters, then i's) with t0: dchi2 = chi2_joint -
+//     chi2_i - chi2_o must be <= chi2_joint cut.
+//  5. Every track keeps its best candidate by (dchi2 rounded to FP32,
+//     partner index); a pair is accepted when each is the other's best.
+// Outputs per track (T entries; both members of a pair get the pair's
+// joint fit): partner (-1: none), t0, params6 [6], cov6 [21], chi2, ndf,
+// dchi2.  margin (optional, T entries): the smallest relative margin of the
+// decisions that involved the track (gates and the best-vs-next order),
+// infinity when none.  Returns the number of pairs, -1 on invalid input.
+int64_t orc_match_sides(const float* y, const float* z, const uint16_t* row, int64_t n, const int64_t* off,
+                        int32_t n_events, const int32_t* trk_off, const int32_t* trk_hits, int32_t T,
+                        const orc_params* prm_, const orc_sides_params* sp_, int32_t* partner, double* t0o,
+                        double* params6, double* cov6, double* chi2o, int32_t* ndfo, double* dchi2o,
+                        double* margin) {
+    const orc_params& prm = *prm_;
+    const orc_sides_params& sp = *sp_;
+    const int G = n_events * NSEC;
+    if (off[0] != 0 || off[G] != n || T < 0) return -1;
+    for (int g = 0; g < G; ++g)
+        if (off[g + 1] < off[g]) return -1;
+    std::vector<int32_t> sec(n), evt(n);
+    for (int g = 0; g < G; ++g)
+        for (int64_t c = off[g]; c < off[g + 1]; ++c) {
+            sec[c] = g % NSEC;
+            evt[c] = g / NSEC;
+        }
+    for (int t = 0; t < T; ++t) {
+        partner[t] = -1;
+        t0o[t] = 0.0;
+        for (int i = 0; i < 6; ++i) params6[t * 6 + i] = 0.0;
+        for (int i = 0; i < 21; ++i) cov6[t * 21 + i] = 0.0;
+        chi2o[t] = 0.0;
+        ndfo[t] = -1;
+        dchi2o[t] = 0.0;
+        if (margin) margin[t] = std::numeric_limits<double>::infinity();
+    }
+    // 1. per-track classification and the two fits
+    std::vector<SideTrack> st(T);
+    const int nt = orc_get_threads();
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nt)
+    for (int t = 0; t < T; ++t) {
+        const int b = trk_off[t], m = trk_off[t + 1] - b;
+        SideTrack& s = st[t];
+        if (m < std::max(3, sp.n_min)) continue;
+        const int32_t* h = trk_hits + b;
+        s.sgn = side_sign(sec[h[0]]);
+        s.event = evt[h[0]];
+        bool one = true;
+        for (int j = 0; j < m; ++j) one = one && side_sign(sec[h[j]]) == s.sgn && evt[h[j]] == s.event;
+        if (!one) continue;
+        s.r_out = row[h[0]];
+        s.s_out = sec[h[0]];
+        s.r_in = row[h[m - 1]];
+        s.s_in = sec[h[m - 1]];
+        auto th = [](int) -> const double* { return nullptr; };
+        double xl = 0;
+        if (!kf_fit<double>(y, z, row, sec.data(), h, m, true, prm, th, s.p_in, s.C_in, s.chi2_in, &xl)) continue;
+        s.x_in = xl;
+        std::vector<int32_t> rev(h, h + m);
+        std::reverse(rev.begin(), rev.end());
+        double c2o;
+        if (!kf_fit<double>(y, z, row, sec.data(), rev.data(), m, false, prm, th, s.p_out, s.C_out, c2o, &xl)) continue;
+        s.x_out = xl;
+        s.usable = true;
+    }
+    // 2-3. candidates, bucketed by (event, side, phi sector, row) of the
+    // outer segment's innermost cluster
+    std::map<int64_t, std::vector<int>> by_inner_end;
+    for (int t = 0; t < T; ++t)
+        if (st[t].usable) {
+            const int64_t key = ((int64_t)(st[t].event * 2 + (st[t].sgn > 0 ? 0 : 1)) * NPHI + st[t].s_in % NPHI) * NROW + st[t].r_in;
+            by_inner_end[key].push_back(t);
+        }
+    std::vector<std::vector<SideCand>> cand_i(T);
+    // (partner, margin) of every evaluated candidate, listed at the inner track
+    std::vector<std::vector<std::pair<int, double>>> gm_i(T);
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nt)
+    for (int i = 0; i < T; ++i) {
+        const SideTrack& a = st[i];
+        if (!a.usable) continue;
+        for (int dp = -1; dp <= 1; ++dp)
+        for (int gap = 1; gap <= sp.gap_max; ++gap) {
+            const int r = a.r_out + gap;
+            if (r >= NROW) break;
+            const int ph = (a.s_out % NPHI + dp + NPHI) % NPHI;
+            const int64_t key = ((int64_t)(a.event * 2 + (a.sgn > 0 ? 1 : 0)) * NPHI + ph) * NROW + r;
+            auto it = by_inner_end.find(key);
+            if (it == by_inner_end.end()) continue;
+            for (int o : it->second) {
+                const SideTrack& b = st[o];
+                // the inner segment's outward state moved to o's innermost plane
+                double x = a.x_out, p[5], C[15], J[25], dX[5];
+                for (int k = 0; k < 5; ++k) p[k] = a.p_out[k];
+                for (int k = 0; k < 15; ++k) C[k] = a.C_out[k];
+                int frame = a.s_out;
+                if (!move_state<double>(x, p, frame, b.x_in, b.s_in, J, dX, prm)) continue;
+                cov_transform(C, J);
+                static const int ix[4] = {0, 2, 3, 4};
+                double rv[4], M[16];
+                for (int u = 0; u < 4; ++u) {
+                    rv[u] = b.p_in[ix[u]] - p[ix[u]];
+                    for (int w = 0; w < 4; ++w) M[u * 4 + w] = C[sidx(ix[u], ix[w])] + b.C_in[sidx(ix[u], ix[w])];
+                }
+                double c4;
+                if (!chi2_dense(rv, M, 4, c4)) continue;
+                const double zmem = 0.5 * (p[1] + b.p_in[1]);
+                double m_i = std::min(rel_m(c4, sp.chi2_junction), rel_m(std::fabs(zmem), sp.z_membrane));
+                if (c4 > sp.chi2_junction || std::fabs(zmem) > sp.z_membrane) {
+                    gm_i[i].push_back({o, m_i});
+                    continue;
+                }
+                SideCand cd;
+                cd.i = i;
+                cd.o = o;
+                cd.t0s = (b.p_in[1] - p[1]) / (2.0 * a.sgn * sp.v_drift);
+                // 4. the joint fit
+                const int bi = trk_off[i], ni = trk_off[i + 1] - bi;
+                const int bo = trk_off[o], no = trk_off[o + 1] - bo;
+                std::vector<int32_t> jh(trk_hits + bo, trk_hits + bo + no);
+                jh.insert(jh.end(), trk_hits + bi, trk_hits + bi + ni);
+                if (!fit_t0(y, z, row, sec.data(), jh.data(), ni + no, no, cd.t0s, prm, sp, cd.p6, cd.C6, cd.chi2)) {
+                    gm_i[i].push_back({o, m_i});
+                    continue;
+                }
+                cd.dchi2 = cd.chi2 - a.chi2_in - b.chi2_in;
+                m_i = std::min(m_i, rel_m(cd.dchi2, sp.chi2_joint));
+                gm_i[i].push_back({o, m_i});
+                if (cd.dchi2 > sp.chi2_joint) continue;
+                cand_i[i].push_back(cd);
+            }
+        }
+    }
+    std::vector<SideCand> cand;
+    for (auto& v : cand_i)
+        for (auto& c : v) cand.push_back(c);
+    // margins of the gate decisions reach both members
+    std::vector<double> mrg2(T, std::numeric_limits<double>::infinity());
+    for (int i = 0; i < T; ++i)
+        for (const auto& om : gm_i[i]) {
+            mrg2[i] = std::min(mrg2[i], om.second);
+            mrg2[om.first] = std::min(mrg2[om.first], om.second);
+        }
+    // 5. mutual best by (dchi2 as FP32, partner index)
+    using Key = std::pair<float, int>;
+    const Key none{std::numeric_limits<float>::infinity(), std::numeric_limits<int>::max()};
+    std::vector<Key> best(T, none), second(T, none);
+    auto offer = [&](int t, Key k) {
+        if (k < best[t]) {
+            second[t] = best[t];
+            best[t] = k;
+        } else if (k < second[t]) {
+            second[t] = k;
+        }
+    };
+    for (const auto& c : cand) {
+        offer(c.i, {(float)c.dchi2, c.o});
+        offer(c.o, {(float)c.dchi2, c.i});
+    }
+    for (int t = 0; t < T; ++t)
+        if (best[t].second != none.second && second[t].second != none.second)
+            mrg2[t] = std::min(mrg2[t], rel_m(best[t].first, second[t].first));
+    int64_t pairs = 0;
+    for (const auto& c : cand) {
+        if (best[c.i].second != c.o || best[c.o].second != c.i) continue;
+        ++pairs;
+        for (int t : {c.i, c.o}) {
+            partner[t] = t == c.i ? c.o : c.i;
+            t0o[t] = c.p6[5];
+            for (int k = 0; k < 6; ++k) params6[t * 6 + k] = c.p6[k];
+            for (int k = 0; k < 21; ++k) cov6[t * 21 + k] = c.C6[k];
+            chi2o[t] = c.chi2;
+            ndfo[t] = 2 * (trk_off[c.i + 1] - trk_off[c.i] + trk_off[c.o + 1] - trk_off[c.o]) - 6;
+            dchi2o[t] = c.dchi2;
+        }
+    }
+    if (margin)
+        for (int t = 0; t < T; ++t) margin[t] = mrg2[t];
+    return pairs;
 }
 
 }  // extern "C"

@@ -240,6 +240,51 @@ int orc_field_gn_blocks(const float* y, const float* z, const uint16_t* row,
                         const orc_field_grid* grid, const double* field,
                         const orc_params* prm, double* blocks);
 
+/* NEXT-4: the drift-time offset t0 as a sixth state parameter.  A
+ * collision at offset t0 (us) is seen at z' = z - v t0 on side A (sectors
+ * 0..17) and z' = z + v t0 on side C.  The association pairs the one-side
+ * found tracks that are the inner and outer segments of one
+ * membrane-crossing track (the build's reading; the paper gives no
+ * algorithm: it reconstructs continuous-readout time frames, Sec. 1 and
+ * Sec. 4). */
+typedef struct {
+    int32_t n_min;         /* minimum clusters of a segment                   */
+    int32_t gap_max;       /* 1 <= row(outer's innermost) - row(inner's
+                              outermost) <= gap_max                           */
+    double chi2_junction;  /* 4-d (y, sin phi, tan lambda, q/pT) junction cut */
+    double z_membrane;     /* |true z at the junction| cut (cm)               */
+    double chi2_joint;     /* cut on the joint fit's chi2 increase            */
+    double t0_prior;       /* prior sigma of t0 in the joint fit (us)         */
+    double v_drift;        /* drift velocity (cm/us)                          */
+} orc_sides_params;
+
+void orc_default_sides_params(orc_sides_params* p);
+
+/* The six-parameter fit (y, z, sin phi, tan lambda, q/pT, t0; z the true
+ * z) of hits[0..n): the first n_outer are the outer segment (outermost
+ * first, one side), the rest continue inward on the other side.  Seeded
+ * from the outer segment's three-cluster seed with t0 = t0_seed.  State at
+ * the innermost cluster; cov6 packed as the upper triangle row by row (21).
+ * Returns 0, 1 when the fit fails. */
+int orc_fit_t0(const float* y, const float* z, const uint16_t* row, const int32_t* sector_of,
+               const int32_t* hits, int32_t n, int32_t n_outer, double t0_seed,
+               const orc_params* prm, const orc_sides_params* sp, double* params6,
+               double* cov6, double* chi2);
+
+/* Pairs the A- and C-side segments of membrane-crossing tracks among the
+ * found tracks (trk_off[T + 1], trk_hits: outermost first) and fits each
+ * pair with t0.  Outputs per track (both members of a pair get its joint
+ * fit): partner[T] (-1 none), t0[T], params6[6 T], cov6[21 T], chi2[T],
+ * ndf[T], dchi2[T] (the joint fit's chi2 increase); margin[T] (may be
+ * NULL): smallest relative margin of the decisions that involved the track.
+ * Returns the number of pairs, -1 on invalid input. */
+int64_t orc_match_sides(const float* y, const float* z, const uint16_t* row, int64_t n,
+                        const int64_t* off, int32_t n_events, const int32_t* trk_off,
+                        const int32_t* trk_hits, int32_t T, const orc_params* prm,
+                        const orc_sides_params* sp, int32_t* partner, double* t0,
+                        double* params6, double* cov6, double* chi2, int32_t* ndf,
+                        double* dchi2, double* margin);
+
 /* Threads used by the OpenMP loops (0 = library default). */
 void orc_set_threads(int n);
 int orc_get_threads(void);

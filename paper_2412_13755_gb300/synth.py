@@ -94,6 +94,7 @@ class Events:
     snp_true: np.ndarray | None = None
     arc_true: np.ndarray | None = None
     align: np.ndarray | None = None  # f64 [216] true correction parameters
+    trk_vz: np.ndarray | None = None  # f64 [T] vertex z (cm)
 
     @property
     def n(self) -> int:
@@ -124,6 +125,25 @@ class Events:
         off[1:] = np.cumsum(cnt[keep])
         return off, hits, ids[keep]
 
+    def truth_segments(self, n_min: int = 10):
+        """Truth hit lists split by side: one segment per (track, side) with
+        >= n_min clusters, outermost first.  Returns (trk_off, trk_hits,
+        track ids, sides (0 = A, 1 = C)); a track that crosses the central
+        membrane gives two segments."""
+        sig = np.nonzero(self.mc_track >= 0)[0]
+        side = (self.sector_of_cluster()[sig] >= N_PHI).astype(np.int64)
+        arc = self.arc_true[sig] if self.arc_true is not None else ROW_X[self.row[sig]]
+        order = np.lexsort((-arc, side, self.mc_track[sig]))
+        sig, side = sig[order], side[order]
+        key = self.mc_track[sig].astype(np.int64) * 2 + side
+        keys, start, cnt = np.unique(key, return_index=True, return_counts=True)
+        keep = cnt >= n_min
+        parts = [sig[s_:s_ + c] for s_, c, k in zip(start, cnt, keep) if k]
+        hits = np.concatenate(parts).astype(np.int32) if parts else np.zeros(0, np.int32)
+        off = np.zeros(int(keep.sum()) + 1, np.int32)
+        off[1:] = np.cumsum(cnt[keep])
+        return off, hits, (keys[keep] // 2).astype(np.int64), (keys[keep] % 2).astype(np.int32)
+
 
 def _grid_voxel(sector, row, y, z, grid):
     """Voxel of the distortion model (grid as in FIELD_GRID) at local (y, z)
@@ -136,8 +156,13 @@ def _grid_voxel(sector, row, y, z, grid):
     return ((sector * nb + band) * ny + iy) * nz + iz
 
 
-def _crossings(phi0, k, tgl, wedge, misalign, want_truth, distortion=None):
+def _crossings(phi0, k, tgl, wedge, misalign, want_truth, distortion=None, vz=None):
     """Intersect each helix with every accepted (sector, row) plane.
+
+    vz: None (every track from z = 0, its side fixed by the sign of tan
+    lambda), or the vertex z of each track: z = vz + tan(lambda) s, and each
+    crossing goes to the sector of the side its own z lies on (a track can
+    cross the central membrane and leave clusters on both sides).
 
     Works in the global transverse plane: the track circle has centre
     C = (sin phi0, -cos phi0)/k and passes through the origin; the outgoing
@@ -185,6 +210,11 @@ def _crossings(phi0, k, tgl, wedge, misalign, want_truth, distortion=None):
         zl = tgl[t_idx][:, None] * s
         snp = np.sin(psi - a[:, None])
         sector = (iphi[t_idx] % N_PHI + side[t_idx])[:, None] + np.zeros_like(s, dtype=np.int64)
+        if vz is not None:
+            zl = zl + vz[t_idx][:, None]
+            sector = (iphi[t_idx] % N_PHI)[:, None] + np.where(zl >= 0.0, 0, N_PHI)
+        if (misalign is not None or distortion is not None) and vz is not None:
+            raise ValueError("a vertex spread is not combined with misalignment or distortion")
         if misalign is not None or distortion is not None:
             # measured point on the displaced plane: x of R^T (P - D) = x_r,
             # solved only where the nominal crossing exists
@@ -269,15 +299,19 @@ def _draw_tracks(rng, n, pt_min, pt_slope, wedge):
 
 
 def _one_collision(rng, n_tracks, noise_frac, wedge, pt_min, pt_slope,
-                   misalign, want_truth, t0_us, tid0, distortion=None):
+                   misalign, want_truth, t0_us, tid0, distortion=None, vz_sigma=0.0):
     q, pt, tgl, phi0 = _draw_tracks(rng, n_tracks, pt_min, pt_slope, wedge)
+    # vertex z spread: drawn only when asked for, so that every other
+    # workload keeps its random stream
+    vz = rng.normal(0.0, vz_sigma, n_tracks) if vz_sigma > 0 else None
     k = KAPPA * BZ * q / pt
     parts = []
     CH = 8192
     for c0 in range(0, n_tracks, CH):
         sl = slice(c0, min(n_tracks, c0 + CH))
         tr, sec, row, y, z, snp, arc = _crossings(phi0[sl], k[sl], tgl[sl], wedge,
-                                                  misalign, want_truth, distortion)
+                                                  misalign, want_truth, distortion,
+                                                  None if vz is None else vz[sl])
         parts.append((tr + c0, sec, row, y, z, snp, arc))
     tr, sec, row, yt, zt, snp, arc = (np.concatenate([p[j] for p in parts]) for j in range(7))
     keep = rng.uniform(size=tr.shape[0]) >= ROW_DROP
@@ -313,13 +347,16 @@ def _one_collision(rng, n_tracks, noise_frac, wedge, pt_min, pt_slope,
         snp_true=np.concatenate([snp, np.full(n_noise, np.nan)]),
         arc_true=np.concatenate([arc, np.full(n_noise, np.nan)]),
     )
-    trk = dict(q=q, pt=pt, tgl=tgl, phi0=phi0)
+    trk = dict(q=q, pt=pt, tgl=tgl, phi0=phi0, vz=np.zeros(n_tracks) if vz is None else vz)
     return cl, trk
 
 
 def generate(events, seed, wedge=None, pt_min=0.2, pt_slope=0.5,
-             misalign=None, truth=False, frame=None, distortion=None):
+             misalign=None, truth=False, frame=None, distortion=None, vz_sigma=0.0):
     """Generate a batch.
+
+    vz_sigma: the Gaussian spread (cm) of the tracks' vertex z (0: every
+            track from z = 0, none crossing the central membrane).
 
     distortion: None, or (grid, field[n_voxels, 3]): each signal cluster is
             measured displaced by -field[v] from the helix crossing (the
@@ -342,7 +379,7 @@ def generate(events, seed, wedge=None, pt_min=0.2, pt_slope=0.5,
     for ev, colls in enumerate(specs):
         for nt, nf, t0 in colls:
             cl, trk = _one_collision(rng, nt, nf, wedge, pt_min, pt_slope,
-                                     misalign, truth, t0, tid0, distortion)
+                                     misalign, truth, t0, tid0, distortion, vz_sigma)
             cl['event'] = np.full(cl['row'].shape[0], ev, np.int64)
             trk['event'] = np.full(nt, ev, np.int32)
             trk['t0'] = np.full(nt, t0)
@@ -378,6 +415,7 @@ def generate(events, seed, wedge=None, pt_min=0.2, pt_slope=0.5,
         trk_q=trk['q'], trk_pt=trk['pt'], trk_tgl=trk['tgl'],
         trk_phi0=trk['phi0'], trk_event=trk['event'], trk_t0=trk['t0'],
     )
+    ev.trk_vz = trk['vz']
     ev.arc_true = cat['arc_true'][order]
     if truth:
         ev.y_true = cat['y_true'][order]
@@ -395,9 +433,10 @@ def generate(events, seed, wedge=None, pt_min=0.2, pt_slope=0.5,
 def _unit(args):
     """One independently seeded generation unit (an event, a collision of a
     frame, or a chunk of the tracks of one event) for generate_parallel."""
-    seed, n_tracks, noise, wedge, pt_min, pt_slope, misalign, t0 = args
+    seed, n_tracks, noise, wedge, pt_min, pt_slope, misalign, t0, vz_sigma = args
     rng = np.random.default_rng(seed)
-    cl, trk = _one_collision(rng, n_tracks, noise, wedge, pt_min, pt_slope, misalign, False, t0, 0)
+    cl, trk = _one_collision(rng, n_tracks, noise, wedge, pt_min, pt_slope, misalign, False, t0, 0,
+                             vz_sigma=vz_sigma)
     keep = ("sector", "row", "y", "z", "charge", "mc", "arc_true")
     cl = {k: cl[k] for k in keep}
     cl["y"] = cl["y"].astype(np.float32)
@@ -406,7 +445,7 @@ def _unit(args):
 
 
 def generate_parallel(units, seed, workers=None, wedge=None, pt_min=0.2, pt_slope=0.5,
-                      misalign=None):
+                      misalign=None, vz_sigma=0.0):
     """Like generate() for many units, in a spawn-context process pool.
 
     units: list of (event index, n_tracks, noise_frac[, t0_us]); units of
@@ -420,7 +459,7 @@ def generate_parallel(units, seed, workers=None, wedge=None, pt_min=0.2, pt_slop
     if workers is None:
         workers = max(1, len(os.sched_getaffinity(0)))
     units = [tuple(u) + (0.0,) * (4 - len(u)) for u in units]
-    jobs = [((seed, u), nt, nf, wedge, pt_min, pt_slope, misalign, t0)
+    jobs = [((seed, u), nt, nf, wedge, pt_min, pt_slope, misalign, t0, vz_sigma)
             for u, (_, nt, nf, t0) in enumerate(units)]
     with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
         res = list(ex.map(_unit, jobs, chunksize=max(1, len(jobs) // (4 * workers))))
@@ -447,6 +486,7 @@ def generate_parallel(units, seed, workers=None, wedge=None, pt_min=0.2, pt_slop
                 charge=cat["charge"][order], evt_sector_off=off, n_events=E,
                 mc_track=cat["mc"][order], trk_q=trk["q"], trk_pt=trk["pt"], trk_tgl=trk["tgl"],
                 trk_phi0=trk["phi0"], trk_event=trk["event"], trk_t0=trk["t0"])
+    ev.trk_vz = trk["vz"]
     ev.arc_true = cat["arc_true"][order]
     if misalign is not None:
         ev.align = np.asarray(misalign, np.float64).copy()
@@ -502,6 +542,28 @@ def pileup_frame(n_collisions=100, n_tracks=10000, noise=0.20,
     """50 kHz frame: collisions at uniform drift-time offsets over 2 ms."""
     return generate(None, seed, frame=[(n_tracks, noise)] * n_collisions,
                     truth=truth)
+
+
+VZ_SIGMA = 6.0   # cm, vertex z spread of the membrane-crossing frames
+
+
+def membrane_frame(n_collisions=20, n_tracks=2000, noise=0.20, vz_sigma=VZ_SIGMA,
+                   seed=SEED_BASE + 8, truth=False):
+    """A pile-up frame whose collisions have a vertex z spread: tracks of
+    small |tan lambda| cross the central membrane and leave one segment on
+    each side, seen shifted in opposite directions by the collision's
+    drift-time offset."""
+    return generate(None, seed, frame=[(n_tracks, noise)] * n_collisions, truth=truth,
+                    vz_sigma=vz_sigma)
+
+
+def membrane_frame_parallel(n_collisions=100, n_tracks=10000, noise=0.20, vz_sigma=VZ_SIGMA,
+                            seed=SEED_BASE + 8, workers=None):
+    """The 50 kHz frame with a vertex z spread, generated in parallel."""
+    rng = np.random.default_rng(seed + 2000003)
+    t0 = rng.uniform(0.0, FRAME_US, n_collisions)
+    return generate_parallel([(0, n_tracks, noise, float(t0[i])) for i in range(n_collisions)],
+                             seed, workers=workers, vz_sigma=vz_sigma)
 
 
 def uneven_batch(n_events=512, lo=10, hi=10000, seed=SEED_BASE + 3, truth=False):
