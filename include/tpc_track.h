@@ -276,10 +276,10 @@ tpc_status tpc_autotune(tpc_ctx* ctx, int32_t* track_of_cluster, int32_t* trk_of
  * call of each kind, the milliseconds of the stages listed in
  * TPC_STAGE_NAMES (ms_out[TPC_N_STAGES]).  Disabled by default; enabling it
  * creates the events (host-side CUDA objects, no device memory). */
-#define TPC_N_STAGES 12
+#define TPC_N_STAGES 13
 #define TPC_STAGE_NAMES                                                         \
     "bin", "neighbours", "links", "chains", "tracklets", "select", "merge_cand", \
-        "match", "output", "fit", "adjoint", "find_total"
+        "match", "output", "fit", "adjoint", "find_total", "sides"
 tpc_status tpc_stage_timing(tpc_ctx* ctx, int enable);
 tpc_status tpc_stage_times(tpc_ctx* ctx, float* ms_out);
 
@@ -421,6 +421,68 @@ tpc_status tpc_find_clusters(const uint16_t* digits, int32_t n_events, int32_t n
 
 /* Clears the device status word and counters (asynchronous). */
 tpc_status tpc_reset_status(tpc_ctx* ctx, tpc_stream_t stream);
+
+/* NEXT-4: the drift-time offset t0 as a sixth state parameter, and the
+ * association of the A- and C-side segments of membrane-crossing tracks.
+ * The paper reconstructs continuous-readout time frames (Sec. 1, Sec. 4)
+ * and gives no algorithm; this is the build's reading.  A collision at
+ * drift-time offset t0 (us) is seen at z' = z - v t0 on side A (sectors
+ * 0..17) and z' = z + v t0 on side C.  Found tracks never span both sides,
+ * so a track that crosses the central membrane is found as an inner and an
+ * outer segment, on opposite sides of one phi sector (or of two adjacent
+ * ones), with adjacent row ranges.  A candidate pair (inner i, outer o)
+ * passes when
+ *   - 1 <= row(o's innermost cluster) - row(i's outermost) <= gap_max;
+ *   - i's outward-fit state, moved to o's innermost plane, agrees with o's
+ *     inward-fit state in (y, sin phi, tan lambda, q/pT): 4-d chi2 with the
+ *     sum of both covariances <= chi2_junction;
+ *   - the true z at the junction, the mean of the two apparent z there, is
+ *     within z_membrane of the membrane;
+ *   - the six-parameter fit of o's clusters then i's (state y, z, sin phi,
+ *     tan lambda, q/pT, t0 with z the true z; seeded from o's three-cluster
+ *     seed with t0 = (z'_o - z'_i) / (2 sgn_i v) at the junction, prior
+ *     sigma t0_prior) raises the chi2 by at most chi2_joint over the two
+ *     five-parameter fits.
+ * Each track keeps its best candidate by (chi2 increase rounded to FP32,
+ * partner index); a pair is accepted when each member is the other's best.
+ * All fits in FP64.  NULL options select the defaults below. */
+typedef struct {
+    int32_t n_min;        /* minimum clusters of a segment (default 10)       */
+    int32_t gap_max;      /* default 8                                        */
+    double chi2_junction; /* default 30                                       */
+    double z_membrane;    /* cm, default 3                                    */
+    double chi2_joint;    /* default 40                                       */
+    double t0_prior;      /* us, default 1                                    */
+    double v_drift;       /* cm/us, default 2.58                              */
+} tpc_sides_options;
+
+/* Device bytes of the caller's scratch for tpc_match_sides: max_tracks
+ * tracks, n_events events, cand_cap candidate pairs after the junction
+ * test.  0 for invalid sizes. */
+size_t tpc_sides_workspace_bytes(int32_t max_tracks, int32_t n_events, int32_t cand_cap);
+
+/* Pairs the segments among the found tracks trk_off[n_tracks + 1],
+ * trk_hits (outermost first, input-order cluster indices of the loaded
+ * batch, as tpc_find_tracks writes them) and fits each pair with t0.
+ * n_tracks_dev (device, may be NULL) caps the count on the device.
+ * workspace: device, 256-byte aligned, tpc_sides_workspace_bytes(n_tracks,
+ * loaded events, cand_cap) bytes.  Outputs (device, caller-owned; entries
+ * [0, track count) are written, both members of a pair get the pair's
+ * joint fit): partner[n] (the other member, -1 none), t0[n] (us),
+ * params6[6 n] (y, z, sin phi, tan lambda, q/pT, t0 at the inner segment's
+ * innermost cluster, z the true z), cov6[21 n] (upper triangle row by row),
+ * chi2[n], ndf[n] (2 (clusters of both) - 6; -1 unpaired), dchi2[n] (the
+ * chi2 increase); n_pairs_dev[1].  More candidates than cand_cap set
+ * TPC_ERR_CAPACITY in the device status word (read by tpc_get_stats); the
+ * pairs are then incomplete.  Asynchronous on stream.  Errors:
+ * TPC_ERR_STATE (no workspace or clusters), TPC_ERR_ARG (null pointer,
+ * bad options, misaligned or short scratch), TPC_ERR_CAPACITY (n_tracks
+ * above the context's track capacity). */
+tpc_status tpc_match_sides(tpc_ctx* ctx, const int32_t* trk_off, const int32_t* trk_hits, int32_t n_tracks,
+                           const int32_t* n_tracks_dev, const tpc_sides_options* options, void* workspace,
+                           size_t workspace_bytes, int32_t cand_cap, int32_t* partner, double* t0,
+                           double* params6, double* cov6, double* chi2, int32_t* ndf, double* dchi2,
+                           int32_t* n_pairs_dev, tpc_stream_t stream);
 
 #ifdef __cplusplus
 }

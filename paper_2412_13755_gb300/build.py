@@ -12,7 +12,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libtpctrack.so")
 SOURCES = ["tpc_common.cu", "tpc_find.cu", "tpc_fit.cu", "tpc_fit_ex.cu", "tpc_adjoint.cu",
-           "tpc_abi.cu", "tpc_noalloc.cu", "tpc_cluster.cu"]
+           "tpc_abi.cu", "tpc_noalloc.cu", "tpc_cluster.cu", "tpc_sides.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
          "-Xcompiler", "-fPIC,-ffp-contract=off", "-I", os.path.join(HERE, "..", "include")]

@@ -1,11 +1,13 @@
 // C ABI of libtpctrack: context, workspace layout, argument checks, and the
 // entry points declared in include/tpc_track.h.  No C++ exception leaves
 // these functions.
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
 
 #include "tpc_internal.h"
+#include "tpc_sides.cuh"
 
 using namespace tpc;
 
@@ -206,8 +208,8 @@ tpc_status tpc_stage_times(tpc_ctx* c, float* ms) {
     if (!c || !ms) return TPC_ERR_ARG;
     if (!c->marks[0]) return fail(c, TPC_ERR_STATE, "stage timing was never enabled");
     // pairs of marks per stage; a pair never recorded reads as 0
-    static const int pairs[TPC_N_STAGES][2] = {{0, 1}, {1, 2},  {2, 3},  {3, 4},  {4, 5},   {5, 6},
-                                               {6, 7}, {7, 8},  {8, 9},  {10, 11}, {12, 13}, {0, 9}};
+    static const int pairs[TPC_N_STAGES][2] = {{0, 1}, {1, 2}, {2, 3},   {3, 4},   {4, 5}, {5, 6}, {6, 7},
+                                               {7, 8}, {8, 9}, {10, 11}, {12, 13}, {0, 9}, {14, 15}};
     for (int i = 0; i < TPC_N_STAGES; ++i) {
         float v = 0.f;
         if (cudaEventSynchronize(c->marks[pairs[i][1]]) == cudaSuccess &&
@@ -321,6 +323,48 @@ tpc_status tpc_fit_adjoint(tpc_ctx* c, const int32_t* trk_off, const int32_t* tr
     cudaError_t e = run_adjoint(c, trk_off, trk_hits, n_tracks, align, chi2_total, grad,
                                 (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "tpc_fit_adjoint");
+    return TPC_OK;
+}
+
+static bool sides_prm(const tpc_sides_options* o, SidesPrm& S) {
+    S = SidesPrm{10, 8, 30.0, 3.0, 40.0, 1.0, 2.58};
+    if (!o) return true;
+    if (o->n_min < 3 || o->n_min > NROW * 4 || o->gap_max < 1 || o->gap_max >= NROW ||
+        !(o->chi2_junction > 0.0) || !(o->z_membrane > 0.0) || !(o->chi2_joint > 0.0) ||
+        !(o->t0_prior > 0.0) || !(o->v_drift > 0.0) || !std::isfinite(o->chi2_junction) ||
+        !std::isfinite(o->z_membrane) || !std::isfinite(o->chi2_joint) || !std::isfinite(o->t0_prior) ||
+        !std::isfinite(o->v_drift))
+        return false;
+    S = SidesPrm{o->n_min, o->gap_max, o->chi2_junction, o->z_membrane, o->chi2_joint, o->t0_prior, o->v_drift};
+    return true;
+}
+
+size_t tpc_sides_workspace_bytes(int32_t max_tracks, int32_t n_events, int32_t cand_cap) {
+    if (max_tracks < 0 || n_events < 1 || n_events > (1 << 16) || cand_cap < 0) return 0;
+    return sides_layout(max_tracks, n_events, cand_cap).total;
+}
+
+tpc_status tpc_match_sides(tpc_ctx* c, const int32_t* trk_off, const int32_t* trk_hits, int32_t n_tracks,
+                           const int32_t* n_tracks_dev, const tpc_sides_options* o, void* workspace,
+                           size_t workspace_bytes, int32_t cand_cap, int32_t* partner, double* t0,
+                           double* params6, double* cov6, double* chi2, int32_t* ndf, double* dchi2,
+                           int32_t* n_pairs_dev, tpc_stream_t stream) {
+    if (!c) return TPC_ERR_ARG;
+    if (!c->have_ws || !c->have_clusters) return fail(c, TPC_ERR_STATE, "no workspace or clusters");
+    SidesPrm S;
+    if (!sides_prm(o, S)) return fail(c, TPC_ERR_ARG, "tpc_match_sides: bad options");
+    if (n_tracks < 0 || cand_cap < 0 || !workspace || !n_pairs_dev ||
+        (n_tracks > 0 && (!trk_off || !trk_hits || !partner || !t0 || !params6 || !cov6 || !chi2 || !ndf ||
+                          !dchi2)))
+        return fail(c, TPC_ERR_ARG, "tpc_match_sides: bad argument");
+    if (((uintptr_t)workspace & 255) != 0) return fail(c, TPC_ERR_ARG, "tpc_match_sides: workspace not 256-byte aligned");
+    if (n_tracks > c->ws.L.T - 1) return fail(c, TPC_ERR_CAPACITY, "tpc_match_sides: too many tracks");
+    const SidesLayout L = sides_layout(n_tracks, c->n_events, cand_cap);
+    if (workspace_bytes < L.total) return fail(c, TPC_ERR_ARG, "tpc_match_sides: workspace too small");
+    cudaError_t e = run_match_sides(c, trk_off, trk_hits, n_tracks, n_tracks_dev, S, static_cast<char*>(workspace),
+                                    L, cand_cap, partner, t0, params6, cov6, chi2, ndf, dchi2, n_pairs_dev,
+                                    (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "tpc_match_sides");
     return TPC_OK;
 }
 

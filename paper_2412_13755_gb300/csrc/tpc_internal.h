@@ -126,7 +126,8 @@ struct tpc_ctx {
     int n_sm = 152;                     // SMs of the device (queried at set-up)
     cudaGraphExec_t graph = nullptr;    // S7 graph (tpc_graph_capture)
     long long graph_kernels = 0;        // kernels in that graph
-    // stage timing: marks 0..9 around the find stages, 10/11 fit, 12/13 adjoint
+    // stage timing: marks 0..9 around the find stages, 10/11 fit, 12/13 adjoint,
+    // 14/15 the A/C-side association
     bool timing = false;
     cudaEvent_t marks[16] = {};
     void mark(int i, cudaStream_t s) {
@@ -154,6 +155,18 @@ cudaError_t run_adjoint_field(tpc_ctx* c, const int32_t* trk_off, const int32_t*
                               int32_t n_tracks, const double* align, const FieldGridD& fg,
                               const double* field, double* chi2_total, double* grad_align,
                               double* grad_field, cudaStream_t s);
+// NEXT-4: the A/C-side association (tpc_sides.cu); its scratch is the
+// caller's (tpc_sides_workspace_bytes)
+struct SidesPrm;
+struct SidesLayout {
+    int64_t K;  // buckets: events x 2 sides x 18 phi sectors x 152 rows
+    size_t ends, cls, need, best, blist, bcnt, boff, bfill, scan, cand, counters, total;
+};
+SidesLayout sides_layout(int64_t max_tracks, int32_t n_events, int64_t cand_cap);
+cudaError_t run_match_sides(tpc_ctx* c, const int32_t* trk_off, const int32_t* trk_hits, int32_t n_tracks,
+                            const int32_t* n_tracks_dev, const SidesPrm& S, char* ws, const SidesLayout& L,
+                            int32_t cand_cap, int32_t* partner, double* t0, double* params6, double* cov6,
+                            double* chi2, int32_t* ndf, double* dchi2, int32_t* n_pairs_dev, cudaStream_t s);
 cudaError_t fill_i32(int32_t* p, int64_t n, int32_t v, cudaStream_t s);
 // exclusive scan of in[0..L) into out[0..L] (out[L] = total); tmp from the workspace
 cudaError_t scan_i32(const int32_t* in, int32_t* out, int64_t L, int32_t* tmp, cudaStream_t s);

@@ -25,9 +25,9 @@ EXPORTS = ("tpc_default_params", "tpc_create", "tpc_destroy", "tpc_workspace_byt
            "tpc_stage_timing", "tpc_stage_times", "tpc_find_tracks_noalloc", "tpc_set_tune",
            "tpc_autotune", "tpc_field_voxels", "tpc_fit_adjoint_field", "tpc_track_batch",
            "tpc_graph_capture", "tpc_graph_launch", "tpc_fit_tracks_ex", "tpc_cluster_workspace_bytes",
-           "tpc_find_clusters")
+           "tpc_find_clusters", "tpc_sides_workspace_bytes", "tpc_match_sides")
 STAGE_NAMES = ("bin", "neighbours", "links", "chains", "tracklets", "select", "merge_cand",
-               "match", "output", "fit", "adjoint", "find_total")
+               "match", "output", "fit", "adjoint", "find_total", "sides")
 
 
 class Params(C.Structure):
@@ -57,6 +57,20 @@ class FitOptions(C.Structure):
 
 def fit_options(mat_x_x0=0.0, mat_eloss=0.0, mass=0.13957, outward=False) -> FitOptions:
     return FitOptions(float(mat_x_x0), float(mat_eloss), float(mass), 1 if outward else 0)
+
+
+class SidesOptions(C.Structure):
+    """Options of the A/C-side association with t0 (tpc_sides_options)."""
+    _fields_ = [("n_min", C.c_int32), ("gap_max", C.c_int32), ("chi2_junction", C.c_double),
+                ("z_membrane", C.c_double), ("chi2_joint", C.c_double), ("t0_prior", C.c_double),
+                ("v_drift", C.c_double)]
+
+
+def sides_options(n_min=10, gap_max=8, chi2_junction=30.0, z_membrane=3.0, chi2_joint=40.0, t0_prior=1.0,
+                  v_drift=2.58) -> SidesOptions:
+    """The library's defaults unless overridden."""
+    return SidesOptions(int(n_min), int(gap_max), float(chi2_junction), float(z_membrane), float(chi2_joint),
+                        float(t0_prior), float(v_drift))
 
 
 class BatchOutputs(C.Structure):
@@ -135,11 +149,14 @@ def load_library(build_if_missing: bool = True):
     lib.tpc_fit_tracks_ex.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.tpc_cluster_workspace_bytes.argtypes = [i32, i32]
     lib.tpc_cluster_workspace_bytes.restype = sz
+    lib.tpc_sides_workspace_bytes.argtypes = [i32, i32, i32]
+    lib.tpc_sides_workspace_bytes.restype = sz
+    lib.tpc_match_sides.argtypes = [vp, vp, vp, i32, vp, vp, vp, sz, i32] + [vp] * 8 + [vp]
     lib.tpc_find_clusters.argtypes = [vp, i32, i32, i32, vp, sz, vp, vp, vp, vp, vp, i64, vp, vp, vp]
     for name in EXPORTS:
         f = getattr(lib, name)
         if name not in ("tpc_default_params", "tpc_destroy", "tpc_workspace_bytes",
-                        "tpc_field_voxels", "tpc_cluster_workspace_bytes"):
+                        "tpc_field_voxels", "tpc_cluster_workspace_bytes", "tpc_sides_workspace_bytes"):
             f.restype = C.c_int
     _lib = lib
     return lib
@@ -329,6 +346,54 @@ def tpc_fit_tracks_ex(ctx, trk_off, trk_hits, n_tracks, n_tracks_dev, options, p
                                           _ptr(n_tracks_dev), C.byref(options) if options is not None else None,
                                           _ptr(params), _ptr(cov), _ptr(chi2), _ptr(ndf), _ptr(smoothed),
                                           _stream(stream))
+    _check(ctx, rc, what)
+
+
+def tpc_sides_workspace_bytes(max_tracks: int, n_events: int, cand_cap: int) -> int:
+    return int(load_library().tpc_sides_workspace_bytes(int(max_tracks), int(n_events), int(cand_cap)))
+
+
+SIDES_OUT = (("partner", torch.int32, 1), ("t0", torch.float64, 1), ("params6", torch.float64, 6),
+             ("cov6", torch.float64, 21), ("chi2", torch.float64, 1), ("ndf", torch.int32, 1),
+             ("dchi2", torch.float64, 1))
+
+
+def check_sides_buffers(n_tracks, trk_off, out, n_pairs_dev, workspace, need, what="tpc_match_sides"):
+    """tpc_match_sides reads trk_off[n_tracks + 1] and writes n_tracks
+    entries of each per-track output (partner, t0, params6 x 6, cov6 x 21,
+    chi2, ndf, dchi2), one of n_pairs_dev, and uses need bytes of scratch."""
+    T = int(n_tracks)
+    if T < 0:
+        raise ValueError(f"{what}: n_tracks {T} < 0")
+    _need_len(trk_off, T + 1, "trk_off", what)
+    for (name, _, k), t in zip(SIDES_OUT, out):
+        _need_len(t, k * T, name, what)
+    _need_len(n_pairs_dev, 1, "n_pairs_dev", what)
+    if need == 0:
+        raise ValueError(f"{what}: invalid sizes")
+    if workspace.numel() * workspace.element_size() < need:
+        raise ValueError(f"{what}: workspace holds {workspace.numel() * workspace.element_size()} bytes, "
+                         f"the call needs {need}")
+
+
+def tpc_match_sides(ctx, trk_off, trk_hits, n_tracks, n_tracks_dev, options, workspace, cand_cap, out,
+                    n_pairs_dev, n_events, stream=None):
+    """out = (partner, t0, params6, cov6, chi2, ndf, dchi2) as SIDES_OUT."""
+    what = "tpc_match_sides"
+    _need(trk_off, torch.int32, "trk_off")
+    _need(trk_hits, torch.int32, "trk_hits")
+    for (name, dt, _), t in zip(SIDES_OUT, out):
+        _need(t, dt, name)
+    _need(n_pairs_dev, torch.int32, "n_pairs_dev")
+    if n_tracks_dev is not None:
+        _need(n_tracks_dev, torch.int32, "n_tracks_dev")
+    _need(workspace, torch.uint8, "workspace")
+    need = tpc_sides_workspace_bytes(n_tracks, n_events, cand_cap)
+    check_sides_buffers(n_tracks, trk_off, out, n_pairs_dev, workspace, need, what)
+    rc = load_library().tpc_match_sides(ctx, _ptr(trk_off), _ptr(trk_hits), int(n_tracks), _ptr(n_tracks_dev),
+                                        C.byref(options) if options is not None else None, _ptr(workspace),
+                                        workspace.numel() * workspace.element_size(), int(cand_cap),
+                                        *[_ptr(t) for t in out], _ptr(n_pairs_dev), _stream(stream))
     _check(ctx, rc, what)
 
 
@@ -580,6 +645,7 @@ class Tracker:
         self.ctx = tpc_create(self.params)
         self.max_clusters = int(max_clusters)
         self.max_events = int(max_events)
+        self.n_events_loaded = 1
         nbytes = tpc_workspace_bytes(self.ctx, self.max_clusters, self.max_events)
         self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
         tpc_set_workspace(self.ctx, self.workspace, self.max_clusters, self.max_events)
@@ -603,6 +669,7 @@ class Tracker:
         refused before any find kernel could run on it."""
         self._inputs = (y, z, row, charge, evt_sector_off)  # keep alive
         tpc_load_clusters(self.ctx, y, z, row, charge, evt_sector_off, n_events, stream)
+        self.n_events_loaded = int(n_events)
         self.n = y.numel()
         if validate:
             self.check(stream)
@@ -649,6 +716,26 @@ class Tracker:
         sm = torch.zeros(max(trk_hits.numel(), 1), 20, dtype=torch.float64, device=dev) if smooth else None
         tpc_fit_tracks_ex(self.ctx, trk_off, trk_hits, n_tracks, n_tracks_dev, options, *out, sm, stream)
         return (*out, sm)
+
+    def match_sides(self, trk_off, trk_hits, n_tracks, n_tracks_dev=None, options=None, cand_cap=None,
+                    stream=None):
+        """NEXT-4: pairs the A- and C-side segments of membrane-crossing
+        tracks among the found tracks and fits each pair with t0.  Returns a
+        dict of per-track device tensors (partner, t0, params6, cov6, chi2,
+        ndf, dchi2) and n_pairs (device int32[1])."""
+        dev = self.device
+        T = int(n_tracks)
+        cap = max(T, 1024) if cand_cap is None else int(cand_cap)
+        out = tuple(torch.empty(max(T, 1), *(() if k == 1 else (k,)), dtype=dt, device=dev)
+                    for _, dt, k in SIDES_OUT)
+        n_pairs = torch.zeros(1, dtype=torch.int32, device=dev)
+        E = self.n_events_loaded
+        need = tpc_sides_workspace_bytes(T, E, cap)
+        ws = torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
+        tpc_match_sides(self.ctx, trk_off, trk_hits, T, n_tracks_dev, options, ws, cap, out, n_pairs, E, stream)
+        res = {name: t for (name, _, _), t in zip(SIDES_OUT, out)}
+        res["n_pairs"] = n_pairs
+        return res
 
     def adjoint(self, trk_off, trk_hits, n_tracks, align, want_grad=True, stream=None):
         chi2 = torch.zeros(1, dtype=torch.float64, device=self.device)
@@ -700,6 +787,7 @@ class Tracker:
         self._inputs = (y, z, row, charge, evt_sector_off)
         tpc_track_batch(self.ctx, y, z, row, charge, evt_sector_off, n_events, find_out, fit_out, stream)
         self.n = y.numel()
+        self.n_events_loaded = int(n_events)
 
     def capture(self, y, z, row, evt_sector_off, n_events, find_out, fit_out=None, charge=None):
         """Records the batch call into the context's CUDA graph; replay()
@@ -707,6 +795,7 @@ class Tracker:
         self._graph_buffers = (y, z, row, charge, evt_sector_off, find_out, fit_out)
         tpc_graph_capture(self.ctx, y, z, row, charge, evt_sector_off, n_events, find_out, fit_out)
         self.n = y.numel()
+        self.n_events_loaded = int(n_events)
 
     def replay(self, stream=None):
         tpc_graph_launch(self.ctx, stream)

@@ -75,14 +75,15 @@ def test_struct_sizes_match_header(lib, tmp_path):
     inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
     src = tmp_path / "sizes.c"
     src.write_text('#include <stdio.h>\n#include "tpc_track.h"\n'
-                   'int main(void) { printf("%zu %zu %zu %zu\\n", sizeof(tpc_params), sizeof(tpc_stats), '
-                   'sizeof(tpc_tune), sizeof(tpc_field_grid)); return 0; }\n')
+                   'int main(void) { printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(tpc_params), sizeof(tpc_stats), '
+                   'sizeof(tpc_tune), sizeof(tpc_field_grid), sizeof(tpc_fit_options), '
+                   'sizeof(tpc_sides_options)); return 0; }\n')
     exe = tmp_path / "sizes"
     subprocess.run([cc, "-I", inc, str(src), "-o", str(exe)], check=True)
     sizes = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True,
                                             text=True).stdout.split()]
     assert sizes == [C.sizeof(tpc.Params), C.sizeof(tpc.Stats), C.sizeof(tpc.Tune),
-                     C.sizeof(tpc.FieldGrid)]
+                     C.sizeof(tpc.FieldGrid), C.sizeof(tpc.FitOptions), C.sizeof(tpc.SidesOptions)]
 
 
 def test_field_voxels(lib):
@@ -139,3 +140,18 @@ def test_batch_calls_refused_without_device_work(lib):
         assert lib.tpc_set_tune(ctx, None) == tpc.TPC_OK
     finally:
         tpc.tpc_destroy(ctx)
+
+
+def test_match_sides_refused_without_device_work(lib):
+    """Host-side refusals of tpc_match_sides (NEXT-4): nothing is launched."""
+    from paper_2412_13755_gb300 import tpc
+    assert lib.tpc_match_sides(None, None, None, 0, None, None, None, 0, 0, *([None] * 8), None) == tpc.TPC_ERR_ARG
+    ctx = tpc.tpc_create(tpc.default_params())
+    try:
+        # no workspace, no clusters
+        assert lib.tpc_match_sides(ctx, None, None, 0, None, None, None, 0, 0, *([None] * 8), None) == \
+            tpc.TPC_ERR_STATE
+    finally:
+        tpc.tpc_destroy(ctx)
+    assert tpc.tpc_sides_workspace_bytes(10, 1, 0) > 0
+    assert tpc.tpc_sides_workspace_bytes(10, 1 << 17, 0) == 0

@@ -24,7 +24,8 @@ class StubLib:
 
     def __getattr__(self, name):
         real_f = getattr(self.real, name)
-        if name in ("tpc_field_voxels", "tpc_cluster_workspace_bytes"):  # host-only: the real one
+        if name in ("tpc_field_voxels", "tpc_cluster_workspace_bytes",
+                    "tpc_sides_workspace_bytes"):  # host-only: the real one
             return real_f
 
         def f(*args):
@@ -282,3 +283,36 @@ def test_find_clusters(stub):
                               torch.zeros(nb, dtype=torch.uint8), outs)
     with pytest.raises(ValueError, match="status_dev"):
         tpc.tpc_find_clusters(d, n_ev, torch.zeros(nb, dtype=torch.uint8), outs[:6] + (i32(1),))
+
+
+def test_match_sides(stub):
+    T, E, cap = 50, 2, 64
+    nb = tpc.tpc_sides_workspace_bytes(T, E, cap)
+    assert nb > 0 and tpc.tpc_sides_workspace_bytes(-1, 1, 1) == 0 and tpc.tpc_sides_workspace_bytes(5, 0, 1) == 0
+    assert tpc.tpc_sides_workspace_bytes(T, E, 2 * cap) > nb
+    out = (i32(T), f64(T), f64(T, 6), f64(T, 21), f64(T), i32(T), f64(T))
+    ws = torch.zeros(nb, dtype=torch.uint8)
+    o = tpc.sides_options(gap_max=5)
+    tpc.tpc_match_sides(CTX, i32(T + 1), i32(100), T, i32(1), o, ws, cap, out, i32(1), E)
+    tpc.tpc_match_sides(CTX, i32(T + 1), i32(100), T, None, None, ws, cap, out, i32(1), E)
+    assert stub.calls[-1] == "tpc_match_sides"
+    for k, name in enumerate(("partner", "t0", "params6", "cov6", "chi2", "ndf", "dchi2")):
+        short = list(out)
+        short[k] = short[k].reshape(-1)[:-1].clone()
+        with pytest.raises(ValueError, match=name):
+            tpc.tpc_match_sides(CTX, i32(T + 1), i32(100), T, None, None, ws, cap, tuple(short), i32(1), E)
+    with pytest.raises(ValueError, match="workspace"):
+        tpc.tpc_match_sides(CTX, i32(T + 1), i32(100), T, None, None, ws[:-1].clone(), cap, out, i32(1), E)
+    with pytest.raises(ValueError, match="trk_off"):
+        tpc.tpc_match_sides(CTX, i32(T), i32(100), T, None, None, ws, cap, out, i32(1), E)
+    with pytest.raises(TypeError, match="cov6"):
+        tpc.tpc_match_sides(CTX, i32(T + 1), i32(100), T, None, None, ws, cap,
+                            out[:3] + (f32(T, 21),) + out[4:], i32(1), E)
+    tr = object.__new__(tpc.Tracker)
+    tr.device = torch.device("cpu")
+    tr.ctx = CTX
+    tr.n_events_loaded = E
+    r = tr.match_sides(i32(T + 1), i32(100), T)
+    assert r["params6"].shape == (T, 6) and r["cov6"].shape == (T, 21) and r["partner"].shape == (T,)
+    assert r["n_pairs"].shape == (1,)
+    tr.ctx = None
