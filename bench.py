@@ -235,6 +235,48 @@ def pileup_bench(torch, tpc, dev, steps):
             "workspace_gb": tr.workspace.numel() / 1e9, "generation_s": gen_s}
 
 
+def sides_bench(torch, tpc, dev, steps):
+    """NEXT-4: a 20-collision frame with a vertex z spread (sigma 6 cm),
+    found once; the timed step is the A/C-side association with t0 over all
+    found tracks (tpc_match_sides), candidates, end fits and joint fits."""
+    from paper_2412_13755_gb300 import synth
+    t0 = time.perf_counter()
+    ev = synth.membrane_frame_parallel(n_collisions=20)
+    gen_s = time.perf_counter() - t0
+    n = ev.n
+    cap = n // 10 + 16
+    tr = tpc.Tracker(n, 1, device=dev)
+    y = torch.from_numpy(ev.y).to(dev)
+    z = torch.from_numpy(ev.z).to(dev)
+    row = torch.from_numpy(ev.row.view(np.int16)).to(dev).view(torch.uint16)
+    d_off = torch.from_numpy(ev.evt_sector_off).to(dev)
+    tr.load(y, z, row, d_off, 1)
+    out = tr.alloc_find_outputs(cap)
+    tr.find(out=out)
+    torch.cuda.synchronize()
+    tr.check()
+    T = int(out[3].item())
+    r = tr.match_sides(out[1], out[2], T)
+    torch.cuda.synchronize()
+    tr.check()
+    pairs = int(r["n_pairs"].item())
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        r = tr.match_sides(out[1], out[2], T)
+    e1.record()
+    torch.cuda.synchronize()
+    tr.check()
+    sec = e0.elapsed_time(e1) / 1e3 / steps
+    p = r["partner"][:T]
+    sel = torch.nonzero(p >= 0).flatten()
+    sig = torch.sqrt(r["cov6"][sel, 20])
+    return {"workload": f"membrane_frame: 20 collisions x 1e4 tracks over 2 ms, vertex z sigma 6 cm, {n} clusters, "
+                        f"{T} found tracks", "tracks_per_s": T / sec, "ms_per_step": 1e3 * sec, "pairs": pairs,
+            "t0_sigma_median_us": float(sig.median().item()) if len(sel) else None, "generation_s": gen_s}
+
+
 def field_adjoint_bench(torch, tpc, dev, steps):
     """NEXT-1: chi2 and its gradient with respect to the voxel displacement
     field (36 x 160 voxels x 3) plus the alignment, on 2e5 pT > 1 GeV/c
@@ -310,7 +352,7 @@ def clusterize_bench(torch, tpc, dev, steps, ev):
             "inputs_vs_l2": "0.9 GB of digits, larger than L2 (no flush needed)"}
 
 
-EXTRA_NAMES = ("batched_vs_plain", "adjoint", "clusterize", "field_adjoint", "pileup_frame")
+EXTRA_NAMES = ("batched_vs_plain", "adjoint", "clusterize", "field_adjoint", "sides", "pileup_frame")
 
 
 def parse():
@@ -757,7 +799,8 @@ def run_ours(args):
         extras += [("batched_vs_plain", lambda: batched_vs_plain(torch, tpc, dev, max(3, args.steps // 4))),
                    ("adjoint", lambda: adjoint_bench(torch, tpc, dev, max(3, args.steps // 4))),
                    ("clusterize", lambda: clusterize_bench(torch, tpc, dev, max(3, args.steps // 2), ev)),
-                   ("field_adjoint", lambda: field_adjoint_bench(torch, tpc, dev, max(3, args.steps // 4)))]
+                   ("field_adjoint", lambda: field_adjoint_bench(torch, tpc, dev, max(3, args.steps // 4))),
+                   ("sides", lambda: sides_bench(torch, tpc, dev, max(3, args.steps // 4)))]
     if args.pileup:
         extras.append(("pileup_frame", lambda: pileup_bench(torch, tpc, dev, 2)))
     for name, fn in extras:
@@ -781,6 +824,7 @@ def run_only(args):
            "adjoint": lambda: adjoint_bench(torch, tpc, dev, k),
            "clusterize": lambda: clusterize_bench(torch, tpc, dev, max(3, args.steps // 2), make_event()),
            "field_adjoint": lambda: field_adjoint_bench(torch, tpc, dev, k),
+           "sides": lambda: sides_bench(torch, tpc, dev, k),
            "pileup_frame": lambda: pileup_bench(torch, tpc, dev, 2)}
     print(json.dumps({args.only: fns[args.only]()}), flush=True)
 

@@ -433,6 +433,10 @@ tpc_status tpc_reset_status(tpc_ctx* ctx, tpc_stream_t stream);
  * ones), with adjacent row ranges.  A candidate pair (inner i, outer o)
  * passes when
  *   - 1 <= row(o's innermost cluster) - row(i's outermost) <= gap_max;
+ *   - before any fit, the mean of the apparent z of those two clusters is
+ *     within z_pre of the membrane (segments of different collisions lie
+ *     v |t0_a - t0_b| apart there; the sum of the two FP32 values is exact
+ *     in FP64);
  *   - i's outward-fit state, moved to o's innermost plane, agrees with o's
  *     inward-fit state in (y, sin phi, tan lambda, q/pT): 4-d chi2 with the
  *     sum of both covariances <= chi2_junction;
@@ -451,6 +455,7 @@ typedef struct {
     int32_t gap_max;      /* default 8                                        */
     double chi2_junction; /* default 30                                       */
     double z_membrane;    /* cm, default 3                                    */
+    double z_pre;         /* cm, default 10                                   */
     double chi2_joint;    /* default 40                                       */
     double t0_prior;      /* us, default 1                                    */
     double v_drift;       /* cm/us, default 2.58                              */

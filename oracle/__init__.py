@@ -51,7 +51,8 @@ class Diag(C.Structure):
 class SidesParams(C.Structure):
     """Parameters of the A/C-side association with t0 (orc_sides_params)."""
     _fields_ = [("n_min", C.c_int32), ("gap_max", C.c_int32), ("chi2_junction", C.c_double),
-                ("z_membrane", C.c_double), ("chi2_joint", C.c_double), ("t0_prior", C.c_double),
+                ("z_membrane", C.c_double), ("z_pre", C.c_double), ("chi2_joint", C.c_double),
+                ("t0_prior", C.c_double),
                 ("v_drift", C.c_double)]
 
 

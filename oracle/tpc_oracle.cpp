@@ -2154,6 +2154,7 @@ void orc_default_sides_params(orc_sides_params* p) {
     p->gap_max = 8;
     p->chi2_junction = 30.0;
     p->z_membrane = 3.0;
+    p->z_pre = 10.0;
     p->chi2_joint = 40.0;
     p->t0_prior = 1.0;
     p->v_drift = 2.58;
@@ -2174,6 +2175,10 @@ int orc_fit_t0(const float* y, const float* z, const uint16_t* row, const int32_
 //     or an adjacent phi sector at the junction (i's outermost cluster,
 //     o's innermost: a low-pT track may cross a sector border there too),
 //     1 <= row(o innermost) - row(i outermost) <= gap_max.
+//  2b. Coarse gate: the mean of the apparent z of i's outermost and o's
+//     innermost cluster lies within z_pre of the membrane (the true z near
+//     the junction; segments of different collisions are v |t0_a - t0_b|
+//     apart there).
 //  3. Junction: i's outward state moved to o's innermost plane; the 4-d
 //     chi2 of (y, sin phi, tan lambda, q/pT) against o's inward state with
 //     the sum of both covariances must be <= chi2_junction; with z'_i and
@@ -2270,6 +2275,11 @@ int64_t orc_match_sides(const float* y, const float* z, const uint16_t* row, int
             if (it == by_inner_end.end()) continue;
             for (int o : it->second) {
                 const SideTrack& b = st[o];
+                // coarse gate on the two end clusters' apparent z (their sum
+                // is exact in FP64): segments of different collisions lie
+                // v |t0_a - t0_b| apart there
+                const double zc = 0.5 * ((double)z[trk_hits[trk_off[i]]] + (double)z[trk_hits[trk_off[o + 1] - 1]]);
+                if (std::fabs(zc) > sp.z_pre) continue;
                 // the inner segment's outward state moved to o's innermost plane
                 double x = a.x_out, p[5], C[15], J[25], dX[5];
                 for (int k = 0; k < 5; ++k) p[k] = a.p_out[k];

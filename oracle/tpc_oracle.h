@@ -253,6 +253,8 @@ typedef struct {
                               outermost) <= gap_max                           */
     double chi2_junction;  /* 4-d (y, sin phi, tan lambda, q/pT) junction cut */
     double z_membrane;     /* |true z at the junction| cut (cm)               */
+    double z_pre;          /* coarse gate before any fit: |z'(i's outermost
+                              cluster) + z'(o's innermost)| / 2 <= z_pre (cm) */
     double chi2_joint;     /* cut on the joint fit's chi2 increase            */
     double t0_prior;       /* prior sigma of t0 in the joint fit (us)         */
     double v_drift;        /* drift velocity (cm/us)                          */

@@ -327,15 +327,17 @@ tpc_status tpc_fit_adjoint(tpc_ctx* c, const int32_t* trk_off, const int32_t* tr
 }
 
 static bool sides_prm(const tpc_sides_options* o, SidesPrm& S) {
-    S = SidesPrm{10, 8, 30.0, 3.0, 40.0, 1.0, 2.58};
+    S = SidesPrm{10, 8, 30.0, 3.0, 10.0, 40.0, 1.0, 2.58};
     if (!o) return true;
     if (o->n_min < 3 || o->n_min > NROW * 4 || o->gap_max < 1 || o->gap_max >= NROW ||
-        !(o->chi2_junction > 0.0) || !(o->z_membrane > 0.0) || !(o->chi2_joint > 0.0) ||
+        !(o->chi2_junction > 0.0) || !(o->z_membrane > 0.0) || !(o->z_pre > 0.0) || !std::isfinite(o->z_pre) ||
+        !(o->chi2_joint > 0.0) ||
         !(o->t0_prior > 0.0) || !(o->v_drift > 0.0) || !std::isfinite(o->chi2_junction) ||
         !std::isfinite(o->z_membrane) || !std::isfinite(o->chi2_joint) || !std::isfinite(o->t0_prior) ||
         !std::isfinite(o->v_drift))
         return false;
-    S = SidesPrm{o->n_min, o->gap_max, o->chi2_junction, o->z_membrane, o->chi2_joint, o->t0_prior, o->v_drift};
+    S = SidesPrm{o->n_min,      o->gap_max,    o->chi2_junction, o->z_membrane,
+                 o->z_pre,      o->chi2_joint, o->t0_prior,      o->v_drift};
     return true;
 }
 

@@ -53,8 +53,11 @@ struct AdjAccDevice {
     __device__ __forceinline__ void status(int code, int detail) { set_status(st, code, detail); }
 };
 
+constexpr int ADJ_T = 128;
+constexpr size_t ADJ_SEG_BYTES = sizeof(float) * CK * PRE_W * ADJ_T;
+
 template <bool FIELD>
-__global__ void __launch_bounds__(128) k_adjoint(
+__global__ void __launch_bounds__(ADJ_T) k_adjoint(
     const int32_t* __restrict__ trk_off, const int32_t* __restrict__ trk_hits, int32_t T,
     const float* __restrict__ yin, const float* __restrict__ zin, const uint16_t* __restrict__ row,
     const int64_t* __restrict__ evt_off, int G, const float* __restrict__ rot_tab,
@@ -64,21 +67,43 @@ __global__ void __launch_bounds__(128) k_adjoint(
     __shared__ double sg[216];
     __shared__ double schi2;
     __shared__ float tab[NSEC * ROT_TAB];
+    // the recomputed states of each thread's current segment, one column per
+    // thread (CK x PRE_W words x ADJ_T threads): the reverse sweep's working
+    // set stays on chip
+    extern __shared__ float seg_sh[];
     for (int i = threadIdx.x; i < NSEC * ROT_TAB; i += blockDim.x) tab[i] = rot_tab[i];
     for (int i = threadIdx.x; i < 216; i += blockDim.x) sg[i] = 0.0;
     if (threadIdx.x == 0) schi2 = 0.0;
     __syncthreads();
     AdjAccDevice acc{sg, &schi2, grad_field, st};
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x) {
-        const int b = trk_off[t];
-        adjoint_track<FIELD>(trk_hits + b, trk_off[t + 1] - b, yin, zin, row, evt_off, G, tab, geo, P, field,
-                             fg, acc);
+    // tracks handed out 32 at a time to whichever warp is free, so that the
+    // blocks finish together (a fixed grid stride leaves a third of the
+    // threads idle at the end when tracks per thread is not whole)
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(&st[ST_ADJ_NEXT], 32);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= T) break;
+        const int t = base + lane;
+        if (t < T) {
+            const int b = trk_off[t];
+            adjoint_track<FIELD>(trk_hits + b, trk_off[t + 1] - b, yin, zin, row, evt_off, G, tab, geo, P,
+                                 field, fg, seg_sh + threadIdx.x, ADJ_T, acc);
+        }
     }
     __syncthreads();
     if (P.want_grad && (!FIELD || grad != nullptr))
         for (int i = threadIdx.x; i < 216; i += blockDim.x)
             if (sg[i] != 0.0) atomicAdd(&grad[i], sg[i]);
     if (threadIdx.x == 0) atomicAdd(chi2_total, schi2);
+}
+
+template <bool FIELD>
+cudaError_t adjoint_smem_opt_in() {
+    static cudaError_t e = cudaFuncSetAttribute(k_adjoint<FIELD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)ADJ_SEG_BYTES);
+    return e;
 }
 
 __global__ void k_zero_f64(double* p, int n) {
@@ -99,7 +124,10 @@ cudaError_t run_adjoint(tpc_ctx* c, const int32_t* trk_off, const int32_t* trk_h
         float* rot_tab = c->ws.at<float>(c->ws.L.adj_rot);
         tpc::LaunchCount{}, k_adj_tables<<<1, 64, 0, s>>>(align, rot_tab);
         const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((n_tracks + 127) / 128, 152 * 4));
-        tpc::LaunchCount{}, k_adjoint<false><<<(unsigned)blocks, 128, 0, s>>>(trk_off, trk_hits, n_tracks, c->y, c->z, c->row,
+        cudaError_t e = adjoint_smem_opt_in<false>();
+        if (e == cudaSuccess) e = fill_i32(c->ws.at<int32_t>(c->ws.L.status) + ST_ADJ_NEXT, 1, 0, s);
+        if (e != cudaSuccess) return e;
+        tpc::LaunchCount{}, k_adjoint<false><<<(unsigned)blocks, ADJ_T, ADJ_SEG_BYTES, s>>>(trk_off, trk_hits, n_tracks, c->y, c->z, c->row,
                                                    c->evt_sector_off, c->n_events * NSEC, rot_tab,
                                                    c->ws.at<Geo>(c->ws.L.geo), ap, chi2_total, grad,
                                                    c->ws.at<int32_t>(c->ws.L.status),
@@ -126,7 +154,10 @@ cudaError_t run_adjoint_field(tpc_ctx* c, const int32_t* trk_off, const int32_t*
         float* rot_tab = c->ws.at<float>(c->ws.L.adj_rot);
         tpc::LaunchCount{}, k_adj_tables<<<1, 64, 0, s>>>(align, rot_tab);
         const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((n_tracks + 127) / 128, 152 * 4));
-        tpc::LaunchCount{}, k_adjoint<true><<<(unsigned)blocks, 128, 0, s>>>(
+        cudaError_t e = adjoint_smem_opt_in<true>();
+        if (e == cudaSuccess) e = fill_i32(c->ws.at<int32_t>(c->ws.L.status) + ST_ADJ_NEXT, 1, 0, s);
+        if (e != cudaSuccess) return e;
+        tpc::LaunchCount{}, k_adjoint<true><<<(unsigned)blocks, ADJ_T, ADJ_SEG_BYTES, s>>>(
             trk_off, trk_hits, n_tracks, c->y, c->z, c->row, c->evt_sector_off, c->n_events * NSEC,
             rot_tab, c->ws.at<Geo>(c->ws.L.geo), ap, chi2_total, grad_align,
             c->ws.at<int32_t>(c->ws.L.status), field, fg, grad_field);

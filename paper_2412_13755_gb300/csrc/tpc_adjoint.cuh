@@ -11,8 +11,8 @@ namespace tpc {
 
 namespace {
 
-constexpr int CK = 16;      // clusters per checkpoint segment
-constexpr int NSLOT = 8;    // sectors a track may touch
+constexpr int CK = 8;       // clusters per checkpoint segment
+constexpr int PRE_W = 23;   // words of a recomputed state in the segment store: p[5], lo[3], C[15]
 constexpr int ND = 6;       // tangent directions: y, s, t, w, x_from, x_to
 
 struct D6 {
@@ -317,12 +317,17 @@ TPC_HD void flush_field(Acc& acc, int v, double f[3]) {
 // i = 6 sector + k), the voxel gradients (acc.field(i, v) when
 // acc.want_field()) and capacity errors (acc.status).  tab holds the
 // per-sector rotation tables.
+// seg: the store of one segment's recomputed states, CK x PRE_W words, word
+// w of entry k at seg[(k PRE_W + w) seg_stride] (the kernel gives each
+// thread a column of shared memory, stride = threads per block; a host
+// program a plain array, stride 1).
 template <bool FIELD, class Acc>
 TPC_HD void adjoint_track(const int32_t* h, int n, const float* __restrict__ yin,
                           const float* __restrict__ zin, const uint16_t* __restrict__ row,
                           const int64_t* __restrict__ evt_off, int G, const float* tab,
                           const Geo* __restrict__ geo, const AdjPrm& P,
-                          const double* __restrict__ field, const FieldGridD& fg, Acc& acc) {
+                          const double* __restrict__ field, const FieldGridD& fg, float* seg, int seg_stride,
+                          Acc& acc) {
     if (n < 3) return;
     // seed from the uncorrected clusters
     KF s;
@@ -350,7 +355,7 @@ TPC_HD void adjoint_track(const int32_t* h, int n, const float* __restrict__ yin
     int gcur = -1;
     int64_t gb = 0, ge = 0;
     for (int j = 0; j < n && ok; ++j) {
-        if (j % CK == 0) {
+        if (P.want_grad && j % CK == 0) {  // checkpoints only for the reverse sweep
             Pre& q = ck[j / CK];
             q.x = s.x; q.frame = s.frame;
             for (int i = 0; i < 5; ++i) q.p[i] = s.p[i];
@@ -380,13 +385,15 @@ TPC_HD void adjoint_track(const int32_t* h, int n, const float* __restrict__ yin
     float pb[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
     float A[15];
     for (int i = 0; i < 15; ++i) A[i] = 0.f;
-    int slot_sec[NSLOT];
-    double slot_g[NSLOT][6];
-    int nslot = 0;
+    // the alignment gradient of the run of consecutive clusters in one
+    // sector, flushed when the sector changes
+    int gsec = -1;
+    double gacc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     float xbar_from_next = 0.f;  // x_from adjoint of the step after the current one
     int vcur = -1;               // voxel of the run of clusters being summed
     double facc[3] = {0.0, 0.0, 0.0};
-    Pre seg[CK];
+    double segx[CK];
+    int segf[CK];
     for (int k = nck - 1; k >= 0; --k) {
         const int j0 = k * CK, j1 = min(n, j0 + CK);
         // recompute the segment's pre-transport states
@@ -396,11 +403,14 @@ TPC_HD void adjoint_track(const int32_t* h, int n, const float* __restrict__ yin
         for (int i = 0; i < 3; ++i) r.lo[i] = ck[k].lo[i];
         for (int i = 0; i < 15; ++i) r.C[i] = ck[k].C[i];
         for (int j = j0; j < j1; ++j) {
-            Pre& q = seg[j - j0];
-            q.x = r.x; q.frame = r.frame;
-            for (int i = 0; i < 5; ++i) q.p[i] = r.p[i];
-            for (int i = 0; i < 3; ++i) q.lo[i] = r.lo[i];
-            for (int i = 0; i < 15; ++i) q.C[i] = r.C[i];
+            {
+                float* o = seg + (size_t)(j - j0) * PRE_W * seg_stride;
+                for (int i = 0; i < 5; ++i) o[i * seg_stride] = r.p[i];
+                for (int i = 0; i < 3; ++i) o[(5 + i) * seg_stride] = r.lo[i];
+                for (int i = 0; i < 15; ++i) o[(8 + i) * seg_stride] = r.C[i];
+                segx[j - j0] = r.x;
+                segf[j - j0] = r.frame;
+            }
             const int c = h[j];
             if (c < gb || c >= ge) {
                 gcur = group_of(evt_off, G, c);
@@ -417,7 +427,15 @@ TPC_HD void adjoint_track(const int32_t* h, int n, const float* __restrict__ yin
             kf_update(r, yc, zc, P.sy2, P.sz2, P.fp64_ratio, P.fp64_det, nullptr, &mj);
         }
         for (int j = j1 - 1; j >= j0; --j) {
-            const Pre& q = seg[j - j0];
+            Pre q;
+            {
+                const float* o = seg + (size_t)(j - j0) * PRE_W * seg_stride;
+                for (int i = 0; i < 5; ++i) q.p[i] = o[i * seg_stride];
+                for (int i = 0; i < 3; ++i) q.lo[i] = o[(5 + i) * seg_stride];
+                for (int i = 0; i < 15; ++i) q.C[i] = o[(8 + i) * seg_stride];
+                q.x = segx[j - j0];
+                q.frame = segf[j - j0];
+            }
             const int c = h[j];
             if (c < gb || c >= ge) {
                 gcur = group_of(evt_off, G, c);
@@ -598,26 +616,18 @@ TPC_HD void adjoint_track(const int32_t* h, int n, const float* __restrict__ yin
             xbar_from_next = xbar_from;
             float gr[3];
             rot_grad_tab(tb, (float)xr, yin[c], zin[c], (float)xb, ybar, zbar, gr);
-            int sl = 0;
-            while (sl < nslot && slot_sec[sl] != sec) ++sl;
-            if (sl == nslot) {
-                if (nslot == NSLOT) {
-                    acc.status(TPC_ERR_CAPACITY, 6);
-                    sl = -1;
-                } else {
-                    slot_sec[sl] = sec;
-                    for (int i = 0; i < 6; ++i) slot_g[sl][i] = 0.0;
-                    ++nslot;
-                }
+            if (sec != gsec) {
+                if (gsec >= 0)
+                    for (int i = 0; i < 6; ++i) acc.align(gsec * 6 + i, gacc[i]);
+                gsec = sec;
+                for (int i = 0; i < 6; ++i) gacc[i] = 0.0;
             }
-            if (sl >= 0) {
-                slot_g[sl][0] += xb;
-                slot_g[sl][1] += ybar;
-                slot_g[sl][2] += zbar;
-                slot_g[sl][3] += gr[0];
-                slot_g[sl][4] += gr[1];
-                slot_g[sl][5] += gr[2];
-            }
+            gacc[0] += xb;
+            gacc[1] += ybar;
+            gacc[2] += zbar;
+            gacc[3] += gr[0];
+            gacc[4] += gr[1];
+            gacc[5] += gr[2];
             if constexpr (FIELD) {
                 if (acc.want_field()) {
                     if (vox != vcur) {
@@ -634,8 +644,8 @@ TPC_HD void adjoint_track(const int32_t* h, int n, const float* __restrict__ yin
     if constexpr (FIELD) {
         if (acc.want_field()) flush_field(acc, vcur, facc);
     }
-    for (int sl = 0; sl < nslot; ++sl)
-        for (int i = 0; i < 6; ++i) acc.align(slot_sec[sl] * 6 + i, slot_g[sl][i]);
+    if (gsec >= 0)
+        for (int i = 0; i < 6; ++i) acc.align(gsec * 6 + i, gacc[i]);
 }
 
 }  // namespace

@@ -73,7 +73,8 @@ enum StatusSlot {
     ST_MATCH_LIVE, ST_Q_BUILD, ST_Q_REFIT, ST_NB_Q3, ST_KFSTEPS = 12 /* 64-bit: slots 12-13 */,
     ST_NB_OVF = 14, ST_NB_Q2 = 15,
     ST_INPUT_BAD = 16,  // nonzero when the last validated batch was rejected
-    ST_N_SLOTS = 17
+    ST_ADJ_NEXT = 17,   // the adjoint's work cursor (next track to hand out)
+    ST_N_SLOTS = 18
 };
 
 // Workspace layout: byte offsets of every buffer, computed from capacities.

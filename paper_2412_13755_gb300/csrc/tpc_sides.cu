@@ -38,6 +38,7 @@ struct SideCls {
     int32_t r_in, r_out;
     int32_t key_in;  // bucket of the innermost cluster, -1: not usable
     int32_t info;    // bit 1: side C of the outermost cluster's sector; bits 2..: event
+    float z_in, z_out;  // apparent z of the innermost and outermost cluster
 };
 
 struct SideCand {
@@ -80,7 +81,7 @@ __global__ void __launch_bounds__(SIDES_T) k_sides_class(
         dchi2[t] = 0.0;
         need[t] = 0;
         best[t] = ~0ull;
-        SideCls c{0, 0, -1, 0};
+        SideCls c{0, 0, -1, 0, 0.f, 0.f};
         const int b = trk_off[t], m = trk_off[t + 1] - b;
         if (!rejected && m >= max(3, S.n_min)) {
             const int g0 = group_of(H.evt_off, H.G, trk_hits[b]);
@@ -96,6 +97,8 @@ __global__ void __launch_bounds__(SIDES_T) k_sides_class(
                 c.r_in = H.row[trk_hits[b + m - 1]];
                 c.key_in = bucket_key(ev, gl % NSEC, c.r_in);
                 c.info = (side0 << 1) | (ev << 2);
+                c.z_out = H.z[trk_hits[b]];
+                c.z_in = H.z[trk_hits[b + m - 1]];
                 atomicAdd(&bcnt[c.key_in], 1);
             }
         }
@@ -116,11 +119,13 @@ __global__ void __launch_bounds__(SIDES_T) k_sides_scatter(int32_t n_tracks, con
 
 // The buckets of the outer candidates of inner track t: same event, the
 // other side, the same or an adjacent phi sector of its outermost cluster,
-// rows r_out + 1 .. r_out + gap_max.  f(o) for every track o listed there.
+// rows r_out + 1 .. r_out + gap_max; f(o) for every track o listed there
+// whose innermost cluster passes the coarse z gate with t's outermost (the
+// mean apparent z within z_pre of the membrane; exact in FP64).
 template <class F>
 __device__ __forceinline__ void for_outer(const SideCls& a, int sec_out, const SidesPrm& S,
-                                          const int32_t* __restrict__ boff, const int32_t* __restrict__ blist,
-                                          F f) {
+                                          const SideCls* __restrict__ cls, const int32_t* __restrict__ boff,
+                                          const int32_t* __restrict__ blist, F f) {
     const int ev = a.info >> 2;
     const int other = (sec_out >= NPHI) ? 0 : NPHI;
     for (int dp = -1; dp <= 1; ++dp) {
@@ -129,7 +134,10 @@ __device__ __forceinline__ void for_outer(const SideCls& a, int sec_out, const S
             const int r = a.r_out + gap;
             if (r >= NROW) break;
             const int k = bucket_key(ev, other + ph, r);
-            for (int q = boff[k]; q < boff[k + 1]; ++q) f(blist[q]);
+            for (int q = boff[k]; q < boff[k + 1]; ++q) {
+                const int o = blist[q];
+                if (fabs(0.5 * ((double)a.z_out + (double)cls[o].z_in)) <= S.z_pre) f(o);
+            }
         }
     }
 }
@@ -146,7 +154,7 @@ __global__ void __launch_bounds__(SIDES_T) k_sides_need(const int32_t* __restric
         if (a.key_in < 0) continue;
         const int sec_out = sector_of(H, trk_hits[trk_off[t]]);
         bool any = false;
-        for_outer(a, sec_out, S, boff, blist, [&](int o) {
+        for_outer(a, sec_out, S, cls, boff, blist, [&](int o) {
             if (o != t) {
                 need[o] = 1;
                 any = true;
@@ -201,7 +209,7 @@ __global__ void __launch_bounds__(SIDES_T) k_sides_pairs(const int32_t* __restri
         if (a.key_in < 0 || !ends[t].ok) continue;
         const int sec_out = sector_of(H, trk_hits[trk_off[t]]);
         const int sgn_i = side_sgn(sec_out);
-        for_outer(a, sec_out, S, boff, blist, [&](int o) {
+        for_outer(a, sec_out, S, cls, boff, blist, [&](int o) {
             if (o == t || !ends[o].ok) return;
             double c4, zmem, t0s;
             if (!junction(ends[t], sgn_i, ends[o], geo, P, S, c4, zmem, t0s)) return;

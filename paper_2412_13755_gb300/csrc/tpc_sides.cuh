@@ -17,7 +17,7 @@ namespace tpc {
 
 struct SidesPrm {
     int n_min, gap_max;
-    double chi2_junction, z_membrane, chi2_joint, t0_prior, v_drift;
+    double chi2_junction, z_membrane, z_pre, chi2_joint, t0_prior, v_drift;
 };
 
 // Packed symmetric 6x6, upper triangle row by row:

@@ -62,15 +62,15 @@ def fit_options(mat_x_x0=0.0, mat_eloss=0.0, mass=0.13957, outward=False) -> Fit
 class SidesOptions(C.Structure):
     """Options of the A/C-side association with t0 (tpc_sides_options)."""
     _fields_ = [("n_min", C.c_int32), ("gap_max", C.c_int32), ("chi2_junction", C.c_double),
-                ("z_membrane", C.c_double), ("chi2_joint", C.c_double), ("t0_prior", C.c_double),
-                ("v_drift", C.c_double)]
+                ("z_membrane", C.c_double), ("z_pre", C.c_double), ("chi2_joint", C.c_double),
+                ("t0_prior", C.c_double), ("v_drift", C.c_double)]
 
 
-def sides_options(n_min=10, gap_max=8, chi2_junction=30.0, z_membrane=3.0, chi2_joint=40.0, t0_prior=1.0,
-                  v_drift=2.58) -> SidesOptions:
+def sides_options(n_min=10, gap_max=8, chi2_junction=30.0, z_membrane=3.0, z_pre=10.0, chi2_joint=40.0,
+                  t0_prior=1.0, v_drift=2.58) -> SidesOptions:
     """The library's defaults unless overridden."""
-    return SidesOptions(int(n_min), int(gap_max), float(chi2_junction), float(z_membrane), float(chi2_joint),
-                        float(t0_prior), float(v_drift))
+    return SidesOptions(int(n_min), int(gap_max), float(chi2_junction), float(z_membrane), float(z_pre),
+                        float(chi2_joint), float(t0_prior), float(v_drift))
 
 
 class BatchOutputs(C.Structure):

@@ -85,14 +85,15 @@ int main(int argc, char** argv) {
     HostAcc acc;
     acc.field_on = gi[0] != 0;
     acc.fl.assign(3 * nv, 0.0);
+    std::vector<float> seg(CK * PRE_W);
     for (int64_t t = 0; t < T; ++t) {
         const int b = toff[t], m = toff[t + 1] - b;
         if (gi[0])
             adjoint_track<true>(hits.data() + b, m, y.data(), z.data(), row.data(), off.data(), (int)G,
-                                tab.data(), &geo, P, field.data(), fg, acc);
+                                tab.data(), &geo, P, field.data(), fg, seg.data(), 1, acc);
         else
             adjoint_track<false>(hits.data() + b, m, y.data(), z.data(), row.data(), off.data(), (int)G,
-                                 tab.data(), &geo, P, nullptr, fg, acc);
+                                 tab.data(), &geo, P, nullptr, fg, seg.data(), 1, acc);
     }
     FILE* o = fopen(argv[2], "wb");
     if (!o) return 2;

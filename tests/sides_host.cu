@@ -77,7 +77,7 @@ int main(int argc, char** argv) {
     P.eloss = 0.0;
     P.mass = 0.13957;
     P.outward = false;
-    SidesPrm S{10, 8, 30.0, 3.0, 40.0, sd[0], sd[1]};
+    SidesPrm S{10, 8, 30.0, 3.0, 10.0, 40.0, sd[0], sd[1]};
     const Geo geo = make_geo();
     const HitSrc H{y.data(), z.data(), row.data(), off.data(), (int)G};
     FILE* o = fopen(argv[2], "wb");
