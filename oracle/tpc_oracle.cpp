@@ -2125,7 +2125,8 @@ bool fit_t0(const float* y, const float* z, const uint16_t* row, const int32_t* 
 
 // One found track as seen by the association.
 struct SideTrack {
-    bool usable = false;  // one side, >= n_min clusters, both fits done
+    bool usable = false;  // one side, >= n_min clusters, inward fit done (the outer role)
+    bool out_ok = false;  // outward fit done too (the inner role)
     int event = 0, sgn = 0;
     int r_in = 0, r_out = 0;   // rows of the innermost and outermost clusters
     int s_in = 0, s_out = 0;   // their sectors
@@ -2170,7 +2171,8 @@ int orc_fit_t0(const float* y, const float* z, const uint16_t* row, const int32_
 //  1. Per found track: usable when all its clusters lie on one side and it
 //     has >= n_min of them; the inward fit gives the state at its innermost
 //     cluster and the segment's chi2, the outward fit the state at its
-//     outermost cluster.
+//     outermost cluster.  The outer role needs the inward fit, the inner
+//     role both.
 //  2. Candidates (i inner, o outer): one event, opposite sides, the same
 //     or an adjacent phi sector at the junction (i's outermost cluster,
 //     o's innermost: a low-pT track may cross a sector border there too),
@@ -2243,12 +2245,13 @@ int64_t orc_match_sides(const float* y, const float* z, const uint16_t* row, int
         double xl = 0;
         if (!kf_fit<double>(y, z, row, sec.data(), h, m, true, prm, th, s.p_in, s.C_in, s.chi2_in, &xl)) continue;
         s.x_in = xl;
+        s.usable = true;
         std::vector<int32_t> rev(h, h + m);
         std::reverse(rev.begin(), rev.end());
         double c2o;
         if (!kf_fit<double>(y, z, row, sec.data(), rev.data(), m, false, prm, th, s.p_out, s.C_out, c2o, &xl)) continue;
         s.x_out = xl;
-        s.usable = true;
+        s.out_ok = true;
     }
     // 2-3. candidates, bucketed by (event, side, phi sector, row) of the
     // outer segment's innermost cluster
@@ -2264,7 +2267,7 @@ int64_t orc_match_sides(const float* y, const float* z, const uint16_t* row, int
 #pragma omp parallel for schedule(dynamic, 16) num_threads(nt)
     for (int i = 0; i < T; ++i) {
         const SideTrack& a = st[i];
-        if (!a.usable) continue;
+        if (!a.usable || !a.out_ok) continue;
         for (int dp = -1; dp <= 1; ++dp)
         for (int gap = 1; gap <= sp.gap_max; ++gap) {
             const int r = a.r_out + gap;

@@ -161,7 +161,7 @@ cudaError_t run_adjoint_field(tpc_ctx* c, const int32_t* trk_off, const int32_t*
 struct SidesPrm;
 struct SidesLayout {
     int64_t K;  // buckets: events x 2 sides x 18 phi sectors x 152 rows
-    size_t ends, cls, need, best, blist, bcnt, boff, bfill, scan, cand, counters, total;
+    size_t ends, cls, need, role, need_off, list, scan_t, best, blist, bcnt, boff, bfill, scan, cand, counters, total;
 };
 SidesLayout sides_layout(int64_t max_tracks, int32_t n_events, int64_t cand_cap);
 cudaError_t run_match_sides(tpc_ctx* c, const int32_t* trk_off, const int32_t* trk_hits, int32_t n_tracks,

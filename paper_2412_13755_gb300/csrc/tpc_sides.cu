@@ -45,6 +45,7 @@ struct SideCand {
     int32_t i, o;  // inner and outer track
     double t0s;    // t0 from the junction states
     double dchi2;  // chi2 increase of the joint fit (infinity: rejected)
+    double q[6], C[21], chi2;  // the joint fit
 };
 
 __host__ __device__ inline int bucket_key(int event, int sector, int r) {
@@ -66,12 +67,17 @@ __device__ __forceinline__ int n_eff(int32_t n_tracks, const int32_t* n_tracks_d
 
 __global__ void __launch_bounds__(SIDES_T) k_sides_class(
     const int32_t* __restrict__ trk_off, const int32_t* __restrict__ trk_hits, int32_t n_tracks,
-    const int32_t* __restrict__ n_tracks_dev, HitSrc H, SidesPrm S, SideCls* cls, int32_t* need,
+    const int32_t* __restrict__ n_tracks_dev, HitSrc H, SidesPrm S, SideCls* cls, int32_t* need, int32_t* role,
     unsigned long long* best, int32_t* bcnt, int32_t* partner, double* t0, double* params6, double* cov6,
     double* chi2, int32_t* ndf, double* dchi2, const int32_t* __restrict__ st) {
     const bool rejected = input_rejected(st);
     const int T = n_eff(n_tracks, n_tracks_dev);
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n_tracks; t += gridDim.x * blockDim.x) {
+        if (t >= T) {  // beyond the device count: only the flag the scan reads
+            need[t] = 0;
+            continue;
+        }
+        role[t] = 0;
         partner[t] = -1;
         t0[t] = 0.0;
         for (int k = 0; k < 6; ++k) params6[(int64_t)t * 6 + k] = 0.0;
@@ -147,7 +153,8 @@ __global__ void __launch_bounds__(SIDES_T) k_sides_need(const int32_t* __restric
                                                        const int32_t* __restrict__ n_tracks_dev, HitSrc H, SidesPrm S,
                                                        const SideCls* __restrict__ cls,
                                                        const int32_t* __restrict__ boff,
-                                                       const int32_t* __restrict__ blist, int32_t* need) {
+                                                       const int32_t* __restrict__ blist, int32_t* need,
+                                                       int32_t* role) {
     const int T = n_eff(n_tracks, n_tracks_dev);
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x) {
         const SideCls a = cls[t];
@@ -157,23 +164,43 @@ __global__ void __launch_bounds__(SIDES_T) k_sides_need(const int32_t* __restric
         for_outer(a, sec_out, S, cls, boff, blist, [&](int o) {
             if (o != t) {
                 need[o] = 1;
+                atomicOr(&role[o], 1);  // the outer role: the inward fit
                 any = true;
             }
         });
-        if (any) need[t] = 1;
+        if (any) {
+            need[t] = 1;
+            atomicOr(&role[t], 3);  // the inner role: both fits
+        }
     }
 }
 
-__global__ void __launch_bounds__(SIDES_T) k_sides_fit(const int32_t* __restrict__ trk_off,
-                                                      const int32_t* __restrict__ trk_hits, int32_t n_tracks,
-                                                      const int32_t* __restrict__ n_tracks_dev, HitSrc H,
-                                                      const Geo* __restrict__ geo, ExPrm P,
-                                                      const int32_t* __restrict__ need, SideEnd* ends) {
+// The needed tracks as a dense list (need_off: exclusive scan of need), so
+// that the FP64 fits and junction tests run on full warps.
+__global__ void __launch_bounds__(SIDES_T) k_sides_compact(int32_t n_tracks, const int32_t* __restrict__ n_tracks_dev,
+                                                          const int32_t* __restrict__ need,
+                                                          const int32_t* __restrict__ need_off, int32_t* list,
+                                                          SideEnd* ends) {
     const int T = n_eff(n_tracks, n_tracks_dev);
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x) {
+        ends[t].ok = 0;
+        if (need[t]) list[need_off[t]] = t;
+    }
+}
+
+// The fits each listed track's roles need: the inward fit (state at the
+// innermost cluster, the segment's chi2) always, the outward fit (state at
+// the outermost cluster) for the inner role.
+__global__ void __launch_bounds__(SIDES_T) k_sides_fit(const int32_t* __restrict__ trk_off,
+                                                      const int32_t* __restrict__ trk_hits, HitSrc H,
+                                                      const Geo* __restrict__ geo, ExPrm P,
+                                                      const int32_t* __restrict__ list,
+                                                      const int32_t* __restrict__ n_list,
+                                                      const int32_t* __restrict__ role, SideEnd* ends) {
+    const int N = *n_list;
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < N; u += gridDim.x * blockDim.x) {
+        const int t = list[u];
         SideEnd& e = ends[t];
-        e.ok = 0;
-        if (!need[t]) continue;
         const int b = trk_off[t], m = trk_off[t + 1] - b;
         KFD s;
         double c2;
@@ -184,39 +211,48 @@ __global__ void __launch_bounds__(SIDES_T) k_sides_fit(const int32_t* __restrict
         e.x_in = s.x;
         e.s_in = s.frame;
         e.chi2_in = c2;
-        P.outward = true;
-        if (!fit_ex(trk_hits + b, m, H, geo, P, s, c2, nullptr)) continue;
-        for (int k = 0; k < 5; ++k) e.p_out[k] = s.p[k] + (k < 3 ? s.lo[k] : 0.0);
-        for (int k = 0; k < 15; ++k) e.C_out[k] = s.C[k];
-        e.x_out = s.x;
-        e.s_out = s.frame;
-        e.ok = 1;
+        int ok = 1;
+        if (role[t] & 2) {
+            P.outward = true;
+            if (fit_ex(trk_hits + b, m, H, geo, P, s, c2, nullptr)) {
+                for (int k = 0; k < 5; ++k) e.p_out[k] = s.p[k] + (k < 3 ? s.lo[k] : 0.0);
+                for (int k = 0; k < 15; ++k) e.C_out[k] = s.C[k];
+                e.x_out = s.x;
+                e.s_out = s.frame;
+                ok |= 2;
+            }
+        }
+        e.ok = ok;
     }
 }
 
 __global__ void __launch_bounds__(SIDES_T) k_sides_pairs(const int32_t* __restrict__ trk_off,
-                                                        const int32_t* __restrict__ trk_hits, int32_t n_tracks,
-                                                        const int32_t* __restrict__ n_tracks_dev, HitSrc H,
+                                                        const int32_t* __restrict__ trk_hits, HitSrc H,
                                                         const Geo* __restrict__ geo, ExPrm P, SidesPrm S,
                                                         const SideCls* __restrict__ cls,
                                                         const int32_t* __restrict__ boff,
                                                         const int32_t* __restrict__ blist,
+                                                        const int32_t* __restrict__ list,
+                                                        const int32_t* __restrict__ n_list,
                                                         const SideEnd* __restrict__ ends, SideCand* cand,
                                                         int32_t cap, int32_t* n_cand, int32_t* st) {
-    const int T = n_eff(n_tracks, n_tracks_dev);
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x) {
+    const int N = *n_list;
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < N; u += gridDim.x * blockDim.x) {
+        const int t = list[u];
         const SideCls a = cls[t];
-        if (a.key_in < 0 || !ends[t].ok) continue;
+        if (a.key_in < 0 || ends[t].ok != 3) continue;
         const int sec_out = sector_of(H, trk_hits[trk_off[t]]);
         const int sgn_i = side_sgn(sec_out);
         for_outer(a, sec_out, S, cls, boff, blist, [&](int o) {
-            if (o == t || !ends[o].ok) return;
+            if (o == t || !(ends[o].ok & 1)) return;
             double c4, zmem, t0s;
             if (!junction(ends[t], sgn_i, ends[o], geo, P, S, c4, zmem, t0s)) return;
             if (c4 > S.chi2_junction || fabs(zmem) > S.z_membrane) return;
             const int k = atomicAdd(n_cand, 1);
             if (k < cap) {
-                cand[k] = SideCand{t, o, t0s, 0.0};
+                cand[k].i = t;
+                cand[k].o = o;
+                cand[k].t0s = t0s;
             } else {
                 set_status(st, TPC_ERR_CAPACITY, 301);
             }
@@ -232,16 +268,15 @@ __global__ void __launch_bounds__(SIDES_T) k_sides_joint(const int32_t* __restri
                                                         unsigned long long* best) {
     const int N = min(*n_cand, cap);
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
-        SideCand c = cand[k];
+        SideCand& c = cand[k];
         const int bi = trk_off[c.i], ni = trk_off[c.i + 1] - bi;
         const int bo = trk_off[c.o], no = trk_off[c.o + 1] - bo;
-        double q[6], C[21], chi2;
         double d = INFINITY;
-        if (fit_t0(trk_hits + bo, no, trk_hits + bi, ni, c.t0s, H, geo, P, S, q, C, chi2)) {
-            d = chi2 - ends[c.i].chi2_in - ends[c.o].chi2_in;
+        if (fit_t0(trk_hits + bo, no, trk_hits + bi, ni, c.t0s, H, geo, P, S, c.q, c.C, c.chi2)) {
+            d = c.chi2 - ends[c.i].chi2_in - ends[c.o].chi2_in;
             if (!(d <= S.chi2_joint)) d = INFINITY;
         }
-        cand[k].dchi2 = d;
+        c.dchi2 = d;
         if (d != INFINITY) {
             atomicMin(&best[c.i], cand_key(d, c.o));
             atomicMin(&best[c.o], cand_key(d, c.i));
@@ -260,13 +295,14 @@ __global__ void __launch_bounds__(SIDES_T) k_sides_pick(const int32_t* __restric
                                                        int32_t* n_pairs) {
     const int N = min(*n_cand, cap);
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
-        const SideCand c = cand[k];
+        const SideCand& c = cand[k];
         if (c.dchi2 == INFINITY) continue;
         if (best[c.i] != cand_key(c.dchi2, c.o) || best[c.o] != cand_key(c.dchi2, c.i)) continue;
-        const int bi = trk_off[c.i], ni = trk_off[c.i + 1] - bi;
-        const int bo = trk_off[c.o], no = trk_off[c.o + 1] - bo;
-        double q[6], C[21], chi2;
-        if (!fit_t0(trk_hits + bo, no, trk_hits + bi, ni, c.t0s, H, geo, P, S, q, C, chi2)) continue;
+        const int ni = trk_off[c.i + 1] - trk_off[c.i];
+        const int no = trk_off[c.o + 1] - trk_off[c.o];
+        const double* q = c.q;
+        const double* C = c.C;
+        const double chi2 = c.chi2;
         atomicAdd(n_pairs, 1);
         const int mem[2] = {c.i, c.o};
         for (int u = 0; u < 2; ++u) {
@@ -296,6 +332,10 @@ SidesLayout sides_layout(int64_t max_tracks, int32_t n_events, int64_t cand_cap)
     L.ends = take(sizeof(SideEnd) * (size_t)max_tracks);
     L.cls = take(sizeof(SideCls) * (size_t)max_tracks);
     L.need = take(4 * (size_t)max_tracks);
+    L.role = take(4 * (size_t)max_tracks);
+    L.need_off = take(4 * (size_t)(max_tracks + 1));
+    L.list = take(4 * (size_t)max_tracks);
+    L.scan_t = take(4 * (size_t)(max_tracks / 4096 + 64));
     L.best = take(8 * (size_t)max_tracks);
     L.blist = take(4 * (size_t)max_tracks);
     L.bcnt = take(4 * (size_t)L.K);
@@ -332,6 +372,10 @@ cudaError_t run_match_sides(tpc_ctx* c, const int32_t* trk_off, const int32_t* t
     auto* ends = reinterpret_cast<SideEnd*>(ws + L.ends);
     auto* cls = reinterpret_cast<SideCls*>(ws + L.cls);
     auto* need = reinterpret_cast<int32_t*>(ws + L.need);
+    auto* role = reinterpret_cast<int32_t*>(ws + L.role);
+    auto* need_off = reinterpret_cast<int32_t*>(ws + L.need_off);
+    auto* list = reinterpret_cast<int32_t*>(ws + L.list);
+    auto* scan_t = reinterpret_cast<int32_t*>(ws + L.scan_t);
     auto* best = reinterpret_cast<unsigned long long*>(ws + L.best);
     auto* blist = reinterpret_cast<int32_t*>(ws + L.blist);
     auto* bcnt = reinterpret_cast<int32_t*>(ws + L.bcnt);
@@ -352,7 +396,7 @@ cudaError_t run_match_sides(tpc_ctx* c, const int32_t* trk_off, const int32_t* t
     if (e != cudaSuccess) return e;
     if (n_tracks > 0) {
         tpc::LaunchCount{}, k_sides_class<<<(unsigned)blocks, SIDES_T, 0, s>>>(
-            trk_off, trk_hits, n_tracks, n_tracks_dev, H, S, cls, need, best, bcnt, partner, t0, params6, cov6,
+            trk_off, trk_hits, n_tracks, n_tracks_dev, H, S, cls, need, role, best, bcnt, partner, t0, params6, cov6,
             chi2, ndf, dchi2, st);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = scan_i32(bcnt, boff, L.K, scan, s);
@@ -360,12 +404,18 @@ cudaError_t run_match_sides(tpc_ctx* c, const int32_t* trk_off, const int32_t* t
             tpc::LaunchCount{}, k_sides_scatter<<<(unsigned)blocks, SIDES_T, 0, s>>>(n_tracks, n_tracks_dev, cls,
                                                                                  boff, bfill, blist);
             tpc::LaunchCount{}, k_sides_need<<<(unsigned)blocks, SIDES_T, 0, s>>>(
-                trk_off, trk_hits, n_tracks, n_tracks_dev, H, S, cls, boff, blist, need);
-            tpc::LaunchCount{}, k_sides_fit<<<(unsigned)blocks, SIDES_T, 0, s>>>(trk_off, trk_hits, n_tracks,
-                                                                             n_tracks_dev, H, geo, P, need, ends);
+                trk_off, trk_hits, n_tracks, n_tracks_dev, H, S, cls, boff, blist, need, role);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = scan_i32(need, need_off, n_tracks, scan_t, s);
+        if (e == cudaSuccess) {
+            const int32_t* n_list = need_off + n_tracks;
+            tpc::LaunchCount{}, k_sides_compact<<<(unsigned)blocks, SIDES_T, 0, s>>>(n_tracks, n_tracks_dev, need,
+                                                                                 need_off, list, ends);
+            tpc::LaunchCount{}, k_sides_fit<<<(unsigned)blocks, SIDES_T, 0, s>>>(trk_off, trk_hits, H, geo, P, list,
+                                                                             n_list, role, ends);
             tpc::LaunchCount{}, k_sides_pairs<<<(unsigned)blocks, SIDES_T, 0, s>>>(
-                trk_off, trk_hits, n_tracks, n_tracks_dev, H, geo, P, S, cls, boff, blist, ends, cand, cand_cap,
-                n_cand, st);
+                trk_off, trk_hits, H, geo, P, S, cls, boff, blist, list, n_list, ends, cand, cand_cap, n_cand, st);
             tpc::LaunchCount{}, k_sides_joint<<<(unsigned)cblocks, SIDES_T, 0, s>>>(
                 trk_off, trk_hits, H, geo, P, S, ends, cand, cand_cap, n_cand, best);
             tpc::LaunchCount{}, k_sides_pick<<<(unsigned)cblocks, SIDES_T, 0, s>>>(

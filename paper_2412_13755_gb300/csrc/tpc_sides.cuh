@@ -37,7 +37,7 @@ struct SideEnd {
     double p_in[5], C_in[15], x_in, chi2_in;  // inward fit: state at the innermost cluster
     double p_out[5], C_out[15], x_out;        // outward fit: state at the outermost cluster
     int32_t s_in, s_out;                      // sectors of those clusters
-    int32_t ok;                               // both fits done
+    int32_t ok;                               // bit 0: inward fit done; bit 1: outward fit done
 };
 
 // Kalman update of the six-parameter state with one cluster, a = -sgn v:
