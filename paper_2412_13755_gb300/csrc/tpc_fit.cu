@@ -64,9 +64,13 @@ cudaError_t run_fit(tpc_ctx* c, const int32_t* trk_off, const int32_t* trk_hits,
     fp.seed_snp = p.seed_snp_max;
     fp.seed_qpt = p.seed_qpt_max;
     for (int i = 0; i < 5; ++i) fp.prior[i] = p.prior[i];
-    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((n_tracks + 127) / 128, 152 * 32));
+    // one warp per block: the tracks the device count leaves are few
+    // compared with the capacity the grid is sized for, and single-warp
+    // blocks spread the working warps over every SM instead of packing them
+    // four to an SM on the first ones
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((n_tracks + 31) / 32, (int64_t)c->n_sm * 128));
     c->mark(10, s);
-    tpc::LaunchCount{}, k_fit<<<(unsigned)blocks, 128, 0, s>>>(trk_off, trk_hits, n_tracks, n_tracks_dev, c->y, c->z,
+    tpc::LaunchCount{}, k_fit<<<(unsigned)blocks, 32, 0, s>>>(trk_off, trk_hits, n_tracks, n_tracks_dev, c->y, c->z,
                                            c->row, c->evt_sector_off, c->n_events * NSEC,
                                            c->ws.at<Geo>(c->ws.L.geo), fp, params, cov, chi2, ndf,
                                            c->ws.at<int32_t>(c->ws.L.status));
