@@ -56,13 +56,35 @@ struct AdjAccDevice {
 constexpr int ADJ_T = 128;
 constexpr size_t ADJ_SEG_BYTES = sizeof(float) * CK * PRE_W * ADJ_T;
 
+// The tracks' clusters copied in track order (position, row, sector at each
+// entry of trk_hits), when they fit the copy's capacity: the three sweeps
+// over a track then read consecutive entries instead of one scattered
+// cluster per hit three times over.
+__global__ void k_adj_gather(const int32_t* __restrict__ trk_off, const int32_t* __restrict__ trk_hits,
+                             int32_t T, const float* __restrict__ y, const float* __restrict__ z,
+                             const uint16_t* __restrict__ row, const int64_t* __restrict__ evt_off, int G,
+                             int64_t cap, float2* gyz, uint8_t* grow, uint8_t* gsec,
+                             const int32_t* __restrict__ st) {
+    if (input_rejected(st)) return;
+    const int64_t total = trk_off[T];
+    if (total > cap) return;  // the sweeps read through the hit lists instead
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int c = trk_hits[k];
+        gyz[k] = make_float2(y[c], z[c]);
+        grow[k] = (uint8_t)row[c];
+        gsec[k] = (uint8_t)(group_of(evt_off, G, c) % NSEC);
+    }
+}
+
 template <bool FIELD>
 __global__ void __launch_bounds__(ADJ_T) k_adjoint(
     const int32_t* __restrict__ trk_off, const int32_t* __restrict__ trk_hits, int32_t T,
     const float* __restrict__ yin, const float* __restrict__ zin, const uint16_t* __restrict__ row,
     const int64_t* __restrict__ evt_off, int G, const float* __restrict__ rot_tab,
     const Geo* __restrict__ geo, AdjPrm P, double* chi2_total, double* grad, int32_t* st,
-    const double* __restrict__ field, FieldGridD fg, double* grad_field) {
+    const double* __restrict__ field, FieldGridD fg, double* grad_field, const float2* __restrict__ gyz,
+    const uint8_t* __restrict__ grow, const uint8_t* __restrict__ gsec, int64_t gcap) {
     if (input_rejected(st)) return;  // clusters that failed validation are not read
     __shared__ double sg[216];
     __shared__ double schi2;
@@ -76,6 +98,7 @@ __global__ void __launch_bounds__(ADJ_T) k_adjoint(
     if (threadIdx.x == 0) schi2 = 0.0;
     __syncthreads();
     AdjAccDevice acc{sg, &schi2, grad_field, st};
+    const bool gathered = T > 0 && gyz != nullptr && (int64_t)trk_off[T] <= gcap;
     // tracks handed out 32 at a time to whichever warp is free, so that the
     // blocks finish together (a fixed grid stride leaves a third of the
     // threads idle at the end when tracks per thread is not whole)
@@ -88,8 +111,15 @@ __global__ void __launch_bounds__(ADJ_T) k_adjoint(
         const int t = base + lane;
         if (t < T) {
             const int b = trk_off[t];
-            adjoint_track<FIELD>(trk_hits + b, trk_off[t + 1] - b, yin, zin, row, evt_off, G, tab, geo, P,
-                                 field, fg, seg_sh + threadIdx.x, ADJ_T, acc);
+            AdjHits hits = adj_hits_direct(trk_hits + b, yin, zin, row, evt_off, G);
+            if (gathered) {
+                hits.gyz = gyz;
+                hits.grow = grow;
+                hits.gsec = gsec;
+                hits.gbase = b;
+            }
+            adjoint_track<FIELD>(hits, trk_off[t + 1] - b, tab, geo, P, field, fg, seg_sh + threadIdx.x, ADJ_T,
+                                 acc);
         }
     }
     __syncthreads();
@@ -104,6 +134,22 @@ cudaError_t adjoint_smem_opt_in() {
     static cudaError_t e = cudaFuncSetAttribute(k_adjoint<FIELD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                 (int)ADJ_SEG_BYTES);
     return e;
+}
+
+// The gathered copy lives in the find's binned-cluster scratch (positions,
+// rows, groups: N entries each), unused between find calls.
+#define ADJ_GATHER_ARGS(c, ap)                                                                    \
+    (ap).want_grad ? (c)->ws.at<float2>((c)->ws.L.yzb) : nullptr, (c)->ws.at<uint8_t>((c)->ws.L.rowb), \
+        (c)->ws.at<uint8_t>((c)->ws.L.grpb), (int64_t)(c)->ws.L.N
+
+cudaError_t adj_gather(tpc_ctx* c, const int32_t* trk_off, const int32_t* trk_hits, int32_t n_tracks,
+                       cudaStream_t s) {
+    const int64_t blocks = (int64_t)c->n_sm * 8;
+    tpc::LaunchCount{}, k_adj_gather<<<(unsigned)blocks, 256, 0, s>>>(
+        trk_off, trk_hits, n_tracks, c->y, c->z, c->row, c->evt_sector_off, c->n_events * NSEC,
+        (int64_t)c->ws.L.N, c->ws.at<float2>(c->ws.L.yzb), c->ws.at<uint8_t>(c->ws.L.rowb),
+        c->ws.at<uint8_t>(c->ws.L.grpb), c->ws.at<int32_t>(c->ws.L.status));
+    return cudaGetLastError();
 }
 
 __global__ void k_zero_f64(double* p, int n) {
@@ -126,12 +172,15 @@ cudaError_t run_adjoint(tpc_ctx* c, const int32_t* trk_off, const int32_t* trk_h
         const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((n_tracks + 127) / 128, 152 * 4));
         cudaError_t e = adjoint_smem_opt_in<false>();
         if (e == cudaSuccess) e = fill_i32(c->ws.at<int32_t>(c->ws.L.status) + ST_ADJ_NEXT, 1, 0, s);
+        // the reverse sweep alone needs the segment store and reads each
+        // track three times; forward only keeps L1 and reads through the lists
+        if (e == cudaSuccess && ap.want_grad) e = adj_gather(c, trk_off, trk_hits, n_tracks, s);
         if (e != cudaSuccess) return e;
-        tpc::LaunchCount{}, k_adjoint<false><<<(unsigned)blocks, ADJ_T, ADJ_SEG_BYTES, s>>>(trk_off, trk_hits, n_tracks, c->y, c->z, c->row,
+        tpc::LaunchCount{}, k_adjoint<false><<<(unsigned)blocks, ADJ_T, ap.want_grad ? ADJ_SEG_BYTES : 0, s>>>(trk_off, trk_hits, n_tracks, c->y, c->z, c->row,
                                                    c->evt_sector_off, c->n_events * NSEC, rot_tab,
                                                    c->ws.at<Geo>(c->ws.L.geo), ap, chi2_total, grad,
                                                    c->ws.at<int32_t>(c->ws.L.status),
-                                                   nullptr, FieldGridD{}, nullptr);
+                                                   nullptr, FieldGridD{}, nullptr, ADJ_GATHER_ARGS(c, ap));
     }
     c->mark(13, s);
     return cudaGetLastError();
@@ -156,11 +205,14 @@ cudaError_t run_adjoint_field(tpc_ctx* c, const int32_t* trk_off, const int32_t*
         const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((n_tracks + 127) / 128, 152 * 4));
         cudaError_t e = adjoint_smem_opt_in<true>();
         if (e == cudaSuccess) e = fill_i32(c->ws.at<int32_t>(c->ws.L.status) + ST_ADJ_NEXT, 1, 0, s);
+        // the reverse sweep alone needs the segment store and reads each
+        // track three times; forward only keeps L1 and reads through the lists
+        if (e == cudaSuccess && ap.want_grad) e = adj_gather(c, trk_off, trk_hits, n_tracks, s);
         if (e != cudaSuccess) return e;
-        tpc::LaunchCount{}, k_adjoint<true><<<(unsigned)blocks, ADJ_T, ADJ_SEG_BYTES, s>>>(
+        tpc::LaunchCount{}, k_adjoint<true><<<(unsigned)blocks, ADJ_T, ap.want_grad ? ADJ_SEG_BYTES : 0, s>>>(
             trk_off, trk_hits, n_tracks, c->y, c->z, c->row, c->evt_sector_off, c->n_events * NSEC,
             rot_tab, c->ws.at<Geo>(c->ws.L.geo), ap, chi2_total, grad_align,
-            c->ws.at<int32_t>(c->ws.L.status), field, fg, grad_field);
+            c->ws.at<int32_t>(c->ws.L.status), field, fg, grad_field, ADJ_GATHER_ARGS(c, ap));
     }
     c->mark(13, s);
     return cudaGetLastError();

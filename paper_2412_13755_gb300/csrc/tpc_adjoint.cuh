@@ -317,15 +317,62 @@ TPC_HD void flush_field(Acc& acc, int v, double f[3]) {
 // i = 6 sector + k), the voxel gradients (acc.field(i, v) when
 // acc.want_field()) and capacity errors (acc.status).  tab holds the
 // per-sector rotation tables.
+// Where one track's clusters are read: through its hit list (the group of
+// each cluster found by binary search, cached while the hits stay in one
+// group), or from a copy gathered in track order (position, row and sector
+// at the track's offset into gyz, grow, gsec).
+struct AdjHit {
+    float y, z;
+    int row, sec;
+};
+struct AdjHits {
+    const int32_t* h;
+    const float* y;
+    const float* z;
+    const uint16_t* row;
+    const int64_t* evt_off;
+    int G;
+    const float2* gyz;  // gathered copy, or nullptr
+    const uint8_t* grow;
+    const uint8_t* gsec;
+    int64_t gbase;
+    int gcur;
+    int64_t gb, ge;
+    TPC_HD AdjHit at(int j) {
+        AdjHit r;
+        if (gyz) {
+            const float2 v = gyz[gbase + j];
+            r.y = v.x;
+            r.z = v.y;
+            r.row = grow[gbase + j];
+            r.sec = gsec[gbase + j];
+            return r;
+        }
+        const int c = h[j];
+        if (c < gb || c >= ge) {
+            gcur = group_of(evt_off, G, c);
+            gb = evt_off[gcur];
+            ge = evt_off[gcur + 1];
+        }
+        r.y = y[c];
+        r.z = z[c];
+        r.row = row[c];
+        r.sec = gcur % NSEC;
+        return r;
+    }
+};
+
+TPC_HD AdjHits adj_hits_direct(const int32_t* h, const float* y, const float* z, const uint16_t* row,
+                               const int64_t* evt_off, int G) {
+    return AdjHits{h, y, z, row, evt_off, G, nullptr, nullptr, nullptr, 0, -1, 0, 0};
+}
+
 // seg: the store of one segment's recomputed states, CK x PRE_W words, word
 // w of entry k at seg[(k PRE_W + w) seg_stride] (the kernel gives each
 // thread a column of shared memory, stride = threads per block; a host
 // program a plain array, stride 1).
 template <bool FIELD, class Acc>
-TPC_HD void adjoint_track(const int32_t* h, int n, const float* __restrict__ yin,
-                          const float* __restrict__ zin, const uint16_t* __restrict__ row,
-                          const int64_t* __restrict__ evt_off, int G, const float* tab,
-                          const Geo* __restrict__ geo, const AdjPrm& P,
+TPC_HD void adjoint_track(AdjHits& hits, int n, const float* tab, const Geo* __restrict__ geo, const AdjPrm& P,
                           const double* __restrict__ field, const FieldGridD& fg, float* seg, int seg_stride,
                           Acc& acc) {
     if (n < 3) return;
@@ -336,11 +383,11 @@ TPC_HD void adjoint_track(const int32_t* h, int n, const float* __restrict__ yin
         float ys[3], zs[3];
         const int pick[3] = {0, n / 2, n - 1};
         for (int k = 0; k < 3; ++k) {
-            const int c = h[pick[k]];
-            rows[k] = row[c];
-            secs[k] = group_of(evt_off, G, c) % NSEC;
-            ys[k] = yin[c];
-            zs[k] = zin[c];
+            const AdjHit a = hits.at(pick[k]);
+            rows[k] = a.row;
+            secs[k] = a.sec;
+            ys[k] = a.y;
+            zs[k] = a.z;
         }
         kf_seed(s, rows, secs, ys, zs, true, geo, P.bz, P.seed_snp, P.seed_qpt, P.prior);
     }
@@ -352,8 +399,6 @@ TPC_HD void adjoint_track(const int32_t* h, int n, const float* __restrict__ yin
     }
     NSum chi2;
     bool ok = true;
-    int gcur = -1;
-    int64_t gb = 0, ge = 0;
     for (int j = 0; j < n && ok; ++j) {
         if (P.want_grad && j % CK == 0) {  // checkpoints only for the reverse sweep
             Pre& q = ck[j / CK];
@@ -362,17 +407,12 @@ TPC_HD void adjoint_track(const int32_t* h, int n, const float* __restrict__ yin
             for (int i = 0; i < 3; ++i) q.lo[i] = s.lo[i];
             for (int i = 0; i < 15; ++i) q.C[i] = s.C[i];
         }
-        const int c = h[j];
-        if (c < gb || c >= ge) {  // group lookup, cached while hits stay in one group
-            gcur = group_of(evt_off, G, c);
-            gb = evt_off[gcur];
-            ge = evt_off[gcur + 1];
-        }
-        const int sec = gcur % NSEC;
+        const AdjHit hc = hits.at(j);
+        const int sec = hc.sec;
         double xc;
         float yc, zc;
-        corr_tab(tab + sec * ROT_TAB, geo->row_xd[row[c]], yin[c], zin[c], xc, yc, zc);
-        if constexpr (FIELD) add_field(field, fg, geo, row[c], sec, yin[c], zin[c], xc, yc, zc);
+        corr_tab(tab + sec * ROT_TAB, geo->row_xd[hc.row], hc.y, hc.z, xc, yc, zc);
+        if constexpr (FIELD) add_field(field, fg, geo, hc.row, sec, hc.y, hc.z, xc, yc, zc);
         MoveJ mj;
         ok = kf_move<float>(s, xc, sec, geo, P.kb, P.snp_max, &mj);
         if (ok) chi2.add(kf_update(s, yc, zc, P.sy2, P.sz2, P.fp64_ratio, P.fp64_det, nullptr, &mj));
@@ -411,17 +451,12 @@ TPC_HD void adjoint_track(const int32_t* h, int n, const float* __restrict__ yin
                 segx[j - j0] = r.x;
                 segf[j - j0] = r.frame;
             }
-            const int c = h[j];
-            if (c < gb || c >= ge) {
-                gcur = group_of(evt_off, G, c);
-                gb = evt_off[gcur];
-                ge = evt_off[gcur + 1];
-            }
-            const int sec = gcur % NSEC;
+            const AdjHit hc = hits.at(j);
+            const int sec = hc.sec;
             double xc;
             float yc, zc;
-            corr_tab(tab + sec * ROT_TAB, geo->row_xd[row[c]], yin[c], zin[c], xc, yc, zc);
-            if constexpr (FIELD) add_field(field, fg, geo, row[c], sec, yin[c], zin[c], xc, yc, zc);
+            corr_tab(tab + sec * ROT_TAB, geo->row_xd[hc.row], hc.y, hc.z, xc, yc, zc);
+            if constexpr (FIELD) add_field(field, fg, geo, hc.row, sec, hc.y, hc.z, xc, yc, zc);
             MoveJ mj;
             kf_move<float>(r, xc, sec, geo, P.kb, P.snp_max, &mj);
             kf_update(r, yc, zc, P.sy2, P.sz2, P.fp64_ratio, P.fp64_det, nullptr, &mj);
@@ -436,20 +471,15 @@ TPC_HD void adjoint_track(const int32_t* h, int n, const float* __restrict__ yin
                 q.x = segx[j - j0];
                 q.frame = segf[j - j0];
             }
-            const int c = h[j];
-            if (c < gb || c >= ge) {
-                gcur = group_of(evt_off, G, c);
-                gb = evt_off[gcur];
-                ge = evt_off[gcur + 1];
-            }
-            const int sec = gcur % NSEC;
+            const AdjHit hc = hits.at(j);
+            const int sec = hc.sec;
             const float* tb = tab + sec * ROT_TAB;
-            const double xr = geo->row_xd[row[c]];
+            const double xr = geo->row_xd[hc.row];
             double xc;
             float yc, zc;
-            corr_tab(tb, xr, yin[c], zin[c], xc, yc, zc);
+            corr_tab(tb, xr, hc.y, hc.z, xc, yc, zc);
             int vox = -1;
-            if constexpr (FIELD) vox = add_field(field, fg, geo, row[c], sec, yin[c], zin[c], xc, yc, zc);
+            if constexpr (FIELD) vox = add_field(field, fg, geo, hc.row, sec, hc.y, hc.z, xc, yc, zc);
             // forward of this step again: transport, then update pieces
             KF m;
             m.x = q.x; m.frame = q.frame;
@@ -615,7 +645,7 @@ TPC_HD void adjoint_track(const int32_t* h, int n, const float* __restrict__ yin
             const double xb = (double)xbar_to + (double)xbar_from_next;
             xbar_from_next = xbar_from;
             float gr[3];
-            rot_grad_tab(tb, (float)xr, yin[c], zin[c], (float)xb, ybar, zbar, gr);
+            rot_grad_tab(tb, (float)xr, hc.y, hc.z, (float)xb, ybar, zbar, gr);
             if (sec != gsec) {
                 if (gsec >= 0)
                     for (int i = 0; i < 6; ++i) acc.align(gsec * 6 + i, gacc[i]);

@@ -88,12 +88,11 @@ int main(int argc, char** argv) {
     std::vector<float> seg(CK * PRE_W);
     for (int64_t t = 0; t < T; ++t) {
         const int b = toff[t], m = toff[t + 1] - b;
+        AdjHits hv = adj_hits_direct(hits.data() + b, y.data(), z.data(), row.data(), off.data(), (int)G);
         if (gi[0])
-            adjoint_track<true>(hits.data() + b, m, y.data(), z.data(), row.data(), off.data(), (int)G,
-                                tab.data(), &geo, P, field.data(), fg, seg.data(), 1, acc);
+            adjoint_track<true>(hv, m, tab.data(), &geo, P, field.data(), fg, seg.data(), 1, acc);
         else
-            adjoint_track<false>(hits.data() + b, m, y.data(), z.data(), row.data(), off.data(), (int)G,
-                                 tab.data(), &geo, P, nullptr, fg, seg.data(), 1, acc);
+            adjoint_track<false>(hv, m, tab.data(), &geo, P, nullptr, fg, seg.data(), 1, acc);
     }
     FILE* o = fopen(argv[2], "wb");
     if (!o) return 2;
