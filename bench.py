@@ -190,9 +190,21 @@ def adjoint_bench(torch, tpc, dev, steps):
     e1.record()
     torch.cuda.synchronize()
     s_fwd = e0.elapsed_time(e1) / 1e3 / steps
+    # lower-bound roofline: the two forward Kalman sweeps per cluster (the
+    # checkpointing pass and the recompute of each segment) at the oracle's
+    # counted operations per step; the reverse step's own operations have
+    # no independent count and are left out
+    n_hits = int(off_h[-1])
+    ops = kf_ops_per_step()
+    peak_tf, sms = fp32_peak_tflops(torch, dev, measured_sm_max_mhz())
+    ach = 2 * n_hits * ops / s_grad / 1e12
     return {"workload": f"alignment_sample: {T} tracks pT>1 GeV/c, {ev.n} clusters, 216 parameters",
             "tracks_per_s": T / s_grad, "forward_only_tracks_per_s": T / s_fwd,
-            "ms_per_step": 1e3 * s_grad, "chi2": float(chi2.item())}
+            "ms_per_step": 1e3 * s_grad, "chi2": float(chi2.item()),
+            "roofline": {"bound": "alu", "achieved": ach, "peak": peak_tf, "unit": "TFLOP/s",
+                         "frac": ach / peak_tf, "kernel": "k_adjoint",
+                         "work": f"2 forward Kalman steps per cluster x {ops:.1f} counted operations "
+                                 "(the reverse step not counted: a lower bound)"}}
 
 
 def pileup_bench(torch, tpc, dev, steps):
