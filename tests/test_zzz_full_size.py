@@ -11,7 +11,11 @@ benchmark times:
   within |dp_i| <= 1e-5 max(|p_i|, s_i);
 * the 100-collision pile-up frame (about 1.8e8 clusters, one event): the
   whole track list passes the structural checks, and the fit of 5000 tracks
-  drawn with a fixed seed matches the oracle's fit of their hit lists.
+  drawn with a fixed seed matches the oracle's fit of their hit lists;
+* NEXT-4 on the same frame shape with a vertex z spread: the generator's
+  A/C segments associated on the GPU and by the oracle over the whole
+  frame, every track's partner and every pair's joint fit compared, and
+  each collision's t0 recovered from its pairs.
 
 The oracle cannot find a whole frame in seconds; for it the assignment is
 covered by the smaller pile-up parity test and, at full size, by the
@@ -169,3 +173,36 @@ def test_alignment_descent_full_size(orc):
           f"(largest error {np.abs(err).max():.1f} target units)")
     assert chi2s[-1] < chi2s[0]
     assert stat.max() < 0.1
+
+
+def test_sides_membrane_frame_full_size(orc):
+    from test_gpu_sides import _compare
+    ev = synth.membrane_frame_parallel(n_collisions=100)
+    off, hits, ids, sides = ev.truth_segments()
+    T = len(off) - 1
+    tr = tpc.Tracker(ev.n, 1)
+    tr.load(*_device_inputs(ev), 1)
+    r = tr.match_sides(torch.from_numpy(off).cuda(), torch.from_numpy(hits).cuda(), T)
+    torch.cuda.synchronize()
+    tr.check()
+    g = {k: v.cpu().numpy() for k, v in r.items()}
+    del tr
+    o = orc.match_sides(ev.y, ev.z, ev.row, ev.evt_sector_off, 1, off, hits)
+    both = _compare(g, o, T)
+    u, cnt = np.unique(ids, return_counts=True)
+    crossing = set(u[cnt == 2].tolist())
+    p = g["partner"][:T]
+    pairs = [(i, int(p[i])) for i in range(T) if p[i] > i]
+    good = sum(1 for i, j in pairs if ids[i] == ids[j])
+    print(f"{T} segments, {len(crossing)} crossing tracks, {len(pairs)} pairs, {good} of one track")
+    assert good >= 0.995 * len(pairs) and good >= 0.97 * len(crossing)
+    # each collision's t0 from the median of its pairs
+    sel = np.array([i for i, j in pairs if ids[i] == ids[j]])
+    t0_true = ev.trk_t0[ids[sel]]
+    res = []
+    for t0c in np.unique(t0_true):
+        m = t0_true == t0c
+        res.append(np.median(g["t0"][sel][m]) - t0c)
+    res = np.abs(np.array(res))
+    print(f"per-collision t0: median |residual| {np.median(res) * 1e3:.2f} ns, largest {res.max() * 1e3:.2f} ns")
+    assert len(res) == 100 and res.max() < 0.01
