@@ -666,12 +666,13 @@ def run_ours(args):
     # end to end: host buffers -> device, step, results back to the host.
     # Steps are pipelined as for a stream of events: while a step computes,
     # a copy stream uploads the next step's inputs and downloads the previous
-    # step's results (two buffer sets, ordered by events).
+    # step's results (two buffer sets, ordered by events); each set's step
+    # is the library graph of load + find + fit over that set's buffers.
     main_s = torch.cuda.current_stream(dev)
     copy_s = torch.cuda.Stream(device=dev)
 
     def buffer_set():
-        return {
+        b = {
             "y": torch.empty_like(d_y), "z": torch.empty_like(d_z),
             "row": torch.empty(n, dtype=torch.int16, device=dev), "off": torch.empty_like(d_off),
             "find": tuple(torch.empty_like(t) for t in find_out),
@@ -682,6 +683,17 @@ def run_ours(args):
             "h_nt": torch.empty(1, dtype=torch.int32).pin_memory(),
             "in": torch.cuda.Event(), "done": torch.cuda.Event(), "out": torch.cuda.Event(),
         }
+        # each buffer set has its own context holding the graph of the step
+        # over that set's buffers (the same call a server replays per event)
+        b["tr"] = tpc.Tracker(n, 1, device=dev)
+        b["y"].copy_(d_y)
+        b["z"].copy_(d_z)
+        b["row"].copy_(d_row.view(torch.int16))
+        b["off"].copy_(d_off)
+        b["tr"].load(b["y"], b["z"], b["row"].view(torch.uint16), b["off"], 1)
+        b["tr"].set_tune(tune)
+        b["tr"].capture(b["y"], b["z"], b["row"].view(torch.uint16), b["off"], 1, b["find"], b["fit"])
+        return b
 
     sets = [buffer_set(), buffer_set()]
 
@@ -697,10 +709,7 @@ def run_ours(args):
     def compute(b):
         main_s.wait_event(b["in"])
         main_s.wait_event(b["out"])  # the outputs' previous download has finished
-        fo = b["find"]
-        tr.load(b["y"], b["z"], b["row"].view(torch.uint16), b["off"], 1)
-        tr.find(out=fo)
-        tr.fit(fo[1], fo[2], track_cap, fo[3], out=b["fit"])
+        b["tr"].replay(stream=main_s)
         b["done"].record(main_s)
 
     def download(b):
