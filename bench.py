@@ -616,6 +616,9 @@ def run_ours(args):
     # find, fit) recorded once as the library's CUDA graph: the timed steps
     # replay it, as a server does for every event of a fixed-size stream
     tune = tr.autotune(out=find_out)
+    # stage events on at capture: they become event nodes of the graph, so
+    # each timed replay carries its own stage times
+    tr.stage_timing(True)
     tr.capture(d_y, d_z, d_row, d_off, 1, find_out, fit_out)
     for _ in range(max(args.warmup, 3)):
         flush.zero_()
@@ -631,11 +634,15 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     sync()
+    stage_sum = {}
     for k in range(args.steps):
         flush.zero_()
         e0[k].record(stream)
         tr.replay()
         e1[k].record(stream)
+        sync()
+        for name, ms in tr.stage_times().items():
+            stage_sum[name] = stage_sum.get(name, 0.0) + ms
     sync()
     step_ms = [a.elapsed_time(b) for a, b in zip(e0, e1)]
     total_s = max_over_ranks(sum(step_ms) / 1e3, dist if world > 1 else None, dev)
@@ -643,10 +650,7 @@ def run_ours(args):
     T = int(find_out[3].item())
     value = weak_value(n, world, args.steps, total_s)
     # the same step through the per-call entry points (load, find, fit as
-    # three calls), with the library's stage events on: the stage times and
-    # the roofline come from this pass, since stage events are off in graphs
-    tr.stage_timing(True)
-    stage_sum = {}
+    # three calls)
     plain_ms = []
     for k in range(args.steps):
         flush.zero_()
@@ -655,8 +659,6 @@ def run_ours(args):
         e1[k].record(stream)
         sync()
         plain_ms.append(e0[k].elapsed_time(e1[k]))
-        for name, ms in tr.stage_times().items():
-            stage_sum[name] = stage_sum.get(name, 0.0) + ms
     sync()
     clk = clocks.stop()
     tr.stage_timing(False)

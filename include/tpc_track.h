@@ -272,8 +272,9 @@ tpc_status tpc_autotune(tpc_ctx* ctx, int32_t* track_of_cluster, int32_t* trk_of
 
 /* Stage timing (no counterpart in the paper; a measurement aid).  When
  * enabled, the library records CUDA events on the launch stream around its
- * main kernels; tpc_stage_times then synchronises and writes, for the last
- * call of each kind, the milliseconds of the stages listed in
+ * main kernels (inside a graph captured with timing on, as event nodes of
+ * the graph); tpc_stage_times then synchronises and writes, for the last
+ * call or replay of each kind, the milliseconds of the stages listed in
  * TPC_STAGE_NAMES (ms_out[TPC_N_STAGES]).  Disabled by default; enabling it
  * creates the events (host-side CUDA objects, no device memory). */
 #define TPC_N_STAGES 13
@@ -350,9 +351,10 @@ tpc_status tpc_track_batch(tpc_ctx* ctx, const float* y, const float* z, const u
  * context held; nothing runs.  tpc_graph_launch then runs the whole batch
  * as one graph launch on `stream`.  A replay reads the same input and
  * output buffers, so refill the inputs in place between replays (the
- * sizes n and n_events are fixed by the capture).  The stage timing is off
- * inside the graph.  TPC_ERR_STATE from tpc_graph_launch if nothing was
- * captured. */
+ * sizes n and n_events are fixed by the capture).  With stage timing
+ * enabled at capture time the stage events are recorded into the graph as
+ * event nodes: tpc_stage_times after a replay gives that replay's stages.
+ * TPC_ERR_STATE from tpc_graph_launch if nothing was captured. */
 tpc_status tpc_graph_capture(tpc_ctx* ctx, const float* y, const float* z, const uint16_t* row,
                              const uint16_t* charge, int64_t n, const int64_t* evt_sector_off,
                              int32_t n_events, const tpc_batch_outputs* out);

@@ -514,8 +514,9 @@ tpc_status tpc_graph_capture(tpc_ctx* c, const float* y, const float* z, const u
     cudaStream_t cs = nullptr;
     cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
     if (e != cudaSuccess) return cuda_fail(c, e, "tpc_graph_capture");
-    const bool timing = c->timing;
-    c->timing = false;
+    // with stage timing on, the stage events are recorded into the graph as
+    // event nodes, so that every replay carries its own stage times
+    c->capturing = true;
     const long long l0 = g_launches.load(std::memory_order_relaxed);
     tpc_status st = TPC_OK;
     cudaGraph_t g = nullptr;
@@ -525,7 +526,7 @@ tpc_status tpc_graph_capture(tpc_ctx* c, const float* y, const float* z, const u
         // the capture always ends, also after a failed enqueue
         e = cudaStreamEndCapture(cs, &g);
     }
-    c->timing = timing;
+    c->capturing = false;
     const long long kernels = g_launches.load(std::memory_order_relaxed) - l0;
     cudaGraphExec_t x = nullptr;
     if (st == TPC_OK && e == cudaSuccess) e = cudaGraphInstantiate(&x, g, 0);

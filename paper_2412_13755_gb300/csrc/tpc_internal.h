@@ -130,9 +130,10 @@ struct tpc_ctx {
     // stage timing: marks 0..9 around the find stages, 10/11 fit, 12/13 adjoint,
     // 14/15 the A/C-side association
     bool timing = false;
+    bool capturing = false;  // inside tpc_graph_capture: marks become event nodes of the graph
     cudaEvent_t marks[16] = {};
     void mark(int i, cudaStream_t s) {
-        if (timing) cudaEventRecord(marks[i], s);
+        if (timing) cudaEventRecordWithFlags(marks[i], s, capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
     }
 };
 
