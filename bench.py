@@ -35,6 +35,7 @@ METRIC = "TPC clusters/s tracked (CA+Kalman), 1 GB300"
 WORKLOAD = ("central_event: 1 event x 36 sectors, 1e4 primary tracks (pT exp slope 0.5 GeV/c "
             "min 0.2, |eta|<0.9), 20% noise, ~1.8e6 clusters, Bz 0.5 T")
 FP32_LANES_PER_SM = 128                 # Blackwell SM: 4 partitions x 32 FP32 lanes
+FP64_NOMINAL_TFLOPS = 1.25   # GB300 dense FP64, nominal (no FP64 figure is measured on this machine)
 # algorithmic traffic / work per unit, fixed before measuring
 # the whole find + fit path, every intermediate product written once and read
 # once: binning 22, neighbours 16, chains and tracks 16, fit 12.7, scatter 12
@@ -247,6 +248,52 @@ def pileup_bench(torch, tpc, dev, steps):
             "workspace_gb": tr.workspace.numel() / 1e9, "generation_s": gen_s}
 
 
+def kf_variants_bench(torch, tpc, dev, steps):
+    """NEXT-3: the Kalman-filter variants on 2e4 pions through material (one
+    sector, material in every pad-row plane): the inward fit with material,
+    the outward refit and the fit with the Rauch-Tung-Striebel smoother,
+    FP64 per track (tpc_fit_tracks_ex)."""
+    from paper_2412_13755_gb300 import synth
+    ev = synth.material_tracks(n_tracks=20000)
+    off_h, hits_h, _ = ev.truth_tracks(n_min=10)
+    T = len(off_h) - 1
+    tr = tpc.Tracker(ev.n, 1, device=dev)
+    y = torch.from_numpy(ev.y).to(dev)
+    z = torch.from_numpy(ev.z).to(dev)
+    row = torch.from_numpy(ev.row.view(np.int16)).to(dev).view(torch.uint16)
+    d_off = torch.from_numpy(ev.evt_sector_off).to(dev)
+    tr.load(y, z, row, d_off, 1)
+    trk_off = torch.from_numpy(off_h).to(dev)
+    trk_hits = torch.from_numpy(hits_h).to(dev)
+    out = {}
+    for name, outward, smooth in (("material_fit", False, False), ("outward_refit", True, False),
+                                  ("fit_and_smoother", False, True)):
+        o = tpc.fit_options(synth.MAT_X_X0_ROW, synth.MAT_ELOSS_ROW, synth.PION_MASS, outward=outward)
+        tr.fit_ex(trk_off, trk_hits, T, o, smooth=smooth)
+        torch.cuda.synchronize()
+        tr.check()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            tr.fit_ex(trk_off, trk_hits, T, o, smooth=smooth)
+        e1.record()
+        torch.cuda.synchronize()
+        out[name] = {"tracks_per_s": T * steps / (e0.elapsed_time(e1) / 1e3),
+                     "ms_per_step": e0.elapsed_time(e1) / steps}
+    # FP64 roofline of the material fit: the oracle's counted operations per
+    # cluster through material (tests/golden/kf_ops_per_step.json) against
+    # the nominal FP64 rate (no FP64 figure is measured on this pool)
+    with open(os.path.join(ROOT, "tests", "golden", "kf_ops_per_step.json")) as f:
+        ops_hit = float(json.load(f)["material"]["ops_per_hit"])
+    ach = int(off_h[-1]) * ops_hit / (out["material_fit"]["ms_per_step"] * 1e-3) / 1e12
+    out["roofline"] = {"bound": "fp64", "achieved": ach, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                       "frac": ach / FP64_NOMINAL_TFLOPS, "kernel": "k_fit_ex (material fit)",
+                       "peak_source": "nominal GB300 FP64 (not measured)", "ops_per_hit": ops_hit}
+    out["workload"] = f"material_tracks: {T} pions pT > 0.3 GeV/c in one sector, {int(off_h[-1])} clusters"
+    return out
+
+
 def sides_bench(torch, tpc, dev, steps):
     """NEXT-4: a 20-collision frame with a vertex z spread (sigma 6 cm),
     found once; the timed step is the A/C-side association with t0 over all
@@ -322,9 +369,17 @@ def field_adjoint_bench(torch, tpc, dev, steps):
     e1.record()
     torch.cuda.synchronize()
     sec = e0.elapsed_time(e1) / 1e3 / steps
+    # lower-bound roofline as for the alignment adjoint
+    ops = kf_ops_per_step()
+    peak_tf, _ = fp32_peak_tflops(torch, dev, measured_sm_max_mhz())
+    ach = 2 * int(trk_off[-1].item()) * ops / sec / 1e12
     return {"workload": f"distortion map: {T} tracks pT>1 GeV/c, {ev.n} clusters, "
                         f"{synth.n_voxels(grid)} voxels x 3 + 216 alignment parameters",
-            "tracks_per_s": T / sec, "ms_per_step": 1e3 * sec}
+            "tracks_per_s": T / sec, "ms_per_step": 1e3 * sec,
+            "roofline": {"bound": "alu", "achieved": ach, "peak": peak_tf, "unit": "TFLOP/s",
+                         "frac": ach / peak_tf, "kernel": "k_adjoint<true>",
+                         "work": f"2 forward Kalman steps per cluster x {ops:.1f} counted operations "
+                                 "(the reverse step not counted: a lower bound)"}}
 
 
 def clusterize_bench(torch, tpc, dev, steps, ev):
@@ -364,7 +419,8 @@ def clusterize_bench(torch, tpc, dev, steps, ev):
             "inputs_vs_l2": "0.9 GB of digits, larger than L2 (no flush needed)"}
 
 
-EXTRA_NAMES = ("batched_vs_plain", "adjoint", "clusterize", "field_adjoint", "sides", "pileup_frame")
+EXTRA_NAMES = ("batched_vs_plain", "adjoint", "clusterize", "field_adjoint", "kf_variants", "sides",
+               "pileup_frame")
 
 
 def parse():
@@ -823,6 +879,7 @@ def run_ours(args):
                    ("adjoint", lambda: adjoint_bench(torch, tpc, dev, max(3, args.steps // 4))),
                    ("clusterize", lambda: clusterize_bench(torch, tpc, dev, max(3, args.steps // 2), ev)),
                    ("field_adjoint", lambda: field_adjoint_bench(torch, tpc, dev, max(3, args.steps // 4))),
+                   ("kf_variants", lambda: kf_variants_bench(torch, tpc, dev, max(3, args.steps // 4))),
                    ("sides", lambda: sides_bench(torch, tpc, dev, max(3, args.steps // 4)))]
     if args.pileup:
         extras.append(("pileup_frame", lambda: pileup_bench(torch, tpc, dev, 2)))
@@ -848,6 +905,7 @@ def run_only(args):
            "clusterize": lambda: clusterize_bench(torch, tpc, dev, max(3, args.steps // 2), make_event()),
            "field_adjoint": lambda: field_adjoint_bench(torch, tpc, dev, k),
            "sides": lambda: sides_bench(torch, tpc, dev, k),
+           "kf_variants": lambda: kf_variants_bench(torch, tpc, dev, k),
            "pileup_frame": lambda: pileup_bench(torch, tpc, dev, 2)}
     print(json.dumps({args.only: fns[args.only]()}), flush=True)
 

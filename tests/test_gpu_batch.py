@@ -117,3 +117,31 @@ def test_every_tuning_gives_identical_tracks():
     assert best.nb_sub_lanes in (4, 8, 16) and best.lane_blocks_per_sm in (4, 8, 16)
     assert best.lane_tile in (1, 4)
     _same(_host(tr.find(out=tr.alloc_find_outputs(cap)), None), base)
+
+
+def test_stage_times_from_graph_replays():
+    """With stage timing on at capture the stage events are event nodes of
+    the graph: each replay's stages are positive, the find stages add up to
+    the find total, and the replay's own duration bounds them."""
+    ev = synth.central_event(n_tracks=2000, seed=31)
+    tr = tpc.Tracker(ev.n, 1)
+    y, z, row, off = to_dev(ev)
+    find_out = tr.alloc_find_outputs(ev.n // 10 + 16)
+    fit_out = tr.alloc_fit_outputs(ev.n // 10 + 16)
+    tr.load(y, z, row, off, 1)
+    tr.stage_timing(True)
+    tr.capture(y, z, row, off, 1, find_out, fit_out)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(3):
+        e0.record()
+        tr.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        st = tr.stage_times()
+        total = e0.elapsed_time(e1)
+        parts = [st[k] for k in ("bin", "neighbours", "links", "chains", "tracklets", "select", "merge_cand",
+                                 "match", "output")]
+        assert all(p > 0 for p in parts) and st["fit"] > 0
+        assert abs(sum(parts) - st["find_total"]) <= 1e-3 * st["find_total"] + 1e-3
+        assert st["find_total"] + st["fit"] <= total * 1.001
+    tr.check()

@@ -24,6 +24,9 @@ def test_stored_count_is_current(orc):
     now = m.count()
     assert now["ops"] == stored["ops"] and now["steps"] == stored["steps"]
     assert 150 < stored["ops_per_step"] < 450
+    # through material every plane between two clusters is crossed too
+    assert now["material"] == stored["material"]
+    assert stored["material"]["ops_per_hit"] > stored["ops_per_step"]
 
 
 def test_count_grows_linearly_with_the_steps(orc):
