@@ -60,9 +60,11 @@ cudaError_t run_fit_ex(tpc_ctx* c, const int32_t* trk_off, const int32_t* trk_hi
     P.mass = o ? o->mass : 0.13957;
     P.outward = o && o->direction == 1;
     const HitSrc H{c->y, c->z, c->row, c->evt_sector_off, c->n_events * NSEC};
-    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((n_tracks + 127) / 128, (int64_t)c->n_sm * 32));
+    // single-warp blocks: the FP64 pipe of every SM takes part even when
+    // the tracks fill fewer than 128 x SMs lanes
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((n_tracks + 31) / 32, (int64_t)c->n_sm * 128));
     c->mark(10, s);
-    tpc::LaunchCount{}, k_fit_ex<<<(unsigned)blocks, 128, 0, s>>>(
+    tpc::LaunchCount{}, k_fit_ex<<<(unsigned)blocks, 32, 0, s>>>(
         trk_off, trk_hits, n_tracks, n_tracks_dev, H, c->ws.at<Geo>(c->ws.L.geo), P, params, cov, chi2, ndf,
         smoothed, c->ws.at<int32_t>(c->ws.L.status));
     c->mark(11, s);

@@ -388,6 +388,10 @@ cudaError_t run_match_sides(tpc_ctx* c, const int32_t* trk_off, const int32_t* t
         std::max<int64_t>(1, std::min<int64_t>((n_tracks + SIDES_T - 1) / SIDES_T, (int64_t)c->n_sm * 8));
     const int64_t cblocks =
         std::max<int64_t>(1, std::min<int64_t>((cand_cap + SIDES_T - 1) / SIDES_T, (int64_t)c->n_sm * 8));
+    // the FP64 kernels over the dense lists: single-warp blocks, so that
+    // the first entries spread over every SM's FP64 pipe
+    const int64_t wblocks = std::max<int64_t>(1, std::min<int64_t>((n_tracks + 31) / 32, (int64_t)c->n_sm * 64));
+    const int64_t wcblocks = std::max<int64_t>(1, std::min<int64_t>((cand_cap + 31) / 32, (int64_t)c->n_sm * 64));
     c->mark(14, s);
     cudaError_t e = fill_i32(bcnt, L.K, 0, s);
     if (e == cudaSuccess) e = fill_i32(bfill, L.K, 0, s);
@@ -412,11 +416,11 @@ cudaError_t run_match_sides(tpc_ctx* c, const int32_t* trk_off, const int32_t* t
             const int32_t* n_list = need_off + n_tracks;
             tpc::LaunchCount{}, k_sides_compact<<<(unsigned)blocks, SIDES_T, 0, s>>>(n_tracks, n_tracks_dev, need,
                                                                                  need_off, list, ends);
-            tpc::LaunchCount{}, k_sides_fit<<<(unsigned)blocks, SIDES_T, 0, s>>>(trk_off, trk_hits, H, geo, P, list,
-                                                                             n_list, role, ends);
-            tpc::LaunchCount{}, k_sides_pairs<<<(unsigned)blocks, SIDES_T, 0, s>>>(
+            tpc::LaunchCount{}, k_sides_fit<<<(unsigned)wblocks, 32, 0, s>>>(trk_off, trk_hits, H, geo, P, list,
+                                                                          n_list, role, ends);
+            tpc::LaunchCount{}, k_sides_pairs<<<(unsigned)wblocks, 32, 0, s>>>(
                 trk_off, trk_hits, H, geo, P, S, cls, boff, blist, list, n_list, ends, cand, cand_cap, n_cand, st);
-            tpc::LaunchCount{}, k_sides_joint<<<(unsigned)cblocks, SIDES_T, 0, s>>>(
+            tpc::LaunchCount{}, k_sides_joint<<<(unsigned)wcblocks, 32, 0, s>>>(
                 trk_off, trk_hits, H, geo, P, S, ends, cand, cand_cap, n_cand, best);
             tpc::LaunchCount{}, k_sides_pick<<<(unsigned)cblocks, SIDES_T, 0, s>>>(
                 trk_off, trk_hits, H, geo, P, S, cand, cand_cap, n_cand, best, partner, t0, params6, cov6, chi2,
