@@ -1655,6 +1655,36 @@ __global__ void k_fill_u32(uint32_t* p, int64_t n, uint32_t v) {
         p[i] = v;
 }
 
+// The per-call initialisations of a find in one launch: a table of (array,
+// count, value, 4- or 8-byte element); each entry owns a run of blocks of
+// MF_PER elements each.
+constexpr int MF_T = 256, MF_PER = MF_T * 16, MF_MAX = 24;
+struct FillDesc {
+    void* p;
+    int64_t n;
+    unsigned long long v;
+    int32_t w;     // element bytes: 4 or 8
+    int32_t blk0;  // first block of the entry
+};
+struct FillSet {
+    int32_t nd;
+    FillDesc d[MF_MAX];
+};
+__global__ void __launch_bounds__(MF_T) k_multi_fill(FillSet f) {
+    int k = 0;
+    while (k + 1 < f.nd && (int)blockIdx.x >= f.d[k + 1].blk0) ++k;
+    const FillDesc d = f.d[k];
+    const int64_t b0 = (int64_t)((int)blockIdx.x - d.blk0) * MF_PER;
+    const int64_t e = min(b0 + (int64_t)MF_PER, d.n);
+    if (d.w == 8) {
+        auto* q = static_cast<unsigned long long*>(d.p);
+        for (int64_t i = b0 + threadIdx.x; i < e; i += MF_T) q[i] = d.v;
+    } else {
+        auto* q = static_cast<uint32_t*>(d.p);
+        for (int64_t i = b0 + threadIdx.x; i < e; i += MF_T) q[i] = (uint32_t)d.v;
+    }
+}
+
 }  // namespace
 
 #define TPC_TRY(x)                                  \
@@ -1675,12 +1705,43 @@ cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hi
     int32_t* scan_tmp = W.at<int32_t>(L.scan_a);
 
     c->mark(0, s);
+    // Every per-call initialisation in one launch, ahead of the kernels: the
     // per-call counters (the status word and the FP64 count are cumulative)
-    TPC_TRY(fill_i32(st + ST_NSEG, ST_NTRACKS - ST_NSEG + 1, 0, s));
-    TPC_TRY(fill_i32(st + ST_MATCH_LIVE, ST_NB_Q2 + 1 - ST_MATCH_LIVE, 0, s));
+    // and each buffer that a later stage fills before use (none of them is
+    // written before its stage; the first up-claim table is not here: it
+    // serves as a neighbour queue before the claims)
+    {
+        FillSet f{};
+        int blk = 0;
+        auto add = [&](void* ptr, int64_t cnt, unsigned long long v, int w) {
+            if (cnt <= 0) return;
+            f.d[f.nd] = FillDesc{ptr, cnt, v, w, blk};
+            blk += (int)((cnt + MF_PER - 1) / MF_PER);
+            ++f.nd;
+        };
+        add(st + ST_NSEG, ST_NTRACKS - ST_NSEG + 1, 0, 4);
+        add(st + ST_MATCH_LIVE, ST_NB_Q2 + 1 - ST_MATCH_LIVE, 0, 4);
+        add(W.at<uint32_t>(L.g_zmin_u), G, 0xffffffffu, 4);
+        add(W.at<uint32_t>(L.g_zmax_u), G, 0u, 4);
+        add(W.at<int32_t>(L.cell_cnt), L.K + 1, 0, 4);
+        add(W.at<unsigned long long>(L.claim_dn), n, KEY_MAX, 8);
+        add(W.at<int32_t>(L.link_dn), n, 0xffffffffu, 4);
+        add(W.at<int32_t>(L.link_up), n, 0xffffffffu, 4);
+        add(W.at<unsigned long long>(L.owner), n, KEY_MAX, 8);
+        add(W.at<int32_t>(L.grp_tl_cnt), L.KT + 1, 0, 4);
+        add(W.at<int32_t>(L.grp_tl_cur), L.KT, 0, 4);
+        add(W.at<int32_t>(L.cand_n), L.S, 0, 4);
+        add(W.at<int32_t>(L.nxt), L.S, 0xffffffffu, 4);
+        add(W.at<int32_t>(L.prv), L.S, 0xffffffffu, 4);
+        add(W.at<unsigned long long>(L.best_a), L.S, KEY_MAX, 8);
+        add(W.at<unsigned long long>(L.best_b), L.S, KEY_MAX, 8);
+        add(W.at<int32_t>(L.trk_flag), n, 0, 4);
+        add(W.at<int32_t>(L.len_by_rank), track_cap, 0, 4);
+        add(toc, n, 0xffffffffu, 4);
+        tpc::LaunchCount{}, k_multi_fill<<<(unsigned)std::max(blk, 1), MF_T, 0, s>>>(f);
+        TPC_TRY(cudaGetLastError());
+    }
     // S1: z range per group, cells, histogram, scan, scatter
-    tpc::LaunchCount{}, k_fill_u32<<<grid_for(G), TPB, 0, s>>>(W.at<uint32_t>(L.g_zmin_u), G, 0xffffffffu);
-    tpc::LaunchCount{}, k_fill_u32<<<grid_for(G), TPB, 0, s>>>(W.at<uint32_t>(L.g_zmax_u), G, 0u);
     int32_t* grp_of = W.at<int32_t>(L.d2);  // group of every input cluster (d2 is free in S1)
     tpc::LaunchCount{}, k_zrange<<<grid_for(n), TPB, 0, s>>>(c->z, n, c->evt_sector_off, G, W.at<uint32_t>(L.g_zmin_u),
                                          W.at<uint32_t>(L.g_zmax_u), grp_of, st);
@@ -1689,7 +1750,6 @@ cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hi
                                W.at<int32_t>(L.g_nz), W.at<int32_t>(L.g_kbase), L.K, st);
     Cells cells{W.at<float>(L.g_zmin), W.at<float>(L.g_inv), W.at<int32_t>(L.g_nz),
                 W.at<int32_t>(L.g_kbase), W.at<int32_t>(L.cell_off)};
-    TPC_TRY(fill_i32(W.at<int32_t>(L.cell_cnt), L.K + 1, 0, s));
     tpc::LaunchCount{}, k_hist<<<grid_for(n), TPB, 0, s>>>(c->y, c->z, c->row, n, grp_of, cells, geo,
                                        W.at<int32_t>(L.cell_cnt), W.at<int32_t>(L.key_in),
                                        W.at<int32_t>(L.slot_in), L.K, st);
@@ -1734,12 +1794,9 @@ cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hi
     auto* claim_up = W.at<unsigned long long>(L.claim_up);
     auto* claim_dn = W.at<unsigned long long>(L.claim_dn);
     tpc::LaunchCount{}, k_fill_u64<<<grid_for(n), TPB, 0, s>>>(claim_up, n, KEY_MAX);
-    tpc::LaunchCount{}, k_fill_u64<<<grid_for(n), TPB, 0, s>>>(claim_dn, n, KEY_MAX);
     tpc::LaunchCount{}, k_claims<<<grid_for(n), TPB, 0, s>>>(n, cdn, cup, d2, orig, claim_up, claim_dn, st);
     int32_t* ldn = W.at<int32_t>(L.link_dn);
     int32_t* lup = W.at<int32_t>(L.link_up);
-    TPC_TRY(fill_i32(ldn, n, -1, s));
-    TPC_TRY(fill_i32(lup, n, -1, s));
     tpc::LaunchCount{}, k_links<<<grid_for(n), TPB, 0, s>>>(n, cdn, cup, d2, orig, claim_up, claim_dn, ldn, lup, st);
 
     c->mark(3, s);
@@ -1777,7 +1834,6 @@ cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hi
         nullptr, tile);
     c->mark(5, s);
     auto* owner = W.at<unsigned long long>(L.owner);
-    tpc::LaunchCount{}, k_fill_u64<<<grid_for(n), TPB, 0, s>>>(owner, n, KEY_MAX);
     tpc::LaunchCount{}, k_owner<<<grid_for(L.S * NROW), TPB, 0, s>>>(tl_rowhit, tl_key, L.S, st, owner);
     int32_t* grp_cnt = W.at<int32_t>(L.grp_tl_cnt);
     TlBins tb{W.at<float>(L.tb_zmin), W.at<float>(L.tb_inv), W.at<int32_t>(L.tb_nb), W.at<int32_t>(L.tb_base)};
@@ -1785,7 +1841,6 @@ cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hi
                                                    W.at<uint32_t>(L.g_zmax_u), W.at<float>(L.tb_zmin),
                                                    W.at<float>(L.tb_inv), W.at<int32_t>(L.tb_nb),
                                                    W.at<int32_t>(L.tb_base), st);
-    TPC_TRY(fill_i32(grp_cnt, L.KT + 1, 0, s));
     tpc::LaunchCount{}, k_keep<<<grid_for(L.S * 32, 128), 128, 0, s>>>(tl_rowhit, tl_key, owner, W.at<int32_t>(L.seg_grp), yzb,
                                  orig, p.n_seg, L.S, st, W.at<int32_t>(L.tl_keep),
                                  W.at<int32_t>(L.tl_canon), W.at<int32_t>(L.tl_rmin),
@@ -1793,7 +1848,6 @@ cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hi
                                  W.at<float>(L.tl_zout), W.at<int32_t>(L.tl_ok), grp_cnt, tb,
                                  W.at<int32_t>(L.tl_binkey), L.KT, tl_mask);
     TPC_TRY(scan_i32(grp_cnt, W.at<int32_t>(L.grp_tl_off), L.KT, scan_tmp, s));
-    TPC_TRY(fill_i32(W.at<int32_t>(L.grp_tl_cur), L.KT, 0, s));
     tpc::LaunchCount{}, k_tl_scatter<<<sgrid, 128, 0, s>>>(W.at<int32_t>(L.tl_keep), W.at<int32_t>(L.seg_grp),
                                        W.at<int32_t>(L.grp_tl_off), L.S, st,
                                        W.at<int32_t>(L.grp_tl_cur), W.at<int32_t>(L.tl_sorted),
@@ -1811,7 +1865,6 @@ cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hi
              (double)p.chi2_merge, (float)(KAPPA * (double)p.bz), p.snp_max, (float)(162.0 / 151.0),
              L.KT, L.S};
     // cand_n of slots that are not kept must read 0 for the matching
-    TPC_TRY(fill_i32(W.at<int32_t>(L.cand_n), L.S, 0, s));
     tpc::LaunchCount{}, k_merge_cand<<<grid_for(L.S * 32, 256), 256, 0, s>>>(
         W.at<int32_t>(L.seg_grp), W.at<float>(L.tl_state), W.at<int32_t>(L.grp_tl_off),
         W.at<int4>(L.gs_meta), geo, mp, st, W.at<int32_t>(L.cand_n), W.at<int32_t>(L.cand_a),
@@ -1819,32 +1872,25 @@ cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hi
     c->mark(7, s);
     int32_t* nxt = W.at<int32_t>(L.nxt);
     int32_t* prv = W.at<int32_t>(L.prv);
-    TPC_TRY(fill_i32(nxt, L.S, -1, s));
-    TPC_TRY(fill_i32(prv, L.S, -1, s));
     auto* best_a = W.at<unsigned long long>(L.best_a);
     auto* best_b = W.at<unsigned long long>(L.best_b);
-    tpc::LaunchCount{}, k_fill_u64<<<grid_for(L.S), TPB, 0, s>>>(best_a, L.S, KEY_MAX);
-    tpc::LaunchCount{}, k_fill_u64<<<grid_for(L.S), TPB, 0, s>>>(best_b, L.S, KEY_MAX);
     tpc::LaunchCount{}, k_match<<<MATCH_CTAS, 1024, 0, s>>>(W.at<int32_t>(L.cand_n), W.at<int32_t>(L.cand_a), W.at<float>(L.cand_c2),
                                W.at<int32_t>(L.tl_canon), L.S, st, best_a, best_b, nxt, prv,
                                W.at<int32_t>(L.match_act));
     c->mark(8, s);
     // output: canonical order by smallest input index
     int32_t* flag = W.at<int32_t>(L.trk_flag);
-    TPC_TRY(fill_i32(flag, n, 0, s));
     tpc::LaunchCount{}, k_track_heads<<<grid_for(L.S * 32, 128), 128, 0, s>>>(W.at<int32_t>(L.tl_keep), nxt, prv, W.at<int32_t>(L.tl_canon),
                                         tl_rowhit, p.n_min, L.S, st, flag, W.at<int32_t>(L.trk_len_at),
                                         W.at<int32_t>(L.trk_head_at));
     int32_t* rank = W.at<int32_t>(L.trk_rank);
     TPC_TRY(scan_i32(flag, rank, n, scan_tmp, s));
     int32_t* len_by_rank = W.at<int32_t>(L.len_by_rank);
-    TPC_TRY(fill_i32(len_by_rank, track_cap, 0, s));
     int32_t* head_by_rank = W.at<int32_t>(L.head_by_rank);
     tpc::LaunchCount{}, k_track_len<<<grid_for(n), TPB, 0, s>>>(n, flag, rank, W.at<int32_t>(L.trk_len_at),
                                             W.at<int32_t>(L.trk_head_at), track_cap, len_by_rank,
                                             head_by_rank, st, n_tracks_dev);
     TPC_TRY(scan_i32(len_by_rank, trk_off, track_cap, scan_tmp, s));
-    TPC_TRY(fill_i32(toc, n, -1, s));
     tpc::LaunchCount{}, k_track_write<<<grid_for((int64_t)track_cap * 32), TPB, 0, s>>>(
         st, track_cap, head_by_rank, prv, tl_rowhit, orig, trk_off, n, toc, trk_hits, st);
     c->mark(9, s);

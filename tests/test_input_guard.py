@@ -17,7 +17,7 @@ CSRC = os.path.join(ROOT, "paper_2412_13755_gb300", "csrc")
 # kernels that touch only buffers sized on the host (fills, scans, tables,
 # the status copy) and the validation itself
 UNGUARDED = {"k_fill_u64", "k_fill_u32", "k_fill_i32", "k_scan_reduce", "k_scan_top", "k_scan_down",
-             "k_init_geo", "k_validate", "k_adj_tables", "k_zero_f64", "k_copy_status"}
+             "k_init_geo", "k_validate", "k_adj_tables", "k_zero_f64", "k_copy_status", "k_multi_fill"}
 
 
 def kernels(path):
