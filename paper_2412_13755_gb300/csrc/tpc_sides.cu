@@ -285,8 +285,6 @@ __global__ void __launch_bounds__(SIDES_T) k_sides_joint(const int32_t* __restri
 }
 
 __global__ void __launch_bounds__(SIDES_T) k_sides_pick(const int32_t* __restrict__ trk_off,
-                                                       const int32_t* __restrict__ trk_hits, HitSrc H,
-                                                       const Geo* __restrict__ geo, ExPrm P, SidesPrm S,
                                                        const SideCand* __restrict__ cand, int32_t cap,
                                                        const int32_t* __restrict__ n_cand,
                                                        const unsigned long long* __restrict__ best,
@@ -423,8 +421,7 @@ cudaError_t run_match_sides(tpc_ctx* c, const int32_t* trk_off, const int32_t* t
             tpc::LaunchCount{}, k_sides_joint<<<(unsigned)wcblocks, 32, 0, s>>>(
                 trk_off, trk_hits, H, geo, P, S, ends, cand, cand_cap, n_cand, best);
             tpc::LaunchCount{}, k_sides_pick<<<(unsigned)cblocks, SIDES_T, 0, s>>>(
-                trk_off, trk_hits, H, geo, P, S, cand, cand_cap, n_cand, best, partner, t0, params6, cov6, chi2,
-                ndf, dchi2, n_pairs_dev);
+                trk_off, cand, cand_cap, n_cand, best, partner, t0, params6, cov6, chi2, ndf, dchi2, n_pairs_dev);
             e = cudaGetLastError();
         }
     }
