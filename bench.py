@@ -43,6 +43,9 @@ PATH_BYTES_PER_CLUSTER = 78.7
 # the fused lower bound: read y, z, row once (10), write each cluster's track
 # (4) and the per-track fit outputs (88 B per ~120 clusters, 0.7)
 PATH_FUSED_BYTES_PER_CLUSTER = 14.7
+# the neighbour stage alone: binned (y, z) read (8), the two choices (8) and
+# D^2 (4) written
+NB_BYTES_PER_CLUSTER = 20.0
 FIT_BYTES_PER_HIT = 14.0                # hit index (4) + y, z (8) + row (2)
 FIT_BYTES_PER_TRACK = 88.0              # 5 params + 15 cov + chi2 + ndf
 
@@ -432,7 +435,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-profiler", action="store_true", help="(kept for compatibility)")
     ap.add_argument("--pileup", action="store_true",
-                    help="also time the 100-collision pile-up frame (~1.5e8 clusters)")
+                    help="(kept for compatibility: the pile-up frame is timed by default)")
+    ap.add_argument("--no-pileup", action="store_true",
+                    help="skip the 100-collision pile-up frame (~1.8e8 clusters)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-vs-plain and adjoint measurements")
     ap.add_argument("--only", choices=sorted(EXTRA_NAMES),
@@ -866,6 +871,15 @@ def run_ours(args):
                           "fused_bytes_per_cluster": PATH_FUSED_BYTES_PER_CLUSTER,
                           "fused_frac": value * PATH_FUSED_BYTES_PER_CLUSTER / 1e9 / hbm_peak,
                           "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)"},
+        "neighbours_roofline": {
+            "bound": "hbm", "bytes_per_cluster": NB_BYTES_PER_CLUSTER,
+            "achieved": n * NB_BYTES_PER_CLUSTER / (per_step.get("neighbours", 0.0) * 1e-3) / 1e9
+            if per_step.get("neighbours", 0.0) > 0 else None,
+            "peak": hbm_peak, "unit": "GB/s",
+            "frac": n * NB_BYTES_PER_CLUSTER / (per_step.get("neighbours", 0.0) * 1e-3) / 1e9 / hbm_peak
+            if per_step.get("neighbours", 0.0) > 0 else None,
+            "stage_ms": per_step.get("neighbours", 0.0),
+            "kernels": "k_neighbours_first, k_neighbours_sub, k_neighbours_warp (one stage)"},
         "status": {"fp64_updates": st.n_fp64_updates, "segments": st.n_segments,
                    "tracklets": st.n_tracklets, "merges": st.n_merges},
     }
@@ -881,7 +895,7 @@ def run_ours(args):
                    ("field_adjoint", lambda: field_adjoint_bench(torch, tpc, dev, max(3, args.steps // 4))),
                    ("kf_variants", lambda: kf_variants_bench(torch, tpc, dev, max(3, args.steps // 4))),
                    ("sides", lambda: sides_bench(torch, tpc, dev, max(3, args.steps // 4)))]
-    if args.pileup:
+    if not args.no_extras and not args.no_pileup:
         extras.append(("pileup_frame", lambda: pileup_bench(torch, tpc, dev, 2)))
     for name, fn in extras:
         try:
