@@ -16,7 +16,19 @@
 //       derivative of the fit as computed (forward-mode dual numbers).
 // Floating point that decides an integer in S2 (window cuts, D^2 and its
 // comparisons) is evaluated in FP32 with one rounding per operation, the
-// precision the GPU kernel decides in; everything else is FP64.
+// precision the GPU kernel decides in; everything else is FP64 (an FP64
+// diagnostic mode of S2 measures how many decisions that changes).
+//
+// Pins (tests/test_oracle_*.py) tie each part to something other than this
+// file: the transport to the generator's global-frame crossings and to
+// central differences; the fit to closed-form least squares in the linear
+// case and to unit-width pulls; the seed to exact helix points; extension
+// and merging to noise-free tracks and to the least-squares chi2 identity;
+// the whole find to brute-force chain enumeration on tiny events; the
+// gradients to central differences.  Parity unpinned beyond those cases
+// and determinism: the tie-break orders of S2, S3b and S4, the greedy merge
+// order and the tracklet ownership rule, which are heuristic rules with no
+// closed form (pinned only by their stated definitions).
 #include "tpc_oracle.h"
 
 #include <algorithm>
