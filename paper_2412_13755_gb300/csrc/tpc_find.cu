@@ -1175,7 +1175,9 @@ __global__ void k_owner(const int32_t* __restrict__ tl_rowhit, const unsigned lo
 
 // keep tracklets owning >= n_seg clusters (hits they do not own are
 // cleared); the refits of the kept ones run in k_tracklet_lanes.  One warp
-// per slot, the lanes over the rows.
+// per slot, the lanes over the rows: the row table, the owners and the
+// canonical ids of the five 32-row rounds are each loaded in one batch, and
+// a warp counts its kept slots in a register (one atomic per warp).
 __global__ void k_keep(int32_t* tl_rowhit, const unsigned long long* __restrict__ tl_key,
                        const unsigned long long* __restrict__ owner, const int32_t* __restrict__ seg_grp,
                        const float2* __restrict__ yzb, const int32_t* __restrict__ orig, int n_seg,
@@ -1188,28 +1190,31 @@ __global__ void k_keep(int32_t* tl_rowhit, const unsigned long long* __restrict_
     const int lane = threadIdx.x & 31;
     const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    int kept = 0;  // slots kept by this warp (lane 0)
     for (int64_t s = w0; s < nseg; s += nw) {
         int32_t* hit = tl_rowhit + s * NROW;
         const unsigned long long key = tl_key[s];
-        int n = 0, rmin = NROW, rmax = -1;
+        int h[MASK_W];
+#pragma unroll
+        for (int w = 0; w < MASK_W; ++w) {
+            const int r = 32 * w + lane;
+            h[w] = r < NROW ? hit[r] : -1;
+        }
+        bool own[MASK_W];
+#pragma unroll
+        for (int w = 0; w < MASK_W; ++w) own[w] = h[w] >= 0 && owner[h[w]] == key;
         int32_t canon = 0x7fffffff;
+#pragma unroll
+        for (int w = 0; w < MASK_W; ++w) {
+            if (own[w]) canon = min(canon, orig[h[w]]);
+            else if (h[w] >= 0) hit[32 * w + lane] = -1;
+        }
+        int n = 0, rmin = NROW, rmax = -1;
         uint32_t mw[MASK_W];
 #pragma unroll
         for (int w = 0; w < MASK_W; ++w) {
             const int r0 = 32 * w;
-            const int r = r0 + lane;
-            bool own = false;
-            if (r < NROW) {
-                const int h = hit[r];
-                if (h >= 0) {
-                    if (owner[h] != key) hit[r] = -1;
-                    else {
-                        own = true;
-                        canon = min(canon, orig[h]);
-                    }
-                }
-            }
-            const unsigned m = __ballot_sync(0xffffffffu, own);
+            const unsigned m = __ballot_sync(0xffffffffu, own[w]);
             mw[w] = m;
             if (m) {
                 n += __popc(m);
@@ -1218,6 +1223,15 @@ __global__ void k_keep(int32_t* tl_rowhit, const unsigned long long* __restrict_
             }
         }
         canon = __reduce_min_sync(0xffffffffu, canon);
+        // the innermost and outermost kept hits, from the lanes holding them
+        int hin_w = h[0], hout_w = h[0];
+#pragma unroll
+        for (int w = 1; w < MASK_W; ++w) {
+            if ((rmin >> 5) == w) hin_w = h[w];
+            if ((rmax >> 5) == w) hout_w = h[w];
+        }
+        const int h_in = __shfl_sync(0xffffffffu, hin_w, rmin & 31);
+        const int h_out = __shfl_sync(0xffffffffu, hout_w, rmax & 31);
         if (lane != 0) continue;
         tl_ok[s] = 0;
         if (n < n_seg) {
@@ -1231,17 +1245,19 @@ __global__ void k_keep(int32_t* tl_rowhit, const unsigned long long* __restrict_
         tl_canon[s] = canon;
         tl_rmin[s] = rmin;
         tl_rmax[s] = rmax;
-        tl_zin[s] = yzb[hit[rmin]].y;
-        tl_zout[s] = yzb[hit[rmax]].y;
-        const int bkey = tb.base[g] + (rmax / MRB) * tb.nb[g] + tl_bin(tb, g, yzb[hit[rmax]].y);
+        const float zin = yzb[h_in].y, zout = yzb[h_out].y;
+        tl_zin[s] = zin;
+        tl_zout[s] = zout;
+        const int bkey = tb.base[g] + (rmax / MRB) * tb.nb[g] + tl_bin(tb, g, zout);
         if (!in_range(bkey, KT, st, 301)) {
             tl_keep[s] = 0;
             continue;
         }
         tl_binkey[s] = bkey;
-        atomicAdd(&st[ST_NTL], 1);
+        ++kept;
         atomicAdd(&grp_tl_cnt[bkey], 1);
     }
+    if (lane == 0 && kept > 0) atomicAdd(&st[ST_NTL], kept);
 }
 
 __global__ void k_tl_scatter(const int32_t* __restrict__ tl_keep, const int32_t* __restrict__ seg_grp,
