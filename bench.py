@@ -438,6 +438,9 @@ def parse():
                     help="(kept for compatibility: the pile-up frame is timed by default)")
     ap.add_argument("--no-pileup", action="store_true",
                     help="skip the 100-collision pile-up frame (~1.8e8 clusters)")
+    ap.add_argument("--tune", default="",
+                    help="LANE_BLOCKS_PER_SM,LANE_TILE,NB_SUB_LANES: use this tuning of the central "
+                         "event instead of autotuning it (for profiler runs)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-vs-plain and adjoint measurements")
     ap.add_argument("--only", choices=sorted(EXTRA_NAMES),
@@ -676,7 +679,15 @@ def run_ours(args):
     # the work-queue tiles tuned on this event, then the whole step (load,
     # find, fit) recorded once as the library's CUDA graph: the timed steps
     # replay it, as a server does for every event of a fixed-size stream
-    tune = tr.autotune(out=find_out)
+    if args.tune:
+        # a fixed tuning (for profiler runs, where the autotuner's timings
+        # would be those of the profiler)
+        lb, tile, nb = (int(v) for v in args.tune.split(","))
+        tune = tpc.Tune()
+        tune.lane_blocks_per_sm, tune.lane_tile, tune.nb_sub_lanes = lb, tile, nb
+        tr.set_tune(tune)
+    else:
+        tune = tr.autotune(out=find_out)
     # stage events on at capture: they become event nodes of the graph, so
     # each timed replay carries its own stage times
     tr.stage_timing(True)
