@@ -385,6 +385,33 @@ def field_adjoint_bench(torch, tpc, dev, steps):
                                  "(the reverse step not counted: a lower bound)"}}
 
 
+def fit_precision_bench(torch, tr, find_out, track_cap, dev, steps):
+    """The central event's found tracks fitted by the two precision modes of
+    the fit: float-float covariance (tpc_fit_tracks, the path's fit) and FP32
+    covariance with FP64 redos of cancelling updates (tpc_fit_tracks_fp32);
+    CUDA events around each launch, after warm-up."""
+    T = int(find_out[3].item())
+    out = (torch.empty(max(T, 1), 5, dtype=torch.float32, device=dev),
+           torch.empty(max(T, 1), 15, dtype=torch.float32, device=dev),
+           torch.empty(max(T, 1), dtype=torch.float32, device=dev),
+           torch.empty(max(T, 1), dtype=torch.int32, device=dev))
+    res = {"tracks": T}
+    for name, prec in (("float_float_ms", "ff"), ("fp32_fp64_redo_ms", "fp32")):
+        for _ in range(3):
+            tr.fit(find_out[1], find_out[2], T, out=out, precision=prec)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            tr.fit(find_out[1], find_out[2], T, out=out, precision=prec)
+        e1.record()
+        torch.cuda.synchronize()
+        res[name] = e0.elapsed_time(e1) / steps
+    tr.check()
+    res["parity_bars"] = "float-float: 1e-5 of the FP64 oracle; FP32 with FP64 redos: 1e-4 (tests/test_gpu_parity.py)"
+    return res
+
+
 def clusterize_bench(torch, tpc, dev, steps, ev):
     """NEXT-2: clusterization of the central event's pad-time digits
     (36 x 152 planes x 512 time bins x 160 pads, u16: 0.9 GB, larger than
@@ -905,7 +932,9 @@ def run_ours(args):
                    ("clusterize", lambda: clusterize_bench(torch, tpc, dev, max(3, args.steps // 2), ev)),
                    ("field_adjoint", lambda: field_adjoint_bench(torch, tpc, dev, max(3, args.steps // 4))),
                    ("kf_variants", lambda: kf_variants_bench(torch, tpc, dev, max(3, args.steps // 4))),
-                   ("sides", lambda: sides_bench(torch, tpc, dev, max(3, args.steps // 4)))]
+                   ("sides", lambda: sides_bench(torch, tpc, dev, max(3, args.steps // 4))),
+                   ("fit_precision", lambda: fit_precision_bench(torch, tr, find_out, track_cap, dev,
+                                                                 max(3, args.steps // 2)))]
     if not args.no_extras and not args.no_pileup:
         extras.append(("pileup_frame", lambda: pileup_bench(torch, tpc, dev, 2)))
     for name, fn in extras:

@@ -74,9 +74,9 @@ typedef struct {
     float seed_snp_max;        /* clamp of the seed |sin phi|                */
     float seed_qpt_max;        /* clamp of the seed |q/pT| (c/GeV)           */
     float snp_max;             /* transport fails when |sin phi| reaches it  */
-    float fp64_ratio;          /* tracklet building: redo an update in FP64
-                                  when a posterior variance drops below
-                                  fp64_ratio x prior                         */
+    float fp64_ratio;          /* tracklet building and tpc_fit_tracks_fp32:
+                                  redo an update in FP64 when a posterior
+                                  variance drops below fp64_ratio x prior    */
     float fp64_det;            /* ... or det S <= fp64_det S00 S11           */
     float fp64_weak_qpt;       /* reserved (not read): tpc_fit_tracks keeps
                                   its covariance in float-float for every
@@ -186,6 +186,18 @@ tpc_status tpc_find_tracks(tpc_ctx* ctx, int32_t* track_of_cluster, int32_t* trk
 tpc_status tpc_fit_tracks(tpc_ctx* ctx, const int32_t* trk_off, const int32_t* trk_hits,
                           int32_t n_tracks, const int32_t* n_tracks_dev, float* params,
                           float* cov, float* chi2, int32_t* ndf, tpc_stream_t stream);
+
+/* S5 with the precision pattern of the tracklet lanes instead of
+ * float-float: the same inputs, outputs and fit as tpc_fit_tracks (Sec. 4.2
+ * names the TPC track fit as part of the GPU reconstruction), with the
+ * covariance in FP32 and an update redone in FP64 when it cancels (a
+ * posterior variance below fp64_ratio x its prior, or det S <= fp64_det S00
+ * S11); each redo is counted in tpc_stats.n_fp64_updates.  Faster than
+ * tpc_fit_tracks, with parameters within about 1e-4 of an FP64 fit instead
+ * of 1e-5. */
+tpc_status tpc_fit_tracks_fp32(tpc_ctx* ctx, const int32_t* trk_off, const int32_t* trk_hits,
+                               int32_t n_tracks, const int32_t* n_tracks_dev, float* params,
+                               float* cov, float* chi2, int32_t* ndf, tpc_stream_t stream);
 
 /* S6: alignment chi2 and gradient.  align[216] (device FP64) holds per-sector
  * corrections (dx, dy, dz, a, b, g): a cluster's corrected position in its

@@ -296,6 +296,20 @@ tpc_status tpc_fit_tracks(tpc_ctx* c, const int32_t* trk_off, const int32_t* trk
     return TPC_OK;
 }
 
+tpc_status tpc_fit_tracks_fp32(tpc_ctx* c, const int32_t* trk_off, const int32_t* trk_hits,
+                               int32_t n_tracks, const int32_t* n_tracks_dev, float* params, float* cov,
+                               float* chi2, int32_t* ndf, tpc_stream_t stream) {
+    if (!c) return TPC_ERR_ARG;
+    if (!c->have_ws || !c->have_clusters) return fail(c, TPC_ERR_STATE, "no workspace or clusters");
+    if (n_tracks < 0 || (n_tracks > 0 && (!trk_off || !trk_hits || !params || !cov || !chi2 || !ndf)))
+        return fail(c, TPC_ERR_ARG, "tpc_fit_tracks_fp32: bad argument");
+    if (n_tracks > c->ws.L.T - 1) return fail(c, TPC_ERR_CAPACITY, "tpc_fit_tracks_fp32: too many tracks");
+    cudaError_t e = run_fit32(c, trk_off, trk_hits, n_tracks, n_tracks_dev, params, cov, chi2, ndf,
+                              (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "tpc_fit_tracks_fp32");
+    return TPC_OK;
+}
+
 tpc_status tpc_fit_tracks_ex(tpc_ctx* c, const int32_t* trk_off, const int32_t* trk_hits, int32_t n_tracks,
                              const int32_t* n_tracks_dev, const tpc_fit_options* o, float* params, float* cov,
                              float* chi2, int32_t* ndf, double* smoothed, tpc_stream_t stream) {

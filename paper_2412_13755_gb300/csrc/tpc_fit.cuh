@@ -73,4 +73,56 @@ TPC_HD bool fit_track(const int32_t* h, int n, const float* __restrict__ y,
     return ok;
 }
 
+// The same fit with the covariance in FP32 and an update redone in FP64
+// when it cancels (a posterior variance below fp64_ratio x its prior, or det
+// S <= fp64_det S00 S11; kf_update counts each redo in *n_fp64): the
+// precision pattern of the tracklet lanes, where float-float is not carried.
+// s.C holds the covariance at the last cluster.
+TPC_HD bool fit_track_f32(const int32_t* h, int n, const float* __restrict__ y,
+                          const float* __restrict__ z, const uint16_t* __restrict__ row,
+                          const int64_t* __restrict__ evt_off, int G, const Geo* __restrict__ geo,
+                          FitPrm P, float fp64_ratio, float fp64_det, int* n_fp64, KF& s, NSum& chi2) {
+    bool ok = n >= 3;
+    if (ok) {
+        int rows[3], secs[3];
+        float ys[3], zs[3];
+        const int pick[3] = {0, n / 2, n - 1};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const int c = h[pick[k]];
+            rows[k] = row[c];
+            secs[k] = group_of(evt_off, G, c) % NSEC;
+            ys[k] = y[c];
+            zs[k] = z[c];
+        }
+        kf_seed(s, rows, secs, ys, zs, true, geo, P.bz, P.seed_snp, P.seed_qpt, P.prior);
+        int g = -1;
+        int64_t gb = 0, ge = 0;
+        // the next hit's index and data are read a step ahead
+        int cn = h[0];
+        int rn = row[cn];
+        float yn = y[cn], zn = z[cn];
+        for (int j = 0; j < n && ok; ++j) {
+            const int c = cn, rc = rn;
+            const float yc = yn, zc = zn;
+            if (j + 1 < n) cn = h[j + 1];
+            if (c < gb || c >= ge) {
+                g = group_of(evt_off, G, c);
+                gb = evt_off[g];
+                ge = evt_off[g + 1];
+            }
+            MoveJ mj;
+            mj.valid = false;
+            ok = kf_move<float>(s, geo->row_xd[rc], g % NSEC, geo, P.kb, P.snp_max, &mj);
+            if (j + 1 < n) {
+                rn = row[cn];
+                yn = y[cn];
+                zn = z[cn];
+            }
+            if (ok) chi2.add(kf_update(s, yc, zc, P.sy2, P.sz2, fp64_ratio, fp64_det, n_fp64, &mj));
+        }
+    }
+    return ok;
+}
+
 }  // namespace tpc

@@ -147,6 +147,9 @@ cudaError_t run_find(tpc_ctx* c, int32_t* toc, int32_t* trk_off, int32_t* trk_hi
 cudaError_t run_fit(tpc_ctx* c, const int32_t* trk_off, const int32_t* trk_hits, int32_t n_tracks,
                     const int32_t* n_tracks_dev, float* params, float* cov, float* chi2,
                     int32_t* ndf, cudaStream_t s);
+cudaError_t run_fit32(tpc_ctx* c, const int32_t* trk_off, const int32_t* trk_hits, int32_t n_tracks,
+                      const int32_t* n_tracks_dev, float* params, float* cov, float* chi2,
+                      int32_t* ndf, cudaStream_t s);
 cudaError_t run_fit_ex(tpc_ctx* c, const int32_t* trk_off, const int32_t* trk_hits, int32_t n_tracks,
                        const int32_t* n_tracks_dev, const tpc_fit_options* o, float* params, float* cov,
                        float* chi2, int32_t* ndf, double* smoothed, cudaStream_t s);

@@ -25,7 +25,7 @@ EXPORTS = ("tpc_default_params", "tpc_create", "tpc_destroy", "tpc_workspace_byt
            "tpc_stage_timing", "tpc_stage_times", "tpc_find_tracks_noalloc", "tpc_set_tune",
            "tpc_autotune", "tpc_field_voxels", "tpc_fit_adjoint_field", "tpc_track_batch",
            "tpc_graph_capture", "tpc_graph_launch", "tpc_fit_tracks_ex", "tpc_cluster_workspace_bytes",
-           "tpc_find_clusters", "tpc_sides_workspace_bytes", "tpc_match_sides")
+           "tpc_find_clusters", "tpc_sides_workspace_bytes", "tpc_match_sides", "tpc_fit_tracks_fp32")
 STAGE_NAMES = ("bin", "neighbours", "links", "chains", "tracklets", "select", "merge_cand",
                "match", "output", "fit", "adjoint", "find_total", "sides")
 
@@ -130,6 +130,7 @@ def load_library(build_if_missing: bool = True):
     lib.tpc_load_clusters.argtypes = [vp, vp, vp, vp, vp, i64, vp, i32, vp]
     lib.tpc_find_tracks.argtypes = [vp, vp, vp, vp, vp, i32, vp]
     lib.tpc_fit_tracks.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp, vp, vp]
+    lib.tpc_fit_tracks_fp32.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp, vp, vp]
     lib.tpc_fit_adjoint.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp]
     lib.tpc_get_stats.argtypes = [vp, vp, vp]
     lib.tpc_last_error.argtypes = [vp, C.c_char_p, sz]
@@ -312,7 +313,7 @@ def tpc_find_tracks(ctx, track_of_cluster, trk_off, trk_hits, n_tracks_dev, stre
 
 
 def tpc_fit_tracks(ctx, trk_off, trk_hits, n_tracks, n_tracks_dev, params, cov, chi2, ndf,
-                   stream=None):
+                   stream=None, what="tpc_fit_tracks"):
     _need(trk_off, torch.int32, "trk_off")
     _need(trk_hits, torch.int32, "trk_hits")
     for t, n in ((params, "params"), (cov, "cov"), (chi2, "chi2")):
@@ -320,11 +321,19 @@ def tpc_fit_tracks(ctx, trk_off, trk_hits, n_tracks, n_tracks_dev, params, cov, 
     _need(ndf, torch.int32, "ndf")
     if n_tracks_dev is not None:
         _need(n_tracks_dev, torch.int32, "n_tracks_dev")
-    check_fit_buffers(n_tracks, trk_off, params, cov, chi2, ndf)
-    rc = load_library().tpc_fit_tracks(ctx, _ptr(trk_off), _ptr(trk_hits), int(n_tracks),
-                                       _ptr(n_tracks_dev), _ptr(params), _ptr(cov), _ptr(chi2),
-                                       _ptr(ndf), _stream(stream))
-    _check(ctx, rc, "tpc_fit_tracks")
+    check_fit_buffers(n_tracks, trk_off, params, cov, chi2, ndf, what=what)
+    fn = getattr(load_library(), what)
+    rc = fn(ctx, _ptr(trk_off), _ptr(trk_hits), int(n_tracks), _ptr(n_tracks_dev), _ptr(params),
+            _ptr(cov), _ptr(chi2), _ptr(ndf), _stream(stream))
+    _check(ctx, rc, what)
+
+
+def tpc_fit_tracks_fp32(ctx, trk_off, trk_hits, n_tracks, n_tracks_dev, params, cov, chi2, ndf,
+                        stream=None):
+    """The fit with the covariance in FP32 and cancelling updates redone in
+    FP64 (same arguments as tpc_fit_tracks)."""
+    tpc_fit_tracks(ctx, trk_off, trk_hits, n_tracks, n_tracks_dev, params, cov, chi2, ndf,
+                   stream=stream, what="tpc_fit_tracks_fp32")
 
 
 def tpc_fit_tracks_ex(ctx, trk_off, trk_hits, n_tracks, n_tracks_dev, options, params, cov, chi2, ndf,
@@ -692,14 +701,20 @@ class Tracker:
         tpc_find_tracks(self.ctx, *out, stream=stream)
         return out
 
-    def fit(self, trk_off, trk_hits, n_tracks, n_tracks_dev=None, out=None, stream=None):
+    def fit(self, trk_off, trk_hits, n_tracks, n_tracks_dev=None, out=None, stream=None,
+            precision="ff"):
+        """precision "ff": float-float covariance (tpc_fit_tracks); "fp32":
+        FP32 covariance with FP64 redos (tpc_fit_tracks_fp32)."""
+        if precision not in ("ff", "fp32"):
+            raise ValueError(f"precision must be 'ff' or 'fp32', not {precision!r}")
         dev = self.device
         T = max(int(n_tracks), 1)
         out = out or (torch.empty(T, 5, dtype=torch.float32, device=dev),
                       torch.empty(T, 15, dtype=torch.float32, device=dev),
                       torch.empty(T, dtype=torch.float32, device=dev),
                       torch.empty(T, dtype=torch.int32, device=dev))
-        tpc_fit_tracks(self.ctx, trk_off, trk_hits, n_tracks, n_tracks_dev, *out, stream=stream)
+        fn = tpc_fit_tracks if precision == "ff" else tpc_fit_tracks_fp32
+        fn(self.ctx, trk_off, trk_hits, n_tracks, n_tracks_dev, *out, stream=stream)
         return out
 
     def fit_ex(self, trk_off, trk_hits, n_tracks, options=None, n_tracks_dev=None, smooth=False,

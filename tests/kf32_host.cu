@@ -1,8 +1,10 @@
-// The tracklet lanes' Kalman step (tpc_dev.cuh: kf_move<float> with the
-// covariance in FP32, kf_update with its FP64 redo of cancelling updates)
-// run over whole tracks on the host, from the fit's seed: reads a batch and
-// track lists from argv[1], writes every track's fit to argv[2], for
-// comparison with the FP64 oracle.  Host code only; no kernel is launched.
+// The FP32-covariance fit (tpc_fit.cuh: fit_track_f32, the per-track
+// function of tpc_fit_tracks_fp32 and the precision pattern of the tracklet
+// lanes: kf_move<float> with the covariance in FP32, kf_update with its FP64
+// redo of cancelling updates) run over whole tracks on the host: reads a
+// batch and track lists from argv[1], writes every track's fit to argv[2],
+// for comparison with the FP64 oracle.  Host code only; no kernel is
+// launched.
 //   input:  n, G, T (int64); y[n], z[n] (float); row[n] (uint16);
 //           evt_off[G+1] (int64); trk_off[T+1], trk_hits[...] (int32);
 //           sy2, sz2, snp_max, bz, seed_snp, seed_qpt, prior[5],
@@ -59,28 +61,8 @@ int main(int argc, char** argv) {
         const int32_t* h = hits.data() + b;
         KF s;
         NSum chi2;
-        bool ok = m >= 3;
-        if (ok) {
-            int rows[3], secs[3];
-            float ys[3], zs[3];
-            const int pick[3] = {0, m / 2, m - 1};
-            for (int k = 0; k < 3; ++k) {
-                const int c = h[pick[k]];
-                rows[k] = row[c];
-                secs[k] = group_of(off.data(), (int)G, c) % NSEC;
-                ys[k] = y[c];
-                zs[k] = z[c];
-            }
-            kf_seed(s, rows, secs, ys, zs, true, &geo, P.bz, P.seed_snp, P.seed_qpt, P.prior);
-            for (int j = 0; j < m && ok; ++j) {
-                const int c = h[j];
-                MoveJ mj;
-                mj.valid = false;
-                ok = kf_move<float>(s, geo.row_xd[row[c]], group_of(off.data(), (int)G, c) % NSEC, &geo, P.kb,
-                                    P.snp_max, &mj);
-                if (ok) chi2.add(kf_update(s, y[c], z[c], P.sy2, P.sz2, prm[11], prm[12], &n_fp64, &mj));
-            }
-        }
+        const bool ok = fit_track_f32(h, m, y.data(), z.data(), row.data(), off.data(), (int)G, &geo, P,
+                                      prm[11], prm[12], &n_fp64, s, chi2);
         float out[21] = {};
         int32_t ndf = -1;
         if (ok) {

@@ -120,6 +120,14 @@ def test_fit(stub):
         tpc.tpc_fit_tracks(CTX, i32(T), i32(100), T, None, f32(T, 5), f32(T, 15), f32(T), i32(T))
 
 
+def test_fit_fp32(stub):
+    T = 5
+    tpc.tpc_fit_tracks_fp32(CTX, i32(T + 1), i32(100), T, i32(1), f32(T, 5), f32(T, 15), f32(T), i32(T))
+    assert stub.calls[-1] == "tpc_fit_tracks_fp32"
+    with pytest.raises(ValueError, match="tpc_fit_tracks_fp32.*chi2"):
+        tpc.tpc_fit_tracks_fp32(CTX, i32(T + 1), i32(100), T, None, f32(T, 5), f32(T, 15), f32(T - 1), i32(T))
+
+
 def test_adjoint(stub):
     T = 9
     tpc.tpc_fit_adjoint(CTX, i32(T + 1), i32(100), T, f64(216), f64(1), f64(216))

@@ -114,7 +114,8 @@ def kf32_host(tmp_path_factory):
 
 @pytest.mark.parametrize("kind", ["found", "truth"])
 def test_fp32_kalman_step_on_host(orc, kf32_host, tmp_path, kind):
-    """The tracklet lanes' Kalman step (FP32 covariance, FP64 redo of
+    """fit_track_f32 (the per-track function of tpc_fit_tracks_fp32 and the
+    precision pattern of the tracklet lanes: FP32 covariance, FP64 redo of
     cancelling updates) over whole tracks from the fit's seed, against the
     oracle: the same tracks fail, parameters within 1e-4 max(|p_i|, s_i)
     (FP32 covariance, an order above the float-float fit's bar; measured

@@ -145,12 +145,13 @@ def test_find_multi_event_batch(orc):
     _assign_parity(orc, synth.uneven_batch(n_events=6, lo=10, hi=800, seed=303))
 
 
-def _check_fit_parity(gpar, gcov, gchi2, gndf, opar, ocov, ochi2, ondf, ok):
+def _check_fit_parity(gpar, gcov, gchi2, gndf, opar, ocov, ochi2, ondf, ok, bars=(1e-5, 1e-5, 1e-5)):
     """Fit bar per quantity, on the tracks that both sides fitted: the five
     parameters within 1e-5 max(|p|, s); the 15 covariance terms within 1e-5
     of sqrt(C_ii C_jj) (a relative error for the diagonal, on the scale of
     the variances for the correlations); chi2 within 1e-5 max(chi2, 1);
-    identical ndf."""
+    identical ndf.  bars = (parameters, covariance, chi2) replaces the three
+    1e-5 bars."""
     rel = np.abs(gpar - opar) / np.maximum(np.abs(opar), SCALE)
     d = ocov[:, [0, 5, 9, 12, 14]]
     iu = [(i, j) for i in range(5) for j in range(i, 5)]
@@ -162,9 +163,9 @@ def _check_fit_parity(gpar, gcov, gchi2, gndf, opar, ocov, ochi2, ondf, ok):
         print(f"  {name:10s} median {np.median(rel[ok, i]):.2e} max {rel[ok, i].max():.2e}")
     print(f"  cov terms max {crel[ok].max(0)}")
     print(f"  chi2 median {np.median(chrel[ok]):.2e} max {chrel[ok].max():.2e}")
-    assert np.all(rel[ok] <= 1e-5), rel[ok].max(0)
-    assert np.all(crel[ok] <= 1e-5), crel[ok].max(0)
-    assert np.all(chrel[ok] <= 1e-5), chrel[ok].max()
+    assert np.all(rel[ok] <= bars[0]), rel[ok].max(0)
+    assert np.all(crel[ok] <= bars[1]), crel[ok].max(0)
+    assert np.all(chrel[ok] <= bars[2]), chrel[ok].max()
     assert np.array_equal(gndf[ok], ondf[ok])
 
 
@@ -236,6 +237,37 @@ def test_fit_parity_found_tracks(orc):
     ok = ondf > 0
     _check_fit_parity(par.cpu().numpy().astype(np.float64), cov.cpu().numpy().astype(np.float64),
                       chi2.cpu().numpy().astype(np.float64), gndf, opar, ocov, ochi2, ondf, ok)
+
+
+def test_fit_fp32_parity_found_tracks(orc):
+    """tpc_fit_tracks_fp32 (FP32 covariance, FP64 redo of cancelling
+    updates) on every track the pipeline finds in a noisy event, against the
+    FP64 oracle on the same hit lists, at its own bars: parameters within
+    1e-4 max(|p|, s) and within 0.05 of their own sigma, covariance terms
+    and chi2 within 2e-3 (measured on the host: 5.8e-5, 0.034 sigma, 8e-4,
+    7.8e-4); the float-float fit meets 1e-5 on the same tracks.  The FP64
+    redo is exercised."""
+    ev = synth.central_event(n_tracks=2000, seed=101)
+    toc, off, hits, st, tr = gpu_find(ev)
+    T = len(off) - 1
+    d_off = torch.from_numpy(off.astype(np.int32)).cuda()
+    d_hits = torch.from_numpy(hits.astype(np.int32)).cuda()
+    n0 = tr.stats().n_fp64_updates
+    par, cov, chi2, ndf = tr.fit(d_off, d_hits, T, precision="fp32")
+    torch.cuda.synchronize()
+    tr.check()
+    n_redo = tr.stats().n_fp64_updates - n0
+    opar, ocov, ochi2, ondf = orc.fit_tracks(ev.y, ev.z, ev.row, ev.sector_of_cluster(), off, hits)
+    gndf = ndf.cpu().numpy()
+    assert np.array_equal(gndf <= 0, ondf <= 0)
+    ok = ondf > 0
+    gpar = par.cpu().numpy().astype(np.float64)
+    print("FP32 covariance with FP64 redos:", n_redo, "redos")
+    _check_fit_parity(gpar, cov.cpu().numpy().astype(np.float64), chi2.cpu().numpy().astype(np.float64),
+                      gndf, opar, ocov, ochi2, ondf, ok, bars=(1e-4, 2e-3, 2e-3))
+    in_sigma = np.abs(gpar - opar) / np.sqrt(ocov[:, [0, 5, 9, 12, 14]])
+    assert in_sigma[ok].max() <= 0.05, in_sigma[ok].max(0)
+    assert n_redo > 0
 
 
 def test_empty_input():
