@@ -450,7 +450,7 @@ def clusterize_bench(torch, tpc, dev, steps, ev):
 
 
 EXTRA_NAMES = ("batched_vs_plain", "adjoint", "clusterize", "field_adjoint", "kf_variants", "sides",
-               "pileup_frame")
+               "pileup_frame", "fit_precision")
 
 
 def parse():
@@ -960,8 +960,25 @@ def run_only(args):
            "field_adjoint": lambda: field_adjoint_bench(torch, tpc, dev, k),
            "sides": lambda: sides_bench(torch, tpc, dev, k),
            "kf_variants": lambda: kf_variants_bench(torch, tpc, dev, k),
-           "pileup_frame": lambda: pileup_bench(torch, tpc, dev, 2)}
+           "pileup_frame": lambda: pileup_bench(torch, tpc, dev, 2),
+           "fit_precision": lambda: central_fit_precision(torch, tpc, dev, k)}
     print(json.dumps({args.only: fns[args.only]()}), flush=True)
+
+
+def central_fit_precision(torch, tpc, dev, steps):
+    """fit_precision on its own: the central event is found once, then its
+    tracks are fitted by both precision modes."""
+    ev = make_event()
+    tr = tpc.Tracker(ev.n, 1, device=dev)
+    y = torch.from_numpy(ev.y).to(dev)
+    z = torch.from_numpy(ev.z).to(dev)
+    row = torch.from_numpy(ev.row.view(np.int16)).to(dev).view(torch.uint16)
+    off = torch.from_numpy(ev.evt_sector_off).to(dev)
+    tr.load(y, z, row, off, 1)
+    track_cap = 32768
+    find_out = tr.alloc_find_outputs(track_cap)
+    tr.find(out=find_out)
+    return fit_precision_bench(torch, tr, find_out, track_cap, dev, steps)
 
 
 def main():
