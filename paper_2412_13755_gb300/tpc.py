@@ -312,8 +312,8 @@ def tpc_find_tracks(ctx, track_of_cluster, trk_off, trk_hits, n_tracks_dev, stre
     _check(ctx, rc, "tpc_find_tracks")
 
 
-def tpc_fit_tracks(ctx, trk_off, trk_hits, n_tracks, n_tracks_dev, params, cov, chi2, ndf,
-                   stream=None, what="tpc_fit_tracks"):
+def _fit_call(what, ctx, trk_off, trk_hits, n_tracks, n_tracks_dev, params, cov, chi2, ndf, stream):
+    """tpc_fit_tracks and tpc_fit_tracks_fp32 take the same arguments."""
     _need(trk_off, torch.int32, "trk_off")
     _need(trk_hits, torch.int32, "trk_hits")
     for t, n in ((params, "params"), (cov, "cov"), (chi2, "chi2")):
@@ -328,12 +328,18 @@ def tpc_fit_tracks(ctx, trk_off, trk_hits, n_tracks, n_tracks_dev, params, cov, 
     _check(ctx, rc, what)
 
 
+def tpc_fit_tracks(ctx, trk_off, trk_hits, n_tracks, n_tracks_dev, params, cov, chi2, ndf,
+                   stream=None):
+    _fit_call("tpc_fit_tracks", ctx, trk_off, trk_hits, n_tracks, n_tracks_dev, params, cov, chi2, ndf,
+              stream)
+
+
 def tpc_fit_tracks_fp32(ctx, trk_off, trk_hits, n_tracks, n_tracks_dev, params, cov, chi2, ndf,
                         stream=None):
     """The fit with the covariance in FP32 and cancelling updates redone in
     FP64 (same arguments as tpc_fit_tracks)."""
-    tpc_fit_tracks(ctx, trk_off, trk_hits, n_tracks, n_tracks_dev, params, cov, chi2, ndf,
-                   stream=stream, what="tpc_fit_tracks_fp32")
+    _fit_call("tpc_fit_tracks_fp32", ctx, trk_off, trk_hits, n_tracks, n_tracks_dev, params, cov, chi2,
+              ndf, stream)
 
 
 def tpc_fit_tracks_ex(ctx, trk_off, trk_hits, n_tracks, n_tracks_dev, options, params, cov, chi2, ndf,
